@@ -1,0 +1,159 @@
+/*
+ * ns_adjoint.h - C ABI of the GB300 (sm_103a) unsteady discrete adjoint of the
+ * compressible Navier-Stokes equations (Talnikar, Wang & Laskowski, arXiv 1511.06959).
+ *
+ * Problem statement (section "Unsteady adjoint"): march w_t + div(F - F^v) = s
+ * (Eq. e:vector) forward in time, accumulate the time-averaged pressure-loss objective
+ * Jbar (Eq. e:pressure_loss), then integrate the adjoint backward from a zero terminal
+ * condition, recomputing primal states from checkpoints ("Implementation").  The
+ * stabilised adjoint adds div(lambda sigma_1 grad w_hat) where sigma_1 is the largest
+ * singular value of the growth matrix M = M1 - M2 ("Energy analysis").
+ *
+ * Discretisation: periodic structured box of nx*ny*nz cells (nz = 1 is a 2D box),
+ * central 2nd-order face fluxes, compact viscous stencil, classical RK4 with a constant
+ * dt; the adjoint is the exact transpose of that discrete map.
+ *
+ * Conventions shared by every call:
+ *  - Field pointers are DEVICE pointers owned by the caller, in SoA layout
+ *    [batch][5][nz][ny][nx] (x fastest), components (rho, rho u1, rho u2, rho u3, rho E)
+ *    for states and the same order for adjoints.  Scalar fields (sigma_1, nu) are
+ *    [batch][nz][ny][nx].  All must be 8-byte aligned (cudaMalloc memory is).
+ *  - Work is enqueued on the stream given to ns_create (or ns_set_stream) and is
+ *    asynchronous unless a call says it returns a host value.
+ *  - Every call returns NS_OK (0) or a negative NS_ERR_* code.  NS_ERR_ARG: null
+ *    context, null required pointer, bad size, or an aliasing rule broken.
+ *    NS_ERR_CUDA: a launch or allocation failed.  Faults found on the device
+ *    (non-finite values, an unstable adjoint viscosity) set a sticky error word
+ *    that ns_last_error() reads back.
+ *  - A context owns only its workspace (stage buffers and reduction scratch,
+ *    allocated by ns_create), never the caller's fields.  One context must not be
+ *    used from two host threads at once.
+ */
+#ifndef NS_ADJOINT_H
+#define NS_ADJOINT_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NS_OK 0
+#define NS_ERR_ARG (-1)
+#define NS_ERR_BUDGET (-2)
+#define NS_ERR_NONFINITE (-3)
+#define NS_ERR_UNSTABLE (-4)
+#define NS_ERR_CUDA (-5)
+
+#define NS_FP64 0  /* every flux, transpose and stage state in FP64 */
+#define NS_MIXED 1 /* fluxes, transposes and stage states in FP32; w, adjoint, objective,
+                      reductions and time accumulation in FP64 */
+
+typedef struct {
+  int nx, ny, nz;   /* cells per direction; nz = 1 is a 2D box */
+  int batch;        /* independent boxes, leading dimension of every field */
+  double dx, dy, dz;/* cell sizes */
+  double gamma;     /* ratio of specific heats (1.4), Eq. (e:navier) */
+  double mu;        /* constant dynamic viscosity, Eq. (e:navier) */
+  double Pr;        /* Prandtl number (0.72); heat flux alpha = gamma mu / Pr */
+  double dt;        /* constant RK4 time step */
+  int precision;    /* NS_FP64 or NS_MIXED */
+  int plane_i;      /* objective plane = x-face between cell columns plane_i-1, plane_i */
+  double pt_in;     /* reference stagnation pressure p_t,in of Eq. (e:pressure_loss) */
+} ns_params;
+
+typedef struct ns_ctx ns_ctx;
+
+/* Create a context: validates params, allocates the workspace (5 stage-state fields
+ * of the precision's stage type plus reduction scratch) on the current device.
+ * stream: a cudaStream_t (NULL = default stream). */
+int ns_create(const ns_params* p, void* stream, ns_ctx** out);
+void ns_destroy(ns_ctx* ctx);
+int ns_set_stream(ns_ctx* ctx, void* stream);
+int ns_set_dt(ns_ctx* ctx, double dt);
+/* Bytes of device workspace this context holds. */
+size_t ns_workspace_bytes(const ns_ctx* ctx);
+
+/* R = R(w) + s: the semi-discrete right-hand side (Eq. e:vector with source s,
+ * section "Unsteady adjoint").  s may be NULL.  R must not alias w. */
+int ns_rhs(ns_ctx* ctx, const double* w, const double* s, double* R);
+
+/* Rd = (dR/dw)(w) wd: the tangent of the residual (test support for the
+ * dot-product identity).  FP64 in both precision modes. */
+int ns_rhs_tangent(ns_ctx* ctx, const double* w, const double* wd, double* Rd);
+
+/* out = (dR/dw)(w)^T a + L_nu a: the transposed residual Jacobian, the discrete form
+ * of the A_kji, A^v_kji and D_kjil terms of the adjoint equation (section "Unsteady
+ * adjoint"), plus the added adjoint viscosity div(nu grad a) when nu != NULL
+ * (section "Energy analysis", stabilised adjoint).  out must not alias w or a. */
+int ns_rhs_transpose(ns_ctx* ctx, const double* w, const double* a, const float* nu,
+                     double* out);
+
+/* w_out = RK4 step of w_in with source s (may be NULL).  w_out must not alias w_in. */
+int ns_primal_step(ns_ctx* ctx, const double* w_in, const double* s, double* w_out);
+
+/* Tangent of one RK4 step (FP64): wd_out = d(w^{n+1})/d(w^n) wd_in + d/ds sd.
+ * s is the primal source (may be NULL), sd its perturbation (may be NULL). */
+int ns_tangent_step(ns_ctx* ctx, const double* w_n, const double* s, const double* wd_in,
+                    const double* sd, double* wd_out);
+
+/* Discrete adjoint of one RK4 step ("Implementation": the adjoint of the discrete
+ * scheme, with the primal stage states recomputed from w_n):
+ *   lam_n = (d w^{n+1} / d w^n)^T lam_np1
+ * nu: per-cell added adjoint viscosity (NULL = none), applied in each of the four
+ *     stage products.
+ * sbar_acc: if not NULL, sbar_acc += sum of the four stage seeds; the source
+ *     sensitivity dJ/ds of a time-constant source is the final sbar_acc.
+ * lam_n must not alias lam_np1 or w_n. */
+int ns_adjoint_step(ns_ctx* ctx, const double* w_n, const double* s, const double* lam_np1,
+                    const float* nu, double* lam_n, double* sbar_acc);
+
+/* Pressure loss on the plane (Eq. e:pressure_loss, instantaneous plane average):
+ *   J_acc[b] += weight * J(w_b)  for each box b (device array of batch doubles),
+ *   lam += weight * dJ/dw        if lam != NULL (only the two plane columns change).
+ * FP64 in both modes; a non-finite J sets NS_ERR_NONFINITE. */
+int ns_objective(ns_ctx* ctx, const double* w, double weight, double* J_acc, double* lam);
+
+/* sigma_1 per cell: the largest singular value of M = M1 - M2 built from central
+ * differences of rho, u, p, a, b (section "Energy analysis", closed forms of M1 and M2;
+ * for nz = 1 the (rho, u1, u2, p) block).  stats (device, may be NULL) receives
+ * [batch][2] = (max, mean) per box. */
+int ns_growth_sigma1(ns_ctx* ctx, const double* w, float* sigma1, double* stats);
+
+/* nu = lambda * sigma_1 where sigma_1 > tau, else 0 (section "Energy analysis":
+ * the lambda sigma_1 coefficient; tau = 0 is the paper's rule).  lambda has units of
+ * length^2.  If dt * nu * sum_d 4/dx_d^2 exceeds the RK4 real-axis limit 2.78 in any
+ * cell, NS_ERR_UNSTABLE is set in the sticky error word. */
+int ns_add_adjoint_viscosity(ns_ctx* ctx, const float* sigma1, double lambda, double tau,
+                             float* nu);
+
+/* out += L_nu a = div(nu grad a) per component, nu_face = mean of the two cells
+ * (the discrete added-viscosity operator alone). */
+int ns_apply_adjoint_viscosity(ns_ctx* ctx, const float* nu, const double* a, double* out);
+
+/* Adjoint energy E[b] = sum_cells v_hat . v_hat dV with w_hat = T^T v_hat, T = S V
+ * (section "Symmetrization"; "Energy analysis" defines E_vhat).  E: device array of
+ * batch doubles, overwritten.  A non-finite value sets NS_ERR_NONFINITE. */
+int ns_adjoint_energy(ns_ctx* ctx, const double* w, const double* lam, double* E);
+
+/* out[m] = <a, phi_m> for m < nphi over n elements (FP64, deterministic).
+ * phi is [nphi][n]; out is a device array of nphi doubles, overwritten. */
+int ns_dot(ns_ctx* ctx, const double* a, const double* phi, int nphi, size_t n, double* out);
+
+/* s = sum_m theta[m] phi_m over n elements (device theta[nphi], phi[nphi][n]). */
+int ns_combine(ns_ctx* ctx, const double* theta, const double* phi, int nphi, size_t n,
+               double* s);
+
+/* max over all cells of |u| + c; writes one double to the device pointer out. */
+int ns_max_wave_speed(ns_ctx* ctx, const double* w, double* out);
+
+/* Synchronises the stream, then returns and clears the sticky device error word
+ * (NS_OK, NS_ERR_NONFINITE or NS_ERR_UNSTABLE). */
+int ns_last_error(ns_ctx* ctx);
+const char* ns_error_string(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NS_ADJOINT_H */

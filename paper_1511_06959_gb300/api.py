@@ -1,0 +1,233 @@
+"""Thin Python binding of the C ABI in include/ns_adjoint.h.
+
+Argument marshalling only: torch CUDA tensors are passed as raw device pointers and
+every step runs in the CUDA library.  Importing this module loads
+``libns_adjoint.so`` and raises if it has not been built (there is no CPU fallback).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libns_adjoint.so")
+
+NS_OK = 0
+NS_ERR_ARG = -1
+NS_ERR_BUDGET = -2
+NS_ERR_NONFINITE = -3
+NS_ERR_UNSTABLE = -4
+NS_ERR_CUDA = -5
+NS_FP64 = 0
+NS_MIXED = 1
+
+EXPORTED = [
+    "ns_create", "ns_destroy", "ns_set_stream", "ns_set_dt", "ns_workspace_bytes", "ns_rhs",
+    "ns_rhs_tangent", "ns_rhs_transpose", "ns_primal_step", "ns_tangent_step", "ns_adjoint_step",
+    "ns_objective", "ns_growth_sigma1", "ns_add_adjoint_viscosity", "ns_apply_adjoint_viscosity",
+    "ns_adjoint_energy", "ns_dot", "ns_combine", "ns_max_wave_speed", "ns_last_error",
+    "ns_error_string",
+]
+
+
+class NsParams(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("batch", ctypes.c_int),
+        ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double),
+        ("gamma", ctypes.c_double), ("mu", ctypes.c_double), ("Pr", ctypes.c_double),
+        ("dt", ctypes.c_double), ("precision", ctypes.c_int), ("plane_i", ctypes.c_int),
+        ("pt_in", ctypes.c_double),
+    ]
+
+
+class NsError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        msg = _lib().ns_error_string(code).decode() if _LIB is not None else str(code)
+        super().__init__(f"{where}: {msg} ({code})")
+        self.code = code
+
+
+_LIB = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load the CUDA library and declare its signatures."""
+    if not os.path.exists(path):
+        raise RuntimeError(
+            f"CUDA library not built: {path} is missing (run paper_1511_06959_gb300.build)")
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    I = ctypes.c_int
+    D = ctypes.c_double
+    S = ctypes.c_size_t
+    sig = {
+        "ns_create": ([ctypes.POINTER(NsParams), P, ctypes.POINTER(P)], I),
+        "ns_destroy": ([P], None),
+        "ns_set_stream": ([P, P], I),
+        "ns_set_dt": ([P, D], I),
+        "ns_workspace_bytes": ([P], S),
+        "ns_rhs": ([P, P, P, P], I),
+        "ns_rhs_tangent": ([P, P, P, P], I),
+        "ns_rhs_transpose": ([P, P, P, P, P], I),
+        "ns_primal_step": ([P, P, P, P], I),
+        "ns_tangent_step": ([P, P, P, P, P, P], I),
+        "ns_adjoint_step": ([P, P, P, P, P, P, P], I),
+        "ns_objective": ([P, P, D, P, P], I),
+        "ns_growth_sigma1": ([P, P, P, P], I),
+        "ns_add_adjoint_viscosity": ([P, P, D, D, P], I),
+        "ns_apply_adjoint_viscosity": ([P, P, P, P], I),
+        "ns_adjoint_energy": ([P, P, P, P], I),
+        "ns_dot": ([P, P, P, I, S, P], I),
+        "ns_combine": ([P, P, P, I, S, P], I),
+        "ns_max_wave_speed": ([P, P, P], I),
+        "ns_last_error": ([P], I),
+        "ns_error_string": ([I], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    return lib
+
+
+def _lib() -> ctypes.CDLL:
+    global _LIB
+    if _LIB is None:
+        _LIB = load_library()
+    return _LIB
+
+
+def _ptr(t, dtype=None):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"expected {dtype}, got {t.dtype}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _check(code: int, where: str):
+    if code != NS_OK:
+        raise NsError(code, where)
+
+
+class Solver:
+    """One context of the C library: a periodic box (or a batch of boxes) with fixed
+    physical parameters, precision and time step."""
+
+    def __init__(self, nx, ny, nz, dx, gamma=1.4, mu=0.0, Pr=0.72, dt=0.0, precision=NS_FP64,
+                 plane_i=0, pt_in=1.0, batch=1, stream=None):
+        self.lib = _lib()
+        d = dx if isinstance(dx, (tuple, list)) else (dx, dx, dx)
+        self.params = NsParams(nx, ny, nz, batch, d[0], d[1], d[2], gamma, mu, Pr, dt,
+                               precision, plane_i, pt_in)
+        self.shape = (batch, 5, nz, ny, nx)
+        self.cells = nx * ny * nz
+        self.batch = batch
+        self._ctx = ctypes.c_void_p()
+        st = stream if stream is not None else torch.cuda.current_stream()
+        _check(self.lib.ns_create(ctypes.byref(self.params), ctypes.c_void_p(st.cuda_stream),
+                                  ctypes.byref(self._ctx)), "ns_create")
+
+    def close(self):
+        if self._ctx:
+            self.lib.ns_destroy(self._ctx)
+            self._ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def dt(self):
+        return self.params.dt
+
+    def set_dt(self, dt):
+        self.params.dt = dt
+        _check(self.lib.ns_set_dt(self._ctx, dt), "ns_set_dt")
+
+    def set_stream(self, stream):
+        _check(self.lib.ns_set_stream(self._ctx, ctypes.c_void_p(stream.cuda_stream)), "ns_set_stream")
+
+    def workspace_bytes(self):
+        return int(self.lib.ns_workspace_bytes(self._ctx))
+
+    # --- field operations -------------------------------------------------------
+    def rhs(self, w, R, s=None):
+        _check(self.lib.ns_rhs(self._ctx, _ptr(w, torch.float64), _ptr(s, torch.float64),
+                               _ptr(R, torch.float64)), "ns_rhs")
+
+    def rhs_tangent(self, w, wd, Rd):
+        _check(self.lib.ns_rhs_tangent(self._ctx, _ptr(w, torch.float64), _ptr(wd, torch.float64),
+                                       _ptr(Rd, torch.float64)), "ns_rhs_tangent")
+
+    def rhs_transpose(self, w, a, out, nu=None):
+        _check(self.lib.ns_rhs_transpose(self._ctx, _ptr(w, torch.float64), _ptr(a, torch.float64),
+                                         _ptr(nu, torch.float32), _ptr(out, torch.float64)),
+               "ns_rhs_transpose")
+
+    def primal_step(self, w_in, w_out, s=None):
+        _check(self.lib.ns_primal_step(self._ctx, _ptr(w_in, torch.float64), _ptr(s, torch.float64),
+                                       _ptr(w_out, torch.float64)), "ns_primal_step")
+
+    def tangent_step(self, w, wd_in, wd_out, s=None, sd=None):
+        _check(self.lib.ns_tangent_step(self._ctx, _ptr(w, torch.float64), _ptr(s, torch.float64),
+                                        _ptr(wd_in, torch.float64), _ptr(sd, torch.float64),
+                                        _ptr(wd_out, torch.float64)), "ns_tangent_step")
+
+    def adjoint_step(self, w_n, lam_np1, lam_n, s=None, nu=None, sbar=None):
+        _check(self.lib.ns_adjoint_step(self._ctx, _ptr(w_n, torch.float64), _ptr(s, torch.float64),
+                                        _ptr(lam_np1, torch.float64), _ptr(nu, torch.float32),
+                                        _ptr(lam_n, torch.float64), _ptr(sbar, torch.float64)),
+               "ns_adjoint_step")
+
+    def objective(self, w, J_acc, weight=1.0, lam=None):
+        _check(self.lib.ns_objective(self._ctx, _ptr(w, torch.float64), float(weight),
+                                     _ptr(J_acc, torch.float64), _ptr(lam, torch.float64)),
+               "ns_objective")
+
+    def growth_sigma1(self, w, sigma1, stats=None):
+        _check(self.lib.ns_growth_sigma1(self._ctx, _ptr(w, torch.float64), _ptr(sigma1, torch.float32),
+                                         _ptr(stats, torch.float64)), "ns_growth_sigma1")
+
+    def add_adjoint_viscosity(self, sigma1, lam_coef, nu, tau=0.0):
+        _check(self.lib.ns_add_adjoint_viscosity(self._ctx, _ptr(sigma1, torch.float32), float(lam_coef),
+                                                 float(tau), _ptr(nu, torch.float32)),
+               "ns_add_adjoint_viscosity")
+
+    def apply_adjoint_viscosity(self, nu, a, out):
+        _check(self.lib.ns_apply_adjoint_viscosity(self._ctx, _ptr(nu, torch.float32),
+                                                   _ptr(a, torch.float64), _ptr(out, torch.float64)),
+               "ns_apply_adjoint_viscosity")
+
+    def adjoint_energy(self, w, lam, E):
+        _check(self.lib.ns_adjoint_energy(self._ctx, _ptr(w, torch.float64), _ptr(lam, torch.float64),
+                                          _ptr(E, torch.float64)), "ns_adjoint_energy")
+
+    def dot(self, a, phi, out):
+        nphi = phi.shape[0]
+        n = a.numel()
+        if phi.numel() != nphi * n:
+            raise ValueError("phi must be [nphi, a.numel()]")
+        _check(self.lib.ns_dot(self._ctx, _ptr(a, torch.float64), _ptr(phi, torch.float64), nphi, n,
+                               _ptr(out, torch.float64)), "ns_dot")
+
+    def combine(self, theta, phi, s):
+        nphi = phi.shape[0]
+        n = s.numel()
+        _check(self.lib.ns_combine(self._ctx, _ptr(theta, torch.float64), _ptr(phi, torch.float64), nphi,
+                                   n, _ptr(s, torch.float64)), "ns_combine")
+
+    def max_wave_speed(self, w, out):
+        _check(self.lib.ns_max_wave_speed(self._ctx, _ptr(w, torch.float64), _ptr(out, torch.float64)),
+               "ns_max_wave_speed")
+
+    def last_error(self) -> int:
+        return int(self.lib.ns_last_error(self._ctx))

@@ -1,0 +1,446 @@
+// Transposed residual Jacobian, fused into one stage of the RK4 discrete adjoint
+// (section "Unsteady adjoint": the A_kji, A^v_kji, D_kjil terms; "Implementation":
+// the adjoint of the discrete scheme; "Energy analysis": the added viscosity).
+//
+// For the face flux Phi = (F_L + F_R)/2 - F^v of ns_rhs.cu the transpose is gathered
+// per cell c from quantities built per face f = (L, R) in direction d:
+//   Fb   = (a_L - a_R) / dx_d                                (adjoint of F^v at f)
+//   s_j  = Fb[1+j] + Fb[4] uf_j                              (adjoint of sigma_dj)
+//   normal gradient adjoint  nb_k = mu s_k + [k = d] mu s_d / 3,  nb_e = alpha Fb[4]
+//   face-velocity adjoint    ub_j = Fb[4] sigma_dj           (primal stress row d)
+// The tangential gradient adjoints of a face only ever hit u_d (mu s_l) and u_l
+// (-2/3 mu s_d) for l != d, so per cell it suffices to sum s over the two faces in
+// each direction, S_d(c) = s(c - e_d/2) + s(c + e_d/2), and
+//   T[k][l] = mu S_k[l] (k != l),   T[l][l] = -2/3 mu sum_{d != l} S_d[d]
+//   ubar_k(c) += (T[k][l](c - e_l) - T[k][l](c + e_l)) / (4 dx_l).
+// The convective part is sum_d A_d(w_c)^T (a(c+e_d) - a(c-e_d)) / (2 dx_d).  The sum of
+// primitive adjoints is then pulled back to conservative variables.
+//
+// Epilogue (FP64): lacc = (init ? lam : lacc) + g;  Anext = cl lam + cg g;  sbar += a.
+#include <type_traits>
+
+#include "ns_common.cuh"
+#include "ns_kernels.h"
+
+namespace ns {
+
+namespace {
+
+template <class CT, class TIN>
+__device__ __forceinline__ void fill_prims(CT* __restrict__ sq, const GridDesc& g, int b, int k,
+                                           int x0, int y0, const TIN* __restrict__ W) {
+  const int kz = wrap(k, g.nz);
+  const size_t boxoff = (size_t)b * 5 * g.cells + (size_t)kz * g.plane;
+  for (int t = threadIdx.x; t < SP; t += NT) {
+    const int ly = t / SX;
+    const int lx = t - ly * SX;
+    const size_t o = boxoff + (size_t)wrap(y0 + ly - 1, g.ny) * g.nx + wrap(x0 + lx - 1, g.nx);
+    const CT r = CT(W[o]);
+    const CT ir = CT(1) / r;
+    const CT u0 = CT(W[o + g.cells]) * ir;
+    const CT u1 = CT(W[o + 2 * g.cells]) * ir;
+    const CT u2 = CT(W[o + 3 * g.cells]) * ir;
+    sq[0 * SP + t] = r;
+    sq[1 * SP + t] = u0;
+    sq[2 * SP + t] = u1;
+    sq[3 * SP + t] = u2;
+    sq[4 * SP + t] = CT(W[o + 4 * g.cells]) * ir - CT(0.5) * (u0 * u0 + u1 * u1 + u2 * u2);
+  }
+}
+
+template <class CT, class TA>
+__device__ __forceinline__ void fill_adj(CT* __restrict__ sa, const GridDesc& g, int b, int k,
+                                         int x0, int y0, const TA* __restrict__ A, double ca) {
+  const int kz = wrap(k, g.nz);
+  const size_t boxoff = (size_t)b * 5 * g.cells + (size_t)kz * g.plane;
+  for (int t = threadIdx.x; t < SP; t += NT) {
+    const int ly = t / SX;
+    const int lx = t - ly * SX;
+    const size_t o = boxoff + (size_t)wrap(y0 + ly - 1, g.ny) * g.nx + wrap(x0 + lx - 1, g.nx);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) sa[v * SP + t] = CT(ca * (double)A[o + v * g.cells]);
+  }
+}
+
+// s-vector of the face between shared positions iL (slot of QL/AL) and iR.
+template <int D, class CT>
+__device__ __forceinline__ void face_s(const Coef<CT>& c, const CT* QL, const CT* AL, int iL,
+                                       const CT* QR, const CT* AR, int iR, CT s[3], CT& fb4) {
+  fb4 = (AL[4 * SP + iL] - AR[4 * SP + iR]) * c.idx[D];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const CT fb = (AL[(1 + j) * SP + iL] - AR[(1 + j) * SP + iR]) * c.idx[D];
+    const CT uf = CT(0.5) * (QL[(1 + j) * SP + iL] + QR[(1 + j) * SP + iR]);
+    s[j] = fb + fb4 * uf;
+  }
+}
+
+// Primal stress row D at a face from the two cells' primitives and the tangential face
+// gradients of (u1, u2, u3) along T1 = (D+1)%3, T2 = (D+2)%3.
+template <int D, class CT>
+__device__ __forceinline__ void face_stress(const Coef<CT>& c, const CT* qL, const CT* qR,
+                                            const CT* gt1, const CT* gt2, CT sig[3]) {
+  constexpr int T1 = (D + 1) % 3, T2 = (D + 2) % 3;
+  CT g[3][3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    g[k][D] = (qR[k] - qL[k]) * c.idx[D];
+    g[k][T1] = gt1[k];
+    g[k][T2] = gt2[k];
+  }
+  const CT div = g[0][0] + g[1][1] + g[2][2];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) sig[j] = c.mu * (g[j][D] + g[D][j]);
+  sig[D] = sig[D] - CT(2.0 / 3.0) * c.mu * div;
+}
+
+// 7-value packet of a face: nb[0..2] (u), nb[3] (e), ub[0..2].
+template <int D, class CT>
+__device__ __forceinline__ void face_packet(const Coef<CT>& c, const CT* QL, const CT* AL, int iL,
+                                            const CT* QR, const CT* AR, int iR, const CT* gt1,
+                                            const CT* gt2, CT pk[7]) {
+  CT s[3], fb4;
+  face_s<D>(c, QL, AL, iL, QR, AR, iR, s, fb4);
+  CT uL[3], uR[3], sig[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    uL[j] = QL[(1 + j) * SP + iL];
+    uR[j] = QR[(1 + j) * SP + iR];
+  }
+  face_stress<D>(c, uL, uR, gt1, gt2, sig);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) pk[k] = c.mu * s[k];
+  pk[D] = pk[D] + CT(1.0 / 3.0) * c.mu * s[D];
+  pk[3] = c.alpha * fb4;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) pk[4 + j] = fb4 * sig[j];
+}
+
+template <class CT>
+__device__ __forceinline__ void xpacket(const CT* sQ, const CT* sA, const Coef<CT>& c, int sm,
+                                        int s0, int sp, int row, int fx, CT pk[7]) {
+  const int iL = row * SX + fx, iR = iL + 1;
+  const CT* Q0 = sQ + s0 * 5 * SP;
+  const CT* Qm = sQ + sm * 5 * SP;
+  const CT* Qp = sQ + sp * 5 * SP;
+  CT gy[3], gz[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const CT* p0 = Q0 + (1 + k) * SP;
+    gy[k] = (p0[iL + SX] - p0[iL - SX] + p0[iR + SX] - p0[iR - SX]) * c.i4dx[1];
+    gz[k] = (Qp[(1 + k) * SP + iL] - Qm[(1 + k) * SP + iL] + Qp[(1 + k) * SP + iR] -
+             Qm[(1 + k) * SP + iR]) * c.i4dx[2];
+  }
+  const CT* A0 = sA + s0 * 5 * SP;
+  face_packet<0>(c, Q0, A0, iL, Q0, A0, iR, gy, gz, pk);
+}
+
+template <class CT>
+__device__ __forceinline__ void ypacket(const CT* sQ, const CT* sA, const Coef<CT>& c, int sm,
+                                        int s0, int sp, int fy, int col, CT pk[7]) {
+  const int iL = fy * SX + col, iR = iL + SX;
+  const CT* Q0 = sQ + s0 * 5 * SP;
+  const CT* Qm = sQ + sm * 5 * SP;
+  const CT* Qp = sQ + sp * 5 * SP;
+  CT gz[3], gx[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const CT* p0 = Q0 + (1 + k) * SP;
+    gz[k] = (Qp[(1 + k) * SP + iL] - Qm[(1 + k) * SP + iL] + Qp[(1 + k) * SP + iR] -
+             Qm[(1 + k) * SP + iR]) * c.i4dx[2];
+    gx[k] = (p0[iL + 1] - p0[iL - 1] + p0[iR + 1] - p0[iR - 1]) * c.i4dx[0];
+  }
+  const CT* A0 = sA + s0 * 5 * SP;
+  face_packet<1>(c, Q0, A0, iL, Q0, A0, iR, gz, gx, pk);
+}
+
+template <class CT>
+__device__ __forceinline__ void zpacket(const CT* sQ, const CT* sA, const Coef<CT>& c, int sL,
+                                        int sR, int i, CT pk[7]) {
+  const CT* QL = sQ + sL * 5 * SP;
+  const CT* QR = sQ + sR * 5 * SP;
+  CT gx[3], gy[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const CT* a = QL + (1 + k) * SP;
+    const CT* bq = QR + (1 + k) * SP;
+    gx[k] = (a[i + 1] - a[i - 1] + bq[i + 1] - bq[i - 1]) * c.i4dx[0];
+    gy[k] = (a[i + SX] - a[i - SX] + bq[i + SX] - bq[i - SX]) * c.i4dx[1];
+  }
+  face_packet<2>(c, QL, sA + sL * 5 * SP, i, QR, sA + sR * 5 * SP, i, gx, gy, pk);
+}
+
+// In-plane S-vector sums for one plane slot: S_x valid for lx in [1, SX-2],
+// S_y valid for ly in [1, SY-2].  Layout sS[slot][6][SP]: (S_x[0..2], S_y[0..2]).
+template <class CT>
+__device__ __forceinline__ void fill_S(CT* sS, const CT* sQ, const CT* sA, const Coef<CT>& c,
+                                       int slot) {
+  const CT* Q = sQ + slot * 5 * SP;
+  const CT* A = sA + slot * 5 * SP;
+  CT* S = sS + slot * 6 * SP;
+  for (int t = threadIdx.x; t < SP; t += NT) {
+    const int ly = t / SX;
+    const int lx = t - ly * SX;
+    if (lx >= 1 && lx <= SX - 2) {
+      CT s1[3], s2[3], f;
+      face_s<0>(c, Q, A, t - 1, Q, A, t, s1, f);
+      face_s<0>(c, Q, A, t, Q, A, t + 1, s2, f);
+#pragma unroll
+      for (int j = 0; j < 3; ++j) S[j * SP + t] = s1[j] + s2[j];
+    }
+    if (ly >= 1 && ly <= SY - 2) {
+      CT s1[3], s2[3], f;
+      face_s<1>(c, Q, A, t - SX, Q, A, t, s1, f);
+      face_s<1>(c, Q, A, t, Q, A, t + SX, s2, f);
+#pragma unroll
+      for (int j = 0; j < 3; ++j) S[(3 + j) * SP + t] = s1[j] + s2[j];
+    }
+  }
+}
+
+// z-face s-vectors between plane slots sL and sR at every shared column.
+template <class CT>
+__device__ __forceinline__ void fill_Z(CT* Z, const CT* sQ, const CT* sA, const Coef<CT>& c,
+                                       int sL, int sR) {
+  const CT* QL = sQ + sL * 5 * SP;
+  const CT* AL = sA + sL * 5 * SP;
+  const CT* QR = sQ + sR * 5 * SP;
+  const CT* AR = sA + sR * 5 * SP;
+  for (int t = threadIdx.x; t < SP; t += NT) {
+    CT s[3], f;
+    face_s<2>(c, QL, AL, t, QR, AR, t, s, f);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) Z[j * SP + t] = s[j];
+  }
+}
+
+}  // namespace
+
+template <class CT, class TIN, class TA, class TST>
+__global__ void __launch_bounds__(NT) k_adj_stage(GridDesc g, Coef<CT> c, AdjArgs<TIN, TA, TST> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  CT* sQ = reinterpret_cast<CT*>(smem_raw);   // [3][5][SP] primal primitives
+  CT* sA = sQ + 3 * 5 * SP;                    // [3][5][SP] adjoint input a
+  CT* sS = sA + 3 * 5 * SP;                    // [3][6][SP] in-plane S sums
+  CT* sZ = sS + 3 * 6 * SP;                    // [2][3][SP] z-face s-vectors
+  CT* sFX = sZ + 2 * 3 * SP;                   // [7][TY][TX+1]
+  CT* sFY = sFX + 7 * TY * (TX + 1);           // [7][TY+1][TX]
+  const int tid = threadIdx.x;
+  const int tx = tid % TX, ty = tid / TX;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  const int b = blockIdx.z / g.nzchunks;
+  const int kz0 = (blockIdx.z % g.nzchunks) * g.kchunk;
+  const int kz1 = min(g.nz, kz0 + g.kchunk);
+  const int gx = x0 + tx, gy = y0 + ty;
+  const bool valid = gx < g.nx && gy < g.ny;
+  auto slot = [&](int k) { return (k - kz0 + 1) % 3; };
+  auto zslot = [&](int k) { return (k - kz0 + 1) & 1; };   // z-face k + 1/2
+
+  for (int k = kz0 - 1; k <= kz0 + 1; ++k) {
+    fill_prims<CT>(sQ + slot(k) * 5 * SP, g, b, k, x0, y0, a.W);
+    fill_adj<CT>(sA + slot(k) * 5 * SP, g, b, k, x0, y0, a.A, a.ca);
+  }
+  __syncthreads();
+  fill_S(sS, sQ, sA, c, slot(kz0 - 1));
+  fill_S(sS, sQ, sA, c, slot(kz0));
+  fill_Z(sZ + zslot(kz0 - 1) * 3 * SP, sQ, sA, c, slot(kz0 - 1), slot(kz0));
+  const int ic = (ty + 1) * SX + (tx + 1);
+  CT zlo[7], zhi[7];
+  zpacket(sQ, sA, c, slot(kz0 - 1), slot(kz0), ic, zlo);
+  __syncthreads();
+
+  for (int k = kz0; k < kz1; ++k) {
+    const int sm = slot(k - 1), s0 = slot(k), sp = slot(k + 1);
+    fill_S(sS, sQ, sA, c, sp);
+    fill_Z(sZ + zslot(k) * 3 * SP, sQ, sA, c, s0, sp);
+    {
+      CT pk[7];
+      xpacket(sQ, sA, c, sm, s0, sp, ty + 1, tx, pk);
+#pragma unroll
+      for (int v = 0; v < 7; ++v) sFX[(v * TY + ty) * (TX + 1) + tx] = pk[v];
+      ypacket(sQ, sA, c, sm, s0, sp, ty, tx + 1, pk);
+#pragma unroll
+      for (int v = 0; v < 7; ++v) sFY[(v * (TY + 1) + ty) * TX + tx] = pk[v];
+    }
+    zpacket(sQ, sA, c, s0, sp, ic, zhi);
+    if (tid < TX) {
+      CT pk[7];
+      ypacket(sQ, sA, c, sm, s0, sp, TY, tid + 1, pk);
+#pragma unroll
+      for (int v = 0; v < 7; ++v) sFY[(v * (TY + 1) + TY) * TX + tid] = pk[v];
+    } else if (tid < TX + TY) {
+      CT pk[7];
+      const int r = tid - TX;
+      xpacket(sQ, sA, c, sm, s0, sp, r + 1, TX, pk);
+#pragma unroll
+      for (int v = 0; v < 7; ++v) sFX[(v * TY + r) * (TX + 1) + TX] = pk[v];
+    }
+    __syncthreads();
+
+    if (valid) {
+      const CT* Q0 = sQ + s0 * 5 * SP;
+      const CT* A0 = sA + s0 * 5 * SP;
+      const CT* Am = sA + sm * 5 * SP;
+      const CT* Ap = sA + sp * 5 * SP;
+      const CT* S0 = sS + s0 * 6 * SP;
+      const CT* Sm = sS + sm * 6 * SP;
+      const CT* Sp = sS + sp * 6 * SP;
+      const CT* Zl = sZ + zslot(k - 1) * 3 * SP;
+      const CT* Zh = sZ + zslot(k) * 3 * SP;
+      // ---- viscous: primitive adjoints of (u1, u2, u3, e)
+      CT qb[4];
+      const CT h = CT(0.5);
+      {
+        const int fl = ty * (TX + 1) + tx;
+        const int yl = ty * TX + tx;
+#pragma unroll
+        for (int v = 0; v < 3; ++v) {
+          const CT xl = sFX[v * TY * (TX + 1) + fl], xh = sFX[v * TY * (TX + 1) + fl + 1];
+          const CT yl_ = sFY[v * (TY + 1) * TX + yl], yh = sFY[v * (TY + 1) * TX + yl + TX];
+          const CT uxl = sFX[(4 + v) * TY * (TX + 1) + fl], uxh = sFX[(4 + v) * TY * (TX + 1) + fl + 1];
+          const CT uyl = sFY[(4 + v) * (TY + 1) * TX + yl], uyh = sFY[(4 + v) * (TY + 1) * TX + yl + TX];
+          qb[v] = (xl - xh) * c.idx[0] + (yl_ - yh) * c.idx[1] + (zlo[v] - zhi[v]) * c.idx[2] +
+                  h * (uxl + uxh + uyl + uyh + zlo[4 + v] + zhi[4 + v]);
+        }
+        qb[3] = (sFX[3 * TY * (TX + 1) + fl] - sFX[3 * TY * (TX + 1) + fl + 1]) * c.idx[0] +
+                (sFY[3 * (TY + 1) * TX + yl] - sFY[3 * (TY + 1) * TX + yl + TX]) * c.idx[1] +
+                (zlo[3] - zhi[3]) * c.idx[2];
+      }
+      {
+        // tangential parts, T[k][l] differenced along l
+        const CT m = c.mu, m23 = CT(-2.0 / 3.0) * c.mu;
+        const int il = ic - 1, ir = ic + 1, idn = ic - SX, iup = ic + SX;
+        // S_z at a plane-k position = Zl + Zh
+        auto Sz = [&](int j, int i) { return Zl[j * SP + i] + Zh[j * SP + i]; };
+        // l = x (neighbours ic -+ 1): T[y][x] = mu S_y[x], T[z][x] = mu S_z[x],
+        //                            T[x][x] = -2/3 mu (S_y[y] + S_z[z])
+        qb[0] = qb[0] + m23 * ((S0[4 * SP + il] + Sz(2, il)) - (S0[4 * SP + ir] + Sz(2, ir))) * c.i4dx[0];
+        qb[1] = qb[1] + m * (S0[3 * SP + il] - S0[3 * SP + ir]) * c.i4dx[0];
+        qb[2] = qb[2] + m * (Sz(0, il) - Sz(0, ir)) * c.i4dx[0];
+        // l = y (neighbours ic -+ SX): T[x][y] = mu S_x[y], T[z][y] = mu S_z[y],
+        //                             T[y][y] = -2/3 mu (S_x[x] + S_z[z])
+        qb[0] = qb[0] + m * (S0[1 * SP + idn] - S0[1 * SP + iup]) * c.i4dx[1];
+        qb[1] = qb[1] + m23 * ((S0[0 * SP + idn] + Sz(2, idn)) - (S0[0 * SP + iup] + Sz(2, iup))) * c.i4dx[1];
+        qb[2] = qb[2] + m * (Sz(1, idn) - Sz(1, iup)) * c.i4dx[1];
+        // l = z (planes k -+ 1): T[x][z] = mu S_x[z], T[y][z] = mu S_y[z],
+        //                       T[z][z] = -2/3 mu (S_x[x] + S_y[y])
+        qb[0] = qb[0] + m * (Sm[2 * SP + ic] - Sp[2 * SP + ic]) * c.i4dx[2];
+        qb[1] = qb[1] + m * (Sm[5 * SP + ic] - Sp[5 * SP + ic]) * c.i4dx[2];
+        qb[2] = qb[2] + m23 * ((Sm[0 * SP + ic] + Sm[4 * SP + ic]) - (Sp[0 * SP + ic] + Sp[4 * SP + ic])) * c.i4dx[2];
+      }
+      // ---- convective part and pull-back to conservative variables
+      const CT rho = Q0[ic];
+      const CT u[3] = {Q0[SP + ic], Q0[2 * SP + ic], Q0[3 * SP + ic]};
+      const CT e = Q0[4 * SP + ic];
+      const CT ir_ = CT(1) / rho;
+      const CT Esp = e + h * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);   // rho E / rho
+      const CT p = c.gm1 * rho * e;
+      const CT rE = rho * Esp;
+      CT rb = CT(0), mb[3] = {CT(0), CT(0), CT(0)}, Eb = CT(0), pb = CT(0);
+      CT ub[3] = {qb[0], qb[1], qb[2]};
+      CT eb = qb[3];
+      const int nb_lo[3] = {ic - 1, ic - SX, ic};
+      const int nb_hi[3] = {ic + 1, ic + SX, ic};
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const CT* Alo = d == 2 ? Am : A0;
+        const CT* Ahi = d == 2 ? Ap : A0;
+        CT F[5];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) F[v] = (Ahi[v * SP + nb_hi[d]] - Alo[v * SP + nb_lo[d]]) * c.hidx[d];
+        const CT md = rho * u[d];
+        mb[d] = mb[d] + F[0] + F[1] * u[0] + F[2] * u[1] + F[3] * u[2];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) ub[j] = ub[j] + F[1 + j] * md;
+        pb = pb + F[1 + d] + F[4] * u[d];
+        Eb = Eb + F[4] * u[d];
+        ub[d] = ub[d] + F[4] * (rE + p);
+      }
+      rb = rb + c.gm1 * e * pb;
+      eb = eb + c.gm1 * rho * pb;
+      Eb = Eb + eb * ir_;
+      rb = rb - eb * Esp * ir_;
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        ub[j] = ub[j] - eb * u[j];
+        mb[j] = mb[j] + ub[j] * ir_;
+        rb = rb - ub[j] * u[j] * ir_;
+      }
+      CT gout[5] = {rb, mb[0], mb[1], mb[2], Eb};
+      const size_t o0 = (size_t)b * 5 * g.cells + (size_t)k * g.plane + (size_t)gy * g.nx + gx;
+      // ---- added adjoint viscosity L_nu a
+      if (a.nu) {
+        const size_t so = (size_t)b * g.cells;
+        const float* nub = a.nu + so;
+        const int kp = wrap(k + 1, g.nz), km = wrap(k - 1, g.nz);
+        const size_t pl = (size_t)k * g.plane;
+        const CT nc = CT(nub[pl + (size_t)gy * g.nx + gx]);
+        const CT nxm = CT(nub[pl + (size_t)gy * g.nx + wrap(gx - 1, g.nx)]);
+        const CT nxp = CT(nub[pl + (size_t)gy * g.nx + wrap(gx + 1, g.nx)]);
+        const CT nym = CT(nub[pl + (size_t)wrap(gy - 1, g.ny) * g.nx + gx]);
+        const CT nyp = CT(nub[pl + (size_t)wrap(gy + 1, g.ny) * g.nx + gx]);
+        const CT nzm = CT(nub[(size_t)km * g.plane + (size_t)gy * g.nx + gx]);
+        const CT nzp = CT(nub[(size_t)kp * g.plane + (size_t)gy * g.nx + gx]);
+        const CT ix2 = c.idx[0] * c.idx[0], iy2 = c.idx[1] * c.idx[1], iz2 = c.idx[2] * c.idx[2];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+          const CT* Av = A0 + v * SP;
+          const CT ac = Av[ic];
+          CT L = (h * (nc + nxp) * (Av[ic + 1] - ac) - h * (nc + nxm) * (ac - Av[ic - 1])) * ix2 +
+                 (h * (nc + nyp) * (Av[ic + SX] - ac) - h * (nc + nym) * (ac - Av[ic - SX])) * iy2 +
+                 (h * (nc + nzp) * (Ap[v * SP + ic] - ac) - h * (nc + nzm) * (ac - Am[v * SP + ic])) * iz2;
+          gout[v] = gout[v] + L;
+        }
+      }
+      // ---- epilogue
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        const size_t o = o0 + (size_t)v * g.cells;
+        const double gv = (double)gout[v];
+        const double lam = a.lam ? a.lam[o] : 0.0;
+        const double prev = a.lacc_init ? lam : a.lacc[o];
+        a.lacc[o] = prev + gv;
+        if (a.Anext) a.Anext[o] = (TST)(a.cl * lam + a.cg * gv);
+        if (a.sbar) a.sbar[o] += a.ca * (double)a.A[o];
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < 7; ++v) zlo[v] = zhi[v];
+    __syncthreads();
+    if (k + 1 < kz1) {
+      fill_prims<CT>(sQ + slot(k + 2) * 5 * SP, g, b, k + 2, x0, y0, a.W);
+      fill_adj<CT>(sA + slot(k + 2) * 5 * SP, g, b, k + 2, x0, y0, a.A, a.ca);
+      __syncthreads();
+    }
+  }
+}
+
+template <class CT>
+size_t adj_smem_bytes() {
+  return sizeof(CT) * (3 * 5 * SP * 2 + 3 * 6 * SP + 2 * 3 * SP + 7 * TY * (TX + 1) + 7 * (TY + 1) * TX);
+}
+
+template <class CT, class TIN, class TA, class TST>
+cudaError_t launch_adj_stage(const GridDesc& g, const Coef<CT>& c, const AdjArgs<TIN, TA, TST>& a,
+                             cudaStream_t st) {
+  const size_t smem = adj_smem_bytes<CT>();
+  auto kern = k_adj_stage<CT, TIN, TA, TST>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, g.batch * g.nzchunks);
+  kern<<<grid, NT, smem, st>>>(g, c, a);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_adj_stage<double, double, double, double>(
+    const GridDesc&, const Coef<double>&, const AdjArgs<double, double, double>&, cudaStream_t);
+template cudaError_t launch_adj_stage<float, double, double, float>(
+    const GridDesc&, const Coef<float>&, const AdjArgs<double, double, float>&, cudaStream_t);
+template cudaError_t launch_adj_stage<float, double, float, float>(
+    const GridDesc&, const Coef<float>&, const AdjArgs<double, float, float>&, cudaStream_t);
+template cudaError_t launch_adj_stage<float, float, double, float>(
+    const GridDesc&, const Coef<float>&, const AdjArgs<float, double, float>&, cudaStream_t);
+template cudaError_t launch_adj_stage<float, float, float, float>(
+    const GridDesc&, const Coef<float>&, const AdjArgs<float, float, float>&, cudaStream_t);
+
+}  // namespace ns

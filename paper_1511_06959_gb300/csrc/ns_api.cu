@@ -1,0 +1,375 @@
+// C-ABI entry points (include/ns_adjoint.h): argument checks, workspace ownership and
+// the sequencing of the fused stage kernels into RK4 primal, tangent and adjoint steps.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include "../../include/ns_adjoint.h"
+#include "ns_common.cuh"
+#include "ns_kernels.h"
+
+using ns::Coef;
+using ns::Dual;
+using ns::GridDesc;
+
+struct ns_ctx {
+  ns_params p;
+  cudaStream_t st;
+  GridDesc g;
+  Coef<double> cd;
+  Coef<float> cf;
+  Coef<Dual> cx;
+  size_t field;          // elements of one [batch][5][cells] field
+  void* stage[5];        // stage buffers (double in FP64 mode, float in MIXED mode)
+  double* tan[5];        // FP64 buffers of the tangent step, allocated on first use
+  double* scratch;       // reduction scratch
+  size_t scratch_n;
+  unsigned* err;         // sticky device error word
+  size_t ws_bytes;
+};
+
+namespace {
+
+template <class T>
+Coef<T> make_coef(const ns_params& p) {
+  Coef<T> c;
+  c.gamma = T(p.gamma);
+  c.gm1 = T(p.gamma - 1.0);
+  c.mu = T(p.mu);
+  c.alpha = T(p.gamma * p.mu / p.Pr);
+  const double d[3] = {p.dx, p.dy, p.dz};
+  for (int i = 0; i < 3; ++i) {
+    c.idx[i] = T(1.0 / d[i]);
+    c.i4dx[i] = T(0.25 / d[i]);
+    c.hidx[i] = T(0.5 / d[i]);
+  }
+  return c;
+}
+
+int cuerr(cudaError_t e) { return e == cudaSuccess ? NS_OK : NS_ERR_CUDA; }
+
+int choose_kchunk(const ns_params& p) {
+  const char* env = getenv("NS_KCHUNK");
+  if (env && atoi(env) > 0) return std::min(atoi(env), p.nz);
+  const long long cols = (long long)((p.nx + ns::TX - 1) / ns::TX) * ((p.ny + ns::TY - 1) / ns::TY) * p.batch;
+  const long long target = 8LL * 152;
+  long long chunks = (target + cols - 1) / cols;
+  if (chunks < 1) chunks = 1;
+  int k = (int)((p.nz + chunks - 1) / chunks);
+  k = std::max(k, 4);
+  return std::min(k, p.nz);
+}
+
+bool mixed(const ns_ctx* c) { return c->p.precision == NS_MIXED; }
+
+}  // namespace
+
+static int ensure_tangent_buffers(ns_ctx* c) {
+  for (int i = 0; i < 5; ++i) {
+    if (!c->tan[i]) {
+      if (cudaMalloc(&c->tan[i], c->field * sizeof(double)) != cudaSuccess) return NS_ERR_CUDA;
+      c->ws_bytes += c->field * sizeof(double);
+    }
+  }
+  return NS_OK;
+}
+
+template <class CT, class TST>
+static int primal_step_t(ns_ctx* c, const Coef<CT>& cf, const double* w, const double* s, double* wo,
+                         TST* Wa, TST* Wb) {
+  const double dt = c->p.dt;
+  cudaError_t e;
+  {
+    ns::StageArgs<double, TST> a{};
+    a.W = w; a.base = w; a.src = s; a.acc = wo; a.acc_init = 1; a.cacc = dt / 6.0;
+    a.Wout = Wa; a.cout = 0.5 * dt;
+    if ((e = ns::launch_rhs_stage<CT, double, TST>(c->g, cf, a, c->st)) != cudaSuccess) return NS_ERR_CUDA;
+  }
+  const TST* in[3] = {Wa, Wb, Wa};
+  TST* outs[3] = {Wb, Wa, nullptr};
+  const double cacc[3] = {dt / 3.0, dt / 3.0, dt / 6.0};
+  const double cout[3] = {0.5 * dt, dt, 0.0};
+  for (int i = 0; i < 3; ++i) {
+    ns::StageArgs<TST, TST> a{};
+    a.W = in[i]; a.base = w; a.src = s; a.acc = wo; a.acc_init = 0; a.cacc = cacc[i];
+    a.Wout = outs[i]; a.cout = cout[i];
+    if ((e = ns::launch_rhs_stage<CT, TST, TST>(c->g, cf, a, c->st)) != cudaSuccess) return NS_ERR_CUDA;
+  }
+  return NS_OK;
+}
+
+template <class CT, class TST>
+static int adjoint_step_t(ns_ctx* c, const Coef<CT>& cf, const double* w, const double* s,
+                          const double* lam, const float* nu, double* lo, double* sbar) {
+  const double dt = c->p.dt;
+  TST* W2 = (TST*)c->stage[0];
+  TST* W3 = (TST*)c->stage[1];
+  TST* W4 = (TST*)c->stage[2];
+  TST* Aa = (TST*)c->stage[3];
+  TST* Ab = (TST*)c->stage[4];
+  // recompute the stage states W2..W4 from w^n
+  {
+    ns::StageArgs<double, TST> a{};
+    a.W = w; a.base = w; a.src = s; a.Wout = W2; a.cout = 0.5 * dt;
+    if (ns::launch_rhs_stage<CT, double, TST>(c->g, cf, a, c->st) != cudaSuccess) return NS_ERR_CUDA;
+  }
+  {
+    ns::StageArgs<TST, TST> a{};
+    a.W = W2; a.base = w; a.src = s; a.Wout = W3; a.cout = 0.5 * dt;
+    if (ns::launch_rhs_stage<CT, TST, TST>(c->g, cf, a, c->st) != cudaSuccess) return NS_ERR_CUDA;
+    a.W = W3; a.Wout = W4; a.cout = dt;
+    if (ns::launch_rhs_stage<CT, TST, TST>(c->g, cf, a, c->st) != cudaSuccess) return NS_ERR_CUDA;
+  }
+  // transposed stages 4, 3, 2, 1
+  {
+    ns::AdjArgs<TST, double, TST> a{};
+    a.W = W4; a.A = lam; a.ca = dt / 6.0; a.nu = nu; a.lam = lam; a.lacc = lo; a.lacc_init = 1;
+    a.Anext = Aa; a.cl = dt / 3.0; a.cg = dt; a.sbar = sbar;
+    if (ns::launch_adj_stage<CT, TST, double, TST>(c->g, cf, a, c->st) != cudaSuccess) return NS_ERR_CUDA;
+  }
+  {
+    ns::AdjArgs<TST, TST, TST> a{};
+    a.W = W3; a.A = Aa; a.ca = 1.0; a.nu = nu; a.lam = lam; a.lacc = lo; a.lacc_init = 0;
+    a.Anext = Ab; a.cl = dt / 3.0; a.cg = 0.5 * dt; a.sbar = sbar;
+    if (ns::launch_adj_stage<CT, TST, TST, TST>(c->g, cf, a, c->st) != cudaSuccess) return NS_ERR_CUDA;
+    a.W = W2; a.A = Ab; a.Anext = Aa; a.cl = dt / 6.0; a.cg = 0.5 * dt;
+    if (ns::launch_adj_stage<CT, TST, TST, TST>(c->g, cf, a, c->st) != cudaSuccess) return NS_ERR_CUDA;
+  }
+  {
+    ns::AdjArgs<double, TST, TST> a{};
+    a.W = w; a.A = Aa; a.ca = 1.0; a.nu = nu; a.lam = lam; a.lacc = lo; a.lacc_init = 0;
+    a.Anext = nullptr; a.sbar = sbar;
+    if (ns::launch_adj_stage<CT, double, TST, TST>(c->g, cf, a, c->st) != cudaSuccess) return NS_ERR_CUDA;
+  }
+  return NS_OK;
+}
+
+extern "C" {
+
+const char* ns_error_string(int code) {
+  switch (code) {
+    case NS_OK: return "ok";
+    case NS_ERR_ARG: return "invalid argument";
+    case NS_ERR_BUDGET: return "memory budget too small";
+    case NS_ERR_NONFINITE: return "non-finite value detected";
+    case NS_ERR_UNSTABLE: return "adjoint viscosity exceeds the explicit stability limit";
+    case NS_ERR_CUDA: return "CUDA error";
+    default: return "unknown error";
+  }
+}
+
+int ns_create(const ns_params* p, void* stream, ns_ctx** out) {
+  if (!p || !out) return NS_ERR_ARG;
+  *out = nullptr;
+  if (p->nx < 1 || p->ny < 1 || p->nz < 1 || p->batch < 1) return NS_ERR_ARG;
+  if (!(p->dx > 0) || !(p->dy > 0) || !(p->dz > 0) || !(p->gamma > 1.0) || !(p->mu >= 0) ||
+      !(p->Pr > 0) || !(p->dt >= 0))
+    return NS_ERR_ARG;
+  if (p->precision != NS_FP64 && p->precision != NS_MIXED) return NS_ERR_ARG;
+  if ((long long)p->nx * p->ny > (1LL << 31) || (long long)p->nx * p->ny * p->nz > (1LL << 40))
+    return NS_ERR_ARG;
+  ns_ctx* c = (ns_ctx*)calloc(1, sizeof(ns_ctx));
+  if (!c) return NS_ERR_ARG;
+  c->p = *p;
+  c->st = (cudaStream_t)stream;
+  c->g.nx = p->nx;
+  c->g.ny = p->ny;
+  c->g.nz = p->nz;
+  c->g.batch = p->batch;
+  c->g.plane = (long long)p->nx * p->ny;
+  c->g.cells = c->g.plane * p->nz;
+  c->g.kchunk = choose_kchunk(*p);
+  c->g.nzchunks = (p->nz + c->g.kchunk - 1) / c->g.kchunk;
+  c->cd = make_coef<double>(*p);
+  c->cf = make_coef<float>(*p);
+  {
+    Coef<double> d = c->cd;
+    Coef<Dual>& x = c->cx;
+    x.gamma = Dual(d.gamma);
+    x.gm1 = Dual(d.gm1);
+    x.mu = Dual(d.mu);
+    x.alpha = Dual(d.alpha);
+    for (int i = 0; i < 3; ++i) {
+      x.idx[i] = Dual(d.idx[i]);
+      x.i4dx[i] = Dual(d.i4dx[i]);
+      x.hidx[i] = Dual(d.hidx[i]);
+    }
+  }
+  c->field = (size_t)5 * c->g.cells * p->batch;
+  const size_t esz = p->precision == NS_MIXED ? sizeof(float) : sizeof(double);
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < 5 && e == cudaSuccess; ++i) e = cudaMalloc(&c->stage[i], c->field * esz);
+  c->scratch_n = ns::diag_scratch_doubles(c->g, 256);
+  if (e == cudaSuccess) e = cudaMalloc(&c->scratch, c->scratch_n * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&c->err, sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->err, 0, sizeof(unsigned), c->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+  if (e != cudaSuccess) {
+    ns_destroy(c);
+    return NS_ERR_CUDA;
+  }
+  c->ws_bytes = 5 * c->field * esz + c->scratch_n * sizeof(double) + sizeof(unsigned);
+  *out = c;
+  return NS_OK;
+}
+
+void ns_destroy(ns_ctx* c) {
+  if (!c) return;
+  for (int i = 0; i < 5; ++i) {
+    if (c->stage[i]) cudaFree(c->stage[i]);
+    if (c->tan[i]) cudaFree(c->tan[i]);
+  }
+  if (c->scratch) cudaFree(c->scratch);
+  if (c->err) cudaFree(c->err);
+  free(c);
+}
+
+int ns_set_stream(ns_ctx* c, void* stream) {
+  if (!c) return NS_ERR_ARG;
+  c->st = (cudaStream_t)stream;
+  return NS_OK;
+}
+
+int ns_set_dt(ns_ctx* c, double dt) {
+  if (!c || !(dt >= 0)) return NS_ERR_ARG;
+  c->p.dt = dt;
+  return NS_OK;
+}
+
+size_t ns_workspace_bytes(const ns_ctx* c) { return c ? c->ws_bytes : 0; }
+
+int ns_rhs(ns_ctx* c, const double* w, const double* s, double* R) {
+  if (!c || !w || !R || (const double*)R == w) return NS_ERR_ARG;
+  if (mixed(c)) {
+    ns::StageArgs<double, float> a{};
+    a.W = w; a.src = s; a.acc = R; a.acc_init = 1; a.cacc = 1.0;
+    return cuerr(ns::launch_rhs_stage<float, double, float>(c->g, c->cf, a, c->st));
+  }
+  ns::StageArgs<double, double> a{};
+  a.W = w; a.src = s; a.acc = R; a.acc_init = 1; a.cacc = 1.0;
+  return cuerr(ns::launch_rhs_stage<double, double, double>(c->g, c->cd, a, c->st));
+}
+
+int ns_rhs_tangent(ns_ctx* c, const double* w, const double* wd, double* Rd) {
+  if (!c || !w || !wd || !Rd || Rd == w || Rd == wd) return NS_ERR_ARG;
+  int r = ensure_tangent_buffers(c);
+  if (r) return r;
+  ns::StageArgs<double, double> a{};
+  a.W = w; a.Wd = wd;
+  a.acc = c->tan[0]; a.accd = Rd; a.acc_init = 1; a.cacc = 1.0;
+  return cuerr(ns::launch_rhs_stage<Dual, double, double>(c->g, c->cx, a, c->st));
+}
+
+int ns_primal_step(ns_ctx* c, const double* w, const double* s, double* wo) {
+  if (!c || !w || !wo || wo == w || wo == s) return NS_ERR_ARG;
+  if (mixed(c))
+    return primal_step_t<float, float>(c, c->cf, w, s, wo, (float*)c->stage[0], (float*)c->stage[1]);
+  return primal_step_t<double, double>(c, c->cd, w, s, wo, (double*)c->stage[0], (double*)c->stage[1]);
+}
+
+int ns_tangent_step(ns_ctx* c, const double* w, const double* s, const double* wd, const double* sd,
+                    double* wdo) {
+  if (!c || !w || !wd || !wdo || wdo == wd || wdo == w) return NS_ERR_ARG;
+  int r = ensure_tangent_buffers(c);
+  if (r) return r;
+  const double dt = c->p.dt;
+  double *acc = c->tan[0], *Wa = c->tan[1], *Wb = c->tan[2], *Wda = c->tan[3], *Wdb = c->tan[4];
+  const double* Win[4] = {w, Wa, Wb, Wa};
+  const double* Wdin[4] = {wd, Wda, Wdb, Wda};
+  double* Wout[4] = {Wa, Wb, Wa, nullptr};
+  double* Wdout[4] = {Wda, Wdb, Wda, nullptr};
+  const double cacc[4] = {dt / 6.0, dt / 3.0, dt / 3.0, dt / 6.0};
+  const double cout[4] = {0.5 * dt, 0.5 * dt, dt, 0.0};
+  for (int i = 0; i < 4; ++i) {
+    ns::StageArgs<double, double> a{};
+    a.W = Win[i]; a.Wd = Wdin[i];
+    a.base = w; a.based = wd; a.src = s; a.srcd = sd;
+    a.acc = acc; a.accd = wdo; a.acc_init = i == 0; a.cacc = cacc[i];
+    a.Wout = Wout[i]; a.Woutd = Wdout[i]; a.cout = cout[i];
+    if (ns::launch_rhs_stage<Dual, double, double>(c->g, c->cx, a, c->st) != cudaSuccess) return NS_ERR_CUDA;
+  }
+  return NS_OK;
+}
+
+int ns_adjoint_step(ns_ctx* c, const double* w, const double* s, const double* lam, const float* nu,
+                    double* lo, double* sbar) {
+  if (!c || !w || !lam || !lo || lo == lam || lo == w || (sbar && (sbar == lo || sbar == lam)))
+    return NS_ERR_ARG;
+  if (mixed(c)) return adjoint_step_t<float, float>(c, c->cf, w, s, lam, nu, lo, sbar);
+  return adjoint_step_t<double, double>(c, c->cd, w, s, lam, nu, lo, sbar);
+}
+
+int ns_rhs_transpose(ns_ctx* c, const double* w, const double* a_, const float* nu, double* out) {
+  if (!c || !w || !a_ || !out || out == w || out == a_) return NS_ERR_ARG;
+  if (mixed(c)) {
+    ns::AdjArgs<double, double, float> a{};
+    a.W = w; a.A = a_; a.ca = 1.0; a.nu = nu; a.lacc = out; a.lacc_init = 1;
+    return cuerr(ns::launch_adj_stage<float, double, double, float>(c->g, c->cf, a, c->st));
+  }
+  ns::AdjArgs<double, double, double> a{};
+  a.W = w; a.A = a_; a.ca = 1.0; a.nu = nu; a.lacc = out; a.lacc_init = 1;
+  return cuerr(ns::launch_adj_stage<double, double, double, double>(c->g, c->cd, a, c->st));
+}
+
+int ns_objective(ns_ctx* c, const double* w, double weight, double* J_acc, double* lam) {
+  if (!c || !w || !J_acc || lam == w) return NS_ERR_ARG;
+  const int i0 = c->p.plane_i;
+  return cuerr(ns::launch_objective(c->g, c->p.gamma, i0, c->p.pt_in, w, weight, J_acc, lam, c->err, c->st));
+}
+
+int ns_growth_sigma1(ns_ctx* c, const double* w, float* sigma1, double* stats) {
+  if (!c || !w || !sigma1) return NS_ERR_ARG;
+  if (mixed(c)) return cuerr(ns::launch_sigma1<float>(c->g, c->cf, w, sigma1, stats, c->scratch, c->st));
+  return cuerr(ns::launch_sigma1<double>(c->g, c->cd, w, sigma1, stats, c->scratch, c->st));
+}
+
+int ns_add_adjoint_viscosity(ns_ctx* c, const float* sigma1, double lambda, double tau, float* nu) {
+  if (!c || !sigma1 || !nu || !(lambda >= 0)) return NS_ERR_ARG;
+  const double k = 4.0 * (1.0 / (c->p.dx * c->p.dx) + 1.0 / (c->p.dy * c->p.dy) +
+                          (c->p.nz > 1 ? 1.0 / (c->p.dz * c->p.dz) : 0.0));
+  const double limit = c->p.dt > 0 ? 2.78 / (c->p.dt * k) : INFINITY;
+  return cuerr(ns::launch_nu_rule(c->g, sigma1, lambda, tau, limit, nu, c->err, c->st));
+}
+
+int ns_apply_adjoint_viscosity(ns_ctx* c, const float* nu, const double* a, double* out) {
+  if (!c || !nu || !a || !out || out == a) return NS_ERR_ARG;
+  const double i2[3] = {1.0 / (c->p.dx * c->p.dx), 1.0 / (c->p.dy * c->p.dy), 1.0 / (c->p.dz * c->p.dz)};
+  return cuerr(ns::launch_visc_apply(c->g, i2, nu, a, out, c->st));
+}
+
+int ns_adjoint_energy(ns_ctx* c, const double* w, const double* lam, double* E) {
+  if (!c || !w || !lam || !E) return NS_ERR_ARG;
+  const double dV = c->p.dx * c->p.dy * c->p.dz;
+  return cuerr(ns::launch_energy(c->g, c->p.gamma, dV, w, lam, E, c->scratch, c->err, c->st));
+}
+
+int ns_dot(ns_ctx* c, const double* a, const double* phi, int nphi, size_t n, double* out) {
+  if (!c || !a || !phi || !out || nphi < 1 || nphi > 256 || n == 0) return NS_ERR_ARG;
+  return cuerr(ns::launch_dot(a, phi, nphi, n, out, c->scratch, c->st));
+}
+
+int ns_combine(ns_ctx* c, const double* theta, const double* phi, int nphi, size_t n, double* s) {
+  if (!c || !theta || !phi || !s || nphi < 1 || n == 0) return NS_ERR_ARG;
+  return cuerr(ns::launch_combine(theta, phi, nphi, n, s, c->st));
+}
+
+int ns_max_wave_speed(ns_ctx* c, const double* w, double* out) {
+  if (!c || !w || !out) return NS_ERR_ARG;
+  return cuerr(ns::launch_max_wave(c->g, c->p.gamma, w, out, c->scratch, c->st));
+}
+
+int ns_last_error(ns_ctx* c) {
+  if (!c) return NS_ERR_ARG;
+  unsigned h = 0;
+  if (cudaStreamSynchronize(c->st) != cudaSuccess) return NS_ERR_CUDA;
+  if (cudaMemcpy(&h, c->err, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess) return NS_ERR_CUDA;
+  if (cudaMemset(c->err, 0, sizeof(unsigned)) != cudaSuccess) return NS_ERR_CUDA;
+  if (h & ns::ERRBIT_NONFINITE) return NS_ERR_NONFINITE;
+  if (h & ns::ERRBIT_UNSTABLE) return NS_ERR_UNSTABLE;
+  return NS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,509 @@
+// Objective, growth matrix sigma_1, adjoint viscosity, adjoint energy and FP64
+// reductions.  Every reduction is deterministic: fixed grid, fixed per-thread order,
+// a shared-memory tree per block, then one block combines the block partials.
+#include <math.h>
+
+#include "ns_common.cuh"
+#include "ns_kernels.h"
+
+namespace ns {
+
+namespace {
+
+constexpr int RB = 256;      // threads per reduction block
+constexpr int RG = 296;      // blocks per reduced quantity (2 x 148, fixed for determinism)
+
+template <class T, class Op>
+__device__ __forceinline__ T block_reduce(T v, T* sh, Op op) {
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sh[threadIdx.x] = op(sh[threadIdx.x], sh[threadIdx.x + s]);
+    __syncthreads();
+  }
+  T r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+struct AddOp {
+  __device__ double operator()(double a, double b) const { return a + b; }
+};
+struct MaxOp {
+  __device__ double operator()(double a, double b) const { return fmax(a, b); }
+};
+
+// ---------------------------------------------------------------------------------
+// pressure-loss objective, Eq. (e:pressure_loss): one block per box
+// ---------------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_objective(GridDesc g, double gamma, int i0, double pt_in,
+                                                    const double* __restrict__ w, double weight,
+                                                    double* J_acc, double* lam, unsigned* err) {
+  __shared__ double sh[1024];
+  const int b = blockIdx.x;
+  const int nf = g.ny * g.nz;
+  const int iL = wrap(i0 - 1, g.nx), iR = wrap(i0, g.nx);
+  const size_t box = (size_t)b * 5 * g.cells;
+  const double gm1 = gamma - 1.0, ex = gamma / gm1;
+  double N = 0.0, D = 0.0;
+  for (int f = threadIdx.x; f < nf; f += blockDim.x) {
+    const size_t row = (size_t)f * g.nx;   // f = z * ny + y
+    double q[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v)
+      q[v] = 0.5 * (w[box + v * g.cells + row + iL] + w[box + v * g.cells + row + iR]);
+    const double r = q[0];
+    const double u2 = (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]) / (r * r);
+    const double p = gm1 * (q[4] - 0.5 * r * u2);
+    const double M2 = u2 * r / (gamma * p);
+    const double pt = p * pow(1.0 + 0.5 * gm1 * M2, ex);
+    N += r * (pt_in - pt);
+    D += r;
+  }
+  N = block_reduce(N, sh, AddOp());
+  D = block_reduce(D, sh, AddOp());
+  const double J = N / (D * pt_in);
+  if (threadIdx.x == 0) {
+    if (!isfinite(J)) atomicOr(err, ERRBIT_NONFINITE);
+    J_acc[b] += weight * J;
+  }
+  if (!lam) return;
+  // dJ/dw_f = [d(rho_f (pt_in - pt_f))/dw_f - (N/D) e_0] / (D pt_in), split 1/2 : 1/2
+  const double NoD = N / D;
+  const double sc = 0.5 * weight / (D * pt_in);
+  for (int f = threadIdx.x; f < nf; f += blockDim.x) {
+    const size_t row = (size_t)f * g.nx;
+    double q[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v)
+      q[v] = 0.5 * (w[box + v * g.cells + row + iL] + w[box + v * g.cells + row + iR]);
+    const double r = q[0], ir = 1.0 / r;
+    const double u[3] = {q[1] * ir, q[2] * ir, q[3] * ir};
+    const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    const double p = gm1 * (q[4] - 0.5 * r * uu);
+    const double B = 1.0 + 0.5 * gm1 * r * uu / (gamma * p);
+    const double pt = p * pow(B, ex);
+    // derivatives of pt in primitive variables (rho, u, p)
+    const double dr = pt * uu / (2.0 * p * B);
+    const double dp = pt / p * (1.0 - r * uu / (2.0 * p * B));
+    double du[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) du[k] = pt * r * u[k] / (p * B);
+    // chain to conservative variables through dq/dw
+    double dw[5];
+    dw[0] = dr - (u[0] * du[0] + u[1] * du[1] + u[2] * du[2]) * ir + 0.5 * gm1 * uu * dp;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) dw[1 + k] = du[k] * ir - gm1 * u[k] * dp;
+    dw[4] = gm1 * dp;
+    double gv[5];
+    gv[0] = ((pt_in - pt) - r * dw[0] - NoD) * sc;
+#pragma unroll
+    for (int v = 1; v < 5; ++v) gv[v] = -r * dw[v] * sc;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      lam[box + v * g.cells + row + iL] += gv[v];
+      lam[box + v * g.cells + row + iR] += gv[v];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// growth matrix M = M1 - M2 and sigma_1 ("Energy analysis")
+// ---------------------------------------------------------------------------------
+template <class T>
+struct Prim {
+  T rho, u[3], p, a, b;
+};
+
+template <class T>
+__device__ __forceinline__ Prim<T> prim_at(const double* __restrict__ w, size_t o, long long cells,
+                                           T gamma) {
+  Prim<T> P;
+  P.rho = T(w[o]);
+  const T ir = T(1) / P.rho;
+  P.u[0] = T(w[o + cells]) * ir;
+  P.u[1] = T(w[o + 2 * cells]) * ir;
+  P.u[2] = T(w[o + 3 * cells]) * ir;
+  P.p = (gamma - T(1)) * (T(w[o + 4 * cells]) - T(0.5) * P.rho * (P.u[0] * P.u[0] + P.u[1] * P.u[1] + P.u[2] * P.u[2]));
+  const T cs = sqrt(gamma * P.p * ir);
+  P.b = cs / sqrt(gamma);
+  P.a = sqrt((gamma - T(1)) / gamma) * cs;
+  return P;
+}
+
+// largest eigenvalue of a symmetric N x N matrix by cyclic Jacobi rotations
+template <class T, int N>
+__device__ T max_eig_sym(T A[N][N]) {
+  const T eps = sizeof(T) == 8 ? T(1e-30) : T(1e-20);
+  for (int sweep = 0; sweep < 12; ++sweep) {
+    T off = T(0), dia = T(0);
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      dia += A[i][i] * A[i][i];
+#pragma unroll
+      for (int j = i + 1; j < N; ++j) off += A[i][j] * A[i][j];
+    }
+    const T tol = sizeof(T) == 8 ? T(1e-32) : T(1e-14);
+    if (off <= tol * dia || off < eps) break;
+#pragma unroll
+    for (int p = 0; p < N; ++p) {
+#pragma unroll
+      for (int q = p + 1; q < N; ++q) {
+        const T apq = A[p][q];
+        if (fabs(apq) <= eps) continue;
+        const T theta = (A[q][q] - A[p][p]) / (T(2) * apq);
+        const T t = (theta >= T(0) ? T(1) : T(-1)) / (fabs(theta) + sqrt(theta * theta + T(1)));
+        const T cs = T(1) / sqrt(t * t + T(1));
+        const T sn = t * cs;
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+          const T akp = A[k][p], akq = A[k][q];
+          A[k][p] = cs * akp - sn * akq;
+          A[k][q] = sn * akp + cs * akq;
+        }
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+          const T apk = A[p][k], aqk = A[q][k];
+          A[p][k] = cs * apk - sn * aqk;
+          A[q][k] = sn * apk + cs * aqk;
+        }
+      }
+    }
+  }
+  T m = A[0][0];
+#pragma unroll
+  for (int i = 1; i < N; ++i) m = A[i][i] > m ? A[i][i] : m;
+  return m;
+}
+
+template <class T, int N>
+__device__ T sigma1_of(const T M[5][5]) {
+  // 2D: the (rho, u1, u2, p) block
+  const int id5[5] = {0, 1, 2, 3, 4};
+  const int id4[4] = {0, 1, 2, 4};
+  T B[N][N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      T s = T(0);
+#pragma unroll
+      for (int k = 0; k < N; ++k) {
+        const int ki = N == 5 ? id5[k] : id4[k];
+        s += M[ki][N == 5 ? id5[i] : id4[i]] * M[ki][N == 5 ? id5[j] : id4[j]];
+      }
+      B[i][j] = s;
+    }
+  }
+  const T l = max_eig_sym<T, N>(B);
+  return sqrt(l > T(0) ? l : T(0));
+}
+
+template <class CT>
+__global__ void __launch_bounds__(RB) k_sigma1(GridDesc g, Coef<CT> c, const double* __restrict__ w,
+                                               float* __restrict__ sig, double* partial) {
+  __shared__ double sh[RB];
+  const int b = blockIdx.y;
+  double vmax = 0.0, vsum = 0.0;
+  const CT gam = c.gamma, gm1 = c.gm1;
+  for (long long i = (long long)blockIdx.x * RB + threadIdx.x; i < g.cells; i += (long long)gridDim.x * RB) {
+    const int x = (int)(i % g.nx);
+    const int y = (int)((i / g.nx) % g.ny);
+    const int z = (int)(i / g.plane);
+    const size_t box = (size_t)b * 5 * g.cells;
+    auto at = [&](int xx, int yy, int zz) {
+      return box + (size_t)wrap(zz, g.nz) * g.plane + (size_t)wrap(yy, g.ny) * g.nx + wrap(xx, g.nx);
+    };
+    const Prim<CT> P0 = prim_at<CT>(w, at(x, y, z), g.cells, gam);
+    Prim<CT> Pm[3], Pp[3];
+    Pm[0] = prim_at<CT>(w, at(x - 1, y, z), g.cells, gam);
+    Pp[0] = prim_at<CT>(w, at(x + 1, y, z), g.cells, gam);
+    Pm[1] = prim_at<CT>(w, at(x, y - 1, z), g.cells, gam);
+    Pp[1] = prim_at<CT>(w, at(x, y + 1, z), g.cells, gam);
+    Pm[2] = prim_at<CT>(w, at(x, y, z - 1), g.cells, gam);
+    Pp[2] = prim_at<CT>(w, at(x, y, z + 1), g.cells, gam);
+    CT drho[3], du[3][3], dp[3], da[3], db[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const CT h = c.hidx[j];
+      drho[j] = (Pp[j].rho - Pm[j].rho) * h;
+      dp[j] = (Pp[j].p - Pm[j].p) * h;
+      da[j] = (Pp[j].a - Pm[j].a) * h;
+      db[j] = (Pp[j].b - Pm[j].b) * h;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) du[k][j] = (Pp[j].u[k] - Pm[j].u[k]) * h;
+    }
+    const CT div = du[0][0] + du[1][1] + du[2][2];
+    CT M[5][5];
+    // M1 (closed form)
+#pragma unroll
+    for (int i2 = 0; i2 < 5; ++i2)
+#pragma unroll
+      for (int j2 = 0; j2 < 5; ++j2) M[i2][j2] = i2 == j2 ? CT(0.5) * div : CT(0);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      M[0][1 + j] = M[1 + j][0] = CT(0.5) * db[j];
+      M[1 + j][4] = M[4][1 + j] = CT(0.5) * da[j];
+    }
+    // minus M2 (closed form)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      M[0][1 + j] -= P0.b / P0.rho * drho[j];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) M[1 + k][1 + j] -= du[k][j];
+      M[4][1 + j] -= CT(2) / gm1 * da[j];
+      M[1 + j][4] -= P0.a / (CT(2) * P0.p) * dp[j];
+    }
+    M[0][4] -= sqrt(gm1) / CT(2) * div;
+    M[4][4] -= gm1 / CT(2) * div;
+    const CT s1 = g.nz == 1 ? sigma1_of<CT, 4>(M) : sigma1_of<CT, 5>(M);
+    const float sf = (float)s1;
+    sig[(size_t)b * g.cells + i] = sf;
+    vmax = fmax(vmax, (double)sf);
+    vsum += (double)sf;
+  }
+  vmax = block_reduce(vmax, sh, MaxOp());
+  vsum = block_reduce(vsum, sh, AddOp());
+  if (threadIdx.x == 0) {
+    partial[(size_t)b * 2 * gridDim.x + blockIdx.x] = vmax;
+    partial[(size_t)b * 2 * gridDim.x + gridDim.x + blockIdx.x] = vsum;
+  }
+}
+
+__global__ void __launch_bounds__(RB) k_sigma1_stats(int nblk, double inv_cells, const double* partial,
+                                                     double* stats) {
+  __shared__ double sh[RB];
+  const int b = blockIdx.x;
+  double vmax = 0.0, vsum = 0.0;
+  for (int i = threadIdx.x; i < nblk; i += RB) {
+    vmax = fmax(vmax, partial[(size_t)b * 2 * nblk + i]);
+    vsum += partial[(size_t)b * 2 * nblk + nblk + i];
+  }
+  vmax = block_reduce(vmax, sh, MaxOp());
+  vsum = block_reduce(vsum, sh, AddOp());
+  if (threadIdx.x == 0) {
+    stats[2 * b] = vmax;
+    stats[2 * b + 1] = vsum * inv_cells;
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// added adjoint viscosity: coefficient rule and the operator alone
+// ---------------------------------------------------------------------------------
+__global__ void k_nu_rule(long long n, const float* __restrict__ s1, float lam, float tau,
+                          float limit_nu, float* __restrict__ nu, unsigned* err) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float s = s1[i];
+  const float v = s > tau ? lam * s : 0.0f;
+  nu[i] = v;
+  if (!(v <= limit_nu)) atomicOr(err, ERRBIT_UNSTABLE);
+}
+
+__global__ void k_visc_apply(GridDesc g, double ix2, double iy2, double iz2, const float* __restrict__ nu,
+                             const double* __restrict__ a, double* __restrict__ out) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long tot = g.cells * g.batch;
+  if (i >= tot) return;
+  const long long b = i / g.cells, r = i - b * g.cells;
+  const int x = (int)(r % g.nx), y = (int)((r / g.nx) % g.ny), z = (int)(r / g.plane);
+  auto cell = [&](int xx, int yy, int zz) {
+    return (size_t)wrap(zz, g.nz) * g.plane + (size_t)wrap(yy, g.ny) * g.nx + wrap(xx, g.nx);
+  };
+  const size_t c0 = cell(x, y, z);
+  const size_t nb[6] = {cell(x - 1, y, z), cell(x + 1, y, z), cell(x, y - 1, z),
+                        cell(x, y + 1, z), cell(x, y, z - 1), cell(x, y, z + 1)};
+  const float* nub = nu + b * g.cells;
+  const double nc = nub[c0];
+  const double i2[3] = {ix2, iy2, iz2};
+  for (int v = 0; v < 5; ++v) {
+    const double* av = a + (size_t)b * 5 * g.cells + (size_t)v * g.cells;
+    const double ac = av[c0];
+    double L = 0.0;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const double nm = 0.5 * (nc + nub[nb[2 * d]]);
+      const double np = 0.5 * (nc + nub[nb[2 * d + 1]]);
+      L += (np * (av[nb[2 * d + 1]] - ac) - nm * (ac - av[nb[2 * d]])) * i2[d];
+    }
+    out[(size_t)b * 5 * g.cells + (size_t)v * g.cells + c0] += L;
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// adjoint energy: v_hat = S^-T V^-T w_hat in closed form ("Symmetrization")
+// ---------------------------------------------------------------------------------
+__global__ void __launch_bounds__(RB) k_energy(GridDesc g, double gamma, const double* __restrict__ w,
+                                               const double* __restrict__ lam, double* partial) {
+  __shared__ double sh[RB];
+  const int b = blockIdx.y;
+  const size_t box = (size_t)b * 5 * g.cells;
+  const double gm1 = gamma - 1.0, sg = sqrt(gamma), sgg = sqrt(gm1 / gamma);
+  double acc = 0.0;
+  for (long long i = (long long)blockIdx.x * RB + threadIdx.x; i < g.cells; i += (long long)gridDim.x * RB) {
+    const double r = w[box + i], ir = 1.0 / r;
+    const double u0 = w[box + g.cells + i] * ir, u1 = w[box + 2 * g.cells + i] * ir,
+                 u2 = w[box + 3 * g.cells + i] * ir;
+    const double uu = u0 * u0 + u1 * u1 + u2 * u2;
+    const double p = gm1 * (w[box + 4 * g.cells + i] - 0.5 * r * uu);
+    const double cs = sqrt(gamma * p * ir);
+    const double l0 = lam[box + i], l1 = lam[box + g.cells + i], l2 = lam[box + 2 * g.cells + i],
+                 l3 = lam[box + 3 * g.cells + i], l4 = lam[box + 4 * g.cells + i];
+    // y = V^-T lam, V^-1 = dw/dq
+    const double y0 = l0 + u0 * l1 + u1 * l2 + u2 * l3 + 0.5 * uu * l4;
+    const double y1 = r * (l1 + u0 * l4), y2 = r * (l2 + u1 * l4), y3 = r * (l3 + u2 * l4);
+    const double y4 = l4 / gm1;
+    // v_hat = S^-T y
+    const double v0 = sg * r / cs * y0 + r * cs / sg * y4;
+    const double v4 = r * cs * sgg * y4;
+    acc += v0 * v0 + y1 * y1 + y2 * y2 + y3 * y3 + v4 * v4;
+  }
+  acc = block_reduce(acc, sh, AddOp());
+  if (threadIdx.x == 0) partial[(size_t)b * gridDim.x + blockIdx.x] = acc;
+}
+
+__global__ void __launch_bounds__(RB) k_sum_partials(int nblk, double scale, const double* partial,
+                                                     double* out, unsigned* err) {
+  __shared__ double sh[RB];
+  const int b = blockIdx.x;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < nblk; i += RB) s += partial[(size_t)b * nblk + i];
+  s = block_reduce(s, sh, AddOp());
+  if (threadIdx.x == 0) {
+    const double v = s * scale;
+    out[b] = v;
+    if (err && !isfinite(v)) atomicOr(err, ERRBIT_NONFINITE);
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// inner products with source shapes, source assembly, wave speed
+// ---------------------------------------------------------------------------------
+__global__ void __launch_bounds__(RB) k_dot(const double* __restrict__ a, const double* __restrict__ phi,
+                                            size_t n, double* partial) {
+  __shared__ double sh[RB];
+  const int m = blockIdx.y;
+  const double* pm = phi + (size_t)m * n;
+  double s = 0.0;
+  for (size_t i = (size_t)blockIdx.x * RB + threadIdx.x; i < n; i += (size_t)gridDim.x * RB) s += a[i] * pm[i];
+  s = block_reduce(s, sh, AddOp());
+  if (threadIdx.x == 0) partial[(size_t)m * gridDim.x + blockIdx.x] = s;
+}
+
+__global__ void k_combine(const double* __restrict__ theta, const double* __restrict__ phi, int nphi,
+                          size_t n, double* __restrict__ s) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double acc = 0.0;
+  for (int m = 0; m < nphi; ++m) acc += theta[m] * phi[(size_t)m * n + i];
+  s[i] = acc;
+}
+
+__global__ void __launch_bounds__(RB) k_max_wave(GridDesc g, double gamma, const double* __restrict__ w,
+                                                 double* partial) {
+  __shared__ double sh[RB];
+  double mx = 0.0;
+  const long long tot = g.cells * g.batch;
+  for (long long i = (long long)blockIdx.x * RB + threadIdx.x; i < tot; i += (long long)gridDim.x * RB) {
+    const long long b = i / g.cells, r = i - b * g.cells;
+    const size_t o = (size_t)b * 5 * g.cells + r;
+    const double rho = w[o], ir = 1.0 / rho;
+    const double u0 = w[o + g.cells] * ir, u1 = w[o + 2 * g.cells] * ir, u2 = w[o + 3 * g.cells] * ir;
+    const double uu = u0 * u0 + u1 * u1 + u2 * u2;
+    const double p = (gamma - 1.0) * (w[o + 4 * g.cells] - 0.5 * rho * uu);
+    const double s = sqrt(uu) + sqrt(gamma * p * ir);
+    mx = fmax(mx, isfinite(s) ? s : INFINITY);
+  }
+  mx = block_reduce(mx, sh, MaxOp());
+  if (threadIdx.x == 0) partial[blockIdx.x] = mx;
+}
+
+__global__ void __launch_bounds__(RB) k_max_partials(int nblk, const double* partial, double* out) {
+  __shared__ double sh[RB];
+  double m = 0.0;
+  for (int i = threadIdx.x; i < nblk; i += RB) m = fmax(m, partial[i]);
+  m = block_reduce(m, sh, MaxOp());
+  if (threadIdx.x == 0) out[0] = m;
+}
+
+}  // namespace
+
+size_t diag_scratch_doubles(const GridDesc& g, int nphi) {
+  size_t a = (size_t)2 * RG * g.batch;
+  size_t b = (size_t)RG * (nphi > 0 ? nphi : 1);
+  return (a > b ? a : b) + 64;
+}
+
+cudaError_t launch_objective(const GridDesc& g, double gamma, int plane_i, double pt_in,
+                             const double* w, double weight, double* J_acc, double* lam,
+                             unsigned* err, cudaStream_t st) {
+  k_objective<<<g.batch, 1024, 0, st>>>(g, gamma, plane_i, pt_in, w, weight, J_acc, lam, err);
+  return cudaGetLastError();
+}
+
+template <class CT>
+cudaError_t launch_sigma1(const GridDesc& g, const Coef<CT>& c, const double* w, float* sigma1,
+                          double* stats, double* scratch, cudaStream_t st) {
+  dim3 grid(RG, g.batch);
+  k_sigma1<CT><<<grid, RB, 0, st>>>(g, c, w, sigma1, scratch);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || !stats) return e;
+  k_sigma1_stats<<<g.batch, RB, 0, st>>>(RG, 1.0 / (double)g.cells, scratch, stats);
+  return cudaGetLastError();
+}
+template cudaError_t launch_sigma1<double>(const GridDesc&, const Coef<double>&, const double*, float*,
+                                           double*, double*, cudaStream_t);
+template cudaError_t launch_sigma1<float>(const GridDesc&, const Coef<float>&, const double*, float*,
+                                          double*, double*, cudaStream_t);
+
+cudaError_t launch_nu_rule(const GridDesc& g, const float* sigma1, double lambda, double tau,
+                           double limit_nu, float* nu, unsigned* err, cudaStream_t st) {
+  const long long n = g.cells * g.batch;
+  k_nu_rule<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, sigma1, (float)lambda, (float)tau,
+                                                           (float)limit_nu, nu, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_visc_apply(const GridDesc& g, const double* idx2, const float* nu, const double* a,
+                              double* out, cudaStream_t st) {
+  const long long n = g.cells * g.batch;
+  k_visc_apply<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g, idx2[0], idx2[1], idx2[2], nu, a, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_energy(const GridDesc& g, double gamma, double dV, const double* w, const double* lam,
+                          double* E, double* scratch, unsigned* err, cudaStream_t st) {
+  dim3 grid(RG, g.batch);
+  k_energy<<<grid, RB, 0, st>>>(g, gamma, w, lam, scratch);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_sum_partials<<<g.batch, RB, 0, st>>>(RG, dV, scratch, E, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dot(const double* a, const double* phi, int nphi, size_t n, double* out,
+                       double* scratch, cudaStream_t st) {
+  dim3 grid(RG, nphi);
+  k_dot<<<grid, RB, 0, st>>>(a, phi, n, scratch);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_sum_partials<<<nphi, RB, 0, st>>>(RG, 1.0, scratch, out, nullptr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_combine(const double* theta, const double* phi, int nphi, size_t n, double* s,
+                           cudaStream_t st) {
+  k_combine<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(theta, phi, nphi, n, s);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_max_wave(const GridDesc& g, double gamma, const double* w, double* out,
+                            double* scratch, cudaStream_t st) {
+  k_max_wave<<<RG, RB, 0, st>>>(g, gamma, w, scratch);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_max_partials<<<1, RB, 0, st>>>(RG, scratch, out);
+  return cudaGetLastError();
+}
+
+}  // namespace ns

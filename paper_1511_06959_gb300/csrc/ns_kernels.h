@@ -1,0 +1,78 @@
+// Internal launch interface between the C-ABI host code and the CUDA kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "ns_common.cuh"
+
+namespace ns {
+
+// Fused RK4 stage of the primal (see ns_rhs.cu):
+//   R = R(W) + src;  acc = (acc_init ? base (or 0) : acc) + cacc*R;  Wout = base + cout*R
+template <class TIN, class TST>
+struct StageArgs {
+  const TIN* W;
+  const double* Wd;       // tangent of W (Dual instantiation only)
+  const double* base;
+  const double* based;
+  const double* src;
+  const double* srcd;
+  double* acc;
+  double* accd;
+  int acc_init;
+  double cacc;
+  TST* Wout;
+  double* Woutd;
+  double cout;
+};
+
+// Fused stage of the discrete adjoint (see ns_adj.cu), a = ca*A:
+//   g = (dR/dw)(W)^T a + L_nu a
+//   lacc = (lacc_init ? (lam or 0) : lacc) + g;  Anext = cl*lam + cg*g;  sbar += a
+template <class TIN, class TA, class TST>
+struct AdjArgs {
+  const TIN* W;
+  const TA* A;
+  double ca;
+  const float* nu;
+  const double* lam;
+  double* lacc;
+  int lacc_init;
+  TST* Anext;
+  double cl, cg;
+  double* sbar;
+};
+
+template <class CT, class TIN, class TST>
+cudaError_t launch_rhs_stage(const GridDesc& g, const Coef<CT>& c, const StageArgs<TIN, TST>& a,
+                             cudaStream_t st);
+
+template <class CT, class TIN, class TA, class TST>
+cudaError_t launch_adj_stage(const GridDesc& g, const Coef<CT>& c, const AdjArgs<TIN, TA, TST>& a,
+                             cudaStream_t st);
+
+// diagnostics and reductions (ns_diag.cu); `scratch` is context workspace of at
+// least diag_scratch_doubles(g) doubles, `err` the sticky device error word
+size_t diag_scratch_doubles(const GridDesc& g, int nphi);
+cudaError_t launch_objective(const GridDesc& g, double gamma, int plane_i, double pt_in,
+                             const double* w, double weight, double* J_acc, double* lam,
+                             unsigned* err, cudaStream_t st);
+template <class CT>
+cudaError_t launch_sigma1(const GridDesc& g, const Coef<CT>& c, const double* w, float* sigma1,
+                          double* stats, double* scratch, cudaStream_t st);
+cudaError_t launch_nu_rule(const GridDesc& g, const float* sigma1, double lambda, double tau,
+                           double limit_nu, float* nu, unsigned* err, cudaStream_t st);
+cudaError_t launch_visc_apply(const GridDesc& g, const double* idx2, const float* nu,
+                              const double* a, double* out, cudaStream_t st);
+cudaError_t launch_energy(const GridDesc& g, double gamma, double dV, const double* w,
+                          const double* lam, double* E, double* scratch, unsigned* err,
+                          cudaStream_t st);
+cudaError_t launch_dot(const double* a, const double* phi, int nphi, size_t n, double* out,
+                       double* scratch, cudaStream_t st);
+cudaError_t launch_combine(const double* theta, const double* phi, int nphi, size_t n,
+                           double* s, cudaStream_t st);
+cudaError_t launch_max_wave(const GridDesc& g, double gamma, const double* w, double* out,
+                            double* scratch, cudaStream_t st);
+
+}  // namespace ns

@@ -1,0 +1,282 @@
+// Primal residual and fused RK4 stage kernel (Eq. e:navier, Eq. e:vector).
+//
+// R(w)_c = -sum_d (Phi_d(c+1/2) - Phi_d(c-1/2)) / dx_d + s_c with the face flux
+// Phi = (F_L + F_R)/2 - F^v(face).  F^v uses the compact normal difference and the
+// mean of the two cell-centred central differences for the tangential derivatives of
+// (u1, u2, u3, e); the face velocity is the two-cell mean; alpha = gamma mu / Pr.
+//
+// One CTA = TX x TY columns x kchunk planes.  Per plane: every thread computes its
+// cell's lower x-face and lower y-face and the z-face above it; 36 extra threads
+// compute the tile's upper x/y boundary faces; the z-face below is carried in
+// registers from the previous plane.  Each face flux is thus evaluated once per tile.
+//
+// Epilogue (fused RK4 update, FP64 accumulation in both precision modes):
+//   acc  = (acc_init ? base : acc) + cacc * R
+//   Wout = base + cout * R          (next stage state, stored in the stage type)
+// The same template instantiated on ns::Dual gives the tangent (dR/dw) wd.
+#include <type_traits>
+
+#include "ns_common.cuh"
+#include "ns_kernels.h"
+
+namespace ns {
+
+template <class CT, class TIN>
+struct Loader {
+  const TIN* W;
+  const double* Wd;
+  __device__ __forceinline__ CT ld(size_t o) const { return CT(W[o]); }
+};
+template <>
+struct Loader<Dual, double> {
+  const double* W;
+  const double* Wd;
+  __device__ __forceinline__ Dual ld(size_t o) const { return Dual(W[o], Wd[o]); }
+};
+
+// Load plane k (wrapped) of box b into one ring slot, converting to primitives
+// (rho, u1, u2, u3, e).
+template <class CT, class L>
+__device__ __forceinline__ void fill_plane(CT* __restrict__ sq, const GridDesc& g, int b, int k,
+                                           int x0, int y0, const L& in) {
+  const int kz = wrap(k, g.nz);
+  const size_t boxoff = (size_t)b * 5 * g.cells + (size_t)kz * g.plane;
+  for (int t = threadIdx.x; t < SP; t += NT) {
+    const int ly = t / SX;
+    const int lx = t - ly * SX;
+    const int gx = wrap(x0 + lx - 1, g.nx);
+    const int gy = wrap(y0 + ly - 1, g.ny);
+    const size_t o = boxoff + (size_t)gy * g.nx + gx;
+    const CT r = in.ld(o);
+    const CT m0 = in.ld(o + g.cells);
+    const CT m1 = in.ld(o + 2 * g.cells);
+    const CT m2 = in.ld(o + 3 * g.cells);
+    const CT E = in.ld(o + 4 * g.cells);
+    const CT ir = one_over(r);
+    const CT u0 = m0 * ir, u1 = m1 * ir, u2 = m2 * ir;
+    sq[0 * SP + t] = r;
+    sq[1 * SP + t] = u0;
+    sq[2 * SP + t] = u1;
+    sq[3 * SP + t] = u2;
+    sq[4 * SP + t] = E * ir - CT(0.5) * (u0 * u0 + u1 * u1 + u2 * u2);
+  }
+}
+
+// Face flux Phi_D between cells L and R given the tangential face gradients of
+// (u1, u2, u3, e) along T1 = (D+1)%3 and T2 = (D+2)%3.
+template <int D, class CT>
+__device__ __forceinline__ void face_flux(const Coef<CT>& c, const CT* qL, const CT* qR,
+                                          const CT* gt1, const CT* gt2, CT* phi) {
+  constexpr int T1 = (D + 1) % 3, T2 = (D + 2) % 3;
+  CT g[4][3];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    g[k][D] = (qR[1 + k] - qL[1 + k]) * c.idx[D];
+    g[k][T1] = gt1[k];
+    g[k][T2] = gt2[k];
+  }
+  const CT div = g[0][0] + g[1][1] + g[2][2];
+  CT sig[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) sig[j] = c.mu * (g[j][D] + g[D][j]);
+  sig[D] = sig[D] - CT(2.0 / 3.0) * c.mu * div;
+  CT fv4 = c.alpha * g[3][D];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) fv4 = fv4 + CT(0.5) * (qL[1 + j] + qR[1 + j]) * sig[j];
+  const CT pL = c.gm1 * qL[0] * qL[4];
+  const CT pR = c.gm1 * qR[0] * qR[4];
+  const CT mL = qL[0] * qL[1 + D];
+  const CT mR = qR[0] * qR[1 + D];
+  const CT kL = CT(0.5) * (qL[1] * qL[1] + qL[2] * qL[2] + qL[3] * qL[3]);
+  const CT kR = CT(0.5) * (qR[1] * qR[1] + qR[2] * qR[2] + qR[3] * qR[3]);
+  phi[0] = CT(0.5) * (mL + mR);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) phi[1 + k] = CT(0.5) * (mL * qL[1 + k] + mR * qR[1 + k]) - sig[k];
+  phi[1 + D] = phi[1 + D] + CT(0.5) * (pL + pR);
+  phi[4] = CT(0.5) * (mL * (qL[4] + kL) + pL * qL[1 + D] + mR * (qR[4] + kR) + pR * qR[1 + D]) - fv4;
+}
+
+template <class CT>
+__device__ __forceinline__ const CT* qs(const CT* sQ, int slot, int v) {
+  return sQ + (slot * 5 + v) * SP;
+}
+
+// x-face between shared cells (row, fx) and (row, fx+1); row/fx in shared coords.
+template <class CT>
+__device__ __forceinline__ void xface(const CT* sQ, const Coef<CT>& c, int sm, int s0, int sp,
+                                      int row, int fx, CT* phi) {
+  const int iL = row * SX + fx, iR = iL + 1;
+  CT qL[5], qR[5], gy[4], gz[4];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    qL[v] = qs(sQ, s0, v)[iL];
+    qR[v] = qs(sQ, s0, v)[iR];
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const CT* p0 = qs(sQ, s0, 1 + k);
+    const CT* pm = qs(sQ, sm, 1 + k);
+    const CT* pp = qs(sQ, sp, 1 + k);
+    gy[k] = (p0[iL + SX] - p0[iL - SX] + p0[iR + SX] - p0[iR - SX]) * c.i4dx[1];
+    gz[k] = (pp[iL] - pm[iL] + pp[iR] - pm[iR]) * c.i4dx[2];
+  }
+  face_flux<0>(c, qL, qR, gy, gz, phi);
+}
+
+// y-face between shared cells (fy, col) and (fy+1, col).
+template <class CT>
+__device__ __forceinline__ void yface(const CT* sQ, const Coef<CT>& c, int sm, int s0, int sp,
+                                      int fy, int col, CT* phi) {
+  const int iL = fy * SX + col, iR = iL + SX;
+  CT qL[5], qR[5], gz[4], gx[4];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    qL[v] = qs(sQ, s0, v)[iL];
+    qR[v] = qs(sQ, s0, v)[iR];
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const CT* p0 = qs(sQ, s0, 1 + k);
+    const CT* pm = qs(sQ, sm, 1 + k);
+    const CT* pp = qs(sQ, sp, 1 + k);
+    gz[k] = (pp[iL] - pm[iL] + pp[iR] - pm[iR]) * c.i4dx[2];
+    gx[k] = (p0[iL + 1] - p0[iL - 1] + p0[iR + 1] - p0[iR - 1]) * c.i4dx[0];
+  }
+  face_flux<1>(c, qL, qR, gz, gx, phi);
+}
+
+// z-face between slot sL (lower plane) and sR (upper plane) at shared cell index i.
+template <class CT>
+__device__ __forceinline__ void zface(const CT* sQ, const Coef<CT>& c, int sL, int sR, int i,
+                                      CT* phi) {
+  CT qL[5], qR[5], gx[4], gy[4];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    qL[v] = qs(sQ, sL, v)[i];
+    qR[v] = qs(sQ, sR, v)[i];
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const CT* a = qs(sQ, sL, 1 + k);
+    const CT* bq = qs(sQ, sR, 1 + k);
+    gx[k] = (a[i + 1] - a[i - 1] + bq[i + 1] - bq[i - 1]) * c.i4dx[0];
+    gy[k] = (a[i + SX] - a[i - SX] + bq[i + SX] - bq[i - SX]) * c.i4dx[1];
+  }
+  face_flux<2>(c, qL, qR, gx, gy, phi);
+}
+
+template <class CT, class TIN, class TST>
+__global__ void __launch_bounds__(NT) k_rhs_stage(GridDesc g, Coef<CT> c, StageArgs<TIN, TST> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  CT* sQ = reinterpret_cast<CT*>(smem_raw);          // [3][5][SP]
+  CT* sFX = sQ + 3 * 5 * SP;                          // [5][TY][TX+1]
+  CT* sFY = sFX + 5 * TY * (TX + 1);                  // [5][TY+1][TX]
+  const int tid = threadIdx.x;
+  const int tx = tid % TX, ty = tid / TX;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  const int b = blockIdx.z / g.nzchunks;
+  const int kz0 = (blockIdx.z % g.nzchunks) * g.kchunk;
+  const int kz1 = min(g.nz, kz0 + g.kchunk);
+  const int gx = x0 + tx, gy = y0 + ty;
+  const bool valid = gx < g.nx && gy < g.ny;
+  Loader<CT, TIN> in{a.W, a.Wd};
+
+  auto slot = [&](int k) { return (k - kz0 + 1) % 3; };
+  fill_plane<CT>(sQ + slot(kz0 - 1) * 5 * SP, g, b, kz0 - 1, x0, y0, in);
+  fill_plane<CT>(sQ + slot(kz0) * 5 * SP, g, b, kz0, x0, y0, in);
+  fill_plane<CT>(sQ + slot(kz0 + 1) * 5 * SP, g, b, kz0 + 1, x0, y0, in);
+  __syncthreads();
+  const int ic = (ty + 1) * SX + (tx + 1);
+  CT zlo[5], zhi[5];
+  zface(sQ, c, slot(kz0 - 1), slot(kz0), ic, zlo);
+
+  for (int k = kz0; k < kz1; ++k) {
+    const int sm = slot(k - 1), s0 = slot(k), sp = slot(k + 1);
+    {
+      CT phi[5];
+      xface(sQ, c, sm, s0, sp, ty + 1, tx, phi);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) sFX[(v * TY + ty) * (TX + 1) + tx] = phi[v];
+      yface(sQ, c, sm, s0, sp, ty, tx + 1, phi);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) sFY[(v * (TY + 1) + ty) * TX + tx] = phi[v];
+    }
+    zface(sQ, c, s0, sp, ic, zhi);
+    if (tid < TX) {
+      CT phi[5];
+      yface(sQ, c, sm, s0, sp, TY, tid + 1, phi);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) sFY[(v * (TY + 1) + TY) * TX + tid] = phi[v];
+    } else if (tid < TX + TY) {
+      CT phi[5];
+      const int r = tid - TX;
+      xface(sQ, c, sm, s0, sp, r + 1, TX, phi);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) sFX[(v * TY + r) * (TX + 1) + TX] = phi[v];
+    }
+    __syncthreads();
+    if (valid) {
+      const size_t o0 = (size_t)b * 5 * g.cells + (size_t)k * g.plane + (size_t)gy * g.nx + gx;
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        const CT fxp = sFX[(v * TY + ty) * (TX + 1) + tx + 1];
+        const CT fxm = sFX[(v * TY + ty) * (TX + 1) + tx];
+        const CT fyp = sFY[(v * (TY + 1) + ty + 1) * TX + tx];
+        const CT fym = sFY[(v * (TY + 1) + ty) * TX + tx];
+        const CT R = -((fxp - fxm) * c.idx[0] + (fyp - fym) * c.idx[1] + (zhi[v] - zlo[v]) * c.idx[2]);
+        const size_t o = o0 + (size_t)v * g.cells;
+        double Rv = (double)val(R);
+        if (a.src) Rv += a.src[o];
+        if (a.acc) {
+          const double accv = a.acc_init ? (a.base ? a.base[o] : 0.0) : a.acc[o];
+          a.acc[o] = accv + a.cacc * Rv;
+        }
+        if (a.Wout) a.Wout[o] = (TST)(a.base[o] + a.cout * Rv);
+        if constexpr (std::is_same<CT, Dual>::value) {
+          double Rd = tan_of(R);
+          if (a.srcd) Rd += a.srcd[o];
+          if (a.accd) {
+            const double accd = a.acc_init ? (a.based ? a.based[o] : 0.0) : a.accd[o];
+            a.accd[o] = accd + a.cacc * Rd;
+          }
+          if (a.Woutd) a.Woutd[o] = a.based[o] + a.cout * Rd;
+        }
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < 5; ++v) zlo[v] = zhi[v];
+    __syncthreads();
+    if (k + 1 < kz1) {
+      fill_plane<CT>(sQ + slot(k + 2) * 5 * SP, g, b, k + 2, x0, y0, in);
+      __syncthreads();
+    }
+  }
+}
+
+template <class CT>
+size_t rhs_smem_bytes() {
+  return sizeof(CT) * (3 * 5 * SP + 5 * TY * (TX + 1) + 5 * (TY + 1) * TX);
+}
+
+template <class CT, class TIN, class TST>
+cudaError_t launch_rhs_stage(const GridDesc& g, const Coef<CT>& c, const StageArgs<TIN, TST>& a,
+                             cudaStream_t st) {
+  const size_t smem = rhs_smem_bytes<CT>();
+  auto kern = k_rhs_stage<CT, TIN, TST>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, g.batch * g.nzchunks);
+  kern<<<grid, NT, smem, st>>>(g, c, a);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_rhs_stage<double, double, double>(const GridDesc&, const Coef<double>&,
+                                                              const StageArgs<double, double>&, cudaStream_t);
+template cudaError_t launch_rhs_stage<float, double, float>(const GridDesc&, const Coef<float>&,
+                                                            const StageArgs<double, float>&, cudaStream_t);
+template cudaError_t launch_rhs_stage<float, float, float>(const GridDesc&, const Coef<float>&,
+                                                           const StageArgs<float, float>&, cudaStream_t);
+template cudaError_t launch_rhs_stage<Dual, double, double>(const GridDesc&, const Coef<Dual>&,
+                                                            const StageArgs<double, double>&, cudaStream_t);
+
+}  // namespace ns
