@@ -1,0 +1,410 @@
+#!/usr/bin/env python
+"""Benchmark of the checkpointed unsteady discrete adjoint on one GB300 per rank.
+
+One step = the whole hot path over one synthetic box: the RK4 primal forward pass
+with the pressure-loss objective, then the backward sweep that replays each
+checkpoint segment, evaluates sigma_1 and the added adjoint viscosity, applies the four
+transposed RK4 stages, adds the objective source and records the adjoint energy.
+The metric is adjoint cell-steps/s (cells x RK4 steps reversed, per second).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload box128]
+                  [--precision mixed|fp64] [--impl ours|reference]
+
+Under torchrun each rank runs its own independent box (weak scaling, no data-path
+collective); rank 0 prints one JSON line.  --impl reference times the FP64 CPU
+oracle instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1511_06959_gb300 import config as C  # noqa: E402
+
+METRIC = "adjoint cell-steps/s and % HBM roofline, mixed+checkpointed vs FP64 at stated grad err"
+UNIT = "adjoint cell-steps/s"
+
+# algorithmic bytes per cell of one adjoint-stage launch, averaged over the four stages
+# (inputs read once, outputs written once; nu field present, no source seed)
+ADJ_STAGE_BYTES = {"mixed": (124 + 184 + 184 + 144) / 4.0, "fp64": (164 + 244 + 244 + 164) / 4.0}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="box128", choices=sorted(C.WORKLOADS))
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--nsteps", type=int, default=0,
+                    help="override the workload's RK4 step count (profiling runs)")
+    return ap.parse_args()
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ----------------------------------------------------------------------------------
+# CPU oracle: one checkpointed adjoint step of the workload on the host cores
+# ----------------------------------------------------------------------------------
+def oracle_unit(w, P, lam_tilde, dx0):
+    """Forward step + replay step + stabilised adjoint step (sigma_1, nu, objective source,
+    adjoint energy) of the full box: the work the GPU sweep does per reversed step."""
+    from oracle import ns_oracle as O
+    w1, _ = O.rk4_step(w, P)
+    O.objective(w1, P)
+    w1, _ = O.rk4_step(w, P)
+    lam = O.objective_grad(w1, P)
+    nu = lam_tilde * dx0 ** 2 * O.sigma1_field(w, P)
+    lam, _ = O.rk4_adjoint_step(w, lam, P, None, nu)
+    lam = lam + O.objective_grad(w, P)
+    O.adjoint_energy(w, lam, P)
+
+
+def oracle_setup(wl):
+    from oracle import ns_oracle as O
+    w = wl.initial_state()
+    P = O.Params(gamma=wl.gamma, mu=wl.mu, Pr=wl.Pr, dx=wl.dx, plane_i=wl.plane_i, pt_in=wl.pt_in)
+    P.dt = C.cfl_dt(wl, O.max_wave_speed(w, P))
+    return w, P
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def run_reference(args, wl):
+    ws, rank, _ = dist_init()
+    if rank != 0:
+        return
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
+    w, P = oracle_setup(wl)
+    for _ in range(min(args.warmup, 1)):
+        oracle_unit(w, P, wl.lam_tilde, wl.dx[0])
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_unit(w, P, wl.lam_tilde, wl.dx[0])
+    t = time.perf_counter() - t0
+    v = args.steps * wl.cells * wl.batch / t
+    sample = (f"{args.steps} x one checkpointed adjoint step (forward + replay + stabilised "
+              f"adjoint + source + energy) of the full {wl.nx}x{wl.ny}x{wl.nz} box")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": min(args.warmup, 1), "ms_per_step": 1e3 * t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": C.describe(wl), "name": wl.name},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+# ----------------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_id):
+        self.bus_id = bus_id
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                   "-lms", "200"]
+            if self.bus_id:
+                cmd.insert(1, f"--id={self.bus_id}")
+            self.proc = subprocess.Popen(cmd, stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                rows.append((float(p[1]), float(p[2]), float(p[3]), p[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[3]) if v.lower() == "active"})
+        pmax = max(r[2] for r in rows)
+        load = [r for r in rows if r[2] >= 0.5 * pmax] or rows
+        return {"sm_mhz": statistics.median(r[0] for r in load), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows), "power_w_max": pmax}
+
+
+def launches_in_run(plan_actions, N, need_sigma, lam_on, record_energy, record_sigma):
+    """Kernel launches of one ns_adjoint_run (counted from its plan)."""
+    n = 0
+    touched = 0
+    for op, a, b in plan_actions:
+        if op == 1:
+            n += 4 * (b - a)
+            new = max(0, b - max(a, touched))
+            n += new
+            touched = max(touched, b)
+        elif op == 6:
+            n += 1 + (2 if record_energy else 0)
+        elif op == 4:
+            if need_sigma:
+                n += 1 + (1 if record_sigma else 0)
+            if lam_on:
+                n += 1
+            n += 7 + (1 if a >= 1 else 0) + (2 if record_energy else 0)
+    return n
+
+
+def run_ours(args, wl):
+    import torch
+
+    from paper_1511_06959_gb300 import api
+
+    ws, rank, local = dist_init()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    prec = api.NS_MIXED if args.precision == "mixed" else api.NS_FP64
+
+    w0_host = wl.initial_state()
+    w0 = torch.from_numpy(w0_host).to(dev)
+    S = api.Solver(wl.nx, wl.ny, wl.nz, wl.dx, gamma=wl.gamma, mu=wl.mu, Pr=wl.Pr, dt=0.0,
+                   precision=prec, plane_i=wl.plane_i, pt_in=wl.pt_in, batch=wl.batch)
+    m = torch.empty(1, dtype=torch.float64, device=dev)
+    S.max_wave_speed(w0, m)
+    dt = C.cfl_dt(wl, m.item())
+    S.set_dt(dt)
+    field_bytes = w0.numel() * 8
+    param = wl.param if wl.schedule != "revolve" or wl.param else C.revolve_slots(wl, field_bytes)
+    sched = C.SCHEDULES[wl.schedule]
+    opts = S.run_opts(wl.nsteps, sched, param, wl.lam_coef, 0.0, True, True)
+    arena = torch.empty(S.arena_bytes(opts), dtype=torch.uint8, device=dev)
+    J = torch.empty(wl.batch, dtype=torch.float64, device=dev)
+    lam0 = torch.empty_like(w0)
+    E = torch.empty((wl.nsteps + 1, wl.batch), dtype=torch.float64, device=dev)
+    sig = torch.empty((wl.nsteps, wl.batch, 2), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+
+    def step():
+        S.adjoint_run(w0, opts, arena, J, lam0, energy=E, sigma_stats=sig)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    err = S.last_error()
+    if err != 0:
+        raise RuntimeError(f"device error word {err} after warm-up")
+
+    bus = torch.cuda.get_device_properties(dev).pci_bus_id if hasattr(
+        torch.cuda.get_device_properties(dev), "pci_bus_id") else None
+    clk = ClockSampler(bus)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clk.start()
+    S.profile_enable(True)
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)          # L2 flush between timed steps, outside the event pair
+        ev[i][0].record()
+        step()
+        ev[i][1].record()
+    torch.cuda.synchronize()
+    S.profile_enable(False)
+    clocks = clk.stop()
+    if ws > 1:
+        torch.distributed.barrier()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    kms, klaunch = S.profile_read()
+    if S.last_error() != 0:
+        raise RuntimeError("device error word set in the timed region")
+    Jv = J.cpu().numpy().copy()
+    E_host = E.cpu().numpy()
+    if not np.all(np.isfinite(Jv)) or not np.all(np.isfinite(E_host)):
+        raise RuntimeError("non-finite objective or adjoint energy")
+
+    # end to end through the public call with host buffers
+    w_pin = torch.from_numpy(w0_host).pin_memory()
+    lam_pin = torch.empty(lam0.shape, dtype=torch.float64).pin_memory()
+    J_pin = torch.empty(wl.batch, dtype=torch.float64).pin_memory()
+    w_e2e = torch.empty_like(w0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        w_e2e.copy_(w_pin, non_blocking=True)
+        S.adjoint_run(w_e2e, opts, arena, J, lam0, energy=E, sigma_stats=sig)
+        lam_pin.copy_(lam0, non_blocking=True)
+        J_pin.copy_(J, non_blocking=True)
+        torch.cuda.synchronize()
+    t_e2e = (time.perf_counter() - t0) / args.steps
+
+    cell_steps = wl.cells * wl.batch * wl.nsteps
+    # max over ranks
+    if ws > 1:
+        tt = torch.tensor([ms, t_e2e], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        ms, t_e2e = tt[0].item(), tt[1].item()
+    value = ws * cell_steps / (ms * 1e-3)
+    e2e_value = ws * cell_steps / t_e2e
+
+    out = None
+    if rank == 0:
+        actions, _, _ = api.plan(wl.nsteps, sched, param)
+        gl = launches_in_run(actions, wl.nsteps, True, wl.lam_coef > 0, True, True) * args.steps
+        kavg = kms / max(klaunch, 1)
+        bytes_launch = ADJ_STAGE_BYTES[args.precision] * wl.cells * wl.batch
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+            os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+        hbm = peaks.get("hbm_gbs", 6800.0)
+        achieved = bytes_launch / (kavg * 1e-3) / 1e9
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 (f64 accumulate)" if prec == api.NS_MIXED else "f64",
+            "data": "synthetic",
+            "config": {"workload": C.describe(wl), "name": wl.name, "cells": wl.cells,
+                       "nsteps": wl.nsteps, "schedule": wl.schedule, "param": param,
+                       "lambda_tilde": wl.lam_tilde, "precision": args.precision, "dt": dt,
+                       "l2": "flushed (256 MB write) between timed steps; arena "
+                             f"{arena.numel() / 1e9:.2f} GB > L2",
+                       "J_bar": float(Jv[0]), "E_vhat_0": float(E_host[0, 0])},
+            "roofline": {"bound": "hbm", "kernel": "k_adj_stage", "achieved": achieved,
+                         "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                         "avg_launch_us": 1e3 * kavg, "launches": klaunch,
+                         "bytes_per_launch": bytes_launch, "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(w0.numel() * 8),
+                    "d2h_bytes_per_step": int(lam0.numel() * 8 + J.numel() * 8)},
+            "gpu_launches": gl,
+            "clocks": clocks,
+        }
+        if not args.no_fp64_compare and prec == api.NS_MIXED:
+            out["fp64"] = fp64_compare(api, torch, wl, w0, dt, sched, param, lam0, Jv)
+        if not args.no_cpu_baseline and ws == 1:
+            out["cpu_baseline"] = cpu_baseline(wl)
+    return out
+
+
+def fp64_compare(api, torch, wl, w0, dt, sched, param, lam_mixed, J_mixed):
+    """The same checkpointed sweep in FP64 (timed once) and the mixed-precision
+    gradient error against it."""
+    S = api.Solver(wl.nx, wl.ny, wl.nz, wl.dx, gamma=wl.gamma, mu=wl.mu, Pr=wl.Pr, dt=dt,
+                   precision=api.NS_FP64, plane_i=wl.plane_i, pt_in=wl.pt_in, batch=wl.batch)
+    opts = S.run_opts(wl.nsteps, sched, param, wl.lam_coef, 0.0, True, True)
+    arena = torch.empty(S.arena_bytes(opts), dtype=torch.uint8, device=w0.device)
+    J = torch.empty(wl.batch, dtype=torch.float64, device=w0.device)
+    lam = torch.empty_like(w0)
+    E = torch.empty((wl.nsteps + 1, wl.batch), dtype=torch.float64, device=w0.device)
+    sg = torch.empty((wl.nsteps, wl.batch, 2), dtype=torch.float64, device=w0.device)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    S.profile_enable(True)
+    a.record()
+    S.adjoint_run(w0, opts, arena, J, lam, energy=E, sigma_stats=sg)
+    b.record()
+    torch.cuda.synchronize()
+    S.profile_enable(False)
+    ms = a.elapsed_time(b)
+    kms, kn = S.profile_read()
+    d = (lam_mixed - lam).double()
+    rel = (torch.linalg.vector_norm(d) / torch.linalg.vector_norm(lam)).item()
+    Jf = J.cpu().numpy()
+    return {"value": wl.cells * wl.batch * wl.nsteps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+            "grad_rel_l2_mixed_vs_fp64": rel,
+            "J_rel_mixed_vs_fp64": float(abs(J_mixed[0] - Jf[0]) / abs(Jf[0])),
+            "adj_stage_avg_launch_us": 1e3 * kms / max(kn, 1),
+            "note": "FP64 is bound by the FP64 ALU rate, not HBM; timed once on the same workload"}
+
+
+def cpu_baseline(wl):
+    """The FP64 oracle on this host's cores: one checkpointed adjoint step of the full box
+    (10-30 s of CPU work), scaled to adjoint cell-steps/s.  It runs in a spawned process
+    so that no fork happens after CUDA is initialised."""
+    import multiprocessing as mp
+    saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in saved:
+        os.environ[k] = "1"
+    try:
+        ctx = mp.get_context("spawn")
+        with ctx.Pool(1) as pool:
+            t = pool.apply(_cpu_sample, (wl.name,))
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    return {"value": wl.cells * wl.batch / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"1 checkpointed adjoint step (forward + replay + stabilised adjoint + "
+                      f"source + energy) of the full {wl.nx}x{wl.ny}x{wl.nz} box, numpy FP64, "
+                      f"{t:.1f} s", "host_cores_available": cpu_cores()}
+
+
+def _cpu_sample(name):
+    wl = C.WORKLOADS[name]
+    w, P = oracle_setup(wl)
+    t0 = time.perf_counter()
+    oracle_unit(w, P, wl.lam_tilde, wl.dx[0])
+    return time.perf_counter() - t0
+
+
+def main():
+    args = parse()
+    wl = C.WORKLOADS[args.workload]
+    if args.nsteps > 0:
+        import dataclasses
+        wl = dataclasses.replace(wl, nsteps=args.nsteps)
+    if args.impl == "reference":
+        run_reference(args, wl)
+        return
+    out = run_ours(args, wl)
+    if out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -147,6 +147,75 @@ int ns_combine(ns_ctx* ctx, const double* theta, const double* phi, int nphi, si
 /* max over all cells of |u| + c; writes one double to the device pointer out. */
 int ns_max_wave_speed(ns_ctx* ctx, const double* w, double* out);
 
+/* ------------------------------------------------------------------------------
+ * Checkpointed adjoint sweep ("Implementation": periodic snapshots of the primal,
+ * segments recomputed during the backward sweep).  The host runtime plans which
+ * primal states to keep (ns_plan) and executes the plan on the context's stream
+ * (ns_adjoint_run).  Schedules:
+ *   NS_CKPT_ALL     keep every state (no recomputation)
+ *   NS_CKPT_STRIDE  keep every param-th state; replay one segment at a time and keep
+ *                   all its states during its reversal
+ *   NS_CKPT_REVOLVE binomial checkpointing with param state slots: each step is
+ *                   recomputed at most r times, r the least integer with
+ *                   C(param + r, param) >= nsteps
+ * ---------------------------------------------------------------------------- */
+#define NS_CKPT_ALL 0
+#define NS_CKPT_STRIDE 1
+#define NS_CKPT_REVOLVE 2
+
+#define NS_OP_ADVANCE 1 /* advance the current state from step a to step b */
+#define NS_OP_STORE 2   /* keep the current state (step a) in slot b */
+#define NS_OP_LOAD 3    /* make the state of step a in slot b current (b = -1: w^0) */
+#define NS_OP_ADJOINT 4 /* reverse step a (current state is w^a), then add the
+                           objective source of step a if a >= 1 */
+#define NS_OP_FREE 5    /* release slot b (held step a) */
+#define NS_OP_SOURCE 6  /* add the objective source of step a (current state w^a) */
+
+typedef struct {
+  int op, a, b;
+} ns_action;
+
+/* Plan a sweep of nsteps steps (pure host computation, no CUDA call).  Writes up to
+ * max_actions actions to out (out may be NULL to query the count), the number of
+ * actions to *n_actions, the largest number of simultaneously used slots to
+ * *slots_used and the number of primal steps advanced (first pass included) to
+ * *advances.  NS_ERR_ARG for nsteps < 1, a bad schedule or param < 1 where needed;
+ * NS_ERR_BUDGET if max_actions is too small (n_actions still reports the need). */
+int ns_plan(int nsteps, int schedule, int param, ns_action* out, int max_actions, int* n_actions,
+            int* slots_used, long long* advances);
+
+typedef struct {
+  int nsteps;        /* primal steps N; Jbar = (1/N) sum_{n=1..N} J(w^n) */
+  int schedule;      /* NS_CKPT_* */
+  int param;         /* stride (NS_CKPT_STRIDE) or state slots (NS_CKPT_REVOLVE) */
+  double lambda;     /* added adjoint viscosity nu = lambda sigma_1 [sigma_1 > tau]; 0 = none */
+  double tau;
+  int record_energy; /* write E_vhat(w^n, lam^n), n = 0..N, to energy[n][batch] */
+  int record_sigma;  /* write (max, mean) of sigma_1(w^n), n = 0..N-1, to sigma_stats[n][batch][2]
+                        (sigma_1 is always evaluated when lambda > 0) */
+} ns_run_opts;
+
+/* Device bytes the caller must provide as the arena of ns_adjoint_run (state slots,
+ * two working states, one adjoint field, sigma_1 and nu fields, scalars). */
+size_t ns_run_arena_bytes(const ns_ctx* ctx, const ns_run_opts* o);
+
+/* Whole forward + checkpointed backward sweep from w^0 with the time-constant source s
+ * (may be NULL): Jbar[batch] (device) receives the time-averaged pressure loss,
+ * lam0 (device field) dJbar/dw^0, sbar (device field, may be NULL) dJbar/ds.
+ * energy / sigma_stats: device arrays or NULL (see ns_run_opts).  arena: caller-owned
+ * device memory of at least ns_run_arena_bytes(ctx, o) bytes, 256-byte aligned;
+ * NS_ERR_BUDGET if it is smaller.  The sweep is deterministic: replayed states are
+ * bitwise identical to the first pass. */
+int ns_adjoint_run(ns_ctx* ctx, const double* w0, const double* s, const ns_run_opts* o,
+                   void* arena, size_t arena_bytes, double* Jbar, double* lam0, double* sbar,
+                   double* energy, double* sigma_stats);
+
+/* Kernel timing for roofline reports: when on, the context records a CUDA event pair
+ * around every adjoint-stage kernel it launches; ns_profile_read synchronises and
+ * returns the summed milliseconds and the launch count since profiling was enabled. */
+int ns_profile_enable(ns_ctx* ctx, int on);
+int ns_profile_read(ns_ctx* ctx, double* ms, long long* launches);
+
 /* Synchronises the stream, then returns and clears the sticky device error word
  * (NS_OK, NS_ERR_NONFINITE or NS_ERR_UNSTABLE). */
 int ns_last_error(ns_ctx* ctx);

@@ -28,8 +28,14 @@ EXPORTED = [
     "ns_rhs_tangent", "ns_rhs_transpose", "ns_primal_step", "ns_tangent_step", "ns_adjoint_step",
     "ns_objective", "ns_growth_sigma1", "ns_add_adjoint_viscosity", "ns_apply_adjoint_viscosity",
     "ns_adjoint_energy", "ns_dot", "ns_combine", "ns_max_wave_speed", "ns_last_error",
-    "ns_error_string",
+    "ns_error_string", "ns_plan", "ns_run_arena_bytes", "ns_adjoint_run", "ns_profile_enable",
+    "ns_profile_read",
 ]
+
+NS_CKPT_ALL = 0
+NS_CKPT_STRIDE = 1
+NS_CKPT_REVOLVE = 2
+NS_OP_ADVANCE, NS_OP_STORE, NS_OP_LOAD, NS_OP_ADJOINT, NS_OP_FREE, NS_OP_SOURCE = 1, 2, 3, 4, 5, 6
 
 
 class NsParams(ctypes.Structure):
@@ -39,6 +45,18 @@ class NsParams(ctypes.Structure):
         ("gamma", ctypes.c_double), ("mu", ctypes.c_double), ("Pr", ctypes.c_double),
         ("dt", ctypes.c_double), ("precision", ctypes.c_int), ("plane_i", ctypes.c_int),
         ("pt_in", ctypes.c_double),
+    ]
+
+
+class NsAction(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_int), ("a", ctypes.c_int), ("b", ctypes.c_int)]
+
+
+class NsRunOpts(ctypes.Structure):
+    _fields_ = [
+        ("nsteps", ctypes.c_int), ("schedule", ctypes.c_int), ("param", ctypes.c_int),
+        ("lambda_", ctypes.c_double), ("tau", ctypes.c_double), ("record_energy", ctypes.c_int),
+        ("record_sigma", ctypes.c_int),
     ]
 
 
@@ -84,6 +102,12 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "ns_max_wave_speed": ([P, P, P], I),
         "ns_last_error": ([P], I),
         "ns_error_string": ([I], ctypes.c_char_p),
+        "ns_plan": ([I, I, I, P, I, ctypes.POINTER(I), ctypes.POINTER(I),
+                     ctypes.POINTER(ctypes.c_longlong)], I),
+        "ns_run_arena_bytes": ([P, ctypes.POINTER(NsRunOpts)], S),
+        "ns_adjoint_run": ([P, P, P, ctypes.POINTER(NsRunOpts), P, S, P, P, P, P, P], I),
+        "ns_profile_enable": ([P, I], I),
+        "ns_profile_read": ([P, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_longlong)], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -97,6 +121,20 @@ def _lib() -> ctypes.CDLL:
     if _LIB is None:
         _LIB = load_library()
     return _LIB
+
+
+def plan(nsteps: int, schedule: int, param: int = 0):
+    """Checkpoint plan (host computation): (actions as (op, a, b) tuples, slots, advances)."""
+    lib = _lib()
+    n = ctypes.c_int()
+    slots = ctypes.c_int()
+    adv = ctypes.c_longlong()
+    _check(lib.ns_plan(nsteps, schedule, param, None, 0, ctypes.byref(n), ctypes.byref(slots),
+                       ctypes.byref(adv)), "ns_plan")
+    arr = (NsAction * max(n.value, 1))()
+    _check(lib.ns_plan(nsteps, schedule, param, arr, n.value, ctypes.byref(n), ctypes.byref(slots),
+                       ctypes.byref(adv)), "ns_plan")
+    return [(a.op, a.a, a.b) for a in arr[: n.value]], slots.value, adv.value
 
 
 def _ptr(t, dtype=None):
@@ -231,3 +269,30 @@ class Solver:
 
     def last_error(self) -> int:
         return int(self.lib.ns_last_error(self._ctx))
+
+    # --- checkpointed sweep ----------------------------------------------------------
+    def run_opts(self, nsteps, schedule=NS_CKPT_ALL, param=0, lam_coef=0.0, tau=0.0,
+                 record_energy=False, record_sigma=False):
+        return NsRunOpts(nsteps, schedule, param, lam_coef, tau, int(record_energy), int(record_sigma))
+
+    def arena_bytes(self, opts) -> int:
+        return int(self.lib.ns_run_arena_bytes(self._ctx, ctypes.byref(opts)))
+
+    def adjoint_run(self, w0, opts, arena, Jbar, lam0, s=None, sbar=None, energy=None,
+                    sigma_stats=None):
+        """Forward + checkpointed backward sweep; arena is a uint8 CUDA tensor of at least
+        arena_bytes(opts) bytes."""
+        _check(self.lib.ns_adjoint_run(self._ctx, _ptr(w0, torch.float64), _ptr(s, torch.float64),
+                                       ctypes.byref(opts), _ptr(arena), arena.numel() * arena.element_size(),
+                                       _ptr(Jbar, torch.float64), _ptr(lam0, torch.float64),
+                                       _ptr(sbar, torch.float64), _ptr(energy, torch.float64),
+                                       _ptr(sigma_stats, torch.float64)), "ns_adjoint_run")
+
+    def profile_enable(self, on=True):
+        _check(self.lib.ns_profile_enable(self._ctx, int(on)), "ns_profile_enable")
+
+    def profile_read(self):
+        ms = ctypes.c_double()
+        n = ctypes.c_longlong()
+        _check(self.lib.ns_profile_read(self._ctx, ctypes.byref(ms), ctypes.byref(n)), "ns_profile_read")
+        return ms.value, n.value

@@ -10,26 +10,11 @@
 #include "../../include/ns_adjoint.h"
 #include "ns_common.cuh"
 #include "ns_kernels.h"
+#include "ns_ctx.h"
 
 using ns::Coef;
 using ns::Dual;
 using ns::GridDesc;
-
-struct ns_ctx {
-  ns_params p;
-  cudaStream_t st;
-  GridDesc g;
-  Coef<double> cd;
-  Coef<float> cf;
-  Coef<Dual> cx;
-  size_t field;          // elements of one [batch][5][cells] field
-  void* stage[5];        // stage buffers (double in FP64 mode, float in MIXED mode)
-  double* tan[5];        // FP64 buffers of the tangent step, allocated on first use
-  double* scratch;       // reduction scratch
-  size_t scratch_n;
-  unsigned* err;         // sticky device error word
-  size_t ws_bytes;
-};
 
 namespace {
 
@@ -101,6 +86,25 @@ static int primal_step_t(ns_ctx* c, const Coef<CT>& cf, const double* w, const d
   return NS_OK;
 }
 
+// CUDA event pair around one adjoint-stage launch when kernel profiling is on.
+static void prof_mark(ns_ctx* c) {
+  if (!c->prof_on) return;
+  if (c->prof_used == c->events.size()) {
+    cudaEvent_t ev;
+    if (cudaEventCreate(&ev) != cudaSuccess) return;
+    c->events.push_back(ev);
+  }
+  cudaEventRecord(c->events[c->prof_used++], c->st);
+}
+
+template <class CT, class TIN, class TA, class TST>
+static cudaError_t adj_launch(ns_ctx* c, const Coef<CT>& cf, const ns::AdjArgs<TIN, TA, TST>& a) {
+  prof_mark(c);
+  cudaError_t e = ns::launch_adj_stage<CT, TIN, TA, TST>(c->g, cf, a, c->st);
+  prof_mark(c);
+  return e;
+}
+
 template <class CT, class TST>
 static int adjoint_step_t(ns_ctx* c, const Coef<CT>& cf, const double* w, const double* s,
                           const double* lam, const float* nu, double* lo, double* sbar) {
@@ -128,21 +132,21 @@ static int adjoint_step_t(ns_ctx* c, const Coef<CT>& cf, const double* w, const 
     ns::AdjArgs<TST, double, TST> a{};
     a.W = W4; a.A = lam; a.ca = dt / 6.0; a.nu = nu; a.lam = lam; a.lacc = lo; a.lacc_init = 1;
     a.Anext = Aa; a.cl = dt / 3.0; a.cg = dt; a.sbar = sbar;
-    if (ns::launch_adj_stage<CT, TST, double, TST>(c->g, cf, a, c->st) != cudaSuccess) return NS_ERR_CUDA;
+    if (adj_launch(c, cf, a) != cudaSuccess) return NS_ERR_CUDA;
   }
   {
     ns::AdjArgs<TST, TST, TST> a{};
     a.W = W3; a.A = Aa; a.ca = 1.0; a.nu = nu; a.lam = lam; a.lacc = lo; a.lacc_init = 0;
     a.Anext = Ab; a.cl = dt / 3.0; a.cg = 0.5 * dt; a.sbar = sbar;
-    if (ns::launch_adj_stage<CT, TST, TST, TST>(c->g, cf, a, c->st) != cudaSuccess) return NS_ERR_CUDA;
+    if (adj_launch(c, cf, a) != cudaSuccess) return NS_ERR_CUDA;
     a.W = W2; a.A = Ab; a.Anext = Aa; a.cl = dt / 6.0; a.cg = 0.5 * dt;
-    if (ns::launch_adj_stage<CT, TST, TST, TST>(c->g, cf, a, c->st) != cudaSuccess) return NS_ERR_CUDA;
+    if (adj_launch(c, cf, a) != cudaSuccess) return NS_ERR_CUDA;
   }
   {
     ns::AdjArgs<double, TST, TST> a{};
-    a.W = w; a.A = Aa; a.ca = 1.0; a.nu = nu; a.lam = lam; a.lacc = lo; a.lacc_init = 0;
+    a.W = w; a.A = Aa; a.ca = 1.0; a.nu = nu; a.lam = nullptr; a.lacc = lo; a.lacc_init = 0;
     a.Anext = nullptr; a.sbar = sbar;
-    if (ns::launch_adj_stage<CT, double, TST, TST>(c->g, cf, a, c->st) != cudaSuccess) return NS_ERR_CUDA;
+    if (adj_launch(c, cf, a) != cudaSuccess) return NS_ERR_CUDA;
   }
   return NS_OK;
 }
@@ -171,8 +175,7 @@ int ns_create(const ns_params* p, void* stream, ns_ctx** out) {
   if (p->precision != NS_FP64 && p->precision != NS_MIXED) return NS_ERR_ARG;
   if ((long long)p->nx * p->ny > (1LL << 31) || (long long)p->nx * p->ny * p->nz > (1LL << 40))
     return NS_ERR_ARG;
-  ns_ctx* c = (ns_ctx*)calloc(1, sizeof(ns_ctx));
-  if (!c) return NS_ERR_ARG;
+  ns_ctx* c = new ns_ctx();
   c->p = *p;
   c->st = (cudaStream_t)stream;
   c->g.nx = p->nx;
@@ -224,7 +227,8 @@ void ns_destroy(ns_ctx* c) {
   }
   if (c->scratch) cudaFree(c->scratch);
   if (c->err) cudaFree(c->err);
-  free(c);
+  for (cudaEvent_t ev : c->events) cudaEventDestroy(ev);
+  delete c;
 }
 
 int ns_set_stream(ns_ctx* c, void* stream) {
@@ -373,3 +377,25 @@ int ns_last_error(ns_ctx* c) {
 }
 
 }  // extern "C"
+
+extern "C" int ns_profile_enable(ns_ctx* c, int on) {
+  if (!c) return NS_ERR_ARG;
+  if (on && !c->prof_on) c->prof_used = 0;
+  c->prof_on = on != 0;
+  return NS_OK;
+}
+
+extern "C" int ns_profile_read(ns_ctx* c, double* ms, long long* launches) {
+  if (!c || !ms || !launches) return NS_ERR_ARG;
+  if (cudaStreamSynchronize(c->st) != cudaSuccess) return NS_ERR_CUDA;
+  double tot = 0.0;
+  for (size_t i = 0; i + 1 < c->prof_used; i += 2) {
+    float t = 0.0f;
+    if (cudaEventElapsedTime(&t, c->events[i], c->events[i + 1]) != cudaSuccess) return NS_ERR_CUDA;
+    tot += t;
+  }
+  *ms = tot;
+  *launches = (long long)(c->prof_used / 2);
+  c->prof_used = 0;
+  return NS_OK;
+}

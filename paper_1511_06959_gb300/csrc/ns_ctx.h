@@ -1,0 +1,28 @@
+// Context object behind the opaque ns_ctx handle of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "../../include/ns_adjoint.h"
+#include "ns_common.cuh"
+
+struct ns_ctx {
+  ns_params p;
+  cudaStream_t st = nullptr;
+  ns::GridDesc g;
+  ns::Coef<double> cd;
+  ns::Coef<float> cf;
+  ns::Coef<ns::Dual> cx;
+  size_t field = 0;              // elements of one [batch][5][cells] field
+  void* stage[5] = {};           // stage buffers (double in FP64 mode, float in MIXED mode)
+  double* tan[5] = {};           // FP64 buffers of the tangent step, allocated on first use
+  double* scratch = nullptr;     // reduction scratch
+  size_t scratch_n = 0;
+  unsigned* err = nullptr;       // sticky device error word
+  size_t ws_bytes = 0;
+  bool prof_on = false;          // event pairs around adjoint-stage launches
+  size_t prof_used = 0;
+  std::vector<cudaEvent_t> events;
+};

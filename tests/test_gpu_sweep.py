@@ -1,0 +1,111 @@
+"""GPU checkpointed sweep (ns_adjoint_run) against the oracle's store-all adjoint and
+across schedules: replay is bitwise deterministic, so every schedule gives the same
+bits; the added viscosity, sigma_1 statistics and the adjoint-energy series follow the
+oracle."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import ns_oracle as O
+from paper_1511_06959_gb300 import synth
+from tests.test_gpu_parity import _api, dev, host, make_solver, rel_l2
+from tests.test_oracle_primal import params_for
+
+pytestmark = pytest.mark.gpu
+
+
+def _run(api, S, w0, N, schedule, param, s=None, lam_coef=0.0, tau=0.0, energy=False, sigma=False):
+    opts = S.run_opts(N, schedule, param, lam_coef, tau, energy, sigma)
+    arena = torch.empty(S.arena_bytes(opts), dtype=torch.uint8, device="cuda")
+    J = torch.empty(S.batch, dtype=torch.float64, device="cuda")
+    lam0 = torch.empty(w0.shape, dtype=torch.float64, device="cuda")
+    sbar = torch.empty_like(lam0)
+    E = torch.zeros((N + 1, S.batch), dtype=torch.float64, device="cuda") if energy else None
+    st = torch.zeros((N, S.batch, 2), dtype=torch.float64, device="cuda") if sigma else None
+    S.adjoint_run(dev(w0), opts, arena, J, lam0, s=None if s is None else dev(s), sbar=sbar,
+                  energy=E, sigma_stats=st)
+    torch.cuda.synchronize()
+    return J, lam0, sbar, E, st
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_schedules_agree_bitwise_and_match_oracle(prec):
+    api = _api()
+    w0 = synth.isentropic_vortex(33, 10, 3, noise=1e-3, seed=5)
+    P = params_for(w0, mu=1e-3, dt=4e-3)
+    s = np.zeros_like(w0)
+    s[1] = 0.05 * synth.forcing_bumps(33, 10, 3, n=4)[0]
+    N = 13
+    S = make_solver(api, w0, P, prec)
+    res = [_run(api, S, w0, N, sch, prm, s) for sch, prm in [(0, 0), (1, 4), (2, 3), (2, 1)]]
+    for J, lam, sb, _, _ in res[1:]:
+        assert torch.equal(J, res[0][0])
+        assert torch.equal(lam, res[0][1])
+        assert torch.equal(sb, res[0][2])
+    ws, Jref = O.primal_run(w0, P, N, s)
+    lam_ref, sbar_ref = O.adjoint_run(ws, P, s)
+    tol = 1e-10 if prec == 0 else 1e-4
+    J, lam, sb, _, _ = res[0]
+    assert abs(J.item() - Jref) <= tol * abs(Jref)
+    assert rel_l2(host(lam), lam_ref) < tol
+    assert rel_l2(host(sb), sbar_ref) < tol
+
+
+def test_stabilised_sweep_energy_and_sigma_series():
+    api = _api()
+    w0 = synth.isentropic_vortex(40, 12, 1, noise=1e-3, seed=6)
+    P = params_for(w0, mu=1e-3, dt=4e-3)
+    N = 9
+    lam_coef = 0.5 * P.dx[0] ** 2
+    S = make_solver(api, w0, P)
+    J, lam, sb, E, st = _run(api, S, w0, N, 2, 2, lam_coef=lam_coef, energy=True, sigma=True)
+    assert S.last_error() == 0
+    ws, Jref = O.primal_run(w0, P, N)
+    nu_of = lambda w: lam_coef * O.sigma1_field(w, P)
+    lam_ref, _ = O.adjoint_run(ws, P, None, nu_of)
+    assert rel_l2(host(lam), lam_ref) < 1e-6
+    # energy series E(w^n, lam^n): recompute lam^n with the oracle sweep
+    lam_n = np.zeros_like(w0)
+    Eref = np.zeros(N + 1)
+    lam_n = O.objective_grad(ws[N], P) / N
+    Eref[N] = O.adjoint_energy(ws[N], lam_n, P)
+    for n in range(N, 0, -1):
+        lam_n, _ = O.rk4_adjoint_step(ws[n - 1], lam_n, P, None, nu_of(ws[n - 1]))
+        if n - 1 >= 1:
+            lam_n = lam_n + O.objective_grad(ws[n - 1], P) / N
+        Eref[n - 1] = O.adjoint_energy(ws[n - 1], lam_n, P)
+    np.testing.assert_allclose(host(E)[:, 0], Eref, rtol=1e-6)
+    sig_ref = np.array([[O.sigma1_field(ws[n], P).max(), O.sigma1_field(ws[n], P).mean()]
+                        for n in range(N)])
+    np.testing.assert_allclose(host(st)[:, 0, :], sig_ref, rtol=1e-6)
+
+
+def test_budget_too_small_is_reported():
+    api = _api()
+    w0 = synth.isentropic_vortex(33, 10, 1, noise=0.0)
+    P = params_for(w0, mu=1e-3, dt=4e-3)
+    S = make_solver(api, w0, P)
+    opts = S.run_opts(10, 0, 0)
+    need = S.arena_bytes(opts)
+    arena = torch.empty(need - 256, dtype=torch.uint8, device="cuda")
+    J = torch.empty(1, dtype=torch.float64, device="cuda")
+    lam0 = torch.empty(w0.shape, dtype=torch.float64, device="cuda")
+    with pytest.raises(api.NsError) as e:
+        S.adjoint_run(dev(w0), opts, arena, J, lam0)
+    assert e.value.code == api.NS_ERR_BUDGET
+
+
+def test_batched_sweep_matches_single_boxes():
+    api = _api()
+    shape = (33, 8, 4)
+    ws0 = np.stack([synth.isentropic_vortex(*shape, noise=1e-3, seed=20 + i) for i in range(3)])
+    P = params_for(ws0[0], mu=1e-3, dt=4e-3)
+    N = 6
+    S = make_solver(api, ws0[0], P, batch=3)
+    J, lam, _, _, _ = _run(api, S, ws0, N, 1, 2)
+    S1 = make_solver(api, ws0[0], P)
+    for i in range(3):
+        Ji, li, _, _, _ = _run(api, S1, ws0[i], N, 1, 2)
+        assert J[i].item() == Ji.item()
+        assert torch.equal(lam[i], li[0] if li.dim() == 5 else li)
