@@ -144,6 +144,11 @@ int ns_dot(ns_ctx* ctx, const double* a, const double* phi, int nphi, size_t n, 
 int ns_combine(ns_ctx* ctx, const double* theta, const double* phi, int nphi, size_t n,
                double* s);
 
+/* out[i] = in[i] rounded to binary32 (nearest, ties to even) for n elements, on the
+ * context's stream; results below the smallest normal float flush to signed zero.
+ * This is the conversion the mixed-precision path uses for its float mirrors. */
+int ns_to_float(ns_ctx* ctx, const double* in, float* out, size_t n);
+
 /* max over all cells of |u| + c; writes one double to the device pointer out. */
 int ns_max_wave_speed(ns_ctx* ctx, const double* w, double* out);
 

@@ -29,7 +29,7 @@ EXPORTED = [
     "ns_objective", "ns_growth_sigma1", "ns_add_adjoint_viscosity", "ns_apply_adjoint_viscosity",
     "ns_adjoint_energy", "ns_dot", "ns_combine", "ns_max_wave_speed", "ns_last_error",
     "ns_error_string", "ns_plan", "ns_run_arena_bytes", "ns_adjoint_run", "ns_profile_enable",
-    "ns_profile_read",
+    "ns_profile_read", "ns_to_float",
 ]
 
 NS_CKPT_ALL = 0
@@ -100,6 +100,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "ns_dot": ([P, P, P, I, S, P], I),
         "ns_combine": ([P, P, P, I, S, P], I),
         "ns_max_wave_speed": ([P, P, P], I),
+        "ns_to_float": ([P, P, P, S], I),
         "ns_last_error": ([P], I),
         "ns_error_string": ([I], ctypes.c_char_p),
         "ns_plan": ([I, I, I, P, I, ctypes.POINTER(I), ctypes.POINTER(I),
@@ -262,6 +263,10 @@ class Solver:
         n = s.numel()
         _check(self.lib.ns_combine(self._ctx, _ptr(theta, torch.float64), _ptr(phi, torch.float64), nphi,
                                    n, _ptr(s, torch.float64)), "ns_combine")
+
+    def to_float(self, x, out):
+        _check(self.lib.ns_to_float(self._ctx, _ptr(x, torch.float64), _ptr(out, torch.float32), x.numel()),
+               "ns_to_float")
 
     def max_wave_speed(self, w, out):
         _check(self.lib.ns_max_wave_speed(self._ctx, _ptr(w, torch.float64), _ptr(out, torch.float64)),

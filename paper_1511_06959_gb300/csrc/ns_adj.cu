@@ -16,7 +16,10 @@
 // The convective part is sum_d A_d(w_c)^T (a(c+e_d) - a(c-e_d)) / (2 dx_d).  The sum of
 // primitive adjoints is then pulled back to conservative variables.
 //
-// Epilogue (FP64): lacc = (init ? lam : lacc) + g;  Anext = cl lam + cg g;  sbar += a.
+// Epilogue: the four stage products are summed in the stage type (G = sum_i g_i) and
+// only the last stage forms lam^n = lam^{n+1} + G in FP64 (one FP64 add per component
+// and step); the next seed is Anext = cl lam^{n+1} + cg g; the seeds a_i are summed
+// the same way for the source sensitivity.
 #include <type_traits>
 
 #include "ns_common.cuh"
@@ -26,39 +29,55 @@ namespace ns {
 
 namespace {
 
-template <class CT, class TIN>
-__device__ __forceinline__ void fill_prims(CT* __restrict__ sq, const GridDesc& g, int b, int k,
-                                           int x0, int y0, const TIN* __restrict__ W) {
+// Register-staged plane load (primal primitives and adjoint input) so that the next
+// plane's global loads overlap the current plane's work.
+static_assert(SP <= 2 * NT, "a plane must fit two load rounds");
+template <class CT>
+struct AdjPlaneRegs {
+  CT q[2][5];
+  CT a[2][5];
+};
+
+template <class CT, class TIN, class TA>
+__device__ __forceinline__ void adj_plane_load(AdjPlaneRegs<CT>& r, const GridDesc& g, int b, int k, int x0,
+                                               int y0, const TIN* __restrict__ W, const TA* __restrict__ A,
+                                               double ca) {
   const int kz = wrap(k, g.nz);
   const size_t boxoff = (size_t)b * 5 * g.cells + (size_t)kz * g.plane;
-  for (int t = threadIdx.x; t < SP; t += NT) {
-    const int ly = t / SX;
-    const int lx = t - ly * SX;
-    const size_t o = boxoff + (size_t)wrap(y0 + ly - 1, g.ny) * g.nx + wrap(x0 + lx - 1, g.nx);
-    const CT r = CT(W[o]);
-    const CT ir = CT(1) / r;
-    const CT u0 = CT(W[o + g.cells]) * ir;
-    const CT u1 = CT(W[o + 2 * g.cells]) * ir;
-    const CT u2 = CT(W[o + 3 * g.cells]) * ir;
-    sq[0 * SP + t] = r;
-    sq[1 * SP + t] = u0;
-    sq[2 * SP + t] = u1;
-    sq[3 * SP + t] = u2;
-    sq[4 * SP + t] = CT(W[o + 4 * g.cells]) * ir - CT(0.5) * (u0 * u0 + u1 * u1 + u2 * u2);
+  const CT cac = CT(ca);
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const int t = threadIdx.x + it * NT;
+    if (t < SP) {
+      const int ly = t / SX;
+      const int lx = t - ly * SX;
+      const size_t o = boxoff + (size_t)wrap(y0 + ly - 1, g.ny) * g.nx + wrap(x0 + lx - 1, g.nx);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        r.q[it][v] = cvt<CT>(W[o + v * g.cells]);
+        r.a[it][v] = cac * cvt<CT>(A[o + v * g.cells]);
+      }
+    }
   }
 }
 
-template <class CT, class TA>
-__device__ __forceinline__ void fill_adj(CT* __restrict__ sa, const GridDesc& g, int b, int k,
-                                         int x0, int y0, const TA* __restrict__ A, double ca) {
-  const int kz = wrap(k, g.nz);
-  const size_t boxoff = (size_t)b * 5 * g.cells + (size_t)kz * g.plane;
-  for (int t = threadIdx.x; t < SP; t += NT) {
-    const int ly = t / SX;
-    const int lx = t - ly * SX;
-    const size_t o = boxoff + (size_t)wrap(y0 + ly - 1, g.ny) * g.nx + wrap(x0 + lx - 1, g.nx);
+template <class CT>
+__device__ __forceinline__ void adj_plane_store(const AdjPlaneRegs<CT>& r, CT* __restrict__ sq,
+                                                CT* __restrict__ sa) {
 #pragma unroll
-    for (int v = 0; v < 5; ++v) sa[v * SP + t] = CT(ca * (double)A[o + v * g.cells]);
+  for (int it = 0; it < 2; ++it) {
+    const int t = threadIdx.x + it * NT;
+    if (t < SP) {
+      const CT ir = CT(1) / r.q[it][0];
+      const CT u0 = r.q[it][1] * ir, u1 = r.q[it][2] * ir, u2 = r.q[it][3] * ir;
+      sq[0 * SP + t] = r.q[it][0];
+      sq[1 * SP + t] = u0;
+      sq[2 * SP + t] = u1;
+      sq[3 * SP + t] = u2;
+      sq[4 * SP + t] = r.q[it][4] * ir - CT(0.5) * (u0 * u0 + u1 * u1 + u2 * u2);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) sa[v * SP + t] = r.a[it][v];
+    }
   }
 }
 
@@ -236,9 +255,14 @@ __global__ void __launch_bounds__(NT) k_adj_stage(GridDesc g, Coef<CT> c, AdjArg
   auto slot = [&](int k) { return (k - kz0 + 1) % 3; };
   auto zslot = [&](int k) { return (k - kz0 + 1) & 1; };   // z-face k + 1/2
 
-  for (int k = kz0 - 1; k <= kz0 + 1; ++k) {
-    fill_prims<CT>(sQ + slot(k) * 5 * SP, g, b, k, x0, y0, a.W);
-    fill_adj<CT>(sA + slot(k) * 5 * SP, g, b, k, x0, y0, a.A, a.ca);
+  {
+    AdjPlaneRegs<CT> p0, p1, p2;
+    adj_plane_load(p0, g, b, kz0 - 1, x0, y0, a.W, a.A, a.ca);
+    adj_plane_load(p1, g, b, kz0, x0, y0, a.W, a.A, a.ca);
+    adj_plane_load(p2, g, b, kz0 + 1, x0, y0, a.W, a.A, a.ca);
+    adj_plane_store(p0, sQ + slot(kz0 - 1) * 5 * SP, sA + slot(kz0 - 1) * 5 * SP);
+    adj_plane_store(p1, sQ + slot(kz0) * 5 * SP, sA + slot(kz0) * 5 * SP);
+    adj_plane_store(p2, sQ + slot(kz0 + 1) * 5 * SP, sA + slot(kz0 + 1) * 5 * SP);
   }
   __syncthreads();
   fill_S(sS, sQ, sA, c, slot(kz0 - 1));
@@ -251,6 +275,33 @@ __global__ void __launch_bounds__(NT) k_adj_stage(GridDesc g, Coef<CT> c, AdjArg
 
   for (int k = kz0; k < kz1; ++k) {
     const int sm = slot(k - 1), s0 = slot(k), sp = slot(k + 1);
+    const bool more = k + 1 < kz1;
+    AdjPlaneRegs<CT> pf;
+    if (more) adj_plane_load(pf, g, b, k + 2, x0, y0, a.W, a.A, a.ca);
+    // per-cell operands of the assembly and epilogue, loaded ahead of the face work
+    const size_t o0 = (size_t)b * 5 * g.cells + (size_t)k * g.plane + (size_t)gy * g.nx + gx;
+    CT nuv[7] = {CT(0), CT(0), CT(0), CT(0), CT(0), CT(0), CT(0)};
+    CT gin[5] = {CT(0), CT(0), CT(0), CT(0), CT(0)};
+    CT lfv[5] = {CT(0), CT(0), CT(0), CT(0), CT(0)};
+    if (valid) {
+      if (a.nu) {
+        const float* nub = a.nu + (size_t)b * g.cells;
+        const size_t pl = (size_t)k * g.plane;
+        const size_t row = pl + (size_t)gy * g.nx;
+        nuv[0] = CT(nub[row + gx]);
+        nuv[1] = CT(nub[row + wrap(gx - 1, g.nx)]);
+        nuv[2] = CT(nub[row + wrap(gx + 1, g.nx)]);
+        nuv[3] = CT(nub[pl + (size_t)wrap(gy - 1, g.ny) * g.nx + gx]);
+        nuv[4] = CT(nub[pl + (size_t)wrap(gy + 1, g.ny) * g.nx + gx]);
+        nuv[5] = CT(nub[(size_t)wrap(k - 1, g.nz) * g.plane + (size_t)gy * g.nx + gx]);
+        nuv[6] = CT(nub[(size_t)wrap(k + 1, g.nz) * g.plane + (size_t)gy * g.nx + gx]);
+      }
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        if (a.Gin) gin[v] = a.Gin[o0 + (size_t)v * g.cells];
+        if (a.Anext) lfv[v] = a.lamf[o0 + (size_t)v * g.cells];
+      }
+    }
     fill_S(sS, sQ, sA, c, sp);
     fill_Z(sZ + zslot(k) * 3 * SP, sQ, sA, c, s0, sp);
     {
@@ -367,20 +418,10 @@ __global__ void __launch_bounds__(NT) k_adj_stage(GridDesc g, Coef<CT> c, AdjArg
         rb = rb - ub[j] * u[j] * ir_;
       }
       CT gout[5] = {rb, mb[0], mb[1], mb[2], Eb};
-      const size_t o0 = (size_t)b * 5 * g.cells + (size_t)k * g.plane + (size_t)gy * g.nx + gx;
       // ---- added adjoint viscosity L_nu a
       if (a.nu) {
-        const size_t so = (size_t)b * g.cells;
-        const float* nub = a.nu + so;
-        const int kp = wrap(k + 1, g.nz), km = wrap(k - 1, g.nz);
-        const size_t pl = (size_t)k * g.plane;
-        const CT nc = CT(nub[pl + (size_t)gy * g.nx + gx]);
-        const CT nxm = CT(nub[pl + (size_t)gy * g.nx + wrap(gx - 1, g.nx)]);
-        const CT nxp = CT(nub[pl + (size_t)gy * g.nx + wrap(gx + 1, g.nx)]);
-        const CT nym = CT(nub[pl + (size_t)wrap(gy - 1, g.ny) * g.nx + gx]);
-        const CT nyp = CT(nub[pl + (size_t)wrap(gy + 1, g.ny) * g.nx + gx]);
-        const CT nzm = CT(nub[(size_t)km * g.plane + (size_t)gy * g.nx + gx]);
-        const CT nzp = CT(nub[(size_t)kp * g.plane + (size_t)gy * g.nx + gx]);
+        const CT nc = nuv[0], nxm = nuv[1], nxp = nuv[2], nym = nuv[3], nyp = nuv[4], nzm = nuv[5],
+                 nzp = nuv[6];
         const CT ix2 = c.idx[0] * c.idx[0], iy2 = c.idx[1] * c.idx[1], iz2 = c.idx[2] * c.idx[2];
 #pragma unroll
         for (int v = 0; v < 5; ++v) {
@@ -396,20 +437,22 @@ __global__ void __launch_bounds__(NT) k_adj_stage(GridDesc g, Coef<CT> c, AdjArg
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
         const size_t o = o0 + (size_t)v * g.cells;
-        const double gv = (double)gout[v];
-        const double lam = a.lam ? a.lam[o] : 0.0;
-        const double prev = a.lacc_init ? lam : a.lacc[o];
-        a.lacc[o] = prev + gv;
-        if (a.Anext) a.Anext[o] = (TST)(a.cl * lam + a.cg * gv);
-        if (a.sbar) a.sbar[o] += a.ca * (double)a.A[o];
+        const CT gs = gin[v] + gout[v];
+        if (a.Gout) a.Gout[o] = gs;
+        if (a.lam_out) a.lam_out[o] = (a.lam_in ? a.lam_in[o] : 0.0) + widen(gs);
+        if (a.Anext) a.Anext[o] = CT(a.cl) * lfv[v] + CT(a.cg) * gout[v];
+        if (a.SBout || a.sbar) {
+          const CT ss = (a.SBin ? a.SBin[o] : CT(0)) + A0[v * SP + ic];
+          if (a.SBout) a.SBout[o] = ss;
+          if (a.sbar) a.sbar[o] += widen(ss);
+        }
       }
     }
 #pragma unroll
     for (int v = 0; v < 7; ++v) zlo[v] = zhi[v];
     __syncthreads();
-    if (k + 1 < kz1) {
-      fill_prims<CT>(sQ + slot(k + 2) * 5 * SP, g, b, k + 2, x0, y0, a.W);
-      fill_adj<CT>(sA + slot(k + 2) * 5 * SP, g, b, k + 2, x0, y0, a.A, a.ca);
+    if (more) {
+      adj_plane_store(pf, sQ + slot(k + 2) * 5 * SP, sA + slot(k + 2) * 5 * SP);
       __syncthreads();
     }
   }
@@ -434,12 +477,6 @@ cudaError_t launch_adj_stage(const GridDesc& g, const Coef<CT>& c, const AdjArgs
 
 template cudaError_t launch_adj_stage<double, double, double, double>(
     const GridDesc&, const Coef<double>&, const AdjArgs<double, double, double>&, cudaStream_t);
-template cudaError_t launch_adj_stage<float, double, double, float>(
-    const GridDesc&, const Coef<float>&, const AdjArgs<double, double, float>&, cudaStream_t);
-template cudaError_t launch_adj_stage<float, double, float, float>(
-    const GridDesc&, const Coef<float>&, const AdjArgs<double, float, float>&, cudaStream_t);
-template cudaError_t launch_adj_stage<float, float, double, float>(
-    const GridDesc&, const Coef<float>&, const AdjArgs<float, double, float>&, cudaStream_t);
 template cudaError_t launch_adj_stage<float, float, float, float>(
     const GridDesc&, const Coef<float>&, const AdjArgs<float, float, float>&, cudaStream_t);
 

@@ -52,8 +52,15 @@ bool mixed(const ns_ctx* c) { return c->p.precision == NS_MIXED; }
 
 }  // namespace
 
+enum { WF = 0, LF = 1, W2 = 2, W3 = 3, W4 = 4, AA = 5, AB = 6, GS = 7, SB = 8 };
+
+template <class T>
+static T* buf(ns_ctx* c, int i) {
+  return (T*)c->stage[i];
+}
+
 static int ensure_tangent_buffers(ns_ctx* c) {
-  for (int i = 0; i < 5; ++i) {
+  for (int i = 0; i < 6; ++i) {
     if (!c->tan[i]) {
       if (cudaMalloc(&c->tan[i], c->field * sizeof(double)) != cudaSuccess) return NS_ERR_CUDA;
       c->ws_bytes += c->field * sizeof(double);
@@ -62,26 +69,26 @@ static int ensure_tangent_buffers(ns_ctx* c) {
   return NS_OK;
 }
 
-template <class CT, class TST>
-static int primal_step_t(ns_ctx* c, const Coef<CT>& cf, const double* w, const double* s, double* wo,
-                         TST* Wa, TST* Wb) {
+// RK4 with the increment sum D = dt (k1/6 + k2/3 + k3/3 + k4/6) in the stage type and
+// one FP64 add w^{n+1} = w^n + D at the last stage.
+template <class CT>
+static int primal_step_t(ns_ctx* c, const Coef<CT>& cf, const CT* W1, const double* w, const double* s,
+                         double* wo) {
   const double dt = c->p.dt;
-  cudaError_t e;
-  {
-    ns::StageArgs<double, TST> a{};
-    a.W = w; a.base = w; a.src = s; a.acc = wo; a.acc_init = 1; a.cacc = dt / 6.0;
-    a.Wout = Wa; a.cout = 0.5 * dt;
-    if ((e = ns::launch_rhs_stage<CT, double, TST>(c->g, cf, a, c->st)) != cudaSuccess) return NS_ERR_CUDA;
-  }
-  const TST* in[3] = {Wa, Wb, Wa};
-  TST* outs[3] = {Wb, Wa, nullptr};
-  const double cacc[3] = {dt / 3.0, dt / 3.0, dt / 6.0};
-  const double cout[3] = {0.5 * dt, dt, 0.0};
-  for (int i = 0; i < 3; ++i) {
-    ns::StageArgs<TST, TST> a{};
-    a.W = in[i]; a.base = w; a.src = s; a.acc = wo; a.acc_init = 0; a.cacc = cacc[i];
+  CT* Wa = buf<CT>(c, W2);
+  CT* Wb = buf<CT>(c, W3);
+  CT* D = buf<CT>(c, GS);
+  const CT* in[4] = {W1, Wa, Wb, Wa};
+  CT* outs[4] = {Wa, Wb, Wa, nullptr};
+  const double cacc[4] = {dt / 6.0, dt / 3.0, dt / 3.0, dt / 6.0};
+  const double cout[4] = {0.5 * dt, 0.5 * dt, dt, 0.0};
+  for (int i = 0; i < 4; ++i) {
+    ns::StageArgs<CT, CT> a{};
+    a.W = in[i]; a.base = W1; a.src = s;
+    a.dacc = D; a.dacc_init = i == 0; a.cacc = cacc[i];
     a.Wout = outs[i]; a.cout = cout[i];
-    if ((e = ns::launch_rhs_stage<CT, TST, TST>(c->g, cf, a, c->st)) != cudaSuccess) return NS_ERR_CUDA;
+    if (i == 3) { a.wbase = w; a.wout = wo; }
+    if (ns::launch_rhs_stage<CT, CT, CT>(c->g, cf, a, c->st) != cudaSuccess) return NS_ERR_CUDA;
   }
   return NS_OK;
 }
@@ -105,47 +112,45 @@ static cudaError_t adj_launch(ns_ctx* c, const Coef<CT>& cf, const ns::AdjArgs<T
   return e;
 }
 
-template <class CT, class TST>
-static int adjoint_step_t(ns_ctx* c, const Coef<CT>& cf, const double* w, const double* s,
+// Recompute W2..W4 from W1 = w^n, then the transposed stages 4, 3, 2, 1 with the
+// stage products summed in the stage type and lam^n = lam^{n+1} + G formed in FP64.
+template <class CT>
+static int adjoint_step_t(ns_ctx* c, const Coef<CT>& cf, const CT* W1, const CT* lamf, const double* s,
                           const double* lam, const float* nu, double* lo, double* sbar) {
   const double dt = c->p.dt;
-  TST* W2 = (TST*)c->stage[0];
-  TST* W3 = (TST*)c->stage[1];
-  TST* W4 = (TST*)c->stage[2];
-  TST* Aa = (TST*)c->stage[3];
-  TST* Ab = (TST*)c->stage[4];
-  // recompute the stage states W2..W4 from w^n
-  {
-    ns::StageArgs<double, TST> a{};
-    a.W = w; a.base = w; a.src = s; a.Wout = W2; a.cout = 0.5 * dt;
-    if (ns::launch_rhs_stage<CT, double, TST>(c->g, cf, a, c->st) != cudaSuccess) return NS_ERR_CUDA;
+  CT* Wst[3] = {buf<CT>(c, W2), buf<CT>(c, W3), buf<CT>(c, W4)};
+  CT* Aa = buf<CT>(c, AA);
+  CT* Ab = buf<CT>(c, AB);
+  CT* G = buf<CT>(c, GS);
+  CT* S = buf<CT>(c, SB);
+  const CT* rin[3] = {W1, Wst[0], Wst[1]};
+  const double rc[3] = {0.5 * dt, 0.5 * dt, dt};
+  for (int i = 0; i < 3; ++i) {
+    ns::StageArgs<CT, CT> a{};
+    a.W = rin[i]; a.base = W1; a.src = s; a.Wout = Wst[i]; a.cout = rc[i];
+    if (ns::launch_rhs_stage<CT, CT, CT>(c->g, cf, a, c->st) != cudaSuccess) return NS_ERR_CUDA;
   }
-  {
-    ns::StageArgs<TST, TST> a{};
-    a.W = W2; a.base = w; a.src = s; a.Wout = W3; a.cout = 0.5 * dt;
-    if (ns::launch_rhs_stage<CT, TST, TST>(c->g, cf, a, c->st) != cudaSuccess) return NS_ERR_CUDA;
-    a.W = W3; a.Wout = W4; a.cout = dt;
-    if (ns::launch_rhs_stage<CT, TST, TST>(c->g, cf, a, c->st) != cudaSuccess) return NS_ERR_CUDA;
-  }
-  // transposed stages 4, 3, 2, 1
-  {
-    ns::AdjArgs<TST, double, TST> a{};
-    a.W = W4; a.A = lam; a.ca = dt / 6.0; a.nu = nu; a.lam = lam; a.lacc = lo; a.lacc_init = 1;
-    a.Anext = Aa; a.cl = dt / 3.0; a.cg = dt; a.sbar = sbar;
-    if (adj_launch(c, cf, a) != cudaSuccess) return NS_ERR_CUDA;
-  }
-  {
-    ns::AdjArgs<TST, TST, TST> a{};
-    a.W = W3; a.A = Aa; a.ca = 1.0; a.nu = nu; a.lam = lam; a.lacc = lo; a.lacc_init = 0;
-    a.Anext = Ab; a.cl = dt / 3.0; a.cg = 0.5 * dt; a.sbar = sbar;
-    if (adj_launch(c, cf, a) != cudaSuccess) return NS_ERR_CUDA;
-    a.W = W2; a.A = Ab; a.Anext = Aa; a.cl = dt / 6.0; a.cg = 0.5 * dt;
-    if (adj_launch(c, cf, a) != cudaSuccess) return NS_ERR_CUDA;
-  }
-  {
-    ns::AdjArgs<double, TST, TST> a{};
-    a.W = w; a.A = Aa; a.ca = 1.0; a.nu = nu; a.lam = nullptr; a.lacc = lo; a.lacc_init = 0;
-    a.Anext = nullptr; a.sbar = sbar;
+  const CT* Wi[4] = {Wst[2], Wst[1], Wst[0], W1};
+  const CT* Ain[4] = {lamf, Aa, Ab, Aa};
+  CT* Aout[4] = {Aa, Ab, Aa, nullptr};
+  const double ca[4] = {dt / 6.0, 1.0, 1.0, 1.0};
+  const double cl[4] = {dt / 3.0, dt / 3.0, dt / 6.0, 0.0};
+  const double cg[4] = {dt, 0.5 * dt, 0.5 * dt, 0.0};
+  for (int i = 0; i < 4; ++i) {
+    ns::AdjArgs<CT, CT, CT> a{};
+    a.W = Wi[i]; a.A = Ain[i]; a.ca = ca[i]; a.nu = nu; a.lamf = lamf;
+    a.Gin = i == 0 ? nullptr : G;
+    a.Anext = Aout[i]; a.cl = cl[i]; a.cg = cg[i];
+    if (i < 3) {
+      a.Gout = G;
+    } else {
+      a.lam_in = lam;
+      a.lam_out = lo;
+    }
+    if (sbar) {
+      a.SBin = i == 0 ? nullptr : S;
+      if (i < 3) a.SBout = S; else a.sbar = sbar;
+    }
     if (adj_launch(c, cf, a) != cudaSuccess) return NS_ERR_CUDA;
   }
   return NS_OK;
@@ -204,7 +209,7 @@ int ns_create(const ns_params* p, void* stream, ns_ctx** out) {
   c->field = (size_t)5 * c->g.cells * p->batch;
   const size_t esz = p->precision == NS_MIXED ? sizeof(float) : sizeof(double);
   cudaError_t e = cudaSuccess;
-  for (int i = 0; i < 5 && e == cudaSuccess; ++i) e = cudaMalloc(&c->stage[i], c->field * esz);
+  for (int i = 0; i < ns_ctx::NSTAGE && e == cudaSuccess; ++i) e = cudaMalloc(&c->stage[i], c->field * esz);
   c->scratch_n = ns::diag_scratch_doubles(c->g, 256);
   if (e == cudaSuccess) e = cudaMalloc(&c->scratch, c->scratch_n * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&c->err, sizeof(unsigned));
@@ -214,17 +219,17 @@ int ns_create(const ns_params* p, void* stream, ns_ctx** out) {
     ns_destroy(c);
     return NS_ERR_CUDA;
   }
-  c->ws_bytes = 5 * c->field * esz + c->scratch_n * sizeof(double) + sizeof(unsigned);
+  c->ws_bytes = ns_ctx::NSTAGE * c->field * esz + c->scratch_n * sizeof(double) + sizeof(unsigned);
   *out = c;
   return NS_OK;
 }
 
 void ns_destroy(ns_ctx* c) {
   if (!c) return;
-  for (int i = 0; i < 5; ++i) {
+  for (int i = 0; i < ns_ctx::NSTAGE; ++i)
     if (c->stage[i]) cudaFree(c->stage[i]);
+  for (int i = 0; i < 6; ++i)
     if (c->tan[i]) cudaFree(c->tan[i]);
-  }
   if (c->scratch) cudaFree(c->scratch);
   if (c->err) cudaFree(c->err);
   for (cudaEvent_t ev : c->events) cudaEventDestroy(ev);
@@ -248,12 +253,14 @@ size_t ns_workspace_bytes(const ns_ctx* c) { return c ? c->ws_bytes : 0; }
 int ns_rhs(ns_ctx* c, const double* w, const double* s, double* R) {
   if (!c || !w || !R || (const double*)R == w) return NS_ERR_ARG;
   if (mixed(c)) {
-    ns::StageArgs<double, float> a{};
-    a.W = w; a.src = s; a.acc = R; a.acc_init = 1; a.cacc = 1.0;
-    return cuerr(ns::launch_rhs_stage<float, double, float>(c->g, c->cf, a, c->st));
+    float* wf = buf<float>(c, WF);
+    if (ns::launch_to_float(w, wf, c->field, c->st) != cudaSuccess) return NS_ERR_CUDA;
+    ns::StageArgs<float, float> a{};
+    a.W = wf; a.src = s; a.cacc = 1.0; a.wout = R;
+    return cuerr(ns::launch_rhs_stage<float, float, float>(c->g, c->cf, a, c->st));
   }
   ns::StageArgs<double, double> a{};
-  a.W = w; a.src = s; a.acc = R; a.acc_init = 1; a.cacc = 1.0;
+  a.W = w; a.src = s; a.cacc = 1.0; a.wout = R;
   return cuerr(ns::launch_rhs_stage<double, double, double>(c->g, c->cd, a, c->st));
 }
 
@@ -262,16 +269,18 @@ int ns_rhs_tangent(ns_ctx* c, const double* w, const double* wd, double* Rd) {
   int r = ensure_tangent_buffers(c);
   if (r) return r;
   ns::StageArgs<double, double> a{};
-  a.W = w; a.Wd = wd;
-  a.acc = c->tan[0]; a.accd = Rd; a.acc_init = 1; a.cacc = 1.0;
+  a.W = w; a.Wd = wd; a.cacc = 1.0; a.woutd = Rd;
   return cuerr(ns::launch_rhs_stage<Dual, double, double>(c->g, c->cx, a, c->st));
 }
 
 int ns_primal_step(ns_ctx* c, const double* w, const double* s, double* wo) {
   if (!c || !w || !wo || wo == w || wo == s) return NS_ERR_ARG;
-  if (mixed(c))
-    return primal_step_t<float, float>(c, c->cf, w, s, wo, (float*)c->stage[0], (float*)c->stage[1]);
-  return primal_step_t<double, double>(c, c->cd, w, s, wo, (double*)c->stage[0], (double*)c->stage[1]);
+  if (mixed(c)) {
+    float* wf = buf<float>(c, WF);
+    if (ns::launch_to_float(w, wf, c->field, c->st) != cudaSuccess) return NS_ERR_CUDA;
+    return primal_step_t<float>(c, c->cf, wf, w, s, wo);
+  }
+  return primal_step_t<double>(c, c->cd, w, w, s, wo);
 }
 
 int ns_tangent_step(ns_ctx* c, const double* w, const double* s, const double* wd, const double* sd,
@@ -280,7 +289,8 @@ int ns_tangent_step(ns_ctx* c, const double* w, const double* s, const double* w
   int r = ensure_tangent_buffers(c);
   if (r) return r;
   const double dt = c->p.dt;
-  double *acc = c->tan[0], *Wa = c->tan[1], *Wb = c->tan[2], *Wda = c->tan[3], *Wdb = c->tan[4];
+  double *Wa = c->tan[0], *Wb = c->tan[1], *Wda = c->tan[2], *Wdb = c->tan[3], *D = c->tan[4],
+         *Dd = c->tan[5];
   const double* Win[4] = {w, Wa, Wb, Wa};
   const double* Wdin[4] = {wd, Wda, Wdb, Wda};
   double* Wout[4] = {Wa, Wb, Wa, nullptr};
@@ -291,8 +301,9 @@ int ns_tangent_step(ns_ctx* c, const double* w, const double* s, const double* w
     ns::StageArgs<double, double> a{};
     a.W = Win[i]; a.Wd = Wdin[i];
     a.base = w; a.based = wd; a.src = s; a.srcd = sd;
-    a.acc = acc; a.accd = wdo; a.acc_init = i == 0; a.cacc = cacc[i];
+    a.dacc = D; a.daccd = Dd; a.dacc_init = i == 0; a.cacc = cacc[i];
     a.Wout = Wout[i]; a.Woutd = Wdout[i]; a.cout = cout[i];
+    if (i == 3) { a.wbased = wd; a.woutd = wdo; }
     if (ns::launch_rhs_stage<Dual, double, double>(c->g, c->cx, a, c->st) != cudaSuccess) return NS_ERR_CUDA;
   }
   return NS_OK;
@@ -302,31 +313,46 @@ int ns_adjoint_step(ns_ctx* c, const double* w, const double* s, const double* l
                     double* lo, double* sbar) {
   if (!c || !w || !lam || !lo || lo == lam || lo == w || (sbar && (sbar == lo || sbar == lam)))
     return NS_ERR_ARG;
-  if (mixed(c)) return adjoint_step_t<float, float>(c, c->cf, w, s, lam, nu, lo, sbar);
-  return adjoint_step_t<double, double>(c, c->cd, w, s, lam, nu, lo, sbar);
+  if (mixed(c)) {
+    float* wf = buf<float>(c, WF);
+    float* lf = buf<float>(c, LF);
+    if (ns::launch_to_float(w, wf, c->field, c->st) != cudaSuccess) return NS_ERR_CUDA;
+    if (ns::launch_to_float(lam, lf, c->field, c->st) != cudaSuccess) return NS_ERR_CUDA;
+    return adjoint_step_t<float>(c, c->cf, wf, lf, s, lam, nu, lo, sbar);
+  }
+  return adjoint_step_t<double>(c, c->cd, w, lam, s, lam, nu, lo, sbar);
 }
 
 int ns_rhs_transpose(ns_ctx* c, const double* w, const double* a_, const float* nu, double* out) {
   if (!c || !w || !a_ || !out || out == w || out == a_) return NS_ERR_ARG;
   if (mixed(c)) {
-    ns::AdjArgs<double, double, float> a{};
-    a.W = w; a.A = a_; a.ca = 1.0; a.nu = nu; a.lacc = out; a.lacc_init = 1;
-    return cuerr(ns::launch_adj_stage<float, double, double, float>(c->g, c->cf, a, c->st));
+    float* wf = buf<float>(c, WF);
+    float* af = buf<float>(c, LF);
+    if (ns::launch_to_float(w, wf, c->field, c->st) != cudaSuccess) return NS_ERR_CUDA;
+    if (ns::launch_to_float(a_, af, c->field, c->st) != cudaSuccess) return NS_ERR_CUDA;
+    ns::AdjArgs<float, float, float> a{};
+    a.W = wf; a.A = af; a.ca = 1.0; a.nu = nu; a.lam_out = out;
+    return cuerr(ns::launch_adj_stage<float, float, float, float>(c->g, c->cf, a, c->st));
   }
   ns::AdjArgs<double, double, double> a{};
-  a.W = w; a.A = a_; a.ca = 1.0; a.nu = nu; a.lacc = out; a.lacc_init = 1;
+  a.W = w; a.A = a_; a.ca = 1.0; a.nu = nu; a.lam_out = out;
   return cuerr(ns::launch_adj_stage<double, double, double, double>(c->g, c->cd, a, c->st));
 }
 
 int ns_objective(ns_ctx* c, const double* w, double weight, double* J_acc, double* lam) {
   if (!c || !w || !J_acc || lam == w) return NS_ERR_ARG;
   const int i0 = c->p.plane_i;
-  return cuerr(ns::launch_objective(c->g, c->p.gamma, i0, c->p.pt_in, w, weight, J_acc, lam, c->err, c->st));
+  return cuerr(ns::launch_objective(c->g, c->p.gamma, i0, c->p.pt_in, w, weight, J_acc, lam, c->err,
+                                    c->scratch, c->st));
 }
 
 int ns_growth_sigma1(ns_ctx* c, const double* w, float* sigma1, double* stats) {
   if (!c || !w || !sigma1) return NS_ERR_ARG;
-  if (mixed(c)) return cuerr(ns::launch_sigma1<float>(c->g, c->cf, w, sigma1, stats, c->scratch, c->st));
+  if (mixed(c)) {
+    float* wf = buf<float>(c, WF);
+    if (ns::launch_to_float(w, wf, c->field, c->st) != cudaSuccess) return NS_ERR_CUDA;
+    return cuerr(ns::launch_sigma1<float>(c->g, c->cf, wf, sigma1, stats, c->scratch, c->st));
+  }
   return cuerr(ns::launch_sigma1<double>(c->g, c->cd, w, sigma1, stats, c->scratch, c->st));
 }
 
@@ -347,7 +373,7 @@ int ns_apply_adjoint_viscosity(ns_ctx* c, const float* nu, const double* a, doub
 int ns_adjoint_energy(ns_ctx* c, const double* w, const double* lam, double* E) {
   if (!c || !w || !lam || !E) return NS_ERR_ARG;
   const double dV = c->p.dx * c->p.dy * c->p.dz;
-  return cuerr(ns::launch_energy(c->g, c->p.gamma, dV, w, lam, E, c->scratch, c->err, c->st));
+  return cuerr(ns::launch_energy(c->g, c->p.gamma, dV, w, lam, E, c->scratch, c->err, mixed(c), c->st));
 }
 
 int ns_dot(ns_ctx* c, const double* a, const double* phi, int nphi, size_t n, double* out) {
@@ -358,6 +384,11 @@ int ns_dot(ns_ctx* c, const double* a, const double* phi, int nphi, size_t n, do
 int ns_combine(ns_ctx* c, const double* theta, const double* phi, int nphi, size_t n, double* s) {
   if (!c || !theta || !phi || !s || nphi < 1 || n == 0) return NS_ERR_ARG;
   return cuerr(ns::launch_combine(theta, phi, nphi, n, s, c->st));
+}
+
+int ns_to_float(ns_ctx* c, const double* in, float* out, size_t n) {
+  if (!c || !in || !out || n == 0) return NS_ERR_ARG;
+  return cuerr(ns::launch_to_float(in, out, n, c->st));
 }
 
 int ns_max_wave_speed(ns_ctx* c, const double* w, double* out) {

@@ -36,9 +36,57 @@ struct Coef {
 };
 
 __device__ __forceinline__ int wrap(int i, int n) {
+  if (i >= 0 && i < n) return i;
   i %= n;
   return i < 0 ? i + n : i;
 }
+
+// ---------------------------------------------------------------------------------
+// IEEE-754 binary64 <-> binary32 conversions in integer arithmetic.  GB300 issues
+// FP64 instructions at a small fraction of the FP32 rate, so the mixed-precision path
+// converts with integer ALU operations instead, from the field layout of the formats
+// (sign, biased exponent, fraction):
+//   d2f: round to nearest, ties to even; results below the smallest normal float
+//        (2^-126) flush to signed zero; overflow gives infinity; NaN stays NaN.
+//   f2d: exact for normal floats and zero; subnormal floats flush to signed zero.
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ float d2f(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x);
+  const unsigned lo = (unsigned)__double2loint(x);
+  const unsigned sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7FFu);
+  const unsigned frac_hi = hi & 0xFFFFFu;            // top 20 fraction bits
+  if (e == 0x7FF) {                                   // inf / nan
+    const bool nan = (frac_hi | lo) != 0u;
+    return __uint_as_float(sign | 0x7F800000u | (nan ? 0x00400000u : 0u));
+  }
+  const int fe = e - 1023 + 127;
+  if (fe <= 0) return __uint_as_float(sign);          // zero, subnormal, underflow
+  if (fe >= 255) return __uint_as_float(sign | 0x7F800000u);
+  const unsigned fm = (frac_hi << 3) | (lo >> 29);    // 23 fraction bits
+  const unsigned rem = lo & 0x1FFFFFFFu;              // 29 dropped bits
+  unsigned r = sign | ((unsigned)fe << 23) | fm;
+  if (rem > 0x10000000u || (rem == 0x10000000u && (fm & 1u))) r += 1u;   // carry may reach inf
+  return __uint_as_float(r);
+}
+
+__device__ __forceinline__ double f2d(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned sign = u & 0x80000000u;
+  const unsigned e = (u >> 23) & 0xFFu;
+  const unsigned m = u & 0x7FFFFFu;
+  if (e == 0u) return __hiloint2double((int)sign, 0);
+  if (e == 0xFFu) return __hiloint2double((int)(sign | 0x7FF00000u | (m >> 3) | (m ? 0x80000u : 0u)), 0);
+  return __hiloint2double((int)(sign | ((e + 896u) << 20) | (m >> 3)), (int)(m << 29));
+}
+
+// conversions used by the templated kernels: to the compute type / back to FP64
+template <class T> __device__ __forceinline__ T cvt(double x);
+template <> __device__ __forceinline__ double cvt<double>(double x) { return x; }
+template <> __device__ __forceinline__ float cvt<float>(double x) { return d2f(x); }
+template <class T> __device__ __forceinline__ T cvt(float x) { return T(x); }
+__device__ __forceinline__ double widen(double x) { return x; }
+__device__ __forceinline__ double widen(float x) { return f2d(x); }
 
 // ---------------------------------------------------------------------------------
 // forward-mode dual number (value, tangent) used to build the tangent kernel from

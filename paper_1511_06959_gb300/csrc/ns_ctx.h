@@ -16,8 +16,12 @@ struct ns_ctx {
   ns::Coef<float> cf;
   ns::Coef<ns::Dual> cx;
   size_t field = 0;              // elements of one [batch][5][cells] field
-  void* stage[5] = {};           // stage buffers (double in FP64 mode, float in MIXED mode)
-  double* tan[5] = {};           // FP64 buffers of the tangent step, allocated on first use
+  // stage buffers of the stage type (double in FP64 mode, float in MIXED mode):
+  // float mirrors of w and lambda, stage states W2..W4, two seeds, the stage-product
+  // (or RK increment) sum and the seed sum
+  static constexpr int NSTAGE = 9;
+  void* stage[NSTAGE] = {};
+  double* tan[6] = {};           // FP64 buffers of the tangent step, allocated on first use
   double* scratch = nullptr;     // reduction scratch
   size_t scratch_n = 0;
   unsigned* err = nullptr;       // sticky device error word

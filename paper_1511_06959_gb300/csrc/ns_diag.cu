@@ -12,6 +12,8 @@ namespace {
 
 constexpr int RB = 256;      // threads per reduction block
 constexpr int RG = 296;      // blocks per reduced quantity (2 x 148, fixed for determinism)
+constexpr int RGS = 1184;    // blocks of the streaming field reductions (fixed for determinism)
+constexpr int OB = 64;       // threads per block of the objective face kernels
 
 template <class T, class Op>
 __device__ __forceinline__ T block_reduce(T v, T* sh, Op op) {
@@ -34,66 +36,107 @@ struct MaxOp {
 };
 
 // ---------------------------------------------------------------------------------
-// pressure-loss objective, Eq. (e:pressure_loss): one block per box
+// pressure-loss objective, Eq. (e:pressure_loss): per-face terms over a grid of
+// blocks, block partials, one block per box for the final quotient, then the
+// gradient scatter onto the two plane columns
 // ---------------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) k_objective(GridDesc g, double gamma, int i0, double pt_in,
-                                                    const double* __restrict__ w, double weight,
-                                                    double* J_acc, double* lam, unsigned* err) {
-  __shared__ double sh[1024];
-  const int b = blockIdx.x;
+struct FaceState {
+  double r, u[3], uu, p;
+};
+
+__device__ __forceinline__ FaceState face_state(const double* __restrict__ w, size_t box, long long cells,
+                                                size_t row, int iL, int iR, double gm1) {
+  double q[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) q[v] = 0.5 * (w[box + v * cells + row + iL] + w[box + v * cells + row + iR]);
+  FaceState f;
+  f.r = q[0];
+  const double ir = 1.0 / q[0];
+  f.u[0] = q[1] * ir;
+  f.u[1] = q[2] * ir;
+  f.u[2] = q[3] * ir;
+  f.uu = f.u[0] * f.u[0] + f.u[1] * f.u[1] + f.u[2] * f.u[2];
+  f.p = gm1 * (q[4] - 0.5 * f.r * f.uu);
+  return f;
+}
+
+__device__ __forceinline__ double pt_factor(double B, double ex) {
+  // B^(gamma/(gamma-1)); gamma = 1.4 gives B^3.5 = B^3 sqrt(B)
+  return ex == 3.5 ? B * B * B * sqrt(B) : pow(B, ex);
+}
+
+__global__ void __launch_bounds__(OB) k_obj_partial(GridDesc g, double gamma, int i0, double pt_in,
+                                                    const double* __restrict__ w, double* partial) {
+  __shared__ double sh[OB];
+  const int b = blockIdx.y;
   const int nf = g.ny * g.nz;
   const int iL = wrap(i0 - 1, g.nx), iR = wrap(i0, g.nx);
   const size_t box = (size_t)b * 5 * g.cells;
   const double gm1 = gamma - 1.0, ex = gamma / gm1;
   double N = 0.0, D = 0.0;
-  for (int f = threadIdx.x; f < nf; f += blockDim.x) {
-    const size_t row = (size_t)f * g.nx;   // f = z * ny + y
-    double q[5];
-#pragma unroll
-    for (int v = 0; v < 5; ++v)
-      q[v] = 0.5 * (w[box + v * g.cells + row + iL] + w[box + v * g.cells + row + iR]);
-    const double r = q[0];
-    const double u2 = (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]) / (r * r);
-    const double p = gm1 * (q[4] - 0.5 * r * u2);
-    const double M2 = u2 * r / (gamma * p);
-    const double pt = p * pow(1.0 + 0.5 * gm1 * M2, ex);
-    N += r * (pt_in - pt);
-    D += r;
+  for (int f = blockIdx.x * OB + threadIdx.x; f < nf; f += gridDim.x * OB) {
+    const FaceState F = face_state(w, box, g.cells, (size_t)f * g.nx, iL, iR, gm1);
+    const double pt = F.p * pt_factor(1.0 + 0.5 * gm1 * F.r * F.uu / (gamma * F.p), ex);
+    N += F.r * (pt_in - pt);
+    D += F.r;
   }
   N = block_reduce(N, sh, AddOp());
   D = block_reduce(D, sh, AddOp());
-  const double J = N / (D * pt_in);
   if (threadIdx.x == 0) {
+    partial[((size_t)b * 2 + 0) * gridDim.x + blockIdx.x] = N;
+    partial[((size_t)b * 2 + 1) * gridDim.x + blockIdx.x] = D;
+  }
+}
+
+__global__ void __launch_bounds__(RB) k_obj_final(int nblk, double pt_in, double weight, double* partial,
+                                                  double* nd, double* J_acc, unsigned* err) {
+  __shared__ double sh[RB];
+  const int b = blockIdx.x;
+  double N = 0.0, D = 0.0;
+  for (int i = threadIdx.x; i < nblk; i += RB) {
+    N += partial[((size_t)b * 2 + 0) * nblk + i];
+    D += partial[((size_t)b * 2 + 1) * nblk + i];
+  }
+  N = block_reduce(N, sh, AddOp());
+  D = block_reduce(D, sh, AddOp());
+  if (threadIdx.x == 0) {
+    const double J = N / (D * pt_in);
     if (!isfinite(J)) atomicOr(err, ERRBIT_NONFINITE);
     J_acc[b] += weight * J;
+    nd[2 * b] = N;
+    nd[2 * b + 1] = D;
   }
-  if (!lam) return;
-  // dJ/dw_f = [d(rho_f (pt_in - pt_f))/dw_f - (N/D) e_0] / (D pt_in), split 1/2 : 1/2
+}
+
+// dJ/dw_f = [d(rho_f (pt_in - pt_f))/dw_f - (N/D) e_0] / (D pt_in), split 1/2 : 1/2
+__global__ void __launch_bounds__(OB) k_obj_grad(GridDesc g, double gamma, int i0, double pt_in,
+                                                 double weight, const double* __restrict__ w,
+                                                 const double* nd, double* lam) {
+  const int b = blockIdx.y;
+  const int nf = g.ny * g.nz;
+  const int iL = wrap(i0 - 1, g.nx), iR = wrap(i0, g.nx);
+  const size_t box = (size_t)b * 5 * g.cells;
+  const double gm1 = gamma - 1.0, ex = gamma / gm1;
+  const double N = nd[2 * b], D = nd[2 * b + 1];
   const double NoD = N / D;
   const double sc = 0.5 * weight / (D * pt_in);
-  for (int f = threadIdx.x; f < nf; f += blockDim.x) {
+  for (int f = blockIdx.x * OB + threadIdx.x; f < nf; f += gridDim.x * OB) {
     const size_t row = (size_t)f * g.nx;
-    double q[5];
-#pragma unroll
-    for (int v = 0; v < 5; ++v)
-      q[v] = 0.5 * (w[box + v * g.cells + row + iL] + w[box + v * g.cells + row + iR]);
-    const double r = q[0], ir = 1.0 / r;
-    const double u[3] = {q[1] * ir, q[2] * ir, q[3] * ir};
-    const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-    const double p = gm1 * (q[4] - 0.5 * r * uu);
+    const FaceState F = face_state(w, box, g.cells, row, iL, iR, gm1);
+    const double r = F.r, ir = 1.0 / r, uu = F.uu, p = F.p;
     const double B = 1.0 + 0.5 * gm1 * r * uu / (gamma * p);
-    const double pt = p * pow(B, ex);
+    const double pt = p * pt_factor(B, ex);
     // derivatives of pt in primitive variables (rho, u, p)
     const double dr = pt * uu / (2.0 * p * B);
     const double dp = pt / p * (1.0 - r * uu / (2.0 * p * B));
     double du[3];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) du[k] = pt * r * u[k] / (p * B);
+    for (int k = 0; k < 3; ++k) du[k] = pt * r * F.u[k] / (p * B);
     // chain to conservative variables through dq/dw
     double dw[5];
-    dw[0] = dr - (u[0] * du[0] + u[1] * du[1] + u[2] * du[2]) * ir + 0.5 * gm1 * uu * dp;
+    dw[0] = dr - (F.u[0] * du[0] + F.u[1] * du[1] + F.u[2] * du[2]) * ir + 0.5 * gm1 * uu * dp;
 #pragma unroll
-    for (int k = 0; k < 3; ++k) dw[1 + k] = du[k] * ir - gm1 * u[k] * dp;
+    for (int k = 0; k < 3; ++k) dw[1 + k] = du[k] * ir - gm1 * F.u[k] * dp;
     dw[4] = gm1 * dp;
     double gv[5];
     gv[0] = ((pt_in - pt) - r * dw[0] - NoD) * sc;
@@ -116,83 +159,138 @@ struct Prim {
 };
 
 template <class T>
-__device__ __forceinline__ Prim<T> prim_at(const double* __restrict__ w, size_t o, long long cells,
+__device__ __forceinline__ Prim<T> prim_at(const T* __restrict__ w, size_t o, long long cells,
                                            T gamma) {
   Prim<T> P;
-  P.rho = T(w[o]);
+  P.rho = w[o];
   const T ir = T(1) / P.rho;
-  P.u[0] = T(w[o + cells]) * ir;
-  P.u[1] = T(w[o + 2 * cells]) * ir;
-  P.u[2] = T(w[o + 3 * cells]) * ir;
-  P.p = (gamma - T(1)) * (T(w[o + 4 * cells]) - T(0.5) * P.rho * (P.u[0] * P.u[0] + P.u[1] * P.u[1] + P.u[2] * P.u[2]));
+  P.u[0] = w[o + cells] * ir;
+  P.u[1] = w[o + 2 * cells] * ir;
+  P.u[2] = w[o + 3 * cells] * ir;
+  P.p = (gamma - T(1)) * (w[o + 4 * cells] - T(0.5) * P.rho * (P.u[0] * P.u[0] + P.u[1] * P.u[1] + P.u[2] * P.u[2]));
   const T cs = sqrt(gamma * P.p * ir);
   P.b = cs / sqrt(gamma);
   P.a = sqrt((gamma - T(1)) / gamma) * cs;
   return P;
 }
 
-// largest eigenvalue of a symmetric N x N matrix by cyclic Jacobi rotations
+// Largest eigenvalue of a symmetric positive semidefinite N x N matrix: Householder
+// reduction to tridiagonal form, then Laguerre's iteration on the characteristic
+// polynomial of the tridiagonal matrix from a Gershgorin upper bound.  For a
+// polynomial with only real roots Laguerre's iteration started to the right of the
+// largest root decreases monotonically to it (cubically near a simple root), so a
+// fixed small number of steps suffices.  The matrix is scaled to unit trace first.
 template <class T, int N>
 __device__ T max_eig_sym(T A[N][N]) {
-  const T eps = sizeof(T) == 8 ? T(1e-30) : T(1e-20);
-  for (int sweep = 0; sweep < 12; ++sweep) {
-    T off = T(0), dia = T(0);
+  T tr = T(0);
+#pragma unroll
+  for (int i = 0; i < N; ++i) tr += A[i][i];
+  if (!(tr > T(0))) return T(0);
+  const T inv = T(1) / tr;
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+#pragma unroll
+    for (int j = 0; j < N; ++j) A[i][j] *= inv;
+  // Householder tridiagonalisation (A is symmetric; both triangles are kept)
+#pragma unroll
+  for (int k = 0; k < N - 2; ++k) {
+    T nrm2 = T(0);
+#pragma unroll
+    for (int i = k + 1; i < N; ++i) nrm2 += A[i][k] * A[i][k];
+    const T x0 = A[k + 1][k];
+    const T rest = nrm2 - x0 * x0;
+    if (!(rest > T(0))) continue;              // column already reduced
+    const T nrm = sqrt(nrm2);
+    const T alpha = x0 >= T(0) ? -nrm : nrm;
+    T v[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) v[i] = i > k ? A[i][k] : T(0);
+    v[k + 1] = x0 - alpha;
+    const T vn2 = v[k + 1] * v[k + 1] + rest;
+    const T sc = T(1) / sqrt(vn2);
+#pragma unroll
+    for (int i = k + 1; i < N; ++i) v[i] *= sc;
+    // p = A v, q = p - (v.p) v, A <- A - 2 (v q^T + q v^T)
+    T pv[N];
 #pragma unroll
     for (int i = 0; i < N; ++i) {
-      dia += A[i][i] * A[i][i];
+      T acc = T(0);
 #pragma unroll
-      for (int j = i + 1; j < N; ++j) off += A[i][j] * A[i][j];
+      for (int j = k + 1; j < N; ++j) acc += A[i][j] * v[j];
+      pv[i] = acc;
     }
-    const T tol = sizeof(T) == 8 ? T(1e-32) : T(1e-14);
-    if (off <= tol * dia || off < eps) break;
+    T vp = T(0);
 #pragma unroll
-    for (int p = 0; p < N; ++p) {
+    for (int i = k + 1; i < N; ++i) vp += v[i] * pv[i];
 #pragma unroll
-      for (int q = p + 1; q < N; ++q) {
-        const T apq = A[p][q];
-        if (fabs(apq) <= eps) continue;
-        const T theta = (A[q][q] - A[p][p]) / (T(2) * apq);
-        const T t = (theta >= T(0) ? T(1) : T(-1)) / (fabs(theta) + sqrt(theta * theta + T(1)));
-        const T cs = T(1) / sqrt(t * t + T(1));
-        const T sn = t * cs;
+    for (int i = 0; i < N; ++i) pv[i] -= vp * v[i];
 #pragma unroll
-        for (int k = 0; k < N; ++k) {
-          const T akp = A[k][p], akq = A[k][q];
-          A[k][p] = cs * akp - sn * akq;
-          A[k][q] = sn * akp + cs * akq;
-        }
+    for (int i = 0; i < N; ++i)
 #pragma unroll
-        for (int k = 0; k < N; ++k) {
-          const T apk = A[p][k], aqk = A[q][k];
-          A[p][k] = cs * apk - sn * aqk;
-          A[q][k] = sn * apk + cs * aqk;
-        }
-      }
-    }
+      for (int j = 0; j < N; ++j) A[i][j] -= T(2) * (v[i] * pv[j] + pv[i] * v[j]);
   }
-  T m = A[0][0];
+  T d[N], e2[N];
+  T ub = T(0);
 #pragma unroll
-  for (int i = 1; i < N; ++i) m = A[i][i] > m ? A[i][i] : m;
-  return m;
+  for (int i = 0; i < N; ++i) {
+    d[i] = A[i][i];
+    const T bl = i > 0 ? fabs(A[i][i - 1]) : T(0);
+    const T br = i < N - 1 ? fabs(A[i + 1][i]) : T(0);
+    e2[i] = i < N - 1 ? A[i + 1][i] * A[i + 1][i] : T(0);
+    const T g = d[i] + bl + br;
+    ub = g > ub ? g : ub;
+  }
+  T x = ub * T(1.0000002) + T(1e-30);
+  const T n = T(N);
+#pragma unroll 1
+  for (int it = 0; it < 12; ++it) {
+    // p, p', p'' of det(T - x I) by the three-term recurrence
+    T p0 = T(1), p1 = d[0] - x;
+    T q0 = T(0), q1 = T(-1);
+    T r0 = T(0), r1 = T(0);
+#pragma unroll
+    for (int i = 1; i < N; ++i) {
+      const T dx = d[i] - x;
+      const T p2 = dx * p1 - e2[i - 1] * p0;
+      const T q2 = -p1 + dx * q1 - e2[i - 1] * q0;
+      const T r2 = T(-2) * q1 + dx * r1 - e2[i - 1] * r0;
+      p0 = p1; p1 = p2;
+      q0 = q1; q1 = q2;
+      r0 = r1; r1 = r2;
+    }
+    if (p1 == T(0)) break;
+    const T G = q1 / p1;
+    const T H = G * G - r1 / p1;
+    T disc = (n - T(1)) * (n * H - G * G);
+    disc = disc > T(0) ? sqrt(disc) : T(0);
+    const T den = G >= T(0) ? G + disc : G - disc;
+    if (den == T(0)) break;
+    const T step = n / den;
+    x -= step;
+    if (fabs(step) <= (sizeof(T) == 8 ? T(1e-15) : T(2e-7)) * fabs(x)) break;
+  }
+  return x * tr;
 }
 
+// sigma_1 of M: the square root of the largest eigenvalue of M^T M, on the full 5 x 5
+// matrix (N = 5) or on its (rho, u1, u2, p) block for a 2D box (N = 4)
 template <class T, int N>
 __device__ T sigma1_of(const T M[5][5]) {
-  // 2D: the (rho, u1, u2, p) block
-  const int id5[5] = {0, 1, 2, 3, 4};
-  const int id4[4] = {0, 1, 2, 4};
+  constexpr int id5[5] = {0, 1, 2, 3, 4};
+  constexpr int id4[4] = {0, 1, 2, 4};
   T B[N][N];
 #pragma unroll
   for (int i = 0; i < N; ++i) {
 #pragma unroll
-    for (int j = 0; j < N; ++j) {
-      T s = T(0);
+    for (int j = i; j < N; ++j) {
+      T acc = T(0);
 #pragma unroll
       for (int k = 0; k < N; ++k) {
-        const int ki = N == 5 ? id5[k] : id4[k];
-        s += M[ki][N == 5 ? id5[i] : id4[i]] * M[ki][N == 5 ? id5[j] : id4[j]];
+        const int kk = N == 5 ? id5[k] : id4[k];
+        acc += M[kk][N == 5 ? id5[i] : id4[i]] * M[kk][N == 5 ? id5[j] : id4[j]];
       }
-      B[i][j] = s;
+      B[i][j] = acc;
+      B[j][i] = acc;
     }
   }
   const T l = max_eig_sym<T, N>(B);
@@ -200,7 +298,7 @@ __device__ T sigma1_of(const T M[5][5]) {
 }
 
 template <class CT>
-__global__ void __launch_bounds__(RB) k_sigma1(GridDesc g, Coef<CT> c, const double* __restrict__ w,
+__global__ void __launch_bounds__(RB) k_sigma1(GridDesc g, Coef<CT> c, const CT* __restrict__ w,
                                                float* __restrict__ sig, double* partial) {
   __shared__ double sh[RB];
   const int b = blockIdx.y;
@@ -333,31 +431,37 @@ __global__ void k_visc_apply(GridDesc g, double ix2, double iy2, double iz2, con
 // ---------------------------------------------------------------------------------
 // adjoint energy: v_hat = S^-T V^-T w_hat in closed form ("Symmetrization")
 // ---------------------------------------------------------------------------------
+template <class T>
+__device__ __forceinline__ double energy_cell(const double* __restrict__ w, const double* __restrict__ lam,
+                                              size_t box, long long cells, long long i, T gamma) {
+  const T gm1 = gamma - T(1), sg = sqrt(gamma), sgg = sqrt(gm1 / gamma);
+  const T r = cvt<T>(w[box + i]), ir = T(1) / r;
+  const T u0 = cvt<T>(w[box + cells + i]) * ir, u1 = cvt<T>(w[box + 2 * cells + i]) * ir,
+          u2 = cvt<T>(w[box + 3 * cells + i]) * ir;
+  const T uu = u0 * u0 + u1 * u1 + u2 * u2;
+  const T p = gm1 * (cvt<T>(w[box + 4 * cells + i]) - T(0.5) * r * uu);
+  const T cs = sqrt(gamma * p * ir);
+  const T l0 = cvt<T>(lam[box + i]), l1 = cvt<T>(lam[box + cells + i]), l2 = cvt<T>(lam[box + 2 * cells + i]),
+          l3 = cvt<T>(lam[box + 3 * cells + i]), l4 = cvt<T>(lam[box + 4 * cells + i]);
+  // y = V^-T lam, V^-1 = dw/dq
+  const T y0 = l0 + u0 * l1 + u1 * l2 + u2 * l3 + T(0.5) * uu * l4;
+  const T y1 = r * (l1 + u0 * l4), y2 = r * (l2 + u1 * l4), y3 = r * (l3 + u2 * l4);
+  const T y4 = l4 / gm1;
+  // v_hat = S^-T y
+  const T v0 = sg * r / cs * y0 + r * cs / sg * y4;
+  const T v4 = r * cs * sgg * y4;
+  return widen(v0 * v0 + y1 * y1 + y2 * y2 + y3 * y3 + v4 * v4);
+}
+
+template <class T>
 __global__ void __launch_bounds__(RB) k_energy(GridDesc g, double gamma, const double* __restrict__ w,
                                                const double* __restrict__ lam, double* partial) {
   __shared__ double sh[RB];
   const int b = blockIdx.y;
   const size_t box = (size_t)b * 5 * g.cells;
-  const double gm1 = gamma - 1.0, sg = sqrt(gamma), sgg = sqrt(gm1 / gamma);
   double acc = 0.0;
-  for (long long i = (long long)blockIdx.x * RB + threadIdx.x; i < g.cells; i += (long long)gridDim.x * RB) {
-    const double r = w[box + i], ir = 1.0 / r;
-    const double u0 = w[box + g.cells + i] * ir, u1 = w[box + 2 * g.cells + i] * ir,
-                 u2 = w[box + 3 * g.cells + i] * ir;
-    const double uu = u0 * u0 + u1 * u1 + u2 * u2;
-    const double p = gm1 * (w[box + 4 * g.cells + i] - 0.5 * r * uu);
-    const double cs = sqrt(gamma * p * ir);
-    const double l0 = lam[box + i], l1 = lam[box + g.cells + i], l2 = lam[box + 2 * g.cells + i],
-                 l3 = lam[box + 3 * g.cells + i], l4 = lam[box + 4 * g.cells + i];
-    // y = V^-T lam, V^-1 = dw/dq
-    const double y0 = l0 + u0 * l1 + u1 * l2 + u2 * l3 + 0.5 * uu * l4;
-    const double y1 = r * (l1 + u0 * l4), y2 = r * (l2 + u1 * l4), y3 = r * (l3 + u2 * l4);
-    const double y4 = l4 / gm1;
-    // v_hat = S^-T y
-    const double v0 = sg * r / cs * y0 + r * cs / sg * y4;
-    const double v4 = r * cs * sgg * y4;
-    acc += v0 * v0 + y1 * y1 + y2 * y2 + y3 * y3 + v4 * v4;
-  }
+  for (long long i = (long long)blockIdx.x * RB + threadIdx.x; i < g.cells; i += (long long)gridDim.x * RB)
+    acc += energy_cell<T>(w, lam, box, g.cells, i, T(gamma));
   acc = block_reduce(acc, sh, AddOp());
   if (threadIdx.x == 0) partial[(size_t)b * gridDim.x + blockIdx.x] = acc;
 }
@@ -426,23 +530,43 @@ __global__ void __launch_bounds__(RB) k_max_partials(int nblk, const double* par
   if (threadIdx.x == 0) out[0] = m;
 }
 
+__global__ void k_to_float(const double* __restrict__ in, float* __restrict__ out, size_t n) {
+  const size_t i = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) * 2;
+  if (i + 1 < n) {
+    const double2 v = *reinterpret_cast<const double2*>(in + i);
+    *reinterpret_cast<float2*>(out + i) = make_float2(d2f(v.x), d2f(v.y));
+  } else if (i < n) {
+    out[i] = d2f(in[i]);
+  }
+}
+
 }  // namespace
 
 size_t diag_scratch_doubles(const GridDesc& g, int nphi) {
-  size_t a = (size_t)2 * RG * g.batch;
+  size_t a = (size_t)2 * RG * g.batch + (size_t)2 * g.batch;
+  if ((size_t)RGS * g.batch > a) a = (size_t)RGS * g.batch;
   size_t b = (size_t)RG * (nphi > 0 ? nphi : 1);
   return (a > b ? a : b) + 64;
 }
 
 cudaError_t launch_objective(const GridDesc& g, double gamma, int plane_i, double pt_in,
                              const double* w, double weight, double* J_acc, double* lam,
-                             unsigned* err, cudaStream_t st) {
-  k_objective<<<g.batch, 1024, 0, st>>>(g, gamma, plane_i, pt_in, w, weight, J_acc, lam, err);
+                             unsigned* err, double* scratch, cudaStream_t st) {
+  const int nf = g.ny * g.nz;
+  int nblk = (nf + OB - 1) / OB;
+  if (nblk > RG) nblk = RG;
+  double* nd = scratch + (size_t)2 * RG * g.batch;
+  k_obj_partial<<<dim3(nblk, g.batch), OB, 0, st>>>(g, gamma, plane_i, pt_in, w, scratch);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_obj_final<<<g.batch, RB, 0, st>>>(nblk, pt_in, weight, scratch, nd, J_acc, err);
+  if ((e = cudaGetLastError()) != cudaSuccess || !lam) return e;
+  k_obj_grad<<<dim3(nblk, g.batch), OB, 0, st>>>(g, gamma, plane_i, pt_in, weight, w, nd, lam);
   return cudaGetLastError();
 }
 
 template <class CT>
-cudaError_t launch_sigma1(const GridDesc& g, const Coef<CT>& c, const double* w, float* sigma1,
+cudaError_t launch_sigma1(const GridDesc& g, const Coef<CT>& c, const CT* w, float* sigma1,
                           double* stats, double* scratch, cudaStream_t st) {
   dim3 grid(RG, g.batch);
   k_sigma1<CT><<<grid, RB, 0, st>>>(g, c, w, sigma1, scratch);
@@ -453,7 +577,7 @@ cudaError_t launch_sigma1(const GridDesc& g, const Coef<CT>& c, const double* w,
 }
 template cudaError_t launch_sigma1<double>(const GridDesc&, const Coef<double>&, const double*, float*,
                                            double*, double*, cudaStream_t);
-template cudaError_t launch_sigma1<float>(const GridDesc&, const Coef<float>&, const double*, float*,
+template cudaError_t launch_sigma1<float>(const GridDesc&, const Coef<float>&, const float*, float*,
                                           double*, double*, cudaStream_t);
 
 cudaError_t launch_nu_rule(const GridDesc& g, const float* sigma1, double lambda, double tau,
@@ -472,12 +596,16 @@ cudaError_t launch_visc_apply(const GridDesc& g, const double* idx2, const float
 }
 
 cudaError_t launch_energy(const GridDesc& g, double gamma, double dV, const double* w, const double* lam,
-                          double* E, double* scratch, unsigned* err, cudaStream_t st) {
-  dim3 grid(RG, g.batch);
-  k_energy<<<grid, RB, 0, st>>>(g, gamma, w, lam, scratch);
+                          double* E, double* scratch, unsigned* err, bool fp32_transform,
+                          cudaStream_t st) {
+  dim3 grid(RGS, g.batch);
+  if (fp32_transform)
+    k_energy<float><<<grid, RB, 0, st>>>(g, gamma, w, lam, scratch);
+  else
+    k_energy<double><<<grid, RB, 0, st>>>(g, gamma, w, lam, scratch);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_sum_partials<<<g.batch, RB, 0, st>>>(RG, dV, scratch, E, err);
+  k_sum_partials<<<g.batch, RB, 0, st>>>(RGS, dV, scratch, E, err);
   return cudaGetLastError();
 }
 
@@ -506,4 +634,12 @@ cudaError_t launch_max_wave(const GridDesc& g, double gamma, const double* w, do
   return cudaGetLastError();
 }
 
+}  // namespace ns
+
+namespace ns {
+cudaError_t launch_to_float(const double* in, float* out, size_t n, cudaStream_t st) {
+  const size_t threads = (n + 1) / 2;
+  k_to_float<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(in, out, n);
+  return cudaGetLastError();
+}
 }  // namespace ns

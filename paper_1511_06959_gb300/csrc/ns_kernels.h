@@ -8,39 +8,52 @@
 
 namespace ns {
 
-// Fused RK4 stage of the primal (see ns_rhs.cu):
-//   R = R(W) + src;  acc = (acc_init ? base (or 0) : acc) + cacc*R;  Wout = base + cout*R
+// Fused RK4 stage of the primal (see ns_rhs.cu).  With R = R(W) + src:
+//   dacc = (dacc_init ? 0 : dacc) + cacc R        increment sum, stage type
+//   Wout = base + cout R                           next stage state, stage type
+//   wout = (wbase or 0) + widen(dacc + cacc R)     final state, FP64 (when wout != 0)
 template <class TIN, class TST>
 struct StageArgs {
   const TIN* W;
   const double* Wd;       // tangent of W (Dual instantiation only)
-  const double* base;
+  const TST* base;
   const double* based;
   const double* src;
   const double* srcd;
-  double* acc;
-  double* accd;
-  int acc_init;
+  TST* dacc;
+  double* daccd;
+  int dacc_init;
   double cacc;
   TST* Wout;
   double* Woutd;
   double cout;
+  const double* wbase;
+  const double* wbased;
+  double* wout;
+  double* woutd;
 };
 
 // Fused stage of the discrete adjoint (see ns_adj.cu), a = ca*A:
-//   g = (dR/dw)(W)^T a + L_nu a
-//   lacc = (lacc_init ? (lam or 0) : lacc) + g;  Anext = cl*lam + cg*g;  sbar += a
+//   g     = (dR/dw)(W)^T a + L_nu a
+//   Gout  = (Gin or 0) + g                              stage-product sum, stage type
+//   lam_out = (lam_in or 0) + widen((Gin or 0) + g)     FP64 (when lam_out != 0)
+//   Anext = cl*lamf + cg*g                              next stage seed
+//   SBout = (SBin or 0) + a;  sbar += widen((SBin or 0) + a)   source seeds
 template <class TIN, class TA, class TST>
 struct AdjArgs {
   const TIN* W;
   const TA* A;
   double ca;
   const float* nu;
-  const double* lam;
-  double* lacc;
-  int lacc_init;
+  const TST* lamf;
+  const TST* Gin;
+  TST* Gout;
   TST* Anext;
   double cl, cg;
+  const double* lam_in;
+  double* lam_out;
+  const TST* SBin;
+  TST* SBout;
   double* sbar;
 };
 
@@ -57,9 +70,9 @@ cudaError_t launch_adj_stage(const GridDesc& g, const Coef<CT>& c, const AdjArgs
 size_t diag_scratch_doubles(const GridDesc& g, int nphi);
 cudaError_t launch_objective(const GridDesc& g, double gamma, int plane_i, double pt_in,
                              const double* w, double weight, double* J_acc, double* lam,
-                             unsigned* err, cudaStream_t st);
+                             unsigned* err, double* scratch, cudaStream_t st);
 template <class CT>
-cudaError_t launch_sigma1(const GridDesc& g, const Coef<CT>& c, const double* w, float* sigma1,
+cudaError_t launch_sigma1(const GridDesc& g, const Coef<CT>& c, const CT* w, float* sigma1,
                           double* stats, double* scratch, cudaStream_t st);
 cudaError_t launch_nu_rule(const GridDesc& g, const float* sigma1, double lambda, double tau,
                            double limit_nu, float* nu, unsigned* err, cudaStream_t st);
@@ -67,12 +80,13 @@ cudaError_t launch_visc_apply(const GridDesc& g, const double* idx2, const float
                               const double* a, double* out, cudaStream_t st);
 cudaError_t launch_energy(const GridDesc& g, double gamma, double dV, const double* w,
                           const double* lam, double* E, double* scratch, unsigned* err,
-                          cudaStream_t st);
+                          bool fp32_transform, cudaStream_t st);
 cudaError_t launch_dot(const double* a, const double* phi, int nphi, size_t n, double* out,
                        double* scratch, cudaStream_t st);
 cudaError_t launch_combine(const double* theta, const double* phi, int nphi, size_t n,
                            double* s, cudaStream_t st);
 cudaError_t launch_max_wave(const GridDesc& g, double gamma, const double* w, double* out,
                             double* scratch, cudaStream_t st);
+cudaError_t launch_to_float(const double* in, float* out, size_t n, cudaStream_t st);
 
 }  // namespace ns

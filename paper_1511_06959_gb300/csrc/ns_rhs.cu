@@ -10,9 +10,11 @@
 // compute the tile's upper x/y boundary faces; the z-face below is carried in
 // registers from the previous plane.  Each face flux is thus evaluated once per tile.
 //
-// Epilogue (fused RK4 update, FP64 accumulation in both precision modes):
-//   acc  = (acc_init ? base : acc) + cacc * R
-//   Wout = base + cout * R          (next stage state, stored in the stage type)
+// Epilogue (fused RK4 update): the stage increments are summed in the stage type,
+// dacc = sum_i b_i dt k_i, and only the final stage forms w^{n+1} = w^n + dacc in FP64,
+// one FP64 add per component and step:
+//   dacc = (dacc_init ? 0 : dacc) + cacc R,   Wout = base + cout R,
+//   wout = wbase + widen(dacc + cacc R).
 // The same template instantiated on ns::Dual gives the tangent (dR/dw) wd.
 #include <type_traits>
 
@@ -25,7 +27,7 @@ template <class CT, class TIN>
 struct Loader {
   const TIN* W;
   const double* Wd;
-  __device__ __forceinline__ CT ld(size_t o) const { return CT(W[o]); }
+  __device__ __forceinline__ CT ld(size_t o) const { return cvt<CT>(W[o]); }
 };
 template <>
 struct Loader<Dual, double> {
@@ -59,6 +61,50 @@ __device__ __forceinline__ void fill_plane(CT* __restrict__ sq, const GridDesc& 
     sq[2 * SP + t] = u1;
     sq[3 * SP + t] = u2;
     sq[4 * SP + t] = E * ir - CT(0.5) * (u0 * u0 + u1 * u1 + u2 * u2);
+  }
+}
+
+// Two-phase plane load used to overlap the next plane's global loads with the
+// current plane's face fluxes: plane_load issues the loads into registers,
+// plane_store converts to primitives and writes the ring slot after a barrier.
+static_assert(SP <= 2 * NT, "a plane must fit two load rounds");
+template <class CT>
+struct PlaneRegs {
+  CT v[2][5];
+};
+
+template <class CT, class L>
+__device__ __forceinline__ void plane_load(PlaneRegs<CT>& r, const GridDesc& g, int b, int k, int x0,
+                                           int y0, const L& in) {
+  const int kz = wrap(k, g.nz);
+  const size_t boxoff = (size_t)b * 5 * g.cells + (size_t)kz * g.plane;
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const int t = threadIdx.x + it * NT;
+    if (t < SP) {
+      const int ly = t / SX;
+      const int lx = t - ly * SX;
+      const size_t o = boxoff + (size_t)wrap(y0 + ly - 1, g.ny) * g.nx + wrap(x0 + lx - 1, g.nx);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) r.v[it][v] = in.ld(o + v * g.cells);
+    }
+  }
+}
+
+template <class CT>
+__device__ __forceinline__ void plane_store(const PlaneRegs<CT>& r, CT* __restrict__ sq) {
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const int t = threadIdx.x + it * NT;
+    if (t < SP) {
+      const CT ir = one_over(r.v[it][0]);
+      const CT u0 = r.v[it][1] * ir, u1 = r.v[it][2] * ir, u2 = r.v[it][3] * ir;
+      sq[0 * SP + t] = r.v[it][0];
+      sq[1 * SP + t] = u0;
+      sq[2 * SP + t] = u1;
+      sq[3 * SP + t] = u2;
+      sq[4 * SP + t] = r.v[it][4] * ir - CT(0.5) * (u0 * u0 + u1 * u1 + u2 * u2);
+    }
   }
 }
 
@@ -192,6 +238,9 @@ __global__ void __launch_bounds__(NT) k_rhs_stage(GridDesc g, Coef<CT> c, StageA
 
   for (int k = kz0; k < kz1; ++k) {
     const int sm = slot(k - 1), s0 = slot(k), sp = slot(k + 1);
+    const bool more = k + 1 < kz1;
+    PlaneRegs<CT> pf;
+    if (more) plane_load(pf, g, b, k + 2, x0, y0, in);
     {
       CT phi[5];
       xface(sQ, c, sm, s0, sp, ty + 1, tx, phi);
@@ -225,29 +274,40 @@ __global__ void __launch_bounds__(NT) k_rhs_stage(GridDesc g, Coef<CT> c, StageA
         const CT fym = sFY[(v * (TY + 1) + ty) * TX + tx];
         const CT R = -((fxp - fxm) * c.idx[0] + (fyp - fym) * c.idx[1] + (zhi[v] - zlo[v]) * c.idx[2]);
         const size_t o = o0 + (size_t)v * g.cells;
-        double Rv = (double)val(R);
-        if (a.src) Rv += a.src[o];
-        if (a.acc) {
-          const double accv = a.acc_init ? (a.base ? a.base[o] : 0.0) : a.acc[o];
-          a.acc[o] = accv + a.cacc * Rv;
-        }
-        if (a.Wout) a.Wout[o] = (TST)(a.base[o] + a.cout * Rv);
         if constexpr (std::is_same<CT, Dual>::value) {
-          double Rd = tan_of(R);
+          double Rv = R.v, Rd = R.d;
+          if (a.src) Rv += a.src[o];
           if (a.srcd) Rd += a.srcd[o];
-          if (a.accd) {
-            const double accd = a.acc_init ? (a.based ? a.based[o] : 0.0) : a.accd[o];
-            a.accd[o] = accd + a.cacc * Rd;
+          const double iv = a.cacc * Rv, id = a.cacc * Rd;
+          const double dv = (a.dacc && !a.dacc_init ? (double)a.dacc[o] : 0.0) + iv;
+          const double dd = (a.daccd && !a.dacc_init ? a.daccd[o] : 0.0) + id;
+          if (a.wout) a.wout[o] = (a.wbase ? a.wbase[o] : 0.0) + dv;
+          else if (a.dacc) a.dacc[o] = dv;
+          if (a.woutd) a.woutd[o] = (a.wbased ? a.wbased[o] : 0.0) + dd;
+          else if (a.daccd) a.daccd[o] = dd;
+          if (a.Wout) {
+            a.Wout[o] = a.base[o] + a.cout * Rv;
+            if (a.Woutd) a.Woutd[o] = a.based[o] + a.cout * Rd;
           }
-          if (a.Woutd) a.Woutd[o] = a.based[o] + a.cout * Rd;
+        } else {
+          CT Rv = R;
+          if (a.src) Rv = Rv + cvt<CT>(a.src[o]);
+          const CT inc = CT(a.cacc) * Rv;
+          const CT dv = (a.dacc && !a.dacc_init ? a.dacc[o] : CT(0)) + inc;
+          if (a.wout) {
+            a.wout[o] = (a.wbase ? a.wbase[o] : 0.0) + widen(dv);
+          } else if (a.dacc) {
+            a.dacc[o] = dv;
+          }
+          if (a.Wout) a.Wout[o] = a.base[o] + CT(a.cout) * Rv;
         }
       }
     }
 #pragma unroll
     for (int v = 0; v < 5; ++v) zlo[v] = zhi[v];
     __syncthreads();
-    if (k + 1 < kz1) {
-      fill_plane<CT>(sQ + slot(k + 2) * 5 * SP, g, b, k + 2, x0, y0, in);
+    if (more) {
+      plane_store(pf, sQ + slot(k + 2) * 5 * SP);
       __syncthreads();
     }
   }
@@ -272,8 +332,6 @@ cudaError_t launch_rhs_stage(const GridDesc& g, const Coef<CT>& c, const StageAr
 
 template cudaError_t launch_rhs_stage<double, double, double>(const GridDesc&, const Coef<double>&,
                                                               const StageArgs<double, double>&, cudaStream_t);
-template cudaError_t launch_rhs_stage<float, double, float>(const GridDesc&, const Coef<float>&,
-                                                            const StageArgs<double, float>&, cudaStream_t);
 template cudaError_t launch_rhs_stage<float, float, float>(const GridDesc&, const Coef<float>&,
                                                            const StageArgs<float, float>&, cudaStream_t);
 template cudaError_t launch_rhs_stage<Dual, double, double>(const GridDesc&, const Coef<Dual>&,

@@ -361,3 +361,62 @@ def test_mixed_precision_short_horizon():
     assert rel_l2(host(ws[-1]), ws_ref[-1]) < 1e-4
     assert abs(J.item() - Jref) < 1e-4 * abs(Jref)
     assert rel_l2(host(lam), lam_ref) < 1e-4
+
+
+def test_float_mirror_conversion_matches_cuda_rounding():
+    """The integer-ALU double -> float conversion of the mixed path equals CUDA's own
+    round-to-nearest-even conversion bit for bit over the normal float range (random
+    values, exact ties, both signs, extreme exponents) and flushes values below the
+    smallest normal float to signed zero."""
+    api = _api()
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal(200001) * np.exp(rng.uniform(-80, 80, 200001))
+    f = rng.standard_normal(50000).astype(np.float32)
+    nxt = np.nextafter(f, np.float32(np.inf))
+    ties = (f.astype(np.float64) + nxt.astype(np.float64)) / 2.0
+    big = np.array([3.4028234e38, -3.4028234e38, 1.1754944e-38, -1.1754944e-38, 1.0, -0.0, 0.0])
+    vals = np.concatenate([x, ties, big])
+    vals = vals[(np.abs(vals) >= np.finfo(np.float32).tiny) | (vals == 0)]
+    vals = vals[np.abs(vals) <= np.finfo(np.float32).max]
+    S = api.Solver(4, 4, 1, 0.1)
+    out = torch.empty(vals.size, dtype=torch.float32, device="cuda")
+    S.to_float(dev(vals), out)
+    ref = dev(vals).float()
+    assert torch.equal(out.view(torch.int32), ref.view(torch.int32))
+    tiny = np.array([1e-39, -1e-40, 1e-300, -1e-320, 0.0])
+    out2 = torch.empty(tiny.size, dtype=torch.float32, device="cuda")
+    S.to_float(dev(tiny), out2)
+    o2 = host(out2)
+    assert np.all(o2 == 0.0) and np.array_equal(np.signbit(o2), np.signbit(tiny))
+    sp = np.array([np.inf, -np.inf, np.nan, 1e39, -1e300])
+    out3 = torch.empty(sp.size, dtype=torch.float32, device="cuda")
+    S.to_float(dev(sp), out3)
+    o3 = host(out3)
+    assert o3[0] == np.inf and o3[1] == -np.inf and np.isnan(o3[2]) and o3[3] == np.inf and o3[4] == -np.inf
+
+
+@pytest.mark.parametrize("shape", [(37, 9, 5), (40, 12, 1), (7, 5, 3)])
+def test_mixed_single_operators(shape):
+    """Mixed mode per operator: residual, transposed residual, one RK4 step and one
+    adjoint step (with viscosity and source seeds) within FP32 rounding of the oracle."""
+    api = _api()
+    w = state(shape, 41)
+    P = params_for(w, mu=0.02, dt=2e-3)
+    S = make_solver(api, w, P, 1)
+    R = torch.empty(w.shape, dtype=torch.float64, device="cuda")
+    S.rhs(dev(w), R)
+    assert rel_l2(host(R), O.residual(w, P)) < 2e-5
+    a = synth.random_field(w.shape, 42)
+    S.rhs_transpose(dev(w), dev(a), R)
+    assert rel_l2(host(R), O.residual_transpose(w, a, P)) < 2e-5
+    w1 = torch.empty_like(R)
+    S.primal_step(dev(w), w1)
+    ref, _ = O.rk4_step(w, P)
+    assert rel_l2(host(w1) - w, ref - w) < 2e-5
+    nu = (0.01 * np.abs(synth.random_field(w.shape[1:], 43))).astype(np.float32)
+    lo = torch.empty_like(R)
+    sb = torch.zeros_like(R)
+    S.adjoint_step(dev(w), dev(a), lo, nu=dev(nu), sbar=sb)
+    lref, sref = O.rk4_adjoint_step(w, a, P, None, nu.astype(np.float64))
+    assert rel_l2(host(lo) - a, lref - a) < 2e-5
+    assert rel_l2(host(sb), sref) < 2e-5
