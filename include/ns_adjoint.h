@@ -221,6 +221,25 @@ int ns_adjoint_run(ns_ctx* ctx, const double* w0, const double* s, const ns_run_
 int ns_profile_enable(ns_ctx* ctx, int on);
 int ns_profile_read(ns_ctx* ctx, double* ms, long long* launches);
 
+/* ns_objective without any device allocation.  The paper has no counterpart: this is
+ * for callers that cannot call cudaMalloc, such as host frameworks that own every byte
+ * of device memory through their own pool or quota, or timing loops that must not take
+ * cudaMalloc's implicit device synchronisation.  It needs no context: p describes the
+ * grid, stream is a cudaStream_t (NULL = default stream).  Same result as ns_objective
+ * (J_acc[b] += weight * J(w_b); lam += weight * dJ/dw if lam != NULL), computed by the
+ * same kernels, but the reduction scratch is a file-scope device array of 256 KiB held
+ * by every GPU that loads the library until the process exits.
+ *  - Limit: batch <= 55 (2 * 296 * batch + 2 * batch doubles must fit); larger batches
+ *    return NS_ERR_BUDGET before any work is enqueued.
+ *  - The first call on a device looks up the array's device address on that device
+ *    (cudaGetSymbolAddress, with that device current); make that first call before
+ *    any stream capture.  NS_ERR_CUDA if the lookup fails.
+ *  - All calls share the one array: calls that overlap on the GPU (different streams,
+ *    no ordering between them) race and give wrong results.
+ *  - There is no sticky error word: a non-finite J simply shows in J_acc. */
+int ns_objective_noalloc(const ns_params* p, void* stream, const double* w, double weight,
+                         double* J_acc, double* lam);
+
 /* Synchronises the stream, then returns and clears the sticky device error word
  * (NS_OK, NS_ERR_NONFINITE or NS_ERR_UNSTABLE). */
 int ns_last_error(ns_ctx* ctx);

@@ -637,6 +637,10 @@ cudaError_t launch_max_wave(const GridDesc& g, double gamma, const double* w, do
 }  // namespace ns
 
 namespace ns {
+size_t objective_scratch_doubles(const GridDesc& g) {
+  return (size_t)2 * RG * g.batch + (size_t)2 * g.batch;
+}
+
 cudaError_t launch_to_float(const double* in, float* out, size_t n, cudaStream_t st) {
   const size_t threads = (n + 1) / 2;
   k_to_float<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(in, out, n);
