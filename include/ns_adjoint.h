@@ -215,6 +215,27 @@ int ns_adjoint_run(ns_ctx* ctx, const double* w0, const double* s, const ns_run_
                    void* arena, size_t arena_bytes, double* Jbar, double* lam0, double* sbar,
                    double* energy, double* sigma_stats);
 
+/* The two halves of ns_adjoint_run, for callers that separate the forward pass from the
+ * reverse sweep (an autograd wrapper).  ns_forward_run executes the plan up to the
+ * objective source at step N: it keeps the planned checkpoints in the arena and
+ * accumulates Jbar.  ns_backward_run then reverses the sweep on the same context and
+ * arena (w0, s and the arena must be unchanged in between) with a unit seed on Jbar:
+ * lam0 = dJbar/dw^0, sbar = dJbar/ds (may be NULL), energy / sigma_stats as in
+ * ns_adjoint_run.  A forward run is reversed at most once; NS_ERR_ARG otherwise. */
+int ns_forward_run(ns_ctx* ctx, const double* w0, const double* s, const ns_run_opts* o,
+                   void* arena, size_t arena_bytes, double* Jbar);
+int ns_backward_run(ns_ctx* ctx, double* lam0, double* sbar, double* energy, double* sigma_stats);
+
+/* field[b] *= seed[b] for every box b of a [batch][5][cells] field (device seed[batch]):
+ * applies a per-box output cotangent to unit-seed adjoints. */
+int ns_scale_boxes(ns_ctx* ctx, const double* seed, double* field);
+
+/* out[m] = sum_b sum_cells field[b][comp][cell] * phi[m][cell] for m < nphi (FP64,
+ * deterministic): the gradient of a time-constant source s[b][comp] = sum_m theta_m phi_m
+ * shared by all boxes, from the source sensitivity field. */
+int ns_dot_boxes(ns_ctx* ctx, const double* field, int comp, const double* phi, int nphi,
+                 double* out);
+
 /* Kernel timing for roofline reports: when on, the context records a CUDA event pair
  * around every adjoint-stage kernel it launches; ns_profile_read synchronises and
  * returns the summed milliseconds and the launch count since profiling was enabled. */

@@ -29,7 +29,8 @@ EXPORTED = [
     "ns_objective", "ns_growth_sigma1", "ns_add_adjoint_viscosity", "ns_apply_adjoint_viscosity",
     "ns_adjoint_energy", "ns_dot", "ns_combine", "ns_max_wave_speed", "ns_last_error",
     "ns_error_string", "ns_plan", "ns_run_arena_bytes", "ns_adjoint_run", "ns_profile_enable",
-    "ns_profile_read", "ns_to_float",
+    "ns_profile_read", "ns_to_float", "ns_forward_run", "ns_backward_run", "ns_scale_boxes",
+    "ns_dot_boxes",
 ]
 
 NS_CKPT_ALL = 0
@@ -101,6 +102,10 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "ns_combine": ([P, P, P, I, S, P], I),
         "ns_max_wave_speed": ([P, P, P], I),
         "ns_to_float": ([P, P, P, S], I),
+        "ns_forward_run": ([P, P, P, ctypes.POINTER(NsRunOpts), P, S, P], I),
+        "ns_backward_run": ([P, P, P, P, P], I),
+        "ns_scale_boxes": ([P, P, P], I),
+        "ns_dot_boxes": ([P, P, I, P, I, P], I),
         "ns_last_error": ([P], I),
         "ns_error_string": ([I], ctypes.c_char_p),
         "ns_plan": ([I, I, I, P, I, ctypes.POINTER(I), ctypes.POINTER(I),
@@ -292,6 +297,27 @@ class Solver:
                                        _ptr(Jbar, torch.float64), _ptr(lam0, torch.float64),
                                        _ptr(sbar, torch.float64), _ptr(energy, torch.float64),
                                        _ptr(sigma_stats, torch.float64)), "ns_adjoint_run")
+
+    def forward_run(self, w0, opts, arena, Jbar, s=None):
+        """Forward half of the sweep (keeps the checkpoints in arena, accumulates Jbar)."""
+        _check(self.lib.ns_forward_run(self._ctx, _ptr(w0, torch.float64), _ptr(s, torch.float64),
+                                       ctypes.byref(opts), _ptr(arena), arena.numel() * arena.element_size(),
+                                       _ptr(Jbar, torch.float64)), "ns_forward_run")
+
+    def backward_run(self, lam0, sbar=None, energy=None, sigma_stats=None):
+        """Reverse half of the sweep with a unit seed on each box's Jbar."""
+        _check(self.lib.ns_backward_run(self._ctx, _ptr(lam0, torch.float64), _ptr(sbar, torch.float64),
+                                        _ptr(energy, torch.float64), _ptr(sigma_stats, torch.float64)),
+               "ns_backward_run")
+
+    def scale_boxes(self, seed, field):
+        _check(self.lib.ns_scale_boxes(self._ctx, _ptr(seed, torch.float64), _ptr(field, torch.float64)),
+               "ns_scale_boxes")
+
+    def dot_boxes(self, field, comp, phi, out):
+        _check(self.lib.ns_dot_boxes(self._ctx, _ptr(field, torch.float64), int(comp),
+                                     _ptr(phi, torch.float64), phi.shape[0], _ptr(out, torch.float64)),
+               "ns_dot_boxes")
 
     def profile_enable(self, on=True):
         _check(self.lib.ns_profile_enable(self._ctx, int(on)), "ns_profile_enable")

@@ -233,6 +233,7 @@ void ns_destroy(ns_ctx* c) {
   if (c->scratch) cudaFree(c->scratch);
   if (c->err) cudaFree(c->err);
   for (cudaEvent_t ev : c->events) cudaEventDestroy(ev);
+  ns_sweep_release(c);
   delete c;
 }
 
@@ -384,6 +385,16 @@ int ns_dot(ns_ctx* c, const double* a, const double* phi, int nphi, size_t n, do
 int ns_combine(ns_ctx* c, const double* theta, const double* phi, int nphi, size_t n, double* s) {
   if (!c || !theta || !phi || !s || nphi < 1 || n == 0) return NS_ERR_ARG;
   return cuerr(ns::launch_combine(theta, phi, nphi, n, s, c->st));
+}
+
+int ns_scale_boxes(ns_ctx* c, const double* seed, double* field) {
+  if (!c || !seed || !field) return NS_ERR_ARG;
+  return cuerr(ns::launch_scale_boxes(c->g, seed, field, c->st));
+}
+
+int ns_dot_boxes(ns_ctx* c, const double* field, int comp, const double* phi, int nphi, double* out) {
+  if (!c || !field || !phi || !out || comp < 0 || comp > 4 || nphi < 1 || nphi > 256) return NS_ERR_ARG;
+  return cuerr(ns::launch_dot_boxes(c->g, field, comp, phi, nphi, out, c->scratch, c->st));
 }
 
 int ns_to_float(ns_ctx* c, const double* in, float* out, size_t n) {

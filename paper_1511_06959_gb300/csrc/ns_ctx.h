@@ -8,6 +8,8 @@
 #include "../../include/ns_adjoint.h"
 #include "ns_common.cuh"
 
+struct ns_sweep_state;
+
 struct ns_ctx {
   ns_params p;
   cudaStream_t st = nullptr;
@@ -29,4 +31,8 @@ struct ns_ctx {
   bool prof_on = false;          // event pairs around adjoint-stage launches
   size_t prof_used = 0;
   std::vector<cudaEvent_t> events;
+  ns_sweep_state* sweep = nullptr;   // executor state between ns_forward_run and ns_backward_run
 };
+
+// releases the sweep executor state of a context (defined with the executor)
+void ns_sweep_release(ns_ctx* c);

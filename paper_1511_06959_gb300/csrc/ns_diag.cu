@@ -530,6 +530,27 @@ __global__ void __launch_bounds__(RB) k_max_partials(int nblk, const double* par
   if (threadIdx.x == 0) out[0] = m;
 }
 
+__global__ void k_scale_boxes(GridDesc g, const double* __restrict__ seed, double* __restrict__ field) {
+  const long long tot = g.cells * 5 * g.batch;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < tot) field[i] *= seed[i / (g.cells * 5)];
+}
+
+__global__ void __launch_bounds__(RB) k_dot_boxes(GridDesc g, const double* __restrict__ field, int comp,
+                                                  const double* __restrict__ phi, double* partial) {
+  __shared__ double sh[RB];
+  const int m = blockIdx.y;
+  const double* pm = phi + (size_t)m * g.cells;
+  const long long tot = g.cells * g.batch;
+  double s = 0.0;
+  for (long long i = (long long)blockIdx.x * RB + threadIdx.x; i < tot; i += (long long)gridDim.x * RB) {
+    const long long b = i / g.cells, r = i - b * g.cells;
+    s += field[(size_t)b * 5 * g.cells + (size_t)comp * g.cells + r] * pm[r];
+  }
+  s = block_reduce(s, sh, AddOp());
+  if (threadIdx.x == 0) partial[(size_t)m * gridDim.x + blockIdx.x] = s;
+}
+
 __global__ void k_to_float(const double* __restrict__ in, float* __restrict__ out, size_t n) {
   const size_t i = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) * 2;
   if (i + 1 < n) {
@@ -637,6 +658,21 @@ cudaError_t launch_max_wave(const GridDesc& g, double gamma, const double* w, do
 }  // namespace ns
 
 namespace ns {
+cudaError_t launch_scale_boxes(const GridDesc& g, const double* seed, double* field, cudaStream_t st) {
+  const long long tot = g.cells * 5 * g.batch;
+  k_scale_boxes<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(g, seed, field);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dot_boxes(const GridDesc& g, const double* field, int comp, const double* phi, int nphi,
+                             double* out, double* scratch, cudaStream_t st) {
+  k_dot_boxes<<<dim3(RG, nphi), RB, 0, st>>>(g, field, comp, phi, scratch);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_sum_partials<<<nphi, RB, 0, st>>>(RG, 1.0, scratch, out, nullptr);
+  return cudaGetLastError();
+}
+
 size_t objective_scratch_doubles(const GridDesc& g) {
   return (size_t)2 * RG * g.batch + (size_t)2 * g.batch;
 }

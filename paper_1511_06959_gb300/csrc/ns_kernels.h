@@ -88,6 +88,9 @@ cudaError_t launch_combine(const double* theta, const double* phi, int nphi, siz
 cudaError_t launch_max_wave(const GridDesc& g, double gamma, const double* w, double* out,
                             double* scratch, cudaStream_t st);
 cudaError_t launch_to_float(const double* in, float* out, size_t n, cudaStream_t st);
+cudaError_t launch_scale_boxes(const GridDesc& g, const double* seed, double* field, cudaStream_t st);
+cudaError_t launch_dot_boxes(const GridDesc& g, const double* field, int comp, const double* phi,
+                             int nphi, double* out, double* scratch, cudaStream_t st);
 // doubles of scratch that launch_objective uses for a grid (its partials and plane sums)
 size_t objective_scratch_doubles(const GridDesc& g);
 

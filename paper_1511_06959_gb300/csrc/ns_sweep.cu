@@ -217,107 +217,187 @@ size_t ns_run_arena_bytes(const ns_ctx* c, const ns_run_opts* o) {
   return layout_for(c, P.maxlive).total;
 }
 
-int ns_adjoint_run(ns_ctx* c, const double* w0, const double* s, const ns_run_opts* o, void* arena,
-                   size_t arena_bytes, double* Jbar, double* lam0, double* sbar, double* energy,
-                   double* sigma_stats) {
-  if (!c || !w0 || !o || !arena || !Jbar || !lam0 || lam0 == w0) return NS_ERR_ARG;
-  if (((uintptr_t)arena & 255) != 0) return NS_ERR_ARG;
-  if (!(o->lambda >= 0.0)) return NS_ERR_ARG;
+}  // extern "C"
+
+// Executor state between the forward part of a plan (up to its SOURCE action) and the
+// backward part; owned by the context.
+struct ns_sweep_state {
   Planner P;
-  int r = make_plan(o->nsteps, o->schedule, o->param, P);
-  if (r) return r;
-  const Layout L = layout_for(c, P.maxlive);
-  if (arena_bytes < L.total) return NS_ERR_BUDGET;
-  const int N = o->nsteps;
+  Layout L;
+  ns_run_opts o;
+  const double* w0 = nullptr;
+  const double* s = nullptr;
+  std::vector<double*> buf;
+  double* lamA = nullptr;
+  float* sig = nullptr;
+  float* nu = nullptr;
+  double* jtmp = nullptr;
+  double* Jbar = nullptr;
+  std::vector<int> slot_buf;
+  std::vector<char> owned;
+  int cur = -1;       // -1: the caller's w0
+  int touched = 0;
+  size_t pos = 0;     // next action
+  bool forward_done = false;
+};
+
+void ns_sweep_release(ns_ctx* c) {
+  delete c->sweep;
+  c->sweep = nullptr;
+}
+
+namespace {
+
+// Run actions [S.pos, end) until (not including) the first action with op == stop_op
+// (stop_op = 0: to the end).  lam_cur/lam_nxt, sbar, energy, sigma_stats are used by
+// the backward part only.
+int run_actions(ns_ctx* c, ns_sweep_state& S, int stop_op, double*& lam_cur, double*& lam_nxt,
+                double* sbar, double* energy, double* sigma_stats) {
+  const int N = S.o.nsteps;
   const int B = c->g.batch;
   const double wN = 1.0 / N;
-  char* base = (char*)arena;
-  std::vector<double*> buf(L.nbuf);
-  for (int i = 0; i < L.nbuf; ++i) buf[i] = (double*)(base + (size_t)i * L.state);
-  char* q = base + (size_t)L.nbuf * L.state;
-  double* lamA = (double*)q;
-  q += L.lam;
-  float* sig = (float*)q;
-  q += L.sig;
-  float* nu = (float*)q;
-  q += L.nu;
-  double* jtmp = (double*)q;
-  const bool need_sigma = o->lambda > 0.0 || o->record_sigma;
-  cudaStream_t st = c->st;
-  const size_t fbytes = c->field * sizeof(double);
-
-  double* lam_cur = (N % 2 == 0) ? lam0 : lamA;
-  double* lam_nxt = (N % 2 == 0) ? lamA : lam0;
-  if (cudaMemsetAsync(lam_cur, 0, fbytes, st) != cudaSuccess) return NS_ERR_CUDA;
-  if (cudaMemsetAsync(Jbar, 0, B * sizeof(double), st) != cudaSuccess) return NS_ERR_CUDA;
-  if (cudaMemsetAsync(jtmp, 0, 2 * B * sizeof(double), st) != cudaSuccess) return NS_ERR_CUDA;
-  if (sbar && cudaMemsetAsync(sbar, 0, fbytes, st) != cudaSuccess) return NS_ERR_CUDA;
-
-  std::vector<int> slot_buf(std::max(P.maxlive, 1), -1);
-  std::vector<char> owned(L.nbuf, 0);
-  int cur = -1;   // -1: the caller's w0
-  int touched = 0;
-  auto ptr = [&](int i) -> const double* { return i < 0 ? w0 : buf[i]; };
+  const bool need_sigma = S.o.lambda > 0.0 || S.o.record_sigma;
+  auto ptr = [&](int i) -> const double* { return i < 0 ? S.w0 : S.buf[i]; };
   auto pick_free = [&]() -> int {
-    for (int i = 0; i < L.nbuf; ++i)
-      if (!owned[i] && i != cur) return i;
+    for (int i = 0; i < S.L.nbuf; ++i)
+      if (!S.owned[i] && i != S.cur) return i;
     return -2;
   };
-
-  for (const ns_action& A : P.acts) {
+  int r;
+  for (; S.pos < S.P.acts.size(); ++S.pos) {
+    const ns_action& A = S.P.acts[S.pos];
+    if (stop_op && A.op == stop_op) return NS_OK;
     switch (A.op) {
       case NS_OP_ADVANCE:
         for (int n = A.a; n < A.b; ++n) {
           const int out = pick_free();
           if (out < 0) return NS_ERR_BUDGET;
-          if ((r = ns_primal_step(c, ptr(cur), s, buf[out]))) return r;
-          if (n + 1 > touched) {
-            if ((r = ns_objective(c, buf[out], wN, Jbar, nullptr))) return r;
-            touched = n + 1;
+          if ((r = ns_primal_step(c, ptr(S.cur), S.s, S.buf[out]))) return r;
+          if (n + 1 > S.touched) {
+            if ((r = ns_objective(c, S.buf[out], wN, S.Jbar, nullptr))) return r;
+            S.touched = n + 1;
           }
-          cur = out;
+          S.cur = out;
         }
         break;
       case NS_OP_STORE:
-        if (cur < 0) return NS_ERR_ARG;
-        slot_buf[A.b] = cur;
-        owned[cur] = 1;
+        if (S.cur < 0) return NS_ERR_ARG;
+        S.slot_buf[A.b] = S.cur;
+        S.owned[S.cur] = 1;
         break;
       case NS_OP_LOAD:
-        cur = A.b < 0 ? -1 : slot_buf[A.b];
+        S.cur = A.b < 0 ? -1 : S.slot_buf[A.b];
         break;
       case NS_OP_FREE:
-        owned[slot_buf[A.b]] = 0;
-        slot_buf[A.b] = -1;
+        S.owned[S.slot_buf[A.b]] = 0;
+        S.slot_buf[A.b] = -1;
         break;
       case NS_OP_SOURCE:
-        if ((r = ns_objective(c, ptr(cur), wN, jtmp, lam_cur))) return r;
-        if (o->record_energy && (r = ns_adjoint_energy(c, ptr(cur), lam_cur, energy + (size_t)A.a * B)))
+        if ((r = ns_objective(c, ptr(S.cur), wN, S.jtmp, lam_cur))) return r;
+        if (S.o.record_energy && energy &&
+            (r = ns_adjoint_energy(c, ptr(S.cur), lam_cur, energy + (size_t)A.a * B)))
           return r;
         break;
       case NS_OP_ADJOINT: {
         const float* nup = nullptr;
         if (need_sigma) {
-          double* stats = o->record_sigma && sigma_stats ? sigma_stats + (size_t)A.a * 2 * B : nullptr;
-          if ((r = ns_growth_sigma1(c, ptr(cur), sig, stats))) return r;
-          if (o->lambda > 0.0) {
-            if ((r = ns_add_adjoint_viscosity(c, sig, o->lambda, o->tau, nu))) return r;
-            nup = nu;
+          double* stats = S.o.record_sigma && sigma_stats ? sigma_stats + (size_t)A.a * 2 * B : nullptr;
+          if ((r = ns_growth_sigma1(c, ptr(S.cur), S.sig, stats))) return r;
+          if (S.o.lambda > 0.0) {
+            if ((r = ns_add_adjoint_viscosity(c, S.sig, S.o.lambda, S.o.tau, S.nu))) return r;
+            nup = S.nu;
           }
         }
-        if ((r = ns_adjoint_step(c, ptr(cur), s, lam_cur, nup, lam_nxt, sbar))) return r;
+        if ((r = ns_adjoint_step(c, ptr(S.cur), S.s, lam_cur, nup, lam_nxt, sbar))) return r;
         std::swap(lam_cur, lam_nxt);
-        if (A.a >= 1 && (r = ns_objective(c, ptr(cur), wN, jtmp, lam_cur))) return r;
-        if (o->record_energy && (r = ns_adjoint_energy(c, ptr(cur), lam_cur, energy + (size_t)A.a * B)))
+        if (A.a >= 1 && (r = ns_objective(c, ptr(S.cur), wN, S.jtmp, lam_cur))) return r;
+        if (S.o.record_energy && energy &&
+            (r = ns_adjoint_energy(c, ptr(S.cur), lam_cur, energy + (size_t)A.a * B)))
           return r;
         break;
       }
       default: return NS_ERR_ARG;
     }
   }
-  if (lam_cur != lam0 && cudaMemcpyAsync(lam0, lam_cur, fbytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
-    return NS_ERR_CUDA;
   return NS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ns_forward_run(ns_ctx* c, const double* w0, const double* s, const ns_run_opts* o, void* arena,
+                   size_t arena_bytes, double* Jbar) {
+  if (!c || !w0 || !o || !arena || !Jbar) return NS_ERR_ARG;
+  if (((uintptr_t)arena & 255) != 0) return NS_ERR_ARG;
+  if (!(o->lambda >= 0.0)) return NS_ERR_ARG;
+  ns_sweep_release(c);
+  ns_sweep_state* S = new ns_sweep_state();
+  int r = make_plan(o->nsteps, o->schedule, o->param, S->P);
+  if (r) {
+    delete S;
+    return r;
+  }
+  S->L = layout_for(c, S->P.maxlive);
+  if (arena_bytes < S->L.total) {
+    delete S;
+    return NS_ERR_BUDGET;
+  }
+  S->o = *o;
+  S->w0 = w0;
+  S->s = s;
+  S->Jbar = Jbar;
+  char* base = (char*)arena;
+  S->buf.resize(S->L.nbuf);
+  for (int i = 0; i < S->L.nbuf; ++i) S->buf[i] = (double*)(base + (size_t)i * S->L.state);
+  char* q = base + (size_t)S->L.nbuf * S->L.state;
+  S->lamA = (double*)q;
+  q += S->L.lam;
+  S->sig = (float*)q;
+  q += S->L.sig;
+  S->nu = (float*)q;
+  q += S->L.nu;
+  S->jtmp = (double*)q;
+  S->slot_buf.assign(std::max(S->P.maxlive, 1), -1);
+  S->owned.assign(S->L.nbuf, 0);
+  c->sweep = S;
+  const int B = c->g.batch;
+  if (cudaMemsetAsync(Jbar, 0, B * sizeof(double), c->st) != cudaSuccess) return NS_ERR_CUDA;
+  if (cudaMemsetAsync(S->jtmp, 0, 2 * B * sizeof(double), c->st) != cudaSuccess) return NS_ERR_CUDA;
+  double* dummy = nullptr;
+  r = run_actions(c, *S, NS_OP_SOURCE, dummy, dummy, nullptr, nullptr, nullptr);
+  if (r) return r;
+  S->forward_done = true;
+  return NS_OK;
+}
+
+int ns_backward_run(ns_ctx* c, double* lam0, double* sbar, double* energy, double* sigma_stats) {
+  if (!c || !lam0 || !c->sweep || !c->sweep->forward_done) return NS_ERR_ARG;
+  ns_sweep_state& S = *c->sweep;
+  if (lam0 == S.w0 || (sbar && (sbar == lam0 || sbar == S.w0))) return NS_ERR_ARG;
+  const size_t fbytes = c->field * sizeof(double);
+  const int N = S.o.nsteps;
+  double* lam_cur = (N % 2 == 0) ? lam0 : S.lamA;
+  double* lam_nxt = (N % 2 == 0) ? S.lamA : lam0;
+  if (cudaMemsetAsync(lam_cur, 0, fbytes, c->st) != cudaSuccess) return NS_ERR_CUDA;
+  if (sbar && cudaMemsetAsync(sbar, 0, fbytes, c->st) != cudaSuccess) return NS_ERR_CUDA;
+  S.forward_done = false;   // a plan is reversed once
+  int r = run_actions(c, S, 0, lam_cur, lam_nxt, sbar, energy, sigma_stats);
+  if (r) return r;
+  if (lam_cur != lam0 &&
+      cudaMemcpyAsync(lam0, lam_cur, fbytes, cudaMemcpyDeviceToDevice, c->st) != cudaSuccess)
+    return NS_ERR_CUDA;
+  ns_sweep_release(c);
+  return NS_OK;
+}
+
+int ns_adjoint_run(ns_ctx* c, const double* w0, const double* s, const ns_run_opts* o, void* arena,
+                   size_t arena_bytes, double* Jbar, double* lam0, double* sbar, double* energy,
+                   double* sigma_stats) {
+  if (!c || !w0 || !o || !arena || !Jbar || !lam0 || lam0 == w0) return NS_ERR_ARG;
+  int r = ns_forward_run(c, w0, s, o, arena, arena_bytes, Jbar);
+  if (r) return r;
+  return ns_backward_run(c, lam0, sbar, energy, sigma_stats);
 }
 
 }  // extern "C"
