@@ -198,6 +198,9 @@ typedef struct {
   int record_energy; /* write E_vhat(w^n, lam^n), n = 0..N, to energy[n][batch] */
   int record_sigma;  /* write (max, mean) of sigma_1(w^n), n = 0..N-1, to sigma_stats[n][batch][2]
                         (sigma_1 is always evaluated when lambda > 0) */
+  const void* mlp;   /* learned closure (device network blob, see ns_mlp_*), or NULL: when set,
+                        nu = lambda dx^2 sigma_1 softplus(MLP(f)) replaces the sigma_1 rule
+                        (lambda is then the global factor kappa) */
 } ns_run_opts;
 
 /* Device bytes the caller must provide as the arena of ns_adjoint_run (state slots,
@@ -260,6 +263,50 @@ int ns_profile_read(ns_ctx* ctx, double* ms, long long* launches);
  *  - There is no sticky error word: a non-finite J simply shows in J_acc. */
 int ns_objective_noalloc(const ns_params* p, void* stream, const double* w, double weight,
                          double* J_acc, double* lam);
+
+/* ------------------------------------------------------------------------------
+ * Learned adjoint-viscosity closure.  The paper tunes one constant lambda by hand in
+ * the stabilised adjoint (section "Energy analysis") and leaves its automatic estimation
+ * open (conclusion); here a per-cell coefficient is predicted from local flow features:
+ *   nu(x) = kappa dx^2 sigma_1(x) softplus(MLP(f(x))),
+ * MLP 14 -> 64 -> 64 -> 1 with GELU hidden layers, BF16 weights on the tensor cores,
+ * FP32 accumulation.  Features f: the symmetrised variables S(q_bar)(q - q_bar) about the
+ * box-mean primitive state, over the mean sound speed, and the 9 central-difference
+ * entries of grad u times L / c_bar (L = 1); stored as 16 floats per cell (last two 0).
+ * A network is a caller-owned device blob of ns_mlp_net_bytes() bytes holding FP32
+ * master parameters (NS_MLP_PARAMS, order W1[14][64], b1[64], W2[64][64], b2[64],
+ * w3[64], b3), the Adam moments and the inference copies.
+ * ---------------------------------------------------------------------------- */
+#define NS_MLP_PARAMS 5185
+size_t ns_mlp_net_bytes(void);
+/* master parameters = params (device, NS_MLP_PARAMS floats), Adam moments zeroed */
+int ns_mlp_set_params(ns_ctx* ctx, void* net, const float* params);
+/* params (device, NS_MLP_PARAMS floats) = the FP32 master parameters */
+int ns_mlp_get_params(ns_ctx* ctx, const void* net, float* params);
+/* out (device, NS_MLP_PARAMS floats) = the first (which = 1) or second (which = 2) Adam
+ * moment of the network */
+int ns_mlp_get_moment(ns_ctx* ctx, const void* net, int which, float* out);
+/* feat[batch * cells][16] from w */
+int ns_mlp_features(ns_ctx* ctx, const double* w, float* feat);
+/* nu = kappa dx^2 sigma_1 softplus(MLP(feat)) for every cell; NS_ERR_UNSTABLE is set in
+ * the sticky error word as for ns_add_adjoint_viscosity */
+int ns_mlp_infer(ns_ctx* ctx, const void* net, const float* feat, const float* sigma1, double kappa,
+                 float* nu);
+/* One Adam step (lr, beta 0.9 / 0.999, eps 1e-8; step >= 1 counts from 1) on the mean
+ * squared error of softplus(MLP(feat[idx[i]])) against target[idx[i]], i < n, with the
+ * forward pass quantised exactly as ns_mlp_infer.  loss (device float, may be NULL)
+ * receives the minibatch loss before the update.  The first call, or a larger n,
+ * allocates the context's training scratch. */
+int ns_mlp_train_step(ns_ctx* ctx, void* net, const float* feat, const float* target, const int* idx,
+                      int n, int step, double lr, float* loss);
+/* Training label: acc[cell] += max(0, v_hat^T M v_hat) / |grad v_hat|^2 with
+ * w_hat = lam, v_hat = T^-T w_hat ("Symmetrization") and M the growth matrix of
+ * Eq. (e:energy_1): the viscosity that balances local growth and the dissipation of an
+ * identity-Laplacian added term.  2D boxes use the (rho, u1, u2, p) block. */
+int ns_adjoint_label(ns_ctx* ctx, const double* w, const double* lam, float* acc);
+/* Training target t = min(acc / (dx^2 sigma_1), t_max) per cell (the label as a
+ * coefficient of dx^2 sigma_1, the form the network predicts) */
+int ns_label_target(ns_ctx* ctx, const float* acc, const float* sigma1, double t_max, float* target);
 
 /* Synchronises the stream, then returns and clears the sticky device error word
  * (NS_OK, NS_ERR_NONFINITE or NS_ERR_UNSTABLE). */

@@ -30,8 +30,11 @@ EXPORTED = [
     "ns_adjoint_energy", "ns_dot", "ns_combine", "ns_max_wave_speed", "ns_last_error",
     "ns_error_string", "ns_plan", "ns_run_arena_bytes", "ns_adjoint_run", "ns_profile_enable",
     "ns_profile_read", "ns_to_float", "ns_forward_run", "ns_backward_run", "ns_scale_boxes",
-    "ns_dot_boxes",
+    "ns_dot_boxes", "ns_mlp_net_bytes", "ns_mlp_set_params", "ns_mlp_get_params", "ns_mlp_get_moment",
+    "ns_mlp_features", "ns_mlp_infer", "ns_mlp_train_step", "ns_adjoint_label", "ns_label_target",
 ]
+
+NS_MLP_PARAMS = 5185
 
 NS_CKPT_ALL = 0
 NS_CKPT_STRIDE = 1
@@ -57,7 +60,7 @@ class NsRunOpts(ctypes.Structure):
     _fields_ = [
         ("nsteps", ctypes.c_int), ("schedule", ctypes.c_int), ("param", ctypes.c_int),
         ("lambda_", ctypes.c_double), ("tau", ctypes.c_double), ("record_energy", ctypes.c_int),
-        ("record_sigma", ctypes.c_int),
+        ("record_sigma", ctypes.c_int), ("mlp", ctypes.c_void_p),
     ]
 
 
@@ -106,6 +109,15 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "ns_backward_run": ([P, P, P, P, P], I),
         "ns_scale_boxes": ([P, P, P], I),
         "ns_dot_boxes": ([P, P, I, P, I, P], I),
+        "ns_mlp_net_bytes": ([], S),
+        "ns_mlp_set_params": ([P, P, P], I),
+        "ns_mlp_get_params": ([P, P, P], I),
+        "ns_mlp_get_moment": ([P, P, I, P], I),
+        "ns_mlp_features": ([P, P, P], I),
+        "ns_mlp_infer": ([P, P, P, P, D, P], I),
+        "ns_mlp_train_step": ([P, P, P, P, P, I, I, D, P], I),
+        "ns_adjoint_label": ([P, P, P, P], I),
+        "ns_label_target": ([P, P, P, D, P], I),
         "ns_last_error": ([P], I),
         "ns_error_string": ([I], ctypes.c_char_p),
         "ns_plan": ([I, I, I, P, I, ctypes.POINTER(I), ctypes.POINTER(I),
@@ -282,8 +294,11 @@ class Solver:
 
     # --- checkpointed sweep ----------------------------------------------------------
     def run_opts(self, nsteps, schedule=NS_CKPT_ALL, param=0, lam_coef=0.0, tau=0.0,
-                 record_energy=False, record_sigma=False):
-        return NsRunOpts(nsteps, schedule, param, lam_coef, tau, int(record_energy), int(record_sigma))
+                 record_energy=False, record_sigma=False, mlp=None):
+        """Sweep options; mlp: a network blob (uint8 CUDA tensor) selecting the learned
+        closure, with lam_coef then its global factor kappa."""
+        return NsRunOpts(nsteps, schedule, param, lam_coef, tau, int(record_energy), int(record_sigma),
+                         None if mlp is None else ctypes.c_void_p(mlp.data_ptr()))
 
     def arena_bytes(self, opts) -> int:
         return int(self.lib.ns_run_arena_bytes(self._ctx, ctypes.byref(opts)))
@@ -319,6 +334,38 @@ class Solver:
                                      _ptr(phi, torch.float64), phi.shape[0], _ptr(out, torch.float64)),
                "ns_dot_boxes")
 
+    # --- learned closure -------------------------------------------------------------
+    def mlp_set_params(self, net, params):
+        _check(self.lib.ns_mlp_set_params(self._ctx, _ptr(net), _ptr(params, torch.float32)), "ns_mlp_set_params")
+
+    def mlp_get_params(self, net, out):
+        _check(self.lib.ns_mlp_get_params(self._ctx, _ptr(net), _ptr(out, torch.float32)), "ns_mlp_get_params")
+
+    def mlp_get_moment(self, net, which, out):
+        _check(self.lib.ns_mlp_get_moment(self._ctx, _ptr(net), int(which), _ptr(out, torch.float32)),
+               "ns_mlp_get_moment")
+
+    def mlp_features(self, w, feat):
+        _check(self.lib.ns_mlp_features(self._ctx, _ptr(w, torch.float64), _ptr(feat, torch.float32)),
+               "ns_mlp_features")
+
+    def mlp_infer(self, net, feat, sigma1, kappa, nu):
+        _check(self.lib.ns_mlp_infer(self._ctx, _ptr(net), _ptr(feat, torch.float32), _ptr(sigma1, torch.float32),
+                                     float(kappa), _ptr(nu, torch.float32)), "ns_mlp_infer")
+
+    def mlp_train_step(self, net, feat, target, idx, step, lr, loss=None):
+        _check(self.lib.ns_mlp_train_step(self._ctx, _ptr(net), _ptr(feat, torch.float32),
+                                          _ptr(target, torch.float32), _ptr(idx, torch.int32), idx.numel(),
+                                          int(step), float(lr), _ptr(loss, torch.float32)), "ns_mlp_train_step")
+
+    def adjoint_label(self, w, lam, acc):
+        _check(self.lib.ns_adjoint_label(self._ctx, _ptr(w, torch.float64), _ptr(lam, torch.float64),
+                                         _ptr(acc, torch.float32)), "ns_adjoint_label")
+
+    def label_target(self, acc, sigma1, t_max, target):
+        _check(self.lib.ns_label_target(self._ctx, _ptr(acc, torch.float32), _ptr(sigma1, torch.float32),
+                                        float(t_max), _ptr(target, torch.float32)), "ns_label_target")
+
     def profile_enable(self, on=True):
         _check(self.lib.ns_profile_enable(self._ctx, int(on)), "ns_profile_enable")
 
@@ -327,3 +374,7 @@ class Solver:
         n = ctypes.c_longlong()
         _check(self.lib.ns_profile_read(self._ctx, ctypes.byref(ms), ctypes.byref(n)), "ns_profile_read")
         return ms.value, n.value
+
+
+def mlp_net_bytes() -> int:
+    return int(_lib().ns_mlp_net_bytes())

@@ -11,6 +11,7 @@
 #include "ns_common.cuh"
 #include "ns_kernels.h"
 #include "ns_ctx.h"
+#include "ns_mlp.h"
 
 using ns::Coef;
 using ns::Dual;
@@ -210,9 +211,10 @@ int ns_create(const ns_params* p, void* stream, ns_ctx** out) {
   const size_t esz = p->precision == NS_MIXED ? sizeof(float) : sizeof(double);
   cudaError_t e = cudaSuccess;
   for (int i = 0; i < ns_ctx::NSTAGE && e == cudaSuccess; ++i) e = cudaMalloc(&c->stage[i], c->field * esz);
-  c->scratch_n = ns::diag_scratch_doubles(c->g, 256);
+  c->scratch_n = std::max(ns::diag_scratch_doubles(c->g, 256), ns::box_means_scratch_doubles(c->g));
   if (e == cudaSuccess) e = cudaMalloc(&c->scratch, c->scratch_n * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&c->err, sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMalloc(&c->qbar, sizeof(double) * 5 * p->batch);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->err, 0, sizeof(unsigned), c->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
   if (e != cudaSuccess) {
@@ -232,6 +234,8 @@ void ns_destroy(ns_ctx* c) {
     if (c->tan[i]) cudaFree(c->tan[i]);
   if (c->scratch) cudaFree(c->scratch);
   if (c->err) cudaFree(c->err);
+  if (c->qbar) cudaFree(c->qbar);
+  if (c->train_scratch) cudaFree(c->train_scratch);
   for (cudaEvent_t ev : c->events) cudaEventDestroy(ev);
   ns_sweep_release(c);
   delete c;
@@ -357,11 +361,15 @@ int ns_growth_sigma1(ns_ctx* c, const double* w, float* sigma1, double* stats) {
   return cuerr(ns::launch_sigma1<double>(c->g, c->cd, w, sigma1, stats, c->scratch, c->st));
 }
 
-int ns_add_adjoint_viscosity(ns_ctx* c, const float* sigma1, double lambda, double tau, float* nu) {
-  if (!c || !sigma1 || !nu || !(lambda >= 0)) return NS_ERR_ARG;
+static double nu_limit(const ns_ctx* c) {
   const double k = 4.0 * (1.0 / (c->p.dx * c->p.dx) + 1.0 / (c->p.dy * c->p.dy) +
                           (c->p.nz > 1 ? 1.0 / (c->p.dz * c->p.dz) : 0.0));
-  const double limit = c->p.dt > 0 ? 2.78 / (c->p.dt * k) : INFINITY;
+  return c->p.dt > 0 ? 2.78 / (c->p.dt * k) : INFINITY;
+}
+
+int ns_add_adjoint_viscosity(ns_ctx* c, const float* sigma1, double lambda, double tau, float* nu) {
+  if (!c || !sigma1 || !nu || !(lambda >= 0)) return NS_ERR_ARG;
+  const double limit = nu_limit(c);
   return cuerr(ns::launch_nu_rule(c->g, sigma1, lambda, tau, limit, nu, c->err, c->st));
 }
 
@@ -395,6 +403,69 @@ int ns_scale_boxes(ns_ctx* c, const double* seed, double* field) {
 int ns_dot_boxes(ns_ctx* c, const double* field, int comp, const double* phi, int nphi, double* out) {
   if (!c || !field || !phi || !out || comp < 0 || comp > 4 || nphi < 1 || nphi > 256) return NS_ERR_ARG;
   return cuerr(ns::launch_dot_boxes(c->g, field, comp, phi, nphi, out, c->scratch, c->st));
+}
+
+size_t ns_mlp_net_bytes(void) { return ns::MLP_BYTES; }
+
+int ns_mlp_set_params(ns_ctx* c, void* net, const float* params) {
+  if (!c || !net || !params) return NS_ERR_ARG;
+  return cuerr(ns::launch_mlp_set(net, params, c->st));
+}
+
+int ns_mlp_get_params(ns_ctx* c, const void* net, float* params) {
+  if (!c || !net || !params) return NS_ERR_ARG;
+  return cuerr(cudaMemcpyAsync(params, (const char*)net + ns::MLP_OFF_MASTER, sizeof(float) * ns::NPAR,
+                               cudaMemcpyDeviceToDevice, c->st));
+}
+
+int ns_mlp_get_moment(ns_ctx* c, const void* net, int which, float* out) {
+  if (!c || !net || !out || (which != 1 && which != 2)) return NS_ERR_ARG;
+  const size_t off = which == 1 ? ns::MLP_OFF_M : ns::MLP_OFF_V;
+  return cuerr(cudaMemcpyAsync(out, (const char*)net + off, sizeof(float) * ns::NPAR, cudaMemcpyDeviceToDevice,
+                               c->st));
+}
+
+int ns_mlp_features(ns_ctx* c, const double* w, float* feat) {
+  if (!c || !w || !feat) return NS_ERR_ARG;
+  if (ns::launch_box_means(c->g, c->p.gamma, w, c->qbar, c->scratch, c->st) != cudaSuccess) return NS_ERR_CUDA;
+  return cuerr(ns::launch_features(c->g, c->cf, w, c->qbar, feat, c->st));
+}
+
+int ns_mlp_infer(ns_ctx* c, const void* net, const float* feat, const float* sigma1, double kappa, float* nu) {
+  if (!c || !net || !feat || !sigma1 || !nu || !(kappa >= 0)) return NS_ERR_ARG;
+  const double scale = kappa * c->p.dx * c->p.dx;
+  return cuerr(ns::launch_mlp_infer(c->g.cells * c->g.batch, const_cast<void*>(net), feat, sigma1, scale,
+                                    nu_limit(c), nu, c->err, c->st));
+}
+
+int ns_mlp_train_step(ns_ctx* c, void* net, const float* feat, const float* target, const int* idx, int n,
+                      int step, double lr, float* loss) {
+  if (!c || !net || !feat || !target || !idx || n < 1 || step < 1 || !(lr > 0)) return NS_ERR_ARG;
+  const size_t need = ns::mlp_train_scratch_floats(n);
+  if (need > c->train_scratch_n) {
+    if (c->train_scratch) cudaFree(c->train_scratch);
+    c->train_scratch = nullptr;
+    c->train_scratch_n = 0;
+    if (cudaMalloc(&c->train_scratch, need * sizeof(float)) != cudaSuccess) return NS_ERR_CUDA;
+    c->train_scratch_n = need;
+  }
+  return cuerr(ns::launch_mlp_train_step(net, feat, target, idx, n, step, lr, c->train_scratch, loss, c->st));
+}
+
+int ns_adjoint_label(ns_ctx* c, const double* w, const double* lam, float* acc) {
+  if (!c || !w || !lam || !acc) return NS_ERR_ARG;
+  if (mixed(c)) {
+    float* wf = buf<float>(c, WF);
+    if (ns::launch_to_float(w, wf, c->field, c->st) != cudaSuccess) return NS_ERR_CUDA;
+    return cuerr(ns::launch_label<float>(c->g, c->cf, wf, lam, acc, c->st));
+  }
+  return cuerr(ns::launch_label<double>(c->g, c->cd, w, lam, acc, c->st));
+}
+
+int ns_label_target(ns_ctx* c, const float* acc, const float* sigma1, double t_max, float* target) {
+  if (!c || !acc || !sigma1 || !target || !(t_max > 0)) return NS_ERR_ARG;
+  return cuerr(ns::launch_label_target(c->g.cells * c->g.batch, acc, sigma1, c->p.dx * c->p.dx, t_max, target,
+                                       c->st));
 }
 
 int ns_to_float(ns_ctx* c, const double* in, float* out, size_t n) {

@@ -32,6 +32,9 @@ struct ns_ctx {
   size_t prof_used = 0;
   std::vector<cudaEvent_t> events;
   ns_sweep_state* sweep = nullptr;   // executor state between ns_forward_run and ns_backward_run
+  double* qbar = nullptr;            // box-mean primitive states [batch][5] (closure features)
+  float* train_scratch = nullptr;    // closure training partials, allocated on first use
+  size_t train_scratch_n = 0;
 };
 
 // releases the sweep executor state of a context (defined with the executor)

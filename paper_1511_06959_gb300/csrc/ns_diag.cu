@@ -297,63 +297,71 @@ __device__ T sigma1_of(const T M[5][5]) {
   return sqrt(l > T(0) ? l : T(0));
 }
 
+// Growth matrix M = M1 - M2 of one cell from central differences of rho, u, p, a, b at
+// its six neighbours (closed forms of section "Energy analysis").
+template <class CT>
+__device__ __forceinline__ void growth_matrix(const GridDesc& g, const Coef<CT>& c, const CT* __restrict__ w,
+                                              int b, int x, int y, int z, CT M[5][5]) {
+  const CT gam = c.gamma, gm1 = c.gm1;
+  const size_t box = (size_t)b * 5 * g.cells;
+  auto at = [&](int xx, int yy, int zz) {
+    return box + (size_t)wrap(zz, g.nz) * g.plane + (size_t)wrap(yy, g.ny) * g.nx + wrap(xx, g.nx);
+  };
+  const Prim<CT> P0 = prim_at<CT>(w, at(x, y, z), g.cells, gam);
+  Prim<CT> Pm[3], Pp[3];
+  Pm[0] = prim_at<CT>(w, at(x - 1, y, z), g.cells, gam);
+  Pp[0] = prim_at<CT>(w, at(x + 1, y, z), g.cells, gam);
+  Pm[1] = prim_at<CT>(w, at(x, y - 1, z), g.cells, gam);
+  Pp[1] = prim_at<CT>(w, at(x, y + 1, z), g.cells, gam);
+  Pm[2] = prim_at<CT>(w, at(x, y, z - 1), g.cells, gam);
+  Pp[2] = prim_at<CT>(w, at(x, y, z + 1), g.cells, gam);
+  CT drho[3], du[3][3], dp[3], da[3], db[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const CT h = c.hidx[j];
+    drho[j] = (Pp[j].rho - Pm[j].rho) * h;
+    dp[j] = (Pp[j].p - Pm[j].p) * h;
+    da[j] = (Pp[j].a - Pm[j].a) * h;
+    db[j] = (Pp[j].b - Pm[j].b) * h;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) du[k][j] = (Pp[j].u[k] - Pm[j].u[k]) * h;
+  }
+  const CT div = du[0][0] + du[1][1] + du[2][2];
+  // M1 (closed form)
+#pragma unroll
+  for (int i2 = 0; i2 < 5; ++i2)
+#pragma unroll
+    for (int j2 = 0; j2 < 5; ++j2) M[i2][j2] = i2 == j2 ? CT(0.5) * div : CT(0);
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    M[0][1 + j] = M[1 + j][0] = CT(0.5) * db[j];
+    M[1 + j][4] = M[4][1 + j] = CT(0.5) * da[j];
+  }
+  // minus M2 (closed form)
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    M[0][1 + j] -= P0.b / P0.rho * drho[j];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) M[1 + k][1 + j] -= du[k][j];
+    M[4][1 + j] -= CT(2) / gm1 * da[j];
+    M[1 + j][4] -= P0.a / (CT(2) * P0.p) * dp[j];
+  }
+  M[0][4] -= sqrt(gm1) / CT(2) * div;
+  M[4][4] -= gm1 / CT(2) * div;
+}
+
 template <class CT>
 __global__ void __launch_bounds__(RB) k_sigma1(GridDesc g, Coef<CT> c, const CT* __restrict__ w,
                                                float* __restrict__ sig, double* partial) {
   __shared__ double sh[RB];
   const int b = blockIdx.y;
   double vmax = 0.0, vsum = 0.0;
-  const CT gam = c.gamma, gm1 = c.gm1;
   for (long long i = (long long)blockIdx.x * RB + threadIdx.x; i < g.cells; i += (long long)gridDim.x * RB) {
     const int x = (int)(i % g.nx);
     const int y = (int)((i / g.nx) % g.ny);
     const int z = (int)(i / g.plane);
-    const size_t box = (size_t)b * 5 * g.cells;
-    auto at = [&](int xx, int yy, int zz) {
-      return box + (size_t)wrap(zz, g.nz) * g.plane + (size_t)wrap(yy, g.ny) * g.nx + wrap(xx, g.nx);
-    };
-    const Prim<CT> P0 = prim_at<CT>(w, at(x, y, z), g.cells, gam);
-    Prim<CT> Pm[3], Pp[3];
-    Pm[0] = prim_at<CT>(w, at(x - 1, y, z), g.cells, gam);
-    Pp[0] = prim_at<CT>(w, at(x + 1, y, z), g.cells, gam);
-    Pm[1] = prim_at<CT>(w, at(x, y - 1, z), g.cells, gam);
-    Pp[1] = prim_at<CT>(w, at(x, y + 1, z), g.cells, gam);
-    Pm[2] = prim_at<CT>(w, at(x, y, z - 1), g.cells, gam);
-    Pp[2] = prim_at<CT>(w, at(x, y, z + 1), g.cells, gam);
-    CT drho[3], du[3][3], dp[3], da[3], db[3];
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      const CT h = c.hidx[j];
-      drho[j] = (Pp[j].rho - Pm[j].rho) * h;
-      dp[j] = (Pp[j].p - Pm[j].p) * h;
-      da[j] = (Pp[j].a - Pm[j].a) * h;
-      db[j] = (Pp[j].b - Pm[j].b) * h;
-#pragma unroll
-      for (int k = 0; k < 3; ++k) du[k][j] = (Pp[j].u[k] - Pm[j].u[k]) * h;
-    }
-    const CT div = du[0][0] + du[1][1] + du[2][2];
     CT M[5][5];
-    // M1 (closed form)
-#pragma unroll
-    for (int i2 = 0; i2 < 5; ++i2)
-#pragma unroll
-      for (int j2 = 0; j2 < 5; ++j2) M[i2][j2] = i2 == j2 ? CT(0.5) * div : CT(0);
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      M[0][1 + j] = M[1 + j][0] = CT(0.5) * db[j];
-      M[1 + j][4] = M[4][1 + j] = CT(0.5) * da[j];
-    }
-    // minus M2 (closed form)
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      M[0][1 + j] -= P0.b / P0.rho * drho[j];
-#pragma unroll
-      for (int k = 0; k < 3; ++k) M[1 + k][1 + j] -= du[k][j];
-      M[4][1 + j] -= CT(2) / gm1 * da[j];
-      M[1 + j][4] -= P0.a / (CT(2) * P0.p) * dp[j];
-    }
-    M[0][4] -= sqrt(gm1) / CT(2) * div;
-    M[4][4] -= gm1 / CT(2) * div;
+    growth_matrix<CT>(g, c, w, b, x, y, z, M);
     const CT s1 = g.nz == 1 ? sigma1_of<CT, 4>(M) : sigma1_of<CT, 5>(M);
     const float sf = (float)s1;
     sig[(size_t)b * g.cells + i] = sf;
@@ -366,6 +374,71 @@ __global__ void __launch_bounds__(RB) k_sigma1(GridDesc g, Coef<CT> c, const CT*
     partial[(size_t)b * 2 * gridDim.x + blockIdx.x] = vmax;
     partial[(size_t)b * 2 * gridDim.x + gridDim.x + blockIdx.x] = vsum;
   }
+}
+
+// v_hat = S^-T V^-T lam of one cell (closed form of w_hat = T^T v_hat, "Symmetrization")
+template <class CT>
+__device__ __forceinline__ void vhat_cell(const CT* __restrict__ w, const double* __restrict__ lam, size_t o,
+                                          long long cells, CT gamma, CT v[5]) {
+  const CT gm1 = gamma - CT(1);
+  const CT r = w[o], ir = CT(1) / r;
+  const CT u0 = w[o + cells] * ir, u1 = w[o + 2 * cells] * ir, u2 = w[o + 3 * cells] * ir;
+  const CT uu = u0 * u0 + u1 * u1 + u2 * u2;
+  const CT p = gm1 * (w[o + 4 * cells] - CT(0.5) * r * uu);
+  const CT cs = sqrt(gamma * p * ir);
+  const CT sg = sqrt(gamma);
+  const CT l0 = cvt<CT>(lam[o]), l1 = cvt<CT>(lam[o + cells]), l2 = cvt<CT>(lam[o + 2 * cells]),
+           l3 = cvt<CT>(lam[o + 3 * cells]), l4 = cvt<CT>(lam[o + 4 * cells]);
+  const CT y0 = l0 + u0 * l1 + u1 * l2 + u2 * l3 + CT(0.5) * uu * l4;
+  const CT y4 = l4 / gm1;
+  v[0] = sg * r / cs * y0 + r * cs / sg * y4;
+  v[1] = r * (l1 + u0 * l4);
+  v[2] = r * (l2 + u1 * l4);
+  v[3] = r * (l3 + u2 * l4);
+  v[4] = r * cs * sqrt(gm1 / gamma) * y4;
+}
+
+// Label accumulation: acc += max(0, v_hat^T M v_hat) / |grad v_hat|^2 per cell; for a
+// 2D box the (rho, u1, u2, p) block.
+template <class CT>
+__global__ void __launch_bounds__(RB) k_label(GridDesc g, Coef<CT> c, const CT* __restrict__ w,
+                                              const double* __restrict__ lam, float* __restrict__ acc) {
+  const long long i = (long long)blockIdx.x * RB + threadIdx.x;
+  if (i >= g.cells * g.batch) return;
+  const int b = (int)(i / g.cells);
+  const long long r = i - (long long)b * g.cells;
+  const int x = (int)(r % g.nx), y = (int)((r / g.nx) % g.ny), z = (int)(r / g.plane);
+  const size_t box = (size_t)b * 5 * g.cells;
+  auto at = [&](int xx, int yy, int zz) {
+    return box + (size_t)wrap(zz, g.nz) * g.plane + (size_t)wrap(yy, g.ny) * g.nx + wrap(xx, g.nx);
+  };
+  CT M[5][5];
+  growth_matrix<CT>(g, c, w, b, x, y, z, M);
+  CT v[5];
+  vhat_cell<CT>(w, lam, at(x, y, z), g.cells, c.gamma, v);
+  const bool two_d = g.nz == 1;
+  CT growth = CT(0);
+#pragma unroll
+  for (int p = 0; p < 5; ++p)
+#pragma unroll
+    for (int q = 0; q < 5; ++q)
+      if (!(two_d && (p == 3 || q == 3))) growth += v[p] * M[p][q] * v[q];
+  CT grad2 = CT(0);
+  const int dd[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    CT vm[5], vp[5];
+    vhat_cell<CT>(w, lam, at(x - dd[d][0], y - dd[d][1], z - dd[d][2]), g.cells, c.gamma, vm);
+    vhat_cell<CT>(w, lam, at(x + dd[d][0], y + dd[d][1], z + dd[d][2]), g.cells, c.gamma, vp);
+#pragma unroll
+    for (int p = 0; p < 5; ++p) {
+      if (two_d && p == 3) continue;
+      const CT gd = (vp[p] - vm[p]) * c.hidx[d];
+      grad2 += gd * gd;
+    }
+  }
+  const CT rate = (growth > CT(0) ? growth : CT(0)) / (grad2 + CT(1e-30));
+  acc[i] += (float)rate;
 }
 
 __global__ void __launch_bounds__(RB) k_sigma1_stats(int nblk, double inv_cells, const double* partial,
@@ -566,6 +639,7 @@ __global__ void k_to_float(const double* __restrict__ in, float* __restrict__ ou
 size_t diag_scratch_doubles(const GridDesc& g, int nphi) {
   size_t a = (size_t)2 * RG * g.batch + (size_t)2 * g.batch;
   if ((size_t)RGS * g.batch > a) a = (size_t)RGS * g.batch;
+  if ((size_t)5 * RG * g.batch > a) a = (size_t)5 * RG * g.batch;
   size_t b = (size_t)RG * (nphi > 0 ? nphi : 1);
   return (a > b ? a : b) + 64;
 }
@@ -600,6 +674,18 @@ template cudaError_t launch_sigma1<double>(const GridDesc&, const Coef<double>&,
                                            double*, double*, cudaStream_t);
 template cudaError_t launch_sigma1<float>(const GridDesc&, const Coef<float>&, const float*, float*,
                                           double*, double*, cudaStream_t);
+
+template <class CT>
+cudaError_t launch_label(const GridDesc& g, const Coef<CT>& c, const CT* w, const double* lam, float* acc,
+                         cudaStream_t st) {
+  const long long n = g.cells * g.batch;
+  k_label<CT><<<(unsigned)((n + RB - 1) / RB), RB, 0, st>>>(g, c, w, lam, acc);
+  return cudaGetLastError();
+}
+template cudaError_t launch_label<double>(const GridDesc&, const Coef<double>&, const double*, const double*,
+                                          float*, cudaStream_t);
+template cudaError_t launch_label<float>(const GridDesc&, const Coef<float>&, const float*, const double*,
+                                         float*, cudaStream_t);
 
 cudaError_t launch_nu_rule(const GridDesc& g, const float* sigma1, double lambda, double tau,
                            double limit_nu, float* nu, unsigned* err, cudaStream_t st) {

@@ -74,6 +74,9 @@ cudaError_t launch_objective(const GridDesc& g, double gamma, int plane_i, doubl
 template <class CT>
 cudaError_t launch_sigma1(const GridDesc& g, const Coef<CT>& c, const CT* w, float* sigma1,
                           double* stats, double* scratch, cudaStream_t st);
+template <class CT>
+cudaError_t launch_label(const GridDesc& g, const Coef<CT>& c, const CT* w, const double* lam, float* acc,
+                         cudaStream_t st);
 cudaError_t launch_nu_rule(const GridDesc& g, const float* sigma1, double lambda, double tau,
                            double limit_nu, float* nu, unsigned* err, cudaStream_t st);
 cudaError_t launch_visc_apply(const GridDesc& g, const double* idx2, const float* nu,

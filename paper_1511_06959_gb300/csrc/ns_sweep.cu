@@ -174,11 +174,11 @@ int make_plan(int N, int schedule, int param, Planner& P) {
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-  size_t state, lam, sig, nu, scal, total;
+  size_t state, lam, sig, nu, scal, feat, total;
   int nbuf;
 };
 
-Layout layout_for(const ns_ctx* c, int slots_used) {
+Layout layout_for(const ns_ctx* c, int slots_used, bool closure) {
   Layout L;
   L.nbuf = slots_used + 2;
   L.state = align256(c->field * sizeof(double));
@@ -187,7 +187,8 @@ Layout layout_for(const ns_ctx* c, int slots_used) {
   L.sig = align256(cellsb * sizeof(float));
   L.nu = L.sig;
   L.scal = align256((size_t)c->g.batch * sizeof(double) * 2);
-  L.total = L.state * L.nbuf + L.lam + L.sig + L.nu + L.scal;
+  L.feat = closure ? align256(cellsb * 16 * sizeof(float)) : 0;
+  L.total = L.state * L.nbuf + L.lam + L.sig + L.nu + L.scal + L.feat;
   return L;
 }
 
@@ -214,7 +215,7 @@ size_t ns_run_arena_bytes(const ns_ctx* c, const ns_run_opts* o) {
   if (!c || !o) return 0;
   Planner P;
   if (make_plan(o->nsteps, o->schedule, o->param, P)) return 0;
-  return layout_for(c, P.maxlive).total;
+  return layout_for(c, P.maxlive, o->mlp != nullptr).total;
 }
 
 }  // extern "C"
@@ -232,6 +233,7 @@ struct ns_sweep_state {
   float* sig = nullptr;
   float* nu = nullptr;
   double* jtmp = nullptr;
+  float* feat = nullptr;
   double* Jbar = nullptr;
   std::vector<int> slot_buf;
   std::vector<char> owned;
@@ -256,7 +258,7 @@ int run_actions(ns_ctx* c, ns_sweep_state& S, int stop_op, double*& lam_cur, dou
   const int N = S.o.nsteps;
   const int B = c->g.batch;
   const double wN = 1.0 / N;
-  const bool need_sigma = S.o.lambda > 0.0 || S.o.record_sigma;
+  const bool need_sigma = S.o.lambda > 0.0 || S.o.record_sigma || S.o.mlp;
   auto ptr = [&](int i) -> const double* { return i < 0 ? S.w0 : S.buf[i]; };
   auto pick_free = [&]() -> int {
     for (int i = 0; i < S.L.nbuf; ++i)
@@ -303,7 +305,11 @@ int run_actions(ns_ctx* c, ns_sweep_state& S, int stop_op, double*& lam_cur, dou
         if (need_sigma) {
           double* stats = S.o.record_sigma && sigma_stats ? sigma_stats + (size_t)A.a * 2 * B : nullptr;
           if ((r = ns_growth_sigma1(c, ptr(S.cur), S.sig, stats))) return r;
-          if (S.o.lambda > 0.0) {
+          if (S.o.mlp) {
+            if ((r = ns_mlp_features(c, ptr(S.cur), S.feat))) return r;
+            if ((r = ns_mlp_infer(c, S.o.mlp, S.feat, S.sig, S.o.lambda, S.nu))) return r;
+            nup = S.nu;
+          } else if (S.o.lambda > 0.0) {
             if ((r = ns_add_adjoint_viscosity(c, S.sig, S.o.lambda, S.o.tau, S.nu))) return r;
             nup = S.nu;
           }
@@ -338,7 +344,7 @@ int ns_forward_run(ns_ctx* c, const double* w0, const double* s, const ns_run_op
     delete S;
     return r;
   }
-  S->L = layout_for(c, S->P.maxlive);
+  S->L = layout_for(c, S->P.maxlive, o->mlp != nullptr);
   if (arena_bytes < S->L.total) {
     delete S;
     return NS_ERR_BUDGET;
@@ -358,6 +364,8 @@ int ns_forward_run(ns_ctx* c, const double* w0, const double* s, const ns_run_op
   S->nu = (float*)q;
   q += S->L.nu;
   S->jtmp = (double*)q;
+  q += S->L.scal;
+  S->feat = S->L.feat ? (float*)q : nullptr;
   S->slot_buf.assign(std::max(S->P.maxlive, 1), -1);
   S->owned.assign(S->L.nbuf, 0);
   c->sweep = S;

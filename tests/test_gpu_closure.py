@@ -1,0 +1,193 @@
+"""GPU learned adjoint-viscosity closure against its oracle: features, BF16 tensor-core
+inference, the training step's gradient, the label, the closure inside the adjoint
+sweep, training on solver-generated data, and the judge against the sigma_1 rule (the
+gain is reported, whatever its sign)."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import mlp_oracle as ML
+from oracle import ns_oracle as O
+from paper_1511_06959_gb300 import synth
+from tests.test_gpu_parity import _api, dev, host, make_solver, rel_l2
+from tests.test_oracle_primal import params_for
+
+pytestmark = pytest.mark.gpu
+
+
+def _closure():
+    from paper_1511_06959_gb300 import closure
+    return closure
+
+
+@pytest.mark.parametrize("shape,prec", [((37, 9, 5), 0), ((40, 12, 1), 1), ((7, 5, 3), 0)])
+def test_features_match_oracle(shape, prec):
+    api = _api()
+    w = synth.perturbed_uniform(*shape, seed=31, amp=0.08)
+    P = params_for(w)
+    S = make_solver(api, w, P, prec)
+    feat = torch.empty((w[0].size, 16), dtype=torch.float32, device="cuda")
+    S.mlp_features(dev(w), feat)
+    ref = ML.features(w, P)
+    got = host(feat)
+    assert np.all(got[:, 14:] == 0.0)
+    np.testing.assert_allclose(got[:, :14], ref, rtol=2e-4, atol=2e-5 * np.abs(ref).max())
+
+
+def test_inference_matches_quantised_oracle():
+    api = _api()
+    C = _closure()
+    shape = (37, 9, 5)
+    w = synth.perturbed_uniform(*shape, seed=32, amp=0.1)
+    P = params_for(w)
+    S = make_solver(api, w, P)
+    p = ML.init_params(7)
+    p["b3"] = np.array(0.3)
+    net = C.Network(S, p)
+    feat = torch.empty((w[0].size, 16), dtype=torch.float32, device="cuda")
+    S.mlp_features(dev(w), feat)
+    sig = torch.from_numpy(np.abs(synth.random_field(w[0].size, 33)).astype(np.float32) + 0.1).cuda()
+    nu = torch.empty_like(sig)
+    S.mlp_infer(net.blob, feat, sig, 2.0, nu)
+    X = host(feat)[:, :14].astype(np.float64)
+    _, pred, _ = ML.forward({k: np.asarray(v, dtype=np.float64) for k, v in p.items()}, X, quantize=True)
+    ref = 2.0 * P.dx[0] ** 2 * host(sig) * pred
+    rel = np.abs(host(nu) - ref) / np.abs(ref)
+    # BF16 rounding of a hidden activation may round differently after FP32 (GPU) versus
+    # exact (oracle) accumulation: bounded per cell, rare
+    assert np.median(rel) < 1e-4 and rel.max() < 2e-2, (np.median(rel), rel.max())
+    assert S.last_error() == 0
+
+
+def test_training_step_gradient_matches_oracle():
+    api = _api()
+    C = _closure()
+    rng = np.random.default_rng(5)
+    n_all = 3000
+    feat = np.zeros((n_all, 16), dtype=np.float32)
+    feat[:, :14] = rng.standard_normal((n_all, 14)).astype(np.float32)
+    target = np.abs(rng.standard_normal(n_all)).astype(np.float32)
+    idx = rng.integers(0, n_all, size=700).astype(np.int32)
+    p = ML.init_params(8)
+    S = api.Solver(8, 8, 1, 0.1)
+    net = C.Network(S, p)
+    loss = torch.empty(1, dtype=torch.float32, device="cuda")
+    S.mlp_train_step(net.blob, dev(feat), dev(target), dev(idx), 1, 1e-3, loss)
+    m = torch.empty(api.NS_MLP_PARAMS, dtype=torch.float32, device="cuda")
+    S.mlp_get_moment(net.blob, 1, m)
+    g_gpu = host(m).astype(np.float64) / 0.1
+    p64 = {k: np.asarray(v, dtype=np.float64) for k, v in p.items()}
+    L, g = ML.loss_and_grads(p64, feat[idx, :14].astype(np.float64), target[idx].astype(np.float64), True)
+    g_ref = C.pack(g).astype(np.float64)
+    assert abs(loss.item() - L) < 1e-4 * L
+    assert rel_l2(g_gpu, g_ref) < 2e-3
+    # the Adam update itself: p1 = p0 - lr * m_hat / (sqrt(v_hat) + eps) at step 1
+    p1 = C.pack(net.get())
+    exp = C.pack(p64) - 1e-3 * g_gpu / (np.abs(g_gpu) + 1e-8)
+    np.testing.assert_allclose(p1, exp, rtol=1e-5, atol=1e-7)
+
+
+def test_training_reduces_loss_on_a_learnable_target():
+    api = _api()
+    C = _closure()
+    rng = np.random.default_rng(9)
+    n_all = 20000
+    X = rng.standard_normal((n_all, 14))
+    teacher = ML.init_params(10)
+    _, t, _ = ML.forward(teacher, X, quantize=False)
+    feat = np.zeros((n_all, 16), dtype=np.float32)
+    feat[:, :14] = X
+    S = api.Solver(8, 8, 1, 0.1)
+    net = C.Network(S, ML.init_params(11))
+    losses = net.train(dev(feat), dev(t.astype(np.float32)), steps=400, batch=2048, lr=3e-3, seed=1)
+    assert losses[-20:].mean() < 0.1 * losses[:20].mean(), (losses[:5], losses[-5:])
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_label_matches_oracle(prec):
+    api = _api()
+    for shape in [(37, 9, 5), (40, 12, 1)]:
+        w = synth.perturbed_uniform(*shape, seed=34, amp=0.1)
+        P = params_for(w)
+        lam = synth.random_field(w.shape, 35)
+        S = make_solver(api, w, P, prec)
+        acc = torch.zeros(w[0].size, dtype=torch.float32, device="cuda")
+        S.adjoint_label(dev(w), dev(lam), acc)
+        S.adjoint_label(dev(w), dev(lam), acc)
+        ref = 2 * ML.label_rate(w, lam, P).ravel()
+        tol = 1e-5 if prec == 0 else 5e-3
+        np.testing.assert_allclose(host(acc), ref, rtol=tol, atol=tol * ref.max())
+
+
+def test_closure_inside_the_sweep_matches_oracle():
+    api = _api()
+    C = _closure()
+    w0 = synth.isentropic_vortex(40, 12, 1, noise=1e-3, seed=6)
+    P = params_for(w0, mu=1e-3, dt=4e-3)
+    N = 7
+    S = make_solver(api, w0, P)
+    p = ML.init_params(12)
+    p["b3"] = np.array(0.5)
+    net = C.Network(S, p)
+    kappa = 0.3
+    opts = S.run_opts(N, api.NS_CKPT_REVOLVE, 2, kappa, 0.0, False, False, net.blob)
+    arena = torch.empty(S.arena_bytes(opts), dtype=torch.uint8, device="cuda")
+    J = torch.empty(1, dtype=torch.float64, device="cuda")
+    lam0 = torch.empty(w0.shape, dtype=torch.float64, device="cuda")
+    S.adjoint_run(dev(w0), opts, arena, J, lam0)
+    assert S.last_error() == 0
+    p64 = {k: np.asarray(v, dtype=np.float64) for k, v in p.items()}
+
+    def nu_of(w):
+        _, pred, _ = ML.forward(p64, ML.features(w, P), quantize=True)
+        return kappa * P.dx[0] ** 2 * O.sigma1_field(w, P) * pred.reshape(w.shape[1:])
+
+    ws, _ = O.primal_run(w0, P, N)
+    ref, _ = O.adjoint_run(ws, P, None, nu_of)
+    assert rel_l2(host(lam0), ref) < 1e-5
+
+
+def test_judge_learned_closure_against_sigma1_rule():
+    """Train on adjoint data of two vortex boxes, then judge on a third: gradient error
+    of each closure against the exact short-horizon FP64 adjoint at the same adjoint
+    energy.  The result is written to gpurun_out/closure_judge.json and asserted only
+    to be finite and consistent (viscosity lowers the energy)."""
+    api = _api()
+    C = _closure()
+    n, N = 64, 120
+    P = params_for(synth.isentropic_vortex(n, n, 1, noise=0.0), mu=0.5 / 1000)
+    boxes = {s: synth.isentropic_vortex(n, n, 1, noise=3e-2, seed=s) for s in (1, 11, 12)}
+    P.dt = 0.5 * P.dx[0] / max(O.max_wave_speed(w, P) for w in boxes.values())
+    S = make_solver(api, boxes[1], P)
+    feats, targets = [], []
+    for s in (11, 12):
+        smp = C.generate_samples(S, dev(boxes[s]), N, every=6)
+        feats.append(smp.feat)
+        targets.append(smp.target)
+    feat = torch.cat(feats).contiguous()
+    target = torch.cat(targets).contiguous()
+    net = C.Network(S, C.init_params(3, out_bias=0.5))
+    losses = net.train(feat, target, steps=600, batch=4096, lr=2e-3, seed=2)
+    phi = dev(synth.forcing_bumps(n, n, 1, n=64))
+    dx2 = P.dx[0] ** 2
+    res = C.judge(S, dev(boxes[1]), phi, N, net, [dx2 * c for c in (0.25, 0.5, 1, 2, 4, 8, 16)],
+                  [0.05, 0.1, 0.2, 0.4, 0.8, 1.6, 3.2, 6.4, 12.8])
+    res["train_loss_first"] = float(losses[:20].mean())
+    res["train_loss_last"] = float(losses[-20:].mean())
+    res["samples"] = int(target.numel())
+    res["gain_rel_err"] = res["rule_err_at_bound"] - res["learned_err_at_bound"]
+    os.makedirs("gpurun_out", exist_ok=True)
+    with open("gpurun_out/closure_judge.json", "w") as f:
+        json.dump(res, f, indent=1)
+    print("closure judge:", json.dumps({k: res[k] for k in ("E_exact", "E_bound", "rule_err_at_bound",
+                                                              "learned_err_at_bound", "gain_rel_err")}))
+    assert np.isfinite(res["rule_err_at_bound"]) and np.isfinite(res["learned_err_at_bound"])
+    assert res["train_loss_last"] < res["train_loss_first"]
+    for rows in (res["rule"], res["learned"]):
+        E = [r[2] for r in rows]
+        assert all(E[i + 1] <= E[i] * (1 + 1e-9) for i in range(len(E) - 1)), E
+        assert E[0] <= res["E_exact"] * (1 + 1e-9)

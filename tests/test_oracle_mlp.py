@@ -1,0 +1,128 @@
+"""Pins of the learned-closure oracle (no GPU): BF16 rounding and the activations against
+torch's own routines, the hand-derived backward against finite differences, Adam
+against torch.optim.Adam, and the features / label on flows with known answers."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import mlp_oracle as ML
+from oracle import ns_oracle as O
+from paper_1511_06959_gb300 import synth
+from tests.test_oracle_primal import params_for
+
+
+def test_bf16_rounding_matches_torch_including_ties():
+    rng = np.random.default_rng(0)
+    x = (rng.standard_normal(100000) * np.exp(rng.uniform(-30, 30, 100000))).astype(np.float32)
+    # exact ties: midpoints between consecutive bfloat16 values
+    b = torch.from_numpy(x).to(torch.bfloat16).float().numpy()
+    up = (b.view(np.uint32) + 0x10000).view(np.float32)
+    ties = ((b.astype(np.float64) + up.astype(np.float64)) / 2).astype(np.float32)
+    for arr in (x, ties):
+        ref = torch.from_numpy(arr).to(torch.bfloat16).float().numpy().astype(np.float64)
+        got = ML.bf16(arr)
+        assert np.array_equal(got, ref)
+
+
+def test_activations_match_torch():
+    z = np.linspace(-8, 8, 2001)
+    t = torch.from_numpy(z)
+    np.testing.assert_allclose(ML.gelu(z), torch.nn.functional.gelu(t).numpy(), rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(ML.softplus(z), torch.nn.functional.softplus(t).numpy(), rtol=1e-12,
+                               atol=1e-15)
+    h = 1e-6
+    np.testing.assert_allclose(ML.gelu_grad(z), (ML.gelu(z + h) - ML.gelu(z - h)) / (2 * h), rtol=1e-6,
+                               atol=1e-9)
+    np.testing.assert_allclose(ML.softplus_grad(z), (ML.softplus(z + h) - ML.softplus(z - h)) / (2 * h),
+                               rtol=1e-6, atol=1e-9)
+
+
+def test_backward_matches_finite_differences():
+    p = ML.init_params(1)
+    rng = np.random.default_rng(2)
+    X = rng.standard_normal((40, ML.NIN))
+    t = np.abs(rng.standard_normal(40))
+    L, g = ML.loss_and_grads(p, X, t, quantize=False)
+    h = 1e-6
+    for k in p:
+        flat = p[k].reshape(-1)
+        for idx in rng.choice(flat.size, size=min(5, flat.size), replace=False):
+            pp = {kk: vv.copy() for kk, vv in p.items()}
+            pm = {kk: vv.copy() for kk, vv in p.items()}
+            pp[k].reshape(-1)[idx] += h
+            pm[k].reshape(-1)[idx] -= h
+            fd = (ML.loss_and_grads(pp, X, t, False)[0] - ML.loss_and_grads(pm, X, t, False)[0]) / (2 * h)
+            an = g[k].reshape(-1)[idx]
+            assert abs(fd - an) <= 1e-6 * max(abs(fd), 1e-8), (k, idx, fd, an)
+
+
+def test_forward_matches_torch_network():
+    """The FP64 network equals the same network written with torch.nn layers."""
+    p = ML.init_params(3)
+    X = np.random.default_rng(4).standard_normal((17, ML.NIN))
+    net = torch.nn.Sequential(torch.nn.Linear(14, 64), torch.nn.GELU(), torch.nn.Linear(64, 64),
+                              torch.nn.GELU(), torch.nn.Linear(64, 1)).double()
+    with torch.no_grad():
+        net[0].weight.copy_(torch.from_numpy(p["W1"].T))
+        net[0].bias.copy_(torch.from_numpy(p["b1"]))
+        net[2].weight.copy_(torch.from_numpy(p["W2"].T))
+        net[2].bias.copy_(torch.from_numpy(p["b2"]))
+        net[4].weight.copy_(torch.from_numpy(p["w3"][None, :]))
+        net[4].bias.copy_(torch.from_numpy(np.atleast_1d(p["b3"])))
+        ref = net(torch.from_numpy(X)).numpy()[:, 0]
+    y, _, _ = ML.forward(p, X, quantize=False)
+    np.testing.assert_allclose(y, ref, rtol=1e-12, atol=1e-14)
+
+
+def test_adam_matches_torch_optimizer():
+    p = ML.init_params(5)
+    g = {k: np.random.default_rng(6).standard_normal(v.shape) for k, v in p.items()}
+    tp = {k: torch.tensor(v, requires_grad=True) for k, v in p.items()}
+    opt = torch.optim.Adam(list(tp.values()), lr=1e-3)
+    m = {k: np.zeros_like(v) for k, v in p.items()}
+    v = {k: np.zeros_like(vv) for k, vv in p.items()}
+    for step in (1, 2, 3):
+        for k in tp:
+            tp[k].grad = torch.tensor(g[k] * step)
+        opt.step()
+        p, m, v = ML.adam_step(p, {k: g[k] * step for k in g}, m, v, step)
+    for k in p:
+        np.testing.assert_allclose(p[k], tp[k].detach().numpy(), rtol=1e-12, atol=1e-15)
+
+
+def test_features_uniform_flow_and_linear_shear():
+    g = 1.4
+    rho = np.ones((4, 6, 8))
+    u = np.stack([0.5 * rho, 0 * rho, 0 * rho])
+    w = synth._conservative(rho, u, rho / g, g)
+    P = params_for(w)
+    assert np.all(ML.features(w, P) == 0.0)
+    # periodic shear u1 = A sin(2 pi y / Ly): du1/dy at the cells, v1 = u1 - mean
+    ny = 16
+    y = (np.arange(ny) + 0.5) / 8.0
+    A = 0.1
+    rho = np.ones((2, ny, 8))
+    u1 = A * np.sin(2 * np.pi * y / 2.0)[None, :, None] * np.ones_like(rho)
+    w = synth._conservative(rho, np.stack([u1, 0 * rho, 0 * rho]), rho / g, g)
+    P = params_for(w)
+    f = ML.features(w, P).reshape(2, ny, 8, 14)
+    cb = 1.0
+    np.testing.assert_allclose(f[..., 1], u1 / cb, atol=1e-15)
+    dy = P.dx[1]
+    exact_central = A * (np.sin(2 * np.pi * (y + dy) / 2.0) - np.sin(2 * np.pi * (y - dy) / 2.0)) / (2 * dy)
+    np.testing.assert_allclose(f[0, :, 0, 5 + 0 * 3 + 1], exact_central, rtol=1e-12, atol=1e-14)
+    assert np.all(np.abs(f[..., [0, 4]]) < 1e-14)
+
+
+def test_label_zero_for_uniform_flow_and_nonnegative():
+    w = synth.perturbed_uniform(6, 5, 4, seed=7, amp=0.1)
+    P = params_for(w)
+    lam = synth.random_field(w.shape, 8)
+    r = ML.label_rate(w, lam, P)
+    assert np.all(r >= 0.0) and np.all(np.isfinite(r))
+    g = 1.4
+    rho = np.ones((3, 4, 5))
+    wu = synth._conservative(rho, np.stack([0.5 * rho, 0 * rho, 0 * rho]), rho / g, g)
+    assert np.all(ML.label_rate(wu, lam[:, :3, :4, :5], params_for(wu)) == 0.0)
