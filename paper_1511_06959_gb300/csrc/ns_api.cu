@@ -71,16 +71,19 @@ static int ensure_tangent_buffers(ns_ctx* c) {
 }
 
 // RK4 with the increment sum D = dt (k1/6 + k2/3 + k3/3 + k4/6) in the stage type and
-// one FP64 add w^{n+1} = w^n + D at the last stage.
+// one FP64 add w^{n+1} = w^n + D at the last stage.  keep (may be null): buffers that
+// receive the stage states W2, W3, W4 of this step; wo_mirror (may be null): receives
+// w^{n+1} rounded to the stage type.
 template <class CT>
 static int primal_step_t(ns_ctx* c, const Coef<CT>& cf, const CT* W1, const double* w, const double* s,
-                         double* wo) {
+                         double* wo, CT* wo_mirror = nullptr, CT* const* keep = nullptr) {
   const double dt = c->p.dt;
-  CT* Wa = buf<CT>(c, W2);
-  CT* Wb = buf<CT>(c, W3);
+  CT* Wa = keep ? keep[0] : buf<CT>(c, W2);
+  CT* Wb = keep ? keep[1] : buf<CT>(c, W3);
+  CT* Wc = keep ? keep[2] : Wa;
   CT* D = buf<CT>(c, GS);
-  const CT* in[4] = {W1, Wa, Wb, Wa};
-  CT* outs[4] = {Wa, Wb, Wa, nullptr};
+  const CT* in[4] = {W1, Wa, Wb, Wc};
+  CT* outs[4] = {Wa, Wb, Wc, nullptr};
   const double cacc[4] = {dt / 6.0, dt / 3.0, dt / 3.0, dt / 6.0};
   const double cout[4] = {0.5 * dt, 0.5 * dt, dt, 0.0};
   for (int i = 0; i < 4; ++i) {
@@ -88,7 +91,7 @@ static int primal_step_t(ns_ctx* c, const Coef<CT>& cf, const CT* W1, const doub
     a.W = in[i]; a.base = W1; a.src = s;
     a.dacc = D; a.dacc_init = i == 0; a.cacc = cacc[i];
     a.Wout = outs[i]; a.cout = cout[i];
-    if (i == 3) { a.wbase = w; a.wout = wo; }
+    if (i == 3) { a.wbase = w; a.wout = wo; a.wout_mirror = wo_mirror; }
     if (ns::launch_rhs_stage<CT, CT, CT>(c->g, cf, a, c->st) != cudaSuccess) return NS_ERR_CUDA;
   }
   return NS_OK;
@@ -117,19 +120,31 @@ static cudaError_t adj_launch(ns_ctx* c, const Coef<CT>& cf, const ns::AdjArgs<T
 // stage products summed in the stage type and lam^n = lam^{n+1} + G formed in FP64.
 template <class CT>
 static int adjoint_step_t(ns_ctx* c, const Coef<CT>& cf, const CT* W1, const CT* lamf, const double* s,
-                          const double* lam, const float* nu, double* lo, double* sbar) {
+                          const double* lam, const float* nu, double* lo, double* sbar,
+                          const CT* const* kept = nullptr) {
   const double dt = c->p.dt;
-  CT* Wst[3] = {buf<CT>(c, W2), buf<CT>(c, W3), buf<CT>(c, W4)};
+  const CT* Wst[3];
   CT* Aa = buf<CT>(c, AA);
   CT* Ab = buf<CT>(c, AB);
   CT* G = buf<CT>(c, GS);
   CT* S = buf<CT>(c, SB);
-  const CT* rin[3] = {W1, Wst[0], Wst[1]};
-  const double rc[3] = {0.5 * dt, 0.5 * dt, dt};
-  for (int i = 0; i < 3; ++i) {
-    ns::StageArgs<CT, CT> a{};
-    a.W = rin[i]; a.base = W1; a.src = s; a.Wout = Wst[i]; a.cout = rc[i];
-    if (ns::launch_rhs_stage<CT, CT, CT>(c->g, cf, a, c->st) != cudaSuccess) return NS_ERR_CUDA;
+  if (kept) {
+    // stage states kept by the replay of this step
+    Wst[0] = kept[0];
+    Wst[1] = kept[1];
+    Wst[2] = kept[2];
+  } else {
+    CT* Wr[3] = {buf<CT>(c, W2), buf<CT>(c, W3), buf<CT>(c, W4)};
+    const CT* rin[3] = {W1, Wr[0], Wr[1]};
+    const double rc[3] = {0.5 * dt, 0.5 * dt, dt};
+    for (int i = 0; i < 3; ++i) {
+      ns::StageArgs<CT, CT> a{};
+      a.W = rin[i]; a.base = W1; a.src = s; a.Wout = Wr[i]; a.cout = rc[i];
+      if (ns::launch_rhs_stage<CT, CT, CT>(c->g, cf, a, c->st) != cudaSuccess) return NS_ERR_CUDA;
+    }
+    Wst[0] = Wr[0];
+    Wst[1] = Wr[1];
+    Wst[2] = Wr[2];
   }
   const CT* Wi[4] = {Wst[2], Wst[1], Wst[0], W1};
   const CT* Ain[4] = {lamf, Aa, Ab, Aa};
@@ -512,3 +527,45 @@ extern "C" int ns_profile_read(ns_ctx* c, double* ms, long long* launches) {
   c->prof_used = 0;
   return NS_OK;
 }
+
+// ---------------------------------------------------------------------------------
+// internal step variants used by the sweep executor (not part of the C ABI): optional
+// float mirrors of the input/output states and kept stage states (stage-type buffers)
+// ---------------------------------------------------------------------------------
+int ns_i_primal(ns_ctx* c, const double* w, const void* w_mirror, const double* s, double* wo, void* wo_mirror,
+                void* const* keep3) {
+  if (mixed(c)) {
+    const float* W1 = (const float*)w_mirror;
+    if (!W1) {
+      float* wf = buf<float>(c, WF);
+      if (ns::launch_to_float(w, wf, c->field, c->st) != cudaSuccess) return NS_ERR_CUDA;
+      W1 = wf;
+    }
+    return primal_step_t<float>(c, c->cf, W1, w, s, wo, (float*)wo_mirror, (float* const*)keep3);
+  }
+  return primal_step_t<double>(c, c->cd, w, w, s, wo, nullptr, (double* const*)keep3);
+}
+
+int ns_i_adjoint(ns_ctx* c, const double* w, const void* w_mirror, const void* const* kept3, const double* s,
+                 const double* lam, const float* nu, double* lo, double* sbar) {
+  if (mixed(c)) {
+    const float* W1 = (const float*)w_mirror;
+    if (!W1) {
+      float* wf = buf<float>(c, WF);
+      if (ns::launch_to_float(w, wf, c->field, c->st) != cudaSuccess) return NS_ERR_CUDA;
+      W1 = wf;
+    }
+    float* lf = buf<float>(c, LF);
+    if (ns::launch_to_float(lam, lf, c->field, c->st) != cudaSuccess) return NS_ERR_CUDA;
+    return adjoint_step_t<float>(c, c->cf, W1, lf, s, lam, nu, lo, sbar, (const float* const*)kept3);
+  }
+  return adjoint_step_t<double>(c, c->cd, w, lam, s, lam, nu, lo, sbar, (const double* const*)kept3);
+}
+
+int ns_i_sigma1(ns_ctx* c, const double* w, const void* w_mirror, float* sigma1, double* stats) {
+  if (mixed(c) && w_mirror)
+    return cuerr(ns::launch_sigma1<float>(c->g, c->cf, (const float*)w_mirror, sigma1, stats, c->scratch, c->st));
+  return ns_growth_sigma1(c, w, sigma1, stats);
+}
+
+size_t ns_i_stage_bytes(const ns_ctx* c) { return c->field * (mixed(c) ? sizeof(float) : sizeof(double)); }

@@ -39,3 +39,12 @@ struct ns_ctx {
 
 // releases the sweep executor state of a context (defined with the executor)
 void ns_sweep_release(ns_ctx* c);
+
+// step variants for the executor (ns_api.cu): optional float mirrors (mixed mode) of
+// the input and output states and kept stage states W2..W4 (stage-type buffers)
+int ns_i_primal(ns_ctx* c, const double* w, const void* w_mirror, const double* s, double* wo, void* wo_mirror,
+                void* const* keep3);
+int ns_i_adjoint(ns_ctx* c, const double* w, const void* w_mirror, const void* const* kept3, const double* s,
+                 const double* lam, const float* nu, double* lo, double* sbar);
+int ns_i_sigma1(ns_ctx* c, const double* w, const void* w_mirror, float* sigma1, double* stats);
+size_t ns_i_stage_bytes(const ns_ctx* c);

@@ -12,6 +12,7 @@ namespace ns {
 //   dacc = (dacc_init ? 0 : dacc) + cacc R        increment sum, stage type
 //   Wout = base + cout R                           next stage state, stage type
 //   wout = (wbase or 0) + widen(dacc + cacc R)     final state, FP64 (when wout != 0)
+//   wout_mirror = wout rounded to the stage type    (when wout_mirror != 0)
 template <class TIN, class TST>
 struct StageArgs {
   const TIN* W;
@@ -31,6 +32,7 @@ struct StageArgs {
   const double* wbased;
   double* wout;
   double* woutd;
+  TST* wout_mirror;
 };
 
 // Fused stage of the discrete adjoint (see ns_adj.cu), a = ca*A:

@@ -295,7 +295,9 @@ __global__ void __launch_bounds__(NT) k_rhs_stage(GridDesc g, Coef<CT> c, StageA
           const CT inc = CT(a.cacc) * Rv;
           const CT dv = (a.dacc && !a.dacc_init ? a.dacc[o] : CT(0)) + inc;
           if (a.wout) {
-            a.wout[o] = (a.wbase ? a.wbase[o] : 0.0) + widen(dv);
+            const double wv = (a.wbase ? a.wbase[o] : 0.0) + widen(dv);
+            a.wout[o] = wv;
+            if (a.wout_mirror) a.wout_mirror[o] = cvt<TST>(wv);
           } else if (a.dacc) {
             a.dacc[o] = dv;
           }

@@ -11,6 +11,7 @@
 
 #include "../../include/ns_adjoint.h"
 #include "ns_ctx.h"
+#include "ns_kernels.h"
 
 namespace {
 
@@ -173,12 +174,17 @@ int make_plan(int N, int schedule, int param, Planner& P) {
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// Arena regions.  mir: two stage-type fields holding float mirrors of consecutive
+// states of an ADVANCE run (mixed precision).  keep: for stride schedules, one entry of
+// four stage-type fields per step of the segment being reversed (the mirror of w^n and
+// the stage states W2..W4 computed when the segment was replayed), so that the adjoint
+// of a replayed step neither recomputes its stages nor converts its state.
 struct Layout {
-  size_t state, lam, sig, nu, scal, feat, total;
-  int nbuf;
+  size_t state, lam, sig, nu, scal, feat, stage, mir, keep, total;
+  int nbuf, nkeep;
 };
 
-Layout layout_for(const ns_ctx* c, int slots_used, bool closure) {
+Layout layout_for(const ns_ctx* c, int slots_used, bool closure, int schedule, int param) {
   Layout L;
   L.nbuf = slots_used + 2;
   L.state = align256(c->field * sizeof(double));
@@ -188,7 +194,11 @@ Layout layout_for(const ns_ctx* c, int slots_used, bool closure) {
   L.nu = L.sig;
   L.scal = align256((size_t)c->g.batch * sizeof(double) * 2);
   L.feat = closure ? align256(cellsb * 16 * sizeof(float)) : 0;
-  L.total = L.state * L.nbuf + L.lam + L.sig + L.nu + L.scal + L.feat;
+  L.stage = align256(ns_i_stage_bytes(c));
+  L.mir = 2 * L.stage;
+  L.nkeep = schedule == NS_CKPT_STRIDE ? param : 0;
+  L.keep = (size_t)L.nkeep * 4 * L.stage;
+  L.total = L.state * L.nbuf + L.lam + L.sig + L.nu + L.scal + L.feat + L.mir + L.keep;
   return L;
 }
 
@@ -215,7 +225,7 @@ size_t ns_run_arena_bytes(const ns_ctx* c, const ns_run_opts* o) {
   if (!c || !o) return 0;
   Planner P;
   if (make_plan(o->nsteps, o->schedule, o->param, P)) return 0;
-  return layout_for(c, P.maxlive, o->mlp != nullptr).total;
+  return layout_for(c, P.maxlive, o->mlp != nullptr, o->schedule, o->param).total;
 }
 
 }  // extern "C"
@@ -241,6 +251,14 @@ struct ns_sweep_state {
   int touched = 0;
   size_t pos = 0;     // next action
   bool forward_done = false;
+  bool in_backward = false;
+  bool mixed = false;
+  char* mir[2] = {nullptr, nullptr};
+  void* cur_mirror = nullptr;        // float mirror of the current state, if any
+  std::vector<char*> keep;           // [nkeep][4]
+  std::vector<char> has_mirror, has_stages;
+  int seg = -1;                      // first step of the segment the keep entries belong to
+  bool kept_valid(int n) const { return L.nkeep > 0 && seg >= 0 && (n / L.nkeep) * L.nkeep == seg; }
 };
 
 void ns_sweep_release(ns_ctx* c) {
@@ -274,12 +292,46 @@ int run_actions(ns_ctx* c, ns_sweep_state& S, int stop_op, double*& lam_cur, dou
         for (int n = A.a; n < A.b; ++n) {
           const int out = pick_free();
           if (out < 0) return NS_ERR_BUDGET;
-          if ((r = ns_primal_step(c, ptr(S.cur), S.s, S.buf[out]))) return r;
+          const int K = S.L.nkeep;
+          const bool keep = S.in_backward && K > 0;
+          void* in_m = S.mixed ? S.cur_mirror : nullptr;
+          void* out_m = nullptr;
+          void* keep3[3] = {nullptr, nullptr, nullptr};
+          if (keep) {
+            const int e = n % K;
+            if (e == 0 || !S.kept_valid(n)) {
+              std::fill(S.has_mirror.begin(), S.has_mirror.end(), 0);
+              std::fill(S.has_stages.begin(), S.has_stages.end(), 0);
+              S.seg = n - e;
+            }
+            char** E = &S.keep[(size_t)e * 4];
+            if (S.mixed) {
+              if (e == 0 || in_m != E[0]) {
+                if (ns::launch_to_float(ptr(S.cur), (float*)E[0], c->field, c->st) != cudaSuccess) return NS_ERR_CUDA;
+              }
+              in_m = E[0];
+              S.has_mirror[e] = 1;
+              const int e1 = (n + 1) % K;
+              if (e1 != 0) {
+                out_m = S.keep[(size_t)e1 * 4];
+                S.has_mirror[e1] = 1;
+              }
+            }
+            keep3[0] = E[1];
+            keep3[1] = E[2];
+            keep3[2] = E[3];
+            S.has_stages[e] = 1;
+          } else if (S.mixed) {
+            out_m = S.mir[(n + 1) & 1];
+            if (in_m == out_m) in_m = nullptr;
+          }
+          if ((r = ns_i_primal(c, ptr(S.cur), in_m, S.s, S.buf[out], out_m, keep ? keep3 : nullptr))) return r;
           if (n + 1 > S.touched) {
             if ((r = ns_objective(c, S.buf[out], wN, S.Jbar, nullptr))) return r;
             S.touched = n + 1;
           }
           S.cur = out;
+          S.cur_mirror = out_m;
         }
         break;
       case NS_OP_STORE:
@@ -287,9 +339,14 @@ int run_actions(ns_ctx* c, ns_sweep_state& S, int stop_op, double*& lam_cur, dou
         S.slot_buf[A.b] = S.cur;
         S.owned[S.cur] = 1;
         break;
-      case NS_OP_LOAD:
+      case NS_OP_LOAD: {
         S.cur = A.b < 0 ? -1 : S.slot_buf[A.b];
+        const int K = S.L.nkeep;
+        S.cur_mirror = (S.mixed && S.in_backward && S.kept_valid(A.a) && S.has_mirror[A.a % K])
+                           ? S.keep[(size_t)(A.a % K) * 4]
+                           : nullptr;
         break;
+      }
       case NS_OP_FREE:
         S.owned[S.slot_buf[A.b]] = 0;
         S.slot_buf[A.b] = -1;
@@ -301,10 +358,22 @@ int run_actions(ns_ctx* c, ns_sweep_state& S, int stop_op, double*& lam_cur, dou
           return r;
         break;
       case NS_OP_ADJOINT: {
+        const int K = S.L.nkeep;
+        const void* mirror = S.mixed ? S.cur_mirror : nullptr;
+        const void* kept3[3] = {nullptr, nullptr, nullptr};
+        bool kept = false;
+        if (S.kept_valid(A.a) && S.has_stages[A.a % K]) {
+          char** E = &S.keep[(size_t)(A.a % K) * 4];
+          kept3[0] = E[1];
+          kept3[1] = E[2];
+          kept3[2] = E[3];
+          kept = true;
+          if (S.mixed) mirror = E[0];
+        }
         const float* nup = nullptr;
         if (need_sigma) {
           double* stats = S.o.record_sigma && sigma_stats ? sigma_stats + (size_t)A.a * 2 * B : nullptr;
-          if ((r = ns_growth_sigma1(c, ptr(S.cur), S.sig, stats))) return r;
+          if ((r = ns_i_sigma1(c, ptr(S.cur), mirror, S.sig, stats))) return r;
           if (S.o.mlp) {
             if ((r = ns_mlp_features(c, ptr(S.cur), S.feat))) return r;
             if ((r = ns_mlp_infer(c, S.o.mlp, S.feat, S.sig, S.o.lambda, S.nu))) return r;
@@ -314,7 +383,8 @@ int run_actions(ns_ctx* c, ns_sweep_state& S, int stop_op, double*& lam_cur, dou
             nup = S.nu;
           }
         }
-        if ((r = ns_adjoint_step(c, ptr(S.cur), S.s, lam_cur, nup, lam_nxt, sbar))) return r;
+        if ((r = ns_i_adjoint(c, ptr(S.cur), mirror, kept ? kept3 : nullptr, S.s, lam_cur, nup, lam_nxt, sbar)))
+          return r;
         std::swap(lam_cur, lam_nxt);
         if (A.a >= 1 && (r = ns_objective(c, ptr(S.cur), wN, S.jtmp, lam_cur))) return r;
         if (S.o.record_energy && energy &&
@@ -344,7 +414,7 @@ int ns_forward_run(ns_ctx* c, const double* w0, const double* s, const ns_run_op
     delete S;
     return r;
   }
-  S->L = layout_for(c, S->P.maxlive, o->mlp != nullptr);
+  S->L = layout_for(c, S->P.maxlive, o->mlp != nullptr, o->schedule, o->param);
   if (arena_bytes < S->L.total) {
     delete S;
     return NS_ERR_BUDGET;
@@ -366,6 +436,15 @@ int ns_forward_run(ns_ctx* c, const double* w0, const double* s, const ns_run_op
   S->jtmp = (double*)q;
   q += S->L.scal;
   S->feat = S->L.feat ? (float*)q : nullptr;
+  q += S->L.feat;
+  S->mir[0] = q;
+  S->mir[1] = q + S->L.stage;
+  q += S->L.mir;
+  S->keep.resize((size_t)S->L.nkeep * 4);
+  for (size_t i = 0; i < S->keep.size(); ++i) S->keep[i] = q + i * S->L.stage;
+  S->has_mirror.assign(S->L.nkeep, 0);
+  S->has_stages.assign(S->L.nkeep, 0);
+  S->mixed = c->p.precision == NS_MIXED;
   S->slot_buf.assign(std::max(S->P.maxlive, 1), -1);
   S->owned.assign(S->L.nbuf, 0);
   c->sweep = S;
@@ -390,6 +469,7 @@ int ns_backward_run(ns_ctx* c, double* lam0, double* sbar, double* energy, doubl
   if (cudaMemsetAsync(lam_cur, 0, fbytes, c->st) != cudaSuccess) return NS_ERR_CUDA;
   if (sbar && cudaMemsetAsync(sbar, 0, fbytes, c->st) != cudaSuccess) return NS_ERR_CUDA;
   S.forward_done = false;   // a plan is reversed once
+  S.in_backward = true;
   int r = run_actions(c, S, 0, lam_cur, lam_nxt, sbar, energy, sigma_stats);
   if (r) return r;
   if (lam_cur != lam0 &&
