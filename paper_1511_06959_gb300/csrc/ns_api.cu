@@ -230,6 +230,8 @@ int ns_create(const ns_params* p, void* stream, ns_ctx** out) {
   if (e == cudaSuccess) e = cudaMalloc(&c->scratch, c->scratch_n * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&c->err, sizeof(unsigned));
   if (e == cudaSuccess) e = cudaMalloc(&c->qbar, sizeof(double) * 5 * p->batch);
+  if (e == cudaSuccess) e = cudaMalloc(&c->ticket, sizeof(unsigned) * p->batch);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->ticket, 0, sizeof(unsigned) * p->batch, c->st);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->err, 0, sizeof(unsigned), c->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
   if (e != cudaSuccess) {
@@ -250,6 +252,7 @@ void ns_destroy(ns_ctx* c) {
   if (c->scratch) cudaFree(c->scratch);
   if (c->err) cudaFree(c->err);
   if (c->qbar) cudaFree(c->qbar);
+  if (c->ticket) cudaFree(c->ticket);
   if (c->train_scratch) cudaFree(c->train_scratch);
   for (cudaEvent_t ev : c->events) cudaEventDestroy(ev);
   ns_sweep_release(c);
@@ -362,8 +365,8 @@ int ns_rhs_transpose(ns_ctx* c, const double* w, const double* a_, const float* 
 int ns_objective(ns_ctx* c, const double* w, double weight, double* J_acc, double* lam) {
   if (!c || !w || !J_acc || lam == w) return NS_ERR_ARG;
   const int i0 = c->p.plane_i;
-  return cuerr(ns::launch_objective(c->g, c->p.gamma, i0, c->p.pt_in, w, weight, J_acc, lam, c->err,
-                                    c->scratch, c->st));
+  return cuerr(ns::launch_objective_fast(c->g, c->p.gamma, i0, c->p.pt_in, w, weight, J_acc, lam, c->err,
+                                         c->scratch, c->ticket, c->st));
 }
 
 int ns_growth_sigma1(ns_ctx* c, const double* w, float* sigma1, double* stats) {

@@ -33,6 +33,7 @@ struct ns_ctx {
   std::vector<cudaEvent_t> events;
   ns_sweep_state* sweep = nullptr;   // executor state between ns_forward_run and ns_backward_run
   double* qbar = nullptr;            // box-mean primitive states [batch][5] (closure features)
+  unsigned* ticket = nullptr;        // per-box counters of the single-launch objective
   float* train_scratch = nullptr;    // closure training partials, allocated on first use
   size_t train_scratch_n = 0;
 };

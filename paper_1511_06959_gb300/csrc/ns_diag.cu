@@ -150,6 +150,94 @@ __global__ void __launch_bounds__(OB) k_obj_grad(GridDesc g, double gamma, int i
   }
 }
 
+// Objective in two launches.  k_obj_sum: every CTA sums its faces' value terms and,
+// when the gradient is asked for, stores for each face the N/D-independent part a_v
+// of dJ/dw_f = sc (a_v - [v = 0] N/D), sc = weight / (2 D pt_in) (all FP64: the terms
+// p_t,in - p_t and a_0 - N/D cancel).  The last CTA to finish (ticket after a memory
+// fence) reduces the partials in a fixed order, forms J and stores (N/D, sc);
+// k_obj_scatter then adds the gradient to the two plane columns.
+constexpr int OMB = 64;
+
+__global__ void __launch_bounds__(OMB) k_obj_sum(GridDesc g, double gamma, int i0, double pt_in,
+                                                 const double* __restrict__ w, double weight, double* J_acc,
+                                                 bool want_grad, unsigned* err, double* partial,
+                                                 double* aface, double* ndsc, unsigned* ticket) {
+  __shared__ double sh[OMB];
+  __shared__ bool last;
+  const int b = blockIdx.y;
+  const int nf = g.ny * g.nz;
+  const int iL = wrap(i0 - 1, g.nx), iR = wrap(i0, g.nx);
+  const size_t box = (size_t)b * 5 * g.cells;
+  const double gm1 = gamma - 1.0, ex = gamma / gm1;
+  double N = 0.0, D = 0.0;
+  for (int f = blockIdx.x * OMB + threadIdx.x; f < nf; f += gridDim.x * OMB) {
+    const FaceState F = face_state(w, box, g.cells, (size_t)f * g.nx, iL, iR, gm1);
+    const double r = F.r, p = F.p, uu = F.uu;
+    const double B = 1.0 + 0.5 * gm1 * r * uu / (gamma * p);
+    const double pt = p * pt_factor(B, ex);
+    N += r * (pt_in - pt);
+    D += r;
+    if (want_grad) {
+      const double ir = 1.0 / r;
+      const double dr = pt * uu / (2.0 * p * B);
+      const double dp = pt / p * (1.0 - r * uu / (2.0 * p * B));
+      double du[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) du[k] = pt * r * F.u[k] / (p * B);
+      double* A = aface + ((size_t)b * nf + f) * 5;
+      A[0] = (pt_in - pt) - r * (dr - (F.u[0] * du[0] + F.u[1] * du[1] + F.u[2] * du[2]) * ir + 0.5 * gm1 * uu * dp);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) A[1 + k] = -r * (du[k] * ir - gm1 * F.u[k] * dp);
+      A[4] = -r * gm1 * dp;
+    }
+  }
+  N = block_reduce(N, sh, AddOp());
+  D = block_reduce(D, sh, AddOp());
+  if (threadIdx.x == 0) {
+    partial[((size_t)b * 2 + 0) * gridDim.x + blockIdx.x] = N;
+    partial[((size_t)b * 2 + 1) * gridDim.x + blockIdx.x] = D;
+    __threadfence();
+    last = atomicAdd(&ticket[b], 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  N = 0.0;
+  D = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += OMB) {
+    N += partial[((size_t)b * 2 + 0) * gridDim.x + i];
+    D += partial[((size_t)b * 2 + 1) * gridDim.x + i];
+  }
+  N = block_reduce(N, sh, AddOp());
+  D = block_reduce(D, sh, AddOp());
+  if (threadIdx.x == 0) {
+    const double J = N / (D * pt_in);
+    if (!isfinite(J)) atomicOr(err, ERRBIT_NONFINITE);
+    J_acc[b] += weight * J;
+    ndsc[2 * b] = N / D;
+    ndsc[2 * b + 1] = 0.5 * weight / (D * pt_in);
+    ticket[b] = 0u;
+  }
+}
+
+__global__ void k_obj_scatter(GridDesc g, int i0, const double* __restrict__ aface, const double* __restrict__ ndsc,
+                              double* __restrict__ lam) {
+  const int nf = g.ny * g.nz;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)nf * g.batch) return;
+  const int b = (int)(t / nf), f = (int)(t - (long long)b * nf);
+  const int iL = wrap(i0 - 1, g.nx), iR = wrap(i0, g.nx);
+  const size_t box = (size_t)b * 5 * g.cells, row = (size_t)f * g.nx;
+  const double NoD = ndsc[2 * b], sc = ndsc[2 * b + 1];
+  const double* A = aface + ((size_t)b * nf + f) * 5;
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    const double gd = sc * (A[v] - (v == 0 ? NoD : 0.0));
+    lam[box + v * g.cells + row + iL] += gd;
+    lam[box + v * g.cells + row + iR] += gd;
+  }
+}
+
 // ---------------------------------------------------------------------------------
 // growth matrix M = M1 - M2 and sigma_1 ("Energy analysis")
 // ---------------------------------------------------------------------------------
@@ -158,9 +246,10 @@ struct Prim {
   T rho, u[3], p, a, b;
 };
 
+// fb = 1/sqrt(gamma), fa = sqrt((gamma-1)/gamma): b = fb c, a = fa c
 template <class T>
 __device__ __forceinline__ Prim<T> prim_at(const T* __restrict__ w, size_t o, long long cells,
-                                           T gamma) {
+                                           T gamma, T fb, T fa) {
   Prim<T> P;
   P.rho = w[o];
   const T ir = T(1) / P.rho;
@@ -169,8 +258,8 @@ __device__ __forceinline__ Prim<T> prim_at(const T* __restrict__ w, size_t o, lo
   P.u[2] = w[o + 3 * cells] * ir;
   P.p = (gamma - T(1)) * (w[o + 4 * cells] - T(0.5) * P.rho * (P.u[0] * P.u[0] + P.u[1] * P.u[1] + P.u[2] * P.u[2]));
   const T cs = sqrt(gamma * P.p * ir);
-  P.b = cs / sqrt(gamma);
-  P.a = sqrt((gamma - T(1)) / gamma) * cs;
+  P.b = fb * cs;
+  P.a = fa * cs;
   return P;
 }
 
@@ -307,14 +396,15 @@ __device__ __forceinline__ void growth_matrix(const GridDesc& g, const Coef<CT>&
   auto at = [&](int xx, int yy, int zz) {
     return box + (size_t)wrap(zz, g.nz) * g.plane + (size_t)wrap(yy, g.ny) * g.nx + wrap(xx, g.nx);
   };
-  const Prim<CT> P0 = prim_at<CT>(w, at(x, y, z), g.cells, gam);
+  const CT fb = CT(1) / sqrt(gam), fa = sqrt(gm1 / gam);
+  const Prim<CT> P0 = prim_at<CT>(w, at(x, y, z), g.cells, gam, fb, fa);
   Prim<CT> Pm[3], Pp[3];
-  Pm[0] = prim_at<CT>(w, at(x - 1, y, z), g.cells, gam);
-  Pp[0] = prim_at<CT>(w, at(x + 1, y, z), g.cells, gam);
-  Pm[1] = prim_at<CT>(w, at(x, y - 1, z), g.cells, gam);
-  Pp[1] = prim_at<CT>(w, at(x, y + 1, z), g.cells, gam);
-  Pm[2] = prim_at<CT>(w, at(x, y, z - 1), g.cells, gam);
-  Pp[2] = prim_at<CT>(w, at(x, y, z + 1), g.cells, gam);
+  Pm[0] = prim_at<CT>(w, at(x - 1, y, z), g.cells, gam, fb, fa);
+  Pp[0] = prim_at<CT>(w, at(x + 1, y, z), g.cells, gam, fb, fa);
+  Pm[1] = prim_at<CT>(w, at(x, y - 1, z), g.cells, gam, fb, fa);
+  Pp[1] = prim_at<CT>(w, at(x, y + 1, z), g.cells, gam, fb, fa);
+  Pm[2] = prim_at<CT>(w, at(x, y, z - 1), g.cells, gam, fb, fa);
+  Pp[2] = prim_at<CT>(w, at(x, y, z + 1), g.cells, gam, fb, fa);
   CT drho[3], du[3][3], dp[3], da[3], db[3];
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
@@ -640,6 +730,10 @@ size_t diag_scratch_doubles(const GridDesc& g, int nphi) {
   size_t a = (size_t)2 * RG * g.batch + (size_t)2 * g.batch;
   if ((size_t)RGS * g.batch > a) a = (size_t)RGS * g.batch;
   if ((size_t)5 * RG * g.batch > a) a = (size_t)5 * RG * g.batch;
+  if ((size_t)2 * RGS * g.batch > a) a = (size_t)2 * RGS * g.batch;
+  // two-launch objective: partials, (N/D, sc) per box and 5 doubles per plane face
+  const size_t ob = (size_t)2 * RG * g.batch + 2 * (size_t)g.batch + (size_t)g.ny * g.nz * g.batch * 5;
+  if (ob > a) a = ob;
   size_t b = (size_t)RG * (nphi > 0 ? nphi : 1);
   return (a > b ? a : b) + 64;
 }
@@ -660,14 +754,32 @@ cudaError_t launch_objective(const GridDesc& g, double gamma, int plane_i, doubl
   return cudaGetLastError();
 }
 
+cudaError_t launch_objective_fast(const GridDesc& g, double gamma, int plane_i, double pt_in, const double* w,
+                                  double weight, double* J_acc, double* lam, unsigned* err, double* scratch,
+                                  unsigned* ticket, cudaStream_t st) {
+  const int nf = g.ny * g.nz;
+  int nblk = (nf + OMB - 1) / OMB;
+  if (nblk > RG) nblk = RG;
+  double* partial = scratch;
+  double* ndsc = scratch + (size_t)2 * RG * g.batch;
+  double* aface = ndsc + 2 * (size_t)g.batch;
+  k_obj_sum<<<dim3(nblk, g.batch), OMB, 0, st>>>(g, gamma, plane_i, pt_in, w, weight, J_acc, lam != nullptr, err,
+                                                 partial, aface, ndsc, ticket);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || !lam) return e;
+  const long long n = (long long)nf * g.batch;
+  k_obj_scatter<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(g, plane_i, aface, ndsc, lam);
+  return cudaGetLastError();
+}
+
 template <class CT>
 cudaError_t launch_sigma1(const GridDesc& g, const Coef<CT>& c, const CT* w, float* sigma1,
                           double* stats, double* scratch, cudaStream_t st) {
-  dim3 grid(RG, g.batch);
+  dim3 grid(RGS, g.batch);
   k_sigma1<CT><<<grid, RB, 0, st>>>(g, c, w, sigma1, scratch);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || !stats) return e;
-  k_sigma1_stats<<<g.batch, RB, 0, st>>>(RG, 1.0 / (double)g.cells, scratch, stats);
+  k_sigma1_stats<<<g.batch, RB, 0, st>>>(RGS, 1.0 / (double)g.cells, scratch, stats);
   return cudaGetLastError();
 }
 template cudaError_t launch_sigma1<double>(const GridDesc&, const Coef<double>&, const double*, float*,

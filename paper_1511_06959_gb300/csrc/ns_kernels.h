@@ -73,6 +73,10 @@ size_t diag_scratch_doubles(const GridDesc& g, int nphi);
 cudaError_t launch_objective(const GridDesc& g, double gamma, int plane_i, double pt_in,
                              const double* w, double weight, double* J_acc, double* lam,
                              unsigned* err, double* scratch, cudaStream_t st);
+// two-launch objective (value in one launch); ticket: batch zero-initialised counters
+cudaError_t launch_objective_fast(const GridDesc& g, double gamma, int plane_i, double pt_in, const double* w,
+                                   double weight, double* J_acc, double* lam, unsigned* err, double* scratch,
+                                   unsigned* ticket, cudaStream_t st);
 template <class CT>
 cudaError_t launch_sigma1(const GridDesc& g, const Coef<CT>& c, const CT* w, float* sigma1,
                           double* stats, double* scratch, cudaStream_t st);

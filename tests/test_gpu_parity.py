@@ -420,3 +420,20 @@ def test_mixed_single_operators(shape):
     lref, sref = O.rk4_adjoint_step(w, a, P, None, nu.astype(np.float64))
     assert rel_l2(host(lo) - a, lref - a) < 2e-5
     assert rel_l2(host(sb), sref) < 2e-5
+
+
+@pytest.mark.parametrize("shape", [(40, 12, 1), (37, 9, 5), (64, 48, 48)])
+def test_objective_mixed_precision(shape):
+    """The objective of a mixed-precision context is FP64 too (two launches)."""
+    api = _api()
+    w = state(shape, 18, 0.08)
+    P = params_for(w)
+    S = make_solver(api, w, P, 1)
+    J = torch.zeros(1, dtype=torch.float64, device="cuda")
+    lam = torch.zeros(w.shape, dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        S.objective(dev(w), J, 0.5, lam)
+    Jref = O.objective(w, P)
+    assert abs(J.item() - Jref) <= 1e-12 * abs(Jref)
+    assert rel_l2(host(lam), O.objective_grad(w, P)) < 1e-12
+    assert S.last_error() == 0
