@@ -235,8 +235,13 @@ __device__ __forceinline__ void fill_Z(CT* Z, const CT* sQ, const CT* sA, const 
 
 }  // namespace
 
+// Resident CTAs per SM the register allocation is held to: 4 for FP32 (the shared
+// memory allows 4), 2 for FP64.
+template <class CT> struct AdjMinBlocks { static constexpr int value = 2; };
+template <> struct AdjMinBlocks<float> { static constexpr int value = 4; };
+
 template <class CT, class TIN, class TA, class TST>
-__global__ void __launch_bounds__(NT) k_adj_stage(GridDesc g, Coef<CT> c, AdjArgs<TIN, TA, TST> a) {
+__global__ void __launch_bounds__(NT, AdjMinBlocks<CT>::value) k_adj_stage(GridDesc g, Coef<CT> c, AdjArgs<TIN, TA, TST> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   CT* sQ = reinterpret_cast<CT*>(smem_raw);   // [3][5][SP] primal primitives
   CT* sA = sQ + 3 * 5 * SP;                    // [3][5][SP] adjoint input a
@@ -246,10 +251,8 @@ __global__ void __launch_bounds__(NT) k_adj_stage(GridDesc g, Coef<CT> c, AdjArg
   CT* sFY = sFX + 7 * TY * (TX + 1);           // [7][TY+1][TX]
   const int tid = threadIdx.x;
   const int tx = tid % TX, ty = tid / TX;
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-  const int b = blockIdx.z / g.nzchunks;
-  const int kz0 = (blockIdx.z % g.nzchunks) * g.kchunk;
-  const int kz1 = min(g.nz, kz0 + g.kchunk);
+  int b, x0, y0, kz0, kz1;
+  march_range(g, b, x0, y0, kz0, kz1);
   const int gx = x0 + tx, gy = y0 + ty;
   const bool valid = gx < g.nx && gy < g.ny;
   auto slot = [&](int k) { return (k - kz0 + 1) % 3; };
@@ -468,10 +471,12 @@ cudaError_t launch_adj_stage(const GridDesc& g, const Coef<CT>& c, const AdjArgs
                              cudaStream_t st) {
   const size_t smem = adj_smem_bytes<CT>();
   auto kern = k_adj_stage<CT, TIN, TA, TST>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  static MarchShape shape;
+  GridDesc gl = g;
+  int ctas = 0;
+  cudaError_t e = shape.get(kern, smem, gl, "NS_ADJ_CHUNKS", ctas);
   if (e != cudaSuccess) return e;
-  dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, g.batch * g.nzchunks);
-  kern<<<grid, NT, smem, st>>>(g, c, a);
+  kern<<<ctas, NT, smem, st>>>(gl, c, a);
   return cudaGetLastError();
 }
 

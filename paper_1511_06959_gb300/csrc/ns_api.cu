@@ -37,17 +37,6 @@ Coef<T> make_coef(const ns_params& p) {
 
 int cuerr(cudaError_t e) { return e == cudaSuccess ? NS_OK : NS_ERR_CUDA; }
 
-int choose_kchunk(const ns_params& p) {
-  const char* env = getenv("NS_KCHUNK");
-  if (env && atoi(env) > 0) return std::min(atoi(env), p.nz);
-  const long long cols = (long long)((p.nx + ns::TX - 1) / ns::TX) * ((p.ny + ns::TY - 1) / ns::TY) * p.batch;
-  const long long target = 8LL * 152;
-  long long chunks = (target + cols - 1) / cols;
-  if (chunks < 1) chunks = 1;
-  int k = (int)((p.nz + chunks - 1) / chunks);
-  k = std::max(k, 4);
-  return std::min(k, p.nz);
-}
 
 bool mixed(const ns_ctx* c) { return c->p.precision == NS_MIXED; }
 
@@ -205,8 +194,8 @@ int ns_create(const ns_params* p, void* stream, ns_ctx** out) {
   c->g.batch = p->batch;
   c->g.plane = (long long)p->nx * p->ny;
   c->g.cells = c->g.plane * p->nz;
-  c->g.kchunk = choose_kchunk(*p);
-  c->g.nzchunks = (p->nz + c->g.kchunk - 1) / c->g.kchunk;
+  c->g.ncx = (p->nx + ns::TX - 1) / ns::TX;
+  c->g.ncy = (p->ny + ns::TY - 1) / ns::TY;
   c->cd = make_coef<double>(*p);
   c->cf = make_coef<float>(*p);
   {

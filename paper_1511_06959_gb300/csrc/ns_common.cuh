@@ -1,14 +1,20 @@
 // Shared device-side definitions of the NS stencil kernels (sm_103a).
 //
-// Tile geometry: a CTA owns TX x TY cell columns of one box and marches a chunk of
+// Tile geometry: a CTA owns TX x TY cell columns of one box and marches a range of
 // z-planes, keeping a ring of three planes (k-1, k, k+1) of primitive variables with
-// a one-cell halo in x and y in shared memory.  Every face flux of the chunk is
+// a one-cell halo in x and y in shared memory.  Every face flux of the range is
 // computed once; periodic wrap is resolved when a plane is loaded, so every shared
 // position holds a valid cell even when the box is smaller than the tile.
+//
+// Work split: every tile column's planes are cut into the same number m of ranges
+// whose lengths differ by at most one, m = the kernel's resident CTA slots on the
+// device divided by the number of tile columns (at least 1, at most nz / MIN_PLANES),
+// so that one wave of CTAs covers the grid.
 #pragma once
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <stdlib.h>
 
 namespace ns {
 
@@ -21,10 +27,62 @@ constexpr int SP = SX * SY;   // cells per shared plane
 
 struct GridDesc {
   int nx, ny, nz, batch;
-  int kchunk;          // z-planes per CTA
-  int nzchunks;        // ceil(nz / kchunk)
+  int ncx, ncy;        // tile columns along x and y: ceil(nx / TX), ceil(ny / TY)
+  int nchunk;          // plane ranges per tile column (set per launch)
   long long plane;     // nx * ny
   long long cells;     // nx * ny * nz  (one box)
+};
+
+constexpr int MIN_PLANES = 4;   // fewest planes per CTA range (bounds the priming share)
+
+// Plane range of this CTA: tile column blockIdx.x / nchunk, range blockIdx.x % nchunk.
+__device__ __forceinline__ void march_range(const GridDesc& g, int& b, int& x0, int& y0, int& kz0,
+                                            int& kz1) {
+  const int col = blockIdx.x / g.nchunk;
+  const int j = blockIdx.x - col * g.nchunk;
+  kz0 = (int)((long long)g.nz * j / g.nchunk);
+  kz1 = (int)((long long)g.nz * (j + 1) / g.nchunk);
+  x0 = (col % g.ncx) * TX;
+  const int r = col / g.ncx;
+  y0 = (r % g.ncy) * TY;
+  b = r / g.ncy;
+}
+
+// Launch shape of a plane-marching kernel (see the file comment): sets g.nchunk and
+// returns the CTA count.  The resident slots come from the occupancy calculator with
+// the kernel's dynamic shared memory and are cached per device; the kernel's dynamic
+// shared-memory limit is raised once.  The environment variable `env`, when set to a
+// positive count, overrides the number of ranges per column.
+struct MarchShape {
+  int per_dev[16] = {0};
+  template <class K>
+  cudaError_t get(K kern, size_t smem, GridDesc& g, const char* env, int& ctas) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    int slots = (dev >= 0 && dev < 16) ? per_dev[dev] : 0;
+    if (slots == 0) {
+      e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      int per_sm = 0, sms = 0;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem);
+      if (e != cudaSuccess) return e;
+      e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      if (e != cudaSuccess) return e;
+      slots = (per_sm > 0 ? per_sm : 1) * sms;
+      if (dev >= 0 && dev < 16) per_dev[dev] = slots;
+    }
+    const long long cols = (long long)g.ncx * g.ncy * g.batch;
+    long long m = slots / cols;
+    const char* ov = env ? getenv(env) : nullptr;
+    if (ov && atoll(ov) > 0) m = atoll(ov);
+    if (m > g.nz / MIN_PLANES) m = g.nz / MIN_PLANES;
+    if (m < 1) m = 1;
+    if (cols * m > 0x7FFFFFFFLL) return cudaErrorInvalidConfiguration;
+    g.nchunk = (int)m;
+    ctas = (int)(cols * m);
+    return cudaSuccess;
+  }
 };
 
 template <class T>

@@ -5,7 +5,7 @@
 // mean of the two cell-centred central differences for the tangential derivatives of
 // (u1, u2, u3, e); the face velocity is the two-cell mean; alpha = gamma mu / Pr.
 //
-// One CTA = TX x TY columns x kchunk planes.  Per plane: every thread computes its
+// One CTA = TX x TY columns x a range of planes.  Per plane: every thread computes its
 // cell's lower x-face and lower y-face and the z-face above it; 36 extra threads
 // compute the tile's upper x/y boundary faces; the z-face below is carried in
 // registers from the previous plane.  Each face flux is thus evaluated once per tile.
@@ -211,21 +211,25 @@ __device__ __forceinline__ void zface(const CT* sQ, const Coef<CT>& c, int sL, i
   face_flux<2>(c, qL, qR, gx, gy, phi);
 }
 
+// Resident CTAs per SM the register allocation is held to: 5 for FP32 (104 registers
+// or fewer), 3 for FP64, 2 for the dual-number tangent.
+template <class CT> struct RhsMinBlocks { static constexpr int value = 3; };
+template <> struct RhsMinBlocks<float> { static constexpr int value = 5; };
+template <> struct RhsMinBlocks<Dual> { static constexpr int value = 2; };
+
 template <class CT, class TIN, class TST>
-__global__ void __launch_bounds__(NT) k_rhs_stage(GridDesc g, Coef<CT> c, StageArgs<TIN, TST> a) {
+__global__ void __launch_bounds__(NT, RhsMinBlocks<CT>::value) k_rhs_stage(GridDesc g, Coef<CT> c, StageArgs<TIN, TST> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   CT* sQ = reinterpret_cast<CT*>(smem_raw);          // [3][5][SP]
   CT* sFX = sQ + 3 * 5 * SP;                          // [5][TY][TX+1]
   CT* sFY = sFX + 5 * TY * (TX + 1);                  // [5][TY+1][TX]
   const int tid = threadIdx.x;
   const int tx = tid % TX, ty = tid / TX;
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-  const int b = blockIdx.z / g.nzchunks;
-  const int kz0 = (blockIdx.z % g.nzchunks) * g.kchunk;
-  const int kz1 = min(g.nz, kz0 + g.kchunk);
+  Loader<CT, TIN> in{a.W, a.Wd};
+  int b, x0, y0, kz0, kz1;
+  march_range(g, b, x0, y0, kz0, kz1);
   const int gx = x0 + tx, gy = y0 + ty;
   const bool valid = gx < g.nx && gy < g.ny;
-  Loader<CT, TIN> in{a.W, a.Wd};
 
   auto slot = [&](int k) { return (k - kz0 + 1) % 3; };
   fill_plane<CT>(sQ + slot(kz0 - 1) * 5 * SP, g, b, kz0 - 1, x0, y0, in);
@@ -241,6 +245,21 @@ __global__ void __launch_bounds__(NT) k_rhs_stage(GridDesc g, Coef<CT> c, StageA
     const bool more = k + 1 < kz1;
     PlaneRegs<CT> pf;
     if (more) plane_load(pf, g, b, k + 2, x0, y0, in);
+    const size_t o0 = (size_t)b * 5 * g.cells + (size_t)k * g.plane + (size_t)gy * g.nx + gx;
+    // epilogue operands of this plane, issued before the face fluxes so that their
+    // latency overlaps the flux arithmetic (scalar path)
+    CT e_src[5], e_dacc[5], e_base[5];
+    double e_wbase[5];
+    if constexpr (!std::is_same<CT, Dual>::value) {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        const size_t o = o0 + (size_t)v * g.cells;
+        e_src[v] = (valid && a.src) ? cvt<CT>(a.src[o]) : CT(0);
+        e_dacc[v] = (valid && a.dacc && !a.dacc_init) ? CT(a.dacc[o]) : CT(0);
+        e_base[v] = (valid && a.Wout) ? CT(a.base[o]) : CT(0);
+        e_wbase[v] = (valid && a.wout && a.wbase) ? a.wbase[o] : 0.0;
+      }
+    }
     {
       CT phi[5];
       xface(sQ, c, sm, s0, sp, ty + 1, tx, phi);
@@ -265,7 +284,6 @@ __global__ void __launch_bounds__(NT) k_rhs_stage(GridDesc g, Coef<CT> c, StageA
     }
     __syncthreads();
     if (valid) {
-      const size_t o0 = (size_t)b * 5 * g.cells + (size_t)k * g.plane + (size_t)gy * g.nx + gx;
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
         const CT fxp = sFX[(v * TY + ty) * (TX + 1) + tx + 1];
@@ -290,18 +308,17 @@ __global__ void __launch_bounds__(NT) k_rhs_stage(GridDesc g, Coef<CT> c, StageA
             if (a.Woutd) a.Woutd[o] = a.based[o] + a.cout * Rd;
           }
         } else {
-          CT Rv = R;
-          if (a.src) Rv = Rv + cvt<CT>(a.src[o]);
+          const CT Rv = R + e_src[v];
           const CT inc = CT(a.cacc) * Rv;
-          const CT dv = (a.dacc && !a.dacc_init ? a.dacc[o] : CT(0)) + inc;
+          const CT dv = e_dacc[v] + inc;
           if (a.wout) {
-            const double wv = (a.wbase ? a.wbase[o] : 0.0) + widen(dv);
+            const double wv = e_wbase[v] + widen(dv);
             a.wout[o] = wv;
             if (a.wout_mirror) a.wout_mirror[o] = cvt<TST>(wv);
           } else if (a.dacc) {
             a.dacc[o] = dv;
           }
-          if (a.Wout) a.Wout[o] = a.base[o] + CT(a.cout) * Rv;
+          if (a.Wout) a.Wout[o] = e_base[v] + CT(a.cout) * Rv;
         }
       }
     }
@@ -325,10 +342,12 @@ cudaError_t launch_rhs_stage(const GridDesc& g, const Coef<CT>& c, const StageAr
                              cudaStream_t st) {
   const size_t smem = rhs_smem_bytes<CT>();
   auto kern = k_rhs_stage<CT, TIN, TST>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  static MarchShape shape;
+  GridDesc gl = g;
+  int ctas = 0;
+  cudaError_t e = shape.get(kern, smem, gl, "NS_RHS_CHUNKS", ctas);
   if (e != cudaSuccess) return e;
-  dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, g.batch * g.nzchunks);
-  kern<<<grid, NT, smem, st>>>(g, c, a);
+  kern<<<ctas, NT, smem, st>>>(gl, c, a);
   return cudaGetLastError();
 }
 
