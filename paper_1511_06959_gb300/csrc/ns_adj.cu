@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(NT, AdjMinBlocks<CT>::value) k_adj_stage(GridD
   const int tid = threadIdx.x;
   const int tx = tid % TX, ty = tid / TX;
   int b, x0, y0, kz0, kz1;
-  march_range(g, b, x0, y0, kz0, kz1);
+  march_range<TX, TY>(g, b, x0, y0, kz0, kz1);
   const int gx = x0 + tx, gy = y0 + ty;
   const bool valid = gx < g.nx && gy < g.ny;
   auto slot = [&](int k) { return (k - kz0 + 1) % 3; };
@@ -471,7 +471,7 @@ cudaError_t launch_adj_stage(const GridDesc& g, const Coef<CT>& c, const AdjArgs
                              cudaStream_t st) {
   const size_t smem = adj_smem_bytes<CT>();
   auto kern = k_adj_stage<CT, TIN, TA, TST>;
-  static MarchShape shape;
+  static MarchShape<TX, TY> shape;
   GridDesc gl = g;
   int ctas = 0;
   cudaError_t e = shape.get(kern, smem, gl, "NS_ADJ_CHUNKS", ctas);

@@ -194,8 +194,6 @@ int ns_create(const ns_params* p, void* stream, ns_ctx** out) {
   c->g.batch = p->batch;
   c->g.plane = (long long)p->nx * p->ny;
   c->g.cells = c->g.plane * p->nz;
-  c->g.ncx = (p->nx + ns::TX - 1) / ns::TX;
-  c->g.ncy = (p->ny + ns::TY - 1) / ns::TY;
   c->cd = make_coef<double>(*p);
   c->cf = make_coef<float>(*p);
   {

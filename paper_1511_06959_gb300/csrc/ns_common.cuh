@@ -1,6 +1,7 @@
 // Shared device-side definitions of the NS stencil kernels (sm_103a).
 //
-// Tile geometry: a CTA owns TX x TY cell columns of one box and marches a range of
+// Tile geometry: a CTA owns TX x TY cell columns of one box (the adjoint stage kernel's
+// tile below; the primal stage kernel uses 32 x 8) and marches a range of
 // z-planes, keeping a ring of three planes (k-1, k, k+1) of primitive variables with
 // a one-cell halo in x and y in shared memory.  Every face flux of the range is
 // computed once; periodic wrap is resolved when a plane is loaded, so every shared
@@ -27,7 +28,6 @@ constexpr int SP = SX * SY;   // cells per shared plane
 
 struct GridDesc {
   int nx, ny, nz, batch;
-  int ncx, ncy;        // tile columns along x and y: ceil(nx / TX), ceil(ny / TY)
   int nchunk;          // plane ranges per tile column (set per launch)
   long long plane;     // nx * ny
   long long cells;     // nx * ny * nz  (one box)
@@ -35,17 +35,20 @@ struct GridDesc {
 
 constexpr int MIN_PLANES = 4;   // fewest planes per CTA range (bounds the priming share)
 
-// Plane range of this CTA: tile column blockIdx.x / nchunk, range blockIdx.x % nchunk.
+// Plane range of this CTA for tiles of TXK x TYK columns: tile column
+// blockIdx.x / nchunk, range blockIdx.x % nchunk.
+template <int TXK, int TYK>
 __device__ __forceinline__ void march_range(const GridDesc& g, int& b, int& x0, int& y0, int& kz0,
                                             int& kz1) {
+  const int ncx = (g.nx + TXK - 1) / TXK, ncy = (g.ny + TYK - 1) / TYK;
   const int col = blockIdx.x / g.nchunk;
   const int j = blockIdx.x - col * g.nchunk;
   kz0 = (int)((long long)g.nz * j / g.nchunk);
   kz1 = (int)((long long)g.nz * (j + 1) / g.nchunk);
-  x0 = (col % g.ncx) * TX;
-  const int r = col / g.ncx;
-  y0 = (r % g.ncy) * TY;
-  b = r / g.ncy;
+  x0 = (col % ncx) * TXK;
+  const int r = col / ncx;
+  y0 = (r % ncy) * TYK;
+  b = r / ncy;
 }
 
 // Launch shape of a plane-marching kernel (see the file comment): sets g.nchunk and
@@ -53,7 +56,9 @@ __device__ __forceinline__ void march_range(const GridDesc& g, int& b, int& x0, 
 // the kernel's dynamic shared memory and are cached per device; the kernel's dynamic
 // shared-memory limit is raised once.  The environment variable `env`, when set to a
 // positive count, overrides the number of ranges per column.
+template <int TXK, int TYK>
 struct MarchShape {
+  static constexpr int NTK = TXK * TYK;
   int per_dev[16] = {0};
   template <class K>
   cudaError_t get(K kern, size_t smem, GridDesc& g, const char* env, int& ctas) {
@@ -65,14 +70,14 @@ struct MarchShape {
       e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;
       int per_sm = 0, sms = 0;
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NTK, smem);
       if (e != cudaSuccess) return e;
       e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
       if (e != cudaSuccess) return e;
       slots = (per_sm > 0 ? per_sm : 1) * sms;
       if (dev >= 0 && dev < 16) per_dev[dev] = slots;
     }
-    const long long cols = (long long)g.ncx * g.ncy * g.batch;
+    const long long cols = (long long)((g.nx + TXK - 1) / TXK) * ((g.ny + TYK - 1) / TYK) * g.batch;
     long long m = slots / cols;
     const char* ov = env ? getenv(env) : nullptr;
     if (ov && atoll(ov) > 0) m = atoll(ov);

@@ -22,6 +22,14 @@
 #include "ns_kernels.h"
 
 namespace ns {
+namespace rk {
+
+// Tile of the primal stage kernel: 32 x 8 columns (256 threads), which halves the
+// y-halo share of the plane loads and of the boundary faces against the 32 x 4 tile.
+constexpr int TY = 8;
+constexpr int NT = TX * TY;
+constexpr int SY = TY + 2;
+constexpr int SP = SX * SY;
 
 template <class CT, class TIN>
 struct Loader {
@@ -211,11 +219,11 @@ __device__ __forceinline__ void zface(const CT* sQ, const Coef<CT>& c, int sL, i
   face_flux<2>(c, qL, qR, gx, gy, phi);
 }
 
-// Resident CTAs per SM the register allocation is held to: 5 for FP32 (104 registers
-// or fewer), 3 for FP64, 2 for the dual-number tangent.
-template <class CT> struct RhsMinBlocks { static constexpr int value = 3; };
-template <> struct RhsMinBlocks<float> { static constexpr int value = 5; };
-template <> struct RhsMinBlocks<Dual> { static constexpr int value = 2; };
+// Resident CTAs per SM the register allocation is held to: 3 for FP32 (85 registers or
+// fewer), 1 for FP64 and the dual-number tangent.
+template <class CT> struct RhsMinBlocks { static constexpr int value = 1; };
+template <> struct RhsMinBlocks<float> { static constexpr int value = 3; };
+template <> struct RhsMinBlocks<Dual> { static constexpr int value = 1; };
 
 template <class CT, class TIN, class TST>
 __global__ void __launch_bounds__(NT, RhsMinBlocks<CT>::value) k_rhs_stage(GridDesc g, Coef<CT> c, StageArgs<TIN, TST> a) {
@@ -227,7 +235,7 @@ __global__ void __launch_bounds__(NT, RhsMinBlocks<CT>::value) k_rhs_stage(GridD
   const int tx = tid % TX, ty = tid / TX;
   Loader<CT, TIN> in{a.W, a.Wd};
   int b, x0, y0, kz0, kz1;
-  march_range(g, b, x0, y0, kz0, kz1);
+  march_range<TX, TY>(g, b, x0, y0, kz0, kz1);
   const int gx = x0 + tx, gy = y0 + ty;
   const bool valid = gx < g.nx && gy < g.ny;
 
@@ -332,22 +340,24 @@ __global__ void __launch_bounds__(NT, RhsMinBlocks<CT>::value) k_rhs_stage(GridD
   }
 }
 
+}  // namespace rk
+
 template <class CT>
 size_t rhs_smem_bytes() {
-  return sizeof(CT) * (3 * 5 * SP + 5 * TY * (TX + 1) + 5 * (TY + 1) * TX);
+  return sizeof(CT) * (3 * 5 * rk::SP + 5 * rk::TY * (TX + 1) + 5 * (rk::TY + 1) * TX);
 }
 
 template <class CT, class TIN, class TST>
 cudaError_t launch_rhs_stage(const GridDesc& g, const Coef<CT>& c, const StageArgs<TIN, TST>& a,
                              cudaStream_t st) {
   const size_t smem = rhs_smem_bytes<CT>();
-  auto kern = k_rhs_stage<CT, TIN, TST>;
-  static MarchShape shape;
+  auto kern = rk::k_rhs_stage<CT, TIN, TST>;
+  static MarchShape<TX, rk::TY> shape;
   GridDesc gl = g;
   int ctas = 0;
   cudaError_t e = shape.get(kern, smem, gl, "NS_RHS_CHUNKS", ctas);
   if (e != cudaSuccess) return e;
-  kern<<<ctas, NT, smem, st>>>(gl, c, a);
+  kern<<<ctas, rk::NT, smem, st>>>(gl, c, a);
   return cudaGetLastError();
 }
 
