@@ -472,11 +472,10 @@ cudaError_t launch_adj_stage(const GridDesc& g, const Coef<CT>& c, const AdjArgs
   const size_t smem = adj_smem_bytes<CT>();
   auto kern = k_adj_stage<CT, TIN, TA, TST>;
   static MarchShape<TX, TY> shape;
-  GridDesc gl = g;
   int ctas = 0;
-  cudaError_t e = shape.get(kern, smem, gl, "NS_ADJ_CHUNKS", ctas);
+  cudaError_t e = shape.get(kern, smem, g, "NS_ADJ_CTAS", ctas);
   if (e != cudaSuccess) return e;
-  kern<<<ctas, NT, smem, st>>>(gl, c, a);
+  kern<<<ctas, NT, smem, st>>>(g, c, a);
   return cudaGetLastError();
 }
 

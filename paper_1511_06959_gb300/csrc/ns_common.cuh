@@ -7,10 +7,11 @@
 // computed once; periodic wrap is resolved when a plane is loaded, so every shared
 // position holds a valid cell even when the box is smaller than the tile.
 //
-// Work split: every tile column's planes are cut into the same number m of ranges
-// whose lengths differ by at most one, m = the kernel's resident CTA slots on the
-// device divided by the number of tile columns (at least 1, at most nz / MIN_PLANES),
-// so that one wave of CTAs covers the grid.
+// Work split: the CTAs of a launch, as many as the kernel has resident slots on the
+// device (occupancy calculator x SMs), are dealt out to the tile columns as evenly as
+// integers allow (column c gets floor((c+1)G/C) - floor(cG/C) of the G CTAs), and each
+// column's planes are cut into that many ranges whose lengths differ by at most one.
+// One wave of CTAs then covers the grid with every SM holding the same number of CTAs.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -28,40 +29,40 @@ constexpr int SP = SX * SY;   // cells per shared plane
 
 struct GridDesc {
   int nx, ny, nz, batch;
-  int nchunk;          // plane ranges per tile column (set per launch)
   long long plane;     // nx * ny
   long long cells;     // nx * ny * nz  (one box)
 };
 
 constexpr int MIN_PLANES = 4;   // fewest planes per CTA range (bounds the priming share)
 
-// Plane range of this CTA for tiles of TXK x TYK columns: tile column
-// blockIdx.x / nchunk, range blockIdx.x % nchunk.
+// Plane range of this CTA for tiles of TXK x TYK columns (see the file comment).
 template <int TXK, int TYK>
 __device__ __forceinline__ void march_range(const GridDesc& g, int& b, int& x0, int& y0, int& kz0,
                                             int& kz1) {
   const int ncx = (g.nx + TXK - 1) / TXK, ncy = (g.ny + TYK - 1) / TYK;
-  const int col = blockIdx.x / g.nchunk;
-  const int j = blockIdx.x - col * g.nchunk;
-  kz0 = (int)((long long)g.nz * j / g.nchunk);
-  kz1 = (int)((long long)g.nz * (j + 1) / g.nchunk);
+  const long long C = (long long)ncx * ncy * g.batch, G = gridDim.x, i = blockIdx.x;
+  const int col = (int)(((i + 1) * C - 1) / G);
+  const long long s0 = (long long)col * G / C, s1 = (long long)(col + 1) * G / C;
+  const long long j = i - s0, m = s1 - s0;
+  kz0 = (int)(g.nz * j / m);
+  kz1 = (int)(g.nz * (j + 1) / m);
   x0 = (col % ncx) * TXK;
   const int r = col / ncx;
   y0 = (r % ncy) * TYK;
   b = r / ncy;
 }
 
-// Launch shape of a plane-marching kernel (see the file comment): sets g.nchunk and
-// returns the CTA count.  The resident slots come from the occupancy calculator with
+// Launch shape of a plane-marching kernel (see the file comment): the CTA count.  The resident slots come from the occupancy calculator with
 // the kernel's dynamic shared memory and are cached per device; the kernel's dynamic
 // shared-memory limit is raised once.  The environment variable `env`, when set to a
-// positive count, overrides the number of ranges per column.
+// positive count, overrides the CTA count.  At least one CTA per tile column, at most
+// nz / MIN_PLANES per column.
 template <int TXK, int TYK>
 struct MarchShape {
   static constexpr int NTK = TXK * TYK;
   int per_dev[16] = {0};
   template <class K>
-  cudaError_t get(K kern, size_t smem, GridDesc& g, const char* env, int& ctas) {
+  cudaError_t get(K kern, size_t smem, const GridDesc& g, const char* env, int& ctas) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
@@ -78,14 +79,14 @@ struct MarchShape {
       if (dev >= 0 && dev < 16) per_dev[dev] = slots;
     }
     const long long cols = (long long)((g.nx + TXK - 1) / TXK) * ((g.ny + TYK - 1) / TYK) * g.batch;
-    long long m = slots / cols;
+    long long n = slots;
     const char* ov = env ? getenv(env) : nullptr;
-    if (ov && atoll(ov) > 0) m = atoll(ov);
-    if (m > g.nz / MIN_PLANES) m = g.nz / MIN_PLANES;
-    if (m < 1) m = 1;
-    if (cols * m > 0x7FFFFFFFLL) return cudaErrorInvalidConfiguration;
-    g.nchunk = (int)m;
-    ctas = (int)(cols * m);
+    if (ov && atoll(ov) > 0) n = atoll(ov);
+    const long long most = cols * (g.nz / MIN_PLANES > 1 ? g.nz / MIN_PLANES : 1);
+    if (n > most) n = most;
+    if (n < cols) n = cols;
+    if (n > 0x7FFFFFFFLL) return cudaErrorInvalidConfiguration;
+    ctas = (int)n;
     return cudaSuccess;
   }
 };

@@ -53,7 +53,6 @@ extern "C" int ns_objective_noalloc(const ns_params* p, void* stream, const doub
   g.batch = p->batch;
   g.plane = (long long)p->nx * p->ny;
   g.cells = g.plane * p->nz;
-  g.nchunk = 1;
   if (ns::objective_scratch_doubles(g) > kErrOffset) return NS_ERR_BUDGET;
   double* scratch = nullptr;
   int r = scratch_on_current_device(&scratch);

@@ -353,11 +353,10 @@ cudaError_t launch_rhs_stage(const GridDesc& g, const Coef<CT>& c, const StageAr
   const size_t smem = rhs_smem_bytes<CT>();
   auto kern = rk::k_rhs_stage<CT, TIN, TST>;
   static MarchShape<TX, rk::TY> shape;
-  GridDesc gl = g;
   int ctas = 0;
-  cudaError_t e = shape.get(kern, smem, gl, "NS_RHS_CHUNKS", ctas);
+  cudaError_t e = shape.get(kern, smem, g, "NS_RHS_CTAS", ctas);
   if (e != cudaSuccess) return e;
-  kern<<<ctas, rk::NT, smem, st>>>(gl, c, a);
+  kern<<<ctas, rk::NT, smem, st>>>(g, c, a);
   return cudaGetLastError();
 }
 
