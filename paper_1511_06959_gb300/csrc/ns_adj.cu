@@ -113,13 +113,11 @@ __device__ __forceinline__ void face_stress(const Coef<CT>& c, const CT* qL, con
   sig[D] = sig[D] - CT(2.0 / 3.0) * c.mu * div;
 }
 
-// 7-value packet of a face: nb[0..2] (u), nb[3] (e), ub[0..2].
+// 7-value packet of a face from its s-vector and Fb[4]: nb[0..2] (u), nb[3] (e), ub[0..2].
 template <int D, class CT>
-__device__ __forceinline__ void face_packet(const Coef<CT>& c, const CT* QL, const CT* AL, int iL,
-                                            const CT* QR, const CT* AR, int iR, const CT* gt1,
-                                            const CT* gt2, CT pk[7]) {
-  CT s[3], fb4;
-  face_s<D>(c, QL, AL, iL, QR, AR, iR, s, fb4);
+__device__ __forceinline__ void face_packet_s(const Coef<CT>& c, const CT s[3], CT fb4, const CT* QL,
+                                              int iL, const CT* QR, int iR, const CT* gt1,
+                                              const CT* gt2, CT pk[7]) {
   CT uL[3], uR[3], sig[3];
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
@@ -135,8 +133,66 @@ __device__ __forceinline__ void face_packet(const Coef<CT>& c, const CT* QL, con
   for (int j = 0; j < 3; ++j) pk[4 + j] = fb4 * sig[j];
 }
 
+template <int D, class CT>
+__device__ __forceinline__ void face_packet(const Coef<CT>& c, const CT* QL, const CT* AL, int iL,
+                                            const CT* QR, const CT* AR, int iR, const CT* gt1,
+                                            const CT* gt2, CT pk[7]) {
+  CT s[3], fb4;
+  face_s<D>(c, QL, AL, iL, QR, AR, iR, s, fb4);
+  face_packet_s<D>(c, s, fb4, QL, iL, QR, iR, gt1, gt2, pk);
+}
+
+// In-plane face values of one plane slot, each face once: s-vector and Fb[4] of the
+// x-faces between shared columns fx and fx+1 (fx in [0, SX-2]) of every shared row, and
+// of the y-faces between shared rows fy and fy+1 (fy in [0, SY-2]) of every shared
+// column.  Layout F[4][NF]: x-face (row, fx) at row*(SX-1) + fx, y-face (fy, col) at
+// NXF + fy*SX + col; component 3 is Fb[4].  The per-cell sums S_d of the file comment
+// are two reads of these.
+constexpr int NXF = SY * (SX - 1);
+constexpr int NYF = (SY - 1) * SX;
+constexpr int NF = NXF + NYF;
+
 template <class CT>
-__device__ __forceinline__ void xpacket(const CT* sQ, const CT* sA, const Coef<CT>& c, int sm,
+__device__ __forceinline__ const CT& xf(const CT* F, int j, int row, int fx) {
+  return F[j * NF + row * (SX - 1) + fx];
+}
+template <class CT>
+__device__ __forceinline__ const CT& yf(const CT* F, int j, int fy, int col) {
+  return F[j * NF + NXF + fy * SX + col];
+}
+
+template <class CT>
+__device__ __forceinline__ void fill_faces(CT* F, const CT* sQ, const CT* sA, const Coef<CT>& c,
+                                           int slot) {
+  const CT* Q = sQ + slot * 5 * SP;
+  const CT* A = sA + slot * 5 * SP;
+  for (int t = threadIdx.x; t < NF; t += NT) {
+    CT sv[3], fb4;
+    if (t < NXF) {
+      const int row = t / (SX - 1);
+      const int iL = row * SX + (t - row * (SX - 1));
+      face_s<0>(c, Q, A, iL, Q, A, iL + 1, sv, fb4);
+    } else {
+      const int iL = t - NXF;   // fy * SX + col
+      face_s<1>(c, Q, A, iL, Q, A, iL + SX, sv, fb4);
+    }
+#pragma unroll
+    for (int j = 0; j < 3; ++j) F[j * NF + t] = sv[j];
+    F[3 * NF + t] = fb4;
+  }
+}
+
+// S_x[2], S_y[2] and S_x[0] + S_y[1] of the thread's own cell (shared row ty+1, column
+// tx+1): the only components of the neighbouring planes' sums the assembly uses.
+template <class CT>
+__device__ __forceinline__ void own_S(const CT* F, int ty, int tx, CT o[3]) {
+  o[0] = xf(F, 2, ty + 1, tx) + xf(F, 2, ty + 1, tx + 1);
+  o[1] = yf(F, 2, ty, tx + 1) + yf(F, 2, ty + 1, tx + 1);
+  o[2] = (xf(F, 0, ty + 1, tx) + xf(F, 0, ty + 1, tx + 1)) + (yf(F, 1, ty, tx + 1) + yf(F, 1, ty + 1, tx + 1));
+}
+
+template <class CT>
+__device__ __forceinline__ void xpacket(const CT* sQ, const CT* F0, const Coef<CT>& c, int sm,
                                         int s0, int sp, int row, int fx, CT pk[7]) {
   const int iL = row * SX + fx, iR = iL + 1;
   const CT* Q0 = sQ + s0 * 5 * SP;
@@ -150,12 +206,12 @@ __device__ __forceinline__ void xpacket(const CT* sQ, const CT* sA, const Coef<C
     gz[k] = (Qp[(1 + k) * SP + iL] - Qm[(1 + k) * SP + iL] + Qp[(1 + k) * SP + iR] -
              Qm[(1 + k) * SP + iR]) * c.i4dx[2];
   }
-  const CT* A0 = sA + s0 * 5 * SP;
-  face_packet<0>(c, Q0, A0, iL, Q0, A0, iR, gy, gz, pk);
+  const CT sv[3] = {xf(F0, 0, row, fx), xf(F0, 1, row, fx), xf(F0, 2, row, fx)};
+  face_packet_s<0>(c, sv, xf(F0, 3, row, fx), Q0, iL, Q0, iR, gy, gz, pk);
 }
 
 template <class CT>
-__device__ __forceinline__ void ypacket(const CT* sQ, const CT* sA, const Coef<CT>& c, int sm,
+__device__ __forceinline__ void ypacket(const CT* sQ, const CT* F0, const Coef<CT>& c, int sm,
                                         int s0, int sp, int fy, int col, CT pk[7]) {
   const int iL = fy * SX + col, iR = iL + SX;
   const CT* Q0 = sQ + s0 * 5 * SP;
@@ -169,8 +225,8 @@ __device__ __forceinline__ void ypacket(const CT* sQ, const CT* sA, const Coef<C
              Qm[(1 + k) * SP + iR]) * c.i4dx[2];
     gx[k] = (p0[iL + 1] - p0[iL - 1] + p0[iR + 1] - p0[iR - 1]) * c.i4dx[0];
   }
-  const CT* A0 = sA + s0 * 5 * SP;
-  face_packet<1>(c, Q0, A0, iL, Q0, A0, iR, gz, gx, pk);
+  const CT sv[3] = {yf(F0, 0, fy, col), yf(F0, 1, fy, col), yf(F0, 2, fy, col)};
+  face_packet_s<1>(c, sv, yf(F0, 3, fy, col), Q0, iL, Q0, iR, gz, gx, pk);
 }
 
 template <class CT>
@@ -187,34 +243,6 @@ __device__ __forceinline__ void zpacket(const CT* sQ, const CT* sA, const Coef<C
     gy[k] = (a[i + SX] - a[i - SX] + bq[i + SX] - bq[i - SX]) * c.i4dx[1];
   }
   face_packet<2>(c, QL, sA + sL * 5 * SP, i, QR, sA + sR * 5 * SP, i, gx, gy, pk);
-}
-
-// In-plane S-vector sums for one plane slot: S_x valid for lx in [1, SX-2],
-// S_y valid for ly in [1, SY-2].  Layout sS[slot][6][SP]: (S_x[0..2], S_y[0..2]).
-template <class CT>
-__device__ __forceinline__ void fill_S(CT* sS, const CT* sQ, const CT* sA, const Coef<CT>& c,
-                                       int slot) {
-  const CT* Q = sQ + slot * 5 * SP;
-  const CT* A = sA + slot * 5 * SP;
-  CT* S = sS + slot * 6 * SP;
-  for (int t = threadIdx.x; t < SP; t += NT) {
-    const int ly = t / SX;
-    const int lx = t - ly * SX;
-    if (lx >= 1 && lx <= SX - 2) {
-      CT s1[3], s2[3], f;
-      face_s<0>(c, Q, A, t - 1, Q, A, t, s1, f);
-      face_s<0>(c, Q, A, t, Q, A, t + 1, s2, f);
-#pragma unroll
-      for (int j = 0; j < 3; ++j) S[j * SP + t] = s1[j] + s2[j];
-    }
-    if (ly >= 1 && ly <= SY - 2) {
-      CT s1[3], s2[3], f;
-      face_s<1>(c, Q, A, t - SX, Q, A, t, s1, f);
-      face_s<1>(c, Q, A, t, Q, A, t + SX, s2, f);
-#pragma unroll
-      for (int j = 0; j < 3; ++j) S[(3 + j) * SP + t] = s1[j] + s2[j];
-    }
-  }
 }
 
 // z-face s-vectors between plane slots sL and sR at every shared column.
@@ -245,8 +273,8 @@ __global__ void __launch_bounds__(NT, AdjMinBlocks<CT>::value) k_adj_stage(GridD
   extern __shared__ __align__(16) unsigned char smem_raw[];
   CT* sQ = reinterpret_cast<CT*>(smem_raw);   // [3][5][SP] primal primitives
   CT* sA = sQ + 3 * 5 * SP;                    // [3][5][SP] adjoint input a
-  CT* sS = sA + 3 * 5 * SP;                    // [3][6][SP] in-plane S sums
-  CT* sZ = sS + 3 * 6 * SP;                    // [2][3][SP] z-face s-vectors
+  CT* sF = sA + 3 * 5 * SP;                    // [2][4][NF] in-plane face s-vectors, Fb[4]
+  CT* sZ = sF + 2 * 4 * NF;                    // [2][3][SP] z-face s-vectors
   CT* sFX = sZ + 2 * 3 * SP;                   // [7][TY][TX+1]
   CT* sFY = sFX + 7 * TY * (TX + 1);           // [7][TY+1][TX]
   const int tid = threadIdx.x;
@@ -257,6 +285,7 @@ __global__ void __launch_bounds__(NT, AdjMinBlocks<CT>::value) k_adj_stage(GridD
   const bool valid = gx < g.nx && gy < g.ny;
   auto slot = [&](int k) { return (k - kz0 + 1) % 3; };
   auto zslot = [&](int k) { return (k - kz0 + 1) & 1; };   // z-face k + 1/2
+  auto fslot = [&](int k) { return sF + ((k - kz0 + 1) & 1) * 4 * NF; };   // faces of plane k
 
   {
     AdjPlaneRegs<CT> p0, p1, p2;
@@ -268,12 +297,17 @@ __global__ void __launch_bounds__(NT, AdjMinBlocks<CT>::value) k_adj_stage(GridD
     adj_plane_store(p2, sQ + slot(kz0 + 1) * 5 * SP, sA + slot(kz0 + 1) * 5 * SP);
   }
   __syncthreads();
-  fill_S(sS, sQ, sA, c, slot(kz0 - 1));
-  fill_S(sS, sQ, sA, c, slot(kz0));
+  fill_faces(fslot(kz0 - 1), sQ, sA, c, slot(kz0 - 1));
+  fill_faces(fslot(kz0), sQ, sA, c, slot(kz0));
   fill_Z(sZ + zslot(kz0 - 1) * 3 * SP, sQ, sA, c, slot(kz0 - 1), slot(kz0));
   const int ic = (ty + 1) * SX + (tx + 1);
   CT zlo[7], zhi[7];
   zpacket(sQ, sA, c, slot(kz0 - 1), slot(kz0), ic, zlo);
+  __syncthreads();
+  // own-cell S sums of planes k-1 and k, carried in registers along the march
+  CT own_m[3], own_0[3];
+  own_S(fslot(kz0 - 1), ty, tx, own_m);
+  own_S(fslot(kz0), ty, tx, own_0);
   __syncthreads();
 
   for (int k = kz0; k < kz1; ++k) {
@@ -305,40 +339,39 @@ __global__ void __launch_bounds__(NT, AdjMinBlocks<CT>::value) k_adj_stage(GridD
         if (a.Anext) lfv[v] = a.lamf[o0 + (size_t)v * g.cells];
       }
     }
-    fill_S(sS, sQ, sA, c, sp);
+    const CT* F0 = fslot(k);
+    fill_faces(fslot(k + 1), sQ, sA, c, sp);
     fill_Z(sZ + zslot(k) * 3 * SP, sQ, sA, c, s0, sp);
     {
       CT pk[7];
-      xpacket(sQ, sA, c, sm, s0, sp, ty + 1, tx, pk);
+      xpacket(sQ, F0, c, sm, s0, sp, ty + 1, tx, pk);
 #pragma unroll
       for (int v = 0; v < 7; ++v) sFX[(v * TY + ty) * (TX + 1) + tx] = pk[v];
-      ypacket(sQ, sA, c, sm, s0, sp, ty, tx + 1, pk);
+      ypacket(sQ, F0, c, sm, s0, sp, ty, tx + 1, pk);
 #pragma unroll
       for (int v = 0; v < 7; ++v) sFY[(v * (TY + 1) + ty) * TX + tx] = pk[v];
     }
     zpacket(sQ, sA, c, s0, sp, ic, zhi);
     if (tid < TX) {
       CT pk[7];
-      ypacket(sQ, sA, c, sm, s0, sp, TY, tid + 1, pk);
+      ypacket(sQ, F0, c, sm, s0, sp, TY, tid + 1, pk);
 #pragma unroll
       for (int v = 0; v < 7; ++v) sFY[(v * (TY + 1) + TY) * TX + tid] = pk[v];
     } else if (tid < TX + TY) {
       CT pk[7];
       const int r = tid - TX;
-      xpacket(sQ, sA, c, sm, s0, sp, r + 1, TX, pk);
+      xpacket(sQ, F0, c, sm, s0, sp, r + 1, TX, pk);
 #pragma unroll
       for (int v = 0; v < 7; ++v) sFX[(v * TY + r) * (TX + 1) + TX] = pk[v];
     }
     __syncthreads();
 
+    CT own_p[3] = {CT(0), CT(0), CT(0)};
     if (valid) {
       const CT* Q0 = sQ + s0 * 5 * SP;
       const CT* A0 = sA + s0 * 5 * SP;
       const CT* Am = sA + sm * 5 * SP;
       const CT* Ap = sA + sp * 5 * SP;
-      const CT* S0 = sS + s0 * 6 * SP;
-      const CT* Sm = sS + sm * 6 * SP;
-      const CT* Sp = sS + sp * 6 * SP;
       const CT* Zl = sZ + zslot(k - 1) * 3 * SP;
       const CT* Zh = sZ + zslot(k) * 3 * SP;
       // ---- viscous: primitive adjoints of (u1, u2, u3, e)
@@ -368,19 +401,26 @@ __global__ void __launch_bounds__(NT, AdjMinBlocks<CT>::value) k_adj_stage(GridD
         auto Sz = [&](int j, int i) { return Zl[j * SP + i] + Zh[j * SP + i]; };
         // l = x (neighbours ic -+ 1): T[y][x] = mu S_y[x], T[z][x] = mu S_z[x],
         //                            T[x][x] = -2/3 mu (S_y[y] + S_z[z])
-        qb[0] = qb[0] + m23 * ((S0[4 * SP + il] + Sz(2, il)) - (S0[4 * SP + ir] + Sz(2, ir))) * c.i4dx[0];
-        qb[1] = qb[1] + m * (S0[3 * SP + il] - S0[3 * SP + ir]) * c.i4dx[0];
+        // S_y[j] at il = (ty+1, tx) and ir = (ty+1, tx+2); S_x[j] at idn = (ty, tx+1) and
+        // iup = (ty+2, tx+1): sums of the two in-plane faces of each cell (plane k)
+        auto Syl = [&](int j) { return yf(F0, j, ty, tx) + yf(F0, j, ty + 1, tx); };
+        auto Syr = [&](int j) { return yf(F0, j, ty, tx + 2) + yf(F0, j, ty + 1, tx + 2); };
+        auto Sxd = [&](int j) { return xf(F0, j, ty, tx) + xf(F0, j, ty, tx + 1); };
+        auto Sxu = [&](int j) { return xf(F0, j, ty + 2, tx) + xf(F0, j, ty + 2, tx + 1); };
+        qb[0] = qb[0] + m23 * ((Syl(1) + Sz(2, il)) - (Syr(1) + Sz(2, ir))) * c.i4dx[0];
+        qb[1] = qb[1] + m * (Syl(0) - Syr(0)) * c.i4dx[0];
         qb[2] = qb[2] + m * (Sz(0, il) - Sz(0, ir)) * c.i4dx[0];
         // l = y (neighbours ic -+ SX): T[x][y] = mu S_x[y], T[z][y] = mu S_z[y],
         //                             T[y][y] = -2/3 mu (S_x[x] + S_z[z])
-        qb[0] = qb[0] + m * (S0[1 * SP + idn] - S0[1 * SP + iup]) * c.i4dx[1];
-        qb[1] = qb[1] + m23 * ((S0[0 * SP + idn] + Sz(2, idn)) - (S0[0 * SP + iup] + Sz(2, iup))) * c.i4dx[1];
+        qb[0] = qb[0] + m * (Sxd(1) - Sxu(1)) * c.i4dx[1];
+        qb[1] = qb[1] + m23 * ((Sxd(0) + Sz(2, idn)) - (Sxu(0) + Sz(2, iup))) * c.i4dx[1];
         qb[2] = qb[2] + m * (Sz(1, idn) - Sz(1, iup)) * c.i4dx[1];
         // l = z (planes k -+ 1): T[x][z] = mu S_x[z], T[y][z] = mu S_y[z],
         //                       T[z][z] = -2/3 mu (S_x[x] + S_y[y])
-        qb[0] = qb[0] + m * (Sm[2 * SP + ic] - Sp[2 * SP + ic]) * c.i4dx[2];
-        qb[1] = qb[1] + m * (Sm[5 * SP + ic] - Sp[5 * SP + ic]) * c.i4dx[2];
-        qb[2] = qb[2] + m23 * ((Sm[0 * SP + ic] + Sm[4 * SP + ic]) - (Sp[0 * SP + ic] + Sp[4 * SP + ic])) * c.i4dx[2];
+        own_S(fslot(k + 1), ty, tx, own_p);
+        qb[0] = qb[0] + m * (own_m[0] - own_p[0]) * c.i4dx[2];
+        qb[1] = qb[1] + m * (own_m[1] - own_p[1]) * c.i4dx[2];
+        qb[2] = qb[2] + m23 * (own_m[2] - own_p[2]) * c.i4dx[2];
       }
       // ---- convective part and pull-back to conservative variables
       const CT rho = Q0[ic];
@@ -453,6 +493,11 @@ __global__ void __launch_bounds__(NT, AdjMinBlocks<CT>::value) k_adj_stage(GridD
     }
 #pragma unroll
     for (int v = 0; v < 7; ++v) zlo[v] = zhi[v];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      own_m[j] = own_0[j];
+      own_0[j] = own_p[j];
+    }
     __syncthreads();
     if (more) {
       adj_plane_store(pf, sQ + slot(k + 2) * 5 * SP, sA + slot(k + 2) * 5 * SP);
@@ -463,7 +508,7 @@ __global__ void __launch_bounds__(NT, AdjMinBlocks<CT>::value) k_adj_stage(GridD
 
 template <class CT>
 size_t adj_smem_bytes() {
-  return sizeof(CT) * (3 * 5 * SP * 2 + 3 * 6 * SP + 2 * 3 * SP + 7 * TY * (TX + 1) + 7 * (TY + 1) * TX);
+  return sizeof(CT) * (3 * 5 * SP * 2 + 2 * 4 * NF + 2 * 3 * SP + 7 * TY * (TX + 1) + 7 * (TY + 1) * TX);
 }
 
 template <class CT, class TIN, class TA, class TST>
