@@ -364,13 +364,18 @@ __global__ void __launch_bounds__(NT, AdjMinBlocks<CT>::value) k_adj_stage(GridD
 #pragma unroll
       for (int v = 0; v < 7; ++v) sFX[(v * TY + r) * (TX + 1) + TX] = pk[v];
     }
+    // the assembly reads plane k-1 only at the own cell: keep those values so that plane
+    // k+2 can replace plane k-1 in the ring right after the barrier
+    CT am[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) am[v] = sA[(sm * 5 + v) * SP + ic];
     __syncthreads();
+    if (more) adj_plane_store(pf, sQ + slot(k + 2) * 5 * SP, sA + slot(k + 2) * 5 * SP);
 
     CT own_p[3] = {CT(0), CT(0), CT(0)};
     if (valid) {
       const CT* Q0 = sQ + s0 * 5 * SP;
       const CT* A0 = sA + s0 * 5 * SP;
-      const CT* Am = sA + sm * 5 * SP;
       const CT* Ap = sA + sp * 5 * SP;
       const CT* Zl = sZ + zslot(k - 1) * 3 * SP;
       const CT* Zh = sZ + zslot(k) * 3 * SP;
@@ -437,11 +442,11 @@ __global__ void __launch_bounds__(NT, AdjMinBlocks<CT>::value) k_adj_stage(GridD
       const int nb_hi[3] = {ic + 1, ic + SX, ic};
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
-        const CT* Alo = d == 2 ? Am : A0;
         const CT* Ahi = d == 2 ? Ap : A0;
         CT F[5];
 #pragma unroll
-        for (int v = 0; v < 5; ++v) F[v] = (Ahi[v * SP + nb_hi[d]] - Alo[v * SP + nb_lo[d]]) * c.hidx[d];
+        for (int v = 0; v < 5; ++v)
+          F[v] = (Ahi[v * SP + nb_hi[d]] - (d == 2 ? am[v] : A0[v * SP + nb_lo[d]])) * c.hidx[d];
         const CT md = rho * u[d];
         mb[d] = mb[d] + F[0] + F[1] * u[0] + F[2] * u[1] + F[3] * u[2];
 #pragma unroll
@@ -472,7 +477,7 @@ __global__ void __launch_bounds__(NT, AdjMinBlocks<CT>::value) k_adj_stage(GridD
           const CT ac = Av[ic];
           CT L = (h * (nc + nxp) * (Av[ic + 1] - ac) - h * (nc + nxm) * (ac - Av[ic - 1])) * ix2 +
                  (h * (nc + nyp) * (Av[ic + SX] - ac) - h * (nc + nym) * (ac - Av[ic - SX])) * iy2 +
-                 (h * (nc + nzp) * (Ap[v * SP + ic] - ac) - h * (nc + nzm) * (ac - Am[v * SP + ic])) * iz2;
+                 (h * (nc + nzp) * (Ap[v * SP + ic] - ac) - h * (nc + nzm) * (ac - am[v])) * iz2;
           gout[v] = gout[v] + L;
         }
       }
@@ -498,11 +503,7 @@ __global__ void __launch_bounds__(NT, AdjMinBlocks<CT>::value) k_adj_stage(GridD
       own_m[j] = own_0[j];
       own_0[j] = own_p[j];
     }
-    __syncthreads();
-    if (more) {
-      adj_plane_store(pf, sQ + slot(k + 2) * 5 * SP, sA + slot(k + 2) * 5 * SP);
-      __syncthreads();
-    }
+    __syncthreads();   // plane k+2 visible; packets, faces and z-faces free
   }
 }
 

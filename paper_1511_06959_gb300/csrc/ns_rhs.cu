@@ -291,6 +291,8 @@ __global__ void __launch_bounds__(NT, RhsMinBlocks<CT>::value) k_rhs_stage(GridD
       for (int v = 0; v < 5; ++v) sFX[(v * TY + r) * (TX + 1) + TX] = phi[v];
     }
     __syncthreads();
+    // the epilogue reads only the face fluxes: plane k+2 replaces plane k-1 in the ring now
+    if (more) plane_store(pf, sQ + slot(k + 2) * 5 * SP);
     if (valid) {
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
@@ -332,11 +334,7 @@ __global__ void __launch_bounds__(NT, RhsMinBlocks<CT>::value) k_rhs_stage(GridD
     }
 #pragma unroll
     for (int v = 0; v < 5; ++v) zlo[v] = zhi[v];
-    __syncthreads();
-    if (more) {
-      plane_store(pf, sQ + slot(k + 2) * 5 * SP);
-      __syncthreads();
-    }
+    __syncthreads();   // plane k+2 visible; face fluxes free
   }
 }
 
