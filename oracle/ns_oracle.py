@@ -19,7 +19,7 @@ unstructured mesh, section "Numerical methods"):
     compact difference (q_{i+1} - q_i)/dx_d, the tangential parts are the mean of the
     two cell-centred central differences; the face velocity is the two-cell mean
   * R(w)_i = -sum_d (Phi_{d,i+1/2} - Phi_{d,i-1/2}) / dx_d + s_i,  Phi = Phi^c - F^v
-  * classical RK4 in time with a constant dt
+  * classical RK4 in time with a constant dt, or the paper's SSP-RK3 (Shu-Osher form)
   * heat flux alpha grad e with alpha = gamma mu / Pr  (so alpha grad e = k grad T)
 
 Functions whose result has no independent pin are marked "parity unpinned" in their
@@ -43,7 +43,10 @@ class Params:
     """Physical and discrete parameters of one periodic box.
 
     gamma, mu, Pr: ideal gas and constant viscosity of Eq. (e:navier).
-    dx: cell sizes (dx, dy, dz).  dt: the constant RK4 step.
+    dx: cell sizes (dx, dy, dz).  dt: the constant time step.
+    scheme: "rk4" (classical fourth-order Runge-Kutta) or "ssprk3" (the three-stage
+    third-order strong-stability-preserving Runge-Kutta method of section "Numerical
+    methods", in Shu-Osher form).
     plane_i: the objective plane is the x-face between cell columns plane_i-1 and
     plane_i.  pt_in: the reference stagnation pressure p_{t,in} of Eq. (e:pressure_loss).
     """
@@ -55,6 +58,7 @@ class Params:
     dt: float = 0.0
     plane_i: int = 0
     pt_in: float = 1.0
+    scheme: str = "rk4"
 
     @property
     def alpha(self) -> float:
@@ -345,6 +349,76 @@ def rk4_adjoint_step(w, lam, P: Params, s=None, nu=None):
 
 
 # ----------------------------------------------------------------------------------
+# SSP-RK3, section "Numerical methods": the three-stage, third-order strong-stability-
+# preserving Runge-Kutta method, written in its Shu-Osher form (each stage a convex
+# combination of forward-Euler steps):
+#     W2 = w + dt R(w)
+#     W3 = 3/4 w + 1/4 (W2 + dt R(W2))
+#     w' = 1/3 w + 2/3 (W3 + dt R(W3))
+# ----------------------------------------------------------------------------------
+def ssprk3_step(w, P: Params, s=None):
+    """One SSP-RK3 step with constant dt.  Returns w^{n+1} and the stage states W1..W3."""
+    dt = P.dt
+    W1 = w
+    W2 = w + dt * residual(W1, P, s)
+    W3 = 0.75 * w + 0.25 * (W2 + dt * residual(W2, P, s))
+    wn = w / 3.0 + 2.0 / 3.0 * (W3 + dt * residual(W3, P, s))
+    return wn, (W1, W2, W3)
+
+
+def ssprk3_tangent_step(w, wd, P: Params, s=None, sd=None):
+    """Linearisation of ssprk3_step along (wd, sd): returns wd^{n+1}."""
+    dt = P.dt
+    _, (W1, W2, W3) = ssprk3_step(w, P, s)
+    add = (lambda x: x) if sd is None else (lambda x: x + sd)
+    W2d = wd + dt * add(residual_tangent(W1, wd, P))
+    W3d = 0.75 * wd + 0.25 * (W2d + dt * add(residual_tangent(W2, W2d, P)))
+    return wd / 3.0 + 2.0 / 3.0 * (W3d + dt * add(residual_tangent(W3, W3d, P)))
+
+
+def ssprk3_adjoint_step(w, lam, P: Params, s=None, nu=None):
+    """Discrete adjoint of one SSP-RK3 step, the Shu-Osher stages reversed by hand:
+    given lam = dJ/dw^{n+1}, return (dw^{n+1}/dw^n)^T lam and the sum of the adjoints
+    of the three stage residuals (the source sensitivity seeds, as in rk4_adjoint_step).
+    nu adds L_nu to every stage product, as in rk4_adjoint_step."""
+    dt = P.dt
+    _, (W1, W2, W3) = ssprk3_step(w, P, s)
+
+    def JT(W, ab):
+        g = residual_transpose(W, ab, P)
+        if nu is not None:
+            g = g + viscosity_apply(ab, nu, P)
+        return g
+
+    # w' = w/3 + 2/3 W3 + 2/3 dt R(W3)
+    wbar = lam / 3.0
+    r3 = 2.0 / 3.0 * dt * lam
+    W3bar = 2.0 / 3.0 * lam + JT(W3, r3)
+    # W3 = 3/4 w + 1/4 W2 + 1/4 dt R(W2)
+    wbar = wbar + 0.75 * W3bar
+    r2 = 0.25 * dt * W3bar
+    W2bar = 0.25 * W3bar + JT(W2, r2)
+    # W2 = w + dt R(w)
+    wbar = wbar + W2bar
+    r1 = dt * W2bar
+    wbar = wbar + JT(W1, r1)
+    return wbar, r1 + r2 + r3
+
+
+def step(w, P: Params, s=None):
+    """One step of the scheme P.scheme: (w^{n+1}, stage states)."""
+    return ssprk3_step(w, P, s) if P.scheme == "ssprk3" else rk4_step(w, P, s)
+
+
+def tangent_step(w, wd, P: Params, s=None, sd=None):
+    return (ssprk3_tangent_step if P.scheme == "ssprk3" else rk4_tangent_step)(w, wd, P, s, sd)
+
+
+def adjoint_step(w, lam, P: Params, s=None, nu=None):
+    return (ssprk3_adjoint_step if P.scheme == "ssprk3" else rk4_adjoint_step)(w, lam, P, s, nu)
+
+
+# ----------------------------------------------------------------------------------
 # pressure-loss objective, Eq. (e:pressure_loss)
 # ----------------------------------------------------------------------------------
 def stagnation_pressure(rho, m, rhoE, P: Params):
@@ -426,7 +500,7 @@ def primal_run(w0, P: Params, nsteps, s=None):
     ws = [w0]
     Jbar = 0.0
     for n in range(nsteps):
-        wn, _ = rk4_step(ws[-1], P, s)
+        wn, _ = step(ws[-1], P, s)
         ws.append(wn)
         Jbar += objective(wn, P) / nsteps
     return ws, Jbar
@@ -443,7 +517,7 @@ def adjoint_run(ws, P: Params, s=None, nu=None):
     for n in range(N, 0, -1):
         lam = lam + objective_grad(ws[n], P) / N
         nun = nu(ws[n - 1]) if callable(nu) else nu
-        lam, sb = rk4_adjoint_step(ws[n - 1], lam, P, s, nun)
+        lam, sb = adjoint_step(ws[n - 1], lam, P, s, nun)
         sbar += sb
     return lam, sbar
 
@@ -454,7 +528,7 @@ def tangent_run(ws, wd0, P: Params, s=None, sd=None):
     wd = wd0
     Jd = 0.0
     for n in range(N):
-        wd = rk4_tangent_step(ws[n], wd, P, s, sd)
+        wd = tangent_step(ws[n], wd, P, s, sd)
         Jd += np.sum(objective_grad(ws[n + 1], P) * wd) / N
     return Jd
 
