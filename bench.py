@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default="box128", choices=sorted(C.WORKLOADS))
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--scheme", default="rk4", choices=["rk4", "ssprk3"],
+                    help="time integrator (the workload's is RK4; ssprk3 is the paper's own)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -68,20 +70,21 @@ def oracle_unit(w, P, lam_tilde, dx0):
     """Forward step + replay step + stabilised adjoint step (sigma_1, nu, objective source,
     adjoint energy) of the full box: the work the GPU sweep does per reversed step."""
     from oracle import ns_oracle as O
-    w1, _ = O.rk4_step(w, P)
+    w1, _ = O.step(w, P)
     O.objective(w1, P)
-    w1, _ = O.rk4_step(w, P)
+    w1, _ = O.step(w, P)
     lam = O.objective_grad(w1, P)
     nu = lam_tilde * dx0 ** 2 * O.sigma1_field(w, P)
-    lam, _ = O.rk4_adjoint_step(w, lam, P, None, nu)
+    lam, _ = O.adjoint_step(w, lam, P, None, nu)
     lam = lam + O.objective_grad(w, P)
     O.adjoint_energy(w, lam, P)
 
 
-def oracle_setup(wl):
+def oracle_setup(wl, scheme="rk4"):
     from oracle import ns_oracle as O
     w = wl.initial_state()
-    P = O.Params(gamma=wl.gamma, mu=wl.mu, Pr=wl.Pr, dx=wl.dx, plane_i=wl.plane_i, pt_in=wl.pt_in)
+    P = O.Params(gamma=wl.gamma, mu=wl.mu, Pr=wl.Pr, dx=wl.dx, plane_i=wl.plane_i, pt_in=wl.pt_in,
+                 scheme=scheme)
     P.dt = C.cfl_dt(wl, O.max_wave_speed(w, P))
     return w, P
 
@@ -99,7 +102,7 @@ def run_reference(args, wl):
         return
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         os.environ[k] = "1"
-    w, P = oracle_setup(wl)
+    w, P = oracle_setup(wl, args.scheme)
     for _ in range(min(args.warmup, 1)):
         oracle_unit(w, P, wl.lam_tilde, wl.dx[0])
     t0 = time.perf_counter()
@@ -113,7 +116,8 @@ def run_reference(args, wl):
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": min(args.warmup, 1), "ms_per_step": 1e3 * t / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": C.describe(wl), "name": wl.name},
+        "data": "synthetic", "config": {"workload": C.describe(wl, args.scheme), "name": wl.name,
+                                        "scheme": args.scheme},
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
@@ -174,27 +178,6 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows), "power_w_max": pmax}
 
 
-def launches_in_run(plan_actions, N, need_sigma, lam_on, record_energy, record_sigma):
-    """Kernel launches of one ns_adjoint_run (counted from its plan)."""
-    n = 0
-    touched = 0
-    for op, a, b in plan_actions:
-        if op == 1:
-            n += 4 * (b - a)
-            new = max(0, b - max(a, touched))
-            n += new
-            touched = max(touched, b)
-        elif op == 6:
-            n += 1 + (2 if record_energy else 0)
-        elif op == 4:
-            if need_sigma:
-                n += 1 + (1 if record_sigma else 0)
-            if lam_on:
-                n += 1
-            n += 7 + (1 if a >= 1 else 0) + (2 if record_energy else 0)
-    return n
-
-
 def run_ours(args, wl):
     import torch
 
@@ -212,8 +195,9 @@ def run_ours(args, wl):
 
     w0_host = wl.initial_state()
     w0 = torch.from_numpy(w0_host).to(dev)
+    scheme = api.NS_SSPRK3 if args.scheme == "ssprk3" else api.NS_RK4
     S = api.Solver(wl.nx, wl.ny, wl.nz, wl.dx, gamma=wl.gamma, mu=wl.mu, Pr=wl.Pr, dt=0.0,
-                   precision=prec, plane_i=wl.plane_i, pt_in=wl.pt_in, batch=wl.batch)
+                   precision=prec, plane_i=wl.plane_i, pt_in=wl.pt_in, batch=wl.batch, scheme=scheme)
     m = torch.empty(1, dtype=torch.float64, device=dev)
     S.max_wave_speed(w0, m)
     dt = C.cfl_dt(wl, m.item())
@@ -248,12 +232,14 @@ def run_ours(args, wl):
         torch.distributed.barrier()
     torch.cuda.synchronize()
     clk.start()
+    launches0 = api.launch_count()
     for i in range(args.steps):
         flush.fill_(i & 0xFF)          # L2 flush between timed steps, outside the event pair
         ev[i][0].record()
         step()
         ev[i][1].record()
     torch.cuda.synchronize()
+    gl = api.launch_count() - launches0
     if ws > 1:
         torch.distributed.barrier()
     ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
@@ -301,8 +287,6 @@ def run_ours(args, wl):
 
     out = None
     if rank == 0:
-        actions, _, _ = api.plan(wl.nsteps, sched, param)
-        gl = launches_in_run(actions, wl.nsteps, True, wl.lam_coef > 0, True, True) * args.steps
         kavg = kms / max(klaunch, 1)
         bytes_launch = ADJ_STAGE_BYTES[args.precision] * wl.cells * wl.batch
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
@@ -314,7 +298,8 @@ def run_ours(args, wl):
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32 (f64 accumulate)" if prec == api.NS_MIXED else "f64",
             "data": "synthetic",
-            "config": {"workload": C.describe(wl), "name": wl.name, "cells": wl.cells,
+            "config": {"workload": C.describe(wl, args.scheme), "name": wl.name, "cells": wl.cells,
+                       "scheme": args.scheme,
                        "nsteps": wl.nsteps, "schedule": wl.schedule, "param": param,
                        "lambda_tilde": wl.lam_tilde, "precision": args.precision, "dt": dt,
                        "l2": "flushed (256 MB write) between timed steps; arena "
@@ -332,9 +317,9 @@ def run_ours(args, wl):
             "clocks": clocks,
         }
         if not args.no_fp64_compare and prec == api.NS_MIXED:
-            out["fp64"] = fp64_compare(api, torch, wl, w0, dt, sched, param, lam0, Jv)
+            out["fp64"] = fp64_compare(api, torch, wl, w0, dt, sched, param, lam0, Jv, scheme)
         if not args.no_cpu_baseline and ws == 1:
-            out["cpu_baseline"] = cpu_baseline(wl)
+            out["cpu_baseline"] = cpu_baseline(wl, args.scheme)
     return out
 
 
@@ -372,11 +357,12 @@ def adj_traffic(wl, precision):
         return None
 
 
-def fp64_compare(api, torch, wl, w0, dt, sched, param, lam_mixed, J_mixed):
+def fp64_compare(api, torch, wl, w0, dt, sched, param, lam_mixed, J_mixed, scheme):
     """The same checkpointed sweep in FP64 (timed once) and the mixed-precision
     gradient error against it."""
     S = api.Solver(wl.nx, wl.ny, wl.nz, wl.dx, gamma=wl.gamma, mu=wl.mu, Pr=wl.Pr, dt=dt,
-                   precision=api.NS_FP64, plane_i=wl.plane_i, pt_in=wl.pt_in, batch=wl.batch)
+                   precision=api.NS_FP64, plane_i=wl.plane_i, pt_in=wl.pt_in, batch=wl.batch,
+                   scheme=scheme)
     opts = S.run_opts(wl.nsteps, sched, param, wl.lam_coef, 0.0, True, True)
     arena = torch.empty(S.arena_bytes(opts), dtype=torch.uint8, device=w0.device)
     J = torch.empty(wl.batch, dtype=torch.float64, device=w0.device)
@@ -403,7 +389,7 @@ def fp64_compare(api, torch, wl, w0, dt, sched, param, lam_mixed, J_mixed):
             "note": "FP64 is bound by the FP64 ALU rate, not HBM; timed once on the same workload"}
 
 
-def cpu_baseline(wl):
+def cpu_baseline(wl, scheme="rk4"):
     """The FP64 oracle on this host's cores: one checkpointed adjoint step of the full box
     (10-30 s of CPU work), scaled to adjoint cell-steps/s.  It runs in a spawned process
     so that no fork happens after CUDA is initialised."""
@@ -414,7 +400,7 @@ def cpu_baseline(wl):
     try:
         ctx = mp.get_context("spawn")
         with ctx.Pool(1) as pool:
-            t = pool.apply(_cpu_sample, (wl.name,))
+            t = pool.apply(_cpu_sample, (wl.name, scheme))
     finally:
         for k, v in saved.items():
             if v is None:
@@ -427,9 +413,9 @@ def cpu_baseline(wl):
                       f"{t:.1f} s", "host_cores_available": cpu_cores()}
 
 
-def _cpu_sample(name):
+def _cpu_sample(name, scheme="rk4"):
     wl = C.WORKLOADS[name]
-    w, P = oracle_setup(wl)
+    w, P = oracle_setup(wl, scheme)
     t0 = time.perf_counter()
     oracle_unit(w, P, wl.lam_tilde, wl.dx[0])
     return time.perf_counter() - t0

@@ -10,8 +10,9 @@
  * singular value of the growth matrix M = M1 - M2 ("Energy analysis").
  *
  * Discretisation: periodic structured box of nx*ny*nz cells (nz = 1 is a 2D box),
- * central 2nd-order face fluxes, compact viscous stencil, classical RK4 with a constant
- * dt; the adjoint is the exact transpose of that discrete map.
+ * central 2nd-order face fluxes, compact viscous stencil, classical RK4 or the paper's
+ * SSP-RK3 (ns_params.scheme) with a constant dt; the adjoint is the exact transpose of
+ * that discrete map.
  *
  * Conventions shared by every call:
  *  - Field pointers are DEVICE pointers owned by the caller, in SoA layout
@@ -45,6 +46,13 @@ extern "C" {
 #define NS_ERR_UNSTABLE (-4)
 #define NS_ERR_CUDA (-5)
 
+/* time integration (ns_params.scheme) */
+#define NS_RK4 0    /* classical four-stage fourth-order Runge-Kutta, constant dt */
+#define NS_SSPRK3 1 /* three-stage third-order strong-stability-preserving Runge-Kutta
+                       (section "Numerical methods"; Shu-Osher form
+                       W2 = w + dt R(w), W3 = 3/4 w + 1/4 (W2 + dt R(W2)),
+                       w' = 1/3 w + 2/3 (W3 + dt R(W3))) */
+
 #define NS_FP64 0  /* every flux, transpose and stage state in FP64 */
 #define NS_MIXED 1 /* fluxes, transposes and stage states in FP32; w, adjoint, objective,
                       reductions and time accumulation in FP64 */
@@ -56,10 +64,12 @@ typedef struct {
   double gamma;     /* ratio of specific heats (1.4), Eq. (e:navier) */
   double mu;        /* constant dynamic viscosity, Eq. (e:navier) */
   double Pr;        /* Prandtl number (0.72); heat flux alpha = gamma mu / Pr */
-  double dt;        /* constant RK4 time step */
+  double dt;        /* constant time step */
   int precision;    /* NS_FP64 or NS_MIXED */
   int plane_i;      /* objective plane = x-face between cell columns plane_i-1, plane_i */
   double pt_in;     /* reference stagnation pressure p_t,in of Eq. (e:pressure_loss) */
+  int scheme;       /* NS_RK4 or NS_SSPRK3: the explicit Runge-Kutta method of every step,
+                       its tangent and its discrete adjoint */
 } ns_params;
 
 typedef struct ns_ctx ns_ctx;
@@ -89,20 +99,21 @@ int ns_rhs_tangent(ns_ctx* ctx, const double* w, const double* wd, double* Rd);
 int ns_rhs_transpose(ns_ctx* ctx, const double* w, const double* a, const float* nu,
                      double* out);
 
-/* w_out = RK4 step of w_in with source s (may be NULL).  w_out must not alias w_in. */
+/* w_out = one step (RK4 or SSP-RK3, ns_params.scheme) of w_in with source s (may be
+ * NULL).  w_out must not alias w_in. */
 int ns_primal_step(ns_ctx* ctx, const double* w_in, const double* s, double* w_out);
 
-/* Tangent of one RK4 step (FP64): wd_out = d(w^{n+1})/d(w^n) wd_in + d/ds sd.
+/* Tangent of one step (FP64): wd_out = d(w^{n+1})/d(w^n) wd_in + d/ds sd.
  * s is the primal source (may be NULL), sd its perturbation (may be NULL). */
 int ns_tangent_step(ns_ctx* ctx, const double* w_n, const double* s, const double* wd_in,
                     const double* sd, double* wd_out);
 
-/* Discrete adjoint of one RK4 step ("Implementation": the adjoint of the discrete
+/* Discrete adjoint of one step ("Implementation": the adjoint of the discrete
  * scheme, with the primal stage states recomputed from w_n):
  *   lam_n = (d w^{n+1} / d w^n)^T lam_np1
- * nu: per-cell added adjoint viscosity (NULL = none), applied in each of the four
- *     stage products.
- * sbar_acc: if not NULL, sbar_acc += sum of the four stage seeds; the source
+ * nu: per-cell added adjoint viscosity (NULL = none), applied in each of the stage
+ *     products.
+ * sbar_acc: if not NULL, sbar_acc += sum of the stage seeds; the source
  *     sensitivity dJ/ds of a time-constant source is the final sbar_acc.
  * lam_n must not alias lam_np1 or w_n. */
 int ns_adjoint_step(ns_ctx* ctx, const double* w_n, const double* s, const double* lam_np1,
@@ -122,8 +133,9 @@ int ns_growth_sigma1(ns_ctx* ctx, const double* w, float* sigma1, double* stats)
 
 /* nu = lambda * sigma_1 where sigma_1 > tau, else 0 (section "Energy analysis":
  * the lambda sigma_1 coefficient; tau = 0 is the paper's rule).  lambda has units of
- * length^2.  If dt * nu * sum_d 4/dx_d^2 exceeds the RK4 real-axis limit 2.78 in any
- * cell, NS_ERR_UNSTABLE is set in the sticky error word. */
+ * length^2.  If dt * nu * sum_d 4/dx_d^2 exceeds the scheme's real-axis stability limit
+ * (2.78 for RK4, 2.51 for SSP-RK3) in any cell, NS_ERR_UNSTABLE is set in the sticky
+ * error word. */
 int ns_add_adjoint_viscosity(ns_ctx* ctx, const float* sigma1, double lambda, double tau,
                              float* nu);
 
@@ -312,6 +324,11 @@ int ns_label_target(ns_ctx* ctx, const float* acc, const float* sigma1, double t
  * (NS_OK, NS_ERR_NONFINITE or NS_ERR_UNSTABLE). */
 int ns_last_error(ns_ctx* ctx);
 const char* ns_error_string(int code);
+
+/* Number of CUDA kernels this library has launched in this process, over all contexts
+ * (monotone; host-side count, no device synchronisation).  The paper has no
+ * counterpart: it lets a caller state how many kernels a region of its own launched. */
+unsigned long long ns_launch_count(void);
 
 #ifdef __cplusplus
 }

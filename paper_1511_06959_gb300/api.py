@@ -22,6 +22,8 @@ NS_ERR_UNSTABLE = -4
 NS_ERR_CUDA = -5
 NS_FP64 = 0
 NS_MIXED = 1
+NS_RK4 = 0
+NS_SSPRK3 = 1
 
 EXPORTED = [
     "ns_create", "ns_destroy", "ns_set_stream", "ns_set_dt", "ns_workspace_bytes", "ns_rhs",
@@ -32,6 +34,7 @@ EXPORTED = [
     "ns_profile_read", "ns_to_float", "ns_forward_run", "ns_backward_run", "ns_scale_boxes",
     "ns_dot_boxes", "ns_mlp_net_bytes", "ns_mlp_set_params", "ns_mlp_get_params", "ns_mlp_get_moment",
     "ns_mlp_features", "ns_mlp_infer", "ns_mlp_train_step", "ns_adjoint_label", "ns_label_target",
+    "ns_launch_count",
 ]
 
 NS_MLP_PARAMS = 5185
@@ -48,7 +51,7 @@ class NsParams(ctypes.Structure):
         ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double),
         ("gamma", ctypes.c_double), ("mu", ctypes.c_double), ("Pr", ctypes.c_double),
         ("dt", ctypes.c_double), ("precision", ctypes.c_int), ("plane_i", ctypes.c_int),
-        ("pt_in", ctypes.c_double),
+        ("pt_in", ctypes.c_double), ("scheme", ctypes.c_int),
     ]
 
 
@@ -120,6 +123,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "ns_label_target": ([P, P, P, D, P], I),
         "ns_last_error": ([P], I),
         "ns_error_string": ([I], ctypes.c_char_p),
+        "ns_launch_count": ([], ctypes.c_ulonglong),
         "ns_plan": ([I, I, I, P, I, ctypes.POINTER(I), ctypes.POINTER(I),
                      ctypes.POINTER(ctypes.c_longlong)], I),
         "ns_run_arena_bytes": ([P, ctypes.POINTER(NsRunOpts)], S),
@@ -177,11 +181,12 @@ class Solver:
     physical parameters, precision and time step."""
 
     def __init__(self, nx, ny, nz, dx, gamma=1.4, mu=0.0, Pr=0.72, dt=0.0, precision=NS_FP64,
-                 plane_i=0, pt_in=1.0, batch=1, stream=None):
+                 plane_i=0, pt_in=1.0, batch=1, stream=None, scheme=NS_RK4):
         self.lib = _lib()
         d = dx if isinstance(dx, (tuple, list)) else (dx, dx, dx)
         self.params = NsParams(nx, ny, nz, batch, d[0], d[1], d[2], gamma, mu, Pr, dt,
-                               precision, plane_i, pt_in)
+                               precision, plane_i, pt_in, scheme)
+        self.nstages = 3 if scheme == NS_SSPRK3 else 4
         self.shape = (batch, 5, nz, ny, nx)
         self.cells = nx * ny * nz
         self.batch = batch
@@ -374,6 +379,11 @@ class Solver:
         n = ctypes.c_longlong()
         _check(self.lib.ns_profile_read(self._ctx, ctypes.byref(ms), ctypes.byref(n)), "ns_profile_read")
         return ms.value, n.value
+
+
+def launch_count() -> int:
+    """Kernels this library has launched in this process (ns_launch_count)."""
+    return int(_lib().ns_launch_count())
 
 
 def mlp_net_bytes() -> int:

@@ -1,4 +1,4 @@
-// Transposed residual Jacobian, fused into one stage of the RK4 discrete adjoint
+// Transposed residual Jacobian, fused into one stage of the Runge-Kutta discrete adjoint
 // (section "Unsteady adjoint": the A_kji, A^v_kji, D_kjil terms; "Implementation":
 // the adjoint of the discrete scheme; "Energy analysis": the added viscosity).
 //
@@ -18,7 +18,9 @@
 //
 // Epilogue: the four stage products are summed in the stage type (G = sum_i g_i) and
 // only the last stage forms lam^n = lam^{n+1} + G in FP64 (one FP64 add per component
-// and step); the next seed is Anext = cl lam^{n+1} + cg g; the seeds a_i are summed
+// and step); the next seed is Anext = cl lam^{n+1} + cg g + cs G (the G term carries the
+// earlier stages' products that a tableau with two nonzero entries in a column needs,
+// as SSP-RK3's first stage does); the seeds a_i are summed
 // the same way for the source sensitivity.
 #include <type_traits>
 
@@ -488,7 +490,7 @@ __global__ void __launch_bounds__(NT, AdjMinBlocks<CT>::value) k_adj_stage(GridD
         const CT gs = gin[v] + gout[v];
         if (a.Gout) a.Gout[o] = gs;
         if (a.lam_out) a.lam_out[o] = (a.lam_in ? a.lam_in[o] : 0.0) + widen(gs);
-        if (a.Anext) a.Anext[o] = CT(a.cl) * lfv[v] + CT(a.cg) * gout[v];
+        if (a.Anext) a.Anext[o] = CT(a.cl) * lfv[v] + CT(a.cg) * gout[v] + CT(a.cs) * gs;
         if (a.SBout || a.sbar) {
           const CT ss = (a.SBin ? a.SBin[o] : CT(0)) + A0[v * SP + ic];
           if (a.SBout) a.SBout[o] = ss;
@@ -522,6 +524,7 @@ cudaError_t launch_adj_stage(const GridDesc& g, const Coef<CT>& c, const AdjArgs
   cudaError_t e = shape.get(kern, smem, g, "NS_ADJ_CTAS", ctas);
   if (e != cudaSuccess) return e;
   kern<<<ctas, NT, smem, st>>>(g, c, a);
+  count_launch();
   return cudaGetLastError();
 }
 

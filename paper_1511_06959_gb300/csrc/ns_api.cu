@@ -1,5 +1,6 @@
 // C-ABI entry points (include/ns_adjoint.h): argument checks, workspace ownership and
-// the sequencing of the fused stage kernels into RK4 primal, tangent and adjoint steps.
+// the sequencing of the fused stage kernels into Runge-Kutta (RK4, SSP-RK3) primal,
+// tangent and adjoint steps.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdlib.h>
@@ -59,29 +60,68 @@ static int ensure_tangent_buffers(ns_ctx* c) {
   return NS_OK;
 }
 
-// RK4 with the increment sum D = dt (k1/6 + k2/3 + k3/3 + k4/6) in the stage type and
-// one FP64 add w^{n+1} = w^n + D at the last stage.  keep (may be null): buffers that
-// receive the stage states W2, W3, W4 of this step; wo_mirror (may be null): receives
-// w^{n+1} rounded to the stage type.
+// Explicit Runge-Kutta tableaux in the increment-sum form the stage kernels use.  Stage
+// i (0-based) evaluates k_i = R(W_i), adds dt b_i k_i to the increment sum D, and forms
+// the next stage state W_{i+1} = w + dt cout_i k_i + cd_i D.  The adjoint runs the stages
+// backwards (launch j = 0 is the last stage): the seed of the last stage is dt ca0 lam,
+// and launch j < ns-1 forms the seed of the stage before it as
+// dt (cl_j lam + cg_j g + cs_j G), G the sum of the products g of the launches so far
+// (the transpose of a_{i+1,i} g_{i+1} + sum_{m>i+1} a_{m,i} g_m).  limit: the step's
+// stability interval on the negative real axis (for the added adjoint viscosity).
+struct Scheme {
+  int ns;
+  double b[4], cout[4], cd[4];
+  double ca0, cl[3], cg[3], cs[3];
+  double limit;
+  bool needs_sum() const { return cd[0] != 0 || cd[1] != 0 || cd[2] != 0 || cd[3] != 0; }
+};
+
+// classical RK4: W2 = w + dt/2 k1, W3 = w + dt/2 k2, W4 = w + dt k3, b = (1,2,2,1)/6
+static const Scheme kRK4 = {4,
+                            {1.0 / 6, 1.0 / 3, 1.0 / 3, 1.0 / 6},
+                            {0.5, 0.5, 1.0, 0.0},
+                            {0, 0, 0, 0},
+                            1.0 / 6,
+                            {1.0 / 3, 1.0 / 3, 1.0 / 6},
+                            {1.0, 0.5, 0.5},
+                            {0, 0, 0},
+                            2.78};
+// SSP-RK3 (section "Numerical methods"): the Shu-Osher stages in tableau form,
+// W2 = w + dt k1, W3 = w + dt/4 (k1 + k2) = w + 3/2 D, b = (1, 1, 4)/6; adjoint seeds
+// a3 = 2/3 dt lam, a2 = dt (lam/6 + g3/4), a1 = dt (lam/6 + g2 + g3/4)
+static const Scheme kSSPRK3 = {3,
+                               {1.0 / 6, 1.0 / 6, 2.0 / 3, 0},
+                               {1.0, 0.0, 0.0, 0.0},
+                               {0, 1.5, 0, 0},
+                               2.0 / 3,
+                               {1.0 / 6, 1.0 / 6, 0},
+                               {0.25, 0.75, 0},
+                               {0, 0.25, 0},
+                               2.51};
+
+static const Scheme& scheme_of(const ns_ctx* c) { return c->p.scheme == NS_SSPRK3 ? kSSPRK3 : kRK4; }
+
+// One step with the increment sum D in the stage type and one FP64 add
+// w^{n+1} = w^n + D at the last stage.  keep (may be null): buffers that receive the
+// stage states W2..W_ns of this step; wo_mirror (may be null): receives w^{n+1} rounded
+// to the stage type.
 template <class CT>
 static int primal_step_t(ns_ctx* c, const Coef<CT>& cf, const CT* W1, const double* w, const double* s,
                          double* wo, CT* wo_mirror = nullptr, CT* const* keep = nullptr) {
+  const Scheme& sc = scheme_of(c);
   const double dt = c->p.dt;
-  CT* Wa = keep ? keep[0] : buf<CT>(c, W2);
-  CT* Wb = keep ? keep[1] : buf<CT>(c, W3);
-  CT* Wc = keep ? keep[2] : Wa;
   CT* D = buf<CT>(c, GS);
-  const CT* in[4] = {W1, Wa, Wb, Wc};
-  CT* outs[4] = {Wa, Wb, Wc, nullptr};
-  const double cacc[4] = {dt / 6.0, dt / 3.0, dt / 3.0, dt / 6.0};
-  const double cout[4] = {0.5 * dt, 0.5 * dt, dt, 0.0};
-  for (int i = 0; i < 4; ++i) {
+  const CT* in = W1;
+  for (int i = 0; i < sc.ns; ++i) {
+    const bool last = i == sc.ns - 1;
+    CT* out = last ? nullptr : (keep ? keep[i] : buf<CT>(c, i % 2 == 0 ? W2 : W3));
     ns::StageArgs<CT, CT> a{};
-    a.W = in[i]; a.base = W1; a.src = s;
-    a.dacc = D; a.dacc_init = i == 0; a.cacc = cacc[i];
-    a.Wout = outs[i]; a.cout = cout[i];
-    if (i == 3) { a.wbase = w; a.wout = wo; a.wout_mirror = wo_mirror; }
+    a.W = in; a.base = W1; a.src = s;
+    a.dacc = D; a.dacc_init = i == 0; a.cacc = sc.b[i] * dt;
+    a.Wout = out; a.cout = sc.cout[i] * dt; a.cd = sc.cd[i];
+    if (last) { a.wbase = w; a.wout = wo; a.wout_mirror = wo_mirror; }
     if (ns::launch_rhs_stage<CT, CT, CT>(c->g, cf, a, c->st) != cudaSuccess) return NS_ERR_CUDA;
+    in = out;
   }
   return NS_OK;
 }
@@ -105,12 +145,14 @@ static cudaError_t adj_launch(ns_ctx* c, const Coef<CT>& cf, const ns::AdjArgs<T
   return e;
 }
 
-// Recompute W2..W4 from W1 = w^n, then the transposed stages 4, 3, 2, 1 with the
-// stage products summed in the stage type and lam^n = lam^{n+1} + G formed in FP64.
+// Recompute the stage states W2..W_ns from W1 = w^n (unless kept), then the transposed
+// stages last to first with the stage products summed in the stage type and
+// lam^n = lam^{n+1} + G formed in FP64.
 template <class CT>
 static int adjoint_step_t(ns_ctx* c, const Coef<CT>& cf, const CT* W1, const CT* lamf, const double* s,
                           const double* lam, const float* nu, double* lo, double* sbar,
                           const CT* const* kept = nullptr) {
+  const Scheme& sc = scheme_of(c);
   const double dt = c->p.dt;
   const CT* Wst[3];
   CT* Aa = buf<CT>(c, AA);
@@ -119,44 +161,43 @@ static int adjoint_step_t(ns_ctx* c, const Coef<CT>& cf, const CT* W1, const CT*
   CT* S = buf<CT>(c, SB);
   if (kept) {
     // stage states kept by the replay of this step
-    Wst[0] = kept[0];
-    Wst[1] = kept[1];
-    Wst[2] = kept[2];
+    for (int i = 0; i < sc.ns - 1; ++i) Wst[i] = kept[i];
   } else {
-    CT* Wr[3] = {buf<CT>(c, W2), buf<CT>(c, W3), buf<CT>(c, W4)};
-    const CT* rin[3] = {W1, Wr[0], Wr[1]};
-    const double rc[3] = {0.5 * dt, 0.5 * dt, dt};
-    for (int i = 0; i < 3; ++i) {
+    // G doubles as the increment sum of the recompute when the tableau needs it
+    const int wb[3] = {W2, W3, W4};
+    const CT* in = W1;
+    for (int i = 0; i < sc.ns - 1; ++i) {
+      CT* out = buf<CT>(c, wb[i]);
       ns::StageArgs<CT, CT> a{};
-      a.W = rin[i]; a.base = W1; a.src = s; a.Wout = Wr[i]; a.cout = rc[i];
+      a.W = in; a.base = W1; a.src = s; a.Wout = out; a.cout = sc.cout[i] * dt; a.cd = sc.cd[i];
+      if (sc.needs_sum()) { a.dacc = G; a.dacc_init = i == 0; a.cacc = sc.b[i] * dt; }
       if (ns::launch_rhs_stage<CT, CT, CT>(c->g, cf, a, c->st) != cudaSuccess) return NS_ERR_CUDA;
+      Wst[i] = out;
+      in = out;
     }
-    Wst[0] = Wr[0];
-    Wst[1] = Wr[1];
-    Wst[2] = Wr[2];
   }
-  const CT* Wi[4] = {Wst[2], Wst[1], Wst[0], W1};
-  const CT* Ain[4] = {lamf, Aa, Ab, Aa};
-  CT* Aout[4] = {Aa, Ab, Aa, nullptr};
-  const double ca[4] = {dt / 6.0, 1.0, 1.0, 1.0};
-  const double cl[4] = {dt / 3.0, dt / 3.0, dt / 6.0, 0.0};
-  const double cg[4] = {dt, 0.5 * dt, 0.5 * dt, 0.0};
-  for (int i = 0; i < 4; ++i) {
+  const CT* Ain = lamf;
+  for (int j = 0; j < sc.ns; ++j) {
+    const bool last = j == sc.ns - 1;
+    CT* Aout = last ? nullptr : (j % 2 == 0 ? Aa : Ab);
     ns::AdjArgs<CT, CT, CT> a{};
-    a.W = Wi[i]; a.A = Ain[i]; a.ca = ca[i]; a.nu = nu; a.lamf = lamf;
-    a.Gin = i == 0 ? nullptr : G;
-    a.Anext = Aout[i]; a.cl = cl[i]; a.cg = cg[i];
-    if (i < 3) {
+    a.W = last ? W1 : Wst[sc.ns - 2 - j];
+    a.A = Ain; a.ca = j == 0 ? sc.ca0 * dt : 1.0; a.nu = nu; a.lamf = lamf;
+    a.Gin = j == 0 ? nullptr : G;
+    a.Anext = Aout;
+    if (!last) { a.cl = sc.cl[j] * dt; a.cg = sc.cg[j] * dt; a.cs = sc.cs[j] * dt; }
+    if (!last) {
       a.Gout = G;
     } else {
       a.lam_in = lam;
       a.lam_out = lo;
     }
     if (sbar) {
-      a.SBin = i == 0 ? nullptr : S;
-      if (i < 3) a.SBout = S; else a.sbar = sbar;
+      a.SBin = j == 0 ? nullptr : S;
+      if (!last) a.SBout = S; else a.sbar = sbar;
     }
     if (adj_launch(c, cf, a) != cudaSuccess) return NS_ERR_CUDA;
+    Ain = Aout;
   }
   return NS_OK;
 }
@@ -183,6 +224,7 @@ int ns_create(const ns_params* p, void* stream, ns_ctx** out) {
       !(p->Pr > 0) || !(p->dt >= 0))
     return NS_ERR_ARG;
   if (p->precision != NS_FP64 && p->precision != NS_MIXED) return NS_ERR_ARG;
+  if (p->scheme != NS_RK4 && p->scheme != NS_SSPRK3) return NS_ERR_ARG;
   if ((long long)p->nx * p->ny > (1LL << 31) || (long long)p->nx * p->ny * p->nz > (1LL << 40))
     return NS_ERR_ARG;
   ns_ctx* c = new ns_ctx();
@@ -298,23 +340,24 @@ int ns_tangent_step(ns_ctx* c, const double* w, const double* s, const double* w
   if (!c || !w || !wd || !wdo || wdo == wd || wdo == w) return NS_ERR_ARG;
   int r = ensure_tangent_buffers(c);
   if (r) return r;
+  const Scheme& sc = scheme_of(c);
   const double dt = c->p.dt;
   double *Wa = c->tan[0], *Wb = c->tan[1], *Wda = c->tan[2], *Wdb = c->tan[3], *D = c->tan[4],
          *Dd = c->tan[5];
-  const double* Win[4] = {w, Wa, Wb, Wa};
-  const double* Wdin[4] = {wd, Wda, Wdb, Wda};
-  double* Wout[4] = {Wa, Wb, Wa, nullptr};
-  double* Wdout[4] = {Wda, Wdb, Wda, nullptr};
-  const double cacc[4] = {dt / 6.0, dt / 3.0, dt / 3.0, dt / 6.0};
-  const double cout[4] = {0.5 * dt, 0.5 * dt, dt, 0.0};
-  for (int i = 0; i < 4; ++i) {
+  const double *in = w, *ind = wd;
+  for (int i = 0; i < sc.ns; ++i) {
+    const bool last = i == sc.ns - 1;
+    double* out = last ? nullptr : (i % 2 == 0 ? Wa : Wb);
+    double* outd = last ? nullptr : (i % 2 == 0 ? Wda : Wdb);
     ns::StageArgs<double, double> a{};
-    a.W = Win[i]; a.Wd = Wdin[i];
+    a.W = in; a.Wd = ind;
     a.base = w; a.based = wd; a.src = s; a.srcd = sd;
-    a.dacc = D; a.daccd = Dd; a.dacc_init = i == 0; a.cacc = cacc[i];
-    a.Wout = Wout[i]; a.Woutd = Wdout[i]; a.cout = cout[i];
-    if (i == 3) { a.wbased = wd; a.woutd = wdo; }
+    a.dacc = D; a.daccd = Dd; a.dacc_init = i == 0; a.cacc = sc.b[i] * dt;
+    a.Wout = out; a.Woutd = outd; a.cout = sc.cout[i] * dt; a.cd = sc.cd[i];
+    if (last) { a.wbased = wd; a.woutd = wdo; }
     if (ns::launch_rhs_stage<Dual, double, double>(c->g, c->cx, a, c->st) != cudaSuccess) return NS_ERR_CUDA;
+    in = out;
+    ind = outd;
   }
   return NS_OK;
 }
@@ -369,7 +412,7 @@ int ns_growth_sigma1(ns_ctx* c, const double* w, float* sigma1, double* stats) {
 static double nu_limit(const ns_ctx* c) {
   const double k = 4.0 * (1.0 / (c->p.dx * c->p.dx) + 1.0 / (c->p.dy * c->p.dy) +
                           (c->p.nz > 1 ? 1.0 / (c->p.dz * c->p.dz) : 0.0));
-  return c->p.dt > 0 ? 2.78 / (c->p.dt * k) : INFINITY;
+  return c->p.dt > 0 ? scheme_of(c).limit / (c->p.dt * k) : INFINITY;
 }
 
 int ns_add_adjoint_viscosity(ns_ctx* c, const float* sigma1, double lambda, double tau, float* nu) {
@@ -482,6 +525,8 @@ int ns_max_wave_speed(ns_ctx* c, const double* w, double* out) {
   if (!c || !w || !out) return NS_ERR_ARG;
   return cuerr(ns::launch_max_wave(c->g, c->p.gamma, w, out, c->scratch, c->st));
 }
+
+unsigned long long ns_launch_count(void) { return ns::g_launches.load(std::memory_order_relaxed); }
 
 int ns_last_error(ns_ctx* c) {
   if (!c) return NS_ERR_ARG;

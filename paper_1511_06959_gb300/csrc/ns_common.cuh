@@ -18,7 +18,13 @@
 #include <stdint.h>
 #include <stdlib.h>
 
+#include <atomic>
+
 namespace ns {
+
+// Process-wide count of this library's kernel launches (read by ns_launch_count).
+inline std::atomic<unsigned long long> g_launches{0};
+inline void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 constexpr int TX = 32;
 constexpr int TY = 4;

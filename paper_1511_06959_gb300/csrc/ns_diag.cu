@@ -746,11 +746,14 @@ cudaError_t launch_objective(const GridDesc& g, double gamma, int plane_i, doubl
   if (nblk > RG) nblk = RG;
   double* nd = scratch + (size_t)2 * RG * g.batch;
   k_obj_partial<<<dim3(nblk, g.batch), OB, 0, st>>>(g, gamma, plane_i, pt_in, w, scratch);
+  count_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_obj_final<<<g.batch, RB, 0, st>>>(nblk, pt_in, weight, scratch, nd, J_acc, err);
+  count_launch();
   if ((e = cudaGetLastError()) != cudaSuccess || !lam) return e;
   k_obj_grad<<<dim3(nblk, g.batch), OB, 0, st>>>(g, gamma, plane_i, pt_in, weight, w, nd, lam);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -765,10 +768,12 @@ cudaError_t launch_objective_fast(const GridDesc& g, double gamma, int plane_i, 
   double* aface = ndsc + 2 * (size_t)g.batch;
   k_obj_sum<<<dim3(nblk, g.batch), OMB, 0, st>>>(g, gamma, plane_i, pt_in, w, weight, J_acc, lam != nullptr, err,
                                                  partial, aface, ndsc, ticket);
+  count_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || !lam) return e;
   const long long n = (long long)nf * g.batch;
   k_obj_scatter<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(g, plane_i, aface, ndsc, lam);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -777,9 +782,11 @@ cudaError_t launch_sigma1(const GridDesc& g, const Coef<CT>& c, const CT* w, flo
                           double* stats, double* scratch, cudaStream_t st) {
   dim3 grid(RGS, g.batch);
   k_sigma1<CT><<<grid, RB, 0, st>>>(g, c, w, sigma1, scratch);
+  count_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || !stats) return e;
   k_sigma1_stats<<<g.batch, RB, 0, st>>>(RGS, 1.0 / (double)g.cells, scratch, stats);
+  count_launch();
   return cudaGetLastError();
 }
 template cudaError_t launch_sigma1<double>(const GridDesc&, const Coef<double>&, const double*, float*,
@@ -792,6 +799,7 @@ cudaError_t launch_label(const GridDesc& g, const Coef<CT>& c, const CT* w, cons
                          cudaStream_t st) {
   const long long n = g.cells * g.batch;
   k_label<CT><<<(unsigned)((n + RB - 1) / RB), RB, 0, st>>>(g, c, w, lam, acc);
+  count_launch();
   return cudaGetLastError();
 }
 template cudaError_t launch_label<double>(const GridDesc&, const Coef<double>&, const double*, const double*,
@@ -804,6 +812,7 @@ cudaError_t launch_nu_rule(const GridDesc& g, const float* sigma1, double lambda
   const long long n = g.cells * g.batch;
   k_nu_rule<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, sigma1, (float)lambda, (float)tau,
                                                            (float)limit_nu, nu, err);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -811,6 +820,7 @@ cudaError_t launch_visc_apply(const GridDesc& g, const double* idx2, const float
                               double* out, cudaStream_t st) {
   const long long n = g.cells * g.batch;
   k_visc_apply<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g, idx2[0], idx2[1], idx2[2], nu, a, out);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -822,9 +832,11 @@ cudaError_t launch_energy(const GridDesc& g, double gamma, double dV, const doub
     k_energy<float><<<grid, RB, 0, st>>>(g, gamma, w, lam, scratch);
   else
     k_energy<double><<<grid, RB, 0, st>>>(g, gamma, w, lam, scratch);
+  count_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_sum_partials<<<g.batch, RB, 0, st>>>(RGS, dV, scratch, E, err);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -832,24 +844,29 @@ cudaError_t launch_dot(const double* a, const double* phi, int nphi, size_t n, d
                        double* scratch, cudaStream_t st) {
   dim3 grid(RG, nphi);
   k_dot<<<grid, RB, 0, st>>>(a, phi, n, scratch);
+  count_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_sum_partials<<<nphi, RB, 0, st>>>(RG, 1.0, scratch, out, nullptr);
+  count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_combine(const double* theta, const double* phi, int nphi, size_t n, double* s,
                            cudaStream_t st) {
   k_combine<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(theta, phi, nphi, n, s);
+  count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_max_wave(const GridDesc& g, double gamma, const double* w, double* out,
                             double* scratch, cudaStream_t st) {
   k_max_wave<<<RG, RB, 0, st>>>(g, gamma, w, scratch);
+  count_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_max_partials<<<1, RB, 0, st>>>(RG, scratch, out);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -859,15 +876,18 @@ namespace ns {
 cudaError_t launch_scale_boxes(const GridDesc& g, const double* seed, double* field, cudaStream_t st) {
   const long long tot = g.cells * 5 * g.batch;
   k_scale_boxes<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(g, seed, field);
+  count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_dot_boxes(const GridDesc& g, const double* field, int comp, const double* phi, int nphi,
                              double* out, double* scratch, cudaStream_t st) {
   k_dot_boxes<<<dim3(RG, nphi), RB, 0, st>>>(g, field, comp, phi, scratch);
+  count_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_sum_partials<<<nphi, RB, 0, st>>>(RG, 1.0, scratch, out, nullptr);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -878,6 +898,7 @@ size_t objective_scratch_doubles(const GridDesc& g) {
 cudaError_t launch_to_float(const double* in, float* out, size_t n, cudaStream_t st) {
   const size_t threads = (n + 1) / 2;
   k_to_float<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(in, out, n);
+  count_launch();
   return cudaGetLastError();
 }
 }  // namespace ns

@@ -8,9 +8,9 @@
 
 namespace ns {
 
-// Fused RK4 stage of the primal (see ns_rhs.cu).  With R = R(W) + src:
+// Fused Runge-Kutta stage of the primal (see ns_rhs.cu).  With R = R(W) + src:
 //   dacc = (dacc_init ? 0 : dacc) + cacc R        increment sum, stage type
-//   Wout = base + cout R                           next stage state, stage type
+//   Wout = base + cout R + cd dacc                 next stage state, stage type
 //   wout = (wbase or 0) + widen(dacc + cacc R)     final state, FP64 (when wout != 0)
 //   wout_mirror = wout rounded to the stage type    (when wout_mirror != 0)
 template <class TIN, class TST>
@@ -28,6 +28,7 @@ struct StageArgs {
   TST* Wout;
   double* Woutd;
   double cout;
+  double cd;              // Wout also adds cd times the updated increment sum
   const double* wbase;
   const double* wbased;
   double* wout;
@@ -39,7 +40,7 @@ struct StageArgs {
 //   g     = (dR/dw)(W)^T a + L_nu a
 //   Gout  = (Gin or 0) + g                              stage-product sum, stage type
 //   lam_out = (lam_in or 0) + widen((Gin or 0) + g)     FP64 (when lam_out != 0)
-//   Anext = cl*lamf + cg*g                              next stage seed
+//   Anext = cl*lamf + cg*g + cs*(Gin + g)              next stage seed
 //   SBout = (SBin or 0) + a;  sbar += widen((SBin or 0) + a)   source seeds
 template <class TIN, class TA, class TST>
 struct AdjArgs {
@@ -51,7 +52,7 @@ struct AdjArgs {
   const TST* Gin;
   TST* Gout;
   TST* Anext;
-  double cl, cg;
+  double cl, cg, cs;      // Anext = cl lamf + cg g + cs (Gin + g)
   const double* lam_in;
   double* lam_out;
   const TST* SBin;

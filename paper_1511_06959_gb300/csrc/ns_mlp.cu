@@ -435,6 +435,7 @@ __global__ void k_label_target(long long n, const float* __restrict__ acc, const
 cudaError_t launch_label_target(long long n, const float* acc, const float* sig, double dx2, double tmax,
                                 float* t, cudaStream_t st) {
   k_label_target<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, acc, sig, (float)dx2, (float)tmax, t);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -456,9 +457,11 @@ MlpView mlp_view(void* blob) {
 cudaError_t launch_box_means(const GridDesc& g, double gamma, const double* w, double* qbar, double* scratch,
                              cudaStream_t st) {
   k_box_means<<<dim3(RGM, g.batch), RB, 0, st>>>(g, (float)gamma, w, scratch);
+  count_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_box_means_final<<<g.batch * 5, RB, 0, st>>>(RGM, 1.0 / (double)g.cells, scratch, qbar);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -468,6 +471,7 @@ cudaError_t launch_features(const GridDesc& g, const Coef<float>& c, const doubl
                             float* feat, cudaStream_t st) {
   const long long n = g.cells * g.batch;
   k_features<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g, c, w, qbar, feat);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -479,6 +483,7 @@ cudaError_t launch_mlp_infer(long long n, void* blob, const float* feat, const f
   if (blocks < 1) blocks = 1;
   k_mlp_infer<<<(unsigned)blocks, 256, 0, st>>>(n, mlp_view(blob), feat, sigma1, (float)scale, (float)limit_nu,
                                                 nu, err);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -497,23 +502,29 @@ cudaError_t launch_mlp_train_step(void* blob, const float* feat, const float* ta
   cudaError_t e = cudaFuncSetAttribute(k_mlp_train_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k_mlp_train_partial<<<nblk, TT, smem, st>>>(v, feat, target, idx, n, partial, lp);
+  count_launch();
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (loss) {
     k_loss_sum<<<1, 256, 0, st>>>(nblk * TS, n, lp, loss);
+    count_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   k_mlp_adam<<<(NPAR + 255) / 256, 256, 0, st>>>(nblk, v, partial, step, (float)lr, 0.9f, 0.999f, 1e-8f);
+  count_launch();
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   k_mlp_publish<<<(NH * NH + 255) / 256, 256, 0, st>>>(v);
+  count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_mlp_set(void* blob, const float* params, cudaStream_t st) {
   MlpView v = mlp_view(blob);
   k_mlp_reset<<<(NPAR + 255) / 256, 256, 0, st>>>(v, params);
+  count_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_mlp_publish<<<(NH * NH + 255) / 256, 256, 0, st>>>(v);
+  count_launch();
   return cudaGetLastError();
 }
 

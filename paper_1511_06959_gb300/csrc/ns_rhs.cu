@@ -1,4 +1,4 @@
-// Primal residual and fused RK4 stage kernel (Eq. e:navier, Eq. e:vector).
+// Primal residual and fused Runge-Kutta stage kernel (Eq. e:navier, Eq. e:vector).
 //
 // R(w)_c = -sum_d (Phi_d(c+1/2) - Phi_d(c-1/2)) / dx_d + s_c with the face flux
 // Phi = (F_L + F_R)/2 - F^v(face).  F^v uses the compact normal difference and the
@@ -10,10 +10,10 @@
 // compute the tile's upper x/y boundary faces; the z-face below is carried in
 // registers from the previous plane.  Each face flux is thus evaluated once per tile.
 //
-// Epilogue (fused RK4 update): the stage increments are summed in the stage type,
+// Epilogue (fused Runge-Kutta update): the stage increments are summed in the stage type,
 // dacc = sum_i b_i dt k_i, and only the final stage forms w^{n+1} = w^n + dacc in FP64,
 // one FP64 add per component and step:
-//   dacc = (dacc_init ? 0 : dacc) + cacc R,   Wout = base + cout R,
+//   dacc = (dacc_init ? 0 : dacc) + cacc R,   Wout = base + cout R + cd dacc,
 //   wout = wbase + widen(dacc + cacc R).
 // The same template instantiated on ns::Dual gives the tangent (dR/dw) wd.
 #include <type_traits>
@@ -314,8 +314,8 @@ __global__ void __launch_bounds__(NT, RhsMinBlocks<CT>::value) k_rhs_stage(GridD
           if (a.woutd) a.woutd[o] = (a.wbased ? a.wbased[o] : 0.0) + dd;
           else if (a.daccd) a.daccd[o] = dd;
           if (a.Wout) {
-            a.Wout[o] = a.base[o] + a.cout * Rv;
-            if (a.Woutd) a.Woutd[o] = a.based[o] + a.cout * Rd;
+            a.Wout[o] = a.base[o] + a.cout * Rv + a.cd * dv;
+            if (a.Woutd) a.Woutd[o] = a.based[o] + a.cout * Rd + a.cd * dd;
           }
         } else {
           const CT Rv = R + e_src[v];
@@ -328,7 +328,7 @@ __global__ void __launch_bounds__(NT, RhsMinBlocks<CT>::value) k_rhs_stage(GridD
           } else if (a.dacc) {
             a.dacc[o] = dv;
           }
-          if (a.Wout) a.Wout[o] = e_base[v] + CT(a.cout) * Rv;
+          if (a.Wout) a.Wout[o] = e_base[v] + CT(a.cout) * Rv + CT(a.cd) * dv;
         }
       }
     }
@@ -355,6 +355,7 @@ cudaError_t launch_rhs_stage(const GridDesc& g, const Coef<CT>& c, const StageAr
   cudaError_t e = shape.get(kern, smem, g, "NS_RHS_CTAS", ctas);
   if (e != cudaSuccess) return e;
   kern<<<ctas, rk::NT, smem, st>>>(g, c, a);
+  count_launch();
   return cudaGetLastError();
 }
 
