@@ -47,6 +47,10 @@ class Params:
     scheme: "rk4" (classical fourth-order Runge-Kutta) or "ssprk3" (the three-stage
     third-order strong-stability-preserving Runge-Kutta method of section "Numerical
     methods", in Shu-Osher form).
+    nu_split: factors of the added adjoint viscosity for the adjoint of rho, of rho u
+    (three components) and of rho E: the separate viscosities per state variable that
+    the conclusion names as a next step; (1, 1, 1) is the single coefficient of section
+    "Energy analysis".
     plane_i: the objective plane is the x-face between cell columns plane_i-1 and
     plane_i.  pt_in: the reference stagnation pressure p_{t,in} of Eq. (e:pressure_loss).
     """
@@ -59,6 +63,7 @@ class Params:
     plane_i: int = 0
     pt_in: float = 1.0
     scheme: str = "rk4"
+    nu_split: tuple = (1.0, 1.0, 1.0)
 
     @property
     def alpha(self) -> float:
@@ -539,12 +544,16 @@ def tangent_run(ws, wd0, P: Params, s=None, sd=None):
 def viscosity_apply(a, nu, P: Params):
     """L_nu a = sum_d [nu_f+ (a(c+e_d) - a(c)) - nu_f- (a(c) - a(c-e_d))] / dx_d^2 for
     every component, nu_f the two-cell mean: the discrete div(nu grad a_i) of the
-    lambda sigma_1 delta_ki delta_jl term."""
+    lambda sigma_1 delta_ki delta_jl term, times the component's factor in P.nu_split."""
     out = np.zeros_like(a)
     for d in range(3):
         nup = 0.5 * (nu + _sh3(nu, d, 1))
         num = 0.5 * (nu + _sh3(nu, d, -1))
         out += (nup * (_sh3(a, d, 1) - a) - num * (a - _sh3(a, d, -1))) / P.dx[d] ** 2
+    f_rho, f_mom, f_en = P.nu_split
+    out[0] *= f_rho
+    out[1:4] *= f_mom
+    out[4] *= f_en
     return out
 
 

@@ -163,3 +163,24 @@ def test_viscosity_operator_symmetric_nsd_and_fourier_eigenvalue():
                       for d in range(3))
     np.testing.assert_allclose(O.viscosity_apply(am, np.full(shp[::-1], c), P), lam_ev * am,
                                rtol=1e-12, atol=1e-12 * abs(lam_ev))
+
+
+def test_viscosity_split_scales_each_state_variable():
+    """Per-variable adjoint viscosity (the conclusion's next step): with factors
+    (f_rho, f_mom, f_en) each adjoint component equals the single-coefficient operator
+    with nu scaled by its own factor, and the operator stays symmetric negative
+    semidefinite for non-negative factors."""
+    w = synth.perturbed_uniform(6, 5, 4, seed=81)
+    P = params_for(w, mu=0.02, dt=2e-3)
+    a = synth.random_field(w.shape, 82)
+    b = synth.random_field(w.shape, 83)
+    nu = np.abs(synth.random_field(w.shape[1:], 84)) * 1e-3
+    f = (0.5, 2.0, 3.0)
+    Ps = params_for(w, mu=0.02, dt=2e-3)
+    Ps.nu_split = f
+    got = O.viscosity_apply(a, nu, Ps)
+    for v, fv in zip(range(5), (f[0], f[1], f[1], f[1], f[2])):
+        ref = O.viscosity_apply(a, fv * nu, P)[v]
+        np.testing.assert_allclose(got[v], ref, rtol=1e-13, atol=1e-13 * np.abs(ref).max())
+    assert O.dot(a, O.viscosity_apply(a, nu, Ps)) <= 0.0
+    assert _rel(O.dot(a, O.viscosity_apply(b, nu, Ps)), O.dot(O.viscosity_apply(a, nu, Ps), b)) < 1e-13
