@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default="box128", choices=sorted(C.WORKLOADS))
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--nu-split", default="1,1,1",
+                    help="added-viscosity factors for the rho, rho u, rho E adjoints")
     ap.add_argument("--scheme", default="rk4", choices=["rk4", "ssprk3"],
                     help="time integrator (the workload's is RK4; ssprk3 is the paper's own)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
@@ -198,6 +200,8 @@ def run_ours(args, wl):
     scheme = api.NS_SSPRK3 if args.scheme == "ssprk3" else api.NS_RK4
     S = api.Solver(wl.nx, wl.ny, wl.nz, wl.dx, gamma=wl.gamma, mu=wl.mu, Pr=wl.Pr, dt=0.0,
                    precision=prec, plane_i=wl.plane_i, pt_in=wl.pt_in, batch=wl.batch, scheme=scheme)
+    split = tuple(float(x) for x in args.nu_split.split(","))
+    S.set_viscosity_split(*split)
     m = torch.empty(1, dtype=torch.float64, device=dev)
     S.max_wave_speed(w0, m)
     dt = C.cfl_dt(wl, m.item())
@@ -299,7 +303,7 @@ def run_ours(args, wl):
             "vs_baseline": None, "dtype": "f32 (f64 accumulate)" if prec == api.NS_MIXED else "f64",
             "data": "synthetic",
             "config": {"workload": C.describe(wl, args.scheme), "name": wl.name, "cells": wl.cells,
-                       "scheme": args.scheme,
+                       "scheme": args.scheme, "nu_split": list(split),
                        "nsteps": wl.nsteps, "schedule": wl.schedule, "param": param,
                        "lambda_tilde": wl.lam_tilde, "precision": args.precision, "dt": dt,
                        "l2": "flushed (256 MB write) between timed steps; arena "
@@ -317,7 +321,7 @@ def run_ours(args, wl):
             "clocks": clocks,
         }
         if not args.no_fp64_compare and prec == api.NS_MIXED:
-            out["fp64"] = fp64_compare(api, torch, wl, w0, dt, sched, param, lam0, Jv, scheme)
+            out["fp64"] = fp64_compare(api, torch, wl, w0, dt, sched, param, lam0, Jv, scheme, split)
         if not args.no_cpu_baseline and ws == 1:
             out["cpu_baseline"] = cpu_baseline(wl, args.scheme)
     return out
@@ -357,12 +361,13 @@ def adj_traffic(wl, precision):
         return None
 
 
-def fp64_compare(api, torch, wl, w0, dt, sched, param, lam_mixed, J_mixed, scheme):
+def fp64_compare(api, torch, wl, w0, dt, sched, param, lam_mixed, J_mixed, scheme, split=(1.0, 1.0, 1.0)):
     """The same checkpointed sweep in FP64 (timed once) and the mixed-precision
     gradient error against it."""
     S = api.Solver(wl.nx, wl.ny, wl.nz, wl.dx, gamma=wl.gamma, mu=wl.mu, Pr=wl.Pr, dt=dt,
                    precision=api.NS_FP64, plane_i=wl.plane_i, pt_in=wl.pt_in, batch=wl.batch,
                    scheme=scheme)
+    S.set_viscosity_split(*split)
     opts = S.run_opts(wl.nsteps, sched, param, wl.lam_coef, 0.0, True, True)
     arena = torch.empty(S.arena_bytes(opts), dtype=torch.uint8, device=w0.device)
     J = torch.empty(wl.batch, dtype=torch.float64, device=w0.device)

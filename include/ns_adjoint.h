@@ -139,8 +139,19 @@ int ns_growth_sigma1(ns_ctx* ctx, const double* w, float* sigma1, double* stats)
 int ns_add_adjoint_viscosity(ns_ctx* ctx, const float* sigma1, double lambda, double tau,
                              float* nu);
 
+/* Separate added-viscosity factors for the adjoints of rho, of rho u (three
+ * components) and of rho E: every later use of nu by this context (adjoint steps, the
+ * transposed residual, ns_apply_adjoint_viscosity, sweeps, the stability check of
+ * ns_add_adjoint_viscosity, which uses the largest factor) multiplies the viscosity term
+ * of each component by its factor.  The conclusion names different adjoint viscosities
+ * for the different state variables as a next step; (1, 1, 1), the default, is the
+ * single coefficient of section "Energy analysis".  split: host array of 3 finite
+ * non-negative values, else NS_ERR_ARG. */
+int ns_set_viscosity_split(ns_ctx* ctx, const double* split);
+
 /* out += L_nu a = div(nu grad a) per component, nu_face = mean of the two cells
- * (the discrete added-viscosity operator alone). */
+ * (the discrete added-viscosity operator alone), times the component's factor of
+ * ns_set_viscosity_split. */
 int ns_apply_adjoint_viscosity(ns_ctx* ctx, const float* nu, const double* a, double* out);
 
 /* Adjoint energy E[b] = sum_cells v_hat . v_hat dV with w_hat = T^T v_hat, T = S V

@@ -34,7 +34,7 @@ EXPORTED = [
     "ns_profile_read", "ns_to_float", "ns_forward_run", "ns_backward_run", "ns_scale_boxes",
     "ns_dot_boxes", "ns_mlp_net_bytes", "ns_mlp_set_params", "ns_mlp_get_params", "ns_mlp_get_moment",
     "ns_mlp_features", "ns_mlp_infer", "ns_mlp_train_step", "ns_adjoint_label", "ns_label_target",
-    "ns_launch_count",
+    "ns_launch_count", "ns_set_viscosity_split",
 ]
 
 NS_MLP_PARAMS = 5185
@@ -124,6 +124,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "ns_last_error": ([P], I),
         "ns_error_string": ([I], ctypes.c_char_p),
         "ns_launch_count": ([], ctypes.c_ulonglong),
+        "ns_set_viscosity_split": ([P, ctypes.POINTER(ctypes.c_double)], I),
         "ns_plan": ([I, I, I, P, I, ctypes.POINTER(I), ctypes.POINTER(I),
                      ctypes.POINTER(ctypes.c_longlong)], I),
         "ns_run_arena_bytes": ([P, ctypes.POINTER(NsRunOpts)], S),
@@ -293,6 +294,10 @@ class Solver:
     def max_wave_speed(self, w, out):
         _check(self.lib.ns_max_wave_speed(self._ctx, _ptr(w, torch.float64), _ptr(out, torch.float64)),
                "ns_max_wave_speed")
+
+    def set_viscosity_split(self, f_rho: float, f_mom: float, f_en: float):
+        arr = (ctypes.c_double * 3)(f_rho, f_mom, f_en)
+        _check(self.lib.ns_set_viscosity_split(self._ctx, arr), "ns_set_viscosity_split")
 
     def last_error(self) -> int:
         return int(self.lib.ns_last_error(self._ctx))

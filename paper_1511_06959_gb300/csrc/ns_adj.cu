@@ -468,7 +468,8 @@ __global__ void __launch_bounds__(NT, AdjMinBlocks<CT>::value) k_adj_stage(GridD
         rb = rb - ub[j] * u[j] * ir_;
       }
       CT gout[5] = {rb, mb[0], mb[1], mb[2], Eb};
-      // ---- added adjoint viscosity L_nu a
+      // ---- added adjoint viscosity L_nu a, times the factor of the component's state
+      // variable (rho, rho u, rho E)
       if (a.nu) {
         const CT nc = nuv[0], nxm = nuv[1], nxp = nuv[2], nym = nuv[3], nyp = nuv[4], nzm = nuv[5],
                  nzp = nuv[6];
@@ -480,7 +481,7 @@ __global__ void __launch_bounds__(NT, AdjMinBlocks<CT>::value) k_adj_stage(GridD
           CT L = (h * (nc + nxp) * (Av[ic + 1] - ac) - h * (nc + nxm) * (ac - Av[ic - 1])) * ix2 +
                  (h * (nc + nyp) * (Av[ic + SX] - ac) - h * (nc + nym) * (ac - Av[ic - SX])) * iy2 +
                  (h * (nc + nzp) * (Ap[v * SP + ic] - ac) - h * (nc + nzm) * (ac - am[v])) * iz2;
-          gout[v] = gout[v] + L;
+          gout[v] = gout[v] + CT(a.nus[v == 0 ? 0 : (v == 4 ? 2 : 1)]) * L;
         }
       }
       // ---- epilogue

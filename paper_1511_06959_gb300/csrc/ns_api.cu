@@ -2,6 +2,8 @@
 // the sequencing of the fused stage kernels into Runge-Kutta (RK4, SSP-RK3) primal,
 // tangent and adjoint steps.
 #include <cuda_runtime.h>
+
+#include <cmath>
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
@@ -183,6 +185,7 @@ static int adjoint_step_t(ns_ctx* c, const Coef<CT>& cf, const CT* W1, const CT*
     ns::AdjArgs<CT, CT, CT> a{};
     a.W = last ? W1 : Wst[sc.ns - 2 - j];
     a.A = Ain; a.ca = j == 0 ? sc.ca0 * dt : 1.0; a.nu = nu; a.lamf = lamf;
+    for (int q = 0; q < 3; ++q) a.nus[q] = c->nu_split[q];
     a.Gin = j == 0 ? nullptr : G;
     a.Anext = Aout;
     if (!last) { a.cl = sc.cl[j] * dt; a.cg = sc.cg[j] * dt; a.cs = sc.cs[j] * dt; }
@@ -385,10 +388,12 @@ int ns_rhs_transpose(ns_ctx* c, const double* w, const double* a_, const float* 
     if (ns::launch_to_float(a_, af, c->field, c->st) != cudaSuccess) return NS_ERR_CUDA;
     ns::AdjArgs<float, float, float> a{};
     a.W = wf; a.A = af; a.ca = 1.0; a.nu = nu; a.lam_out = out;
+    for (int q = 0; q < 3; ++q) a.nus[q] = c->nu_split[q];
     return cuerr(ns::launch_adj_stage<float, float, float, float>(c->g, c->cf, a, c->st));
   }
   ns::AdjArgs<double, double, double> a{};
   a.W = w; a.A = a_; a.ca = 1.0; a.nu = nu; a.lam_out = out;
+  for (int q = 0; q < 3; ++q) a.nus[q] = c->nu_split[q];
   return cuerr(ns::launch_adj_stage<double, double, double, double>(c->g, c->cd, a, c->st));
 }
 
@@ -412,7 +417,8 @@ int ns_growth_sigma1(ns_ctx* c, const double* w, float* sigma1, double* stats) {
 static double nu_limit(const ns_ctx* c) {
   const double k = 4.0 * (1.0 / (c->p.dx * c->p.dx) + 1.0 / (c->p.dy * c->p.dy) +
                           (c->p.nz > 1 ? 1.0 / (c->p.dz * c->p.dz) : 0.0));
-  return c->p.dt > 0 ? scheme_of(c).limit / (c->p.dt * k) : INFINITY;
+  const double f = std::max(c->nu_split[0], std::max(c->nu_split[1], c->nu_split[2]));
+  return c->p.dt > 0 && f > 0 ? scheme_of(c).limit / (c->p.dt * k * f) : INFINITY;
 }
 
 int ns_add_adjoint_viscosity(ns_ctx* c, const float* sigma1, double lambda, double tau, float* nu) {
@@ -424,7 +430,7 @@ int ns_add_adjoint_viscosity(ns_ctx* c, const float* sigma1, double lambda, doub
 int ns_apply_adjoint_viscosity(ns_ctx* c, const float* nu, const double* a, double* out) {
   if (!c || !nu || !a || !out || out == a) return NS_ERR_ARG;
   const double i2[3] = {1.0 / (c->p.dx * c->p.dx), 1.0 / (c->p.dy * c->p.dy), 1.0 / (c->p.dz * c->p.dz)};
-  return cuerr(ns::launch_visc_apply(c->g, i2, nu, a, out, c->st));
+  return cuerr(ns::launch_visc_apply(c->g, i2, c->nu_split, nu, a, out, c->st));
 }
 
 int ns_adjoint_energy(ns_ctx* c, const double* w, const double* lam, double* E) {
@@ -524,6 +530,14 @@ int ns_to_float(ns_ctx* c, const double* in, float* out, size_t n) {
 int ns_max_wave_speed(ns_ctx* c, const double* w, double* out) {
   if (!c || !w || !out) return NS_ERR_ARG;
   return cuerr(ns::launch_max_wave(c->g, c->p.gamma, w, out, c->scratch, c->st));
+}
+
+int ns_set_viscosity_split(ns_ctx* c, const double* split) {
+  if (!c || !split) return NS_ERR_ARG;
+  for (int q = 0; q < 3; ++q)
+    if (!(split[q] >= 0.0) || !std::isfinite(split[q])) return NS_ERR_ARG;
+  for (int q = 0; q < 3; ++q) c->nu_split[q] = split[q];
+  return NS_OK;
 }
 
 unsigned long long ns_launch_count(void) { return ns::g_launches.load(std::memory_order_relaxed); }

@@ -561,8 +561,9 @@ __global__ void k_nu_rule(long long n, const float* __restrict__ s1, float lam, 
   if (!(v <= limit_nu)) atomicOr(err, ERRBIT_UNSTABLE);
 }
 
-__global__ void k_visc_apply(GridDesc g, double ix2, double iy2, double iz2, const float* __restrict__ nu,
-                             const double* __restrict__ a, double* __restrict__ out) {
+__global__ void k_visc_apply(GridDesc g, double ix2, double iy2, double iz2, double f_rho, double f_mom,
+                             double f_en, const float* __restrict__ nu, const double* __restrict__ a,
+                             double* __restrict__ out) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long tot = g.cells * g.batch;
   if (i >= tot) return;
@@ -587,7 +588,7 @@ __global__ void k_visc_apply(GridDesc g, double ix2, double iy2, double iz2, con
       const double np = 0.5 * (nc + nub[nb[2 * d + 1]]);
       L += (np * (av[nb[2 * d + 1]] - ac) - nm * (ac - av[nb[2 * d]])) * i2[d];
     }
-    out[(size_t)b * 5 * g.cells + (size_t)v * g.cells + c0] += L;
+    out[(size_t)b * 5 * g.cells + (size_t)v * g.cells + c0] += (v == 0 ? f_rho : (v == 4 ? f_en : f_mom)) * L;
   }
 }
 
@@ -816,10 +817,11 @@ cudaError_t launch_nu_rule(const GridDesc& g, const float* sigma1, double lambda
   return cudaGetLastError();
 }
 
-cudaError_t launch_visc_apply(const GridDesc& g, const double* idx2, const float* nu, const double* a,
-                              double* out, cudaStream_t st) {
+cudaError_t launch_visc_apply(const GridDesc& g, const double* idx2, const double* split, const float* nu,
+                              const double* a, double* out, cudaStream_t st) {
   const long long n = g.cells * g.batch;
-  k_visc_apply<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g, idx2[0], idx2[1], idx2[2], nu, a, out);
+  k_visc_apply<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g, idx2[0], idx2[1], idx2[2], split[0], split[1],
+                                                            split[2], nu, a, out);
   count_launch();
   return cudaGetLastError();
 }

@@ -48,6 +48,7 @@ struct AdjArgs {
   const TA* A;
   double ca;
   const float* nu;
+  double nus[3];          // viscosity factors of the rho, rho u, rho E adjoints
   const TST* lamf;
   const TST* Gin;
   TST* Gout;
@@ -86,8 +87,8 @@ cudaError_t launch_label(const GridDesc& g, const Coef<CT>& c, const CT* w, cons
                          cudaStream_t st);
 cudaError_t launch_nu_rule(const GridDesc& g, const float* sigma1, double lambda, double tau,
                            double limit_nu, float* nu, unsigned* err, cudaStream_t st);
-cudaError_t launch_visc_apply(const GridDesc& g, const double* idx2, const float* nu,
-                              const double* a, double* out, cudaStream_t st);
+cudaError_t launch_visc_apply(const GridDesc& g, const double* idx2, const double* split,
+                              const float* nu, const double* a, double* out, cudaStream_t st);
 cudaError_t launch_energy(const GridDesc& g, double gamma, double dV, const double* w,
                           const double* lam, double* E, double* scratch, unsigned* err,
                           bool fp32_transform, cudaStream_t st);
