@@ -14,7 +14,8 @@ is exactly zero, so the 3D formulas reduce to 2D without a special case.
 
 Discretisation (readings of a paper whose own solver was SSP-RK3 + Roe on an
 unstructured mesh, section "Numerical methods"):
-  * convective face flux  Phi^c_{i+1/2} = (F(w_i) + F(w_{i+1})) / 2   (central, 2nd order)
+  * convective face flux  Phi^c_{i+1/2} = (F(w_i) + F(w_{i+1})) / 2   (central, 2nd order),
+    optionally minus the Roe dissipation |A~|(w_{i+1} - w_i)/2 of the paper's solver
   * viscous face flux from the face gradient of (u1, u2, u3, e): the normal part is the
     compact difference (q_{i+1} - q_i)/dx_d, the tangential parts are the mean of the
     two cell-centred central differences; the face velocity is the two-cell mean
@@ -51,6 +52,10 @@ class Params:
     (three components) and of rho E: the separate viscosities per state variable that
     the conclusion names as a next step; (1, 1, 1) is the single coefficient of section
     "Energy analysis".
+    flux: "central" (Phi = (F_L + F_R)/2 - F^v) or "roe" (the approximate Roe solver of
+    section "Numerical methods": the central flux minus the dissipation |A~|(w_R-w_L)/2).
+    roe_delta: Harten's entropy fix, |lam| replaced by (lam^2 + delta^2)/(2 delta)
+    where |lam| < delta, delta = roe_delta times the Roe-averaged sound speed.
     plane_i: the objective plane is the x-face between cell columns plane_i-1 and
     plane_i.  pt_in: the reference stagnation pressure p_{t,in} of Eq. (e:pressure_loss).
     """
@@ -64,6 +69,8 @@ class Params:
     pt_in: float = 1.0
     scheme: str = "rk4"
     nu_split: tuple = (1.0, 1.0, 1.0)
+    flux: str = "central"
+    roe_delta: float = 0.1
 
     @property
     def alpha(self) -> float:
@@ -153,12 +160,101 @@ def viscous_face_flux(w, d, P: Params):
 
 
 # ----------------------------------------------------------------------------------
+# Roe dissipation (section "Numerical methods": the approximate Roe solver).  Written
+# for real or complex arrays: the tangent and the transpose of this term are taken by
+# complex-step differentiation, independently of any hand derivation.
+# ----------------------------------------------------------------------------------
+def _abs_fix(lam, delta, signed):
+    """|lam| with Harten's entropy fix (C^1 at |lam| = delta); signed=True returns lam
+    itself (the Roe matrix A~ instead of |A~|).  The sign is taken from the real part,
+    so the function is complex-step differentiable."""
+    if signed:
+        return lam
+    re = np.real(lam)
+    mag = np.where(re >= 0, lam, -lam)
+    return np.where(np.abs(re) < np.real(delta), (lam * lam + delta * delta) / (2.0 * delta), mag)
+
+
+def roe_dissipation(wL, wR, d, P: Params, signed=False):
+    """D = |A~(wL, wR)| (wR - wL) / 2 for a face with normal e_d (Roe 1981): Roe averages
+    u~, H~ weighted by sqrt(rho), rho~ = sqrt(rho_L rho_R), c~^2 = (gamma-1)(H~ - |u~|^2/2);
+    wave strengths of the acoustic waves (lam = u~_d -+ c~), the entropy wave and the two
+    shear waves (lam = u~_d); eigenvectors of the Euler Jacobian at the Roe state."""
+    g = P.gamma
+    rL, rR = wL[0], wR[0]
+    uL = [wL[1 + k] / rL for k in range(3)]
+    uR = [wR[1 + k] / rR for k in range(3)]
+    pL = (g - 1.0) * (wL[4] - 0.5 * rL * (uL[0] ** 2 + uL[1] ** 2 + uL[2] ** 2))
+    pR = (g - 1.0) * (wR[4] - 0.5 * rR * (uR[0] ** 2 + uR[1] ** 2 + uR[2] ** 2))
+    HL = (wL[4] + pL) / rL
+    HR = (wR[4] + pR) / rR
+    sL, sR = np.sqrt(rL), np.sqrt(rR)
+    rt = sL * sR
+    ut = [(sL * uL[k] + sR * uR[k]) / (sL + sR) for k in range(3)]
+    Ht = (sL * HL + sR * HR) / (sL + sR)
+    q2 = ut[0] ** 2 + ut[1] ** 2 + ut[2] ** 2
+    c2 = (g - 1.0) * (Ht - 0.5 * q2)
+    c = np.sqrt(c2)
+    un = ut[d]
+    dr, dp = rR - rL, pR - pL
+    du = [uR[k] - uL[k] for k in range(3)]
+    dun = du[d]
+    a1 = (dp - rt * c * dun) / (2.0 * c2)
+    a2 = dr - dp / c2
+    a3 = (dp + rt * c * dun) / (2.0 * c2)
+    delta = P.roe_delta * c
+    l1 = _abs_fix(un - c, delta, signed)
+    l2 = _abs_fix(un, delta, signed)
+    l3 = _abs_fix(un + c, delta, signed)
+    D = np.empty((5,) + np.shape(rL), dtype=np.result_type(wL, wR))
+    D[0] = l1 * a1 + l2 * a2 + l3 * a3
+    for k in range(3):
+        n = 1.0 if k == d else 0.0
+        D[1 + k] = (l1 * a1 * (ut[k] - c * n) + l2 * a2 * ut[k] + l3 * a3 * (ut[k] + c * n)
+                    + l2 * rt * (du[k] - dun * n))
+    D[4] = (l1 * a1 * (Ht - un * c) + l2 * a2 * 0.5 * q2 + l3 * a3 * (Ht + un * c)
+            + l2 * rt * (ut[0] * du[0] + ut[1] * du[1] + ut[2] * du[2] - un * dun))
+    return 0.5 * D
+
+
+def _roe_face(w, d, P):
+    """Roe dissipation at every face c + e_d/2 (left cell c)."""
+    return roe_dissipation(w, _sh3(w, d, 1), d, P)
+
+
+_CSTEP = 1e-30
+
+
+def _roe_face_tangent(w, wd, d, P):
+    """Directional derivative of _roe_face along wd, by complex step (exact to roundoff)."""
+    wc = w + 1j * _CSTEP * wd
+    return np.imag(roe_dissipation(wc, _sh3(wc, d, 1), d, P)) / _CSTEP
+
+
+def _roe_face_jacobians(w, d, P):
+    """JL[i, j], JR[i, j] = dD_i/dwL_j, dD_i/dwR_j at every face, by complex step."""
+    wR = _sh3(w, d, 1)
+    JL = np.empty((5, 5) + w.shape[1:])
+    JR = np.empty((5, 5) + w.shape[1:])
+    for j in range(5):
+        e = np.zeros((5,) + (1,) * (w.ndim - 1))
+        e[j] = _CSTEP
+        JL[:, j] = np.imag(roe_dissipation(w + 1j * e, wR, d, P)) / _CSTEP
+        JR[:, j] = np.imag(roe_dissipation(w, wR + 1j * e, d, P)) / _CSTEP
+    return JL, JR
+
+
+# ----------------------------------------------------------------------------------
 # residual R(w): dw/dt = R(w), Eq. (e:vector) with the source s_i
 # ----------------------------------------------------------------------------------
 def face_flux(w, d, P: Params):
-    """Total face flux Phi_d = (F_d(c) + F_d(c+e_d))/2 - F^v_d at the face c + e_d/2."""
+    """Total face flux Phi_d = (F_d(c) + F_d(c+e_d))/2 - F^v_d at the face c + e_d/2, minus
+    the Roe dissipation when P.flux == "roe"."""
     F = euler_flux(w, d, P)
-    return 0.5 * (F + _sh3(F, d, 1)) - viscous_face_flux(w, d, P)
+    Phi = 0.5 * (F + _sh3(F, d, 1)) - viscous_face_flux(w, d, P)
+    if P.flux == "roe":
+        Phi = Phi - _roe_face(w, d, P)
+    return Phi
 
 
 def residual(w, P: Params, s=None):
@@ -211,6 +307,8 @@ def residual_tangent(w, wd, P: Params):
         Fvd[1:4] = sigd
         Fvd[4] = sum(ufd[j] * sig[j] + uf[j] * sigd[j] for j in range(3)) + P.alpha * gd[3, d]
         Phid = 0.5 * (Fd + _sh3(Fd, d, 1)) - Fvd
+        if P.flux == "roe":
+            Phid = Phid - _roe_face_tangent(w, wd, d, P)
         Rd -= (Phid - _sh3(Phid, d, -1)) / P.dx[d]
     return Rd
 
@@ -235,6 +333,11 @@ def residual_transpose(w, a, P: Params):
     for d in range(3):
         # R -= (Phi(c) - Phi(c - e_d)) / dx  ->  Phi_bar(c) = (a(c + e_d) - a(c)) / dx
         Phib = (_sh3(a, d, 1) - a) / P.dx[d]
+        if P.flux == "roe":
+            # Phi -= D(w(c), w(c+e_d)): w_bar(c) -= JL^T Phi_bar, w_bar(c+e_d) -= JR^T Phi_bar
+            JL, JR = _roe_face_jacobians(w, d, P)
+            wb -= np.einsum("ij...,i...->j...", JL, Phib)
+            wb -= _sh3(np.einsum("ij...,i...->j...", JR, Phib), d, -1)
         # Phi = (F(c) + F(c+e_d))/2 - Fv  ->  F_bar(c) = (Phi_bar(c) + Phi_bar(c-e_d))/2
         Fb = 0.5 * (Phib + _sh3(Phib, d, -1))
         Fvb = -Phib
