@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--nu-split", default="1,1,1",
                     help="added-viscosity factors for the rho, rho u, rho E adjoints")
+    ap.add_argument("--flux", default="central", choices=["central", "roe"],
+                    help="convective face flux (the workload's is central; roe adds the paper's "
+                         "Roe dissipation)")
     ap.add_argument("--scheme", default="rk4", choices=["rk4", "ssprk3"],
                     help="time integrator (the workload's is RK4; ssprk3 is the paper's own)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
@@ -82,11 +85,11 @@ def oracle_unit(w, P, lam_tilde, dx0):
     O.adjoint_energy(w, lam, P)
 
 
-def oracle_setup(wl, scheme="rk4"):
+def oracle_setup(wl, scheme="rk4", flux="central"):
     from oracle import ns_oracle as O
     w = wl.initial_state()
     P = O.Params(gamma=wl.gamma, mu=wl.mu, Pr=wl.Pr, dx=wl.dx, plane_i=wl.plane_i, pt_in=wl.pt_in,
-                 scheme=scheme)
+                 scheme=scheme, flux=flux)
     P.dt = C.cfl_dt(wl, O.max_wave_speed(w, P))
     return w, P
 
@@ -104,7 +107,7 @@ def run_reference(args, wl):
         return
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         os.environ[k] = "1"
-    w, P = oracle_setup(wl, args.scheme)
+    w, P = oracle_setup(wl, args.scheme, args.flux)
     for _ in range(min(args.warmup, 1)):
         oracle_unit(w, P, wl.lam_tilde, wl.dx[0])
     t0 = time.perf_counter()
@@ -118,8 +121,8 @@ def run_reference(args, wl):
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": min(args.warmup, 1), "ms_per_step": 1e3 * t / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": C.describe(wl, args.scheme), "name": wl.name,
-                                        "scheme": args.scheme},
+        "data": "synthetic", "config": {"workload": C.describe(wl, args.scheme, args.flux), "name": wl.name,
+                                        "scheme": args.scheme, "flux": args.flux},
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
@@ -198,8 +201,10 @@ def run_ours(args, wl):
     w0_host = wl.initial_state()
     w0 = torch.from_numpy(w0_host).to(dev)
     scheme = api.NS_SSPRK3 if args.scheme == "ssprk3" else api.NS_RK4
+    flux = api.NS_FLUX_ROE if args.flux == "roe" else api.NS_FLUX_CENTRAL
     S = api.Solver(wl.nx, wl.ny, wl.nz, wl.dx, gamma=wl.gamma, mu=wl.mu, Pr=wl.Pr, dt=0.0,
-                   precision=prec, plane_i=wl.plane_i, pt_in=wl.pt_in, batch=wl.batch, scheme=scheme)
+                   precision=prec, plane_i=wl.plane_i, pt_in=wl.pt_in, batch=wl.batch, scheme=scheme,
+                   flux=flux)
     split = tuple(float(x) for x in args.nu_split.split(","))
     S.set_viscosity_split(*split)
     m = torch.empty(1, dtype=torch.float64, device=dev)
@@ -302,8 +307,8 @@ def run_ours(args, wl):
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32 (f64 accumulate)" if prec == api.NS_MIXED else "f64",
             "data": "synthetic",
-            "config": {"workload": C.describe(wl, args.scheme), "name": wl.name, "cells": wl.cells,
-                       "scheme": args.scheme, "nu_split": list(split),
+            "config": {"workload": C.describe(wl, args.scheme, args.flux), "name": wl.name, "cells": wl.cells,
+                       "scheme": args.scheme, "flux": args.flux, "nu_split": list(split),
                        "nsteps": wl.nsteps, "schedule": wl.schedule, "param": param,
                        "lambda_tilde": wl.lam_tilde, "precision": args.precision, "dt": dt,
                        "l2": "flushed (256 MB write) between timed steps; arena "
@@ -321,9 +326,9 @@ def run_ours(args, wl):
             "clocks": clocks,
         }
         if not args.no_fp64_compare and prec == api.NS_MIXED:
-            out["fp64"] = fp64_compare(api, torch, wl, w0, dt, sched, param, lam0, Jv, scheme, split)
+            out["fp64"] = fp64_compare(api, torch, wl, w0, dt, sched, param, lam0, Jv, scheme, split, flux)
         if not args.no_cpu_baseline and ws == 1:
-            out["cpu_baseline"] = cpu_baseline(wl, args.scheme)
+            out["cpu_baseline"] = cpu_baseline(wl, args.scheme, args.flux)
     return out
 
 
@@ -361,12 +366,13 @@ def adj_traffic(wl, precision):
         return None
 
 
-def fp64_compare(api, torch, wl, w0, dt, sched, param, lam_mixed, J_mixed, scheme, split=(1.0, 1.0, 1.0)):
+def fp64_compare(api, torch, wl, w0, dt, sched, param, lam_mixed, J_mixed, scheme, split=(1.0, 1.0, 1.0),
+                 flux=0):
     """The same checkpointed sweep in FP64 (timed once) and the mixed-precision
     gradient error against it."""
     S = api.Solver(wl.nx, wl.ny, wl.nz, wl.dx, gamma=wl.gamma, mu=wl.mu, Pr=wl.Pr, dt=dt,
                    precision=api.NS_FP64, plane_i=wl.plane_i, pt_in=wl.pt_in, batch=wl.batch,
-                   scheme=scheme)
+                   scheme=scheme, flux=flux)
     S.set_viscosity_split(*split)
     opts = S.run_opts(wl.nsteps, sched, param, wl.lam_coef, 0.0, True, True)
     arena = torch.empty(S.arena_bytes(opts), dtype=torch.uint8, device=w0.device)
@@ -394,7 +400,7 @@ def fp64_compare(api, torch, wl, w0, dt, sched, param, lam_mixed, J_mixed, schem
             "note": "FP64 is bound by the FP64 ALU rate, not HBM; timed once on the same workload"}
 
 
-def cpu_baseline(wl, scheme="rk4"):
+def cpu_baseline(wl, scheme="rk4", flux="central"):
     """The FP64 oracle on this host's cores: one checkpointed adjoint step of the full box
     (10-30 s of CPU work), scaled to adjoint cell-steps/s.  It runs in a spawned process
     so that no fork happens after CUDA is initialised."""
@@ -405,7 +411,7 @@ def cpu_baseline(wl, scheme="rk4"):
     try:
         ctx = mp.get_context("spawn")
         with ctx.Pool(1) as pool:
-            t = pool.apply(_cpu_sample, (wl.name, scheme))
+            t = pool.apply(_cpu_sample, (wl.name, scheme, flux))
     finally:
         for k, v in saved.items():
             if v is None:
@@ -418,9 +424,9 @@ def cpu_baseline(wl, scheme="rk4"):
                       f"{t:.1f} s", "host_cores_available": cpu_cores()}
 
 
-def _cpu_sample(name, scheme="rk4"):
+def _cpu_sample(name, scheme="rk4", flux="central"):
     wl = C.WORKLOADS[name]
-    w, P = oracle_setup(wl, scheme)
+    w, P = oracle_setup(wl, scheme, flux)
     t0 = time.perf_counter()
     oracle_unit(w, P, wl.lam_tilde, wl.dx[0])
     return time.perf_counter() - t0

@@ -10,9 +10,10 @@
  * singular value of the growth matrix M = M1 - M2 ("Energy analysis").
  *
  * Discretisation: periodic structured box of nx*ny*nz cells (nz = 1 is a 2D box),
- * central 2nd-order face fluxes, compact viscous stencil, classical RK4 or the paper's
- * SSP-RK3 (ns_params.scheme) with a constant dt; the adjoint is the exact transpose of
- * that discrete map.
+ * central 2nd-order face fluxes (optionally with the paper's Roe dissipation,
+ * ns_params.flux), compact viscous stencil, classical RK4 or the paper's SSP-RK3
+ * (ns_params.scheme) with a constant dt; the adjoint is the exact transpose of that
+ * discrete map.
  *
  * Conventions shared by every call:
  *  - Field pointers are DEVICE pointers owned by the caller, in SoA layout
@@ -53,6 +54,12 @@ extern "C" {
                        W2 = w + dt R(w), W3 = 3/4 w + 1/4 (W2 + dt R(W2)),
                        w' = 1/3 w + 2/3 (W3 + dt R(W3))) */
 
+/* convective face flux (ns_params.flux) */
+#define NS_FLUX_CENTRAL 0 /* Phi = (F_L + F_R)/2 - F^v */
+#define NS_FLUX_ROE 1     /* the approximate Roe solver of section "Numerical methods":
+                             Phi = (F_L + F_R)/2 - |A~|(w_R - w_L)/2 - F^v, with A~ the Roe
+                             matrix (sqrt(rho)-weighted Roe state) and Harten's entropy fix */
+
 #define NS_FP64 0  /* every flux, transpose and stage state in FP64 */
 #define NS_MIXED 1 /* fluxes, transposes and stage states in FP32; w, adjoint, objective,
                       reductions and time accumulation in FP64 */
@@ -70,6 +77,9 @@ typedef struct {
   double pt_in;     /* reference stagnation pressure p_t,in of Eq. (e:pressure_loss) */
   int scheme;       /* NS_RK4 or NS_SSPRK3: the explicit Runge-Kutta method of every step,
                        its tangent and its discrete adjoint */
+  int flux;         /* NS_FLUX_CENTRAL or NS_FLUX_ROE (convective face flux) */
+  double roe_delta; /* NS_FLUX_ROE: Harten's entropy fix, |lam| -> (lam^2 + delta^2)/(2 delta)
+                       where |lam| < delta = roe_delta * (Roe-averaged sound speed); > 0 */
 } ns_params;
 
 typedef struct ns_ctx ns_ctx;

@@ -24,6 +24,8 @@ NS_FP64 = 0
 NS_MIXED = 1
 NS_RK4 = 0
 NS_SSPRK3 = 1
+NS_FLUX_CENTRAL = 0
+NS_FLUX_ROE = 1
 
 EXPORTED = [
     "ns_create", "ns_destroy", "ns_set_stream", "ns_set_dt", "ns_workspace_bytes", "ns_rhs",
@@ -51,7 +53,8 @@ class NsParams(ctypes.Structure):
         ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double),
         ("gamma", ctypes.c_double), ("mu", ctypes.c_double), ("Pr", ctypes.c_double),
         ("dt", ctypes.c_double), ("precision", ctypes.c_int), ("plane_i", ctypes.c_int),
-        ("pt_in", ctypes.c_double), ("scheme", ctypes.c_int),
+        ("pt_in", ctypes.c_double), ("scheme", ctypes.c_int), ("flux", ctypes.c_int),
+        ("roe_delta", ctypes.c_double),
     ]
 
 
@@ -182,11 +185,12 @@ class Solver:
     physical parameters, precision and time step."""
 
     def __init__(self, nx, ny, nz, dx, gamma=1.4, mu=0.0, Pr=0.72, dt=0.0, precision=NS_FP64,
-                 plane_i=0, pt_in=1.0, batch=1, stream=None, scheme=NS_RK4):
+                 plane_i=0, pt_in=1.0, batch=1, stream=None, scheme=NS_RK4, flux=NS_FLUX_CENTRAL,
+                 roe_delta=0.1):
         self.lib = _lib()
         d = dx if isinstance(dx, (tuple, list)) else (dx, dx, dx)
         self.params = NsParams(nx, ny, nz, batch, d[0], d[1], d[2], gamma, mu, Pr, dt,
-                               precision, plane_i, pt_in, scheme)
+                               precision, plane_i, pt_in, scheme, flux, roe_delta)
         self.nstages = 3 if scheme == NS_SSPRK3 else 4
         self.shape = (batch, 5, nz, ny, nx)
         self.cells = nx * ny * nz

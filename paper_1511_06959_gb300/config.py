@@ -88,9 +88,10 @@ def cfl_dt(w: Workload, max_wave_speed: float) -> float:
     return w.cfl * min(w.dx) / max_wave_speed
 
 
-def describe(w: Workload, scheme: str = "rk4") -> str:
+def describe(w: Workload, scheme: str = "rk4", flux: str = "central") -> str:
     name = "SSP-RK3" if scheme == "ssprk3" else "RK4"
-    return (f"{w.nx}x{w.ny}x{w.nz} {w.kind} Mach {w.mach} Re {w.Re:g}, {w.nsteps} {name} steps, "
+    fl = ", Roe flux" if flux == "roe" else ""
+    return (f"{w.nx}x{w.ny}x{w.nz} {w.kind} Mach {w.mach} Re {w.Re:g}, {w.nsteps} {name} steps{fl}, "
             f"{w.schedule}{'' if w.schedule == 'all' else ' ' + str(w.param or 'budget')}")
 
 

@@ -26,6 +26,7 @@
 
 #include "ns_common.cuh"
 #include "ns_kernels.h"
+#include "ns_roe.cuh"
 
 namespace ns {
 
@@ -247,6 +248,22 @@ __device__ __forceinline__ void zpacket(const CT* sQ, const CT* sA, const Coef<C
   face_packet<2>(c, QL, sA + sL * 5 * SP, i, QR, sA + sR * 5 * SP, i, gx, gy, pk);
 }
 
+// Roe part of a face packet: the adjoints of the two cells' primitives from the Roe
+// dissipation, pk[0..4] for the left cell and pk[5..9] for the right cell, for the
+// face adjoint Db = (a_L - a_R) / dx_D (D enters the face flux with the sign of F^v).
+template <int D, class CT>
+__device__ __forceinline__ void roe_packet(const Coef<CT>& c, const CT* QL, const CT* AL, int iL,
+                                           const CT* QR, const CT* AR, int iR, CT* pk) {
+  CT qL[5], qR[5], Db[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    qL[v] = QL[v * SP + iL];
+    qR[v] = QR[v * SP + iR];
+    Db[v] = (AL[v * SP + iL] - AR[v * SP + iR]) * c.idx[D];
+  }
+  roe_dissipation_adj<D>(c, qL, qR, Db, pk, pk + 5);
+}
+
 // z-face s-vectors between plane slots sL and sR at every shared column.
 template <class CT>
 __device__ __forceinline__ void fill_Z(CT* Z, const CT* sQ, const CT* sA, const Coef<CT>& c,
@@ -266,19 +283,24 @@ __device__ __forceinline__ void fill_Z(CT* Z, const CT* sQ, const CT* sA, const 
 }  // namespace
 
 // Resident CTAs per SM the register allocation is held to: 4 for FP32 (the shared
-// memory allows 4), 2 for FP64.
-template <class CT> struct AdjMinBlocks { static constexpr int value = 2; };
-template <> struct AdjMinBlocks<float> { static constexpr int value = 4; };
+// memory allows 4), 3 for FP32 with Roe dissipation, 2 for FP64.
+template <class CT, bool ROE> struct AdjMinBlocks { static constexpr int value = 2; };
+template <> struct AdjMinBlocks<float, false> { static constexpr int value = 4; };
+template <> struct AdjMinBlocks<float, true> { static constexpr int value = 3; };
 
-template <class CT, class TIN, class TA, class TST>
-__global__ void __launch_bounds__(NT, AdjMinBlocks<CT>::value) k_adj_stage(GridDesc g, Coef<CT> c, AdjArgs<TIN, TA, TST> a) {
+// values per face packet: 7 (viscous and face velocity), plus 10 with Roe dissipation
+template <bool ROE> constexpr int npk() { return ROE ? 17 : 7; }
+
+template <class CT, class TIN, class TA, class TST, bool ROE>
+__global__ void __launch_bounds__(NT, AdjMinBlocks<CT, ROE>::value) k_adj_stage(GridDesc g, Coef<CT> c, AdjArgs<TIN, TA, TST> a) {
+  constexpr int NPK = npk<ROE>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   CT* sQ = reinterpret_cast<CT*>(smem_raw);   // [3][5][SP] primal primitives
   CT* sA = sQ + 3 * 5 * SP;                    // [3][5][SP] adjoint input a
   CT* sF = sA + 3 * 5 * SP;                    // [2][4][NF] in-plane face s-vectors, Fb[4]
   CT* sZ = sF + 2 * 4 * NF;                    // [2][3][SP] z-face s-vectors
-  CT* sFX = sZ + 2 * 3 * SP;                   // [7][TY][TX+1]
-  CT* sFY = sFX + 7 * TY * (TX + 1);           // [7][TY+1][TX]
+  CT* sFX = sZ + 2 * 3 * SP;                   // [NPK][TY][TX+1]
+  CT* sFY = sFX + NPK * TY * (TX + 1);         // [NPK][TY+1][TX]
   const int tid = threadIdx.x;
   const int tx = tid % TX, ty = tid / TX;
   int b, x0, y0, kz0, kz1;
@@ -303,8 +325,11 @@ __global__ void __launch_bounds__(NT, AdjMinBlocks<CT>::value) k_adj_stage(GridD
   fill_faces(fslot(kz0), sQ, sA, c, slot(kz0));
   fill_Z(sZ + zslot(kz0 - 1) * 3 * SP, sQ, sA, c, slot(kz0 - 1), slot(kz0));
   const int ic = (ty + 1) * SX + (tx + 1);
-  CT zlo[7], zhi[7];
+  CT zlo[NPK], zhi[NPK];
   zpacket(sQ, sA, c, slot(kz0 - 1), slot(kz0), ic, zlo);
+  if constexpr (ROE)
+    roe_packet<2>(c, sQ + slot(kz0 - 1) * 5 * SP, sA + slot(kz0 - 1) * 5 * SP, ic, sQ + slot(kz0) * 5 * SP,
+                  sA + slot(kz0) * 5 * SP, ic, zlo + 7);
   __syncthreads();
   // own-cell S sums of planes k-1 and k, carried in registers along the march
   CT own_m[3], own_0[3];
@@ -345,26 +370,42 @@ __global__ void __launch_bounds__(NT, AdjMinBlocks<CT>::value) k_adj_stage(GridD
     fill_faces(fslot(k + 1), sQ, sA, c, sp);
     fill_Z(sZ + zslot(k) * 3 * SP, sQ, sA, c, s0, sp);
     {
-      CT pk[7];
+      const CT* Q0 = sQ + s0 * 5 * SP;
+      const CT* A0 = sA + s0 * 5 * SP;
+      CT pk[NPK];
       xpacket(sQ, F0, c, sm, s0, sp, ty + 1, tx, pk);
+      if constexpr (ROE) roe_packet<0>(c, Q0, A0, ic - 1, Q0, A0, ic, pk + 7);
 #pragma unroll
-      for (int v = 0; v < 7; ++v) sFX[(v * TY + ty) * (TX + 1) + tx] = pk[v];
+      for (int v = 0; v < NPK; ++v) sFX[(v * TY + ty) * (TX + 1) + tx] = pk[v];
       ypacket(sQ, F0, c, sm, s0, sp, ty, tx + 1, pk);
+      if constexpr (ROE) roe_packet<1>(c, Q0, A0, ic - SX, Q0, A0, ic, pk + 7);
 #pragma unroll
-      for (int v = 0; v < 7; ++v) sFY[(v * (TY + 1) + ty) * TX + tx] = pk[v];
+      for (int v = 0; v < NPK; ++v) sFY[(v * (TY + 1) + ty) * TX + tx] = pk[v];
     }
     zpacket(sQ, sA, c, s0, sp, ic, zhi);
+    if constexpr (ROE)
+      roe_packet<2>(c, sQ + s0 * 5 * SP, sA + s0 * 5 * SP, ic, sQ + sp * 5 * SP, sA + sp * 5 * SP, ic, zhi + 7);
     if (tid < TX) {
-      CT pk[7];
+      CT pk[NPK];
       ypacket(sQ, F0, c, sm, s0, sp, TY, tid + 1, pk);
+      if constexpr (ROE) {
+        const int iL = TY * SX + tid + 1;
+        roe_packet<1>(c, sQ + s0 * 5 * SP, sA + s0 * 5 * SP, iL, sQ + s0 * 5 * SP, sA + s0 * 5 * SP, iL + SX,
+                      pk + 7);
+      }
 #pragma unroll
-      for (int v = 0; v < 7; ++v) sFY[(v * (TY + 1) + TY) * TX + tid] = pk[v];
+      for (int v = 0; v < NPK; ++v) sFY[(v * (TY + 1) + TY) * TX + tid] = pk[v];
     } else if (tid < TX + TY) {
-      CT pk[7];
+      CT pk[NPK];
       const int r = tid - TX;
       xpacket(sQ, F0, c, sm, s0, sp, r + 1, TX, pk);
+      if constexpr (ROE) {
+        const int iL = (r + 1) * SX + TX;
+        roe_packet<0>(c, sQ + s0 * 5 * SP, sA + s0 * 5 * SP, iL, sQ + s0 * 5 * SP, sA + s0 * 5 * SP, iL + 1,
+                      pk + 7);
+      }
 #pragma unroll
-      for (int v = 0; v < 7; ++v) sFX[(v * TY + r) * (TX + 1) + TX] = pk[v];
+      for (int v = 0; v < NPK; ++v) sFX[(v * TY + r) * (TX + 1) + TX] = pk[v];
     }
     // the assembly reads plane k-1 only at the own cell: keep those values so that plane
     // k+2 can replace plane k-1 in the ring right after the barrier
@@ -440,6 +481,22 @@ __global__ void __launch_bounds__(NT, AdjMinBlocks<CT>::value) k_adj_stage(GridD
       CT rb = CT(0), mb[3] = {CT(0), CT(0), CT(0)}, Eb = CT(0), pb = CT(0);
       CT ub[3] = {qb[0], qb[1], qb[2]};
       CT eb = qb[3];
+      if constexpr (ROE) {
+        // Roe dissipation: the right-cell part of the lower faces and the left-cell part
+        // of the upper faces, as adjoints of (rho, u, e)
+        const int fl = ty * (TX + 1) + tx;
+        const int yl = ty * TX + tx;
+        CT rs[5];
+#pragma unroll
+        for (int v = 0; v < 5; ++v)
+          rs[v] = sFX[(12 + v) * TY * (TX + 1) + fl] + sFX[(7 + v) * TY * (TX + 1) + fl + 1] +
+                  sFY[(12 + v) * (TY + 1) * TX + yl] + sFY[(7 + v) * (TY + 1) * TX + yl + TX] +
+                  zlo[12 + v] + zhi[7 + v];
+        rb = rs[0];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) ub[j] = ub[j] + rs[1 + j];
+        eb = eb + rs[4];
+      }
       const int nb_lo[3] = {ic - 1, ic - SX, ic};
       const int nb_hi[3] = {ic + 1, ic + SX, ic};
 #pragma unroll
@@ -500,7 +557,7 @@ __global__ void __launch_bounds__(NT, AdjMinBlocks<CT>::value) k_adj_stage(GridD
       }
     }
 #pragma unroll
-    for (int v = 0; v < 7; ++v) zlo[v] = zhi[v];
+    for (int v = 0; v < NPK; ++v) zlo[v] = zhi[v];
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
       own_m[j] = own_0[j];
@@ -510,16 +567,17 @@ __global__ void __launch_bounds__(NT, AdjMinBlocks<CT>::value) k_adj_stage(GridD
   }
 }
 
-template <class CT>
+template <class CT, bool ROE>
 size_t adj_smem_bytes() {
-  return sizeof(CT) * (3 * 5 * SP * 2 + 2 * 4 * NF + 2 * 3 * SP + 7 * TY * (TX + 1) + 7 * (TY + 1) * TX);
+  constexpr int NPK = npk<ROE>();
+  return sizeof(CT) * (3 * 5 * SP * 2 + 2 * 4 * NF + 2 * 3 * SP + NPK * TY * (TX + 1) + NPK * (TY + 1) * TX);
 }
 
-template <class CT, class TIN, class TA, class TST>
-cudaError_t launch_adj_stage(const GridDesc& g, const Coef<CT>& c, const AdjArgs<TIN, TA, TST>& a,
-                             cudaStream_t st) {
-  const size_t smem = adj_smem_bytes<CT>();
-  auto kern = k_adj_stage<CT, TIN, TA, TST>;
+template <class CT, class TIN, class TA, class TST, bool ROE>
+static cudaError_t launch_adj_variant(const GridDesc& g, const Coef<CT>& c, const AdjArgs<TIN, TA, TST>& a,
+                                     cudaStream_t st) {
+  const size_t smem = adj_smem_bytes<CT, ROE>();
+  auto kern = k_adj_stage<CT, TIN, TA, TST, ROE>;
   static MarchShape<TX, TY> shape;
   int ctas = 0;
   cudaError_t e = shape.get(kern, smem, g, "NS_ADJ_CTAS", ctas);
@@ -527,6 +585,13 @@ cudaError_t launch_adj_stage(const GridDesc& g, const Coef<CT>& c, const AdjArgs
   kern<<<ctas, NT, smem, st>>>(g, c, a);
   count_launch();
   return cudaGetLastError();
+}
+
+template <class CT, class TIN, class TA, class TST>
+cudaError_t launch_adj_stage(const GridDesc& g, const Coef<CT>& c, const AdjArgs<TIN, TA, TST>& a,
+                             cudaStream_t st) {
+  return c.roe ? launch_adj_variant<CT, TIN, TA, TST, true>(g, c, a, st)
+               : launch_adj_variant<CT, TIN, TA, TST, false>(g, c, a, st);
 }
 
 template cudaError_t launch_adj_stage<double, double, double, double>(

@@ -29,6 +29,8 @@ Coef<T> make_coef(const ns_params& p) {
   c.gm1 = T(p.gamma - 1.0);
   c.mu = T(p.mu);
   c.alpha = T(p.gamma * p.mu / p.Pr);
+  c.roe_delta = T(p.roe_delta);
+  c.roe = p.flux == NS_FLUX_ROE ? 1 : 0;
   const double d[3] = {p.dx, p.dy, p.dz};
   for (int i = 0; i < 3; ++i) {
     c.idx[i] = T(1.0 / d[i]);
@@ -228,6 +230,8 @@ int ns_create(const ns_params* p, void* stream, ns_ctx** out) {
     return NS_ERR_ARG;
   if (p->precision != NS_FP64 && p->precision != NS_MIXED) return NS_ERR_ARG;
   if (p->scheme != NS_RK4 && p->scheme != NS_SSPRK3) return NS_ERR_ARG;
+  if (p->flux != NS_FLUX_CENTRAL && p->flux != NS_FLUX_ROE) return NS_ERR_ARG;
+  if (p->flux == NS_FLUX_ROE && !(p->roe_delta > 0.0 && p->roe_delta < 1e30)) return NS_ERR_ARG;
   if ((long long)p->nx * p->ny > (1LL << 31) || (long long)p->nx * p->ny * p->nz > (1LL << 40))
     return NS_ERR_ARG;
   ns_ctx* c = new ns_ctx();
@@ -248,6 +252,8 @@ int ns_create(const ns_params* p, void* stream, ns_ctx** out) {
     x.gm1 = Dual(d.gm1);
     x.mu = Dual(d.mu);
     x.alpha = Dual(d.alpha);
+    x.roe_delta = Dual(d.roe_delta);
+    x.roe = d.roe;
     for (int i = 0; i < 3; ++i) {
       x.idx[i] = Dual(d.idx[i]);
       x.i4dx[i] = Dual(d.i4dx[i]);

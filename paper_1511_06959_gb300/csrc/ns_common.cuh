@@ -100,6 +100,8 @@ struct MarchShape {
 template <class T>
 struct Coef {
   T gamma, gm1, mu, alpha;
+  T roe_delta;  // Harten's entropy-fix fraction of the Roe sound speed
+  int roe;      // 1: Roe dissipation on the convective face flux
   T idx[3];    // 1 / dx_d
   T i4dx[3];   // 1 / (4 dx_d): tangential face gradient = mean of two central diffs
   T hidx[3];   // 1 / (2 dx_d): cell-centred central difference

@@ -20,6 +20,7 @@
 
 #include "ns_common.cuh"
 #include "ns_kernels.h"
+#include "ns_roe.cuh"
 
 namespace ns {
 namespace rk {
@@ -118,7 +119,7 @@ __device__ __forceinline__ void plane_store(const PlaneRegs<CT>& r, CT* __restri
 
 // Face flux Phi_D between cells L and R given the tangential face gradients of
 // (u1, u2, u3, e) along T1 = (D+1)%3 and T2 = (D+2)%3.
-template <int D, class CT>
+template <int D, bool ROE, class CT>
 __device__ __forceinline__ void face_flux(const Coef<CT>& c, const CT* qL, const CT* qR,
                                           const CT* gt1, const CT* gt2, CT* phi) {
   constexpr int T1 = (D + 1) % 3, T2 = (D + 2) % 3;
@@ -148,6 +149,12 @@ __device__ __forceinline__ void face_flux(const Coef<CT>& c, const CT* qL, const
   for (int k = 0; k < 3; ++k) phi[1 + k] = CT(0.5) * (mL * qL[1 + k] + mR * qR[1 + k]) - sig[k];
   phi[1 + D] = phi[1 + D] + CT(0.5) * (pL + pR);
   phi[4] = CT(0.5) * (mL * (qL[4] + kL) + pL * qL[1 + D] + mR * (qR[4] + kR) + pR * qR[1 + D]) - fv4;
+  if constexpr (ROE) {
+    CT Dv[5];
+    roe_dissipation<D>(c, qL, qR, Dv);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) phi[v] = phi[v] - Dv[v];
+  }
 }
 
 template <class CT>
@@ -156,7 +163,7 @@ __device__ __forceinline__ const CT* qs(const CT* sQ, int slot, int v) {
 }
 
 // x-face between shared cells (row, fx) and (row, fx+1); row/fx in shared coords.
-template <class CT>
+template <bool ROE, class CT>
 __device__ __forceinline__ void xface(const CT* sQ, const Coef<CT>& c, int sm, int s0, int sp,
                                       int row, int fx, CT* phi) {
   const int iL = row * SX + fx, iR = iL + 1;
@@ -174,11 +181,11 @@ __device__ __forceinline__ void xface(const CT* sQ, const Coef<CT>& c, int sm, i
     gy[k] = (p0[iL + SX] - p0[iL - SX] + p0[iR + SX] - p0[iR - SX]) * c.i4dx[1];
     gz[k] = (pp[iL] - pm[iL] + pp[iR] - pm[iR]) * c.i4dx[2];
   }
-  face_flux<0>(c, qL, qR, gy, gz, phi);
+  face_flux<0, ROE>(c, qL, qR, gy, gz, phi);
 }
 
 // y-face between shared cells (fy, col) and (fy+1, col).
-template <class CT>
+template <bool ROE, class CT>
 __device__ __forceinline__ void yface(const CT* sQ, const Coef<CT>& c, int sm, int s0, int sp,
                                       int fy, int col, CT* phi) {
   const int iL = fy * SX + col, iR = iL + SX;
@@ -196,11 +203,11 @@ __device__ __forceinline__ void yface(const CT* sQ, const Coef<CT>& c, int sm, i
     gz[k] = (pp[iL] - pm[iL] + pp[iR] - pm[iR]) * c.i4dx[2];
     gx[k] = (p0[iL + 1] - p0[iL - 1] + p0[iR + 1] - p0[iR - 1]) * c.i4dx[0];
   }
-  face_flux<1>(c, qL, qR, gz, gx, phi);
+  face_flux<1, ROE>(c, qL, qR, gz, gx, phi);
 }
 
 // z-face between slot sL (lower plane) and sR (upper plane) at shared cell index i.
-template <class CT>
+template <bool ROE, class CT>
 __device__ __forceinline__ void zface(const CT* sQ, const Coef<CT>& c, int sL, int sR, int i,
                                       CT* phi) {
   CT qL[5], qR[5], gx[4], gy[4];
@@ -216,17 +223,17 @@ __device__ __forceinline__ void zface(const CT* sQ, const Coef<CT>& c, int sL, i
     gx[k] = (a[i + 1] - a[i - 1] + bq[i + 1] - bq[i - 1]) * c.i4dx[0];
     gy[k] = (a[i + SX] - a[i - SX] + bq[i + SX] - bq[i - SX]) * c.i4dx[1];
   }
-  face_flux<2>(c, qL, qR, gx, gy, phi);
+  face_flux<2, ROE>(c, qL, qR, gx, gy, phi);
 }
 
 // Resident CTAs per SM the register allocation is held to: 3 for FP32 (85 registers or
-// fewer), 1 for FP64 and the dual-number tangent.
-template <class CT> struct RhsMinBlocks { static constexpr int value = 1; };
-template <> struct RhsMinBlocks<float> { static constexpr int value = 3; };
-template <> struct RhsMinBlocks<Dual> { static constexpr int value = 1; };
+// fewer), 2 for FP32 with Roe dissipation, 1 for FP64 and the dual-number tangent.
+template <class CT, bool ROE> struct RhsMinBlocks { static constexpr int value = 1; };
+template <> struct RhsMinBlocks<float, false> { static constexpr int value = 3; };
+template <> struct RhsMinBlocks<float, true> { static constexpr int value = 2; };
 
-template <class CT, class TIN, class TST>
-__global__ void __launch_bounds__(NT, RhsMinBlocks<CT>::value) k_rhs_stage(GridDesc g, Coef<CT> c, StageArgs<TIN, TST> a) {
+template <class CT, class TIN, class TST, bool ROE>
+__global__ void __launch_bounds__(NT, RhsMinBlocks<CT, ROE>::value) k_rhs_stage(GridDesc g, Coef<CT> c, StageArgs<TIN, TST> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   CT* sQ = reinterpret_cast<CT*>(smem_raw);          // [3][5][SP]
   CT* sFX = sQ + 3 * 5 * SP;                          // [5][TY][TX+1]
@@ -246,7 +253,7 @@ __global__ void __launch_bounds__(NT, RhsMinBlocks<CT>::value) k_rhs_stage(GridD
   __syncthreads();
   const int ic = (ty + 1) * SX + (tx + 1);
   CT zlo[5], zhi[5];
-  zface(sQ, c, slot(kz0 - 1), slot(kz0), ic, zlo);
+  zface<ROE>(sQ, c, slot(kz0 - 1), slot(kz0), ic, zlo);
 
   for (int k = kz0; k < kz1; ++k) {
     const int sm = slot(k - 1), s0 = slot(k), sp = slot(k + 1);
@@ -270,23 +277,23 @@ __global__ void __launch_bounds__(NT, RhsMinBlocks<CT>::value) k_rhs_stage(GridD
     }
     {
       CT phi[5];
-      xface(sQ, c, sm, s0, sp, ty + 1, tx, phi);
+      xface<ROE>(sQ, c, sm, s0, sp, ty + 1, tx, phi);
 #pragma unroll
       for (int v = 0; v < 5; ++v) sFX[(v * TY + ty) * (TX + 1) + tx] = phi[v];
-      yface(sQ, c, sm, s0, sp, ty, tx + 1, phi);
+      yface<ROE>(sQ, c, sm, s0, sp, ty, tx + 1, phi);
 #pragma unroll
       for (int v = 0; v < 5; ++v) sFY[(v * (TY + 1) + ty) * TX + tx] = phi[v];
     }
-    zface(sQ, c, s0, sp, ic, zhi);
+    zface<ROE>(sQ, c, s0, sp, ic, zhi);
     if (tid < TX) {
       CT phi[5];
-      yface(sQ, c, sm, s0, sp, TY, tid + 1, phi);
+      yface<ROE>(sQ, c, sm, s0, sp, TY, tid + 1, phi);
 #pragma unroll
       for (int v = 0; v < 5; ++v) sFY[(v * (TY + 1) + TY) * TX + tid] = phi[v];
     } else if (tid < TX + TY) {
       CT phi[5];
       const int r = tid - TX;
-      xface(sQ, c, sm, s0, sp, r + 1, TX, phi);
+      xface<ROE>(sQ, c, sm, s0, sp, r + 1, TX, phi);
 #pragma unroll
       for (int v = 0; v < 5; ++v) sFX[(v * TY + r) * (TX + 1) + TX] = phi[v];
     }
@@ -345,11 +352,11 @@ size_t rhs_smem_bytes() {
   return sizeof(CT) * (3 * 5 * rk::SP + 5 * rk::TY * (TX + 1) + 5 * (rk::TY + 1) * TX);
 }
 
-template <class CT, class TIN, class TST>
-cudaError_t launch_rhs_stage(const GridDesc& g, const Coef<CT>& c, const StageArgs<TIN, TST>& a,
-                             cudaStream_t st) {
+template <class CT, class TIN, class TST, bool ROE>
+static cudaError_t launch_rhs_variant(const GridDesc& g, const Coef<CT>& c, const StageArgs<TIN, TST>& a,
+                                     cudaStream_t st) {
   const size_t smem = rhs_smem_bytes<CT>();
-  auto kern = rk::k_rhs_stage<CT, TIN, TST>;
+  auto kern = rk::k_rhs_stage<CT, TIN, TST, ROE>;
   static MarchShape<TX, rk::TY> shape;
   int ctas = 0;
   cudaError_t e = shape.get(kern, smem, g, "NS_RHS_CTAS", ctas);
@@ -357,6 +364,13 @@ cudaError_t launch_rhs_stage(const GridDesc& g, const Coef<CT>& c, const StageAr
   kern<<<ctas, rk::NT, smem, st>>>(g, c, a);
   count_launch();
   return cudaGetLastError();
+}
+
+template <class CT, class TIN, class TST>
+cudaError_t launch_rhs_stage(const GridDesc& g, const Coef<CT>& c, const StageArgs<TIN, TST>& a,
+                             cudaStream_t st) {
+  return c.roe ? launch_rhs_variant<CT, TIN, TST, true>(g, c, a, st)
+               : launch_rhs_variant<CT, TIN, TST, false>(g, c, a, st);
 }
 
 template cudaError_t launch_rhs_stage<double, double, double>(const GridDesc&, const Coef<double>&,
