@@ -15,25 +15,43 @@ constexpr int RG = 296;      // blocks per reduced quantity (2 x 148, fixed for 
 constexpr int RGS = 1184;    // blocks of the streaming field reductions (fixed for determinism)
 constexpr int OB = 64;       // threads per block of the objective face kernels
 
-template <class T, class Op>
-__device__ __forceinline__ T block_reduce(T v, T* sh, Op op) {
-  sh[threadIdx.x] = v;
-  __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s) sh[threadIdx.x] = op(sh[threadIdx.x], sh[threadIdx.x + s]);
-    __syncthreads();
-  }
-  T r = sh[0];
-  __syncthreads();
-  return r;
-}
-
 struct AddOp {
-  __device__ double operator()(double a, double b) const { return a + b; }
+  template <class T>
+  __device__ T operator()(T a, T b) const { return a + b; }
 };
 struct MaxOp {
-  __device__ double operator()(double a, double b) const { return fmax(a, b); }
+  template <class T>
+  __device__ T operator()(T a, T b) const { return fmax(a, b); }
 };
+
+// Butterfly reduction over the 32 lanes of a warp (every lane gets the result); the
+// order of the operations is fixed, so results are bitwise reproducible.
+template <class T, class Op>
+__device__ __forceinline__ T warp_reduce(T v, Op op) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = op(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Block reduction (blockDim.x a power-of-two multiple of 32, at most 1024): each warp
+// reduces its lanes in TW, the warp results are widened to double and reduced by the
+// first warp in FP64; every thread returns the result.  sh holds >= 32 doubles.  TW =
+// float serves maxima (exact in any type); sums are reduced in double.
+template <class TW, class Op>
+__device__ __forceinline__ double block_reduce(TW v, double* sh, Op op) {
+  v = warp_reduce(v, op);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();                 // sh may still be read by a previous reduction
+  if (lane == 0) sh[wid] = (double)v;
+  __syncthreads();
+  if (wid == 0) {
+    double x = lane < nw ? sh[lane] : 0.0;
+    for (int o = nw >> 1; o > 0; o >>= 1) x = op(x, __shfl_xor_sync(0xffffffffu, x, o));
+    if (lane == 0) sh[0] = x;
+  }
+  __syncthreads();
+  return sh[0];
+}
 
 // ---------------------------------------------------------------------------------
 // pressure-loss objective, Eq. (e:pressure_loss): per-face terms over a grid of
@@ -443,9 +461,11 @@ __device__ __forceinline__ void growth_matrix(const GridDesc& g, const Coef<CT>&
 template <class CT>
 __global__ void __launch_bounds__(RB) k_sigma1(GridDesc g, Coef<CT> c, const CT* __restrict__ w,
                                                float* __restrict__ sig, double* partial) {
-  __shared__ double sh[RB];
+  __shared__ double sh[32];
   const int b = blockIdx.y;
-  double vmax = 0.0, vsum = 0.0;
+  // the max in the compute type (exact in any type), the sum in FP64
+  CT vmax = CT(0);
+  double vsum = 0.0;
   for (long long i = (long long)blockIdx.x * RB + threadIdx.x; i < g.cells; i += (long long)gridDim.x * RB) {
     const int x = (int)(i % g.nx);
     const int y = (int)((i / g.nx) % g.ny);
@@ -455,14 +475,14 @@ __global__ void __launch_bounds__(RB) k_sigma1(GridDesc g, Coef<CT> c, const CT*
     const CT s1 = g.nz == 1 ? sigma1_of<CT, 4>(M) : sigma1_of<CT, 5>(M);
     const float sf = (float)s1;
     sig[(size_t)b * g.cells + i] = sf;
-    vmax = fmax(vmax, (double)sf);
+    vmax = fmax(vmax, CT(sf));
     vsum += (double)sf;
   }
-  vmax = block_reduce(vmax, sh, MaxOp());
-  vsum = block_reduce(vsum, sh, AddOp());
+  const double bmax = block_reduce(vmax, sh, MaxOp());
+  const double bsum = block_reduce(vsum, sh, AddOp());
   if (threadIdx.x == 0) {
-    partial[(size_t)b * 2 * gridDim.x + blockIdx.x] = vmax;
-    partial[(size_t)b * 2 * gridDim.x + gridDim.x + blockIdx.x] = vsum;
+    partial[(size_t)b * 2 * gridDim.x + blockIdx.x] = bmax;
+    partial[(size_t)b * 2 * gridDim.x + gridDim.x + blockIdx.x] = bsum;
   }
 }
 
