@@ -79,8 +79,11 @@ __device__ __forceinline__ FaceState face_state(const double* __restrict__ w, si
 }
 
 __device__ __forceinline__ double pt_factor(double B, double ex) {
-  // B^(gamma/(gamma-1)); gamma = 1.4 gives B^3.5 = B^3 sqrt(B)
-  return ex == 3.5 ? B * B * B * sqrt(B) : pow(B, ex);
+  // B^(gamma/(gamma-1)).  gamma = 1.4 gives the exponent 7/2, which the double
+  // quotient 1.4/0.4 misses by one ulp: within 1e-12 of 3.5 the closed form B^3 sqrt(B)
+  // is used (it differs from pow(B, 1.4/0.4) by about 1e-16 relative and costs a
+  // fraction of a double-precision pow)
+  return fabs(ex - 3.5) < 1e-12 ? B * B * B * sqrt(B) : pow(B, ex);
 }
 
 __global__ void __launch_bounds__(OB) k_obj_partial(GridDesc g, double gamma, int i0, double pt_in,
@@ -191,17 +194,19 @@ __global__ void __launch_bounds__(OMB) k_obj_sum(GridDesc g, double gamma, int i
   for (int f = blockIdx.x * OMB + threadIdx.x; f < nf; f += gridDim.x * OMB) {
     const FaceState F = face_state(w, box, g.cells, (size_t)f * g.nx, iL, iR, gm1);
     const double r = F.r, p = F.p, uu = F.uu;
-    const double B = 1.0 + 0.5 * gm1 * r * uu / (gamma * p);
+    const double ip = 1.0 / p;
+    const double B = 1.0 + 0.5 * gm1 / gamma * r * uu * ip;
     const double pt = p * pt_factor(B, ex);
     N += r * (pt_in - pt);
     D += r;
     if (want_grad) {
-      const double ir = 1.0 / r;
-      const double dr = pt * uu / (2.0 * p * B);
-      const double dp = pt / p * (1.0 - r * uu / (2.0 * p * B));
+      const double ir = 1.0 / r, iB = 1.0 / B;
+      const double ptpB = pt * ip * iB;             // pt / (p B)
+      const double dr = 0.5 * uu * ptpB;
+      const double dp = pt * ip - 0.5 * r * uu * ip * ptpB;
       double du[3];
 #pragma unroll
-      for (int k = 0; k < 3; ++k) du[k] = pt * r * F.u[k] / (p * B);
+      for (int k = 0; k < 3; ++k) du[k] = r * F.u[k] * ptpB;
       double* A = aface + ((size_t)b * nf + f) * 5;
       A[0] = (pt_in - pt) - r * (dr - (F.u[0] * du[0] + F.u[1] * du[1] + F.u[2] * du[2]) * ir + 0.5 * gm1 * uu * dp);
 #pragma unroll
