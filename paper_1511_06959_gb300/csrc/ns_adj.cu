@@ -547,7 +547,11 @@ __global__ void __launch_bounds__(NT, AdjMinBlocks<CT, ROE>::value) k_adj_stage(
         const size_t o = o0 + (size_t)v * g.cells;
         const CT gs = gin[v] + gout[v];
         if (a.Gout) a.Gout[o] = gs;
-        if (a.lam_out) a.lam_out[o] = (a.lam_in ? a.lam_in[o] : 0.0) + widen(gs);
+        if (a.lam_out) {
+          const double lv = (a.lam_in ? a.lam_in[o] : 0.0) + widen(gs);
+          a.lam_out[o] = lv;
+          if (a.lam_out_mirror) a.lam_out_mirror[o] = cvt<TST>(lv);
+        }
         if (a.Anext) a.Anext[o] = CT(a.cl) * lfv[v] + CT(a.cg) * gout[v] + CT(a.cs) * gs;
         if (a.SBout || a.sbar) {
           const CT ss = (a.SBin ? a.SBin[o] : CT(0)) + A0[v * SP + ic];

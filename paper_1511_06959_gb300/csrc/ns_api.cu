@@ -155,7 +155,7 @@ static cudaError_t adj_launch(ns_ctx* c, const Coef<CT>& cf, const ns::AdjArgs<T
 template <class CT>
 static int adjoint_step_t(ns_ctx* c, const Coef<CT>& cf, const CT* W1, const CT* lamf, const double* s,
                           const double* lam, const float* nu, double* lo, double* sbar,
-                          const CT* const* kept = nullptr) {
+                          const CT* const* kept = nullptr, CT* lo_mirror = nullptr) {
   const Scheme& sc = scheme_of(c);
   const double dt = c->p.dt;
   const CT* Wst[3];
@@ -196,6 +196,7 @@ static int adjoint_step_t(ns_ctx* c, const Coef<CT>& cf, const CT* W1, const CT*
     } else {
       a.lam_in = lam;
       a.lam_out = lo;
+      a.lam_out_mirror = lo_mirror;
     }
     if (sbar) {
       a.SBin = j == 0 ? nullptr : S;
@@ -415,9 +416,9 @@ int ns_growth_sigma1(ns_ctx* c, const double* w, float* sigma1, double* stats) {
   if (mixed(c)) {
     float* wf = buf<float>(c, WF);
     if (ns::launch_to_float(w, wf, c->field, c->st) != cudaSuccess) return NS_ERR_CUDA;
-    return cuerr(ns::launch_sigma1<float>(c->g, c->cf, wf, sigma1, stats, c->scratch, c->st));
+    return cuerr(ns::launch_sigma1<float>(c->g, c->cf, wf, sigma1, stats, c->scratch, c->ticket, c->st));
   }
-  return cuerr(ns::launch_sigma1<double>(c->g, c->cd, w, sigma1, stats, c->scratch, c->st));
+  return cuerr(ns::launch_sigma1<double>(c->g, c->cd, w, sigma1, stats, c->scratch, c->ticket, c->st));
 }
 
 static double nu_limit(const ns_ctx* c) {
@@ -442,7 +443,8 @@ int ns_apply_adjoint_viscosity(ns_ctx* c, const float* nu, const double* a, doub
 int ns_adjoint_energy(ns_ctx* c, const double* w, const double* lam, double* E) {
   if (!c || !w || !lam || !E) return NS_ERR_ARG;
   const double dV = c->p.dx * c->p.dy * c->p.dz;
-  return cuerr(ns::launch_energy(c->g, c->p.gamma, dV, w, lam, E, c->scratch, c->err, mixed(c), c->st));
+  return cuerr(ns::launch_energy(c->g, c->p.gamma, dV, w, lam, E, c->scratch, c->err, mixed(c), c->ticket,
+                                 c->st));
 }
 
 int ns_dot(ns_ctx* c, const double* a, const double* phi, int nphi, size_t n, double* out) {
@@ -602,7 +604,8 @@ int ns_i_primal(ns_ctx* c, const double* w, const void* w_mirror, const double* 
 }
 
 int ns_i_adjoint(ns_ctx* c, const double* w, const void* w_mirror, const void* const* kept3, const double* s,
-                 const double* lam, const float* nu, double* lo, double* sbar) {
+                 const double* lam, const void* lam_mirror, const float* nu, double* lo, void* lo_mirror,
+                 double* sbar) {
   if (mixed(c)) {
     const float* W1 = (const float*)w_mirror;
     if (!W1) {
@@ -610,17 +613,38 @@ int ns_i_adjoint(ns_ctx* c, const double* w, const void* w_mirror, const void* c
       if (ns::launch_to_float(w, wf, c->field, c->st) != cudaSuccess) return NS_ERR_CUDA;
       W1 = wf;
     }
-    float* lf = buf<float>(c, LF);
-    if (ns::launch_to_float(lam, lf, c->field, c->st) != cudaSuccess) return NS_ERR_CUDA;
-    return adjoint_step_t<float>(c, c->cf, W1, lf, s, lam, nu, lo, sbar, (const float* const*)kept3);
+    const float* lf = (const float*)lam_mirror;
+    if (!lf) {
+      float* t = buf<float>(c, LF);
+      if (ns::launch_to_float(lam, t, c->field, c->st) != cudaSuccess) return NS_ERR_CUDA;
+      lf = t;
+    }
+    return adjoint_step_t<float>(c, c->cf, W1, lf, s, lam, nu, lo, sbar, (const float* const*)kept3,
+                                 (float*)lo_mirror);
   }
   return adjoint_step_t<double>(c, c->cd, w, lam, s, lam, nu, lo, sbar, (const double* const*)kept3);
 }
 
-int ns_i_sigma1(ns_ctx* c, const double* w, const void* w_mirror, float* sigma1, double* stats) {
-  if (mixed(c) && w_mirror)
-    return cuerr(ns::launch_sigma1<float>(c->g, c->cf, (const float*)w_mirror, sigma1, stats, c->scratch, c->st));
-  return ns_growth_sigma1(c, w, sigma1, stats);
+int ns_i_objective(ns_ctx* c, const double* w, double weight, double* J_acc, double* lam, void* lam_mirror) {
+  return cuerr(ns::launch_objective_fast(c->g, c->p.gamma, c->p.plane_i, c->p.pt_in, w, weight, J_acc, lam,
+                                         c->err, c->scratch, c->ticket, c->st,
+                                         mixed(c) ? (float*)lam_mirror : nullptr));
+}
+
+int ns_i_sigma1(ns_ctx* c, const double* w, const void* w_mirror, float* sigma1, double* stats, double lambda,
+                double tau, float* nu) {
+  ns::NuRule rule{(float)lambda, (float)tau, (float)nu_limit(c), nu, c->err};
+  const ns::NuRule* rp = nu ? &rule : nullptr;
+  if (mixed(c)) {
+    const float* wf = (const float*)w_mirror;
+    if (!wf) {
+      float* t = buf<float>(c, WF);
+      if (ns::launch_to_float(w, t, c->field, c->st) != cudaSuccess) return NS_ERR_CUDA;
+      wf = t;
+    }
+    return cuerr(ns::launch_sigma1<float>(c->g, c->cf, wf, sigma1, stats, c->scratch, c->ticket, c->st, rp));
+  }
+  return cuerr(ns::launch_sigma1<double>(c->g, c->cd, w, sigma1, stats, c->scratch, c->ticket, c->st, rp));
 }
 
 size_t ns_i_stage_bytes(const ns_ctx* c) { return c->field * (mixed(c) ? sizeof(float) : sizeof(double)); }

@@ -47,6 +47,12 @@ void ns_sweep_release(ns_ctx* c);
 int ns_i_primal(ns_ctx* c, const double* w, const void* w_mirror, const double* s, double* wo, void* wo_mirror,
                 void* const* keep3);
 int ns_i_adjoint(ns_ctx* c, const double* w, const void* w_mirror, const void* const* kept3, const double* s,
-                 const double* lam, const float* nu, double* lo, double* sbar);
-int ns_i_sigma1(ns_ctx* c, const double* w, const void* w_mirror, float* sigma1, double* stats);
+                 const double* lam, const void* lam_mirror, const float* nu, double* lo, void* lo_mirror,
+                 double* sbar);
+// ns_objective that also keeps a stage-type mirror of lam (mixed mode; may be null) in step
+int ns_i_objective(ns_ctx* c, const double* w, double weight, double* J_acc, double* lam, void* lam_mirror);
+// sigma_1 (and its stats when stats != null); with nu != null also the viscosity of the
+// sigma_1 rule (nu = lambda sigma_1 [sigma_1 > tau]) with the stability flag
+int ns_i_sigma1(ns_ctx* c, const double* w, const void* w_mirror, float* sigma1, double* stats,
+                double lambda = 0.0, double tau = 0.0, float* nu = nullptr);
 size_t ns_i_stage_bytes(const ns_ctx* c);

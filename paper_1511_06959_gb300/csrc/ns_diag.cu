@@ -244,7 +244,7 @@ __global__ void __launch_bounds__(OMB) k_obj_sum(GridDesc g, double gamma, int i
 }
 
 __global__ void k_obj_scatter(GridDesc g, int i0, const double* __restrict__ aface, const double* __restrict__ ndsc,
-                              double* __restrict__ lam) {
+                              double* __restrict__ lam, float* __restrict__ lamf) {
   const int nf = g.ny * g.nz;
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (long long)nf * g.batch) return;
@@ -256,8 +256,11 @@ __global__ void k_obj_scatter(GridDesc g, int i0, const double* __restrict__ afa
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
     const double gd = sc * (A[v] - (v == 0 ? NoD : 0.0));
-    lam[box + v * g.cells + row + iL] += gd;
-    lam[box + v * g.cells + row + iR] += gd;
+    const size_t oL = box + v * g.cells + row + iL, oR = box + v * g.cells + row + iR;
+    lam[oL] += gd;
+    if (lamf) lamf[oL] = d2f(lam[oL]);
+    lam[oR] += gd;
+    if (lamf) lamf[oR] = d2f(lam[oR]);
   }
 }
 
@@ -464,9 +467,11 @@ __device__ __forceinline__ void growth_matrix(const GridDesc& g, const Coef<CT>&
 }
 
 template <class CT>
-__global__ void __launch_bounds__(RB) k_sigma1(GridDesc g, Coef<CT> c, const CT* __restrict__ w,
-                                               float* __restrict__ sig, double* partial) {
+__global__ void __launch_bounds__(RB, sizeof(CT) == 4 ? 4 : 1) k_sigma1(GridDesc g, Coef<CT> c, const CT* __restrict__ w,
+                                               float* __restrict__ sig, double* partial, double* stats,
+                                               unsigned* ticket, NuRule rule) {
   __shared__ double sh[32];
+  __shared__ bool last;
   const int b = blockIdx.y;
   // the max in the compute type (exact in any type), the sum in FP64
   CT vmax = CT(0);
@@ -479,15 +484,42 @@ __global__ void __launch_bounds__(RB) k_sigma1(GridDesc g, Coef<CT> c, const CT*
     growth_matrix<CT>(g, c, w, b, x, y, z, M);
     const CT s1 = g.nz == 1 ? sigma1_of<CT, 4>(M) : sigma1_of<CT, 5>(M);
     const float sf = (float)s1;
-    sig[(size_t)b * g.cells + i] = sf;
+    const size_t o = (size_t)b * g.cells + i;
+    sig[o] = sf;
+    if (rule.nu) {
+      const float v = sf > rule.tau ? rule.lam * sf : 0.0f;
+      rule.nu[o] = v;
+      if (!(v <= rule.limit)) atomicOr(rule.err, ERRBIT_UNSTABLE);
+    }
     vmax = fmax(vmax, CT(sf));
     vsum += (double)sf;
   }
+  if (!stats) return;
   const double bmax = block_reduce(vmax, sh, MaxOp());
   const double bsum = block_reduce(vsum, sh, AddOp());
+  double* pmax = partial + (size_t)b * 2 * gridDim.x;
+  double* psum = pmax + gridDim.x;
   if (threadIdx.x == 0) {
-    partial[(size_t)b * 2 * gridDim.x + blockIdx.x] = bmax;
-    partial[(size_t)b * 2 * gridDim.x + gridDim.x + blockIdx.x] = bsum;
+    pmax[blockIdx.x] = bmax;
+    psum[blockIdx.x] = bsum;
+    __threadfence();
+    last = atomicAdd(&ticket[b], 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  // the last block of the box: fixed-order reduction of the block partials
+  __threadfence();
+  double m = 0.0, t = 0.0;
+  for (int j = threadIdx.x; j < (int)gridDim.x; j += RB) {
+    m = fmax(m, pmax[j]);
+    t += psum[j];
+  }
+  m = block_reduce(m, sh, MaxOp());
+  t = block_reduce(t, sh, AddOp());
+  if (threadIdx.x == 0) {
+    stats[2 * b] = m;
+    stats[2 * b + 1] = t / (double)g.cells;
+    ticket[b] = 0u;
   }
 }
 
@@ -556,22 +588,6 @@ __global__ void __launch_bounds__(RB) k_label(GridDesc g, Coef<CT> c, const CT* 
   acc[i] += (float)rate;
 }
 
-__global__ void __launch_bounds__(RB) k_sigma1_stats(int nblk, double inv_cells, const double* partial,
-                                                     double* stats) {
-  __shared__ double sh[RB];
-  const int b = blockIdx.x;
-  double vmax = 0.0, vsum = 0.0;
-  for (int i = threadIdx.x; i < nblk; i += RB) {
-    vmax = fmax(vmax, partial[(size_t)b * 2 * nblk + i]);
-    vsum += partial[(size_t)b * 2 * nblk + nblk + i];
-  }
-  vmax = block_reduce(vmax, sh, MaxOp());
-  vsum = block_reduce(vsum, sh, AddOp());
-  if (threadIdx.x == 0) {
-    stats[2 * b] = vmax;
-    stats[2 * b + 1] = vsum * inv_cells;
-  }
-}
 
 // ---------------------------------------------------------------------------------
 // added adjoint viscosity: coefficient rule and the operator alone
@@ -642,17 +658,38 @@ __device__ __forceinline__ double energy_cell(const double* __restrict__ w, cons
   return widen(v0 * v0 + y1 * y1 + y2 * y2 + y3 * y3 + v4 * v4);
 }
 
+// E[b] = dV sum_cells |v_hat|^2; the last block of each box adds the block partials in
+// fixed order (ticket: per-box counters, zero on entry and on exit).
 template <class T>
-__global__ void __launch_bounds__(RB) k_energy(GridDesc g, double gamma, const double* __restrict__ w,
-                                               const double* __restrict__ lam, double* partial) {
-  __shared__ double sh[RB];
+__global__ void __launch_bounds__(RB, sizeof(T) == 4 ? 8 : 1) k_energy(GridDesc g, double gamma, double dV, const double* __restrict__ w,
+                                               const double* __restrict__ lam, double* partial, double* E,
+                                               unsigned* err, unsigned* ticket) {
+  __shared__ double sh[32];
+  __shared__ bool last;
   const int b = blockIdx.y;
   const size_t box = (size_t)b * 5 * g.cells;
   double acc = 0.0;
   for (long long i = (long long)blockIdx.x * RB + threadIdx.x; i < g.cells; i += (long long)gridDim.x * RB)
     acc += energy_cell<T>(w, lam, box, g.cells, i, T(gamma));
   acc = block_reduce(acc, sh, AddOp());
-  if (threadIdx.x == 0) partial[(size_t)b * gridDim.x + blockIdx.x] = acc;
+  double* pb = partial + (size_t)b * gridDim.x;
+  if (threadIdx.x == 0) {
+    pb[blockIdx.x] = acc;
+    __threadfence();
+    last = atomicAdd(&ticket[b], 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double t = 0.0;
+  for (int j = threadIdx.x; j < (int)gridDim.x; j += RB) t += pb[j];
+  t = block_reduce(t, sh, AddOp());
+  if (threadIdx.x == 0) {
+    const double v = t * dV;
+    E[b] = v;
+    if (!isfinite(v)) atomicOr(err, ERRBIT_NONFINITE);
+    ticket[b] = 0u;
+  }
 }
 
 __global__ void __launch_bounds__(RB) k_sum_partials(int nblk, double scale, const double* partial,
@@ -785,7 +822,7 @@ cudaError_t launch_objective(const GridDesc& g, double gamma, int plane_i, doubl
 
 cudaError_t launch_objective_fast(const GridDesc& g, double gamma, int plane_i, double pt_in, const double* w,
                                   double weight, double* J_acc, double* lam, unsigned* err, double* scratch,
-                                  unsigned* ticket, cudaStream_t st) {
+                                  unsigned* ticket, cudaStream_t st, float* lam_mirror) {
   const int nf = g.ny * g.nz;
   int nblk = (nf + OMB - 1) / OMB;
   if (nblk > RG) nblk = RG;
@@ -798,27 +835,25 @@ cudaError_t launch_objective_fast(const GridDesc& g, double gamma, int plane_i, 
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || !lam) return e;
   const long long n = (long long)nf * g.batch;
-  k_obj_scatter<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(g, plane_i, aface, ndsc, lam);
+  k_obj_scatter<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(g, plane_i, aface, ndsc, lam, lam_mirror);
   count_launch();
   return cudaGetLastError();
 }
 
 template <class CT>
 cudaError_t launch_sigma1(const GridDesc& g, const Coef<CT>& c, const CT* w, float* sigma1,
-                          double* stats, double* scratch, cudaStream_t st) {
+                          double* stats, double* scratch, unsigned* ticket, cudaStream_t st,
+                          const NuRule* rule) {
   dim3 grid(RGS, g.batch);
-  k_sigma1<CT><<<grid, RB, 0, st>>>(g, c, w, sigma1, scratch);
-  count_launch();
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess || !stats) return e;
-  k_sigma1_stats<<<g.batch, RB, 0, st>>>(RGS, 1.0 / (double)g.cells, scratch, stats);
+  const NuRule r = rule ? *rule : NuRule{0.f, 0.f, 0.f, nullptr, nullptr};
+  k_sigma1<CT><<<grid, RB, 0, st>>>(g, c, w, sigma1, scratch, stats, ticket, r);
   count_launch();
   return cudaGetLastError();
 }
 template cudaError_t launch_sigma1<double>(const GridDesc&, const Coef<double>&, const double*, float*,
-                                           double*, double*, cudaStream_t);
+                                           double*, double*, unsigned*, cudaStream_t, const NuRule*);
 template cudaError_t launch_sigma1<float>(const GridDesc&, const Coef<float>&, const float*, float*,
-                                          double*, double*, cudaStream_t);
+                                          double*, double*, unsigned*, cudaStream_t, const NuRule*);
 
 template <class CT>
 cudaError_t launch_label(const GridDesc& g, const Coef<CT>& c, const CT* w, const double* lam, float* acc,
@@ -852,17 +887,13 @@ cudaError_t launch_visc_apply(const GridDesc& g, const double* idx2, const doubl
 }
 
 cudaError_t launch_energy(const GridDesc& g, double gamma, double dV, const double* w, const double* lam,
-                          double* E, double* scratch, unsigned* err, bool fp32_transform,
+                          double* E, double* scratch, unsigned* err, bool fp32_transform, unsigned* ticket,
                           cudaStream_t st) {
   dim3 grid(RGS, g.batch);
   if (fp32_transform)
-    k_energy<float><<<grid, RB, 0, st>>>(g, gamma, w, lam, scratch);
+    k_energy<float><<<grid, RB, 0, st>>>(g, gamma, dV, w, lam, scratch, E, err, ticket);
   else
-    k_energy<double><<<grid, RB, 0, st>>>(g, gamma, w, lam, scratch);
-  count_launch();
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  k_sum_partials<<<g.batch, RB, 0, st>>>(RGS, dV, scratch, E, err);
+    k_energy<double><<<grid, RB, 0, st>>>(g, gamma, dV, w, lam, scratch, E, err, ticket);
   count_launch();
   return cudaGetLastError();
 }

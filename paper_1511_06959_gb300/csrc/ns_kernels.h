@@ -56,6 +56,7 @@ struct AdjArgs {
   double cl, cg, cs;      // Anext = cl lamf + cg g + cs (Gin + g)
   const double* lam_in;
   double* lam_out;
+  TST* lam_out_mirror;    // lam_out rounded to the stage type (when lam_out != 0)
   const TST* SBin;
   TST* SBout;
   double* sbar;
@@ -78,10 +79,21 @@ cudaError_t launch_objective(const GridDesc& g, double gamma, int plane_i, doubl
 // two-launch objective (value in one launch); ticket: batch zero-initialised counters
 cudaError_t launch_objective_fast(const GridDesc& g, double gamma, int plane_i, double pt_in, const double* w,
                                    double weight, double* J_acc, double* lam, unsigned* err, double* scratch,
-                                   unsigned* ticket, cudaStream_t st);
+                                   unsigned* ticket, cudaStream_t st, float* lam_mirror = nullptr);
+// nu = lam sigma_1 where sigma_1 > tau, else 0, with the stability flag (see k_nu_rule)
+struct NuRule {
+  float lam, tau, limit;
+  float* nu;      // null: no viscosity output
+  unsigned* err;
+};
+
+// sigma_1 per cell; stats (may be null): [batch][2] = (max, mean), reduced by the last
+// block of each box (ticket: per-box counters, zero on entry and on exit); rule (may be
+// null): also writes the viscosity of the sigma_1 rule.
 template <class CT>
 cudaError_t launch_sigma1(const GridDesc& g, const Coef<CT>& c, const CT* w, float* sigma1,
-                          double* stats, double* scratch, cudaStream_t st);
+                          double* stats, double* scratch, unsigned* ticket, cudaStream_t st,
+                          const NuRule* rule = nullptr);
 template <class CT>
 cudaError_t launch_label(const GridDesc& g, const Coef<CT>& c, const CT* w, const double* lam, float* acc,
                          cudaStream_t st);
@@ -91,7 +103,7 @@ cudaError_t launch_visc_apply(const GridDesc& g, const double* idx2, const doubl
                               const float* nu, const double* a, double* out, cudaStream_t st);
 cudaError_t launch_energy(const GridDesc& g, double gamma, double dV, const double* w,
                           const double* lam, double* E, double* scratch, unsigned* err,
-                          bool fp32_transform, cudaStream_t st);
+                          bool fp32_transform, unsigned* ticket, cudaStream_t st);
 cudaError_t launch_dot(const double* a, const double* phi, int nphi, size_t n, double* out,
                        double* scratch, cudaStream_t st);
 cudaError_t launch_combine(const double* theta, const double* phi, int nphi, size_t n,

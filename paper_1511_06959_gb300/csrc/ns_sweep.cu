@@ -175,12 +175,14 @@ int make_plan(int N, int schedule, int param, Planner& P) {
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Arena regions.  mir: two stage-type fields holding float mirrors of consecutive
-// states of an ADVANCE run (mixed precision).  keep: for stride schedules, one entry of
+// states of an ADVANCE run (mixed precision).  lmir: two float mirrors of the adjoint,
+// written by the last adjoint stage and kept in step by the objective source, so that
+// the next adjoint step needs no conversion (mixed precision).  keep: for stride schedules, one entry of
 // four stage-type fields per step of the segment being reversed (the mirror of w^n and
 // the stage states W2..W4 computed when the segment was replayed), so that the adjoint
 // of a replayed step neither recomputes its stages nor converts its state.
 struct Layout {
-  size_t state, lam, sig, nu, scal, feat, stage, mir, keep, total;
+  size_t state, lam, sig, nu, scal, feat, stage, mir, lmir, keep, total;
   int nbuf, nkeep;
 };
 
@@ -196,9 +198,10 @@ Layout layout_for(const ns_ctx* c, int slots_used, bool closure, int schedule, i
   L.feat = closure ? align256(cellsb * 16 * sizeof(float)) : 0;
   L.stage = align256(ns_i_stage_bytes(c));
   L.mir = 2 * L.stage;
+  L.lmir = c->p.precision == NS_MIXED ? 2 * L.stage : 0;
   L.nkeep = schedule == NS_CKPT_STRIDE ? param : 0;
   L.keep = (size_t)L.nkeep * 4 * L.stage;
-  L.total = L.state * L.nbuf + L.lam + L.sig + L.nu + L.scal + L.feat + L.mir + L.keep;
+  L.total = L.state * L.nbuf + L.lam + L.sig + L.nu + L.scal + L.feat + L.mir + L.lmir + L.keep;
   return L;
 }
 
@@ -258,6 +261,9 @@ struct ns_sweep_state {
   std::vector<char*> keep;           // [nkeep][4]
   std::vector<char> has_mirror, has_stages;
   int seg = -1;                      // first step of the segment the keep entries belong to
+  char* lamf_cur = nullptr;          // float mirror of lam_cur (mixed), valid when lamf_valid
+  char* lamf_nxt = nullptr;
+  bool lamf_valid = false;
   bool kept_valid(int n) const { return L.nkeep > 0 && seg >= 0 && (n / L.nkeep) * L.nkeep == seg; }
 };
 
@@ -353,6 +359,7 @@ int run_actions(ns_ctx* c, ns_sweep_state& S, int stop_op, double*& lam_cur, dou
         break;
       case NS_OP_SOURCE:
         if ((r = ns_objective(c, ptr(S.cur), wN, S.jtmp, lam_cur))) return r;
+        S.lamf_valid = false;
         if (S.o.record_energy && energy &&
             (r = ns_adjoint_energy(c, ptr(S.cur), lam_cur, energy + (size_t)A.a * B)))
           return r;
@@ -373,20 +380,25 @@ int run_actions(ns_ctx* c, ns_sweep_state& S, int stop_op, double*& lam_cur, dou
         const float* nup = nullptr;
         if (need_sigma) {
           double* stats = S.o.record_sigma && sigma_stats ? sigma_stats + (size_t)A.a * 2 * B : nullptr;
-          if ((r = ns_i_sigma1(c, ptr(S.cur), mirror, S.sig, stats))) return r;
+          // the sigma_1 rule's viscosity comes out of the same launch as sigma_1
+          const bool rule = !S.o.mlp && S.o.lambda > 0.0;
+          if ((r = ns_i_sigma1(c, ptr(S.cur), mirror, S.sig, stats, S.o.lambda, S.o.tau, rule ? S.nu : nullptr)))
+            return r;
           if (S.o.mlp) {
             if ((r = ns_mlp_features(c, ptr(S.cur), S.feat))) return r;
             if ((r = ns_mlp_infer(c, S.o.mlp, S.feat, S.sig, S.o.lambda, S.nu))) return r;
             nup = S.nu;
-          } else if (S.o.lambda > 0.0) {
-            if ((r = ns_add_adjoint_viscosity(c, S.sig, S.o.lambda, S.o.tau, S.nu))) return r;
+          } else if (rule) {
             nup = S.nu;
           }
         }
-        if ((r = ns_i_adjoint(c, ptr(S.cur), mirror, kept ? kept3 : nullptr, S.s, lam_cur, nup, lam_nxt, sbar)))
+        if ((r = ns_i_adjoint(c, ptr(S.cur), mirror, kept ? kept3 : nullptr, S.s, lam_cur,
+                              S.lamf_valid ? S.lamf_cur : nullptr, nup, lam_nxt, S.lamf_nxt, sbar)))
           return r;
         std::swap(lam_cur, lam_nxt);
-        if (A.a >= 1 && (r = ns_objective(c, ptr(S.cur), wN, S.jtmp, lam_cur))) return r;
+        std::swap(S.lamf_cur, S.lamf_nxt);
+        S.lamf_valid = S.lamf_cur != nullptr;
+        if (A.a >= 1 && (r = ns_i_objective(c, ptr(S.cur), wN, S.jtmp, lam_cur, S.lamf_cur))) return r;
         if (S.o.record_energy && energy &&
             (r = ns_adjoint_energy(c, ptr(S.cur), lam_cur, energy + (size_t)A.a * B)))
           return r;
@@ -440,6 +452,9 @@ int ns_forward_run(ns_ctx* c, const double* w0, const double* s, const ns_run_op
   S->mir[0] = q;
   S->mir[1] = q + S->L.stage;
   q += S->L.mir;
+  S->lamf_cur = S->L.lmir ? q : nullptr;
+  S->lamf_nxt = S->L.lmir ? q + S->L.stage : nullptr;
+  q += S->L.lmir;
   S->keep.resize((size_t)S->L.nkeep * 4);
   for (size_t i = 0; i < S->keep.size(); ++i) S->keep[i] = q + i * S->L.stage;
   S->has_mirror.assign(S->L.nkeep, 0);
@@ -468,6 +483,7 @@ int ns_backward_run(ns_ctx* c, double* lam0, double* sbar, double* energy, doubl
   double* lam_nxt = (N % 2 == 0) ? S.lamA : lam0;
   if (cudaMemsetAsync(lam_cur, 0, fbytes, c->st) != cudaSuccess) return NS_ERR_CUDA;
   if (sbar && cudaMemsetAsync(sbar, 0, fbytes, c->st) != cudaSuccess) return NS_ERR_CUDA;
+  S.lamf_valid = false;
   S.forward_done = false;   // a plan is reversed once
   S.in_backward = true;
   int r = run_actions(c, S, 0, lam_cur, lam_nxt, sbar, energy, sigma_stats);
