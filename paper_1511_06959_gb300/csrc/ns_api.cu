@@ -625,6 +625,16 @@ int ns_i_adjoint(ns_ctx* c, const double* w, const void* w_mirror, const void* c
   return adjoint_step_t<double>(c, c->cd, w, lam, s, lam, nu, lo, sbar, (const double* const*)kept3);
 }
 
+int ns_i_energy(ns_ctx* c, const double* w, const void* w_mirror, const double* lam, const void* lam_mirror,
+                double* E) {
+  if (mixed(c) && w_mirror && lam_mirror) {
+    const double dV = c->p.dx * c->p.dy * c->p.dz;
+    return cuerr(ns::launch_energy_mirrors(c->g, c->p.gamma, dV, (const float*)w_mirror, (const float*)lam_mirror,
+                                           E, c->scratch, c->err, c->ticket, c->st));
+  }
+  return ns_adjoint_energy(c, w, lam, E);
+}
+
 int ns_i_objective(ns_ctx* c, const double* w, double weight, double* J_acc, double* lam, void* lam_mirror) {
   return cuerr(ns::launch_objective_fast(c->g, c->p.gamma, c->p.plane_i, c->p.pt_in, w, weight, J_acc, lam,
                                          c->err, c->scratch, c->ticket, c->st,

@@ -49,6 +49,9 @@ int ns_i_primal(ns_ctx* c, const double* w, const void* w_mirror, const double* 
 int ns_i_adjoint(ns_ctx* c, const double* w, const void* w_mirror, const void* const* kept3, const double* s,
                  const double* lam, const void* lam_mirror, const float* nu, double* lo, void* lo_mirror,
                  double* sbar);
+// ns_adjoint_energy from the float mirrors of w and lam when both are given (mixed mode)
+int ns_i_energy(ns_ctx* c, const double* w, const void* w_mirror, const double* lam, const void* lam_mirror,
+                double* E);
 // ns_objective that also keeps a stage-type mirror of lam (mixed mode; may be null) in step
 int ns_i_objective(ns_ctx* c, const double* w, double weight, double* J_acc, double* lam, void* lam_mirror);
 // sigma_1 (and its stats when stats != null); with nu != null also the viscosity of the

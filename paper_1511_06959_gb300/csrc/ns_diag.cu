@@ -636,8 +636,8 @@ __global__ void k_visc_apply(GridDesc g, double ix2, double iy2, double iz2, dou
 // ---------------------------------------------------------------------------------
 // adjoint energy: v_hat = S^-T V^-T w_hat in closed form ("Symmetrization")
 // ---------------------------------------------------------------------------------
-template <class T>
-__device__ __forceinline__ double energy_cell(const double* __restrict__ w, const double* __restrict__ lam,
+template <class T, class TIN>
+__device__ __forceinline__ double energy_cell(const TIN* __restrict__ w, const TIN* __restrict__ lam,
                                               size_t box, long long cells, long long i, T gamma) {
   const T gm1 = gamma - T(1), sg = sqrt(gamma), sgg = sqrt(gm1 / gamma);
   const T r = cvt<T>(w[box + i]), ir = T(1) / r;
@@ -660,9 +660,9 @@ __device__ __forceinline__ double energy_cell(const double* __restrict__ w, cons
 
 // E[b] = dV sum_cells |v_hat|^2; the last block of each box adds the block partials in
 // fixed order (ticket: per-box counters, zero on entry and on exit).
-template <class T>
-__global__ void __launch_bounds__(RB, sizeof(T) == 4 ? 8 : 1) k_energy(GridDesc g, double gamma, double dV, const double* __restrict__ w,
-                                               const double* __restrict__ lam, double* partial, double* E,
+template <class T, class TIN>
+__global__ void __launch_bounds__(RB, sizeof(T) == 4 ? 8 : 1) k_energy(GridDesc g, double gamma, double dV, const TIN* __restrict__ w,
+                                               const TIN* __restrict__ lam, double* partial, double* E,
                                                unsigned* err, unsigned* ticket) {
   __shared__ double sh[32];
   __shared__ bool last;
@@ -670,7 +670,7 @@ __global__ void __launch_bounds__(RB, sizeof(T) == 4 ? 8 : 1) k_energy(GridDesc 
   const size_t box = (size_t)b * 5 * g.cells;
   double acc = 0.0;
   for (long long i = (long long)blockIdx.x * RB + threadIdx.x; i < g.cells; i += (long long)gridDim.x * RB)
-    acc += energy_cell<T>(w, lam, box, g.cells, i, T(gamma));
+    acc += energy_cell<T, TIN>(w, lam, box, g.cells, i, T(gamma));
   acc = block_reduce(acc, sh, AddOp());
   double* pb = partial + (size_t)b * gridDim.x;
   if (threadIdx.x == 0) {
@@ -891,9 +891,17 @@ cudaError_t launch_energy(const GridDesc& g, double gamma, double dV, const doub
                           cudaStream_t st) {
   dim3 grid(RGS, g.batch);
   if (fp32_transform)
-    k_energy<float><<<grid, RB, 0, st>>>(g, gamma, dV, w, lam, scratch, E, err, ticket);
+    k_energy<float, double><<<grid, RB, 0, st>>>(g, gamma, dV, w, lam, scratch, E, err, ticket);
   else
-    k_energy<double><<<grid, RB, 0, st>>>(g, gamma, dV, w, lam, scratch, E, err, ticket);
+    k_energy<double, double><<<grid, RB, 0, st>>>(g, gamma, dV, w, lam, scratch, E, err, ticket);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_energy_mirrors(const GridDesc& g, double gamma, double dV, const float* wf, const float* lamf,
+                                  double* E, double* scratch, unsigned* err, unsigned* ticket, cudaStream_t st) {
+  dim3 grid(RGS, g.batch);
+  k_energy<float, float><<<grid, RB, 0, st>>>(g, gamma, dV, wf, lamf, scratch, E, err, ticket);
   count_launch();
   return cudaGetLastError();
 }

@@ -104,6 +104,10 @@ cudaError_t launch_visc_apply(const GridDesc& g, const double* idx2, const doubl
 cudaError_t launch_energy(const GridDesc& g, double gamma, double dV, const double* w,
                           const double* lam, double* E, double* scratch, unsigned* err,
                           bool fp32_transform, unsigned* ticket, cudaStream_t st);
+// The same from the float mirrors of w and lam (mixed precision): the FP32 transform
+// reads the rounded values directly, so each cell's term is bit-identical.
+cudaError_t launch_energy_mirrors(const GridDesc& g, double gamma, double dV, const float* wf, const float* lamf,
+                                  double* E, double* scratch, unsigned* err, unsigned* ticket, cudaStream_t st);
 cudaError_t launch_dot(const double* a, const double* phi, int nphi, size_t n, double* out,
                        double* scratch, cudaStream_t st);
 cudaError_t launch_combine(const double* theta, const double* phi, int nphi, size_t n,

@@ -400,7 +400,8 @@ int run_actions(ns_ctx* c, ns_sweep_state& S, int stop_op, double*& lam_cur, dou
         S.lamf_valid = S.lamf_cur != nullptr;
         if (A.a >= 1 && (r = ns_i_objective(c, ptr(S.cur), wN, S.jtmp, lam_cur, S.lamf_cur))) return r;
         if (S.o.record_energy && energy &&
-            (r = ns_adjoint_energy(c, ptr(S.cur), lam_cur, energy + (size_t)A.a * B)))
+            (r = ns_i_energy(c, ptr(S.cur), mirror, lam_cur, S.lamf_valid ? S.lamf_cur : nullptr,
+                             energy + (size_t)A.a * B)))
           return r;
         break;
       }
