@@ -205,9 +205,8 @@ __device__ __forceinline__ void xpacket(const CT* sQ, const CT* F0, const Coef<C
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     const CT* p0 = Q0 + (1 + k) * SP;
-    gy[k] = (p0[iL + SX] - p0[iL - SX] + p0[iR + SX] - p0[iR - SX]) * c.i4dx[1];
-    gz[k] = (Qp[(1 + k) * SP + iL] - Qm[(1 + k) * SP + iL] + Qp[(1 + k) * SP + iR] -
-             Qm[(1 + k) * SP + iR]) * c.i4dx[2];
+    diff4_pair(p0[iL + SX], p0[iL - SX], p0[iR + SX], p0[iR - SX], c.i4dx[1], Qp[(1 + k) * SP + iL],
+               Qm[(1 + k) * SP + iL], Qp[(1 + k) * SP + iR], Qm[(1 + k) * SP + iR], c.i4dx[2], gy[k], gz[k]);
   }
   const CT sv[3] = {xf(F0, 0, row, fx), xf(F0, 1, row, fx), xf(F0, 2, row, fx)};
   face_packet_s<0>(c, sv, xf(F0, 3, row, fx), Q0, iL, Q0, iR, gy, gz, pk);
@@ -224,9 +223,8 @@ __device__ __forceinline__ void ypacket(const CT* sQ, const CT* F0, const Coef<C
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     const CT* p0 = Q0 + (1 + k) * SP;
-    gz[k] = (Qp[(1 + k) * SP + iL] - Qm[(1 + k) * SP + iL] + Qp[(1 + k) * SP + iR] -
-             Qm[(1 + k) * SP + iR]) * c.i4dx[2];
-    gx[k] = (p0[iL + 1] - p0[iL - 1] + p0[iR + 1] - p0[iR - 1]) * c.i4dx[0];
+    diff4_pair(Qp[(1 + k) * SP + iL], Qm[(1 + k) * SP + iL], Qp[(1 + k) * SP + iR], Qm[(1 + k) * SP + iR],
+               c.i4dx[2], p0[iL + 1], p0[iL - 1], p0[iR + 1], p0[iR - 1], c.i4dx[0], gz[k], gx[k]);
   }
   const CT sv[3] = {yf(F0, 0, fy, col), yf(F0, 1, fy, col), yf(F0, 2, fy, col)};
   face_packet_s<1>(c, sv, yf(F0, 3, fy, col), Q0, iL, Q0, iR, gz, gx, pk);
@@ -242,8 +240,8 @@ __device__ __forceinline__ void zpacket(const CT* sQ, const CT* sA, const Coef<C
   for (int k = 0; k < 3; ++k) {
     const CT* a = QL + (1 + k) * SP;
     const CT* bq = QR + (1 + k) * SP;
-    gx[k] = (a[i + 1] - a[i - 1] + bq[i + 1] - bq[i - 1]) * c.i4dx[0];
-    gy[k] = (a[i + SX] - a[i - SX] + bq[i + SX] - bq[i - SX]) * c.i4dx[1];
+    diff4_pair(a[i + 1], a[i - 1], bq[i + 1], bq[i - 1], c.i4dx[0], a[i + SX], a[i - SX], bq[i + SX],
+               bq[i - SX], c.i4dx[1], gx[k], gy[k]);
   }
   face_packet<2>(c, QL, sA + sL * 5 * SP, i, QR, sA + sR * 5 * SP, i, gx, gy, pk);
 }

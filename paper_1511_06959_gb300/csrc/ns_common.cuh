@@ -19,6 +19,7 @@
 #include <stdlib.h>
 
 #include <atomic>
+#include <type_traits>
 
 namespace ns {
 
@@ -192,6 +193,30 @@ __device__ __forceinline__ double val(Dual a) { return a.v; }
 __device__ __forceinline__ double tan_of(Dual a) { return a.d; }
 
 template <class T> __device__ __forceinline__ T one_over(T a) { return T(1) / a; }
+
+// ---------------------------------------------------------------------------------
+// Paired FP32 arithmetic (sm_100 family): one instruction does two independent FP32
+// operations.  t2 = ((a - b) + c - d) * s for two such expressions at once, with the
+// same rounding as the scalar left-to-right evaluation (a - b is fma(b, -1, a)).
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+
+template <class CT>
+__device__ __forceinline__ void diff4_pair(CT a1, CT b1, CT c1, CT d1, CT s1, CT a2, CT b2, CT c2, CT d2, CT s2,
+                                           CT& r1, CT& r2) {
+  if constexpr (std::is_same<CT, float>::value) {
+    float2 t = sub2(f2(a1, a2), f2(b1, b2));
+    t = __fadd2_rn(t, f2(c1, c2));
+    t = sub2(t, f2(d1, d2));
+    t = __fmul2_rn(t, f2(s1, s2));
+    r1 = t.x;
+    r2 = t.y;
+  } else {
+    r1 = (a1 - b1 + c1 - d1) * s1;
+    r2 = (a2 - b2 + c2 - d2) * s2;
+  }
+}
 
 // ---------------------------------------------------------------------------------
 // error word bits (sticky, OR-ed by kernels, read by ns_last_error)

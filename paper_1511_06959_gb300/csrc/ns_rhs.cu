@@ -138,17 +138,37 @@ __device__ __forceinline__ void face_flux(const Coef<CT>& c, const CT* qL, const
   CT fv4 = c.alpha * g[3][D];
 #pragma unroll
   for (int j = 0; j < 3; ++j) fv4 = fv4 + CT(0.5) * (qL[1 + j] + qR[1 + j]) * sig[j];
-  const CT pL = c.gm1 * qL[0] * qL[4];
-  const CT pR = c.gm1 * qR[0] * qR[4];
-  const CT mL = qL[0] * qL[1 + D];
-  const CT mR = qR[0] * qR[1 + D];
-  const CT kL = CT(0.5) * (qL[1] * qL[1] + qL[2] * qL[2] + qL[3] * qL[3]);
-  const CT kR = CT(0.5) * (qR[1] * qR[1] + qR[2] * qR[2] + qR[3] * qR[3]);
-  phi[0] = CT(0.5) * (mL + mR);
+  if constexpr (std::is_same<CT, float>::value) {
+    // the left and right cells' Euler fluxes side by side in paired FP32 instructions
+    const float2 Q0 = f2(qL[0], qR[0]), Q4 = f2(qL[4], qR[4]), QD = f2(qL[1 + D], qR[1 + D]);
+    const float2 P = __fmul2_rn(__fmul2_rn(f2(c.gm1, c.gm1), Q0), Q4);         // p
+    const float2 M = __fmul2_rn(Q0, QD);                                          // rho u_D
+    float2 K = __fmul2_rn(f2(qL[1], qR[1]), f2(qL[1], qR[1]));
+    K = __ffma2_rn(f2(qL[2], qR[2]), f2(qL[2], qR[2]), K);
+    K = __ffma2_rn(f2(qL[3], qR[3]), f2(qL[3], qR[3]), K);
+    K = __fmul2_rn(f2(0.5f, 0.5f), K);                                          // |u|^2 / 2
+    phi[0] = 0.5f * (M.x + M.y);
 #pragma unroll
-  for (int k = 0; k < 3; ++k) phi[1 + k] = CT(0.5) * (mL * qL[1 + k] + mR * qR[1 + k]) - sig[k];
-  phi[1 + D] = phi[1 + D] + CT(0.5) * (pL + pR);
-  phi[4] = CT(0.5) * (mL * (qL[4] + kL) + pL * qL[1 + D] + mR * (qR[4] + kR) + pR * qR[1 + D]) - fv4;
+    for (int k = 0; k < 3; ++k) {
+      const float2 T = __fmul2_rn(M, f2(qL[1 + k], qR[1 + k]));
+      phi[1 + k] = 0.5f * (T.x + T.y) - sig[k];
+    }
+    phi[1 + D] = phi[1 + D] + 0.5f * (P.x + P.y);
+    const float2 E = __ffma2_rn(P, QD, __fmul2_rn(M, __fadd2_rn(Q4, K)));
+    phi[4] = 0.5f * (E.x + E.y) - fv4;
+  } else {
+    const CT pL = c.gm1 * qL[0] * qL[4];
+    const CT pR = c.gm1 * qR[0] * qR[4];
+    const CT mL = qL[0] * qL[1 + D];
+    const CT mR = qR[0] * qR[1 + D];
+    const CT kL = CT(0.5) * (qL[1] * qL[1] + qL[2] * qL[2] + qL[3] * qL[3]);
+    const CT kR = CT(0.5) * (qR[1] * qR[1] + qR[2] * qR[2] + qR[3] * qR[3]);
+    phi[0] = CT(0.5) * (mL + mR);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) phi[1 + k] = CT(0.5) * (mL * qL[1 + k] + mR * qR[1 + k]) - sig[k];
+    phi[1 + D] = phi[1 + D] + CT(0.5) * (pL + pR);
+    phi[4] = CT(0.5) * (mL * (qL[4] + kL) + pL * qL[1 + D] + mR * (qR[4] + kR) + pR * qR[1 + D]) - fv4;
+  }
   if constexpr (ROE) {
     CT Dv[5];
     roe_dissipation<D>(c, qL, qR, Dv);
@@ -178,8 +198,8 @@ __device__ __forceinline__ void xface(const CT* sQ, const Coef<CT>& c, int sm, i
     const CT* p0 = qs(sQ, s0, 1 + k);
     const CT* pm = qs(sQ, sm, 1 + k);
     const CT* pp = qs(sQ, sp, 1 + k);
-    gy[k] = (p0[iL + SX] - p0[iL - SX] + p0[iR + SX] - p0[iR - SX]) * c.i4dx[1];
-    gz[k] = (pp[iL] - pm[iL] + pp[iR] - pm[iR]) * c.i4dx[2];
+    diff4_pair(p0[iL + SX], p0[iL - SX], p0[iR + SX], p0[iR - SX], c.i4dx[1], pp[iL], pm[iL], pp[iR], pm[iR],
+               c.i4dx[2], gy[k], gz[k]);
   }
   face_flux<0, ROE>(c, qL, qR, gy, gz, phi);
 }
@@ -200,8 +220,8 @@ __device__ __forceinline__ void yface(const CT* sQ, const Coef<CT>& c, int sm, i
     const CT* p0 = qs(sQ, s0, 1 + k);
     const CT* pm = qs(sQ, sm, 1 + k);
     const CT* pp = qs(sQ, sp, 1 + k);
-    gz[k] = (pp[iL] - pm[iL] + pp[iR] - pm[iR]) * c.i4dx[2];
-    gx[k] = (p0[iL + 1] - p0[iL - 1] + p0[iR + 1] - p0[iR - 1]) * c.i4dx[0];
+    diff4_pair(pp[iL], pm[iL], pp[iR], pm[iR], c.i4dx[2], p0[iL + 1], p0[iL - 1], p0[iR + 1], p0[iR - 1],
+               c.i4dx[0], gz[k], gx[k]);
   }
   face_flux<1, ROE>(c, qL, qR, gz, gx, phi);
 }
@@ -220,8 +240,8 @@ __device__ __forceinline__ void zface(const CT* sQ, const Coef<CT>& c, int sL, i
   for (int k = 0; k < 4; ++k) {
     const CT* a = qs(sQ, sL, 1 + k);
     const CT* bq = qs(sQ, sR, 1 + k);
-    gx[k] = (a[i + 1] - a[i - 1] + bq[i + 1] - bq[i - 1]) * c.i4dx[0];
-    gy[k] = (a[i + SX] - a[i - SX] + bq[i + SX] - bq[i - SX]) * c.i4dx[1];
+    diff4_pair(a[i + 1], a[i - 1], bq[i + 1], bq[i - 1], c.i4dx[0], a[i + SX], a[i - SX], bq[i + SX],
+               bq[i - SX], c.i4dx[1], gx[k], gy[k]);
   }
   face_flux<2, ROE>(c, qL, qR, gx, gy, phi);
 }
