@@ -72,6 +72,8 @@ WORKLOADS = {
     # 3D transonic turbulent box, a snapshot every 50 steps
     "box128": Workload("box128", 128, 64, 64, "turbulence", 0.9, 1e4, 1000, "stride", param=50,
                        rms=0.10, seed=2, lam_tilde=0.1),
+    # z-aligned vortex columns, the autograd and closure-judging size (8 boxes in a batch)
+    "column96": Workload("column96", 96, 48, 48, "vortex", 0.5, 1e3, 100, "all", seed=3, batch=8),
     # large transonic box, binomial checkpointing inside a 60 GB budget (500-step window)
     "box512": Workload("box512", 512, 256, 128, "turbulence", 0.9, 5e4, 500, "revolve",
                        budget_gb=60.0, rms=0.08, seed=4, lam_tilde=0.1),
