@@ -183,6 +183,23 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows), "power_w_max": pmax}
 
 
+def max_over_ranks(ms, t_e2e, ws, device):
+    """The slowest rank's step time and end-to-end time (every rank gets them)."""
+    if ws <= 1:
+        return ms, t_e2e
+    import torch
+    tt = torch.tensor([ms, t_e2e], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+    return tt[0].item(), tt[1].item()
+
+
+def whole_job_rates(ws, cell_steps, ms, t_e2e):
+    """Adjoint cell-steps/s of the whole job: every rank reverses its own box (weak
+    scaling, no data-path collective), so the job's work is ws boxes in the slowest
+    rank's time."""
+    return ws * cell_steps / (ms * 1e-3), ws * cell_steps / t_e2e
+
+
 def run_ours(args, wl):
     import torch
 
@@ -287,12 +304,8 @@ def run_ours(args, wl):
 
     cell_steps = wl.cells * wl.batch * wl.nsteps
     # max over ranks
-    if ws > 1:
-        tt = torch.tensor([ms, t_e2e], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        ms, t_e2e = tt[0].item(), tt[1].item()
-    value = ws * cell_steps / (ms * 1e-3)
-    e2e_value = ws * cell_steps / t_e2e
+    ms, t_e2e = max_over_ranks(ms, t_e2e, ws, dev)
+    value, e2e_value = whole_job_rates(ws, cell_steps, ms, t_e2e)
 
     out = None
     if rank == 0:
