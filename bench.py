@@ -270,8 +270,8 @@ def run_ours(args, wl):
         torch.distributed.barrier()
     ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
     # Kernel durations: a second pass of the same K steps with CUDA events recorded by the
-    # library around every adjoint-stage launch on its stream (the event records cost a
-    # few per cent of a step, so the headline value comes from the pass without them).
+    # library on its stream around each step's run of adjoint-stage launches (the event
+    # records cost a little, so the headline value comes from the pass without them).
     S.profile_enable(True)
     for i in range(args.steps):
         flush.fill_(i & 0xFF)
@@ -331,7 +331,7 @@ def run_ours(args, wl):
                          "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                          "traffic": adj_traffic(wl, args.precision),
                          "avg_launch_us": 1e3 * kavg, "launches": klaunch,
-                         "kernel_timing": "second K-step pass, CUDA events around each launch",
+                         "kernel_timing": "second K-step pass, CUDA events around each step's adjoint-stage launches",
                          "bytes_per_launch": bytes_launch, "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(w0.numel() * 8),
                     "d2h_bytes_per_step": int(lam0.numel() * 8 + J.numel() * 8)},

@@ -273,8 +273,10 @@ int ns_dot_boxes(ns_ctx* ctx, const double* field, int comp, const double* phi, 
                  double* out);
 
 /* Kernel timing for roofline reports: when on, the context records a CUDA event pair
- * around every adjoint-stage kernel it launches; ns_profile_read synchronises and
- * returns the summed milliseconds and the launch count since profiling was enabled. */
+ * around the consecutive adjoint-stage launches of each adjoint step (4 for RK4, 3 for
+ * SSP-RK3; the time between them is the launches and the in-stream gaps between them);
+ * ns_profile_read synchronises and returns the summed milliseconds of the pairs and the
+ * number of adjoint-stage launches they bracket since profiling was enabled. */
 int ns_profile_enable(ns_ctx* ctx, int on);
 int ns_profile_read(ns_ctx* ctx, double* ms, long long* launches);
 

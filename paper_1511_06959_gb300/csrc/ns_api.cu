@@ -130,7 +130,8 @@ static int primal_step_t(ns_ctx* c, const Coef<CT>& cf, const CT* W1, const doub
   return NS_OK;
 }
 
-// CUDA event pair around one adjoint-stage launch when kernel profiling is on.
+// One CUDA event of the profiling pairs (kernel profiling on): a pair brackets the
+// consecutive adjoint-stage launches of one step.
 static void prof_mark(ns_ctx* c) {
   if (!c->prof_on) return;
   if (c->prof_used == c->events.size()) {
@@ -143,10 +144,8 @@ static void prof_mark(ns_ctx* c) {
 
 template <class CT, class TIN, class TA, class TST>
 static cudaError_t adj_launch(ns_ctx* c, const Coef<CT>& cf, const ns::AdjArgs<TIN, TA, TST>& a) {
-  prof_mark(c);
-  cudaError_t e = ns::launch_adj_stage<CT, TIN, TA, TST>(c->g, cf, a, c->st);
-  prof_mark(c);
-  return e;
+  if (c->prof_on) ++c->prof_launches;
+  return ns::launch_adj_stage<CT, TIN, TA, TST>(c->g, cf, a, c->st);
 }
 
 // Recompute the stage states W2..W_ns from W1 = w^n (unless kept), then the transposed
@@ -181,6 +180,7 @@ static int adjoint_step_t(ns_ctx* c, const Coef<CT>& cf, const CT* W1, const CT*
     }
   }
   const CT* Ain = lamf;
+  prof_mark(c);
   for (int j = 0; j < sc.ns; ++j) {
     const bool last = j == sc.ns - 1;
     CT* Aout = last ? nullptr : (j % 2 == 0 ? Aa : Ab);
@@ -205,6 +205,7 @@ static int adjoint_step_t(ns_ctx* c, const Coef<CT>& cf, const CT* W1, const CT*
     if (adj_launch(c, cf, a) != cudaSuccess) return NS_ERR_CUDA;
     Ain = Aout;
   }
+  prof_mark(c);
   return NS_OK;
 }
 
@@ -565,7 +566,10 @@ int ns_last_error(ns_ctx* c) {
 
 extern "C" int ns_profile_enable(ns_ctx* c, int on) {
   if (!c) return NS_ERR_ARG;
-  if (on && !c->prof_on) c->prof_used = 0;
+  if (on && !c->prof_on) {
+    c->prof_used = 0;
+    c->prof_launches = 0;
+  }
   c->prof_on = on != 0;
   return NS_OK;
 }
@@ -580,8 +584,9 @@ extern "C" int ns_profile_read(ns_ctx* c, double* ms, long long* launches) {
     tot += t;
   }
   *ms = tot;
-  *launches = (long long)(c->prof_used / 2);
+  *launches = c->prof_launches;
   c->prof_used = 0;
+  c->prof_launches = 0;
   return NS_OK;
 }
 

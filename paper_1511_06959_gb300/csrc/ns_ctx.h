@@ -29,8 +29,9 @@ struct ns_ctx {
   size_t scratch_n = 0;
   unsigned* err = nullptr;       // sticky device error word
   size_t ws_bytes = 0;
-  bool prof_on = false;          // event pairs around adjoint-stage launches
+  bool prof_on = false;          // event pairs around each step's adjoint-stage launches
   size_t prof_used = 0;
+  long long prof_launches = 0;   // adjoint-stage launches inside the event pairs
   std::vector<cudaEvent_t> events;
   ns_sweep_state* sweep = nullptr;   // executor state between ns_forward_run and ns_backward_run
   double* qbar = nullptr;            // box-mean primitive states [batch][5] (closure features)
