@@ -141,7 +141,9 @@ class ClockSampler:
     def __init__(self, bus_id):
         self.bus_id = bus_id
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        import tempfile
+        out = os.environ.get("NS_RESULTS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(out, f"clocks_{os.getpid()}.csv")
 
     def start(self):
         try:
