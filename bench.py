@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--nu-split", default="1,1,1",
                     help="added-viscosity factors for the rho, rho u, rho E adjoints")
+    ap.add_argument("--closure", action="store_true",
+                    help="the learned viscosity closure (an MLP network, kappa = 0.5) inside the sweep "
+                         "instead of the sigma_1 rule")
     ap.add_argument("--flux", default="central", choices=["central", "roe"],
                     help="convective face flux (the workload's is central; roe adds the paper's "
                          "Roe dissipation)")
@@ -233,7 +236,12 @@ def run_ours(args, wl):
     field_bytes = w0.numel() * 8
     param = wl.param if wl.schedule != "revolve" or wl.param else C.revolve_slots(wl, field_bytes)
     sched = C.SCHEDULES[wl.schedule]
-    opts = S.run_opts(wl.nsteps, sched, param, wl.lam_coef, 0.0, True, True)
+    net = None
+    if args.closure:
+        from paper_1511_06959_gb300 import closure
+        net = closure.Network(S, closure.init_params(3, out_bias=0.5))
+    opts = S.run_opts(wl.nsteps, sched, param, 0.5 if net is not None else wl.lam_coef, 0.0, True, True,
+                      net.blob if net is not None else None)
     arena = torch.empty(S.arena_bytes(opts), dtype=torch.uint8, device=dev)
     J = torch.empty(wl.batch, dtype=torch.float64, device=dev)
     lam0 = torch.empty_like(w0)
@@ -324,6 +332,7 @@ def run_ours(args, wl):
             "data": "synthetic",
             "config": {"workload": C.describe(wl, args.scheme, args.flux), "name": wl.name, "cells": wl.cells,
                        "scheme": args.scheme, "flux": args.flux, "nu_split": list(split),
+                       "viscosity": "learned closure (MLP, kappa 0.5)" if args.closure else "sigma_1 rule",
                        "nsteps": wl.nsteps, "schedule": wl.schedule, "param": param,
                        "lambda_tilde": wl.lam_tilde, "precision": args.precision, "dt": dt,
                        "l2": "flushed (256 MB write) between timed steps; arena "
@@ -340,7 +349,7 @@ def run_ours(args, wl):
             "gpu_launches": gl,
             "clocks": clocks,
         }
-        if not args.no_fp64_compare and prec == api.NS_MIXED:
+        if not args.no_fp64_compare and prec == api.NS_MIXED and not args.closure:
             out["fp64"] = fp64_compare(api, torch, wl, w0, dt, sched, param, lam0, Jv, scheme, split, flux)
         if not args.no_cpu_baseline and ws == 1:
             out["cpu_baseline"] = cpu_baseline(wl, args.scheme, args.flux)

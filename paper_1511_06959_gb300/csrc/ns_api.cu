@@ -662,4 +662,11 @@ int ns_i_sigma1(ns_ctx* c, const double* w, const void* w_mirror, float* sigma1,
   return cuerr(ns::launch_sigma1<double>(c->g, c->cd, w, sigma1, stats, c->scratch, c->ticket, c->st, rp));
 }
 
+int ns_i_mlp_features(ns_ctx* c, const double* w, const void* w_mirror, float* feat) {
+  if (!mixed(c) || !w_mirror) return ns_mlp_features(c, w, feat);
+  const float* wf = (const float*)w_mirror;
+  if (ns::launch_box_means(c->g, c->p.gamma, wf, c->qbar, c->scratch, c->st) != cudaSuccess) return NS_ERR_CUDA;
+  return cuerr(ns::launch_features(c->g, c->cf, wf, c->qbar, feat, c->st));
+}
+
 size_t ns_i_stage_bytes(const ns_ctx* c) { return c->field * (mixed(c) ? sizeof(float) : sizeof(double)); }

@@ -50,6 +50,8 @@ int ns_i_primal(ns_ctx* c, const double* w, const void* w_mirror, const double* 
 int ns_i_adjoint(ns_ctx* c, const double* w, const void* w_mirror, const void* const* kept3, const double* s,
                  const double* lam, const void* lam_mirror, const float* nu, double* lo, void* lo_mirror,
                  double* sbar);
+// ns_mlp_features from the float mirror of w when given (mixed mode; the same bits)
+int ns_i_mlp_features(ns_ctx* c, const double* w, const void* w_mirror, float* feat);
 // ns_adjoint_energy from the float mirrors of w and lam when both are given (mixed mode)
 int ns_i_energy(ns_ctx* c, const double* w, const void* w_mirror, const double* lam, const void* lam_mirror,
                 double* E);

@@ -27,21 +27,27 @@ namespace {
 constexpr int RB = 256;
 constexpr int RGM = 296;
 
+// a state value as float: the FP64 state rounded (d2f), or the float mirror as it is
+// (the mirror holds exactly d2f of the state, so both give the same bits)
+__device__ __forceinline__ float ldf(const double* p, size_t o) { return d2f(p[o]); }
+__device__ __forceinline__ float ldf(const float* p, size_t o) { return p[o]; }
+
 // ------------------------------------------------------------------------------------
 // box means of (rho, u1, u2, u3, p): FP32 per cell, FP64 sums, deterministic
 // ------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(RB) k_box_means(GridDesc g, float gamma, const double* __restrict__ w,
+template <class TIN>
+__global__ void __launch_bounds__(RB) k_box_means(GridDesc g, float gamma, const TIN* __restrict__ w,
                                                   double* partial) {
   __shared__ double sh[5][RB];
   const int b = blockIdx.y;
   const size_t box = (size_t)b * 5 * g.cells;
   double acc[5] = {0, 0, 0, 0, 0};
   for (long long i = (long long)blockIdx.x * RB + threadIdx.x; i < g.cells; i += (long long)gridDim.x * RB) {
-    const float r = d2f(w[box + i]);
+    const float r = ldf(w, box + i);
     const float ir = 1.0f / r;
-    const float u0 = d2f(w[box + g.cells + i]) * ir, u1 = d2f(w[box + 2 * g.cells + i]) * ir,
-                u2 = d2f(w[box + 3 * g.cells + i]) * ir;
-    const float p = (gamma - 1.0f) * (d2f(w[box + 4 * g.cells + i]) - 0.5f * r * (u0 * u0 + u1 * u1 + u2 * u2));
+    const float u0 = ldf(w, box + g.cells + i) * ir, u1 = ldf(w, box + 2 * g.cells + i) * ir,
+                u2 = ldf(w, box + 3 * g.cells + i) * ir;
+    const float p = (gamma - 1.0f) * (ldf(w, box + 4 * g.cells + i) - 0.5f * r * (u0 * u0 + u1 * u1 + u2 * u2));
     acc[0] += f2d(r);
     acc[1] += f2d(u0);
     acc[2] += f2d(u1);
@@ -78,7 +84,8 @@ __global__ void __launch_bounds__(RB) k_box_means_final(int nblk, double inv_cel
 // ------------------------------------------------------------------------------------
 // features
 // ------------------------------------------------------------------------------------
-__global__ void k_features(GridDesc g, Coef<float> c, const double* __restrict__ w, const double* qbar,
+template <class TIN>
+__global__ void k_features(GridDesc g, Coef<float> c, const TIN* __restrict__ w, const double* qbar,
                            float* __restrict__ feat) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= g.cells * g.batch) return;
@@ -88,16 +95,16 @@ __global__ void k_features(GridDesc g, Coef<float> c, const double* __restrict__
   const float gam = c.gamma, gm1 = c.gm1;
   auto vel = [&](int xx, int yy, int zz, float* u) {
     const size_t o = box + (size_t)wrap(zz, g.nz) * g.plane + (size_t)wrap(yy, g.ny) * g.nx + wrap(xx, g.nx);
-    const float ir = 1.0f / d2f(w[o]);
-    u[0] = d2f(w[o + g.cells]) * ir;
-    u[1] = d2f(w[o + 2 * g.cells]) * ir;
-    u[2] = d2f(w[o + 3 * g.cells]) * ir;
+    const float ir = 1.0f / ldf(w, o);
+    u[0] = ldf(w, o + g.cells) * ir;
+    u[1] = ldf(w, o + 2 * g.cells) * ir;
+    u[2] = ldf(w, o + 3 * g.cells) * ir;
   };
   const size_t o = box + r;
-  const float rho = d2f(w[o]);
+  const float rho = ldf(w, o);
   float u[3];
   vel(x, y, z, u);
-  const float p = gm1 * (d2f(w[o + 4 * g.cells]) - 0.5f * rho * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]));
+  const float p = gm1 * (ldf(w, o + 4 * g.cells) - 0.5f * rho * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]));
   const float rb = (float)qbar[b * 5 + 0], pb = (float)qbar[b * 5 + 4];
   const float cb = sqrtf(gam * pb / rb);
   const float icb = 1.0f / cb;
@@ -148,37 +155,36 @@ __device__ __forceinline__ void mma_bf16(float d[4], const unsigned a[4], unsign
 }
 
 // ------------------------------------------------------------------------------------
-// tensor-core inference: one warp per 16-cell tile, weights held as B fragments
+// tensor-core inference: one warp per 16-cell tile; the weights are staged once per CTA
+// in shared memory (rows padded so that the B-fragment reads of a warp hit distinct
+// banks) and read as B fragments per mma, which keeps the registers, and so the number
+// of resident warps that hide the GELU latency, at three CTAs of 256 threads per SM
 // ------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_mlp_infer(long long n, MlpView net, const float* __restrict__ feat,
-                                                   const float* __restrict__ sigma1, float scale, float limit_nu,
-                                                   float* __restrict__ nu, unsigned* err) {
+constexpr int W1S = 12;   // padded row stride (32-bit words) of W1t: 16 bf16 = 8 words
+constexpr int W2S = 36;   // padded row stride of W2t: 64 bf16 = 32 words
+
+__global__ void __launch_bounds__(256, 3) k_mlp_infer(long long n, MlpView net, const float* __restrict__ feat,
+                                                      const float* __restrict__ sigma1, float scale, float limit_nu,
+                                                      float* __restrict__ nu, unsigned* err) {
+  __shared__ unsigned sW1[NH * W1S];
+  __shared__ unsigned sW2[NH * W2S];
+  __shared__ float sb1[NH], sb2[NH], sw3[NH];
+  {
+    const unsigned* w1 = reinterpret_cast<const unsigned*>(net.W1t);
+    const unsigned* w2 = reinterpret_cast<const unsigned*>(net.W2t);
+    for (int i = threadIdx.x; i < NH * 8; i += blockDim.x) sW1[(i >> 3) * W1S + (i & 7)] = w1[i];
+    for (int i = threadIdx.x; i < NH * 32; i += blockDim.x) sW2[(i >> 5) * W2S + (i & 31)] = w2[i];
+    for (int i = threadIdx.x; i < NH; i += blockDim.x) {
+      sb1[i] = net.b1[i];
+      sb2[i] = net.b2[i];
+      sw3[i] = net.w3q[i];
+    }
+  }
+  __syncthreads();
   const int lane = threadIdx.x & 31;
   const int gq = lane >> 2, tq = lane & 3;
   const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-  // B fragments: W1t[n][k] (n-major, k padded to 16), W2t[n][k]
-  unsigned w1b[8][2], w2b[8][4][2];
-#pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    const int nn = 8 * j + gq;
-    w1b[j][0] = *reinterpret_cast<const unsigned*>(net.W1t + nn * 16 + 2 * tq);
-    w1b[j][1] = *reinterpret_cast<const unsigned*>(net.W1t + nn * 16 + 2 * tq + 8);
-#pragma unroll
-    for (int kk = 0; kk < 4; ++kk) {
-      w2b[j][kk][0] = *reinterpret_cast<const unsigned*>(net.W2t + nn * 64 + 16 * kk + 2 * tq);
-      w2b[j][kk][1] = *reinterpret_cast<const unsigned*>(net.W2t + nn * 64 + 16 * kk + 2 * tq + 8);
-    }
-  }
-  float bb1[8][2], bb2[8][2], ww3[8][2];
-#pragma unroll
-  for (int j = 0; j < 8; ++j)
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-      bb1[j][e] = net.b1[8 * j + 2 * tq + e];
-      bb2[j][e] = net.b2[8 * j + 2 * tq + e];
-      ww3[j][e] = net.w3q[8 * j + 2 * tq + e];
-    }
   const float b3 = net.b3[0];
   const long long ntiles = (n + 15) / 16;
   for (long long tile = warp; tile < ntiles; tile += nwarps) {
@@ -192,12 +198,14 @@ __global__ void __launch_bounds__(256) k_mlp_infer(long long n, MlpView net, con
     float h1[8][4];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
+      const int row = (8 * j + gq) * W1S + tq;
       h1[j][0] = h1[j][1] = h1[j][2] = h1[j][3] = 0.0f;
-      mma_bf16(h1[j], a, w1b[j][0], w1b[j][1]);
-      h1[j][0] = gelu(h1[j][0] + bb1[j][0]);
-      h1[j][1] = gelu(h1[j][1] + bb1[j][1]);
-      h1[j][2] = gelu(h1[j][2] + bb1[j][0]);
-      h1[j][3] = gelu(h1[j][3] + bb1[j][1]);
+      mma_bf16(h1[j], a, sW1[row], sW1[row + 4]);
+      const float c0 = sb1[8 * j + 2 * tq], c1 = sb1[8 * j + 2 * tq + 1];
+      h1[j][0] = gelu(h1[j][0] + c0);
+      h1[j][1] = gelu(h1[j][1] + c1);
+      h1[j][2] = gelu(h1[j][2] + c0);
+      h1[j][3] = gelu(h1[j][3] + c1);
     }
     unsigned a2[4][4];
 #pragma unroll
@@ -211,10 +219,13 @@ __global__ void __launch_bounds__(256) k_mlp_infer(long long n, MlpView net, con
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       float z[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+      const int row = (8 * j + gq) * W2S + tq;
 #pragma unroll
-      for (int kk = 0; kk < 4; ++kk) mma_bf16(z, a2[kk], w2b[j][kk][0], w2b[j][kk][1]);
-      y0 += gelu(z[0] + bb2[j][0]) * ww3[j][0] + gelu(z[1] + bb2[j][1]) * ww3[j][1];
-      y1 += gelu(z[2] + bb2[j][0]) * ww3[j][0] + gelu(z[3] + bb2[j][1]) * ww3[j][1];
+      for (int kk = 0; kk < 4; ++kk) mma_bf16(z, a2[kk], sW2[row + 8 * kk], sW2[row + 8 * kk + 4]);
+      const float c0 = sb2[8 * j + 2 * tq], c1 = sb2[8 * j + 2 * tq + 1];
+      const float v0 = sw3[8 * j + 2 * tq], v1 = sw3[8 * j + 2 * tq + 1];
+      y0 += gelu(z[0] + c0) * v0 + gelu(z[1] + c1) * v1;
+      y1 += gelu(z[2] + c0) * v0 + gelu(z[3] + c1) * v1;
     }
     y0 += __shfl_xor_sync(0xffffffffu, y0, 1);
     y0 += __shfl_xor_sync(0xffffffffu, y0, 2);
@@ -454,9 +465,10 @@ MlpView mlp_view(void* blob) {
   return v;
 }
 
-cudaError_t launch_box_means(const GridDesc& g, double gamma, const double* w, double* qbar, double* scratch,
+template <class TIN>
+cudaError_t launch_box_means(const GridDesc& g, double gamma, const TIN* w, double* qbar, double* scratch,
                              cudaStream_t st) {
-  k_box_means<<<dim3(RGM, g.batch), RB, 0, st>>>(g, (float)gamma, w, scratch);
+  k_box_means<TIN><<<dim3(RGM, g.batch), RB, 0, st>>>(g, (float)gamma, w, scratch);
   count_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -467,19 +479,26 @@ cudaError_t launch_box_means(const GridDesc& g, double gamma, const double* w, d
 
 size_t box_means_scratch_doubles(const GridDesc& g) { return (size_t)5 * RGM * g.batch; }
 
-cudaError_t launch_features(const GridDesc& g, const Coef<float>& c, const double* w, const double* qbar,
+template <class TIN>
+cudaError_t launch_features(const GridDesc& g, const Coef<float>& c, const TIN* w, const double* qbar,
                             float* feat, cudaStream_t st) {
   const long long n = g.cells * g.batch;
-  k_features<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g, c, w, qbar, feat);
+  k_features<TIN><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g, c, w, qbar, feat);
   count_launch();
   return cudaGetLastError();
 }
+template cudaError_t launch_box_means<double>(const GridDesc&, double, const double*, double*, double*, cudaStream_t);
+template cudaError_t launch_box_means<float>(const GridDesc&, double, const float*, double*, double*, cudaStream_t);
+template cudaError_t launch_features<double>(const GridDesc&, const Coef<float>&, const double*, const double*,
+                                             float*, cudaStream_t);
+template cudaError_t launch_features<float>(const GridDesc&, const Coef<float>&, const float*, const double*,
+                                            float*, cudaStream_t);
 
 cudaError_t launch_mlp_infer(long long n, void* blob, const float* feat, const float* sigma1, double scale,
                              double limit_nu, float* nu, unsigned* err, cudaStream_t st) {
   const long long tiles = (n + 15) / 16;
   long long blocks = (tiles + 7) / 8;
-  if (blocks > 4 * 152) blocks = 4 * 152;
+  if (blocks > 3 * 152) blocks = 3 * 152;   // one wave at three resident CTAs per SM
   if (blocks < 1) blocks = 1;
   k_mlp_infer<<<(unsigned)blocks, 256, 0, st>>>(n, mlp_view(blob), feat, sigma1, (float)scale, (float)limit_nu,
                                                 nu, err);

@@ -46,10 +46,12 @@ struct MlpView {
 };
 
 MlpView mlp_view(void* blob);
-cudaError_t launch_box_means(const GridDesc& g, double gamma, const double* w, double* qbar, double* scratch,
+template <class TIN>
+cudaError_t launch_box_means(const GridDesc& g, double gamma, const TIN* w, double* qbar, double* scratch,
                              cudaStream_t st);
 size_t box_means_scratch_doubles(const GridDesc& g);
-cudaError_t launch_features(const GridDesc& g, const Coef<float>& c, const double* w, const double* qbar,
+template <class TIN>
+cudaError_t launch_features(const GridDesc& g, const Coef<float>& c, const TIN* w, const double* qbar,
                             float* feat, cudaStream_t st);
 cudaError_t launch_mlp_infer(long long n, void* blob, const float* feat, const float* sigma1, double scale,
                              double limit_nu, float* nu, unsigned* err, cudaStream_t st);

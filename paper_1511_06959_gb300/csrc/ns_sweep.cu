@@ -385,7 +385,7 @@ int run_actions(ns_ctx* c, ns_sweep_state& S, int stop_op, double*& lam_cur, dou
           if ((r = ns_i_sigma1(c, ptr(S.cur), mirror, S.sig, stats, S.o.lambda, S.o.tau, rule ? S.nu : nullptr)))
             return r;
           if (S.o.mlp) {
-            if ((r = ns_mlp_features(c, ptr(S.cur), S.feat))) return r;
+            if ((r = ns_i_mlp_features(c, ptr(S.cur), mirror, S.feat))) return r;
             if ((r = ns_mlp_infer(c, S.o.mlp, S.feat, S.sig, S.o.lambda, S.nu))) return r;
             nup = S.nu;
           } else if (rule) {
