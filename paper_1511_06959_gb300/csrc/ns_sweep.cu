@@ -254,6 +254,7 @@ struct ns_sweep_state {
   int touched = 0;
   size_t pos = 0;     // next action
   bool forward_done = false;
+  bool obj_forward = true;           // evaluate J(w^n) when the forward pass first reaches n
   bool in_backward = false;
   bool mixed = false;
   char* mir[2] = {nullptr, nullptr};
@@ -333,7 +334,7 @@ int run_actions(ns_ctx* c, ns_sweep_state& S, int stop_op, double*& lam_cur, dou
           }
           if ((r = ns_i_primal(c, ptr(S.cur), in_m, S.s, S.buf[out], out_m, keep ? keep3 : nullptr))) return r;
           if (n + 1 > S.touched) {
-            if ((r = ns_objective(c, S.buf[out], wN, S.Jbar, nullptr))) return r;
+            if (S.obj_forward && (r = ns_objective(c, S.buf[out], wN, S.Jbar, nullptr))) return r;
             S.touched = n + 1;
           }
           S.cur = out;
@@ -415,8 +416,8 @@ int run_actions(ns_ctx* c, ns_sweep_state& S, int stop_op, double*& lam_cur, dou
 
 extern "C" {
 
-int ns_forward_run(ns_ctx* c, const double* w0, const double* s, const ns_run_opts* o, void* arena,
-                   size_t arena_bytes, double* Jbar) {
+static int forward_run_impl(ns_ctx* c, const double* w0, const double* s, const ns_run_opts* o, void* arena,
+                            size_t arena_bytes, double* Jbar, bool objective_in_forward) {
   if (!c || !w0 || !o || !arena || !Jbar) return NS_ERR_ARG;
   if (((uintptr_t)arena & 255) != 0) return NS_ERR_ARG;
   if (!(o->lambda >= 0.0)) return NS_ERR_ARG;
@@ -436,6 +437,7 @@ int ns_forward_run(ns_ctx* c, const double* w0, const double* s, const ns_run_op
   S->w0 = w0;
   S->s = s;
   S->Jbar = Jbar;
+  S->obj_forward = objective_in_forward;
   char* base = (char*)arena;
   S->buf.resize(S->L.nbuf);
   for (int i = 0; i < S->L.nbuf; ++i) S->buf[i] = (double*)(base + (size_t)i * S->L.state);
@@ -474,6 +476,11 @@ int ns_forward_run(ns_ctx* c, const double* w0, const double* s, const ns_run_op
   return NS_OK;
 }
 
+int ns_forward_run(ns_ctx* c, const double* w0, const double* s, const ns_run_opts* o, void* arena,
+                   size_t arena_bytes, double* Jbar) {
+  return forward_run_impl(c, w0, s, o, arena, arena_bytes, Jbar, true);
+}
+
 int ns_backward_run(ns_ctx* c, double* lam0, double* sbar, double* energy, double* sigma_stats) {
   if (!c || !lam0 || !c->sweep || !c->sweep->forward_done) return NS_ERR_ARG;
   ns_sweep_state& S = *c->sweep;
@@ -500,9 +507,16 @@ int ns_adjoint_run(ns_ctx* c, const double* w0, const double* s, const ns_run_op
                    size_t arena_bytes, double* Jbar, double* lam0, double* sbar, double* energy,
                    double* sigma_stats) {
   if (!c || !w0 || !o || !arena || !Jbar || !lam0 || lam0 == w0) return NS_ERR_ARG;
-  int r = ns_forward_run(c, w0, s, o, arena, arena_bytes, Jbar);
+  // The backward pass evaluates J(w^n) for every n = N..1 (for the objective source), so
+  // the forward pass skips its own evaluations and Jbar is taken from the backward sums.
+  int r = forward_run_impl(c, w0, s, o, arena, arena_bytes, Jbar, false);
   if (r) return r;
-  return ns_backward_run(c, lam0, sbar, energy, sigma_stats);
+  const double* jtmp = c->sweep->jtmp;
+  if ((r = ns_backward_run(c, lam0, sbar, energy, sigma_stats))) return r;
+  return cudaMemcpyAsync(Jbar, jtmp, (size_t)c->g.batch * sizeof(double), cudaMemcpyDeviceToDevice, c->st) ==
+                 cudaSuccess
+             ? NS_OK
+             : NS_ERR_CUDA;
 }
 
 }  // extern "C"
