@@ -46,7 +46,7 @@ def build(verbose: bool = False, extra=()) -> str:
         flags += ["-Xptxas", "-v"]
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(lambda s: _compile(s, flags), SOURCES))
-    cmd = [nvcc(), *ARCH, "-shared", "-o", OUT, *objs, "-lcudart"]
+    cmd = [nvcc(), *ARCH, "-shared", "-o", OUT, *objs, "-lcudart", "-ldl"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -3,6 +3,7 @@
 // snapshots and segment recomputation; here also binomial checkpointing) and the
 // executor that runs a plan on the context's stream with a pool of state buffers.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <algorithm>
@@ -278,6 +279,13 @@ namespace {
 // Run actions [S.pos, end) until (not including) the first action with op == stop_op
 // (stop_op = 0: to the end).  lam_cur/lam_nxt, sbar, energy, sigma_stats are used by
 // the backward part only.
+// NVTX range for the phases of a sweep (forward pass, replay, adjoint steps), visible in
+// a timeline profiler; without one attached the calls do nothing.
+struct Phase {
+  explicit Phase(const char* name) { nvtxRangePushA(name); }
+  ~Phase() { nvtxRangePop(); }
+};
+
 int run_actions(ns_ctx* c, ns_sweep_state& S, int stop_op, double*& lam_cur, double*& lam_nxt,
                 double* sbar, double* energy, double* sigma_stats) {
   const int N = S.o.nsteps;
@@ -295,7 +303,8 @@ int run_actions(ns_ctx* c, ns_sweep_state& S, int stop_op, double*& lam_cur, dou
     const ns_action& A = S.P.acts[S.pos];
     if (stop_op && A.op == stop_op) return NS_OK;
     switch (A.op) {
-      case NS_OP_ADVANCE:
+      case NS_OP_ADVANCE: {
+        Phase ph(S.in_backward ? "ns replay" : "ns forward");
         for (int n = A.a; n < A.b; ++n) {
           const int out = pick_free();
           if (out < 0) return NS_ERR_BUDGET;
@@ -341,6 +350,7 @@ int run_actions(ns_ctx* c, ns_sweep_state& S, int stop_op, double*& lam_cur, dou
           S.cur_mirror = out_m;
         }
         break;
+      }
       case NS_OP_STORE:
         if (S.cur < 0) return NS_ERR_ARG;
         S.slot_buf[A.b] = S.cur;
@@ -366,6 +376,7 @@ int run_actions(ns_ctx* c, ns_sweep_state& S, int stop_op, double*& lam_cur, dou
           return r;
         break;
       case NS_OP_ADJOINT: {
+        Phase ph("ns adjoint step");
         const int K = S.L.nkeep;
         const void* mirror = S.mixed ? S.cur_mirror : nullptr;
         const void* kept3[3] = {nullptr, nullptr, nullptr};
