@@ -832,3 +832,91 @@ def max_wave_speed(w, P: Params):
     rho, u, e, p = primitives(w, P)
     c = np.sqrt(P.gamma * p / rho)
     return float(np.max(np.sqrt(u[0] ** 2 + u[1] ** 2 + u[2] ** 2) + c))
+
+
+# ----------------------------------------------------------------------------------
+# choice of the viscosity scaling factor (Conclusion: estimating the factor for a given
+# problem is the method's first open question; results section, the table of adjoint
+# and finite-difference sensitivities against the factor: too little viscosity leaves
+# the adjoint growing, too much biases it, and in between the sensitivity hardly moves)
+# ----------------------------------------------------------------------------------
+def energy_efolds(E):
+    """Growth of the adjoint energy over the second half of the backward sweep, in
+    e-folds.  E[m] = E_vhat(w^m, lam^m) for m = 0..N (the sweep runs from m = N down to
+    0); with M = N // 2 the result is -M times the least-squares slope of ln E[m]
+    against m over m = 0..M, i.e. the fitted rise of ln E across the window as the
+    adjoint runs backward from step M to step 0.  A non-positive or non-finite energy in
+    the window gives +inf.  (A reading: the paper states that the added viscosity must
+    keep the adjoint energy bounded, section "Energy analysis", without a test.)"""
+    E = np.asarray(E, dtype=np.float64)
+    N = E.shape[0] - 1
+    M = N // 2
+    if M < 1:
+        raise ValueError("the window needs N >= 2")
+    win = E[: M + 1]
+    if not np.all(np.isfinite(win)) or np.any(win <= 0.0):
+        return math.inf
+    m = np.arange(M + 1, dtype=np.float64)
+    y = np.log(win)
+    mc = m - m.mean()
+    slope = float(np.sum(mc * (y - y.mean())) / np.sum(mc * mc))
+    return -M * slope
+
+
+def sensitivity_change(g_a, g_b):
+    """Relative L2 change ||g_b - g_a|| / ||g_b|| of a sensitivity from one factor to the
+    next larger one (over every element); 0 when both norms are 0, +inf when only
+    ||g_b|| is."""
+    g_a = np.asarray(g_a, dtype=np.float64)
+    g_b = np.asarray(g_b, dtype=np.float64)
+    d = math.sqrt(float(np.sum((g_b - g_a) ** 2)))
+    nb = math.sqrt(float(np.sum(g_b * g_b)))
+    if nb == 0.0:
+        return 0.0 if d == 0.0 else math.inf
+    return d / nb
+
+
+def select_lambda(efolds, change, efold_tol, rel_tol):
+    """Index of the smallest candidate factor i (candidates ascending, i < n - 1) whose
+    adjoint energy does not grow by more than efold_tol e-folds over the window and
+    whose sensitivity changes by at most rel_tol to the next candidate's; -1 if none.
+    (A reading of the table and the conclusion: the smallest factor that damps the
+    adjoint and sits on the plateau of the sensitivity.)"""
+    for i in range(len(change)):
+        if efolds[i] <= efold_tol and change[i] <= rel_tol:
+            return i
+    return -1
+
+
+def estimate_lambda(w0, P: Params, nsteps, lambdas, s=None, tau=0.0, efold_tol=1.0, rel_tol=0.1):
+    """Run the stabilised adjoint of an nsteps trajectory once per candidate factor
+    (nu = lambda sigma_1(w^n) [sigma_1 > tau] for the step from w^n, none for lambda = 0)
+    and apply select_lambda to the energy growth of each run and the relative change of
+    the source sensitivity dJbar/ds between consecutive runs.  Returns (chosen index,
+    efolds per candidate, change per consecutive pair, sbar per candidate, energy
+    series E[m], m = 0..N, per candidate)."""
+    ws, _ = primal_run(w0, P, nsteps, s)
+    N = nsteps
+    efolds, sbars, energies = [], [], []
+    for lam_coef in lambdas:
+        def nu_of(w, lam_coef=lam_coef):
+            sig = sigma1_field(w, P)
+            return lam_coef * sig * (sig > tau)
+        # lam^N carries the objective source of step N; each reversed step n -> n - 1
+        # then adds the source of step n - 1 (none for w^0), as in adjoint_run
+        lam = objective_grad(ws[N], P) / N
+        sbar = np.zeros_like(w0)
+        E = np.zeros(N + 1)
+        E[N] = adjoint_energy(ws[N], lam, P)
+        for n in range(N, 0, -1):
+            nun = nu_of(ws[n - 1]) if lam_coef > 0 else None
+            lam, sb = adjoint_step(ws[n - 1], lam, P, s, nun)
+            sbar += sb
+            if n - 1 >= 1:
+                lam = lam + objective_grad(ws[n - 1], P) / N
+            E[n - 1] = adjoint_energy(ws[n - 1], lam, P)
+        efolds.append(energy_efolds(E))
+        sbars.append(sbar)
+        energies.append(E)
+    change = [sensitivity_change(sbars[i], sbars[i + 1]) for i in range(len(lambdas) - 1)]
+    return select_lambda(efolds, change, efold_tol, rel_tol), efolds, change, sbars, energies
