@@ -262,6 +262,60 @@ int ns_forward_run(ns_ctx* ctx, const double* w0, const double* s, const ns_run_
                    void* arena, size_t arena_bytes, double* Jbar);
 int ns_backward_run(ns_ctx* ctx, double* lam0, double* sbar, double* energy, double* sigma_stats);
 
+/* ------------------------------------------------------------------------------
+ * Choice of the viscosity scaling factor lambda for a given problem.  The paper's
+ * conclusion names this as the method's first open question; its results section
+ * tabulates adjoint against finite-difference sensitivity over lambda: too little
+ * viscosity leaves the adjoint growing, too much biases the sensitivity, and in between
+ * the sensitivity hardly moves with lambda.  The rule below (the smallest candidate
+ * that damps the adjoint energy and sits on that plateau) is a reading of the table and
+ * of section "Energy analysis", not a procedure the paper states.
+ * ---------------------------------------------------------------------------- */
+
+/* Growth of the adjoint energy over the second half of the backward sweep, in e-folds,
+ * per box (pure host computation, no CUDA call).  E: host array [nsteps+1][batch] of
+ * E_vhat(w^m, lam^m) as ns_adjoint_run records it; out: host array [batch].  With
+ * M = nsteps / 2 (integer division), out[b] = -M times the least-squares slope of
+ * ln E[m][b] against m over m = 0..M: the fitted rise of ln E across the window as the
+ * adjoint runs backward from step M to step 0.  A non-positive or non-finite energy in
+ * the window gives +infinity for that box.  NS_ERR_ARG for nsteps < 2, batch < 1 or a
+ * NULL pointer. */
+int ns_energy_efolds(const double* E, int nsteps, int batch, double* out);
+
+/* Index of the smallest candidate i < n - 1 with efolds[i] <= efold_tol and
+ * change[i] <= rel_tol, else -1 (pure host computation).  efolds: host array [n];
+ * change: host array [n - 1]; candidates in ascending lambda.  -1 also for n < 2 or a
+ * NULL array; NaN entries never qualify. */
+int ns_lambda_select(int n, const double* efolds, const double* change, double efold_tol, double rel_tol);
+
+/* Device bytes of the work buffer of ns_estimate_lambda: three fields (lam0 and two
+ * source sensitivities), the energy series [nsteps+1][batch], Jbar[batch] and two
+ * norms, each 256-byte aligned.  0 for a NULL argument. */
+size_t ns_estimate_work_bytes(const ns_ctx* ctx, const ns_run_opts* o);
+
+/* Runs ns_adjoint_run with the options o, o->lambda replaced by each of the n
+ * candidates lambdas[0] < ... < lambdas[n-1] (host array, all >= 0), the energy series
+ * recorded and no sigma_1 statistics, and reports on the host:
+ *   efolds[i]  max over boxes of ns_energy_efolds of candidate i's energy series;
+ *   change[i]  (i < n - 1) ||sbar_{i+1} - sbar_i|| / ||sbar_{i+1}||, the relative L2
+ *              change over all boxes and components of the source sensitivity dJbar/ds
+ *              from candidate i to candidate i + 1 (norms in FP64 on the device; 0 when
+ *              both norms are 0, +infinity when only ||sbar_{i+1}|| is);
+ *   *chosen    ns_lambda_select(n, efolds, change, efold_tol, rel_tol).
+ * With o->mlp set the candidates are values of the closure's global factor kappa.
+ * w0, s (may be NULL): as in ns_adjoint_run; arena: as in ns_adjoint_run for o (its
+ * size does not depend on lambda).  work: device memory of at least
+ * ns_estimate_work_bytes(ctx, o) bytes, 256-byte aligned.  Synchronises the context's
+ * stream after each candidate (the host reads the energy series and the norms).
+ * NS_ERR_ARG for n < 2, candidates not strictly ascending or negative, nsteps < 2 or a
+ * NULL pointer (s excepted); NS_ERR_BUDGET for a short arena or work buffer; errors of
+ * ns_adjoint_run are passed through, with the reports of the candidates before the
+ * failing one filled in. */
+int ns_estimate_lambda(ns_ctx* ctx, const double* w0, const double* s, const ns_run_opts* o,
+                       const double* lambdas, int n, double efold_tol, double rel_tol, void* arena,
+                       size_t arena_bytes, void* work, size_t work_bytes, double* efolds, double* change,
+                       int* chosen);
+
 /* field[b] *= seed[b] for every box b of a [batch][5][cells] field (device seed[batch]):
  * applies a per-box output cotangent to unit-seed adjoints. */
 int ns_scale_boxes(ns_ctx* ctx, const double* seed, double* field);

@@ -36,7 +36,8 @@ EXPORTED = [
     "ns_profile_read", "ns_to_float", "ns_forward_run", "ns_backward_run", "ns_scale_boxes",
     "ns_dot_boxes", "ns_mlp_net_bytes", "ns_mlp_set_params", "ns_mlp_get_params", "ns_mlp_get_moment",
     "ns_mlp_features", "ns_mlp_infer", "ns_mlp_train_step", "ns_adjoint_label", "ns_label_target",
-    "ns_launch_count", "ns_set_viscosity_split",
+    "ns_launch_count", "ns_set_viscosity_split", "ns_energy_efolds", "ns_lambda_select",
+    "ns_estimate_work_bytes", "ns_estimate_lambda",
 ]
 
 NS_MLP_PARAMS = 5185
@@ -134,6 +135,11 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "ns_adjoint_run": ([P, P, P, ctypes.POINTER(NsRunOpts), P, S, P, P, P, P, P], I),
         "ns_profile_enable": ([P, I], I),
         "ns_profile_read": ([P, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_longlong)], I),
+        "ns_energy_efolds": ([ctypes.POINTER(D), I, I, ctypes.POINTER(D)], I),
+        "ns_lambda_select": ([I, ctypes.POINTER(D), ctypes.POINTER(D), D, D], I),
+        "ns_estimate_work_bytes": ([P, ctypes.POINTER(NsRunOpts)], S),
+        "ns_estimate_lambda": ([P, P, P, ctypes.POINTER(NsRunOpts), ctypes.POINTER(D), I, D, D, P, S, P, S,
+                                ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(I)], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -147,6 +153,25 @@ def _lib() -> ctypes.CDLL:
     if _LIB is None:
         _LIB = load_library()
     return _LIB
+
+
+def _doubles(values):
+    values = [float(v) for v in values]
+    return (ctypes.c_double * max(len(values), 1))(*values)
+
+
+def energy_efolds(E, nsteps: int, batch: int = 1):
+    """Energy growth over the second half of the backward sweep, in e-folds, per box
+    (host computation); E is a flat or [nsteps+1][batch] sequence of floats."""
+    flat = [float(v) for row in E for v in (row if hasattr(row, "__len__") else [row])]
+    out = (ctypes.c_double * batch)()
+    _check(_lib().ns_energy_efolds(_doubles(flat), nsteps, batch, out), "ns_energy_efolds")
+    return list(out)
+
+
+def lambda_select(efolds, change, efold_tol: float, rel_tol: float) -> int:
+    """Index of the smallest damped candidate on the sensitivity plateau, or -1."""
+    return int(_lib().ns_lambda_select(len(efolds), _doubles(efolds), _doubles(change), efold_tol, rel_tol))
 
 
 def plan(nsteps: int, schedule: int, param: int = 0):
@@ -326,6 +351,25 @@ class Solver:
                                        _ptr(Jbar, torch.float64), _ptr(lam0, torch.float64),
                                        _ptr(sbar, torch.float64), _ptr(energy, torch.float64),
                                        _ptr(sigma_stats, torch.float64)), "ns_adjoint_run")
+
+    def estimate_work_bytes(self, opts) -> int:
+        return int(self.lib.ns_estimate_work_bytes(self._ctx, ctypes.byref(opts)))
+
+    def estimate_lambda(self, w0, opts, lambdas, arena, work, s=None, efold_tol=1.0, rel_tol=0.1):
+        """One stabilised sweep per candidate factor (ascending); returns (chosen index or
+        -1, energy growth in e-folds per candidate, relative sensitivity change per
+        consecutive pair).  arena: as for adjoint_run; work: a uint8 CUDA tensor of at
+        least estimate_work_bytes(opts) bytes."""
+        n = len(lambdas)
+        ef = (ctypes.c_double * n)()
+        ch = (ctypes.c_double * max(n - 1, 1))()
+        chosen = ctypes.c_int(-1)
+        _check(self.lib.ns_estimate_lambda(self._ctx, _ptr(w0, torch.float64), _ptr(s, torch.float64),
+                                           ctypes.byref(opts), _doubles(lambdas), n, efold_tol, rel_tol,
+                                           _ptr(arena), arena.numel() * arena.element_size(), _ptr(work),
+                                           work.numel() * work.element_size(), ef, ch, ctypes.byref(chosen)),
+               "ns_estimate_lambda")
+        return chosen.value, list(ef), list(ch)[: max(n - 1, 0)]
 
     def forward_run(self, w0, opts, arena, Jbar, s=None):
         """Forward half of the sweep (keeps the checkpoints in arena, accumulates Jbar)."""

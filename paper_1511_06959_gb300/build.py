@@ -15,7 +15,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libns_adjoint.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["ns_rhs.cu", "ns_adj.cu", "ns_diag.cu", "ns_api.cu", "ns_sweep.cu", "ns_noalloc.cu", "ns_mlp.cu"]
+SOURCES = ["ns_rhs.cu", "ns_adj.cu", "ns_diag.cu", "ns_api.cu", "ns_sweep.cu", "ns_noalloc.cu", "ns_mlp.cu",
+           "ns_lambda.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-Xptxas", "-warn-spills"]

@@ -62,3 +62,10 @@ int ns_i_objective(ns_ctx* c, const double* w, double weight, double* J_acc, dou
 int ns_i_sigma1(ns_ctx* c, const double* w, const void* w_mirror, float* sigma1, double* stats,
                 double lambda = 0.0, double tau = 0.0, float* nu = nullptr);
 size_t ns_i_stage_bytes(const ns_ctx* c);
+
+namespace ns {
+// out2[0] = sum (b - a)^2, out2[1] = sum b^2 over n doubles (FP64, deterministic; uses
+// 2 x 296 doubles of scratch)
+cudaError_t launch_diff_norms(const double* a, const double* b, size_t n, double* out2, double* scratch,
+                              cudaStream_t st);
+}  // namespace ns

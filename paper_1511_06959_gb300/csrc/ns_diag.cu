@@ -777,6 +777,24 @@ __global__ void __launch_bounds__(RB) k_dot_boxes(GridDesc g, const double* __re
   if (threadIdx.x == 0) partial[(size_t)m * gridDim.x + blockIdx.x] = s;
 }
 
+// relative change of a sensitivity field: sum (b - a)^2 and sum b^2 over n elements
+__global__ void __launch_bounds__(RB) k_diff_norms(const double* __restrict__ a, const double* __restrict__ b,
+                                                   size_t n, double* partial) {
+  __shared__ double sh[RB];
+  double d2 = 0.0, b2 = 0.0;
+  for (size_t i = (size_t)blockIdx.x * RB + threadIdx.x; i < n; i += (size_t)gridDim.x * RB) {
+    const double bv = b[i], dv = bv - a[i];
+    d2 += dv * dv;
+    b2 += bv * bv;
+  }
+  d2 = block_reduce(d2, sh, AddOp());
+  b2 = block_reduce(b2, sh, AddOp());
+  if (threadIdx.x == 0) {
+    partial[blockIdx.x] = d2;
+    partial[gridDim.x + blockIdx.x] = b2;
+  }
+}
+
 __global__ void k_to_float(const double* __restrict__ in, float* __restrict__ out, size_t n) {
   const size_t i = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) * 2;
   if (i + 1 < n) {
@@ -953,6 +971,17 @@ cudaError_t launch_dot_boxes(const GridDesc& g, const double* field, int comp, c
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_sum_partials<<<nphi, RB, 0, st>>>(RG, 1.0, scratch, out, nullptr);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_diff_norms(const double* a, const double* b, size_t n, double* out2, double* scratch,
+                              cudaStream_t st) {
+  k_diff_norms<<<RG, RB, 0, st>>>(a, b, n, scratch);
+  count_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_sum_partials<<<2, RB, 0, st>>>(RG, 1.0, scratch, out2, nullptr);
   count_launch();
   return cudaGetLastError();
 }
