@@ -272,14 +272,18 @@ int ns_backward_run(ns_ctx* ctx, double* lam0, double* sbar, double* energy, dou
  * of section "Energy analysis", not a procedure the paper states.
  * ---------------------------------------------------------------------------- */
 
-/* Growth of the adjoint energy over the second half of the backward sweep, in e-folds,
- * per box (pure host computation, no CUDA call).  E: host array [nsteps+1][batch] of
- * E_vhat(w^m, lam^m) as ns_adjoint_run records it; out: host array [batch].  With
- * M = nsteps / 2 (integer division), out[b] = -M times the least-squares slope of
- * ln E[m][b] against m over m = 0..M: the fitted rise of ln E across the window as the
- * adjoint runs backward from step M to step 0.  A non-positive or non-finite energy in
- * the window gives +infinity for that box.  NS_ERR_ARG for nsteps < 2, batch < 1 or a
- * NULL pointer. */
+/* Growth of the adjoint energy over the second half of the backward sweep beyond what
+ * the objective source alone accounts for, in e-folds, per box (pure host computation,
+ * no CUDA call).  E: host array [nsteps+1][batch] of E_vhat(w^m, lam^m) as
+ * ns_adjoint_run records it; out: host array [batch].  lam^m sums the sources of steps
+ * m..N (N - m + 1 bounded terms), so with a propagator that does not expand the energy
+ * sqrt(E^m) grows at most linearly in N - m + 1 and E^m / (N - m + 1)^2 stays bounded.
+ * With M = nsteps / 2 (integer division), out[b] = -M times the least-squares slope of
+ * ln(E[m][b] / (N - m + 1)^2) against m over m = 0..M: the fitted rise across the window
+ * as the adjoint runs backward from step M to step 0 (about 0 or below for a damped
+ * adjoint, a M for one growing like exp(a (N - m))).  A non-positive or non-finite
+ * energy in the window gives +infinity for that box.  NS_ERR_ARG for nsteps < 2,
+ * batch < 1 or a NULL pointer. */
 int ns_energy_efolds(const double* E, int nsteps, int batch, double* out);
 
 /* Index of the smallest candidate i < n - 1 with efolds[i] <= efold_tol and

@@ -841,13 +841,18 @@ def max_wave_speed(w, P: Params):
 # the adjoint growing, too much biases it, and in between the sensitivity hardly moves)
 # ----------------------------------------------------------------------------------
 def energy_efolds(E):
-    """Growth of the adjoint energy over the second half of the backward sweep, in
-    e-folds.  E[m] = E_vhat(w^m, lam^m) for m = 0..N (the sweep runs from m = N down to
-    0); with M = N // 2 the result is -M times the least-squares slope of ln E[m]
-    against m over m = 0..M, i.e. the fitted rise of ln E across the window as the
-    adjoint runs backward from step M to step 0.  A non-positive or non-finite energy in
-    the window gives +inf.  (A reading: the paper states that the added viscosity must
-    keep the adjoint energy bounded, section "Energy analysis", without a test.)"""
+    """Growth of the adjoint energy over the second half of the backward sweep beyond
+    what the objective source alone accounts for, in e-folds.  E[m] = E_vhat(w^m, lam^m)
+    for m = 0..N (the sweep runs from m = N down to 0).  lam^m sums the sources of steps
+    m..N, N - m + 1 bounded terms, pushed back by the adjoint propagator; when that
+    propagator does not expand the energy norm (what the added viscosity is to ensure,
+    section "Energy analysis") sqrt(E^m) grows at most linearly in N - m + 1, so the
+    normalised energy E^m / (N - m + 1)^2 stays bounded and only exponential growth
+    makes it rise.  With M = N // 2 the result is -M times the least-squares slope of
+    ln(E[m] / (N - m + 1)^2) against m over m = 0..M: the fitted rise across the window
+    as the adjoint runs backward from step M to step 0.  A non-positive or non-finite
+    energy in the window gives +inf.  (A reading: the paper asks the energy to stay
+    bounded without a test.)"""
     E = np.asarray(E, dtype=np.float64)
     N = E.shape[0] - 1
     M = N // 2
@@ -857,7 +862,7 @@ def energy_efolds(E):
     if not np.all(np.isfinite(win)) or np.any(win <= 0.0):
         return math.inf
     m = np.arange(M + 1, dtype=np.float64)
-    y = np.log(win)
+    y = np.log(win / (N - m + 1.0) ** 2)
     mc = m - m.mean()
     slope = float(np.sum(mc * (y - y.mean())) / np.sum(mc * mc))
     return -M * slope

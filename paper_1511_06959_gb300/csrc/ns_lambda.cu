@@ -5,7 +5,8 @@
 // range where the sensitivity hardly moves), and section "Energy analysis" asks the
 // added viscosity to keep the adjoint energy from growing.  The rule read from these:
 // run the stabilised sweep for ascending candidates, fit the growth of the adjoint
-// energy over the second half of each backward sweep, measure how much the source
+// energy over the second half of each backward sweep (beyond the quadratic growth that
+// accumulating the objective source alone gives), measure how much the source
 // sensitivity moves from each candidate to the next, and take the smallest candidate
 // that is damped and on the plateau.
 //
@@ -37,8 +38,10 @@ WorkLayout work_layout(const ns_ctx* c, int nsteps) {
   return L;
 }
 
-// -M times the least-squares slope of ln E[m] against m, m = 0..M, for box b of a
-// [nsteps+1][batch] series
+// -M times the least-squares slope of ln(E[m] / (N - m + 1)^2) against m, m = 0..M, for
+// box b of a [nsteps+1][batch] series: lam^m sums N - m + 1 bounded source terms, so a
+// propagator that does not expand the energy keeps the normalised energy bounded and
+// only exponential growth makes it rise
 double efolds_box(const double* E, int nsteps, int batch, int b) {
   const int M = nsteps / 2;
   std::vector<double> y(M + 1);
@@ -46,7 +49,7 @@ double efolds_box(const double* E, int nsteps, int batch, int b) {
   for (int m = 0; m <= M; ++m) {
     const double v = E[(size_t)m * batch + b];
     if (!(v > 0.0) || !std::isfinite(v)) return std::numeric_limits<double>::infinity();
-    y[m] = std::log(v);
+    y[m] = std::log(v) - 2.0 * std::log((double)(nsteps - m + 1));
     ybar += y[m];
   }
   ybar /= (M + 1);

@@ -21,13 +21,10 @@ from . import api
 from . import config as C
 
 DEFAULT_TILDES = (0.0, 0.0125, 0.025, 0.05, 0.1, 0.2, 0.4)
-SCHEDULES = {"all": api.NS_CKPT_ALL, "stride": api.NS_CKPT_STRIDE, "revolve": api.NS_CKPT_REVOLVE}
 
 
 def run(workload: str, tildes, precision: int, efold_tol: float, rel_tol: float, nsteps: int = 0) -> dict:
     wl = C.WORKLOADS[workload]
-    if wl.schedule == "revolve":
-        raise ValueError("the study runs workloads with a store-all or stride schedule")
     w0 = np.ascontiguousarray(wl.initial_state())
     S = api.Solver(wl.nx, wl.ny, wl.nz, wl.dx, gamma=wl.gamma, mu=wl.mu, Pr=wl.Pr, dt=0.0,
                    precision=precision, plane_i=wl.plane_i, pt_in=wl.pt_in, batch=wl.batch)
@@ -36,7 +33,8 @@ def run(workload: str, tildes, precision: int, efold_tol: float, rel_tol: float,
     S.max_wave_speed(w, m)
     S.set_dt(C.cfl_dt(wl, m.item()))
     N = nsteps or wl.nsteps
-    opts = S.run_opts(N, SCHEDULES[wl.schedule], wl.param)
+    param = wl.param if wl.schedule != "revolve" or wl.param else C.revolve_slots(wl, w0.nbytes)
+    opts = S.run_opts(N, C.SCHEDULES[wl.schedule], param)
     arena = torch.empty(S.arena_bytes(opts), dtype=torch.uint8, device="cuda")
     work = torch.empty(S.estimate_work_bytes(opts), dtype=torch.uint8, device="cuda")
     lambdas = [t * wl.dx[0] ** 2 for t in tildes]

@@ -54,12 +54,12 @@ def test_estimate_matches_oracle(prec):
     assert all(abs(e - 1.0) > 4 * ef_tol for e in ef_ref)
     assert chosen == chosen_ref
     # other thresholds give the oracle's choice on the library's reports (the efolds of
-    # this case fall from 0.95 to 0.91 with lambda, the changes rise from 0.008 to 0.03)
-    for et, rt in [(1.0, 1e-3), (1.0, 0.05), (0.935, 0.1), (0.935, 0.02), (0.5, 0.1)]:
+    # this case fall from -0.22 to -0.26 with lambda, the changes rise from 0.008 to 0.03)
+    for et, rt in [(1.0, 1e-3), (1.0, 0.05), (-0.235, 0.1), (-0.235, 0.02), (-0.5, 0.1)]:
         assert all(abs(e - et) > 4 * ef_tol for e in ef_ref)
         assert all(abs(c - rt) > 4 * ch_tol * c for c in ch_ref)
         assert api.lambda_select(ef, ch, et, rt) == O.select_lambda(ef_ref, ch_ref, et, rt)
-    assert O.select_lambda(ef_ref, ch_ref, 0.935, 0.1) == 3
+    assert O.select_lambda(ef_ref, ch_ref, -0.235, 0.1) == 3
 
 
 def test_batch_takes_the_worst_box_and_pools_the_norms():

@@ -45,10 +45,12 @@ def test_plateau_rule_picks_the_row_where_the_paper_matches_fd():
 
 @pytest.mark.parametrize("N", [2, 3, 10, 41])
 def test_efolds_of_an_exact_exponential(N):
-    """E^m = C exp(a (N - m)): ln E is linear in m, so the fit returns a M exactly."""
+    """E^m = C (N - m + 1)^2 exp(a (N - m)): the normalised energy is exponential in m,
+    so the fit returns a M exactly; a = 0 is a stable adjoint accumulating a constant
+    source (energy growing as the square of the number of sources) and gives 0."""
     M = N // 2
     for a, C in [(0.3, 5.0), (-0.7, 1e-9), (0.0, 2.0)]:
-        E = [C * math.exp(a * (N - m)) for m in range(N + 1)]
+        E = [C * (N - m + 1) ** 2 * math.exp(a * (N - m)) for m in range(N + 1)]
         assert O.energy_efolds(E) == pytest.approx(a * M, rel=1e-12, abs=1e-12)
 
 
@@ -63,10 +65,15 @@ def test_efolds_window_scale_and_degenerate_cases():
     assert O.energy_efolds(E2) == ref
     # a constant factor drops out of the slope
     assert O.energy_efolds(3.0 * E) == pytest.approx(ref, abs=1e-12)
-    # brute force: the slope of np.polyfit
+    # brute force: the slope of np.polyfit on the normalised energy
     m = np.arange(N // 2 + 1)
-    slope = np.polyfit(m, np.log(E[: N // 2 + 1]), 1)[0]
+    slope = np.polyfit(m, np.log(E[: N // 2 + 1]) - 2.0 * np.log(N - m + 1.0), 1)[0]
     assert ref == pytest.approx(-(N // 2) * slope, rel=1e-12)
+    # a pure exponential in the raw energy reads a M less the accumulation's share
+    a = 0.2
+    Ee = [math.exp(a * (N - k)) for k in range(N + 1)]
+    share = -(N // 2) * np.polyfit(m, 2.0 * np.log(N - m + 1.0), 1)[0]
+    assert O.energy_efolds(Ee) == pytest.approx(a * (N // 2) - share, rel=1e-12)
     for bad in (0.0, -1.0, math.inf, math.nan):
         E3 = E.copy()
         E3[1] = bad
