@@ -291,6 +291,7 @@ template <bool ROE> constexpr int npk() { return ROE ? 17 : 7; }
 
 template <class CT, class TIN, class TA, class TST, bool ROE>
 __global__ void __launch_bounds__(NT, AdjMinBlocks<CT, ROE>::value) k_adj_stage(GridDesc g, Coef<CT> c, AdjArgs<TIN, TA, TST> a) {
+  pdl_enter();
   constexpr int NPK = npk<ROE>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   CT* sQ = reinterpret_cast<CT*>(smem_raw);   // [3][5][SP] primal primitives
@@ -584,9 +585,9 @@ static cudaError_t launch_adj_variant(const GridDesc& g, const Coef<CT>& c, cons
   int ctas = 0;
   cudaError_t e = shape.get(kern, smem, g, "NS_ADJ_CTAS", ctas);
   if (e != cudaSuccess) return e;
-  kern<<<ctas, NT, smem, st>>>(g, c, a);
+  e = launch_pdl(kern, dim3(ctas), dim3(NT), smem, st, g, c, a);
   count_launch();
-  return cudaGetLastError();
+  return e;
 }
 
 template <class CT, class TIN, class TA, class TST>

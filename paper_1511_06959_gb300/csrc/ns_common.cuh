@@ -20,6 +20,7 @@
 
 #include <atomic>
 #include <type_traits>
+#include <utility>
 
 namespace ns {
 
@@ -216,6 +217,48 @@ __device__ __forceinline__ void diff4_pair(CT a1, CT b1, CT c1, CT d1, CT s1, CT
     r1 = (a1 - b1 + c1 - d1) * s1;
     r2 = (a2 - b2 + c2 - d2) * s2;
   }
+}
+
+// ---------------------------------------------------------------------------------
+// programmatic dependent launch.  The stencil and per-step diagnostic kernels of the
+// sweep go out with programmatic stream serialisation: the next kernel's CTAs may be
+// scheduled while the current kernel drains, so the launch latency between dependent
+// kernels overlaps the tail of the previous one.  Each such kernel starts with
+// pdl_enter(): griddepcontrol.wait blocks until the preceding grid has completed and
+// its memory is visible (a no-op for a launch without the attribute), and only then
+// does griddepcontrol.launch_dependents release the kernel after it, so every kernel
+// still sees all earlier kernels' results.  The dependent grid starts only after every
+// CTA of this one has started, so the early launch cannot starve this grid.  NS_PDL=0
+// launches without the attribute.
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+inline bool pdl_enabled() {
+  static const bool on = [] {
+    const char* e = getenv("NS_PDL");
+    return !(e && e[0] == '0');
+  }();
+  return on;
+}
+
+// launch k (whose first statement is pdl_enter()) on st with the PDL attribute
+template <class... KArgs, class... Args>
+cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                       Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl_enabled() ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...);
 }
 
 // ---------------------------------------------------------------------------------

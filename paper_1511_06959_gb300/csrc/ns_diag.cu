@@ -183,6 +183,7 @@ __global__ void __launch_bounds__(OMB) k_obj_sum(GridDesc g, double gamma, int i
                                                  const double* __restrict__ w, double weight, double* J_acc,
                                                  bool want_grad, unsigned* err, double* partial,
                                                  double* aface, double* ndsc, unsigned* ticket) {
+  pdl_enter();
   __shared__ double sh[OMB];
   __shared__ bool last;
   const int b = blockIdx.y;
@@ -245,6 +246,7 @@ __global__ void __launch_bounds__(OMB) k_obj_sum(GridDesc g, double gamma, int i
 
 __global__ void k_obj_scatter(GridDesc g, int i0, const double* __restrict__ aface, const double* __restrict__ ndsc,
                               double* __restrict__ lam, float* __restrict__ lamf) {
+  pdl_enter();
   const int nf = g.ny * g.nz;
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (long long)nf * g.batch) return;
@@ -470,6 +472,7 @@ template <class CT>
 __global__ void __launch_bounds__(RB, sizeof(CT) == 4 ? 4 : 1) k_sigma1(GridDesc g, Coef<CT> c, const CT* __restrict__ w,
                                                float* __restrict__ sig, double* partial, double* stats,
                                                unsigned* ticket, NuRule rule) {
+  pdl_enter();
   __shared__ double sh[32];
   __shared__ bool last;
   const int b = blockIdx.y;
@@ -664,6 +667,7 @@ template <class T, class TIN>
 __global__ void __launch_bounds__(RB, sizeof(T) == 4 ? 8 : 1) k_energy(GridDesc g, double gamma, double dV, const TIN* __restrict__ w,
                                                const TIN* __restrict__ lam, double* partial, double* E,
                                                unsigned* err, unsigned* ticket) {
+  pdl_enter();
   __shared__ double sh[32];
   __shared__ bool last;
   const int b = blockIdx.y;
@@ -847,15 +851,15 @@ cudaError_t launch_objective_fast(const GridDesc& g, double gamma, int plane_i, 
   double* partial = scratch;
   double* ndsc = scratch + (size_t)2 * RG * g.batch;
   double* aface = ndsc + 2 * (size_t)g.batch;
-  k_obj_sum<<<dim3(nblk, g.batch), OMB, 0, st>>>(g, gamma, plane_i, pt_in, w, weight, J_acc, lam != nullptr, err,
-                                                 partial, aface, ndsc, ticket);
+  cudaError_t e = launch_pdl(k_obj_sum, dim3(nblk, g.batch), dim3(OMB), 0, st, g, gamma, plane_i, pt_in, w, weight,
+                             J_acc, lam != nullptr, err, partial, aface, ndsc, ticket);
   count_launch();
-  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || !lam) return e;
   const long long n = (long long)nf * g.batch;
-  k_obj_scatter<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(g, plane_i, aface, ndsc, lam, lam_mirror);
+  e = launch_pdl(k_obj_scatter, dim3((unsigned)((n + 127) / 128)), dim3(128), 0, st, g, plane_i,
+                 (const double*)aface, (const double*)ndsc, lam, lam_mirror);
   count_launch();
-  return cudaGetLastError();
+  return e;
 }
 
 template <class CT>
@@ -864,9 +868,9 @@ cudaError_t launch_sigma1(const GridDesc& g, const Coef<CT>& c, const CT* w, flo
                           const NuRule* rule) {
   dim3 grid(RGS, g.batch);
   const NuRule r = rule ? *rule : NuRule{0.f, 0.f, 0.f, nullptr, nullptr};
-  k_sigma1<CT><<<grid, RB, 0, st>>>(g, c, w, sigma1, scratch, stats, ticket, r);
+  cudaError_t e = launch_pdl(k_sigma1<CT>, grid, dim3(RB), 0, st, g, c, w, sigma1, scratch, stats, ticket, r);
   count_launch();
-  return cudaGetLastError();
+  return e;
 }
 template cudaError_t launch_sigma1<double>(const GridDesc&, const Coef<double>&, const double*, float*,
                                            double*, double*, unsigned*, cudaStream_t, const NuRule*);
@@ -908,20 +912,22 @@ cudaError_t launch_energy(const GridDesc& g, double gamma, double dV, const doub
                           double* E, double* scratch, unsigned* err, bool fp32_transform, unsigned* ticket,
                           cudaStream_t st) {
   dim3 grid(RGS, g.batch);
-  if (fp32_transform)
-    k_energy<float, double><<<grid, RB, 0, st>>>(g, gamma, dV, w, lam, scratch, E, err, ticket);
-  else
-    k_energy<double, double><<<grid, RB, 0, st>>>(g, gamma, dV, w, lam, scratch, E, err, ticket);
+  cudaError_t e = fp32_transform
+                      ? launch_pdl(k_energy<float, double>, grid, dim3(RB), 0, st, g, gamma, dV, w, lam, scratch, E,
+                                   err, ticket)
+                      : launch_pdl(k_energy<double, double>, grid, dim3(RB), 0, st, g, gamma, dV, w, lam, scratch,
+                                   E, err, ticket);
   count_launch();
-  return cudaGetLastError();
+  return e;
 }
 
 cudaError_t launch_energy_mirrors(const GridDesc& g, double gamma, double dV, const float* wf, const float* lamf,
                                   double* E, double* scratch, unsigned* err, unsigned* ticket, cudaStream_t st) {
   dim3 grid(RGS, g.batch);
-  k_energy<float, float><<<grid, RB, 0, st>>>(g, gamma, dV, wf, lamf, scratch, E, err, ticket);
+  cudaError_t e = launch_pdl(k_energy<float, float>, grid, dim3(RB), 0, st, g, gamma, dV, wf, lamf, scratch, E, err,
+                             ticket);
   count_launch();
-  return cudaGetLastError();
+  return e;
 }
 
 cudaError_t launch_dot(const double* a, const double* phi, int nphi, size_t n, double* out,

@@ -254,6 +254,7 @@ template <> struct RhsMinBlocks<float, true> { static constexpr int value = 2; }
 
 template <class CT, class TIN, class TST, bool ROE>
 __global__ void __launch_bounds__(NT, RhsMinBlocks<CT, ROE>::value) k_rhs_stage(GridDesc g, Coef<CT> c, StageArgs<TIN, TST> a) {
+  pdl_enter();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   CT* sQ = reinterpret_cast<CT*>(smem_raw);          // [3][5][SP]
   CT* sFX = sQ + 3 * 5 * SP;                          // [5][TY][TX+1]
@@ -381,9 +382,9 @@ static cudaError_t launch_rhs_variant(const GridDesc& g, const Coef<CT>& c, cons
   int ctas = 0;
   cudaError_t e = shape.get(kern, smem, g, "NS_RHS_CTAS", ctas);
   if (e != cudaSuccess) return e;
-  kern<<<ctas, rk::NT, smem, st>>>(g, c, a);
+  e = launch_pdl(kern, dim3(ctas), dim3(rk::NT), smem, st, g, c, a);
   count_launch();
-  return cudaGetLastError();
+  return e;
 }
 
 template <class CT, class TIN, class TST>
