@@ -126,3 +126,41 @@ def test_label_zero_for_uniform_flow_and_nonnegative():
     rho = np.ones((3, 4, 5))
     wu = synth._conservative(rho, np.stack([0.5 * rho, 0 * rho, 0 * rho]), rho / g, g)
     assert np.all(ML.label_rate(wu, lam[:, :3, :4, :5], params_for(wu)) == 0.0)
+
+
+@pytest.mark.parametrize("nz", [1, 3])
+def test_label_closed_form_on_a_sinusoidal_shear(nz):
+    """Uniform rho and p with u1 = A sin(k_y y): a and b are uniform and div u = 0, so
+    M1 = 0 and M = -M2 has one entry, -du1/dy, in row u1, column u2 (the printed M2's
+    velocity block).  Its central difference is exactly A cos(k_y y) sin(k_y h_y) / h_y.  With
+    v_hat = (0, B sin(k_x x), C, D sin(k_x x), 0) the label is
+    max(0, v_hat^T M v_hat) / |grad v_hat|^2 = max(0, -G B C sin(k_x x)) / (B'^2 (cos(k_x x)
+    sin(k_x h_x) / h_x)^2), with B'^2 = B^2 in 2D (the u3 component is outside the
+    (rho, u1, u2, p) block) and B^2 + D^2 in 3D."""
+    g = 1.4
+    nx, ny = 12, 8
+    hx, hy, hz = 1.0 / nx, 1.5 / nx, 2.0 / nx   # unequal, so a mixed-up axis shows
+    A, B, C, D = 0.3, 0.7, -1.3, 0.9
+    ky = 2 * math.pi / (ny * hy)
+    kx = 2 * math.pi / (nx * hx)
+    y = (np.arange(ny) + 0.5) * hy
+    x = (np.arange(nx) + 0.5) * hx
+    Y = np.broadcast_to(y[None, :, None], (nz, ny, nx))
+    X = np.broadcast_to(x[None, None, :], (nz, ny, nx))
+    rho = np.full((nz, ny, nx), 1.2)
+    u = np.stack([A * np.sin(ky * Y), np.zeros_like(rho), np.zeros_like(rho)])
+    w = synth._conservative(rho, u, np.full_like(rho, 0.8 / g), g)
+    P = params_for(w)
+    P.dx = (hx, hy, hz)
+    vh = np.stack([np.zeros_like(rho), B * np.sin(kx * X), np.full_like(rho, C), D * np.sin(kx * X),
+                   np.zeros_like(rho)])
+    # lam = T^T v_hat, so that the label's own T^{-T} lam gives v_hat back
+    T = O.transform_T(w, P)
+    lam = np.moveaxis(np.einsum("...ji,...j->...i", T, np.moveaxis(vh, 0, -1)), -1, 0)
+    G = A * np.cos(ky * Y) * math.sin(ky * hy) / hy
+    B2 = B * B if nz == 1 else B * B + D * D
+    grad2 = B2 * (np.cos(kx * X) * math.sin(kx * hx) / hx) ** 2
+    expect = np.maximum(-G * B * C * np.sin(kx * X), 0.0) / grad2
+    got = ML.label_rate(w, lam, P)
+    np.testing.assert_allclose(got, expect, rtol=1e-10, atol=1e-12 * expect.max())
+    assert np.count_nonzero(expect) > expect.size // 4   # both signs of the growth occur
