@@ -56,6 +56,8 @@ def parse():
                          "Roe dissipation)")
     ap.add_argument("--scheme", default="rk4", choices=["rk4", "ssprk3"],
                     help="time integrator (the workload's is RK4; ssprk3 is the paper's own)")
+    ap.add_argument("--host-snapshots", action="store_true",
+                    help="keep a stride schedule's snapshots in page-locked host memory")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -240,8 +242,15 @@ def run_ours(args, wl):
     if args.closure:
         from paper_1511_06959_gb300 import closure
         net = closure.Network(S, closure.init_params(3, out_bias=0.5))
-    opts = S.run_opts(wl.nsteps, sched, param, 0.5 if net is not None else wl.lam_coef, 0.0, True, True,
-                      net.blob if net is not None else None)
+    run_sched, host = sched, None
+    if args.host_snapshots:
+        if wl.schedule != "stride":
+            raise SystemExit("--host-snapshots needs a workload with a stride schedule")
+        run_sched = api.NS_CKPT_STRIDE_HOST
+        probe = S.run_opts(wl.nsteps, run_sched, param)
+        host = torch.empty(S.host_bytes(probe), dtype=torch.uint8, pin_memory=True)
+    opts = S.run_opts(wl.nsteps, run_sched, param, 0.5 if net is not None else wl.lam_coef, 0.0, True, True,
+                      net.blob if net is not None else None, host_arena=host)
     arena = torch.empty(S.arena_bytes(opts), dtype=torch.uint8, device=dev)
     J = torch.empty(wl.batch, dtype=torch.float64, device=dev)
     lam0 = torch.empty_like(w0)
@@ -333,7 +342,9 @@ def run_ours(args, wl):
             "config": {"workload": C.describe(wl, args.scheme, args.flux), "name": wl.name, "cells": wl.cells,
                        "scheme": args.scheme, "flux": args.flux, "nu_split": list(split),
                        "viscosity": "learned closure (MLP, kappa 0.5)" if args.closure else "sigma_1 rule",
-                       "nsteps": wl.nsteps, "schedule": wl.schedule, "param": param,
+                       "nsteps": wl.nsteps,
+                       "schedule": wl.schedule + (" (snapshots in host memory)" if host is not None else ""),
+                       "param": param,
                        "lambda_tilde": wl.lam_tilde, "precision": args.precision, "dt": dt,
                        "l2": "flushed (256 MB write) between timed steps; arena "
                              f"{arena.numel() / 1e9:.2f} GB > L2",

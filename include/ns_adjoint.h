@@ -196,10 +196,18 @@ int ns_max_wave_speed(ns_ctx* ctx, const double* w, double* out);
  *   NS_CKPT_REVOLVE binomial checkpointing with param state slots: each step is
  *                   recomputed at most r times, r the least integer with
  *                   C(param + r, param) >= nsteps
+ *   NS_CKPT_STRIDE_HOST  NS_CKPT_STRIDE with the every-param-th snapshots in host
+ *                   memory (a caller-owned host arena, ns_run_opts.host_arena): each
+ *                   snapshot is copied out once in the forward pass and back once when
+ *                   its segment is replayed; only the replayed segment's states live
+ *                   in device memory.  The copies run on the context's stream, so a
+ *                   sweep gives the same bits as NS_CKPT_STRIDE.  On a Grace-hosted GPU
+ *                   they cross NVLink-C2C.
  * ---------------------------------------------------------------------------- */
 #define NS_CKPT_ALL 0
 #define NS_CKPT_STRIDE 1
 #define NS_CKPT_REVOLVE 2
+#define NS_CKPT_STRIDE_HOST 3
 
 #define NS_OP_ADVANCE 1 /* advance the current state from step a to step b */
 #define NS_OP_STORE 2   /* keep the current state (step a) in slot b */
@@ -208,6 +216,10 @@ int ns_max_wave_speed(ns_ctx* ctx, const double* w, double* out);
                            objective source of step a if a >= 1 */
 #define NS_OP_FREE 5    /* release slot b (held step a) */
 #define NS_OP_SOURCE 6  /* add the objective source of step a (current state w^a) */
+#define NS_OP_STORE_HOST 7 /* copy the current state (step a) to host slot b */
+#define NS_OP_LOAD_HOST 8  /* copy the state of step a from host slot b into a free device
+                              buffer and make it current */
+#define NS_OP_FREE_HOST 9  /* release host slot b (held step a) */
 
 typedef struct {
   int op, a, b;
@@ -215,9 +227,9 @@ typedef struct {
 
 /* Plan a sweep of nsteps steps (pure host computation, no CUDA call).  Writes up to
  * max_actions actions to out (out may be NULL to query the count), the number of
- * actions to *n_actions, the largest number of simultaneously used slots to
- * *slots_used and the number of primal steps advanced (first pass included) to
- * *advances.  NS_ERR_ARG for nsteps < 1, a bad schedule or param < 1 where needed;
+ * actions to *n_actions, the largest number of simultaneously used device slots to
+ * *slots_used (host slots are not counted: see ns_run_host_bytes) and the number of
+ * primal steps advanced (first pass included) to *advances.  NS_ERR_ARG for nsteps < 1, a bad schedule or param < 1 where needed;
  * NS_ERR_BUDGET if max_actions is too small (n_actions still reports the need). */
 int ns_plan(int nsteps, int schedule, int param, ns_action* out, int max_actions, int* n_actions,
             int* slots_used, long long* advances);
@@ -225,7 +237,8 @@ int ns_plan(int nsteps, int schedule, int param, ns_action* out, int max_actions
 typedef struct {
   int nsteps;        /* primal steps N; Jbar = (1/N) sum_{n=1..N} J(w^n) */
   int schedule;      /* NS_CKPT_* */
-  int param;         /* stride (NS_CKPT_STRIDE) or state slots (NS_CKPT_REVOLVE) */
+  int param;         /* stride (NS_CKPT_STRIDE, NS_CKPT_STRIDE_HOST) or state slots
+                        (NS_CKPT_REVOLVE) */
   double lambda;     /* added adjoint viscosity nu = lambda sigma_1 [sigma_1 > tau]; 0 = none */
   double tau;
   int record_energy; /* write E_vhat(w^n, lam^n), n = 0..N, to energy[n][batch] */
@@ -234,19 +247,30 @@ typedef struct {
   const void* mlp;   /* learned closure (device network blob, see ns_mlp_*), or NULL: when set,
                         nu = lambda dx^2 sigma_1 softplus(MLP(f)) replaces the sigma_1 rule
                         (lambda is then the global factor kappa) */
+  void* host_arena;  /* NS_CKPT_STRIDE_HOST: caller-owned host memory of at least
+                        ns_run_host_bytes bytes for the snapshots (page-locked, e.g.
+                        cudaHostAlloc, for the copies to run asynchronously; pageable
+                        memory works but each copy then blocks the host); else ignored.
+                        The host must not touch it while a sweep runs. */
+  size_t host_bytes; /* its size in bytes */
 } ns_run_opts;
 
 /* Device bytes the caller must provide as the arena of ns_adjoint_run (state slots,
  * two working states, one adjoint field, sigma_1 and nu fields, scalars). */
 size_t ns_run_arena_bytes(const ns_ctx* ctx, const ns_run_opts* o);
 
+/* Host bytes of the snapshot arena of an NS_CKPT_STRIDE_HOST sweep (one FP64 state per
+ * snapshot held at once); 0 for the other schedules or a NULL argument. */
+size_t ns_run_host_bytes(const ns_ctx* ctx, const ns_run_opts* o);
+
 /* Whole forward + checkpointed backward sweep from w^0 with the time-constant source s
  * (may be NULL): Jbar[batch] (device) receives the time-averaged pressure loss,
  * lam0 (device field) dJbar/dw^0, sbar (device field, may be NULL) dJbar/ds.
  * energy / sigma_stats: device arrays or NULL (see ns_run_opts).  arena: caller-owned
  * device memory of at least ns_run_arena_bytes(ctx, o) bytes, 256-byte aligned;
- * NS_ERR_BUDGET if it is smaller.  The sweep is deterministic: replayed states are
- * bitwise identical to the first pass. */
+ * NS_ERR_BUDGET if it is smaller, or if an NS_CKPT_STRIDE_HOST sweep's host_arena is
+ * NULL or shorter than ns_run_host_bytes(ctx, o).  The sweep is deterministic: replayed
+ * states are bitwise identical to the first pass. */
 int ns_adjoint_run(ns_ctx* ctx, const double* w0, const double* s, const ns_run_opts* o,
                    void* arena, size_t arena_bytes, double* Jbar, double* lam0, double* sbar,
                    double* energy, double* sigma_stats);

@@ -37,7 +37,7 @@ EXPORTED = [
     "ns_dot_boxes", "ns_mlp_net_bytes", "ns_mlp_set_params", "ns_mlp_get_params", "ns_mlp_get_moment",
     "ns_mlp_features", "ns_mlp_infer", "ns_mlp_train_step", "ns_adjoint_label", "ns_label_target",
     "ns_launch_count", "ns_set_viscosity_split", "ns_energy_efolds", "ns_lambda_select",
-    "ns_estimate_work_bytes", "ns_estimate_lambda",
+    "ns_estimate_work_bytes", "ns_estimate_lambda", "ns_run_host_bytes",
 ]
 
 NS_MLP_PARAMS = 5185
@@ -45,7 +45,9 @@ NS_MLP_PARAMS = 5185
 NS_CKPT_ALL = 0
 NS_CKPT_STRIDE = 1
 NS_CKPT_REVOLVE = 2
+NS_CKPT_STRIDE_HOST = 3
 NS_OP_ADVANCE, NS_OP_STORE, NS_OP_LOAD, NS_OP_ADJOINT, NS_OP_FREE, NS_OP_SOURCE = 1, 2, 3, 4, 5, 6
+NS_OP_STORE_HOST, NS_OP_LOAD_HOST, NS_OP_FREE_HOST = 7, 8, 9
 
 
 class NsParams(ctypes.Structure):
@@ -67,7 +69,8 @@ class NsRunOpts(ctypes.Structure):
     _fields_ = [
         ("nsteps", ctypes.c_int), ("schedule", ctypes.c_int), ("param", ctypes.c_int),
         ("lambda_", ctypes.c_double), ("tau", ctypes.c_double), ("record_energy", ctypes.c_int),
-        ("record_sigma", ctypes.c_int), ("mlp", ctypes.c_void_p),
+        ("record_sigma", ctypes.c_int), ("mlp", ctypes.c_void_p), ("host_arena", ctypes.c_void_p),
+        ("host_bytes", ctypes.c_size_t),
     ]
 
 
@@ -132,6 +135,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "ns_plan": ([I, I, I, P, I, ctypes.POINTER(I), ctypes.POINTER(I),
                      ctypes.POINTER(ctypes.c_longlong)], I),
         "ns_run_arena_bytes": ([P, ctypes.POINTER(NsRunOpts)], S),
+        "ns_run_host_bytes": ([P, ctypes.POINTER(NsRunOpts)], S),
         "ns_adjoint_run": ([P, P, P, ctypes.POINTER(NsRunOpts), P, S, P, P, P, P, P], I),
         "ns_profile_enable": ([P, I], I),
         "ns_profile_read": ([P, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_longlong)], I),
@@ -333,14 +337,24 @@ class Solver:
 
     # --- checkpointed sweep ----------------------------------------------------------
     def run_opts(self, nsteps, schedule=NS_CKPT_ALL, param=0, lam_coef=0.0, tau=0.0,
-                 record_energy=False, record_sigma=False, mlp=None):
+                 record_energy=False, record_sigma=False, mlp=None, host_arena=None):
         """Sweep options; mlp: a network blob (uint8 CUDA tensor) selecting the learned
-        closure, with lam_coef then its global factor kappa."""
-        return NsRunOpts(nsteps, schedule, param, lam_coef, tau, int(record_energy), int(record_sigma),
-                         None if mlp is None else ctypes.c_void_p(mlp.data_ptr()))
+        closure, with lam_coef then its global factor kappa; host_arena: a uint8 CPU
+        tensor (pinned for asynchronous copies) holding the snapshots of an
+        NS_CKPT_STRIDE_HOST sweep.  The options keep a reference to it."""
+        o = NsRunOpts(nsteps, schedule, param, lam_coef, tau, int(record_energy), int(record_sigma),
+                      None if mlp is None else ctypes.c_void_p(mlp.data_ptr()),
+                      None if host_arena is None else ctypes.c_void_p(host_arena.data_ptr()),
+                      0 if host_arena is None else host_arena.numel() * host_arena.element_size())
+        o._host_arena = host_arena
+        return o
 
     def arena_bytes(self, opts) -> int:
         return int(self.lib.ns_run_arena_bytes(self._ctx, ctypes.byref(opts)))
+
+    def host_bytes(self, opts) -> int:
+        """Host bytes of an NS_CKPT_STRIDE_HOST sweep's snapshot arena (0 otherwise)."""
+        return int(self.lib.ns_run_host_bytes(self._ctx, ctypes.byref(opts)))
 
     def adjoint_run(self, w0, opts, arena, Jbar, lam0, s=None, sbar=None, energy=None,
                     sigma_stats=None):

@@ -44,6 +44,10 @@ struct Planner {
   int next_slot = 0, live = 0, maxlive = 0;
   long long adv = 0;
   std::map<int, int> slot_of;   // step -> slot for stored states
+  // host slots (NS_CKPT_STRIDE_HOST snapshots), a pool of their own
+  std::vector<int> free_hslots;
+  int next_hslot = 0, hlive = 0, maxhost = 0;
+  std::map<int, int> hslot_of;
 
   void emit(int op, int a, int b) {
     acts.push_back(ns_action{op, a, b});
@@ -75,6 +79,27 @@ struct Planner {
     --live;
   }
 
+  void hstore(int step) {
+    int h;
+    if (!free_hslots.empty()) {
+      h = free_hslots.back();
+      free_hslots.pop_back();
+    } else {
+      h = next_hslot++;
+    }
+    maxhost = std::max(maxhost, ++hlive);
+    hslot_of[step] = h;
+    emit(NS_OP_STORE_HOST, step, h);
+  }
+  void hload(int step) { emit(NS_OP_LOAD_HOST, step, hslot_of.at(step)); }
+  void hfree(int step) {
+    const int h = hslot_of.at(step);
+    emit(NS_OP_FREE_HOST, step, h);
+    hslot_of.erase(step);
+    free_hslots.push_back(h);
+    --hlive;
+  }
+
   void plan_all(int N) {
     for (int n = 0; n < N; ++n) {
       emit(NS_OP_ADVANCE, n, n + 1);
@@ -97,6 +122,35 @@ struct Planner {
     for (int a = ((N - 1) / k) * k; a >= 0; a -= k) {
       const int b = std::min(a + k, N);
       load(a);
+      for (int j = a + 1; j < b; ++j) {
+        emit(NS_OP_ADVANCE, j - 1, j);
+        store(j);
+      }
+      for (int n = b - 1; n >= a; --n) {
+        load(n);
+        emit(NS_OP_ADJOINT, n, 0);
+        release(n);
+      }
+    }
+  }
+
+  // plan_stride with the snapshots in host slots: a segment's snapshot comes back into a
+  // device slot once, and the host slot is released at once
+  void plan_stride_host(int N, int k) {
+    for (int n = 0; n < N; ++n) {
+      if (n > 0 && n % k == 0) hstore(n);
+      emit(NS_OP_ADVANCE, n, n + 1);
+    }
+    emit(NS_OP_SOURCE, N, 0);
+    for (int a = ((N - 1) / k) * k; a >= 0; a -= k) {
+      const int b = std::min(a + k, N);
+      if (a == 0) {
+        load(0);
+      } else {
+        hload(a);
+        store(a);
+        hfree(a);
+      }
       for (int j = a + 1; j < b; ++j) {
         emit(NS_OP_ADVANCE, j - 1, j);
         store(j);
@@ -168,6 +222,10 @@ int make_plan(int N, int schedule, int param, Planner& P) {
       if (param < 1) return NS_ERR_ARG;
       P.plan_revolve(N, param);
       break;
+    case NS_CKPT_STRIDE_HOST:
+      if (param < 1) return NS_ERR_ARG;
+      P.plan_stride_host(N, param);
+      break;
     default: return NS_ERR_ARG;
   }
   return NS_OK;
@@ -200,7 +258,7 @@ Layout layout_for(const ns_ctx* c, int slots_used, bool closure, int schedule, i
   L.stage = align256(ns_i_stage_bytes(c));
   L.mir = 2 * L.stage;
   L.lmir = c->p.precision == NS_MIXED ? 2 * L.stage : 0;
-  L.nkeep = schedule == NS_CKPT_STRIDE ? param : 0;
+  L.nkeep = (schedule == NS_CKPT_STRIDE || schedule == NS_CKPT_STRIDE_HOST) ? param : 0;
   L.keep = (size_t)L.nkeep * 4 * L.stage;
   L.total = L.state * L.nbuf + L.lam + L.sig + L.nu + L.scal + L.feat + L.mir + L.lmir + L.keep;
   return L;
@@ -230,6 +288,13 @@ size_t ns_run_arena_bytes(const ns_ctx* c, const ns_run_opts* o) {
   Planner P;
   if (make_plan(o->nsteps, o->schedule, o->param, P)) return 0;
   return layout_for(c, P.maxlive, o->mlp != nullptr, o->schedule, o->param).total;
+}
+
+size_t ns_run_host_bytes(const ns_ctx* c, const ns_run_opts* o) {
+  if (!c || !o || o->schedule != NS_CKPT_STRIDE_HOST) return 0;
+  Planner P;
+  if (make_plan(o->nsteps, o->schedule, o->param, P)) return 0;
+  return (size_t)P.maxhost * align256(c->field * sizeof(double));
 }
 
 }  // extern "C"
@@ -368,6 +433,29 @@ int run_actions(ns_ctx* c, ns_sweep_state& S, int stop_op, double*& lam_cur, dou
         S.owned[S.slot_buf[A.b]] = 0;
         S.slot_buf[A.b] = -1;
         break;
+      case NS_OP_STORE_HOST: {
+        // stream-ordered: later kernels that reuse the buffer run after the copy
+        if (S.cur < 0 || A.b < 0 || A.b >= S.P.maxhost) return NS_ERR_ARG;
+        char* hp = (char*)S.o.host_arena + (size_t)A.b * S.L.state;
+        if (cudaMemcpyAsync(hp, S.buf[S.cur], c->field * sizeof(double), cudaMemcpyDeviceToHost, c->st) !=
+            cudaSuccess)
+          return NS_ERR_CUDA;
+        break;
+      }
+      case NS_OP_LOAD_HOST: {
+        if (A.b < 0 || A.b >= S.P.maxhost) return NS_ERR_ARG;
+        const int out = pick_free();
+        if (out < 0) return NS_ERR_BUDGET;
+        const char* hp = (const char*)S.o.host_arena + (size_t)A.b * S.L.state;
+        if (cudaMemcpyAsync(S.buf[out], hp, c->field * sizeof(double), cudaMemcpyHostToDevice, c->st) !=
+            cudaSuccess)
+          return NS_ERR_CUDA;
+        S.cur = out;
+        S.cur_mirror = nullptr;
+        break;
+      }
+      case NS_OP_FREE_HOST:
+        break;
       case NS_OP_SOURCE:
         if ((r = ns_objective(c, ptr(S.cur), wN, S.jtmp, lam_cur))) return r;
         S.lamf_valid = false;
@@ -441,6 +529,11 @@ static int forward_run_impl(ns_ctx* c, const double* w0, const double* s, const 
   }
   S->L = layout_for(c, S->P.maxlive, o->mlp != nullptr, o->schedule, o->param);
   if (arena_bytes < S->L.total) {
+    delete S;
+    return NS_ERR_BUDGET;
+  }
+  if (o->schedule == NS_CKPT_STRIDE_HOST && S->P.maxhost > 0 &&
+      (!o->host_arena || o->host_bytes < (size_t)S->P.maxhost * S->L.state)) {
     delete S;
     return NS_ERR_BUDGET;
   }

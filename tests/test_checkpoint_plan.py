@@ -12,6 +12,7 @@ from paper_1511_06959_gb300 import synth
 from tests.test_oracle_primal import params_for
 
 ADV, STORE, LOAD, ADJ, FREE, SRC = 1, 2, 3, 4, 5, 6
+HSTORE, HLOAD, HFREE = 7, 8, 9
 
 
 def _api():
@@ -21,11 +22,14 @@ def _api():
     return api
 
 
-def simulate(actions, N, slots_used):
+def simulate(actions, N, slots_used, host_peak=None):
     """Symbolic run: the state is its step index.  Returns (first-touch order, number of
-    adjoint steps, peak live slots, advances)."""
+    adjoint steps, peak live slots, advances); host_peak, a list, receives the peak of
+    live host slots."""
     cur = 0
     slots = {}
+    hslots = {}
+    hpeak = 0
     touched = 0
     first = []
     adj = []
@@ -51,6 +55,15 @@ def simulate(actions, N, slots_used):
             assert cur == a
         elif op == FREE:
             assert slots.pop(b) == a
+        elif op == HSTORE:
+            assert cur == a and a > 0 and b not in hslots
+            hslots[b] = a
+            hpeak = max(hpeak, len(hslots))
+        elif op == HLOAD:
+            cur = hslots[b]
+            assert cur == a
+        elif op == HFREE:
+            assert hslots.pop(b) == a
         elif op == SRC:
             assert a == N and cur == N and not adj
             src_done = True
@@ -58,11 +71,13 @@ def simulate(actions, N, slots_used):
             assert src_done and cur == a
             assert a == (adj[-1] - 1 if adj else N - 1)
             adj.append(a)
-    assert not slots
+    assert not slots and not hslots
+    if host_peak is not None:
+        host_peak.append(hpeak)
     return first, adj, peak, adv
 
 
-CASES = [(0, 0), (1, 1), (1, 4), (1, 50), (2, 1), (2, 2), (2, 3), (2, 5), (2, 20)]
+CASES = [(0, 0), (1, 1), (1, 4), (1, 50), (2, 1), (2, 2), (2, 3), (2, 5), (2, 20), (3, 1), (3, 4), (3, 50)]
 
 
 @pytest.mark.parametrize("N", [1, 2, 3, 7, 13, 50, 201])
@@ -70,10 +85,22 @@ CASES = [(0, 0), (1, 1), (1, 4), (1, 50), (2, 1), (2, 2), (2, 3), (2, 5), (2, 20
 def test_plan_invariants(N, schedule, param):
     api = _api()
     actions, slots_used, advances = api.plan(N, schedule, param)
-    first, adj, peak, adv = simulate(actions, N, slots_used)
+    hp = []
+    first, adj, peak, adv = simulate(actions, N, slots_used, hp)
     assert first == list(range(1, N + 1))
     assert adj == list(range(N - 1, -1, -1))
     assert peak == slots_used and adv == advances
+    if schedule != 3:
+        assert hp == [0]
+    else:
+        # the stride plan's steps, with the snapshots in host slots and only the replayed
+        # segment's states in device slots
+        k = param
+        assert hp == [(N - 1) // k]
+        assert slots_used <= k
+        ref_actions, _, ref_adv = api.plan(N, 1, k)
+        assert advances == ref_adv
+        assert [x for x in actions if x[0] in (ADV, ADJ, SRC)] == [x for x in ref_actions if x[0] in (ADV, ADJ, SRC)]
     if schedule == 0:
         assert advances == N and slots_used == max(N - 1, 0)
     if schedule == 1:
@@ -122,11 +149,14 @@ def test_plan_rejects_bad_arguments():
         api.plan(10, 1, 0)
     with pytest.raises(api.NsError):
         api.plan(10, 9, 3)
+    with pytest.raises(api.NsError):
+        api.plan(10, 3, 0)
 
 
 def execute_with_oracle(actions, w0, P, N, s=None):
     """Run a plan with the oracle's step functions (what the GPU executor does)."""
     slots = {}
+    hslots = {}
     cur = w0
     lam = np.zeros_like(w0)
     J = 0.0
@@ -145,6 +175,12 @@ def execute_with_oracle(actions, w0, P, N, s=None):
             cur = w0 if b == -1 else slots[b]
         elif op == FREE:
             slots.pop(b)
+        elif op == HSTORE:
+            hslots[b] = cur.copy()
+        elif op == HLOAD:
+            cur = hslots[b].copy()
+        elif op == HFREE:
+            hslots.pop(b)
         elif op == SRC:
             lam = lam + O.objective_grad(cur, P) / N
         elif op == ADJ:
@@ -155,7 +191,7 @@ def execute_with_oracle(actions, w0, P, N, s=None):
     return J, lam, sbar
 
 
-@pytest.mark.parametrize("schedule,param", [(0, 0), (1, 4), (2, 2), (2, 3)])
+@pytest.mark.parametrize("schedule,param", [(0, 0), (1, 4), (2, 2), (2, 3), (3, 4), (3, 3), (3, 1)])
 def test_plan_executed_with_oracle_equals_store_all(schedule, param):
     api = _api()
     w0 = synth.isentropic_vortex(8, 6, 1, noise=1e-3, seed=4)

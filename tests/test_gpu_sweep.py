@@ -109,3 +109,51 @@ def test_batched_sweep_matches_single_boxes():
         Ji, li, _, _, _ = _run(api, S1, ws0[i], N, 1, 2)
         assert J[i].item() == Ji.item()
         assert torch.equal(lam[i], li[0] if li.dim() == 5 else li)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_host_snapshots_give_the_stride_bits(prec):
+    """NS_CKPT_STRIDE_HOST keeps the every-k-th snapshots in host memory and copies them
+    on the context's stream: the sweep (stabilised, with a source, energy and sigma_1
+    series) gives the stride schedule's bits, from page-locked and from pageable host
+    memory, in less device memory; a short host arena is a budget error."""
+    api = _api()
+    w0 = synth.isentropic_vortex(33, 10, 3, noise=1e-3, seed=5)
+    P = params_for(w0, mu=1e-3, dt=4e-3)
+    s = np.zeros_like(w0)
+    s[1] = 0.05 * synth.forcing_bumps(33, 10, 3, n=4)[0]
+    N, k = 14, 4
+    lam_coef = 0.5 * P.dx[0] ** 2
+    S = make_solver(api, w0, P, prec)
+    ref = _run(api, S, w0, N, 1, k, s, lam_coef=lam_coef, energy=True, sigma=True)
+    probe = S.run_opts(N, api.NS_CKPT_STRIDE_HOST, k, lam_coef, 0.0, True, True)
+    field = ((w0.size * 8 + 255) // 256) * 256
+    assert S.host_bytes(probe) == ((N - 1) // k) * field
+    assert S.host_bytes(S.run_opts(N, api.NS_CKPT_STRIDE, k)) == 0
+    assert S.arena_bytes(probe) < S.arena_bytes(S.run_opts(N, api.NS_CKPT_STRIDE, k, lam_coef))
+    for pinned in (True, False):
+        host = torch.empty(S.host_bytes(probe), dtype=torch.uint8, pin_memory=pinned)
+        opts = S.run_opts(N, api.NS_CKPT_STRIDE_HOST, k, lam_coef, 0.0, True, True, host_arena=host)
+        arena = torch.empty(S.arena_bytes(opts), dtype=torch.uint8, device="cuda")
+        J = torch.empty(1, dtype=torch.float64, device="cuda")
+        lam0 = torch.empty(w0.shape, dtype=torch.float64, device="cuda")
+        sbar = torch.empty_like(lam0)
+        E = torch.zeros((N + 1, 1), dtype=torch.float64, device="cuda")
+        st = torch.zeros((N, 1, 2), dtype=torch.float64, device="cuda")
+        S.adjoint_run(dev(w0), opts, arena, J, lam0, s=dev(s), sbar=sbar, energy=E, sigma_stats=st)
+        torch.cuda.synchronize()
+        assert S.last_error() == 0
+        for got, want in zip((J, lam0, sbar, E, st), ref):
+            assert torch.equal(got, want)
+    short = torch.empty(S.host_bytes(probe) - 256, dtype=torch.uint8)
+    opts = S.run_opts(N, api.NS_CKPT_STRIDE_HOST, k, lam_coef, host_arena=short)
+    arena = torch.empty(S.arena_bytes(opts), dtype=torch.uint8, device="cuda")
+    with pytest.raises(api.NsError) as e:
+        S.adjoint_run(dev(w0), opts, arena, torch.empty(1, dtype=torch.float64, device="cuda"),
+                      torch.empty(w0.shape, dtype=torch.float64, device="cuda"))
+    assert e.value.code == api.NS_ERR_BUDGET
+    opts = S.run_opts(N, api.NS_CKPT_STRIDE_HOST, k, lam_coef)
+    with pytest.raises(api.NsError) as e:
+        S.adjoint_run(dev(w0), opts, arena, torch.empty(1, dtype=torch.float64, device="cuda"),
+                      torch.empty(w0.shape, dtype=torch.float64, device="cuda"))
+    assert e.value.code == api.NS_ERR_BUDGET
