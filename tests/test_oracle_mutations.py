@@ -1,0 +1,196 @@
+"""The oracle's pins are strong enough to catch plausible mistakes: each test plants one
+mistake in a copy of an oracle function (on the CPU; the oracle module itself is put
+back afterwards) and checks that the pin written for that function then fails.  The
+planted versions live only here."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import mlp_oracle as ML
+from oracle import ns_oracle as O
+from tests import test_oracle_lambda as TL
+from tests import test_oracle_mlp as TM
+from tests import test_oracle_primal as TP
+
+
+def _fails(pin, *args):
+    try:
+        pin(*args)
+    except AssertionError:
+        return True
+    return False
+
+
+# ---- the closure label: nu* = max(0, v^T M v) / |grad v|^2 -------------------------
+def _label(variant):
+    def f(w, lam, P, eps=1e-30):
+        vh = O.symmetric_adjoint(w, lam, P)
+        M = O.growth_matrix_field(w, P)
+        if w.shape[1] == 1 and variant != "u3_in_2d_block":
+            idx = [0, 1, 2, 4]
+            M = M[..., idx, :][..., :, idx]
+            vh = vh[idx]
+        vc = np.moveaxis(vh, 0, -1)
+        growth = np.einsum("...i,...ij,...j->...", vc, M, vc)
+        grad2 = np.zeros(w.shape[1:])
+        for d in range(3):
+            ax = d + 1 if variant == "axis_mixup" else 3 - d
+            den = P.dx[d] if variant == "difference_over_h" else 2.0 * P.dx[d]
+            gd = (np.roll(vh, -1, axis=ax) - np.roll(vh, 1, axis=ax)) / den
+            grad2 += np.sum(gd * gd, axis=0)
+        if variant == "no_clamp":
+            g = growth
+        elif variant == "growth_sign":
+            g = np.maximum(-growth, 0.0)
+        else:
+            g = np.maximum(growth, 0.0)
+        return g / (grad2 + eps)
+    return f
+
+
+@pytest.mark.parametrize("variant", ["u3_in_2d_block", "axis_mixup", "difference_over_h", "no_clamp",
+                                     "growth_sign"])
+def test_label_pin_catches(monkeypatch, variant):
+    monkeypatch.setattr(ML, "label_rate", _label("none"))
+    assert not _fails(TM.test_label_closed_form_on_a_sinusoidal_shear, 1)
+    assert not _fails(TM.test_label_closed_form_on_a_sinusoidal_shear, 3)
+    monkeypatch.setattr(ML, "label_rate", _label(variant))
+    assert (_fails(TM.test_label_closed_form_on_a_sinusoidal_shear, 1) or
+            _fails(TM.test_label_closed_form_on_a_sinusoidal_shear, 3))
+
+
+# ---- the energy-growth fit --------------------------------------------------------
+def _efolds(variant):
+    def f(E):
+        E = np.asarray(E, dtype=np.float64)
+        N = E.shape[0] - 1
+        M = N // 2
+        if M < 1:
+            raise ValueError("the window needs N >= 2")
+        win = E[N - M:] if variant == "first_half_of_sweep" else E[: M + 1]
+        if not np.all(np.isfinite(win)) or np.any(win <= 0.0):
+            return math.inf
+        m = np.arange(M + 1, dtype=np.float64) + (N - M if variant == "first_half_of_sweep" else 0)
+        if variant == "no_normalisation":
+            y = np.log(win)
+        elif variant == "normalised_by_N_minus_m":
+            y = np.log(win / (N - m) ** 2) if np.all(N - m > 0) else np.log(win)
+        else:
+            y = np.log(win / (N - m + 1.0) ** 2)
+        mc = m - m.mean()
+        slope = float(np.sum(mc * (y - y.mean())) / np.sum(mc * mc))
+        scale = N if variant == "scaled_by_N" else M
+        return scale * slope if variant == "sign" else -scale * slope
+    return f
+
+
+@pytest.mark.parametrize("variant", ["first_half_of_sweep", "no_normalisation", "normalised_by_N_minus_m",
+                                     "scaled_by_N", "sign"])
+def test_efolds_pins_catch(monkeypatch, variant):
+    monkeypatch.setattr(O, "energy_efolds", _efolds("none"))
+    for N in (2, 3, 10, 41):
+        assert not _fails(TL.test_efolds_of_an_exact_exponential, N)
+    assert not _fails(TL.test_efolds_window_scale_and_degenerate_cases)
+    monkeypatch.setattr(O, "energy_efolds", _efolds(variant))
+    caught = any(_fails(TL.test_efolds_of_an_exact_exponential, N) for N in (2, 3, 10, 41))
+    caught = caught or _fails(TL.test_efolds_window_scale_and_degenerate_cases)
+    assert caught
+
+
+# ---- the plateau rule -------------------------------------------------------------
+def _select(variant):
+    def f(efolds, change, efold_tol, rel_tol):
+        for i in range(len(change)):
+            if efolds[i] <= efold_tol and change[i] <= rel_tol:
+                return i + 1 if variant == "takes_the_larger_of_the_pair" else i
+        return -1
+    return f
+
+
+def _change(variant):
+    def f(g_a, g_b):
+        g_a = np.asarray(g_a, dtype=np.float64)
+        g_b = np.asarray(g_b, dtype=np.float64)
+        d = math.sqrt(float(np.sum((g_b - g_a) ** 2)))
+        nb = math.sqrt(float(np.sum((g_a if variant == "relative_to_smaller_lambda" else g_b) ** 2)))
+        if nb == 0.0:
+            return 0.0 if d == 0.0 else math.inf
+        return d / nb
+    return f
+
+
+def test_plateau_pin_catches_choosing_the_larger_factor(monkeypatch):
+    monkeypatch.setattr(O, "select_lambda", _select("none"))
+    assert not _fails(TL.test_plateau_rule_picks_the_row_where_the_paper_matches_fd)
+    monkeypatch.setattr(O, "select_lambda", _select("takes_the_larger_of_the_pair"))
+    assert _fails(TL.test_plateau_rule_picks_the_row_where_the_paper_matches_fd)
+
+
+def test_change_pin_catches_the_wrong_reference_norm(monkeypatch):
+    monkeypatch.setattr(O, "sensitivity_change", _change("none"))
+    assert not _fails(TL.test_sensitivity_change_and_selection_edge_cases)
+    monkeypatch.setattr(O, "sensitivity_change", _change("relative_to_smaller_lambda"))
+    assert _fails(TL.test_sensitivity_change_and_selection_edge_cases)
+
+
+# ---- the primal's viscous flux, heat flux and objective ----------------------------
+
+def _stress(variant):
+    def f(g, d, P):
+        div = g[0, 0] + g[1, 1] + g[2, 2]
+        sig = np.empty((3,) + g.shape[2:])
+        for j in range(3):
+            sig[j] = P.mu * (g[j, d] + (0.0 if variant == "no_transpose_term" else g[d, j]))
+            if j == d and variant != "no_dilatation_term":
+                sig[j] -= (2.0 / 3.0) * P.mu * div
+        return sig
+    return f
+
+
+@pytest.mark.parametrize("variant", ["no_dilatation_term", "no_transpose_term"])
+def test_stress_pins_catch(monkeypatch, variant):
+    pins = [TP.test_viscous_flux_of_linear_shear_and_heat,
+            TP.test_viscous_flux_of_linear_compression_stokes_hypothesis]
+    monkeypatch.setattr(O, "stress_row", _stress("none"))
+    assert not any(_fails(p) for p in pins)
+    monkeypatch.setattr(O, "stress_row", _stress(variant))
+    assert any(_fails(p) for p in pins)
+
+
+def test_heat_flux_pin_catches_alpha_without_gamma(monkeypatch):
+    monkeypatch.setattr(O.Params, "alpha", property(lambda self: self.mu / self.Pr))
+    assert _fails(TP.test_heat_flux_through_the_temperature)
+
+
+def _objective(variant):
+    def f(w, P):
+        wf = O.plane_state(w, P)
+        pt = O.stagnation_pressure(wf[0], wf[1:4], wf[4], P)
+        if variant == "unweighted":
+            return float(np.mean(P.pt_in - pt)) / P.pt_in
+        if variant == "sign":
+            return float(np.sum(wf[0] * (pt - P.pt_in)) / np.sum(wf[0])) / P.pt_in
+        if variant == "not_normalised":
+            return float(np.sum(wf[0] * (P.pt_in - pt)) / np.sum(wf[0]))
+        return float(np.sum(wf[0] * (P.pt_in - pt)) / np.sum(wf[0])) / P.pt_in
+    return f
+
+
+@pytest.mark.parametrize("variant", ["unweighted", "sign", "not_normalised"])
+def test_objective_pin_catches(monkeypatch, variant):
+    monkeypatch.setattr(O, "objective", _objective("none"))
+    assert not _fails(TP.test_objective_closed_form_on_a_two_state_plane)
+    monkeypatch.setattr(O, "objective", _objective(variant))
+    assert _fails(TP.test_objective_closed_form_on_a_two_state_plane)
+
+
+def test_stagnation_pin_catches_the_wrong_exponent(monkeypatch):
+    def pt(rho, m, rhoE, P):
+        u2 = (m[0] ** 2 + m[1] ** 2 + m[2] ** 2) / rho ** 2
+        p = (P.gamma - 1.0) * (rhoE - 0.5 * rho * u2)
+        M2 = u2 / (P.gamma * p / rho)
+        return p * (1.0 + 0.5 * (P.gamma - 1.0) * M2) ** (1.0 / (P.gamma - 1.0))
+    monkeypatch.setattr(O, "stagnation_pressure", pt)
+    assert _fails(TP.test_stagnation_pressure_closed_forms)
+    assert _fails(TP.test_objective_closed_form_on_a_two_state_plane)

@@ -173,3 +173,68 @@ def test_objective_uniform_and_gradient_by_fd():
         wm[idx] -= h
         fd = (O.objective(wp, P) - O.objective(wm, P)) / (2 * h)
         assert abs(fd - G[idx]) <= 1e-8 * max(abs(fd), 1e-6), (idx, fd, G[idx])
+
+
+def test_viscous_flux_of_linear_compression_stokes_hypothesis():
+    """u1 = s x (a uniform compression, div u = s): with zero bulk viscosity the normal
+    stresses are 2 mu s - 2/3 mu s = 4/3 mu s along x and -2/3 mu s along y and z, and
+    there is no shear stress (Eq. e:navier).  Checked away from the periodic seam."""
+    nx, ny, nz = 12, 6, 5
+    g, mu, Pr = 1.4, 0.3, 0.72
+    dx = (0.1, 0.2, 0.15)
+    x = (np.arange(nx) + 0.5) * dx[0]
+    s = 0.4
+    rho = np.ones((nz, ny, nx))
+    u = np.stack([np.broadcast_to(s * x, rho.shape), np.zeros_like(rho), np.zeros_like(rho)])
+    w = synth._conservative(rho, u, np.full_like(rho, 0.7), g)
+    P = O.Params(gamma=g, mu=mu, Pr=Pr, dx=dx)
+    interior = (slice(None), slice(None), slice(1, nx - 2))
+    Fx, Fy, Fz = (O.viscous_face_flux(w, d, P) for d in range(3))
+    np.testing.assert_allclose(Fx[1][interior], 4.0 / 3.0 * mu * s, rtol=1e-12)
+    np.testing.assert_allclose(Fy[2][interior], -2.0 / 3.0 * mu * s, rtol=1e-12)
+    np.testing.assert_allclose(Fz[3][interior], -2.0 / 3.0 * mu * s, rtol=1e-12)
+    for F, d in ((Fx, 0), (Fy, 1), (Fz, 2)):
+        for j in range(3):
+            if j != d:
+                np.testing.assert_allclose(F[1 + j][interior], 0.0, atol=1e-13)
+
+
+def test_heat_flux_through_the_temperature():
+    """The heat flux written as k dT/dx with k = mu c_p / Pr and T = e / c_v (any gas
+    constant R: c_v = R / (gamma - 1), c_p = gamma c_v) for a linear internal energy at
+    rest: the energy component of the x-face flux."""
+    nx, ny, nz = 10, 4, 1
+    g, mu, Pr, R = 1.4, 0.3, 0.72, 287.0
+    dx = (0.1, 0.1, 0.1)
+    x = (np.arange(nx) + 0.5) * dx[0]
+    q = 0.25
+    rho = np.full((nz, ny, nx), 1.3)
+    e = np.broadcast_to(2.0 + q * x, rho.shape)
+    w = synth._conservative(rho, np.zeros((3,) + rho.shape), (g - 1) * rho * e, g)
+    P = O.Params(gamma=g, mu=mu, Pr=Pr, dx=dx)
+    cv = R / (g - 1.0)
+    cp = g * cv
+    dTdx = q / cv
+    Fx = O.viscous_face_flux(w, 0, P)
+    np.testing.assert_allclose(Fx[4][..., 1:nx - 2], mu * cp / Pr * dTdx, rtol=1e-12)
+
+
+def test_objective_closed_form_on_a_two_state_plane():
+    """One plane face at rest (p_t = p) and one at Mach 1 (p_t = p (1.2)^3.5 for
+    gamma = 1.4): J = [rho_a (p_t,in - p_a) + rho_b (p_t,in - 1.2^3.5 p_b)] / (rho_a +
+    rho_b) / p_t,in, the density-weighted loss of Eq. (e:pressure_loss)."""
+    g = 1.4
+    nx, ny, nz = 8, 2, 1
+    ra, pa, rb, pb = 1.0, 0.9, 2.0, 0.5
+    rho = np.empty((nz, ny, nx))
+    rho[:, 0], rho[:, 1] = ra, rb
+    p = np.empty_like(rho)
+    p[:, 0], p[:, 1] = pa, pb
+    cb = math.sqrt(g * pb / rb)
+    u = np.zeros((3,) + rho.shape)
+    u[0][:, 1] = cb
+    w = synth._conservative(rho, u, p, g)
+    pt_in = 1.3
+    P = O.Params(gamma=g, dx=synth.box_shape(nx, ny, nz), plane_i=6, pt_in=pt_in)
+    expect = (ra * (pt_in - pa) + rb * (pt_in - 1.2 ** 3.5 * pb)) / (ra + rb) / pt_in
+    assert O.objective(w, P) == pytest.approx(expect, rel=1e-13)
