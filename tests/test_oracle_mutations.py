@@ -9,9 +9,11 @@ import pytest
 
 from oracle import mlp_oracle as ML
 from oracle import ns_oracle as O
+from tests import test_oracle_adjoint as TA
 from tests import test_oracle_lambda as TL
 from tests import test_oracle_mlp as TM
 from tests import test_oracle_primal as TP
+from tests import test_oracle_sigma as TS
 
 
 def _fails(pin, *args):
@@ -194,3 +196,79 @@ def test_stagnation_pin_catches_the_wrong_exponent(monkeypatch):
     monkeypatch.setattr(O, "stagnation_pressure", pt)
     assert _fails(TP.test_stagnation_pressure_closed_forms)
     assert _fails(TP.test_objective_closed_form_on_a_two_state_plane)
+
+
+# ---- the hand-derived transpose and the RK4 adjoint step ---------------------------
+def test_transpose_pins_catch_a_dropped_viscous_part_and_an_untransposed_jacobian(monkeypatch):
+    import dataclasses
+    true_T = O.residual_transpose
+    pin = TA.test_transpose_dot_product_identity
+    assert not _fails(pin, (7, 5, 3))
+    monkeypatch.setattr(O, "residual_transpose", lambda w, a, P: true_T(w, a, dataclasses.replace(P, mu=0.0)))
+    assert _fails(pin, (7, 5, 3))
+    monkeypatch.setattr(O, "residual_transpose", lambda w, a, P: O.residual_tangent(w, a, P))
+    assert _fails(pin, (7, 5, 3))
+
+
+def _rk4_adjoint(variant):
+    def f(w, lam, P, s=None, nu=None):
+        dt = P.dt
+        _, (W1, W2, W3, W4) = O.rk4_step(w, P, s)
+
+        def JT(W, ab):
+            g = O.residual_transpose(W, ab, P)
+            if nu is not None:
+                g = g + O.viscosity_apply(ab, nu, P)
+            return g
+
+        a4 = dt / 6.0 * lam
+        g4 = JT(W3 if variant == "stage_state_off_by_one" else W4, a4)
+        a3 = (dt / 6.0 if variant == "weight_b3" else dt / 3.0) * lam + dt * g4
+        g3 = JT(W3, a3)
+        a2 = dt / 3.0 * lam + (dt if variant == "coefficient_a32" else 0.5 * dt) * g3
+        g2 = JT(W2, a2)
+        a1 = dt / 6.0 * lam + 0.5 * dt * g2
+        g1 = JT(W1, a1)
+        seeds = a1 + a2 + a3 + (0.0 if variant == "seed_sum_without_a4" else a4)
+        return lam + g1 + g2 + g3 + g4, seeds
+    return f
+
+
+@pytest.mark.parametrize("variant", ["stage_state_off_by_one", "weight_b3", "coefficient_a32",
+                                     "seed_sum_without_a4"])
+def test_rk4_adjoint_pins_catch(monkeypatch, variant):
+    pins = [TA.test_rk4_step_adjoint_dot_product, TA.test_trajectory_dot_product_with_source]
+    monkeypatch.setattr(O, "rk4_adjoint_step", _rk4_adjoint("none"))
+    assert not any(_fails(p) for p in pins)
+    monkeypatch.setattr(O, "rk4_adjoint_step", _rk4_adjoint(variant))
+    assert any(_fails(p) for p in pins)
+
+
+# ---- the growth matrix and sigma_1 ------------------------------------------------
+def test_growth_matrix_pin_catches_rows_and_columns_exchanged(monkeypatch):
+    true_M = O.growth_matrix_closed
+    pin = TS.test_closed_form_growth_matrix_equals_definition
+    assert not _fails(pin)
+    monkeypatch.setattr(O, "growth_matrix_closed", lambda *a: np.swapaxes(true_M(*a), -1, -2))
+    assert _fails(pin)
+
+
+def _sigma1(variant):
+    def f(w, P):
+        M = O.growth_matrix_field(w, P)
+        if w.shape[1] == 1:
+            idx = [0, 1, 2, 3] if variant == "u3_instead_of_p_in_2d" else [0, 1, 2, 4]
+            M = M[..., idx, :][..., :, idx]
+        if variant == "symmetric_part":
+            M = 0.5 * (M + np.swapaxes(M, -1, -2))
+        return np.linalg.svd(M, compute_uv=False)[..., 0]
+    return f
+
+
+@pytest.mark.parametrize("variant", ["symmetric_part", "u3_instead_of_p_in_2d"])
+def test_sigma1_pin_catches(monkeypatch, variant):
+    pin = TS.test_sigma1_field_uniform_zero_and_svd_vs_eig
+    monkeypatch.setattr(O, "sigma1_field", _sigma1("none"))
+    assert not _fails(pin)
+    monkeypatch.setattr(O, "sigma1_field", _sigma1(variant))
+    assert _fails(pin)
