@@ -272,3 +272,17 @@ def test_sigma1_pin_catches(monkeypatch, variant):
     assert not _fails(pin)
     monkeypatch.setattr(O, "sigma1_field", _sigma1(variant))
     assert _fails(pin)
+
+
+# ---- the adjoint energy -----------------------------------------------------------
+@pytest.mark.parametrize("variant", ["no_cell_volume", "norm_not_squared"])
+def test_energy_pin_catches(monkeypatch, variant):
+    def E(w, lam, P):
+        vh = O.symmetric_adjoint(w, lam, P)
+        s = float(np.sum(vh * vh))
+        if variant == "norm_not_squared":
+            s = math.sqrt(s)
+        return s if variant == "no_cell_volume" else s * P.dx[0] * P.dx[1] * P.dx[2]
+    monkeypatch.setattr(O, "adjoint_energy", E)
+    assert (_fails(TS.test_adjoint_energy_is_the_integral_of_vhat_squared, (12, 5, 3)) or
+            _fails(TS.test_adjoint_energy_is_the_integral_of_vhat_squared, (7, 4, 1)))

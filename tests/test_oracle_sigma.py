@@ -3,6 +3,7 @@ adjoint energy (sections "Symmetrization" and "Energy analysis").  No GPU."""
 import math
 
 import numpy as np
+import pytest
 
 from oracle import ns_oracle as O
 from paper_1511_06959_gb300 import synth
@@ -170,3 +171,27 @@ def test_symmetric_adjoint_roundtrip_and_sensitivity_invariance():
     assert abs(O.dot(lam, dw) - O.dot(vh, dv)) < 1e-11 * abs(O.dot(lam, dw))
     E = O.adjoint_energy(w, lam, P)
     assert abs(E - np.sum(vh * vh) * np.prod(P.dx)) < 1e-12 * E
+
+
+@pytest.mark.parametrize("shape", [(12, 5, 3), (7, 4, 1)])
+def test_adjoint_energy_is_the_integral_of_vhat_squared(shape):
+    """E_vhat = int v_hat . v_hat dV (section "Energy analysis", read as a sum of
+    squares): on a uniform state with v_hat = (a sin(2 pi x / L_x), 0, b, 0, 0) the
+    midpoint sum of sin^2 over a whole period is exactly half the cell count, so
+    E = (a^2 / 2 + b^2) L_x L_y L_z at any resolution."""
+    nx, ny, nz = shape
+    g = 1.4
+    rho = np.full((nz, ny, nx), 1.2)
+    u = np.stack([np.full_like(rho, 0.4), np.full_like(rho, -0.1), np.zeros_like(rho)])
+    w = synth._conservative(rho, u, np.full_like(rho, 0.8 / g), g)
+    P = params_for(w)
+    dx = P.dx
+    x = (np.arange(nx) + 0.5) * dx[0]
+    a, b = 0.7, -0.3
+    vh = np.zeros_like(w)
+    vh[0] = a * np.sin(2 * math.pi * x / (nx * dx[0]))
+    vh[2] = b
+    T = O.transform_T(w, P)
+    lam = np.moveaxis(np.einsum("...ji,...j->...i", T, np.moveaxis(vh, 0, -1)), -1, 0)
+    volume = nx * dx[0] * ny * dx[1] * nz * dx[2]
+    assert O.adjoint_energy(w, lam, P) == pytest.approx((a * a / 2 + b * b) * volume, rel=1e-12)
