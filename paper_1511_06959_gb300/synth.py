@@ -97,6 +97,15 @@ def solenoidal_turbulence(nx, ny, nz, mach=0.9, rms=0.1, seed=2, kmin=2, kmax=16
     K = np.sqrt(KX ** 2 + KY ** 2 + KZ ** 2)
     kn = K * Ly / (2.0 * math.pi)          # shell index in units of 2 pi / L_y
     shell = (kn >= kmin) & (kn <= kmax)
+    # an even axis's Nyquist plane has no mirror mode, so its real part would not stay
+    # perpendicular to k: leave it empty (it lies outside the shells on the benchmark boxes)
+    for axis, n in ((0, nz), (1, ny), (2, nx)):
+        if n % 2 == 0:
+            nyq = np.zeros(K.shape, dtype=bool)
+            idx = [slice(None)] * 3
+            idx[axis] = n // 2
+            nyq[tuple(idx)] = True
+            shell &= ~nyq
     amp = np.zeros_like(K)
     # 3D: |u_hat(k)|^2 ~ E(k) / k^2 with E ~ k^(-5/3)
     amp[shell] = kn[shell] ** (-11.0 / 6.0)
