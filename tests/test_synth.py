@@ -28,7 +28,7 @@ def test_isentropic_vortex(nz):
     np.testing.assert_allclose(p / rho ** g, 1.0 / g, rtol=1e-12)
     corner = (0, 0, 0)
     assert abs(rho[corner] - 1.0) < 1e-9 and abs(u[0][corner] - mach) < 1e-6
-    # the grid has no node at the centre: compare the four centre cells with the formula
+    # every cell against the closed form (no noise)
     X, Y, _, (Lx, Ly, _) = synth._centres(n, n, nz)
     R = Lx / 10.0
     r2 = ((X - 0.5 * Lx) ** 2 + (Y - 0.5 * Ly) ** 2) / R ** 2
