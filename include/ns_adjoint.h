@@ -20,10 +20,16 @@
  *    [batch][5][nz][ny][nx] (x fastest), components (rho, rho u1, rho u2, rho u3, rho E)
  *    for states and the same order for adjoints.  Scalar fields (sigma_1, nu) are
  *    [batch][nz][ny][nx].  All must be 8-byte aligned (cudaMalloc memory is).
+ *    HOST memory appears only where a call says so: the plan (ns_plan), the energy fit
+ *    and the choice of lambda (ns_energy_efolds, ns_lambda_select, the candidate and
+ *    report arrays of ns_estimate_lambda), the snapshot arena of NS_CKPT_STRIDE_HOST
+ *    (ns_run_opts.host_arena), the parameter structs, and values a call returns.
  *  - Work is enqueued on the stream given to ns_create (or ns_set_stream) and is
  *    asynchronous unless a call says it returns a host value.
  *  - Every call returns NS_OK (0) or a negative NS_ERR_* code.  NS_ERR_ARG: null
  *    context, null required pointer, bad size, or an aliasing rule broken.
+ *    NS_ERR_BUDGET: a caller-provided buffer (arena, host arena, work buffer, plan
+ *    array) is smaller than the call needs; nothing has been enqueued.
  *    NS_ERR_CUDA: a launch or allocation failed.  Faults found on the device
  *    (non-finite values, an unstable adjoint viscosity) set a sticky error word
  *    that ns_last_error() reads back.
