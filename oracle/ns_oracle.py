@@ -10,7 +10,9 @@ an ``np.roll`` on a periodic box, written so that it can be read against the pap
 Layout: one box is ``w[5, nz, ny, nx]`` with x fastest; w = (rho, rho u1, rho u2,
 rho u3, rho E) as in Eq. (e:vector).  Direction d = 0, 1, 2 is x, y, z; it maps to
 numpy axis 3 - d.  A 2D box is nz = 1: every z difference of a periodic size-1 axis
-is exactly zero, so the 3D formulas reduce to 2D without a special case.
+is exactly zero, so the 3D formulas reduce to 2D without a special case.  Boxes are
+periodic, or (Params.bc = "inout") bounded in x by characteristic inflow and outflow
+columns of ghost cells; see the section on characteristic boundaries.
 
 Discretisation (readings of a paper whose own solver was SSP-RK3 + Roe on an
 unstructured mesh, section "Numerical methods"):
@@ -58,6 +60,10 @@ class Params:
     where |lam| < delta, delta = roe_delta times the Roe-averaged sound speed.
     plane_i: the objective plane is the x-face between cell columns plane_i-1 and
     plane_i.  pt_in: the reference stagnation pressure p_{t,in} of Eq. (e:pressure_loss).
+    bc: "periodic" (every direction), or "inout": characteristic inflow at x = 0 and
+    outflow at x = L_x (section "Numerical methods": non-reflecting inlet and outlet),
+    periodic in y and z; far: the far-field primitive state (rho, u1, u2, u3, p) the
+    characteristic conditions refer to.
     """
 
     gamma: float = 1.4
@@ -71,6 +77,8 @@ class Params:
     nu_split: tuple = (1.0, 1.0, 1.0)
     flux: str = "central"
     roe_delta: float = 0.1
+    bc: str = "periodic"
+    far: tuple = (1.0, 0.5, 0.0, 0.0, 1.0 / 1.4)
 
     @property
     def alpha(self) -> float:
@@ -259,7 +267,10 @@ def face_flux(w, d, P: Params):
 
 def residual(w, P: Params, s=None):
     """R(w) = -div(F - F^v) + s, in flux-difference form on the periodic box
-    (Eq. e:vector and the source-term equation that follows it)."""
+    (Eq. e:vector and the source-term equation that follows it); with P.bc = "inout"
+    the same on the box padded by the characteristic ghost columns."""
+    if P.bc == "inout":
+        return _inout_residual(w, P, s)
     R = np.zeros_like(w)
     for d in range(3):
         Phi = face_flux(w, d, P)
@@ -283,6 +294,8 @@ def primitives_tangent(w, wd, P: Params):
 
 def residual_tangent(w, wd, P: Params):
     """(dR/dw) wd: the linearisation of residual(w) along wd (source is w-independent)."""
+    if P.bc == "inout":
+        return _inout_tangent(w, wd, P)
     rho, u, e, p = primitives(w, P)
     rhod, ud, ed, pd = primitives_tangent(w, wd, P)
     q = np.stack([u[0], u[1], u[2], e])
@@ -322,6 +335,8 @@ def residual_transpose(w, a, P: Params):
     equation (section "Unsteady adjoint"); the paper obtained it by automatic
     differentiation ("Implementation"), here each step of residual() is reversed by
     hand, last step first."""
+    if P.bc == "inout":
+        return _inout_transpose(w, a, P)
     rho, u, e, p = primitives(w, P)
     q = np.stack([u[0], u[1], u[2], e])
     gm1 = P.gamma - 1.0
@@ -600,6 +615,102 @@ def objective_grad(w, P: Params):
 
 
 # ----------------------------------------------------------------------------------
+# characteristic inflow and outflow (section "Numerical methods": non-reflecting inlet
+# and outlet; section "Energy analysis": the incoming characteristics are set on the
+# inlet and outlet).  The boundaries are the x-faces of the box; y and z stay periodic.
+# Each boundary gets one ghost column holding the boundary state of the Riemann
+# invariants of the x direction, R+- = u1 +- 2c/(gamma-1), with the entropy p/rho^gamma
+# and the tangential velocity carried by the flow: at the outflow R+, the entropy and
+# the tangential velocity come from the adjacent cell and R- from the far field; at the
+# inflow R- comes from the adjacent cell and the rest from the far field (subsonic flow
+# along +x).  The residual is the periodic residual of the padded box, cropped: every
+# face next to a boundary, its tangential differences included, sees the ghost.  The
+# functions below work on real or complex arrays, so the ghosts' Jacobians are taken by
+# complex-step differentiation.
+# ----------------------------------------------------------------------------------
+def _periodic(P: Params):
+    return dataclasses.replace(P, bc="periodic")
+
+
+def characteristic_state(wc, P: Params, side):
+    """Ghost (boundary) state next to the cells wc[5, ...] on side "in" (x = 0) or
+    "out" (x = L_x), in conservative variables."""
+    g = P.gamma
+    k = 2.0 / (g - 1.0)
+    rho = wc[0]
+    u = wc[1:4] / rho
+    p = (g - 1.0) * (wc[4] - 0.5 * rho * (u[0] ** 2 + u[1] ** 2 + u[2] ** 2))
+    c = np.sqrt(g * p / rho)
+    rf, uf1, uf2, uf3, pf = P.far
+    cf = math.sqrt(g * pf / rf)
+    if side == "out":
+        Rp, Rm = u[0] + k * c, uf1 - k * cf
+        ent, ut2, ut3 = p / rho ** g, u[1], u[2]
+    elif side == "in":
+        Rp, Rm = uf1 + k * cf, u[0] - k * c
+        ent = pf / rf ** g + 0.0 * rho
+        ut2, ut3 = uf2 + 0.0 * rho, uf3 + 0.0 * rho
+    else:
+        raise ValueError(side)
+    ub = 0.5 * (Rp + Rm)
+    cb = 0.25 * (g - 1.0) * (Rp - Rm)
+    rhob = (cb * cb / (g * ent)) ** (1.0 / (g - 1.0))
+    pb = rhob * cb * cb / g
+    out = np.empty(wc.shape, dtype=np.result_type(wc, cb))
+    out[0] = rhob
+    out[1] = rhob * ub
+    out[2] = rhob * ut2
+    out[3] = rhob * ut3
+    out[4] = pb / (g - 1.0) + 0.5 * rhob * (ub * ub + ut2 * ut2 + ut3 * ut3)
+    return out
+
+
+def pad_x(w, P: Params):
+    """w[5, nz, ny, nx] -> [5, nz, ny, nx + 2] with the inflow ghost column first and the
+    outflow ghost column last."""
+    return np.concatenate([characteristic_state(w[..., :1], P, "in"), w,
+                           characteristic_state(w[..., -1:], P, "out")], axis=-1)
+
+
+def ghost_jacobian(wc, P: Params, side, h=1e-30):
+    """G[i, k, ...] = d ghost_i / d wc_k by complex-step differentiation (exact to
+    roundoff)."""
+    G = np.empty((5,) + wc.shape)
+    for k in range(5):
+        z = wc.astype(complex)
+        z[k] += 1j * h
+        G[:, k] = characteristic_state(z, P, side).imag / h
+    return G
+
+
+def _inout_residual(w, P: Params, s=None):
+    sp = None if s is None else np.pad(s, [(0, 0)] * 3 + [(1, 1)])
+    return residual(pad_x(w, P), _periodic(P), sp)[..., 1:-1]
+
+
+def _inout_tangent(w, wd, P: Params):
+    Gi = ghost_jacobian(w[..., :1], P, "in")
+    Go = ghost_jacobian(w[..., -1:], P, "out")
+    wdp = np.concatenate([np.einsum("ik...,k...->i...", Gi, wd[..., :1]), wd,
+                          np.einsum("ik...,k...->i...", Go, wd[..., -1:])], axis=-1)
+    return residual_tangent(pad_x(w, P), wdp, _periodic(P))[..., 1:-1]
+
+
+def _inout_transpose(w, a, P: Params):
+    """(dR/dw)^T a by the chain rule through the padding: the periodic transpose of the
+    padded box, then each ghost column's adjoint pulled back to its adjacent cells with
+    the transposed ghost Jacobian."""
+    ap = np.pad(a, [(0, 0)] * 3 + [(1, 1)])
+    bp = residual_transpose(pad_x(w, P), ap, _periodic(P))
+    out = bp[..., 1:-1].copy()
+    Gi = ghost_jacobian(w[..., :1], P, "in")
+    Go = ghost_jacobian(w[..., -1:], P, "out")
+    out[..., :1] += np.einsum("ik...,i...->k...", Gi, bp[..., :1])
+    out[..., -1:] += np.einsum("ik...,i...->k...", Go, bp[..., -1:])
+    return out
+
+
+# ----------------------------------------------------------------------------------
 # whole trajectories: primal, tangent and adjoint with every state stored
 # ----------------------------------------------------------------------------------
 def primal_run(w0, P: Params, nsteps, s=None):
@@ -647,11 +758,18 @@ def tangent_run(ws, wd0, P: Params, s=None, sd=None):
 def viscosity_apply(a, nu, P: Params):
     """L_nu a = sum_d [nu_f+ (a(c+e_d) - a(c)) - nu_f- (a(c) - a(c-e_d))] / dx_d^2 for
     every component, nu_f the two-cell mean: the discrete div(nu grad a_i) of the
-    lambda sigma_1 delta_ki delta_jl term, times the component's factor in P.nu_split."""
+    lambda sigma_1 delta_ki delta_jl term, times the component's factor in P.nu_split.
+    With P.bc = "inout" the inflow and outflow faces carry no flux."""
     out = np.zeros_like(a)
     for d in range(3):
         nup = 0.5 * (nu + _sh3(nu, d, 1))
         num = 0.5 * (nu + _sh3(nu, d, -1))
+        if d == 0 and P.bc == "inout":
+            # no flux through the inflow and outflow faces (zero normal derivative)
+            nup = nup.copy()
+            num = num.copy()
+            nup[..., -1] = 0.0
+            num[..., 0] = 0.0
         out += (nup * (_sh3(a, d, 1) - a) - num * (a - _sh3(a, d, -1))) / P.dx[d] ** 2
     f_rho, f_mom, f_en = P.nu_split
     out[0] *= f_rho
@@ -777,7 +895,10 @@ def _central(f, d, P):
 
 def growth_matrix_field(w, P: Params):
     """Per-cell growth matrix M from central-difference gradients of rho, u_i, p, a, b
-    (closed form, section "Energy analysis").  Shape (nz, ny, nx, 5, 5)."""
+    (closed form, section "Energy analysis").  Shape (nz, ny, nx, 5, 5).  With
+    P.bc = "inout" the x differences at the boundary columns use the ghost states."""
+    if P.bc == "inout":
+        return growth_matrix_field(pad_x(w, P), _periodic(P))[:, :, 1:-1]
     g = P.gamma
     rho, u, e, p = primitives(w, P)
     c = np.sqrt(g * p / rho)

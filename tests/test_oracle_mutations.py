@@ -10,6 +10,7 @@ import pytest
 from oracle import mlp_oracle as ML
 from oracle import ns_oracle as O
 from tests import test_oracle_adjoint as TA
+from tests import test_oracle_bc as TB
 from tests import test_oracle_lambda as TL
 from tests import test_oracle_mlp as TM
 from tests import test_oracle_primal as TP
@@ -286,3 +287,26 @@ def test_energy_pin_catches(monkeypatch, variant):
     monkeypatch.setattr(O, "adjoint_energy", E)
     assert (_fails(TS.test_adjoint_energy_is_the_integral_of_vhat_squared, (12, 5, 3)) or
             _fails(TS.test_adjoint_energy_is_the_integral_of_vhat_squared, (7, 4, 1)))
+
+
+# ---- characteristic inflow and outflow ----------------------------------------------
+
+def test_boundary_pins_catch_the_sides_exchanged(monkeypatch):
+    true_state = O.characteristic_state
+    pin = TB.test_boundary_states_carry_the_right_invariants
+    assert not _fails(pin)
+    monkeypatch.setattr(O, "characteristic_state",
+                        lambda wc, P, side: true_state(wc, P, "in" if side == "out" else "out"))
+    assert _fails(pin)
+
+
+def test_boundary_transpose_pin_catches_a_missing_ghost_pullback(monkeypatch):
+    import dataclasses
+
+    def transpose(w, a, P):
+        ap = np.pad(a, [(0, 0)] * 3 + [(1, 1)])
+        return O.residual_transpose(O.pad_x(w, P), ap, dataclasses.replace(P, bc="periodic"))[..., 1:-1]
+
+    assert not _fails(TB.test_tangent_and_transpose_equal_fd_jacobian, "central")
+    monkeypatch.setattr(O, "_inout_transpose", transpose)
+    assert _fails(TB.test_tangent_and_transpose_equal_fd_jacobian, "central")
