@@ -29,7 +29,8 @@
  *  - Every call returns NS_OK (0) or a negative NS_ERR_* code.  NS_ERR_ARG: null
  *    context, null required pointer, bad size, or an aliasing rule broken.
  *    NS_ERR_BUDGET: a caller-provided buffer (arena, host arena, work buffer, plan
- *    array) is smaller than the call needs; nothing has been enqueued.
+ *    array) is smaller than the call needs; these size checks run before the call
+ *    enqueues any work.
  *    NS_ERR_CUDA: a launch or allocation failed.  Faults found on the device
  *    (non-finite values, an unstable adjoint viscosity) set a sticky error word
  *    that ns_last_error() reads back.
