@@ -14,6 +14,8 @@ from tests import test_oracle_bc as TB
 from tests import test_oracle_lambda as TL
 from tests import test_oracle_mlp as TM
 from tests import test_oracle_primal as TP
+from tests import test_oracle_rk3 as TR
+from tests import test_oracle_roe as TRoe
 from tests import test_oracle_sigma as TS
 
 
@@ -310,3 +312,50 @@ def test_boundary_transpose_pin_catches_a_missing_ghost_pullback(monkeypatch):
     assert not _fails(TB.test_tangent_and_transpose_equal_fd_jacobian, "central")
     monkeypatch.setattr(O, "_inout_transpose", transpose)
     assert _fails(TB.test_tangent_and_transpose_equal_fd_jacobian, "central")
+
+
+# ---- the paper's own scheme: SSP-RK3 adjoint and the Roe entropy fix ----------------
+def _ssprk3_adjoint(variant):
+    def f(w, lam, P, s=None, nu=None):
+        dt = P.dt
+        _, (W1, W2, W3) = O.ssprk3_step(w, P, s)
+
+        def JT(W, ab):
+            g = O.residual_transpose(W, ab, P)
+            if nu is not None:
+                g = g + O.viscosity_apply(ab, nu, P)
+            return g
+
+        wbar = lam / 3.0
+        r3 = 2.0 / 3.0 * dt * lam
+        W3bar = 2.0 / 3.0 * lam + JT(W3, r3)
+        wbar = wbar + (0.25 if variant == "convex_weights_swapped" else 0.75) * W3bar
+        r2 = (0.75 if variant == "convex_weights_swapped" else 0.25) * dt * W3bar
+        W2bar = 0.25 * W3bar + JT(W2, r2)
+        wbar = wbar + W2bar
+        r1 = dt * W2bar
+        wbar = wbar + JT(W2 if variant == "first_stage_at_W2" else W1, r1)
+        return wbar, r1 + r2 + (0.0 if variant == "seed_without_r3" else r3)
+    return f
+
+
+@pytest.mark.parametrize("variant", ["convex_weights_swapped", "first_stage_at_W2", "seed_without_r3"])
+def test_ssprk3_adjoint_pins_catch(monkeypatch, variant):
+    pins = [(TR.test_adjoint_step_dot_product, (False,)), (TR.test_trajectory_dot_product_with_source, ())]
+    monkeypatch.setattr(O, "ssprk3_adjoint_step", _ssprk3_adjoint("none"))
+    assert not any(_fails(p, *a) for p, a in pins)
+    monkeypatch.setattr(O, "ssprk3_adjoint_step", _ssprk3_adjoint(variant))
+    assert any(_fails(p, *a) for p, a in pins)
+
+
+def test_entropy_fix_pin_catches_a_kink(monkeypatch):
+    def fix(lam, delta, signed):
+        if signed:
+            return lam
+        re = np.real(lam)
+        mag = np.where(re >= 0, lam, -lam)
+        # a value-continuous but kinked blend: delta at |lam| = 0 rising linearly to |lam|
+        return np.where(np.abs(re) < np.real(delta), 0.5 * (delta + mag), mag)
+    assert not _fails(TRoe.test_entropy_fix_is_c1_at_delta)
+    monkeypatch.setattr(O, "_abs_fix", fix)
+    assert _fails(TRoe.test_entropy_fix_is_c1_at_delta)
