@@ -60,10 +60,13 @@ class Params:
     where |lam| < delta, delta = roe_delta times the Roe-averaged sound speed.
     plane_i: the objective plane is the x-face between cell columns plane_i-1 and
     plane_i.  pt_in: the reference stagnation pressure p_{t,in} of Eq. (e:pressure_loss).
-    bc: "periodic" (every direction), or "inout": characteristic inflow at x = 0 and
-    outflow at x = L_x (section "Numerical methods": non-reflecting inlet and outlet),
-    periodic in y and z; far: the far-field primitive state (rho, u1, u2, u3, p) the
-    characteristic conditions refer to.
+    bc: "periodic" (every direction); "inout": characteristic inflow at x = 0 and
+    outflow at x = L_x (section "Numerical methods": non-reflecting inlet and outlet);
+    "walls": isothermal no-slip walls at y = 0 and y = L_y (the vane surface is
+    isothermal, section "Problem setup"); "inout_walls": both.  The other
+    directions stay periodic.  far: the far-field primitive state (rho, u1, u2, u3, p)
+    the characteristic conditions refer to.  wall_e: the internal energy e = c_v T of
+    the bottom and the top wall.
     """
 
     gamma: float = 1.4
@@ -79,6 +82,7 @@ class Params:
     roe_delta: float = 0.1
     bc: str = "periodic"
     far: tuple = (1.0, 0.5, 0.0, 0.0, 1.0 / 1.4)
+    wall_e: tuple = (1.0 / 0.56, 1.0 / 0.56)
 
     @property
     def alpha(self) -> float:
@@ -269,8 +273,8 @@ def residual(w, P: Params, s=None):
     """R(w) = -div(F - F^v) + s, in flux-difference form on the periodic box
     (Eq. e:vector and the source-term equation that follows it); with P.bc = "inout"
     the same on the box padded by the characteristic ghost columns."""
-    if P.bc == "inout":
-        return _inout_residual(w, P, s)
+    if P.bc != "periodic":
+        return _bounded_residual(w, P, s)
     R = np.zeros_like(w)
     for d in range(3):
         Phi = face_flux(w, d, P)
@@ -294,8 +298,8 @@ def primitives_tangent(w, wd, P: Params):
 
 def residual_tangent(w, wd, P: Params):
     """(dR/dw) wd: the linearisation of residual(w) along wd (source is w-independent)."""
-    if P.bc == "inout":
-        return _inout_tangent(w, wd, P)
+    if P.bc != "periodic":
+        return _bounded_tangent(w, wd, P)
     rho, u, e, p = primitives(w, P)
     rhod, ud, ed, pd = primitives_tangent(w, wd, P)
     q = np.stack([u[0], u[1], u[2], e])
@@ -335,8 +339,8 @@ def residual_transpose(w, a, P: Params):
     equation (section "Unsteady adjoint"); the paper obtained it by automatic
     differentiation ("Implementation"), here each step of residual() is reversed by
     hand, last step first."""
-    if P.bc == "inout":
-        return _inout_transpose(w, a, P)
+    if P.bc != "periodic":
+        return _bounded_transpose(w, a, P)
     rho, u, e, p = primitives(w, P)
     q = np.stack([u[0], u[1], u[2], e])
     gm1 = P.gamma - 1.0
@@ -617,7 +621,8 @@ def objective_grad(w, P: Params):
 # ----------------------------------------------------------------------------------
 # characteristic inflow and outflow (section "Numerical methods": non-reflecting inlet
 # and outlet; section "Energy analysis": the incoming characteristics are set on the
-# inlet and outlet).  The boundaries are the x-faces of the box; y and z stay periodic.
+# inlet and outlet), and isothermal no-slip walls (the vane surface is isothermal).
+# Inflow and outflow are the x-faces of the box, walls the y-faces; z stays periodic.
 # Each boundary gets one ghost column holding the boundary state of the Riemann
 # invariants of the x direction, R+- = u1 +- 2c/(gamma-1), with the entropy p/rho^gamma
 # and the tangential velocity carried by the flow: at the outflow R+, the entropy and
@@ -665,6 +670,32 @@ def characteristic_state(wc, P: Params, side):
     return out
 
 
+def wall_state(wc, P: Params, side):
+    """Ghost state of an isothermal no-slip wall next to the cells wc[5, ...] on side
+    "bottom" (y = 0) or "top" (y = L_y): the same density, the velocity reversed (the
+    face velocity is zero) and e_g = 2 e_w - e (the face internal energy, so the face
+    temperature, is the wall's), e_w = P.wall_e[0] or [1].  The mean of cell and ghost
+    carries no mass through the wall."""
+    ew = P.wall_e[0] if side == "bottom" else P.wall_e[1]
+    rho = wc[0]
+    u = wc[1:4] / rho
+    e = wc[4] / rho - 0.5 * (u[0] ** 2 + u[1] ** 2 + u[2] ** 2)
+    eg = 2.0 * ew - e
+    out = np.empty(wc.shape, dtype=wc.dtype)
+    out[0] = rho
+    out[1:4] = -wc[1:4]
+    out[4] = rho * (eg + 0.5 * (u[0] ** 2 + u[1] ** 2 + u[2] ** 2))
+    return out
+
+
+def _x_bounded(P: Params):
+    return P.bc in ("inout", "inout_walls")
+
+
+def _y_walls(P: Params):
+    return P.bc in ("walls", "inout_walls")
+
+
 def pad_x(w, P: Params):
     """w[5, nz, ny, nx] -> [5, nz, ny, nx + 2] with the inflow ghost column first and the
     outflow ghost column last."""
@@ -672,42 +703,101 @@ def pad_x(w, P: Params):
                            characteristic_state(w[..., -1:], P, "out")], axis=-1)
 
 
-def ghost_jacobian(wc, P: Params, side, h=1e-30):
-    """G[i, k, ...] = d ghost_i / d wc_k by complex-step differentiation (exact to
-    roundoff)."""
-    G = np.empty((5,) + wc.shape)
+def pad_y(w, P: Params):
+    """w[5, nz, ny, n] -> [5, nz, ny + 2, n] with the bottom wall's ghost row first and
+    the top wall's last."""
+    return np.concatenate([wall_state(w[..., :1, :], P, "bottom"), w,
+                           wall_state(w[..., -1:, :], P, "top")], axis=-2)
+
+
+def pad(w, P: Params):
+    """The box with its ghost layers: x columns first, then y rows over them (so the
+    corner ghosts are the walls' ghosts of the inflow and outflow ghosts)."""
+    if _x_bounded(P):
+        w = pad_x(w, P)
+    if _y_walls(P):
+        w = pad_y(w, P)
+    return w
+
+
+def _crop_cells(P: Params):
+    """Index of the interior cells in a padded scalar field [nz, ny', nx']."""
+    return (slice(None), slice(1, -1) if _y_walls(P) else slice(None),
+            slice(1, -1) if _x_bounded(P) else slice(None))
+
+
+def _crop(P: Params):
+    return (slice(None),) + _crop_cells(P)
+
+
+def _zero_pad(f, P: Params):
+    width = [(0, 0)] * (f.ndim - 2) + [(1, 1) if _y_walls(P) else (0, 0), (1, 1) if _x_bounded(P) else (0, 0)]
+    return np.pad(f, width)
+
+
+def _cs_jacobian(fn, wc, h=1e-30):
+    """J[i, k, ...] = d fn(wc)_i / d wc_k for a cell-local map, by complex-step
+    differentiation (exact to roundoff)."""
+    J = np.empty((5,) + wc.shape)
     for k in range(5):
         z = wc.astype(complex)
         z[k] += 1j * h
-        G[:, k] = characteristic_state(z, P, side).imag / h
-    return G
+        J[:, k] = fn(z).imag / h
+    return J
 
 
-def _inout_residual(w, P: Params, s=None):
-    sp = None if s is None else np.pad(s, [(0, 0)] * 3 + [(1, 1)])
-    return residual(pad_x(w, P), _periodic(P), sp)[..., 1:-1]
+def ghost_jacobian(wc, P: Params, side, h=1e-30):
+    """G[i, k, ...] = d ghost_i / d wc_k of a characteristic ("in", "out") or wall
+    ("bottom", "top") ghost, by complex-step differentiation."""
+    state = characteristic_state if side in ("in", "out") else wall_state
+    return _cs_jacobian(lambda z: state(z, P, side), wc, h)
 
 
-def _inout_tangent(w, wd, P: Params):
-    Gi = ghost_jacobian(w[..., :1], P, "in")
-    Go = ghost_jacobian(w[..., -1:], P, "out")
-    wdp = np.concatenate([np.einsum("ik...,k...->i...", Gi, wd[..., :1]), wd,
-                          np.einsum("ik...,k...->i...", Go, wd[..., -1:])], axis=-1)
-    return residual_tangent(pad_x(w, P), wdp, _periodic(P))[..., 1:-1]
+def _bounded_residual(w, P: Params, s=None):
+    sp = None if s is None else _zero_pad(s, P)
+    return residual(pad(w, P), _periodic(P), sp)[_crop(P)]
 
 
-def _inout_transpose(w, a, P: Params):
+def _bounded_tangent(w, wd, P: Params):
+    """(dR/dw) wd: the periodic tangent of the padded box along the padded direction
+    (each ghost's Jacobian applied to the direction at its adjacent cells)."""
+    if _x_bounded(P):
+        Gi = ghost_jacobian(w[..., :1], P, "in")
+        Go = ghost_jacobian(w[..., -1:], P, "out")
+        wd = np.concatenate([np.einsum("ik...,k...->i...", Gi, wd[..., :1]), wd,
+                             np.einsum("ik...,k...->i...", Go, wd[..., -1:])], axis=-1)
+        w = pad_x(w, P)
+    if _y_walls(P):
+        Gb = ghost_jacobian(w[..., :1, :], P, "bottom")
+        Gt = ghost_jacobian(w[..., -1:, :], P, "top")
+        wd = np.concatenate([np.einsum("ik...,k...->i...", Gb, wd[..., :1, :]), wd,
+                             np.einsum("ik...,k...->i...", Gt, wd[..., -1:, :])], axis=-2)
+        w = pad_y(w, P)
+    return residual_tangent(w, wd, _periodic(P))[_crop(P)]
+
+
+def _bounded_transpose(w, a, P: Params):
     """(dR/dw)^T a by the chain rule through the padding: the periodic transpose of the
-    padded box, then each ghost column's adjoint pulled back to its adjacent cells with
-    the transposed ghost Jacobian."""
-    ap = np.pad(a, [(0, 0)] * 3 + [(1, 1)])
-    bp = residual_transpose(pad_x(w, P), ap, _periodic(P))
-    out = bp[..., 1:-1].copy()
-    Gi = ghost_jacobian(w[..., :1], P, "in")
-    Go = ghost_jacobian(w[..., -1:], P, "out")
-    out[..., :1] += np.einsum("ik...,i...->k...", Gi, bp[..., :1])
-    out[..., -1:] += np.einsum("ik...,i...->k...", Go, bp[..., -1:])
-    return out
+    padded box, then the wall rows' adjoints pulled back to their adjacent rows, then
+    the inflow and outflow columns' to theirs, each with the transposed ghost Jacobian
+    (the reverse of the order the padding was built in)."""
+    wx = pad_x(w, P) if _x_bounded(P) else w
+    b = residual_transpose(pad(w, P), _zero_pad(a, P), _periodic(P))
+    if _y_walls(P):
+        Gb = ghost_jacobian(wx[..., :1, :], P, "bottom")
+        Gt = ghost_jacobian(wx[..., -1:, :], P, "top")
+        out = b[..., 1:-1, :].copy()
+        out[..., :1, :] += np.einsum("ik...,i...->k...", Gb, b[..., :1, :])
+        out[..., -1:, :] += np.einsum("ik...,i...->k...", Gt, b[..., -1:, :])
+        b = out
+    if _x_bounded(P):
+        Gi = ghost_jacobian(w[..., :1], P, "in")
+        Go = ghost_jacobian(w[..., -1:], P, "out")
+        out = b[..., 1:-1].copy()
+        out[..., :1] += np.einsum("ik...,i...->k...", Gi, b[..., :1])
+        out[..., -1:] += np.einsum("ik...,i...->k...", Go, b[..., -1:])
+        b = out
+    return b
 
 
 # ----------------------------------------------------------------------------------
@@ -759,17 +849,20 @@ def viscosity_apply(a, nu, P: Params):
     """L_nu a = sum_d [nu_f+ (a(c+e_d) - a(c)) - nu_f- (a(c) - a(c-e_d))] / dx_d^2 for
     every component, nu_f the two-cell mean: the discrete div(nu grad a_i) of the
     lambda sigma_1 delta_ki delta_jl term, times the component's factor in P.nu_split.
-    With P.bc = "inout" the inflow and outflow faces carry no flux."""
+    On a bounded box the boundary faces (inflow, outflow, walls) carry no flux."""
     out = np.zeros_like(a)
     for d in range(3):
         nup = 0.5 * (nu + _sh3(nu, d, 1))
         num = 0.5 * (nu + _sh3(nu, d, -1))
-        if d == 0 and P.bc == "inout":
-            # no flux through the inflow and outflow faces (zero normal derivative)
-            nup = nup.copy()
-            num = num.copy()
+        if (d == 0 and _x_bounded(P)) or (d == 1 and _y_walls(P)):
+            # no flux through the boundary faces (zero normal derivative)
+            ax = 2 - d
+            nup = np.moveaxis(nup.copy(), ax, -1)
+            num = np.moveaxis(num.copy(), ax, -1)
             nup[..., -1] = 0.0
             num[..., 0] = 0.0
+            nup = np.moveaxis(nup, -1, ax)
+            num = np.moveaxis(num, -1, ax)
         out += (nup * (_sh3(a, d, 1) - a) - num * (a - _sh3(a, d, -1))) / P.dx[d] ** 2
     f_rho, f_mom, f_en = P.nu_split
     out[0] *= f_rho
@@ -895,10 +988,10 @@ def _central(f, d, P):
 
 def growth_matrix_field(w, P: Params):
     """Per-cell growth matrix M from central-difference gradients of rho, u_i, p, a, b
-    (closed form, section "Energy analysis").  Shape (nz, ny, nx, 5, 5).  With
-    P.bc = "inout" the x differences at the boundary columns use the ghost states."""
-    if P.bc == "inout":
-        return growth_matrix_field(pad_x(w, P), _periodic(P))[:, :, 1:-1]
+    (closed form, section "Energy analysis").  Shape (nz, ny, nx, 5, 5).  On a bounded
+    box the differences at the boundary cells use the ghost states."""
+    if P.bc != "periodic":
+        return growth_matrix_field(pad(w, P), _periodic(P))[_crop_cells(P)]
     g = P.gamma
     rho, u, e, p = primitives(w, P)
     c = np.sqrt(g * p / rho)

@@ -1,6 +1,7 @@
-"""Pins of the oracle's characteristic inflow and outflow boundaries (section "Numerical
+"""Pins of the oracle's bounded boxes: characteristic inflow and outflow (section "Numerical
 methods": non-reflecting inlet and outlet; section "Energy analysis": the incoming
-characteristics are set there).  No GPU."""
+characteristics are set there) and isothermal no-slip walls (section "Problem setup": the
+vane surface is isothermal).  No GPU."""
 import dataclasses
 import math
 
@@ -193,3 +194,124 @@ def test_sigma1_sees_the_ghosts():
     s_p = O.sigma1_field(w, dataclasses.replace(P, bc="periodic"))
     np.testing.assert_allclose(s_b[..., 1:-1], s_p[..., 1:-1], rtol=1e-13)
     assert np.abs(s_b[..., [0, -1]] - s_p[..., [0, -1]]).max() > 1e-6
+
+
+# ---- isothermal no-slip walls at y = 0 and y = L_y ------------------------------------
+def _wall_params(nx, ny, nz, bc="walls", mu=0.02, e_w=(1.0 / 0.56, 1.0 / 0.56), **kw):
+    return O.Params(gamma=G, mu=mu, dx=synth.box_shape(nx, ny, nz), dt=2e-3, bc=bc, wall_e=e_w,
+                    far=kw.get("far", (1.0, 0.0, 0.0, 0.0, 1.0 / G)), plane_i=(3 * nx) // 4, pt_in=1.0)
+
+
+@pytest.mark.parametrize("bc", ["walls", "inout_walls"])
+def test_rest_at_the_wall_temperature_is_steady(bc):
+    nx, ny, nz = 7, 6, 3
+    rho = np.full((nz, ny, nx), 1.0)
+    w = synth._conservative(rho, np.zeros((3,) + rho.shape), rho / G, G)
+    P = _wall_params(nx, ny, nz, bc=bc, e_w=(1.0 / 0.56, 1.0 / 0.56))
+    assert np.abs(O.residual(w, P)).max() <= 1e-13
+
+
+def test_walls_pass_no_mass():
+    """x and z periodic, walls in y: the mass residual sums to zero for any state."""
+    nx, ny, nz = 6, 5, 4
+    w = synth.perturbed_uniform(nx, ny, nz, seed=8, amp=0.1)
+    P = _wall_params(nx, ny, nz, e_w=(1.5, 2.1))
+    R = O.residual(w, P)
+    assert abs(R[0].sum()) <= 1e-13 * np.abs(R[0]).sum()
+    assert abs(R[4].sum()) > 1e-3 * np.abs(R[4]).sum()    # the walls exchange heat
+
+
+def test_wall_heat_flux_and_pressure_closed_forms():
+    """Rest, uniform rho and e with e != e_w: the wall face's heat flux is
+    alpha (e - e_w) / (dy/2), so the wall row's energy residual is
+    2 alpha (e_w - e) / dy^2; its y-momentum residual is the jump to the wall face's
+    pressure, -(gamma-1) rho (e - e_w) / dy (bottom wall, outward normal -y)."""
+    nx, ny, nz = 4, 6, 1
+    rho0, e0, ew = 1.1, 1.8, 2.3
+    rho = np.full((nz, ny, nx), rho0)
+    w = synth._conservative(rho, np.zeros((3,) + rho.shape), (G - 1) * rho * e0, G)
+    P = _wall_params(nx, ny, nz, e_w=(ew, e0))
+    dy = P.dx[1]
+    R = O.residual(w, P)
+    np.testing.assert_allclose(R[4][:, 0], 2 * P.alpha * (ew - e0) / dy ** 2, rtol=1e-12)
+    np.testing.assert_allclose(R[2][:, 0], -(G - 1) * rho0 * (e0 - ew) / dy, rtol=1e-12)
+    np.testing.assert_allclose(R[:, :, 1:], 0.0, atol=1e-12)    # top wall at e0, interior at rest
+
+
+def test_wall_drag_on_a_uniform_stream():
+    """A uniform stream u1 = U at the wall temperature: the no-slip wall's shear stress
+    mu (U - (-U)) / dy drags the wall rows, R_u1 = -2 mu U / dy^2 on both; the walls
+    do no work (the face velocity is zero) and pass no heat."""
+    nx, ny, nz = 5, 4, 2
+    U = 0.3
+    rho = np.ones((nz, ny, nx))
+    u = np.stack([U * rho, 0 * rho, 0 * rho])
+    w = synth._conservative(rho, u, rho / G, G)
+    P = _wall_params(nx, ny, nz, e_w=(1.0 / 0.56, 1.0 / 0.56))
+    dy = P.dx[1]
+    R = O.residual(w, P)
+    for row in (0, -1):
+        np.testing.assert_allclose(R[1][:, row], -2 * P.mu * U / dy ** 2, rtol=1e-12)
+        np.testing.assert_allclose(R[4][:, row], 0.0, atol=1e-12)
+    np.testing.assert_allclose(R[:, :, 1:-1], 0.0, atol=1e-12)
+    np.testing.assert_allclose(R[0], 0.0, atol=1e-12)
+
+
+@pytest.mark.parametrize("bc", ["walls", "inout_walls"])
+def test_wall_tangent_and_transpose_equal_fd_jacobian(bc):
+    nx, ny, nz = 4, 4, 2
+    w = synth.perturbed_uniform(nx, ny, nz, seed=13, amp=0.08)
+    P = _wall_params(nx, ny, nz, bc=bc, mu=0.05, e_w=(1.6, 2.0), far=(1.0, 0.5, 0.0, 0.0, 1.0 / G))
+    n = w.size
+    J = np.empty((n, n))
+    h = 1e-6
+    for j in range(n):
+        e = np.zeros(n)
+        e[j] = h
+        e = e.reshape(w.shape)
+        J[:, j] = ((O.residual(w + e, P) - O.residual(w - e, P)) / (2 * h)).ravel()
+    v = synth.random_field(w.shape, 1)
+    a = synth.random_field(w.shape, 2)
+    scale = np.max(np.abs(J)) * 10
+    np.testing.assert_allclose(O.residual_tangent(w, v, P).ravel(), J @ v.ravel(), atol=2e-7 * scale, rtol=0)
+    np.testing.assert_allclose(O.residual_transpose(w, a, P).ravel(), J.T @ a.ravel(), atol=2e-7 * scale, rtol=0)
+
+
+def test_channel_trajectory_gradient():
+    """Inflow, outflow and walls together: the adjoint of a sourced trajectory against
+    central finite differences of Jbar (eps = 1e-6)."""
+    nx, ny, nz = 12, 6, 1
+    w0 = synth.isentropic_vortex(nx, ny, nz, noise=1e-3, seed=6)
+    P = _wall_params(nx, ny, nz, bc="inout_walls", mu=0.01, e_w=(1.7, 1.9),
+                     far=(1.0, 0.5, 0.0, 0.0, 1.0 / G))
+    P.dt = 4e-3
+    s = np.zeros_like(w0)
+    s[1] = 0.05 * synth.forcing_bumps(nx, ny, nz, n=4)[1]
+    N = 5
+    ws, _ = O.primal_run(w0, P, N, s)
+    lam0, sbar = O.adjoint_run(ws, P, s)
+    eps = 1e-6
+    dw = synth.random_field(w0.shape, 14)
+    fd = (O.primal_run(w0 + eps * dw, P, N, s)[1] - O.primal_run(w0 - eps * dw, P, N, s)[1]) / (2 * eps)
+    assert abs(fd - O.dot(lam0, dw)) <= 1e-6 * abs(fd)
+    ds = np.zeros_like(w0)
+    ds[1] = synth.forcing_bumps(nx, ny, nz, n=4)[3]
+    fd = (O.primal_run(w0, P, N, s + eps * ds)[1] - O.primal_run(w0, P, N, s - eps * ds)[1]) / (2 * eps)
+    assert abs(fd - O.dot(sbar, ds)) <= 1e-6 * abs(fd)
+
+
+def test_adjoint_viscosity_with_closed_walls():
+    nx, ny, nz = 6, 7, 3
+    P = _wall_params(nx, ny, nz, bc="inout_walls")
+    rng = np.random.default_rng(4)
+    nu = 0.1 + rng.random((nz, ny, nx))
+    a = rng.standard_normal((5, nz, ny, nx))
+    b = rng.standard_normal((5, nz, ny, nx))
+    La, Lb = O.viscosity_apply(a, nu, P), O.viscosity_apply(b, nu, P)
+    assert abs(O.dot(a, Lb) - O.dot(La, b)) <= 1e-12 * abs(O.dot(a, Lb))
+    assert O.dot(a, La) < 0.0
+    # a field that varies only along z feels neither walls nor inflow and outflow
+    c = np.broadcast_to(rng.standard_normal((5, nz, 1, 1)), a.shape).copy()
+    np.testing.assert_allclose(O.viscosity_apply(c, np.ones_like(nu), P),
+                               O.viscosity_apply(c, np.ones_like(nu), dataclasses.replace(P, bc="periodic")),
+                               rtol=1e-13, atol=1e-13)

@@ -310,7 +310,7 @@ def test_boundary_transpose_pin_catches_a_missing_ghost_pullback(monkeypatch):
         return O.residual_transpose(O.pad_x(w, P), ap, dataclasses.replace(P, bc="periodic"))[..., 1:-1]
 
     assert not _fails(TB.test_tangent_and_transpose_equal_fd_jacobian, "central")
-    monkeypatch.setattr(O, "_inout_transpose", transpose)
+    monkeypatch.setattr(O, "_bounded_transpose", transpose)
     assert _fails(TB.test_tangent_and_transpose_equal_fd_jacobian, "central")
 
 
@@ -359,3 +359,27 @@ def test_entropy_fix_pin_catches_a_kink(monkeypatch):
     assert not _fails(TRoe.test_entropy_fix_is_c1_at_delta)
     monkeypatch.setattr(O, "_abs_fix", fix)
     assert _fails(TRoe.test_entropy_fix_is_c1_at_delta)
+
+
+def _wall(variant):
+    def f(wc, P, side):
+        ew = P.wall_e[0] if side == "bottom" else P.wall_e[1]
+        rho = wc[0]
+        u = wc[1:4] / rho
+        e = wc[4] / rho - 0.5 * (u[0] ** 2 + u[1] ** 2 + u[2] ** 2)
+        eg = ew if variant == "ghost_at_wall_energy" else 2.0 * ew - e
+        out = np.empty(wc.shape, dtype=wc.dtype)
+        out[0] = rho
+        out[1:4] = wc[1:4] if variant == "slip_velocity" else -wc[1:4]
+        out[4] = rho * (eg + 0.5 * (u[0] ** 2 + u[1] ** 2 + u[2] ** 2))
+        return out
+    return f
+
+
+@pytest.mark.parametrize("variant", ["slip_velocity", "ghost_at_wall_energy"])
+def test_wall_pins_catch(monkeypatch, variant):
+    pins = [TB.test_wall_heat_flux_and_pressure_closed_forms, TB.test_wall_drag_on_a_uniform_stream]
+    monkeypatch.setattr(O, "wall_state", _wall("none"))
+    assert not any(_fails(p) for p in pins)
+    monkeypatch.setattr(O, "wall_state", _wall(variant))
+    assert any(_fails(p) for p in pins)
