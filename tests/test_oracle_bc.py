@@ -257,11 +257,12 @@ def test_wall_drag_on_a_uniform_stream():
     np.testing.assert_allclose(R[0], 0.0, atol=1e-12)
 
 
-@pytest.mark.parametrize("bc", ["walls", "inout_walls"])
-def test_wall_tangent_and_transpose_equal_fd_jacobian(bc):
+@pytest.mark.parametrize("bc,flux", [("walls", "central"), ("inout_walls", "central"), ("inout_walls", "roe")])
+def test_wall_tangent_and_transpose_equal_fd_jacobian(bc, flux):
     nx, ny, nz = 4, 4, 2
     w = synth.perturbed_uniform(nx, ny, nz, seed=13, amp=0.08)
     P = _wall_params(nx, ny, nz, bc=bc, mu=0.05, e_w=(1.6, 2.0), far=(1.0, 0.5, 0.0, 0.0, 1.0 / G))
+    P.flux = flux
     n = w.size
     J = np.empty((n, n))
     h = 1e-6
