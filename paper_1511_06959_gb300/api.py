@@ -204,6 +204,17 @@ def _ptr(t, dtype=None):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _host_ptr(t):
+    """Address of a contiguous CPU tensor (host memory for the library), or None."""
+    if t is None:
+        return None
+    if t.is_cuda:
+        raise ValueError("expected a CPU tensor (host memory)")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
 def _check(code: int, where: str):
     if code != NS_OK:
         raise NsError(code, where)
@@ -344,7 +355,7 @@ class Solver:
         NS_CKPT_STRIDE_HOST sweep.  The options keep a reference to it."""
         o = NsRunOpts(nsteps, schedule, param, lam_coef, tau, int(record_energy), int(record_sigma),
                       None if mlp is None else ctypes.c_void_p(mlp.data_ptr()),
-                      None if host_arena is None else ctypes.c_void_p(host_arena.data_ptr()),
+                      _host_ptr(host_arena),
                       0 if host_arena is None else host_arena.numel() * host_arena.element_size())
         o._host_arena = host_arena
         return o

@@ -66,3 +66,15 @@ def test_create_rejects_bad_params_without_gpu():
     assert lib.ns_create(ctypes.byref(p), None, ctypes.byref(ctx)) == api.NS_ERR_ARG
     assert lib.ns_primal_step(None, None, None, None) == api.NS_ERR_ARG
     assert lib.ns_last_error(None) == api.NS_ERR_ARG
+
+
+def test_host_arena_must_be_contiguous_host_memory():
+    """The snapshot arena of a host-tier sweep is host memory: the binding refuses a
+    non-contiguous tensor before any call (a CUDA tensor is refused the same way)."""
+    torch = pytest.importorskip("torch")
+    from paper_1511_06959_gb300 import api
+    assert api._host_ptr(None) is None
+    t = torch.empty(64, dtype=torch.uint8)
+    assert api._host_ptr(t).value == t.data_ptr()
+    with pytest.raises(ValueError):
+        api._host_ptr(torch.empty((8, 8), dtype=torch.uint8).t())
