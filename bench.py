@@ -34,9 +34,17 @@ from paper_1511_06959_gb300 import config as C  # noqa: E402
 METRIC = "adjoint cell-steps/s and % HBM roofline, mixed+checkpointed vs FP64 at stated grad err"
 UNIT = "adjoint cell-steps/s"
 
-# algorithmic bytes per cell of one adjoint-stage launch, averaged over the four stages
-# (inputs read once, outputs written once; nu field present, no source seed)
-ADJ_STAGE_BYTES = {"mixed": (124 + 184 + 184 + 144) / 4.0, "fp64": (164 + 244 + 244 + 164) / 4.0}
+# Algorithmic bytes per adjoint cell-step, the minimum the method must move: read w^n,
+# read lam^{n+1}, write lam^n, 5 FP64 values each (120 B, the same in mixed precision,
+# whose state and adjoint stay FP64).  One adjoint-stage launch does 1/stages of a step.
+# The checkpointed sweep adds the replay's read and write of the state: about 200 B per
+# adjoint cell-step in all.
+ADJ_STEP_BYTES = 120.0
+SWEEP_BYTES = 200.0
+# operand bytes per cell that the adjoint-stage kernel itself reads and writes, averaged
+# over the four RK4 stages (float mirrors, kept stage states, seeds and sums in mixed
+# precision; nu present, no source seed): a design figure, not the algorithmic minimum
+ADJ_STAGE_OPERAND_BYTES = {"mixed": (124 + 184 + 184 + 144) / 4.0, "fp64": (164 + 244 + 244 + 164) / 4.0}
 
 
 def parse():
@@ -329,11 +337,16 @@ def run_ours(args, wl):
     out = None
     if rank == 0:
         kavg = kms / max(klaunch, 1)
-        bytes_launch = ADJ_STAGE_BYTES[args.precision] * wl.cells * wl.batch
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
-            os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+        stages = 3 if args.scheme == "ssprk3" else 4
+        ncell = wl.cells * wl.batch
+        bytes_launch = ADJ_STEP_BYTES / stages * ncell
+        operand_bytes = ADJ_STAGE_OPERAND_BYTES[args.precision] * ncell
+        peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+        peaks = json.load(open(peaks_path)) if os.path.exists(peaks_path) else {}
         hbm = peaks.get("hbm_gbs", 6800.0)
+        hbm_src = "MEASURED_PEAKS.json hbm_gbs (measured)" if "hbm_gbs" in peaks else "fallback 6800 GB/s"
         achieved = bytes_launch / (kavg * 1e-3) / 1e9
+        sweep_gbs = SWEEP_BYTES * cell_steps / (ms * 1e-3) / 1e9
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -354,7 +367,15 @@ def run_ours(args, wl):
                          "traffic": adj_traffic(wl, args.precision),
                          "avg_launch_us": 1e3 * kavg, "launches": klaunch,
                          "kernel_timing": "second K-step pass, CUDA events around each step's adjoint-stage launches",
-                         "bytes_per_launch": bytes_launch, "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"},
+                         "bytes_per_launch": bytes_launch,
+                         "bytes_rule": f"{ADJ_STEP_BYTES:.0f} B per adjoint cell-step (read w^n and lam^(n+1), "
+                                       f"write lam^n, FP64) / {stages} stage launches",
+                         "peak_source": hbm_src,
+                         "operand_bytes_per_launch": operand_bytes,
+                         "operand_frac": operand_bytes / (kavg * 1e-3) / 1e9 / hbm,
+                         "sweep": {"bytes_per_cell_step": SWEEP_BYTES, "achieved": sweep_gbs,
+                                   "frac": sweep_gbs / hbm, "unit": "GB/s"},
+                         "alu": alu_roofline(wl, args.precision, kavg, api)},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(w0.numel() * 8),
                     "d2h_bytes_per_step": int(lam0.numel() * 8 + J.numel() * 8)},
             "gpu_launches": gl,
@@ -364,6 +385,31 @@ def run_ours(args, wl):
             out["fp64"] = fp64_compare(api, torch, wl, w0, dt, sched, param, lam0, Jv, scheme, split, flux)
         if not args.no_cpu_baseline and ws == 1:
             out["cpu_baseline"] = cpu_baseline(wl, args.scheme, args.flux)
+    return out
+
+
+def alu_roofline(wl, precision, kavg_ms, api):
+    """The adjoint-stage kernel against the FP32 (FP64) multiply-add rate measured here:
+    achieved = FP32 (FP64) flops per launch, counted by ncu on this kernel source and
+    workload (committed summary, hash-checked; None otherwise), over the launch time."""
+    kind = api.NS_PEAK_FP64 if precision == "fp64" else None
+    try:
+        if kind is None:
+            peak = max(api.measure_fma_peak(api.NS_PEAK_FP32), api.measure_fma_peak(api.NS_PEAK_FP32X2))
+        else:
+            peak = api.measure_fma_peak(kind)
+    except Exception:
+        return None
+    flops = adj_profile_field(wl, precision, "fp64_flops_per_launch" if precision == "fp64"
+                              else "fp32_flops_per_launch")
+    out = {"unit": "TFLOP/s", "peak": peak / 1e12,
+           "peak_source": "ns_measure_fma_peak (measured here: best of scalar and paired FMA)"
+           if kind is None else "ns_measure_fma_peak (measured here, FP64 FMA)",
+           "achieved": None, "frac": None, "flops_per_launch": flops}
+    if flops:
+        a = flops / (kavg_ms * 1e-3)
+        out["achieved"] = a / 1e12
+        out["frac"] = a / peak
     return out
 
 
@@ -381,10 +427,10 @@ def adj_source_hash():
     return h.hexdigest()[:16]
 
 
-def adj_traffic(wl, precision):
-    """DRAM bytes per adjoint-stage launch from the committed ncu summary, when it was
-    taken on this workload and precision from the kernel sources as they are now (the
-    summary records their hash); otherwise None."""
+def adj_profile_field(wl, precision, key):
+    """A per-launch figure of the committed ncu summary of the adjoint-stage kernel, when
+    it was taken on this workload and precision from the kernel sources as they are now
+    (the summary records their hash); otherwise None."""
     if wl.name != "box128" or precision != "mixed" or not os.path.exists(ADJ_PROFILE):
         return None
     fields = {}
@@ -396,9 +442,14 @@ def adj_traffic(wl, precision):
     if fields.get("source_sha256_16") != adj_source_hash():
         return None
     try:
-        return int(fields["dram_bytes_per_launch"])
+        return int(fields[key])
     except (KeyError, ValueError):
         return None
+
+
+def adj_traffic(wl, precision):
+    """DRAM bytes per adjoint-stage launch (ncu, committed summary), or None."""
+    return adj_profile_field(wl, precision, "dram_bytes_per_launch")
 
 
 def fp64_compare(api, torch, wl, w0, dt, sched, param, lam_mixed, J_mixed, scheme, split=(1.0, 1.0, 1.0),

@@ -80,7 +80,8 @@ typedef struct {
   double Pr;        /* Prandtl number (0.72); heat flux alpha = gamma mu / Pr */
   double dt;        /* constant time step */
   int precision;    /* NS_FP64 or NS_MIXED */
-  int plane_i;      /* objective plane = x-face between cell columns plane_i-1, plane_i */
+  int plane_i;      /* objective plane = x-face between cell columns plane_i-1, plane_i
+                       (taken modulo nx; must lie within (-2^30, 2^30)) */
   double pt_in;     /* reference stagnation pressure p_t,in of Eq. (e:pressure_loss) */
   int scheme;       /* NS_RK4 or NS_SSPRK3: the explicit Runge-Kutta method of every step,
                        its tangent and its discrete adjoint */
@@ -135,6 +136,12 @@ int ns_tangent_step(ns_ctx* ctx, const double* w_n, const double* s, const doubl
  * lam_n must not alias lam_np1 or w_n. */
 int ns_adjoint_step(ns_ctx* ctx, const double* w_n, const double* s, const double* lam_np1,
                     const float* nu, double* lam_n, double* sbar_acc);
+/* ns_adjoint_step with an FP64 viscosity field nu (double [batch][nz][ny][nx], may be
+ * NULL); FP64 contexts only (NS_ERR_ARG in MIXED).  With ns_growth_sigma1_f64 and
+ * ns_add_adjoint_viscosity_f64 the stabilised adjoint step ("Energy analysis") runs with
+ * every operand in FP64. */
+int ns_adjoint_step_f64(ns_ctx* ctx, const double* w_n, const double* s, const double* lam_np1,
+                        const double* nu, double* lam_n, double* sbar);
 
 /* Pressure loss on the plane (Eq. e:pressure_loss, instantaneous plane average):
  *   J_acc[b] += weight * J(w_b)  for each box b (device array of batch doubles),
@@ -147,6 +154,10 @@ int ns_objective(ns_ctx* ctx, const double* w, double weight, double* J_acc, dou
  * for nz = 1 the (rho, u1, u2, p) block).  stats (device, may be NULL) receives
  * [batch][2] = (max, mean) per box. */
 int ns_growth_sigma1(ns_ctx* ctx, const double* w, float* sigma1, double* stats);
+/* ns_growth_sigma1 with sigma_1 kept in FP64 (sigma1: double [batch][nz][ny][nx]); FP64
+ * contexts only (NS_ERR_ARG in MIXED).  Section "Energy analysis" defines sigma_1; the
+ * FP64 form lets the stabilised adjoint of an FP64 context keep every operand in FP64. */
+int ns_growth_sigma1_f64(ns_ctx* ctx, const double* w, double* sigma1, double* stats);
 
 /* nu = lambda * sigma_1 where sigma_1 > tau, else 0 (section "Energy analysis":
  * the lambda sigma_1 coefficient; tau = 0 is the paper's rule).  lambda has units of
@@ -155,6 +166,9 @@ int ns_growth_sigma1(ns_ctx* ctx, const double* w, float* sigma1, double* stats)
  * error word. */
 int ns_add_adjoint_viscosity(ns_ctx* ctx, const float* sigma1, double lambda, double tau,
                              float* nu);
+/* The same rule in FP64: nu = lambda sigma_1 where sigma_1 > tau, else 0 (double fields),
+ * with the same stability check (NS_ERR_UNSTABLE in the sticky error word). */
+int ns_add_adjoint_viscosity_f64(ns_ctx* ctx, const double* sigma1, double lambda, double tau, double* nu);
 
 /* Separate added-viscosity factors for the adjoints of rho, of rho u (three
  * components) and of rho E: every later use of nu by this context (adjoint steps, the
@@ -292,6 +306,13 @@ int ns_adjoint_run(ns_ctx* ctx, const double* w0, const double* s, const ns_run_
 int ns_forward_run(ns_ctx* ctx, const double* w0, const double* s, const ns_run_opts* o,
                    void* arena, size_t arena_bytes, double* Jbar);
 int ns_backward_run(ns_ctx* ctx, double* lam0, double* sbar, double* energy, double* sigma_stats);
+/* Generation of the forward sweep that awaits its ns_backward_run: every successful
+ * ns_forward_run numbers its sweep 1, 2, ... on this context; 0 when no forward sweep is
+ * pending (none ran, it was reversed, or a later forward replaced it).  A caller that
+ * keeps several losses of one context (an autograd graph) records the number after its
+ * forward and compares it before its backward, so that it never reverses another
+ * forward's trajectory.  The paper has no counterpart. */
+long long ns_sweep_generation(const ns_ctx* ctx);
 
 /* ------------------------------------------------------------------------------
  * Choice of the viscosity scaling factor lambda for a given problem.  The paper's
@@ -373,12 +394,17 @@ int ns_profile_read(ns_ctx* ctx, double* ms, long long* launches);
  * for callers that cannot call cudaMalloc, such as host frameworks that own every byte
  * of device memory through their own pool or quota, or timing loops that must not take
  * cudaMalloc's implicit device synchronisation.  It needs no context: p describes the
- * grid, stream is a cudaStream_t (NULL = default stream).  Same result as ns_objective
- * (J_acc[b] += weight * J(w_b); lam += weight * dJ/dw if lam != NULL), computed by the
- * same kernels, but the reduction scratch is a file-scope device array of 256 KiB held
- * by every GPU that loads the library until the process exits.
+ * grid, stream is a cudaStream_t (NULL = default stream) that must belong to the
+ * current device (else NS_ERR_ARG).  It computes what ns_objective computes
+ * (J_acc[b] += weight * J(w_b); lam += weight * dJ/dw if lam != NULL), equal to it to FP64
+ * roundoff, with the three-kernel form of the objective (per-block partial sums, a final
+ * reduction, the gradient scatter) instead of ns_objective's two kernels; its reduction
+ * scratch is a file-scope device array of 256 KiB held by every GPU that loads the
+ * library until the process exits.
  *  - Limit: batch <= 55 (2 * 296 * batch + 2 * batch doubles must fit); larger batches
- *    return NS_ERR_BUDGET before any work is enqueued.
+ *    return NS_ERR_BUDGET before any work is enqueued.  The size limits of ns_create
+ *    apply; plane_i is taken modulo nx, as in ns_objective, and must lie within
+ *    (-2^30, 2^30).
  *  - The first call on a device looks up the array's device address on that device
  *    (cudaGetSymbolAddress, with that device current); make that first call before
  *    any stream capture.  NS_ERR_CUDA if the lookup fails.
@@ -436,6 +462,19 @@ int ns_label_target(ns_ctx* ctx, const float* acc, const float* sigma1, double t
  * (NS_OK, NS_ERR_NONFINITE or NS_ERR_UNSTABLE). */
 int ns_last_error(ns_ctx* ctx);
 const char* ns_error_string(int code);
+
+/* Measured arithmetic peak of the current device: the rate of independent fused
+ * multiply-adds (2 flops each) of kind NS_PEAK_FP32 (scalar FFMA), NS_PEAK_FP32X2 (the
+ * paired FP32 instruction) or NS_PEAK_FP64, in flop/s, from CUDA events around a
+ * full-occupancy kernel of about 20 ms (best of several launches).  The paper has no
+ * counterpart: the stencil kernels here are bound by FP32 arithmetic and instruction
+ * issue, and this is the denominator of their arithmetic roofline fraction.  Allocates
+ * and frees a small device buffer, a stream and two events; synchronises; NS_ERR_CUDA if
+ * a launch fails. */
+#define NS_PEAK_FP32 0
+#define NS_PEAK_FP32X2 1
+#define NS_PEAK_FP64 2
+int ns_measure_fma_peak(int kind, double* flops_per_s);
 
 /* Number of CUDA kernels this library has launched in this process, over all contexts
  * (monotone; host-side count, no device synchronisation).  The paper has no

@@ -26,6 +26,9 @@ NS_RK4 = 0
 NS_SSPRK3 = 1
 NS_FLUX_CENTRAL = 0
 NS_FLUX_ROE = 1
+NS_PEAK_FP32 = 0
+NS_PEAK_FP32X2 = 1
+NS_PEAK_FP64 = 2
 
 EXPORTED = [
     "ns_create", "ns_destroy", "ns_set_stream", "ns_set_dt", "ns_workspace_bytes", "ns_rhs",
@@ -37,7 +40,8 @@ EXPORTED = [
     "ns_dot_boxes", "ns_mlp_net_bytes", "ns_mlp_set_params", "ns_mlp_get_params", "ns_mlp_get_moment",
     "ns_mlp_features", "ns_mlp_infer", "ns_mlp_train_step", "ns_adjoint_label", "ns_label_target",
     "ns_launch_count", "ns_set_viscosity_split", "ns_energy_efolds", "ns_lambda_select",
-    "ns_estimate_work_bytes", "ns_estimate_lambda", "ns_run_host_bytes",
+    "ns_estimate_work_bytes", "ns_estimate_lambda", "ns_run_host_bytes", "ns_measure_fma_peak",
+    "ns_sweep_generation", "ns_growth_sigma1_f64", "ns_add_adjoint_viscosity_f64", "ns_adjoint_step_f64",
 ]
 
 NS_MLP_PARAMS = 5185
@@ -131,6 +135,11 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "ns_last_error": ([P], I),
         "ns_error_string": ([I], ctypes.c_char_p),
         "ns_launch_count": ([], ctypes.c_ulonglong),
+        "ns_measure_fma_peak": ([I, ctypes.POINTER(D)], I),
+        "ns_sweep_generation": ([P], ctypes.c_longlong),
+        "ns_growth_sigma1_f64": ([P, P, P, P], I),
+        "ns_add_adjoint_viscosity_f64": ([P, P, D, D, P], I),
+        "ns_adjoint_step_f64": ([P, P, P, P, P, P, P], I),
         "ns_set_viscosity_split": ([P, ctypes.POINTER(ctypes.c_double)], I),
         "ns_plan": ([I, I, I, P, I, ctypes.POINTER(I), ctypes.POINTER(I),
                      ctypes.POINTER(ctypes.c_longlong)], I),
@@ -289,6 +298,14 @@ class Solver:
                                         _ptr(wd_out, torch.float64)), "ns_tangent_step")
 
     def adjoint_step(self, w_n, lam_np1, lam_n, s=None, nu=None, sbar=None):
+        """A float64 nu selects ns_adjoint_step_f64 (FP64 contexts), a float32 one (or
+        None) ns_adjoint_step."""
+        if nu is not None and nu.dtype == torch.float64:
+            _check(self.lib.ns_adjoint_step_f64(self._ctx, _ptr(w_n, torch.float64), _ptr(s, torch.float64),
+                                                _ptr(lam_np1, torch.float64), _ptr(nu, torch.float64),
+                                                _ptr(lam_n, torch.float64), _ptr(sbar, torch.float64)),
+                   "ns_adjoint_step_f64")
+            return
         _check(self.lib.ns_adjoint_step(self._ctx, _ptr(w_n, torch.float64), _ptr(s, torch.float64),
                                         _ptr(lam_np1, torch.float64), _ptr(nu, torch.float32),
                                         _ptr(lam_n, torch.float64), _ptr(sbar, torch.float64)),
@@ -300,10 +317,21 @@ class Solver:
                "ns_objective")
 
     def growth_sigma1(self, w, sigma1, stats=None):
+        """A float64 sigma1 selects ns_growth_sigma1_f64 (FP64 contexts)."""
+        if sigma1.dtype == torch.float64:
+            _check(self.lib.ns_growth_sigma1_f64(self._ctx, _ptr(w, torch.float64), _ptr(sigma1, torch.float64),
+                                                 _ptr(stats, torch.float64)), "ns_growth_sigma1_f64")
+            return
         _check(self.lib.ns_growth_sigma1(self._ctx, _ptr(w, torch.float64), _ptr(sigma1, torch.float32),
                                          _ptr(stats, torch.float64)), "ns_growth_sigma1")
 
     def add_adjoint_viscosity(self, sigma1, lam_coef, nu, tau=0.0):
+        """A float64 sigma1 selects ns_add_adjoint_viscosity_f64 (nu float64 too)."""
+        if sigma1.dtype == torch.float64:
+            _check(self.lib.ns_add_adjoint_viscosity_f64(self._ctx, _ptr(sigma1, torch.float64), float(lam_coef),
+                                                         float(tau), _ptr(nu, torch.float64)),
+                   "ns_add_adjoint_viscosity_f64")
+            return
         _check(self.lib.ns_add_adjoint_viscosity(self._ctx, _ptr(sigma1, torch.float32), float(lam_coef),
                                                  float(tau), _ptr(nu, torch.float32)),
                "ns_add_adjoint_viscosity")
@@ -402,6 +430,10 @@ class Solver:
                                        ctypes.byref(opts), _ptr(arena), arena.numel() * arena.element_size(),
                                        _ptr(Jbar, torch.float64)), "ns_forward_run")
 
+    def sweep_generation(self) -> int:
+        """Number of the forward sweep awaiting its backward, 0 if none (ns_sweep_generation)."""
+        return int(self.lib.ns_sweep_generation(self._ctx))
+
     def backward_run(self, lam0, sbar=None, energy=None, sigma_stats=None):
         """Reverse half of the sweep with a unit seed on each box's Jbar."""
         _check(self.lib.ns_backward_run(self._ctx, _ptr(lam0, torch.float64), _ptr(sbar, torch.float64),
@@ -466,3 +498,11 @@ def launch_count() -> int:
 
 def mlp_net_bytes() -> int:
     return int(_lib().ns_mlp_net_bytes())
+
+
+def measure_fma_peak(kind: int) -> float:
+    """Measured multiply-add rate of the current device in flop/s (ns_measure_fma_peak);
+    kind is NS_PEAK_FP32, NS_PEAK_FP32X2 or NS_PEAK_FP64."""
+    out = ctypes.c_double()
+    _check(_lib().ns_measure_fma_peak(int(kind), ctypes.byref(out)), "ns_measure_fma_peak")
+    return out.value

@@ -55,6 +55,7 @@ class PressureLoss(torch.autograd.Function):
         J = torch.empty(S.batch, dtype=torch.float64, device=w.device)
         S.forward_run(w, problem.opts, problem.arena, J, s)
         ctx.problem = problem
+        ctx.generation = S.sweep_generation()   # this loss's trajectory
         ctx.keep = (w, s)            # the reverse sweep reads w0 and s again
         return J
 
@@ -63,6 +64,11 @@ class PressureLoss(torch.autograd.Function):
         problem = ctx.problem
         S = problem.S
         w, s = ctx.keep
+        if S.sweep_generation() != ctx.generation:
+            raise RuntimeError(
+                "PressureLoss.backward: the solver's checkpoints no longer hold this loss's "
+                "trajectory (another forward ran on the same solver, or this one was already "
+                "reversed); run backward before the next forward, or use one solver per loss")
         lam0 = torch.empty_like(w)
         sbar = torch.empty_like(w)
         S.backward_run(lam0, sbar)

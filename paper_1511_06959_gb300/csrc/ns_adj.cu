@@ -29,44 +29,80 @@
 #include "ns_roe.cuh"
 
 namespace ns {
+namespace adjk {
+
+// Tile of the adjoint stage kernel: TX x TY columns (one thread per column).
+#ifndef NS_ADJ_TY
+#define NS_ADJ_TY 4
+#endif
+constexpr int TY = NS_ADJ_TY;
+constexpr int NT = TX * TY;
+constexpr int SY = TY + 2;
+constexpr int SP = SX * SY;
 
 namespace {
 
-// Register-staged plane load (primal primitives and adjoint input) so that the next
-// plane's global loads overlap the current plane's work.
+// In-plane offsets, periodic wrap resolved, of this thread's two shared positions
+// t = tid and t = tid + NT (the same in every plane of the CTA's range).
+struct AdjHalo {
+  int o[2];
+};
+__device__ __forceinline__ AdjHalo adj_halo(const GridDesc& g, int x0, int y0) {
+  AdjHalo h;
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const int t = threadIdx.x + it * NT;
+    const int ly = t / SX;
+    const int lx = t - ly * SX;
+    h.o[it] = t < SP ? wrap(y0 + ly - 1, g.ny) * g.nx + wrap(x0 + lx - 1, g.nx) : 0;
+  }
+  return h;
+}
+
+// Register-staged plane load (primal primitives, adjoint input and, with the added
+// viscosity, nu) so that the next plane's global loads overlap the current plane's work.
 static_assert(SP <= 2 * NT, "a plane must fit two load rounds");
 template <class CT>
 struct AdjPlaneRegs {
   CT q[2][5];
   CT a[2][5];
+  CT n[2];
 };
 
 template <class CT, class TIN, class TA>
-__device__ __forceinline__ void adj_plane_load(AdjPlaneRegs<CT>& r, const GridDesc& g, int b, int k, int x0,
-                                               int y0, const TIN* __restrict__ W, const TA* __restrict__ A,
-                                               double ca) {
+__device__ __forceinline__ void adj_plane_load(AdjPlaneRegs<CT>& r, const GridDesc& g, size_t boxoff, int b,
+                                               int k, const AdjHalo& h, const TIN* __restrict__ W,
+                                               const TA* __restrict__ A, double ca, const float* __restrict__ nu,
+                                               const double* __restrict__ nud) {
   const int kz = wrap(k, g.nz);
-  const size_t boxoff = (size_t)b * 5 * g.cells + (size_t)kz * g.plane;
+  const size_t pb = boxoff + (size_t)kz * g.plane;
   const CT cac = CT(ca);
 #pragma unroll
   for (int it = 0; it < 2; ++it) {
-    const int t = threadIdx.x + it * NT;
-    if (t < SP) {
-      const int ly = t / SX;
-      const int lx = t - ly * SX;
-      const size_t o = boxoff + (size_t)wrap(y0 + ly - 1, g.ny) * g.nx + wrap(x0 + lx - 1, g.nx);
+    if (threadIdx.x + it * NT < SP) {
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
-        r.q[it][v] = cvt<CT>(W[o + v * g.cells]);
-        r.a[it][v] = cac * cvt<CT>(A[o + v * g.cells]);
+        r.q[it][v] = cvt<CT>((W + pb + v * (size_t)g.cells)[h.o[it]]);
+        r.a[it][v] = cac * cvt<CT>((A + pb + v * (size_t)g.cells)[h.o[it]]);
       }
     }
+  }
+  if (nu) {
+    const float* nk = nu + (size_t)b * g.cells + (size_t)kz * g.plane;
+#pragma unroll
+    for (int it = 0; it < 2; ++it)
+      if (threadIdx.x + it * NT < SP) r.n[it] = CT(nk[h.o[it]]);
+  } else if (nud) {
+    const double* nk = nud + (size_t)b * g.cells + (size_t)kz * g.plane;
+#pragma unroll
+    for (int it = 0; it < 2; ++it)
+      if (threadIdx.x + it * NT < SP) r.n[it] = cvt<CT>(nk[h.o[it]]);
   }
 }
 
 template <class CT>
 __device__ __forceinline__ void adj_plane_store(const AdjPlaneRegs<CT>& r, CT* __restrict__ sq,
-                                                CT* __restrict__ sa) {
+                                                CT* __restrict__ sa, CT* __restrict__ sn, bool with_nu) {
 #pragma unroll
   for (int it = 0; it < 2; ++it) {
     const int t = threadIdx.x + it * NT;
@@ -80,6 +116,7 @@ __device__ __forceinline__ void adj_plane_store(const AdjPlaneRegs<CT>& r, CT* _
       sq[4 * SP + t] = r.q[it][4] * ir - CT(0.5) * (u0 * u0 + u1 * u1 + u2 * u2);
 #pragma unroll
       for (int v = 0; v < 5; ++v) sa[v * SP + t] = r.a[it][v];
+      if (with_nu) sn[t] = r.n[it];
     }
   }
 }
@@ -280,11 +317,12 @@ __device__ __forceinline__ void fill_Z(CT* Z, const CT* sQ, const CT* sA, const 
 
 }  // namespace
 
-// Resident CTAs per SM the register allocation is held to: 4 for FP32 (the shared
-// memory allows 4), 3 for FP32 with Roe dissipation, 2 for FP64.
-template <class CT, bool ROE> struct AdjMinBlocks { static constexpr int value = 2; };
-template <> struct AdjMinBlocks<float, false> { static constexpr int value = 4; };
-template <> struct AdjMinBlocks<float, true> { static constexpr int value = 3; };
+// Resident CTAs per SM the register allocation is held to (for the 32 x 4 tile; half
+// as many CTAs of twice the threads for the 32 x 8 tile): 4 for FP32 (the shared memory
+// allows 4), 3 for FP32 with Roe dissipation, 2 for FP64.
+template <class CT, bool ROE> struct AdjMinBlocks { static constexpr int value = NT >= 256 ? 1 : 2; };
+template <> struct AdjMinBlocks<float, false> { static constexpr int value = 512 / NT; };
+template <> struct AdjMinBlocks<float, true> { static constexpr int value = NT >= 256 ? 1 : 3; };
 
 // values per face packet: 7 (viscous and face velocity), plus 10 with Roe dissipation
 template <bool ROE> constexpr int npk() { return ROE ? 17 : 7; }
@@ -300,24 +338,31 @@ __global__ void __launch_bounds__(NT, AdjMinBlocks<CT, ROE>::value) k_adj_stage(
   CT* sZ = sF + 2 * 4 * NF;                    // [2][3][SP] z-face s-vectors
   CT* sFX = sZ + 2 * 3 * SP;                   // [NPK][TY][TX+1]
   CT* sFY = sFX + NPK * TY * (TX + 1);         // [NPK][TY+1][TX]
+  CT* sN = sFY + NPK * (TY + 1) * TX;          // [3][SP] added viscosity nu (when given)
   const int tid = threadIdx.x;
   const int tx = tid % TX, ty = tid / TX;
   int b, x0, y0, kz0, kz1;
   march_range<TX, TY>(g, b, x0, y0, kz0, kz1);
   const int gx = x0 + tx, gy = y0 + ty;
   const bool valid = gx < g.nx && gy < g.ny;
+  const int cp = valid ? gy * g.nx + gx : 0;   // the thread's cell within a plane
+  const size_t boxoff = (size_t)b * 5 * g.cells;
+  const AdjHalo hal = adj_halo(g, x0, y0);
+  const bool with_nu = a.nu != nullptr || a.nud != nullptr;
   auto slot = [&](int k) { return (k - kz0 + 1) % 3; };
   auto zslot = [&](int k) { return (k - kz0 + 1) & 1; };   // z-face k + 1/2
   auto fslot = [&](int k) { return sF + ((k - kz0 + 1) & 1) * 4 * NF; };   // faces of plane k
 
   {
     AdjPlaneRegs<CT> p0, p1, p2;
-    adj_plane_load(p0, g, b, kz0 - 1, x0, y0, a.W, a.A, a.ca);
-    adj_plane_load(p1, g, b, kz0, x0, y0, a.W, a.A, a.ca);
-    adj_plane_load(p2, g, b, kz0 + 1, x0, y0, a.W, a.A, a.ca);
-    adj_plane_store(p0, sQ + slot(kz0 - 1) * 5 * SP, sA + slot(kz0 - 1) * 5 * SP);
-    adj_plane_store(p1, sQ + slot(kz0) * 5 * SP, sA + slot(kz0) * 5 * SP);
-    adj_plane_store(p2, sQ + slot(kz0 + 1) * 5 * SP, sA + slot(kz0 + 1) * 5 * SP);
+    adj_plane_load(p0, g, boxoff, b, kz0 - 1, hal, a.W, a.A, a.ca, a.nu, a.nud);
+    adj_plane_load(p1, g, boxoff, b, kz0, hal, a.W, a.A, a.ca, a.nu, a.nud);
+    adj_plane_load(p2, g, boxoff, b, kz0 + 1, hal, a.W, a.A, a.ca, a.nu, a.nud);
+    adj_plane_store(p0, sQ + slot(kz0 - 1) * 5 * SP, sA + slot(kz0 - 1) * 5 * SP, sN + slot(kz0 - 1) * SP,
+                    with_nu);
+    adj_plane_store(p1, sQ + slot(kz0) * 5 * SP, sA + slot(kz0) * 5 * SP, sN + slot(kz0) * SP, with_nu);
+    adj_plane_store(p2, sQ + slot(kz0 + 1) * 5 * SP, sA + slot(kz0 + 1) * 5 * SP, sN + slot(kz0 + 1) * SP,
+                    with_nu);
   }
   __syncthreads();
   fill_faces(fslot(kz0 - 1), sQ, sA, c, slot(kz0 - 1));
@@ -340,29 +385,20 @@ __global__ void __launch_bounds__(NT, AdjMinBlocks<CT, ROE>::value) k_adj_stage(
     const int sm = slot(k - 1), s0 = slot(k), sp = slot(k + 1);
     const bool more = k + 1 < kz1;
     AdjPlaneRegs<CT> pf;
-    if (more) adj_plane_load(pf, g, b, k + 2, x0, y0, a.W, a.A, a.ca);
+    if (more) adj_plane_load(pf, g, boxoff, b, k + 2, hal, a.W, a.A, a.ca, a.nu, a.nud);
     // per-cell operands of the assembly and epilogue, loaded ahead of the face work
-    const size_t o0 = (size_t)b * 5 * g.cells + (size_t)k * g.plane + (size_t)gy * g.nx + gx;
-    CT nuv[7] = {CT(0), CT(0), CT(0), CT(0), CT(0), CT(0), CT(0)};
+    const size_t pbase = boxoff + (size_t)k * g.plane;   // component 0 of plane k
+    const size_t fc = (size_t)g.cells;
     CT gin[5] = {CT(0), CT(0), CT(0), CT(0), CT(0)};
     CT lfv[5] = {CT(0), CT(0), CT(0), CT(0), CT(0)};
     if (valid) {
-      if (a.nu) {
-        const float* nub = a.nu + (size_t)b * g.cells;
-        const size_t pl = (size_t)k * g.plane;
-        const size_t row = pl + (size_t)gy * g.nx;
-        nuv[0] = CT(nub[row + gx]);
-        nuv[1] = CT(nub[row + wrap(gx - 1, g.nx)]);
-        nuv[2] = CT(nub[row + wrap(gx + 1, g.nx)]);
-        nuv[3] = CT(nub[pl + (size_t)wrap(gy - 1, g.ny) * g.nx + gx]);
-        nuv[4] = CT(nub[pl + (size_t)wrap(gy + 1, g.ny) * g.nx + gx]);
-        nuv[5] = CT(nub[(size_t)wrap(k - 1, g.nz) * g.plane + (size_t)gy * g.nx + gx]);
-        nuv[6] = CT(nub[(size_t)wrap(k + 1, g.nz) * g.plane + (size_t)gy * g.nx + gx]);
-      }
+      if (a.Gin) {
 #pragma unroll
-      for (int v = 0; v < 5; ++v) {
-        if (a.Gin) gin[v] = a.Gin[o0 + (size_t)v * g.cells];
-        if (a.Anext) lfv[v] = a.lamf[o0 + (size_t)v * g.cells];
+        for (int v = 0; v < 5; ++v) gin[v] = (a.Gin + pbase + v * fc)[cp];
+      }
+      if (a.Anext) {
+#pragma unroll
+        for (int v = 0; v < 5; ++v) lfv[v] = (a.lamf + pbase + v * fc)[cp];
       }
     }
     const CT* F0 = fslot(k);
@@ -411,8 +447,10 @@ __global__ void __launch_bounds__(NT, AdjMinBlocks<CT, ROE>::value) k_adj_stage(
     CT am[5];
 #pragma unroll
     for (int v = 0; v < 5; ++v) am[v] = sA[(sm * 5 + v) * SP + ic];
+    const CT nzm = with_nu ? sN[sm * SP + ic] : CT(0);
     __syncthreads();
-    if (more) adj_plane_store(pf, sQ + slot(k + 2) * 5 * SP, sA + slot(k + 2) * 5 * SP);
+    if (more) adj_plane_store(pf, sQ + slot(k + 2) * 5 * SP, sA + slot(k + 2) * 5 * SP, sN + slot(k + 2) * SP,
+                              with_nu);
 
     CT own_p[3] = {CT(0), CT(0), CT(0)};
     if (valid) {
@@ -526,9 +564,10 @@ __global__ void __launch_bounds__(NT, AdjMinBlocks<CT, ROE>::value) k_adj_stage(
       CT gout[5] = {rb, mb[0], mb[1], mb[2], Eb};
       // ---- added adjoint viscosity L_nu a, times the factor of the component's state
       // variable (rho, rho u, rho E)
-      if (a.nu) {
-        const CT nc = nuv[0], nxm = nuv[1], nxp = nuv[2], nym = nuv[3], nyp = nuv[4], nzm = nuv[5],
-                 nzp = nuv[6];
+      if (with_nu) {
+        const CT* N0 = sN + s0 * SP;
+        const CT nc = N0[ic], nxm = N0[ic - 1], nxp = N0[ic + 1], nym = N0[ic - SX], nyp = N0[ic + SX],
+                 nzp = sN[sp * SP + ic];
         const CT ix2 = c.idx[0] * c.idx[0], iy2 = c.idx[1] * c.idx[1], iz2 = c.idx[2] * c.idx[2];
 #pragma unroll
         for (int v = 0; v < 5; ++v) {
@@ -540,22 +579,49 @@ __global__ void __launch_bounds__(NT, AdjMinBlocks<CT, ROE>::value) k_adj_stage(
           gout[v] = gout[v] + CT(a.nus[v == 0 ? 0 : (v == 4 ? 2 : 1)]) * L;
         }
       }
-      // ---- epilogue
+      // ---- epilogue (each optional operand tested once per plane)
+      CT gs[5];
 #pragma unroll
-      for (int v = 0; v < 5; ++v) {
-        const size_t o = o0 + (size_t)v * g.cells;
-        const CT gs = gin[v] + gout[v];
-        if (a.Gout) a.Gout[o] = gs;
-        if (a.lam_out) {
-          const double lv = (a.lam_in ? a.lam_in[o] : 0.0) + widen(gs);
-          a.lam_out[o] = lv;
-          if (a.lam_out_mirror) a.lam_out_mirror[o] = cvt<TST>(lv);
+      for (int v = 0; v < 5; ++v) gs[v] = gin[v] + gout[v];
+      if (a.Gout) {
+#pragma unroll
+        for (int v = 0; v < 5; ++v) (a.Gout + pbase + v * fc)[cp] = gs[v];
+      }
+      if (a.lam_out) {
+        double lv[5];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) lv[v] = widen(gs[v]);
+        if (a.lam_in) {
+#pragma unroll
+          for (int v = 0; v < 5; ++v) lv[v] = (a.lam_in + pbase + v * fc)[cp] + lv[v];
         }
-        if (a.Anext) a.Anext[o] = CT(a.cl) * lfv[v] + CT(a.cg) * gout[v] + CT(a.cs) * gs;
-        if (a.SBout || a.sbar) {
-          const CT ss = (a.SBin ? a.SBin[o] : CT(0)) + A0[v * SP + ic];
-          if (a.SBout) a.SBout[o] = ss;
-          if (a.sbar) a.sbar[o] += widen(ss);
+#pragma unroll
+        for (int v = 0; v < 5; ++v) (a.lam_out + pbase + v * fc)[cp] = lv[v];
+        if (a.lam_out_mirror) {
+#pragma unroll
+          for (int v = 0; v < 5; ++v) (a.lam_out_mirror + pbase + v * fc)[cp] = cvt<TST>(lv[v]);
+        }
+      }
+      if (a.Anext) {
+#pragma unroll
+        for (int v = 0; v < 5; ++v)
+          (a.Anext + pbase + v * fc)[cp] = CT(a.cl) * lfv[v] + CT(a.cg) * gout[v] + CT(a.cs) * gs[v];
+      }
+      if (a.SBout || a.sbar) {
+        CT ss[5];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) ss[v] = A0[v * SP + ic];
+        if (a.SBin) {
+#pragma unroll
+          for (int v = 0; v < 5; ++v) ss[v] = (a.SBin + pbase + v * fc)[cp] + ss[v];
+        }
+        if (a.SBout) {
+#pragma unroll
+          for (int v = 0; v < 5; ++v) (a.SBout + pbase + v * fc)[cp] = ss[v];
+        }
+        if (a.sbar) {
+#pragma unroll
+          for (int v = 0; v < 5; ++v) (a.sbar + pbase + v * fc)[cp] += widen(ss[v]);
         }
       }
     }
@@ -573,7 +639,8 @@ __global__ void __launch_bounds__(NT, AdjMinBlocks<CT, ROE>::value) k_adj_stage(
 template <class CT, bool ROE>
 size_t adj_smem_bytes() {
   constexpr int NPK = npk<ROE>();
-  return sizeof(CT) * (3 * 5 * SP * 2 + 2 * 4 * NF + 2 * 3 * SP + NPK * TY * (TX + 1) + NPK * (TY + 1) * TX);
+  return sizeof(CT) *
+         (3 * 5 * SP * 2 + 2 * 4 * NF + 2 * 3 * SP + NPK * TY * (TX + 1) + NPK * (TY + 1) * TX + 3 * SP);
 }
 
 template <class CT, class TIN, class TA, class TST, bool ROE>
@@ -590,11 +657,13 @@ static cudaError_t launch_adj_variant(const GridDesc& g, const Coef<CT>& c, cons
   return e;
 }
 
+}  // namespace adjk
+
 template <class CT, class TIN, class TA, class TST>
 cudaError_t launch_adj_stage(const GridDesc& g, const Coef<CT>& c, const AdjArgs<TIN, TA, TST>& a,
                              cudaStream_t st) {
-  return c.roe ? launch_adj_variant<CT, TIN, TA, TST, true>(g, c, a, st)
-               : launch_adj_variant<CT, TIN, TA, TST, false>(g, c, a, st);
+  return c.roe ? adjk::launch_adj_variant<CT, TIN, TA, TST, true>(g, c, a, st)
+               : adjk::launch_adj_variant<CT, TIN, TA, TST, false>(g, c, a, st);
 }
 
 template cudaError_t launch_adj_stage<double, double, double, double>(

@@ -154,7 +154,7 @@ static cudaError_t adj_launch(ns_ctx* c, const Coef<CT>& cf, const ns::AdjArgs<T
 template <class CT>
 static int adjoint_step_t(ns_ctx* c, const Coef<CT>& cf, const CT* W1, const CT* lamf, const double* s,
                           const double* lam, const float* nu, double* lo, double* sbar,
-                          const CT* const* kept = nullptr, CT* lo_mirror = nullptr) {
+                          const CT* const* kept = nullptr, CT* lo_mirror = nullptr, const double* nud = nullptr) {
   const Scheme& sc = scheme_of(c);
   const double dt = c->p.dt;
   const CT* Wst[3];
@@ -186,7 +186,7 @@ static int adjoint_step_t(ns_ctx* c, const Coef<CT>& cf, const CT* W1, const CT*
     CT* Aout = last ? nullptr : (j % 2 == 0 ? Aa : Ab);
     ns::AdjArgs<CT, CT, CT> a{};
     a.W = last ? W1 : Wst[sc.ns - 2 - j];
-    a.A = Ain; a.ca = j == 0 ? sc.ca0 * dt : 1.0; a.nu = nu; a.lamf = lamf;
+    a.A = Ain; a.ca = j == 0 ? sc.ca0 * dt : 1.0; a.nu = nu; a.nud = nu ? nullptr : nud; a.lamf = lamf;
     for (int q = 0; q < 3; ++q) a.nus[q] = c->nu_split[q];
     a.Gin = j == 0 ? nullptr : G;
     a.Anext = Aout;
@@ -236,6 +236,7 @@ int ns_create(const ns_params* p, void* stream, ns_ctx** out) {
   if (p->flux == NS_FLUX_ROE && !(p->roe_delta > 0.0 && p->roe_delta < 1e30)) return NS_ERR_ARG;
   if ((long long)p->nx * p->ny > (1LL << 31) || (long long)p->nx * p->ny * p->nz > (1LL << 40))
     return NS_ERR_ARG;
+  if (p->plane_i <= -(1 << 30) || p->plane_i >= (1 << 30)) return NS_ERR_ARG;
   ns_ctx* c = new ns_ctx();
   c->p = *p;
   c->st = (cudaStream_t)stream;
@@ -387,6 +388,13 @@ int ns_adjoint_step(ns_ctx* c, const double* w, const double* s, const double* l
   return adjoint_step_t<double>(c, c->cd, w, lam, s, lam, nu, lo, sbar);
 }
 
+int ns_adjoint_step_f64(ns_ctx* c, const double* w, const double* s, const double* lam, const double* nu,
+                        double* lo, double* sbar) {
+  if (!c || mixed(c) || !w || !lam || !lo || lo == lam || lo == w || (sbar && (sbar == lo || sbar == lam)))
+    return NS_ERR_ARG;
+  return adjoint_step_t<double>(c, c->cd, w, lam, s, lam, nullptr, lo, sbar, nullptr, nullptr, nu);
+}
+
 int ns_rhs_transpose(ns_ctx* c, const double* w, const double* a_, const float* nu, double* out) {
   if (!c || !w || !a_ || !out || out == w || out == a_) return NS_ERR_ARG;
   if (mixed(c)) {
@@ -422,6 +430,12 @@ int ns_growth_sigma1(ns_ctx* c, const double* w, float* sigma1, double* stats) {
   return cuerr(ns::launch_sigma1<double>(c->g, c->cd, w, sigma1, stats, c->scratch, c->ticket, c->st));
 }
 
+int ns_growth_sigma1_f64(ns_ctx* c, const double* w, double* sigma1, double* stats) {
+  if (!c || mixed(c) || !w || !sigma1) return NS_ERR_ARG;
+  return cuerr(ns::launch_sigma1<double>(c->g, c->cd, w, nullptr, stats, c->scratch, c->ticket, c->st, nullptr,
+                                         sigma1));
+}
+
 static double nu_limit(const ns_ctx* c) {
   const double k = 4.0 * (1.0 / (c->p.dx * c->p.dx) + 1.0 / (c->p.dy * c->p.dy) +
                           (c->p.nz > 1 ? 1.0 / (c->p.dz * c->p.dz) : 0.0));
@@ -433,6 +447,11 @@ int ns_add_adjoint_viscosity(ns_ctx* c, const float* sigma1, double lambda, doub
   if (!c || !sigma1 || !nu || !(lambda >= 0)) return NS_ERR_ARG;
   const double limit = nu_limit(c);
   return cuerr(ns::launch_nu_rule(c->g, sigma1, lambda, tau, limit, nu, c->err, c->st));
+}
+
+int ns_add_adjoint_viscosity_f64(ns_ctx* c, const double* sigma1, double lambda, double tau, double* nu) {
+  if (!c || !sigma1 || !nu || !(lambda >= 0)) return NS_ERR_ARG;
+  return cuerr(ns::launch_nu_rule_f64(c->g, sigma1, lambda, tau, nu_limit(c), nu, c->err, c->st));
 }
 
 int ns_apply_adjoint_viscosity(ns_ctx* c, const float* nu, const double* a, double* out) {
@@ -610,7 +629,7 @@ int ns_i_primal(ns_ctx* c, const double* w, const void* w_mirror, const double* 
 
 int ns_i_adjoint(ns_ctx* c, const double* w, const void* w_mirror, const void* const* kept3, const double* s,
                  const double* lam, const void* lam_mirror, const float* nu, double* lo, void* lo_mirror,
-                 double* sbar) {
+                 double* sbar, const double* nud) {
   if (mixed(c)) {
     const float* W1 = (const float*)w_mirror;
     if (!W1) {
@@ -627,7 +646,8 @@ int ns_i_adjoint(ns_ctx* c, const double* w, const void* w_mirror, const void* c
     return adjoint_step_t<float>(c, c->cf, W1, lf, s, lam, nu, lo, sbar, (const float* const*)kept3,
                                  (float*)lo_mirror);
   }
-  return adjoint_step_t<double>(c, c->cd, w, lam, s, lam, nu, lo, sbar, (const double* const*)kept3);
+  return adjoint_step_t<double>(c, c->cd, w, lam, s, lam, nu, lo, sbar, (const double* const*)kept3, nullptr,
+                                nud);
 }
 
 int ns_i_energy(ns_ctx* c, const double* w, const void* w_mirror, const double* lam, const void* lam_mirror,
@@ -646,9 +666,16 @@ int ns_i_objective(ns_ctx* c, const double* w, double weight, double* J_acc, dou
                                          mixed(c) ? (float*)lam_mirror : nullptr));
 }
 
+int ns_i_sigma1_f64(ns_ctx* c, const double* w, double* sigma1, double* stats, double lambda, double tau,
+                    double* nu) {
+  ns::NuRule rule{0.f, 0.f, 0.f, nullptr, c->err, lambda, tau, nu_limit(c), nu};
+  return cuerr(ns::launch_sigma1<double>(c->g, c->cd, w, nullptr, stats, c->scratch, c->ticket, c->st,
+                                         nu ? &rule : nullptr, sigma1));
+}
+
 int ns_i_sigma1(ns_ctx* c, const double* w, const void* w_mirror, float* sigma1, double* stats, double lambda,
                 double tau, float* nu) {
-  ns::NuRule rule{(float)lambda, (float)tau, (float)nu_limit(c), nu, c->err};
+  ns::NuRule rule{(float)lambda, (float)tau, (float)nu_limit(c), nu, c->err, 0.0, 0.0, 0.0, nullptr};
   const ns::NuRule* rp = nu ? &rule : nullptr;
   if (mixed(c)) {
     const float* wf = (const float*)w_mirror;

@@ -34,6 +34,8 @@ struct ns_ctx {
   long long prof_launches = 0;   // adjoint-stage launches inside the event pairs
   std::vector<cudaEvent_t> events;
   ns_sweep_state* sweep = nullptr;   // executor state between ns_forward_run and ns_backward_run
+  long long sweep_gen = 0;           // forward sweeps started on this context
+  long long pending_gen = 0;         // generation of the forward sweep awaiting its backward (0: none)
   double* qbar = nullptr;            // box-mean primitive states [batch][5] (closure features)
   unsigned* ticket = nullptr;        // per-box counters of the single-launch objective
   float* train_scratch = nullptr;    // closure training partials, allocated on first use
@@ -49,7 +51,7 @@ int ns_i_primal(ns_ctx* c, const double* w, const void* w_mirror, const double* 
                 void* const* keep3);
 int ns_i_adjoint(ns_ctx* c, const double* w, const void* w_mirror, const void* const* kept3, const double* s,
                  const double* lam, const void* lam_mirror, const float* nu, double* lo, void* lo_mirror,
-                 double* sbar);
+                 double* sbar, const double* nud = nullptr);
 // ns_mlp_features from the float mirror of w when given (mixed mode; the same bits)
 int ns_i_mlp_features(ns_ctx* c, const double* w, const void* w_mirror, float* feat);
 // ns_adjoint_energy from the float mirrors of w and lam when both are given (mixed mode)
@@ -61,6 +63,9 @@ int ns_i_objective(ns_ctx* c, const double* w, double weight, double* J_acc, dou
 // sigma_1 rule (nu = lambda sigma_1 [sigma_1 > tau]) with the stability flag
 int ns_i_sigma1(ns_ctx* c, const double* w, const void* w_mirror, float* sigma1, double* stats,
                 double lambda = 0.0, double tau = 0.0, float* nu = nullptr);
+// FP64 contexts: sigma_1 (and with nu != null the rule's viscosity) kept in FP64
+int ns_i_sigma1_f64(ns_ctx* c, const double* w, double* sigma1, double* stats, double lambda, double tau,
+                    double* nu);
 size_t ns_i_stage_bytes(const ns_ctx* c);
 
 namespace ns {

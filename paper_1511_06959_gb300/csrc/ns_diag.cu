@@ -471,7 +471,7 @@ __device__ __forceinline__ void growth_matrix(const GridDesc& g, const Coef<CT>&
 template <class CT>
 __global__ void __launch_bounds__(RB, sizeof(CT) == 4 ? 4 : 1) k_sigma1(GridDesc g, Coef<CT> c, const CT* __restrict__ w,
                                                float* __restrict__ sig, double* partial, double* stats,
-                                               unsigned* ticket, NuRule rule) {
+                                               unsigned* ticket, NuRule rule, double* __restrict__ sigd) {
   pdl_enter();
   __shared__ double sh[32];
   __shared__ bool last;
@@ -486,16 +486,29 @@ __global__ void __launch_bounds__(RB, sizeof(CT) == 4 ? 4 : 1) k_sigma1(GridDesc
     CT M[5][5];
     growth_matrix<CT>(g, c, w, b, x, y, z, M);
     const CT s1 = g.nz == 1 ? sigma1_of<CT, 4>(M) : sigma1_of<CT, 5>(M);
-    const float sf = (float)s1;
     const size_t o = (size_t)b * g.cells + i;
-    sig[o] = sf;
-    if (rule.nu) {
-      const float v = sf > rule.tau ? rule.lam * sf : 0.0f;
-      rule.nu[o] = v;
-      if (!(v <= rule.limit)) atomicOr(rule.err, ERRBIT_UNSTABLE);
+    if (sigd) {
+      // FP64 contexts: sigma_1 and the rule's viscosity kept in FP64
+      const double sd = (double)s1;
+      sigd[o] = sd;
+      if (rule.nud) {
+        const double v = sd > rule.taud ? rule.lamd * sd : 0.0;
+        rule.nud[o] = v;
+        if (!(v <= rule.limitd)) atomicOr(rule.err, ERRBIT_UNSTABLE);
+      }
+      vmax = fmax(vmax, s1);
+      vsum += sd;
+    } else {
+      const float sf = (float)s1;
+      sig[o] = sf;
+      if (rule.nu) {
+        const float v = sf > rule.tau ? rule.lam * sf : 0.0f;
+        rule.nu[o] = v;
+        if (!(v <= rule.limit)) atomicOr(rule.err, ERRBIT_UNSTABLE);
+      }
+      vmax = fmax(vmax, CT(sf));
+      vsum += (double)sf;
     }
-    vmax = fmax(vmax, CT(sf));
-    vsum += (double)sf;
   }
   if (!stats) return;
   const double bmax = block_reduce(vmax, sh, MaxOp());
@@ -601,6 +614,17 @@ __global__ void k_nu_rule(long long n, const float* __restrict__ s1, float lam, 
   if (i >= n) return;
   const float s = s1[i];
   const float v = s > tau ? lam * s : 0.0f;
+  nu[i] = v;
+  if (!(v <= limit_nu)) atomicOr(err, ERRBIT_UNSTABLE);
+}
+
+// the same rule in FP64 (FP64 contexts)
+__global__ void k_nu_rule_f64(long long n, const double* __restrict__ s1, double lam, double tau,
+                              double limit_nu, double* __restrict__ nu, unsigned* err) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double s = s1[i];
+  const double v = s > tau ? lam * s : 0.0;
   nu[i] = v;
   if (!(v <= limit_nu)) atomicOr(err, ERRBIT_UNSTABLE);
 }
@@ -865,17 +889,18 @@ cudaError_t launch_objective_fast(const GridDesc& g, double gamma, int plane_i, 
 template <class CT>
 cudaError_t launch_sigma1(const GridDesc& g, const Coef<CT>& c, const CT* w, float* sigma1,
                           double* stats, double* scratch, unsigned* ticket, cudaStream_t st,
-                          const NuRule* rule) {
+                          const NuRule* rule, double* sigma1d) {
   dim3 grid(RGS, g.batch);
-  const NuRule r = rule ? *rule : NuRule{0.f, 0.f, 0.f, nullptr, nullptr};
-  cudaError_t e = launch_pdl(k_sigma1<CT>, grid, dim3(RB), 0, st, g, c, w, sigma1, scratch, stats, ticket, r);
+  const NuRule r = rule ? *rule : NuRule{0.f, 0.f, 0.f, nullptr, nullptr, 0.0, 0.0, 0.0, nullptr};
+  cudaError_t e =
+      launch_pdl(k_sigma1<CT>, grid, dim3(RB), 0, st, g, c, w, sigma1, scratch, stats, ticket, r, sigma1d);
   count_launch();
   return e;
 }
 template cudaError_t launch_sigma1<double>(const GridDesc&, const Coef<double>&, const double*, float*,
-                                           double*, double*, unsigned*, cudaStream_t, const NuRule*);
+                                           double*, double*, unsigned*, cudaStream_t, const NuRule*, double*);
 template cudaError_t launch_sigma1<float>(const GridDesc&, const Coef<float>&, const float*, float*,
-                                          double*, double*, unsigned*, cudaStream_t, const NuRule*);
+                                          double*, double*, unsigned*, cudaStream_t, const NuRule*, double*);
 
 template <class CT>
 cudaError_t launch_label(const GridDesc& g, const Coef<CT>& c, const CT* w, const double* lam, float* acc,
@@ -895,6 +920,14 @@ cudaError_t launch_nu_rule(const GridDesc& g, const float* sigma1, double lambda
   const long long n = g.cells * g.batch;
   k_nu_rule<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, sigma1, (float)lambda, (float)tau,
                                                            (float)limit_nu, nu, err);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_nu_rule_f64(const GridDesc& g, const double* sigma1, double lambda, double tau,
+                               double limit_nu, double* nu, unsigned* err, cudaStream_t st) {
+  const long long n = g.cells * g.batch;
+  k_nu_rule_f64<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, sigma1, lambda, tau, limit_nu, nu, err);
   count_launch();
   return cudaGetLastError();
 }

@@ -48,6 +48,7 @@ struct AdjArgs {
   const TA* A;
   double ca;
   const float* nu;
+  const double* nud;      // FP64 nu (FP64 contexts), in place of nu
   double nus[3];          // viscosity factors of the rho, rho u, rho E adjoints
   const TST* lamf;
   const TST* Gin;
@@ -85,20 +86,26 @@ struct NuRule {
   float lam, tau, limit;
   float* nu;      // null: no viscosity output
   unsigned* err;
+  double lamd, taud, limitd;   // the same rule in FP64 (with nud)
+  double* nud;    // FP64 viscosity output (FP64 contexts, with an FP64 sigma_1 output)
 };
 
 // sigma_1 per cell; stats (may be null): [batch][2] = (max, mean), reduced by the last
 // block of each box (ticket: per-box counters, zero on entry and on exit); rule (may be
 // null): also writes the viscosity of the sigma_1 rule.
+// sigma1d (may be null; FP64 contexts): sigma_1 in FP64 in place of the float field,
+// with rule->nud the rule's FP64 viscosity.
 template <class CT>
 cudaError_t launch_sigma1(const GridDesc& g, const Coef<CT>& c, const CT* w, float* sigma1,
                           double* stats, double* scratch, unsigned* ticket, cudaStream_t st,
-                          const NuRule* rule = nullptr);
+                          const NuRule* rule = nullptr, double* sigma1d = nullptr);
 template <class CT>
 cudaError_t launch_label(const GridDesc& g, const Coef<CT>& c, const CT* w, const double* lam, float* acc,
                          cudaStream_t st);
 cudaError_t launch_nu_rule(const GridDesc& g, const float* sigma1, double lambda, double tau,
                            double limit_nu, float* nu, unsigned* err, cudaStream_t st);
+cudaError_t launch_nu_rule_f64(const GridDesc& g, const double* sigma1, double lambda, double tau,
+                               double limit_nu, double* nu, unsigned* err, cudaStream_t st);
 cudaError_t launch_visc_apply(const GridDesc& g, const double* idx2, const double* split,
                               const float* nu, const double* a, double* out, cudaStream_t st);
 cudaError_t launch_energy(const GridDesc& g, double gamma, double dV, const double* w,

@@ -46,6 +46,10 @@ extern "C" int ns_objective_noalloc(const ns_params* p, void* stream, const doub
                                     double* J_acc, double* lam) {
   if (!p || !w || !J_acc || lam == w) return NS_ERR_ARG;
   if (p->nx < 1 || p->ny < 1 || p->nz < 1 || p->batch < 1 || !(p->gamma > 1.0)) return NS_ERR_ARG;
+  // the size limits of ns_create (the kernels index a plane of faces with 32-bit ints)
+  if ((long long)p->nx * p->ny > (1LL << 31) || (long long)p->nx * p->ny * p->nz > (1LL << 40))
+    return NS_ERR_ARG;
+  if (p->plane_i <= -(1 << 30) || p->plane_i >= (1 << 30)) return NS_ERR_ARG;
   ns::GridDesc g{};
   g.nx = p->nx;
   g.ny = p->ny;
@@ -54,12 +58,17 @@ extern "C" int ns_objective_noalloc(const ns_params* p, void* stream, const doub
   g.plane = (long long)p->nx * p->ny;
   g.cells = g.plane * p->nz;
   if (ns::objective_scratch_doubles(g) > kErrOffset) return NS_ERR_BUDGET;
+  cudaStream_t st = (cudaStream_t)stream;
+  // the scratch address is the current device's: the stream must run on that device
+  int dev = 0, sdev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaStreamGetDevice(st, &sdev) != cudaSuccess) return NS_ERR_CUDA;
+  if (sdev != dev) return NS_ERR_ARG;
   double* scratch = nullptr;
   int r = scratch_on_current_device(&scratch);
   if (r) return r;
-  cudaStream_t st = (cudaStream_t)stream;
+  // the kernels OR their non-finite flag into this word; nothing reads it (a non-finite
+  // objective shows in J_acc itself), so it is never cleared
   unsigned* err = (unsigned*)(scratch + kErrOffset);
-  if (cudaMemsetAsync(err, 0, sizeof(unsigned), st) != cudaSuccess) return NS_ERR_CUDA;
   cudaError_t e = ns::launch_objective(g, p->gamma, p->plane_i, p->pt_in, w, weight, J_acc, lam, err,
                                        scratch, st);
   return e == cudaSuccess ? NS_OK : NS_ERR_CUDA;

@@ -32,45 +32,38 @@ constexpr int NT = TX * TY;
 constexpr int SY = TY + 2;
 constexpr int SP = SX * SY;
 
+// Field reads: element off of the field part that starts at element base (base: box,
+// plane and component, common to the CTA; off: the thread's in-plane offset).
 template <class CT, class TIN>
 struct Loader {
   const TIN* W;
   const double* Wd;
-  __device__ __forceinline__ CT ld(size_t o) const { return cvt<CT>(W[o]); }
+  __device__ __forceinline__ CT ld(size_t base, int off) const { return cvt<CT>((W + base)[off]); }
 };
 template <>
 struct Loader<Dual, double> {
   const double* W;
   const double* Wd;
-  __device__ __forceinline__ Dual ld(size_t o) const { return Dual(W[o], Wd[o]); }
+  __device__ __forceinline__ Dual ld(size_t base, int off) const {
+    return Dual((W + base)[off], (Wd + base)[off]);
+  }
 };
 
-// Load plane k (wrapped) of box b into one ring slot, converting to primitives
-// (rho, u1, u2, u3, e).
-template <class CT, class L>
-__device__ __forceinline__ void fill_plane(CT* __restrict__ sq, const GridDesc& g, int b, int k,
-                                           int x0, int y0, const L& in) {
-  const int kz = wrap(k, g.nz);
-  const size_t boxoff = (size_t)b * 5 * g.cells + (size_t)kz * g.plane;
-  for (int t = threadIdx.x; t < SP; t += NT) {
+// In-plane offsets, periodic wrap resolved, of this thread's two shared positions
+// t = tid and t = tid + NT (the same in every plane of the CTA's range).
+struct HaloOff {
+  int o[2];
+};
+__device__ __forceinline__ HaloOff halo_offsets(const GridDesc& g, int x0, int y0) {
+  HaloOff h;
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const int t = threadIdx.x + it * NT;
     const int ly = t / SX;
     const int lx = t - ly * SX;
-    const int gx = wrap(x0 + lx - 1, g.nx);
-    const int gy = wrap(y0 + ly - 1, g.ny);
-    const size_t o = boxoff + (size_t)gy * g.nx + gx;
-    const CT r = in.ld(o);
-    const CT m0 = in.ld(o + g.cells);
-    const CT m1 = in.ld(o + 2 * g.cells);
-    const CT m2 = in.ld(o + 3 * g.cells);
-    const CT E = in.ld(o + 4 * g.cells);
-    const CT ir = one_over(r);
-    const CT u0 = m0 * ir, u1 = m1 * ir, u2 = m2 * ir;
-    sq[0 * SP + t] = r;
-    sq[1 * SP + t] = u0;
-    sq[2 * SP + t] = u1;
-    sq[3 * SP + t] = u2;
-    sq[4 * SP + t] = E * ir - CT(0.5) * (u0 * u0 + u1 * u1 + u2 * u2);
+    h.o[it] = t < SP ? wrap(y0 + ly - 1, g.ny) * g.nx + wrap(x0 + lx - 1, g.nx) : 0;
   }
+  return h;
 }
 
 // Two-phase plane load used to overlap the next plane's global loads with the
@@ -83,19 +76,14 @@ struct PlaneRegs {
 };
 
 template <class CT, class L>
-__device__ __forceinline__ void plane_load(PlaneRegs<CT>& r, const GridDesc& g, int b, int k, int x0,
-                                           int y0, const L& in) {
-  const int kz = wrap(k, g.nz);
-  const size_t boxoff = (size_t)b * 5 * g.cells + (size_t)kz * g.plane;
+__device__ __forceinline__ void plane_load(PlaneRegs<CT>& r, const GridDesc& g, size_t boxoff, int k,
+                                           const HaloOff& h, const L& in) {
+  const size_t pb = boxoff + (size_t)wrap(k, g.nz) * g.plane;
 #pragma unroll
   for (int it = 0; it < 2; ++it) {
-    const int t = threadIdx.x + it * NT;
-    if (t < SP) {
-      const int ly = t / SX;
-      const int lx = t - ly * SX;
-      const size_t o = boxoff + (size_t)wrap(y0 + ly - 1, g.ny) * g.nx + wrap(x0 + lx - 1, g.nx);
+    if (threadIdx.x + it * NT < SP) {
 #pragma unroll
-      for (int v = 0; v < 5; ++v) r.v[it][v] = in.ld(o + v * g.cells);
+      for (int v = 0; v < 5; ++v) r.v[it][v] = in.ld(pb + v * (size_t)g.cells, h.o[it]);
     }
   }
 }
@@ -266,34 +254,58 @@ __global__ void __launch_bounds__(NT, RhsMinBlocks<CT, ROE>::value) k_rhs_stage(
   march_range<TX, TY>(g, b, x0, y0, kz0, kz1);
   const int gx = x0 + tx, gy = y0 + ty;
   const bool valid = gx < g.nx && gy < g.ny;
+  const int cp = valid ? gy * g.nx + gx : 0;        // the thread's cell within a plane
+  const size_t boxoff = (size_t)b * 5 * g.cells;
+  const HaloOff h = halo_offsets(g, x0, y0);
 
-  auto slot = [&](int k) { return (k - kz0 + 1) % 3; };
-  fill_plane<CT>(sQ + slot(kz0 - 1) * 5 * SP, g, b, kz0 - 1, x0, y0, in);
-  fill_plane<CT>(sQ + slot(kz0) * 5 * SP, g, b, kz0, x0, y0, in);
-  fill_plane<CT>(sQ + slot(kz0 + 1) * 5 * SP, g, b, kz0 + 1, x0, y0, in);
+  // ring slots: plane k-1, k, k+1 sit in slots (k-kz0) % 3, (k-kz0+1) % 3, (k-kz0+2) % 3
+  {
+    PlaneRegs<CT> p0, p1, p2;
+    plane_load(p0, g, boxoff, kz0 - 1, h, in);
+    plane_load(p1, g, boxoff, kz0, h, in);
+    plane_load(p2, g, boxoff, kz0 + 1, h, in);
+    plane_store(p0, sQ);
+    plane_store(p1, sQ + 5 * SP);
+    plane_store(p2, sQ + 2 * 5 * SP);
+  }
   __syncthreads();
   const int ic = (ty + 1) * SX + (tx + 1);
   CT zlo[5], zhi[5];
-  zface<ROE>(sQ, c, slot(kz0 - 1), slot(kz0), ic, zlo);
+  zface<ROE>(sQ, c, 0, 1, ic, zlo);
 
-  for (int k = kz0; k < kz1; ++k) {
-    const int sm = slot(k - 1), s0 = slot(k), sp = slot(k + 1);
+  // the march: at plane k the ring slots of planes k-1, k, k+1 are sm, s0, sp (sm = j
+  // cycles 0, 1, 2).  A loop unrolled over the three rotations, with the slots as
+  // compile-time constants, needs more registers than the 80 this kernel is held to and
+  // measured slower.
+  for (int k = kz0, j = 0; k < kz1; ++k, j = (j == 2 ? 0 : j + 1)) {
+    const int sm = j, s0 = (sm + 1) % 3, sp = (sm + 2) % 3;
     const bool more = k + 1 < kz1;
     PlaneRegs<CT> pf;
-    if (more) plane_load(pf, g, b, k + 2, x0, y0, in);
-    const size_t o0 = (size_t)b * 5 * g.cells + (size_t)k * g.plane + (size_t)gy * g.nx + gx;
+    if (more) plane_load(pf, g, boxoff, k + 2, h, in);
+    const size_t pb = boxoff + (size_t)k * g.plane;   // component 0 of plane k
     // epilogue operands of this plane, issued before the face fluxes so that their
     // latency overlaps the flux arithmetic (scalar path)
     CT e_src[5], e_dacc[5], e_base[5];
-    double e_wbase[5];
     if constexpr (!std::is_same<CT, Dual>::value) {
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
-        const size_t o = o0 + (size_t)v * g.cells;
-        e_src[v] = (valid && a.src) ? cvt<CT>(a.src[o]) : CT(0);
-        e_dacc[v] = (valid && a.dacc && !a.dacc_init) ? CT(a.dacc[o]) : CT(0);
-        e_base[v] = (valid && a.Wout) ? CT(a.base[o]) : CT(0);
-        e_wbase[v] = (valid && a.wout && a.wbase) ? a.wbase[o] : 0.0;
+        e_src[v] = CT(0);
+        e_dacc[v] = CT(0);
+        e_base[v] = CT(0);
+      }
+      if (valid) {
+        if (a.src) {
+#pragma unroll
+          for (int v = 0; v < 5; ++v) e_src[v] = cvt<CT>((a.src + pb + v * (size_t)g.cells)[cp]);
+        }
+        if (a.dacc && !a.dacc_init) {
+#pragma unroll
+          for (int v = 0; v < 5; ++v) e_dacc[v] = CT((a.dacc + pb + v * (size_t)g.cells)[cp]);
+        }
+        if (a.Wout) {
+#pragma unroll
+          for (int v = 0; v < 5; ++v) e_base[v] = CT((a.base + pb + v * (size_t)g.cells)[cp]);
+        }
       }
     }
     {
@@ -320,18 +332,22 @@ __global__ void __launch_bounds__(NT, RhsMinBlocks<CT, ROE>::value) k_rhs_stage(
     }
     __syncthreads();
     // the epilogue reads only the face fluxes: plane k+2 replaces plane k-1 in the ring now
-    if (more) plane_store(pf, sQ + slot(k + 2) * 5 * SP);
+    if (more) plane_store(pf, sQ + sm * 5 * SP);
     if (valid) {
+      CT R[5];
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
         const CT fxp = sFX[(v * TY + ty) * (TX + 1) + tx + 1];
         const CT fxm = sFX[(v * TY + ty) * (TX + 1) + tx];
         const CT fyp = sFY[(v * (TY + 1) + ty + 1) * TX + tx];
         const CT fym = sFY[(v * (TY + 1) + ty) * TX + tx];
-        const CT R = -((fxp - fxm) * c.idx[0] + (fyp - fym) * c.idx[1] + (zhi[v] - zlo[v]) * c.idx[2]);
-        const size_t o = o0 + (size_t)v * g.cells;
-        if constexpr (std::is_same<CT, Dual>::value) {
-          double Rv = R.v, Rd = R.d;
+        R[v] = -((fxp - fxm) * c.idx[0] + (fyp - fym) * c.idx[1] + (zhi[v] - zlo[v]) * c.idx[2]);
+      }
+      if constexpr (std::is_same<CT, Dual>::value) {
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+          const size_t o = pb + v * (size_t)g.cells + cp;
+          double Rv = R[v].v, Rd = R[v].d;
           if (a.src) Rv += a.src[o];
           if (a.srcd) Rd += a.srcd[o];
           const double iv = a.cacc * Rv, id = a.cacc * Rd;
@@ -345,18 +361,40 @@ __global__ void __launch_bounds__(NT, RhsMinBlocks<CT, ROE>::value) k_rhs_stage(
             a.Wout[o] = a.base[o] + a.cout * Rv + a.cd * dv;
             if (a.Woutd) a.Woutd[o] = a.based[o] + a.cout * Rd + a.cd * dd;
           }
-        } else {
-          const CT Rv = R + e_src[v];
-          const CT inc = CT(a.cacc) * Rv;
-          const CT dv = e_dacc[v] + inc;
-          if (a.wout) {
-            const double wv = e_wbase[v] + widen(dv);
-            a.wout[o] = wv;
-            if (a.wout_mirror) a.wout_mirror[o] = cvt<TST>(wv);
-          } else if (a.dacc) {
-            a.dacc[o] = dv;
+        }
+      } else {
+        CT Rv[5], dv[5];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+          Rv[v] = R[v] + e_src[v];
+          const CT inc = CT(a.cacc) * Rv[v];
+          dv[v] = e_dacc[v] + inc;
+        }
+        if (a.wout) {
+          double e_wbase[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+          if (a.wbase) {
+#pragma unroll
+            for (int v = 0; v < 5; ++v) e_wbase[v] = (a.wbase + pb + v * (size_t)g.cells)[cp];
           }
-          if (a.Wout) a.Wout[o] = e_base[v] + CT(a.cout) * Rv + CT(a.cd) * dv;
+          if (a.wout_mirror) {
+#pragma unroll
+            for (int v = 0; v < 5; ++v) {
+              const double wv = e_wbase[v] + widen(dv[v]);
+              (a.wout + pb + v * (size_t)g.cells)[cp] = wv;
+              (a.wout_mirror + pb + v * (size_t)g.cells)[cp] = cvt<TST>(wv);
+            }
+          } else {
+#pragma unroll
+            for (int v = 0; v < 5; ++v) (a.wout + pb + v * (size_t)g.cells)[cp] = e_wbase[v] + widen(dv[v]);
+          }
+        } else if (a.dacc) {
+#pragma unroll
+          for (int v = 0; v < 5; ++v) (a.dacc + pb + v * (size_t)g.cells)[cp] = dv[v];
+        }
+        if (a.Wout) {
+#pragma unroll
+          for (int v = 0; v < 5; ++v)
+            (a.Wout + pb + v * (size_t)g.cells)[cp] = e_base[v] + CT(a.cout) * Rv[v] + CT(a.cd) * dv[v];
         }
       }
     }

@@ -251,7 +251,9 @@ Layout layout_for(const ns_ctx* c, int slots_used, bool closure, int schedule, i
   L.state = align256(c->field * sizeof(double));
   L.lam = L.state;
   const size_t cellsb = (size_t)c->g.cells * c->g.batch;
-  L.sig = align256(cellsb * sizeof(float));
+  // sigma_1 and nu: FP64 in FP64 contexts with the sigma_1 rule, float otherwise
+  const size_t ssz = c->p.precision == NS_FP64 && !closure ? sizeof(double) : sizeof(float);
+  L.sig = align256(cellsb * ssz);
   L.nu = L.sig;
   L.scal = align256((size_t)c->g.batch * sizeof(double) * 2);
   L.feat = closure ? align256(cellsb * 16 * sizeof(float)) : 0;
@@ -311,6 +313,7 @@ struct ns_sweep_state {
   double* lamA = nullptr;
   float* sig = nullptr;
   float* nu = nullptr;
+  bool f64nu = false;                // sigma_1 and nu held in FP64 (the regions hold doubles)
   double* jtmp = nullptr;
   float* feat = nullptr;
   double* Jbar = nullptr;
@@ -478,7 +481,15 @@ int run_actions(ns_ctx* c, ns_sweep_state& S, int stop_op, double*& lam_cur, dou
           if (S.mixed) mirror = E[0];
         }
         const float* nup = nullptr;
-        if (need_sigma) {
+        const double* nudp = nullptr;
+        if (need_sigma && S.f64nu) {
+          double* stats = S.o.record_sigma && sigma_stats ? sigma_stats + (size_t)A.a * 2 * B : nullptr;
+          const bool rule = S.o.lambda > 0.0;
+          if ((r = ns_i_sigma1_f64(c, ptr(S.cur), (double*)S.sig, stats, S.o.lambda, S.o.tau,
+                                   rule ? (double*)S.nu : nullptr)))
+            return r;
+          if (rule) nudp = (const double*)S.nu;
+        } else if (need_sigma) {
           double* stats = S.o.record_sigma && sigma_stats ? sigma_stats + (size_t)A.a * 2 * B : nullptr;
           // the sigma_1 rule's viscosity comes out of the same launch as sigma_1
           const bool rule = !S.o.mlp && S.o.lambda > 0.0;
@@ -493,7 +504,7 @@ int run_actions(ns_ctx* c, ns_sweep_state& S, int stop_op, double*& lam_cur, dou
           }
         }
         if ((r = ns_i_adjoint(c, ptr(S.cur), mirror, kept ? kept3 : nullptr, S.s, lam_cur,
-                              S.lamf_valid ? S.lamf_cur : nullptr, nup, lam_nxt, S.lamf_nxt, sbar)))
+                              S.lamf_valid ? S.lamf_cur : nullptr, nup, lam_nxt, S.lamf_nxt, sbar, nudp)))
           return r;
         std::swap(lam_cur, lam_nxt);
         std::swap(S.lamf_cur, S.lamf_nxt);
@@ -521,6 +532,7 @@ static int forward_run_impl(ns_ctx* c, const double* w0, const double* s, const 
   if (((uintptr_t)arena & 255) != 0) return NS_ERR_ARG;
   if (!(o->lambda >= 0.0)) return NS_ERR_ARG;
   ns_sweep_release(c);
+  c->pending_gen = 0;
   ns_sweep_state* S = new ns_sweep_state();
   int r = make_plan(o->nsteps, o->schedule, o->param, S->P);
   if (r) {
@@ -567,6 +579,7 @@ static int forward_run_impl(ns_ctx* c, const double* w0, const double* s, const 
   S->has_mirror.assign(S->L.nkeep, 0);
   S->has_stages.assign(S->L.nkeep, 0);
   S->mixed = c->p.precision == NS_MIXED;
+  S->f64nu = !S->mixed && o->mlp == nullptr;
   S->slot_buf.assign(std::max(S->P.maxlive, 1), -1);
   S->owned.assign(S->L.nbuf, 0);
   c->sweep = S;
@@ -577,6 +590,7 @@ static int forward_run_impl(ns_ctx* c, const double* w0, const double* s, const 
   r = run_actions(c, *S, NS_OP_SOURCE, dummy, dummy, nullptr, nullptr, nullptr);
   if (r) return r;
   S->forward_done = true;
+  c->pending_gen = ++c->sweep_gen;
   return NS_OK;
 }
 
@@ -597,6 +611,7 @@ int ns_backward_run(ns_ctx* c, double* lam0, double* sbar, double* energy, doubl
   if (sbar && cudaMemsetAsync(sbar, 0, fbytes, c->st) != cudaSuccess) return NS_ERR_CUDA;
   S.lamf_valid = false;
   S.forward_done = false;   // a plan is reversed once
+  c->pending_gen = 0;
   S.in_backward = true;
   int r = run_actions(c, S, 0, lam_cur, lam_nxt, sbar, energy, sigma_stats);
   if (r) return r;
@@ -622,5 +637,7 @@ int ns_adjoint_run(ns_ctx* c, const double* w0, const double* s, const ns_run_op
              ? NS_OK
              : NS_ERR_CUDA;
 }
+
+long long ns_sweep_generation(const ns_ctx* c) { return c ? c->pending_gen : 0; }
 
 }  // extern "C"

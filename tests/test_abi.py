@@ -78,3 +78,25 @@ def test_host_arena_must_be_contiguous_host_memory():
     assert api._host_ptr(t).value == t.data_ptr()
     with pytest.raises(ValueError):
         api._host_ptr(torch.empty((8, 8), dtype=torch.uint8).t())
+
+
+def test_size_and_plane_checks_without_gpu():
+    """ns_create and ns_objective_noalloc refuse grids beyond the kernels' 32-bit plane
+    indexing and objective planes whose index arithmetic could overflow, before any CUDA
+    call."""
+    from paper_1511_06959_gb300 import api
+    lib = api.load_library(_lib_path())
+    f = lib.ns_objective_noalloc
+    f.argtypes = [ctypes.POINTER(api.NsParams), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
+                  ctypes.c_void_p, ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    ctx = ctypes.c_void_p()
+    dummy = ctypes.c_void_p(256)
+    big = api.NsParams(1 << 16, 1 << 16, 1, 1, 0.1, 0.1, 0.1, 1.4, 0.0, 0.72, 0.0, 0, 6, 1.0)
+    assert lib.ns_create(ctypes.byref(big), None, ctypes.byref(ctx)) == api.NS_ERR_ARG
+    assert f(ctypes.byref(big), None, dummy, 1.0, dummy, None) == api.NS_ERR_ARG
+    far = api.NsParams(8, 4, 2, 1, 0.1, 0.1, 0.1, 1.4, 0.0, 0.72, 0.0, 0, 1 << 30, 1.0)
+    assert lib.ns_create(ctypes.byref(far), None, ctypes.byref(ctx)) == api.NS_ERR_ARG
+    assert f(ctypes.byref(far), None, dummy, 1.0, dummy, None) == api.NS_ERR_ARG
+    far.plane_i = -(1 << 30)
+    assert f(ctypes.byref(far), None, dummy, 1.0, dummy, None) == api.NS_ERR_ARG

@@ -104,3 +104,27 @@ def test_mixed_precision_gradients_close_to_fp64():
     assert rel_l2(host(J32), host(J64)) < 1e-6
     assert rel_l2(host(gw32), host(gw64)) < 1e-4
     assert rel_l2(host(gth32), host(gth64)) < 1e-4
+
+
+def test_backward_of_a_replaced_forward_raises():
+    """Two losses on one solver: the second forward replaces the first's checkpoints, so
+    the first loss's backward must raise instead of reversing the second trajectory; the
+    second loss's backward still matches the oracle, and a second backward of it raises."""
+    api, prob, ws, P, phi = _setup()
+    theta_a = np.zeros(64)
+    theta_b = 0.05 * np.random.default_rng(4).standard_normal(64)
+    w_a = dev(ws).requires_grad_(True)
+    w_b = dev(ws).requires_grad_(True)
+    J_a = prob(w_a, dev(theta_a))
+    J_b = prob(w_b, dev(theta_b).requires_grad_(True))
+    with pytest.raises(RuntimeError, match="no longer hold"):
+        torch.sum(J_a).backward()
+    L_b = torch.sum(J_b)
+    L_b.backward(retain_graph=True)
+    s = np.zeros_like(ws[0])
+    s[1] = np.tensordot(theta_b, phi, axes=1)
+    traj, _ = O.primal_run(ws[0], P, N, s)
+    lam, _ = O.adjoint_run(traj, P, s)
+    assert rel_l2(host(w_b.grad[0]), lam) < 1e-10
+    with pytest.raises(RuntimeError, match="no longer hold"):
+        L_b.backward()

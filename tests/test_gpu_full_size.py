@@ -50,7 +50,8 @@ def test_step_objective_and_stabilised_adjoint_step(box, prec):
     J = torch.zeros(1, dtype=torch.float64, device="cuda")
     S.objective(dev(w1_ref), J, 1.0)          # FP64 in both modes: the same input
     assert abs(J.item() - J_ref) <= 1e-12 * abs(J_ref)
-    sig = torch.empty(w.shape[1:], dtype=torch.float32, device="cuda")
+    # sigma_1 and nu in FP64 in the FP64 context (the _f64 entry points), FP32 in mixed
+    sig = torch.empty(w.shape[1:], dtype=torch.float64 if prec == 0 else torch.float32, device="cuda")
     S.growth_sigma1(wd, sig)
     nu = torch.empty_like(sig)
     S.add_adjoint_viscosity(sig, WL.lam_coef, nu)
@@ -58,5 +59,18 @@ def test_step_objective_and_stabilised_adjoint_step(box, prec):
     S.adjoint_step(wd, dev(lam), lo, nu=nu)
     S.objective(wd, torch.zeros(1, dtype=torch.float64, device="cuda"), 1.0 / WL.nsteps, lo)
     assert S.last_error() == 0
-    tol = 1e-6 if prec == 0 else 1e-4   # nu carries sigma_1 in FP32 in both modes
+    tol = 1e-10 if prec == 0 else 1e-4
     assert rel_l2(host(lo), lam0_ref) < tol
+    if prec == 0:
+        np.testing.assert_allclose(host(sig), O.sigma1_field(w, P), rtol=1e-12, atol=1e-12 * abs(host(sig)).max())
+
+
+def test_f64_entry_points_refuse_a_mixed_context(box):
+    api, w, P, *_ = box
+    S = _solver(api, P, 1)
+    wd = dev(w)
+    sig = torch.empty(w.shape[1:], dtype=torch.float64, device="cuda")
+    with pytest.raises(api.NsError):
+        S.growth_sigma1(wd, sig)
+    with pytest.raises(api.NsError):
+        S.adjoint_step(wd, wd.clone(), torch.empty_like(wd), nu=sig)

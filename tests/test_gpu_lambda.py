@@ -42,11 +42,11 @@ def test_estimate_matches_oracle(prec):
     arena, work = _buffers(S, opts)
     chosen, ef, ch = S.estimate_lambda(dev(w0), opts, lambdas, arena, work, s=dev(s), efold_tol=1.0, rel_tol=0.1)
     assert S.last_error() == 0
-    # nu carries sigma_1 in FP32 in both modes, so each sbar is off by about 1e-10
-    # relative in FP64 mode (FP32 products: about 1e-5 in mixed mode); the change is a
-    # difference of two sbar fields over the norm of one, which divides that error by the
-    # change itself (0.008-0.03 here)
-    ef_tol, ch_tol = (1e-9, 1e-6) if prec == 0 else (1e-4, 2e-2)
+    # FP64 mode keeps sigma_1 and nu in FP64 (each sbar to roundoff); mixed mode's FP32
+    # products leave about 1e-5 relative in each sbar, and the change is a difference of
+    # two sbar fields over the norm of one, which divides that error by the change itself
+    # (0.008-0.03 here)
+    ef_tol, ch_tol = (1e-9, 1e-10) if prec == 0 else (1e-4, 2e-2)
     np.testing.assert_allclose(ef, ef_ref, rtol=0, atol=ef_tol)
     np.testing.assert_allclose(ch, ch_ref, rtol=ch_tol, atol=1e-12)
     # the choice is unique where no value sits within the tolerance of a threshold
@@ -80,7 +80,7 @@ def test_batch_takes_the_worst_box_and_pools_the_norms():
     for i in range(len(lambdas) - 1):
         d2 = sum(np.sum((r[3][i + 1] - r[3][i]) ** 2) for r in refs)
         n2 = sum(np.sum(r[3][i + 1] ** 2) for r in refs)
-        assert ch[i] == pytest.approx(math.sqrt(d2) / math.sqrt(n2), rel=1e-6)   # FP32 nu, as above
+        assert ch[i] == pytest.approx(math.sqrt(d2) / math.sqrt(n2), rel=1e-10)   # FP64 nu, as above
     assert chosen == O.select_lambda(ef_ref, ch, 1.0, 0.1)
 
 

@@ -64,7 +64,8 @@ def test_stabilised_sweep_energy_and_sigma_series():
     ws, Jref = O.primal_run(w0, P, N)
     nu_of = lambda w: lam_coef * O.sigma1_field(w, P)
     lam_ref, _ = O.adjoint_run(ws, P, None, nu_of)
-    assert rel_l2(host(lam), lam_ref) < 1e-6
+    # FP64 context: sigma_1 and nu are carried in FP64 through the sweep
+    assert rel_l2(host(lam), lam_ref) < 1e-10
     # energy series E(w^n, lam^n): recompute lam^n with the oracle sweep
     lam_n = np.zeros_like(w0)
     Eref = np.zeros(N + 1)
@@ -75,10 +76,10 @@ def test_stabilised_sweep_energy_and_sigma_series():
         if n - 1 >= 1:
             lam_n = lam_n + O.objective_grad(ws[n - 1], P) / N
         Eref[n - 1] = O.adjoint_energy(ws[n - 1], lam_n, P)
-    np.testing.assert_allclose(host(E)[:, 0], Eref, rtol=1e-6)
+    np.testing.assert_allclose(host(E)[:, 0], Eref, rtol=1e-10)
     sig_ref = np.array([[O.sigma1_field(ws[n], P).max(), O.sigma1_field(ws[n], P).mean()]
                         for n in range(N)])
-    np.testing.assert_allclose(host(st)[:, 0, :], sig_ref, rtol=1e-6)
+    np.testing.assert_allclose(host(st)[:, 0, :], sig_ref, rtol=1e-10)
 
 
 def test_budget_too_small_is_reported():
