@@ -463,6 +463,88 @@ int ns_label_target(ns_ctx* ctx, const float* acc, const float* sigma1, double t
 int ns_last_error(ns_ctx* ctx);
 const char* ns_error_string(int code);
 
+/* ------------------------------------------------------------------------------
+ * Bounded boxes: characteristic (non-reflecting) inflow at x = 0 and outflow at
+ * x = L_x (section "Numerical methods": non-reflecting inlet and outlet; section
+ * "Energy analysis": the incoming characteristics are set there) and isothermal
+ * no-slip walls at y = 0 and y = L_y (the vane surface is isothermal, section "Problem
+ * setup"); z stays periodic.  The paper gives no discrete form; here each boundary has
+ * one ghost layer:
+ *  - inflow/outflow ghost columns hold the boundary state of the x-direction Riemann
+ *    invariants R+- = u1 +- 2c/(gamma-1): at the outflow R+, the entropy p/rho^gamma
+ *    and the tangential velocity from the adjacent cell and R- from the far field; at
+ *    the inflow R- from the adjacent cell and the rest from the far field;
+ *  - wall ghost rows hold the adjacent cell's density, its momentum reversed and the
+ *    internal energy 2 e_w - e (zero face velocity, the wall's face temperature),
+ *    built over the ghost columns, so a corner is the wall's ghost of the inflow or
+ *    outflow ghost.
+ * The residual is the periodic residual of the padded box, cropped; the adjoint is its
+ * exact transpose (the ghosts' Jacobians pulled back); the added adjoint viscosity
+ * passes no flux through boundary faces; sigma_1 uses the ghosts.  Fields stay
+ * unpadded [batch][5][nz][ny][nx]: the context pads and crops internally.
+ * ---------------------------------------------------------------------------- */
+#define NS_BC_PERIODIC 0
+#define NS_BC_INOUT 1        /* characteristic inflow and outflow in x */
+#define NS_BC_WALLS 2        /* isothermal no-slip walls in y */
+#define NS_BC_INOUT_WALLS 3  /* both */
+/* Set the boundaries of a context.  far: the far-field primitive state (rho, u1, u2, u3,
+ * p) of the characteristic conditions (rho, p > 0; needed with inflow/outflow);
+ * wall_e: the internal energy e = c_v T of the bottom and the top wall (> 0; needed
+ * with walls).  Allocates the padded workspace (NS_ERR_CUDA on failure); synchronises
+ * the context's stream.  On a bounded context ns_rhs, ns_rhs_transpose,
+ * ns_primal_step, ns_adjoint_step(_f64), ns_growth_sigma1(_f64) (stats NULL),
+ * ns_objective (a plane inside the box), ns_add_adjoint_viscosity(_f64),
+ * ns_adjoint_energy and ns_max_wave_speed apply; the tangent calls, the checkpointed
+ * sweeps, ns_apply_adjoint_viscosity, the closure's features and label and slab groups
+ * return NS_ERR_ARG.  NS_BC_PERIODIC restores the periodic box. */
+int ns_set_boundaries(ns_ctx* ctx, int bc, const double* far, const double* wall_e);
+
+/* ------------------------------------------------------------------------------
+ * x-slab decomposition (section "Numerical methods": the paper's solver splits its
+ * domain over MPI ranks).  A box of NX columns is cut into slabs along x; slab k is
+ * held by its own context as a padded box of nx_k = (its interior columns) + 2 cells in
+ * x: columns 0 and nx_k - 1 are ghost columns that hold the neighbouring slabs'
+ * boundary columns, and the slabs are periodic as a whole (slab 0's left neighbour is
+ * the last slab).  With ghosts current, every call of a context on its padded slab
+ * (residual, transpose, sigma_1, ...) gives the unsplit box's values in the interior
+ * columns, because the discrete residual and its transpose reach one cell in x; the
+ * group calls below run the Runge-Kutta stages of all slabs in turn and exchange each
+ * stage's output field between them, so that the interior columns of a step or an
+ * adjoint step equal the unsplit box's bit for bit.  Ghost-column values of outputs
+ * are those of the neighbours after each call.  Reductions are per slab: a slab's
+ * objective needs the plane's two columns in its interior, and sums over slabs (J, the
+ * adjoint energy) are the caller's (for several processes an allreduce).
+ * ---------------------------------------------------------------------------- */
+typedef struct ns_slab_group ns_slab_group;
+/* Host exchange of one slab's ghost columns for a group of one slab per process:
+ * field is the slab's device field [batch][ncomp][nz][ny][nx] of elem_bytes-byte
+ * values; the function fills columns 0 and nx-1 from the neighbouring processes' columns
+ * nx-2 (left neighbour) and 1 (right neighbour) in stream order on the slab context's
+ * stream and returns 0, or nonzero on failure. */
+typedef int (*ns_halo_exchange_fn)(void* user, void* field, int elem_bytes, int ncomp);
+/* slabs: n contexts, left to right, on padded slabs (nx >= 3) with the same ny, nz,
+ * batch, precision, scheme, flux, cell sizes, dt and fluid constants (else NS_ERR_ARG).
+ * Each may have its own stream (and device): exchanges order the streams with events.
+ * The group keeps the context pointers; destroy it before its contexts. */
+int ns_slab_group_create(ns_ctx* const* slabs, int n, ns_slab_group** out);
+void ns_slab_group_destroy(ns_slab_group* group);
+/* Replace the in-process exchange (one strided device copy per ghost column) with a
+ * host function, for a group of exactly one slab whose neighbours live in other
+ * processes (NS_ERR_ARG otherwise); fn = NULL restores the in-process exchange. */
+int ns_slab_set_exchange(ns_slab_group* group, ns_halo_exchange_fn fn, void* user);
+/* Fill the ghost columns of fields[k] (device, slab k, elem_bytes 4 or 8, ncomp
+ * components) from the neighbouring slabs. */
+int ns_slab_exchange(ns_slab_group* group, void* const* fields, int elem_bytes, int ncomp);
+/* One step (ns_primal_step) of every slab: w[k] -> wo[k], s NULL or one source per
+ * slab; w's ghost columns must be current; wo's are current on return. */
+int ns_slab_primal_step(ns_slab_group* group, const double* const* w, const double* const* s,
+                        double* const* wo);
+/* One adjoint step (ns_adjoint_step without sbar) of every slab: lam[k] -> lo[k]; w,
+ * lam and nu (NULL, or one float field per slab) must have current ghost columns; lo's
+ * are current on return. */
+int ns_slab_adjoint_step(ns_slab_group* group, const double* const* w, const double* const* s,
+                         const double* const* lam, const float* const* nu, double* const* lo);
+
 /* Measured arithmetic peak of the current device: the rate of independent fused
  * multiply-adds (2 flops each) of kind NS_PEAK_FP32 (scalar FFMA), NS_PEAK_FP32X2 (the
  * paired FP32 instruction) or NS_PEAK_FP64, in flop/s, from CUDA events around a

@@ -26,6 +26,10 @@ NS_RK4 = 0
 NS_SSPRK3 = 1
 NS_FLUX_CENTRAL = 0
 NS_FLUX_ROE = 1
+NS_BC_PERIODIC = 0
+NS_BC_INOUT = 1
+NS_BC_WALLS = 2
+NS_BC_INOUT_WALLS = 3
 NS_PEAK_FP32 = 0
 NS_PEAK_FP32X2 = 1
 NS_PEAK_FP64 = 2
@@ -42,6 +46,8 @@ EXPORTED = [
     "ns_launch_count", "ns_set_viscosity_split", "ns_energy_efolds", "ns_lambda_select",
     "ns_estimate_work_bytes", "ns_estimate_lambda", "ns_run_host_bytes", "ns_measure_fma_peak",
     "ns_sweep_generation", "ns_growth_sigma1_f64", "ns_add_adjoint_viscosity_f64", "ns_adjoint_step_f64",
+    "ns_slab_group_create", "ns_slab_group_destroy", "ns_slab_set_exchange", "ns_slab_exchange",
+    "ns_slab_primal_step", "ns_slab_adjoint_step", "ns_set_boundaries",
 ]
 
 NS_MLP_PARAMS = 5185
@@ -76,6 +82,10 @@ class NsRunOpts(ctypes.Structure):
         ("record_sigma", ctypes.c_int), ("mlp", ctypes.c_void_p), ("host_arena", ctypes.c_void_p),
         ("host_bytes", ctypes.c_size_t),
     ]
+
+
+# host ghost-column exchange of a one-slab group (ns_halo_exchange_fn)
+HALO_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int)
 
 
 class NsError(RuntimeError):
@@ -140,6 +150,14 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "ns_growth_sigma1_f64": ([P, P, P, P], I),
         "ns_add_adjoint_viscosity_f64": ([P, P, D, D, P], I),
         "ns_adjoint_step_f64": ([P, P, P, P, P, P, P], I),
+        "ns_set_boundaries": ([P, I, ctypes.POINTER(D), ctypes.POINTER(D)], I),
+        "ns_slab_group_create": ([ctypes.POINTER(P), I, ctypes.POINTER(P)], I),
+        "ns_slab_group_destroy": ([P], None),
+        "ns_slab_set_exchange": ([P, HALO_FN, P], I),
+        "ns_slab_exchange": ([P, ctypes.POINTER(P), I, I], I),
+        "ns_slab_primal_step": ([P, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P)], I),
+        "ns_slab_adjoint_step": ([P, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P),
+                                  ctypes.POINTER(P)], I),
         "ns_set_viscosity_split": ([P, ctypes.POINTER(ctypes.c_double)], I),
         "ns_plan": ([I, I, I, P, I, ctypes.POINTER(I), ctypes.POINTER(I),
                      ctypes.POINTER(ctypes.c_longlong)], I),
@@ -213,6 +231,16 @@ def _ptr(t, dtype=None):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _sized(t, dtype, n, what):
+    """_ptr of a tensor that must hold at least n elements (the library writes or reads n
+    of them through the raw pointer), or None for None."""
+    if t is None:
+        return None
+    if t.numel() < n:
+        raise ValueError(f"{what}: {t.numel()} elements, the call uses {n}")
+    return _ptr(t, dtype)
+
+
 def _host_ptr(t):
     """Address of a contiguous CPU tensor (host memory for the library), or None."""
     if t is None:
@@ -249,6 +277,16 @@ class Solver:
         _check(self.lib.ns_create(ctypes.byref(self.params), ctypes.c_void_p(st.cuda_stream),
                                   ctypes.byref(self._ctx)), "ns_create")
 
+    # size-checked device pointers: a 5-component field, a scalar field, one value per box
+    def _F(self, t, dtype=torch.float64):
+        return _sized(t, dtype, self.batch * 5 * self.cells, "field")
+
+    def _S(self, t, dtype=torch.float32):
+        return _sized(t, dtype, self.batch * self.cells, "scalar field")
+
+    def _B(self, t, per_box=1):
+        return _sized(t, torch.float64, self.batch * per_box, "per-box array")
+
     def close(self):
         if self._ctx:
             self.lib.ns_destroy(self._ctx)
@@ -276,74 +314,74 @@ class Solver:
 
     # --- field operations -------------------------------------------------------
     def rhs(self, w, R, s=None):
-        _check(self.lib.ns_rhs(self._ctx, _ptr(w, torch.float64), _ptr(s, torch.float64),
-                               _ptr(R, torch.float64)), "ns_rhs")
+        _check(self.lib.ns_rhs(self._ctx, self._F(w), self._F(s),
+                               self._F(R)), "ns_rhs")
 
     def rhs_tangent(self, w, wd, Rd):
-        _check(self.lib.ns_rhs_tangent(self._ctx, _ptr(w, torch.float64), _ptr(wd, torch.float64),
-                                       _ptr(Rd, torch.float64)), "ns_rhs_tangent")
+        _check(self.lib.ns_rhs_tangent(self._ctx, self._F(w), self._F(wd),
+                                       self._F(Rd)), "ns_rhs_tangent")
 
     def rhs_transpose(self, w, a, out, nu=None):
-        _check(self.lib.ns_rhs_transpose(self._ctx, _ptr(w, torch.float64), _ptr(a, torch.float64),
-                                         _ptr(nu, torch.float32), _ptr(out, torch.float64)),
+        _check(self.lib.ns_rhs_transpose(self._ctx, self._F(w), self._F(a),
+                                         self._S(nu), self._F(out)),
                "ns_rhs_transpose")
 
     def primal_step(self, w_in, w_out, s=None):
-        _check(self.lib.ns_primal_step(self._ctx, _ptr(w_in, torch.float64), _ptr(s, torch.float64),
-                                       _ptr(w_out, torch.float64)), "ns_primal_step")
+        _check(self.lib.ns_primal_step(self._ctx, self._F(w_in), self._F(s),
+                                       self._F(w_out)), "ns_primal_step")
 
     def tangent_step(self, w, wd_in, wd_out, s=None, sd=None):
-        _check(self.lib.ns_tangent_step(self._ctx, _ptr(w, torch.float64), _ptr(s, torch.float64),
-                                        _ptr(wd_in, torch.float64), _ptr(sd, torch.float64),
-                                        _ptr(wd_out, torch.float64)), "ns_tangent_step")
+        _check(self.lib.ns_tangent_step(self._ctx, self._F(w), self._F(s),
+                                        self._F(wd_in), self._F(sd),
+                                        self._F(wd_out)), "ns_tangent_step")
 
     def adjoint_step(self, w_n, lam_np1, lam_n, s=None, nu=None, sbar=None):
         """A float64 nu selects ns_adjoint_step_f64 (FP64 contexts), a float32 one (or
         None) ns_adjoint_step."""
         if nu is not None and nu.dtype == torch.float64:
-            _check(self.lib.ns_adjoint_step_f64(self._ctx, _ptr(w_n, torch.float64), _ptr(s, torch.float64),
-                                                _ptr(lam_np1, torch.float64), _ptr(nu, torch.float64),
-                                                _ptr(lam_n, torch.float64), _ptr(sbar, torch.float64)),
+            _check(self.lib.ns_adjoint_step_f64(self._ctx, self._F(w_n), self._F(s),
+                                                self._F(lam_np1), self._S(nu, torch.float64),
+                                                self._F(lam_n), self._F(sbar)),
                    "ns_adjoint_step_f64")
             return
-        _check(self.lib.ns_adjoint_step(self._ctx, _ptr(w_n, torch.float64), _ptr(s, torch.float64),
-                                        _ptr(lam_np1, torch.float64), _ptr(nu, torch.float32),
-                                        _ptr(lam_n, torch.float64), _ptr(sbar, torch.float64)),
+        _check(self.lib.ns_adjoint_step(self._ctx, self._F(w_n), self._F(s),
+                                        self._F(lam_np1), self._S(nu),
+                                        self._F(lam_n), self._F(sbar)),
                "ns_adjoint_step")
 
     def objective(self, w, J_acc, weight=1.0, lam=None):
-        _check(self.lib.ns_objective(self._ctx, _ptr(w, torch.float64), float(weight),
-                                     _ptr(J_acc, torch.float64), _ptr(lam, torch.float64)),
+        _check(self.lib.ns_objective(self._ctx, self._F(w), float(weight),
+                                     self._B(J_acc), self._F(lam)),
                "ns_objective")
 
     def growth_sigma1(self, w, sigma1, stats=None):
         """A float64 sigma1 selects ns_growth_sigma1_f64 (FP64 contexts)."""
         if sigma1.dtype == torch.float64:
-            _check(self.lib.ns_growth_sigma1_f64(self._ctx, _ptr(w, torch.float64), _ptr(sigma1, torch.float64),
-                                                 _ptr(stats, torch.float64)), "ns_growth_sigma1_f64")
+            _check(self.lib.ns_growth_sigma1_f64(self._ctx, self._F(w), self._S(sigma1, torch.float64),
+                                                 self._B(stats, 2)), "ns_growth_sigma1_f64")
             return
-        _check(self.lib.ns_growth_sigma1(self._ctx, _ptr(w, torch.float64), _ptr(sigma1, torch.float32),
-                                         _ptr(stats, torch.float64)), "ns_growth_sigma1")
+        _check(self.lib.ns_growth_sigma1(self._ctx, self._F(w), self._S(sigma1),
+                                         self._B(stats, 2)), "ns_growth_sigma1")
 
     def add_adjoint_viscosity(self, sigma1, lam_coef, nu, tau=0.0):
         """A float64 sigma1 selects ns_add_adjoint_viscosity_f64 (nu float64 too)."""
         if sigma1.dtype == torch.float64:
-            _check(self.lib.ns_add_adjoint_viscosity_f64(self._ctx, _ptr(sigma1, torch.float64), float(lam_coef),
-                                                         float(tau), _ptr(nu, torch.float64)),
+            _check(self.lib.ns_add_adjoint_viscosity_f64(self._ctx, self._S(sigma1, torch.float64), float(lam_coef),
+                                                         float(tau), self._S(nu, torch.float64)),
                    "ns_add_adjoint_viscosity_f64")
             return
-        _check(self.lib.ns_add_adjoint_viscosity(self._ctx, _ptr(sigma1, torch.float32), float(lam_coef),
-                                                 float(tau), _ptr(nu, torch.float32)),
+        _check(self.lib.ns_add_adjoint_viscosity(self._ctx, self._S(sigma1), float(lam_coef),
+                                                 float(tau), self._S(nu)),
                "ns_add_adjoint_viscosity")
 
     def apply_adjoint_viscosity(self, nu, a, out):
-        _check(self.lib.ns_apply_adjoint_viscosity(self._ctx, _ptr(nu, torch.float32),
-                                                   _ptr(a, torch.float64), _ptr(out, torch.float64)),
+        _check(self.lib.ns_apply_adjoint_viscosity(self._ctx, self._S(nu),
+                                                   self._F(a), self._F(out)),
                "ns_apply_adjoint_viscosity")
 
     def adjoint_energy(self, w, lam, E):
-        _check(self.lib.ns_adjoint_energy(self._ctx, _ptr(w, torch.float64), _ptr(lam, torch.float64),
-                                          _ptr(E, torch.float64)), "ns_adjoint_energy")
+        _check(self.lib.ns_adjoint_energy(self._ctx, self._F(w), self._F(lam),
+                                          self._B(E)), "ns_adjoint_energy")
 
     def dot(self, a, phi, out):
         nphi = phi.shape[0]
@@ -364,8 +402,14 @@ class Solver:
                "ns_to_float")
 
     def max_wave_speed(self, w, out):
-        _check(self.lib.ns_max_wave_speed(self._ctx, _ptr(w, torch.float64), _ptr(out, torch.float64)),
+        _check(self.lib.ns_max_wave_speed(self._ctx, self._F(w), _ptr(out, torch.float64)),
                "ns_max_wave_speed")
+
+    def set_boundaries(self, bc: int, far=None, wall_e=None):
+        """Characteristic inflow/outflow in x and/or isothermal walls in y
+        (ns_set_boundaries); far = (rho, u1, u2, u3, p), wall_e = (bottom, top)."""
+        _check(self.lib.ns_set_boundaries(self._ctx, int(bc), None if far is None else _doubles(far),
+                                          None if wall_e is None else _doubles(wall_e)), "ns_set_boundaries")
 
     def set_viscosity_split(self, f_rho: float, f_mom: float, f_en: float):
         arr = (ctypes.c_double * 3)(f_rho, f_mom, f_en)
@@ -399,11 +443,11 @@ class Solver:
                     sigma_stats=None):
         """Forward + checkpointed backward sweep; arena is a uint8 CUDA tensor of at least
         arena_bytes(opts) bytes."""
-        _check(self.lib.ns_adjoint_run(self._ctx, _ptr(w0, torch.float64), _ptr(s, torch.float64),
+        N = opts.nsteps
+        _check(self.lib.ns_adjoint_run(self._ctx, self._F(w0), self._F(s),
                                        ctypes.byref(opts), _ptr(arena), arena.numel() * arena.element_size(),
-                                       _ptr(Jbar, torch.float64), _ptr(lam0, torch.float64),
-                                       _ptr(sbar, torch.float64), _ptr(energy, torch.float64),
-                                       _ptr(sigma_stats, torch.float64)), "ns_adjoint_run")
+                                       self._B(Jbar), self._F(lam0), self._F(sbar), self._B(energy, N + 1),
+                                       self._B(sigma_stats, 2 * N)), "ns_adjoint_run")
 
     def estimate_work_bytes(self, opts) -> int:
         return int(self.lib.ns_estimate_work_bytes(self._ctx, ctypes.byref(opts)))
@@ -426,9 +470,10 @@ class Solver:
 
     def forward_run(self, w0, opts, arena, Jbar, s=None):
         """Forward half of the sweep (keeps the checkpoints in arena, accumulates Jbar)."""
-        _check(self.lib.ns_forward_run(self._ctx, _ptr(w0, torch.float64), _ptr(s, torch.float64),
+        _check(self.lib.ns_forward_run(self._ctx, self._F(w0), self._F(s),
                                        ctypes.byref(opts), _ptr(arena), arena.numel() * arena.element_size(),
-                                       _ptr(Jbar, torch.float64)), "ns_forward_run")
+                                       self._B(Jbar)), "ns_forward_run")
+        self._fwd_steps = opts.nsteps
 
     def sweep_generation(self) -> int:
         """Number of the forward sweep awaiting its backward, 0 if none (ns_sweep_generation)."""
@@ -436,8 +481,9 @@ class Solver:
 
     def backward_run(self, lam0, sbar=None, energy=None, sigma_stats=None):
         """Reverse half of the sweep with a unit seed on each box's Jbar."""
-        _check(self.lib.ns_backward_run(self._ctx, _ptr(lam0, torch.float64), _ptr(sbar, torch.float64),
-                                        _ptr(energy, torch.float64), _ptr(sigma_stats, torch.float64)),
+        N = getattr(self, "_fwd_steps", 0)
+        _check(self.lib.ns_backward_run(self._ctx, self._F(lam0), self._F(sbar),
+                                        self._B(energy, N + 1), self._B(sigma_stats, 2 * N)),
                "ns_backward_run")
 
     def scale_boxes(self, seed, field):
@@ -461,7 +507,7 @@ class Solver:
                "ns_mlp_get_moment")
 
     def mlp_features(self, w, feat):
-        _check(self.lib.ns_mlp_features(self._ctx, _ptr(w, torch.float64), _ptr(feat, torch.float32)),
+        _check(self.lib.ns_mlp_features(self._ctx, self._F(w), _sized(feat, torch.float32, 16 * self.batch * self.cells, "features")),
                "ns_mlp_features")
 
     def mlp_infer(self, net, feat, sigma1, kappa, nu):
@@ -474,8 +520,7 @@ class Solver:
                                           int(step), float(lr), _ptr(loss, torch.float32)), "ns_mlp_train_step")
 
     def adjoint_label(self, w, lam, acc):
-        _check(self.lib.ns_adjoint_label(self._ctx, _ptr(w, torch.float64), _ptr(lam, torch.float64),
-                                         _ptr(acc, torch.float32)), "ns_adjoint_label")
+        _check(self.lib.ns_adjoint_label(self._ctx, self._F(w), self._F(lam), self._S(acc)), "ns_adjoint_label")
 
     def label_target(self, acc, sigma1, t_max, target):
         _check(self.lib.ns_label_target(self._ctx, _ptr(acc, torch.float32), _ptr(sigma1, torch.float32),
@@ -506,3 +551,67 @@ def measure_fma_peak(kind: int) -> float:
     out = ctypes.c_double()
     _check(_lib().ns_measure_fma_peak(int(kind), ctypes.byref(out)), "ns_measure_fma_peak")
     return out.value
+
+
+def _ptr_array(tensors, dtype, sizes=None):
+    """A host array of device pointers (one per slab), or None; sizes: the elements the
+    call uses in each."""
+    if tensors is None:
+        return None
+    arr = (ctypes.c_void_p * len(tensors))()
+    for i, t in enumerate(tensors):
+        arr[i] = _ptr(t, dtype) if sizes is None else _sized(t, dtype, sizes[i], "slab field")
+    return arr
+
+
+class SlabGroup:
+    """x-slabs of one box, each a Solver over its padded slab (one ghost column per
+    side), stepped together with their ghost columns exchanged after every stage
+    (ns_slab_*)."""
+
+    def __init__(self, solvers, exchange=None):
+        self.lib = _lib()
+        self.solvers = list(solvers)
+        arr = (ctypes.c_void_p * len(self.solvers))(*[s._ctx for s in self.solvers])
+        g = ctypes.c_void_p()
+        _check(self.lib.ns_slab_group_create(arr, len(self.solvers), ctypes.byref(g)), "ns_slab_group_create")
+        self._g = g
+        self._fn = None
+        if exchange is not None:
+            # exchange(field_tensor_view_args) is called as exchange(ptr, elem_bytes, ncomp)
+            self._fn = HALO_FN(lambda user, field, eb, nc: int(exchange(field, eb, nc) or 0))
+            _check(self.lib.ns_slab_set_exchange(self._g, self._fn, None), "ns_slab_set_exchange")
+
+    def close(self):
+        if getattr(self, "_g", None):
+            self.lib.ns_slab_group_destroy(self._g)
+            self._g = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _sizes(self, ncomp):
+        return [s.batch * ncomp * s.cells for s in self.solvers]
+
+    def exchange(self, fields, ncomp):
+        if len(fields) != len(self.solvers):
+            raise ValueError("one field per slab")
+        eb = fields[0].element_size()
+        _check(self.lib.ns_slab_exchange(self._g, _ptr_array(fields, fields[0].dtype, self._sizes(ncomp)), eb,
+                                         ncomp), "ns_slab_exchange")
+
+    def primal_step(self, w, wo, s=None):
+        f = self._sizes(5)
+        _check(self.lib.ns_slab_primal_step(self._g, _ptr_array(w, torch.float64, f),
+                                            _ptr_array(s, torch.float64, f), _ptr_array(wo, torch.float64, f)),
+               "ns_slab_primal_step")
+
+    def adjoint_step(self, w, lam, lo, s=None, nu=None):
+        f = self._sizes(5)
+        _check(self.lib.ns_slab_adjoint_step(self._g, _ptr_array(w, torch.float64, f),
+                                             _ptr_array(s, torch.float64, f), _ptr_array(lam, torch.float64, f),
+                                             _ptr_array(nu, torch.float32, self._sizes(1)),
+                                             _ptr_array(lo, torch.float64, f)), "ns_slab_adjoint_step")

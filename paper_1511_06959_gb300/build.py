@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libns_adjoint.so")
 BUILD = os.path.join(HERE, "_build")
 SOURCES = ["ns_rhs.cu", "ns_adj.cu", "ns_diag.cu", "ns_api.cu", "ns_sweep.cu", "ns_noalloc.cu", "ns_mlp.cu",
-           "ns_lambda.cu", "ns_probe.cu"]
+           "ns_lambda.cu", "ns_probe.cu", "ns_bc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-Xptxas", "-warn-spills"]

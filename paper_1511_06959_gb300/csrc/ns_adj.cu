@@ -33,7 +33,7 @@ namespace adjk {
 
 // Tile of the adjoint stage kernel: TX x TY columns (one thread per column).
 #ifndef NS_ADJ_TY
-#define NS_ADJ_TY 4
+#define NS_ADJ_TY 8
 #endif
 constexpr int TY = NS_ADJ_TY;
 constexpr int NT = TX * TY;

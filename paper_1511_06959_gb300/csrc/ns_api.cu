@@ -209,6 +209,160 @@ static int adjoint_step_t(ns_ctx* c, const Coef<CT>& cf, const CT* W1, const CT*
   return NS_OK;
 }
 
+// ---------------------------------------------------------------------------------
+// bounded boxes (ns_set_boundaries): the calls below run the periodic stage kernels on
+// the box padded by its ghost layer (ns_bc.cu), filling the ghosts of every stage state
+// they form, and crop the results
+// ---------------------------------------------------------------------------------
+template <class CT>
+static CT* bW(ns_ctx* c, int i) {
+  return (CT*)c->bstage[i];
+}
+
+template <class CT>
+static const Coef<CT>& bcoef(const ns_ctx* c);
+template <>
+const Coef<float>& bcoef<float>(const ns_ctx* c) { return c->cf; }
+template <>
+const Coef<double>& bcoef<double>(const ns_ctx* c) { return c->cd; }
+
+// W1 (padded, stage type) = w with its ghost layer; the source padded with zero ghosts
+template <class CT>
+static int bounded_prepare(ns_ctx* c, const double* w, const double* s, const double** sp) {
+  if (ns::launch_bc_embed<CT, double>(c->g, c->bc, 5, 1.0, w, bW<CT>(c, 0), c->st) != cudaSuccess ||
+      ns::launch_bc_ghosts<CT>(c->g, c->bc, bW<CT>(c, 0), c->st) != cudaSuccess)
+    return NS_ERR_CUDA;
+  *sp = nullptr;
+  if (s) {
+    if (ns::launch_bc_embed<double, double>(c->g, c->bc, 5, 1.0, s, c->bd[2], c->st) != cudaSuccess)
+      return NS_ERR_CUDA;
+    *sp = c->bd[2];
+  }
+  return NS_OK;
+}
+
+// stage i of the padded step: W_{i+1} with its ghosts (not last) or the padded FP64
+// output (last, base = the padded state w)
+template <class CT>
+static int bounded_stage(ns_ctx* c, int i, bool final_out, const double* sp, bool with_sum) {
+  const Scheme& sc = scheme_of(c);
+  const double dt = c->p.dt;
+  const bool last = final_out && i == sc.ns - 1;
+  ns::StageArgs<CT, CT> a{};
+  a.W = bW<CT>(c, i); a.base = bW<CT>(c, 0); a.src = sp;
+  if (with_sum) { a.dacc = bW<CT>(c, 4); a.dacc_init = i == 0; a.cacc = sc.b[i] * dt; }
+  if (!last) { a.Wout = bW<CT>(c, i + 1); a.cout = sc.cout[i] * dt; a.cd = sc.cd[i]; }
+  else { a.wbase = c->bd[0]; a.wout = c->bd[1]; }
+  if (ns::launch_rhs_stage<CT, CT, CT>(c->gp, bcoef<CT>(c), a, c->st) != cudaSuccess) return NS_ERR_CUDA;
+  if (!last && ns::launch_bc_ghosts<CT>(c->g, c->bc, bW<CT>(c, i + 1), c->st) != cudaSuccess) return NS_ERR_CUDA;
+  return NS_OK;
+}
+
+template <class CT>
+static int bounded_primal_t(ns_ctx* c, const double* w, const double* s, double* wo) {
+  const double* sp = nullptr;
+  int r = bounded_prepare<CT>(c, w, s, &sp);
+  if (r) return r;
+  if (ns::launch_bc_embed<double, double>(c->g, c->bc, 5, 1.0, w, c->bd[0], c->st) != cudaSuccess)
+    return NS_ERR_CUDA;
+  const Scheme& sc = scheme_of(c);
+  for (int i = 0; i < sc.ns; ++i)
+    if ((r = bounded_stage<CT>(c, i, true, sp, true))) return r;
+  return cuerr(ns::launch_bc_crop<double, double>(c->g, c->bc, 5, c->bd[1], wo, c->st));
+}
+
+template <class CT>
+static int bounded_rhs_t(ns_ctx* c, const double* w, const double* s, double* R) {
+  const double* sp = nullptr;
+  int r = bounded_prepare<CT>(c, w, s, &sp);
+  if (r) return r;
+  ns::StageArgs<CT, CT> a{};
+  a.W = bW<CT>(c, 0); a.src = sp; a.cacc = 1.0; a.wout = c->bd[1];
+  if (ns::launch_rhs_stage<CT, CT, CT>(c->gp, bcoef<CT>(c), a, c->st) != cudaSuccess) return NS_ERR_CUDA;
+  return cuerr(ns::launch_bc_crop<double, double>(c->g, c->bc, 5, c->bd[1], R, c->st));
+}
+
+// the transposed product on the padded box of seed sa*A at padded stage state W
+// (into bd[3]), then the boundary epilogue e
+template <class CT, class NU>
+static int bounded_transposed_stage(ns_ctx* c, const CT* W, ns::BcEpilogue& e, const NU* nu) {
+  if (ns::launch_bc_embed<CT, double>(c->g, c->bc, 5, e.sa, e.A, bW<CT>(c, 5), c->st) != cudaSuccess)
+    return NS_ERR_CUDA;
+  ns::AdjArgs<CT, CT, CT> a{};
+  a.W = W; a.A = bW<CT>(c, 5); a.ca = 1.0; a.lam_out = c->bd[3];
+  if (ns::launch_adj_stage<CT, CT, CT, CT>(c->gp, bcoef<CT>(c), a, c->st) != cudaSuccess) return NS_ERR_CUDA;
+  for (int q = 0; q < 3; ++q) e.nus[q] = c->nu_split[q];
+  e.i2[0] = 1.0 / (c->p.dx * c->p.dx);
+  e.i2[1] = 1.0 / (c->p.dy * c->p.dy);
+  e.i2[2] = 1.0 / (c->p.dz * c->p.dz);
+  return cuerr(ns::launch_bc_adj_epilogue<CT, NU>(c->g, c->bc, e, c->bd[3], W, nu, c->st));
+}
+
+template <class CT>
+static int bounded_transposed(ns_ctx* c, const CT* W, ns::BcEpilogue& e, const float* nu, const double* nud) {
+  if (nud) return bounded_transposed_stage<CT, double>(c, W, e, nud);
+  return bounded_transposed_stage<CT, float>(c, W, e, nu);
+}
+
+template <class CT>
+static int bounded_transpose_t(ns_ctx* c, const double* w, const double* a_, const float* nu, double* out) {
+  const double* sp = nullptr;
+  int r = bounded_prepare<CT>(c, w, nullptr, &sp);
+  if (r) return r;
+  ns::BcEpilogue e{};
+  e.A = a_; e.sa = 1.0; e.mode = 0; e.out = out;
+  return bounded_transposed<CT>(c, bW<CT>(c, 0), e, nu, nullptr);
+}
+
+template <class CT>
+static int bounded_adjoint_t(ns_ctx* c, const double* w, const double* s, const double* lam, const float* nu,
+                             const double* nud, double* lo, double* sbar) {
+  const Scheme& sc = scheme_of(c);
+  const double dt = c->p.dt;
+  const double* sp = nullptr;
+  int r = bounded_prepare<CT>(c, w, s, &sp);
+  if (r) return r;
+  for (int i = 0; i < sc.ns - 1; ++i)
+    if ((r = bounded_stage<CT>(c, i, false, sp, sc.needs_sum()))) return r;
+  const double* Ain = lam;
+  double sa = sc.ca0 * dt;
+  for (int j = 0; j < sc.ns; ++j) {
+    const bool last = j == sc.ns - 1;
+    const CT* W = bW<CT>(c, last ? 0 : sc.ns - 1 - j);
+    ns::BcEpilogue e{};
+    e.A = Ain; e.sa = sa; e.mode = 1; e.first = j == 0; e.last = last;
+    e.lam = lam; e.G = c->ba[2];
+    if (!last) { e.cl = sc.cl[j] * dt; e.cg = sc.cg[j] * dt; e.cs = sc.cs[j] * dt; e.a_next = c->ba[j % 2]; }
+    else e.out = lo;
+    e.sbar = sbar;
+    if ((r = bounded_transposed<CT>(c, W, e, nu, nud))) return r;
+    Ain = e.a_next;
+    sa = 1.0;
+  }
+  return NS_OK;
+}
+
+template <class CT>
+static int bounded_sigma1_t(ns_ctx* c, const double* w, float* sigma1, double* sigma1d) {
+  const double* sp = nullptr;
+  int r = bounded_prepare<CT>(c, w, nullptr, &sp);
+  if (r) return r;
+  if (ns::launch_sigma1<CT>(c->gp, bcoef<CT>(c), bW<CT>(c, 0), sigma1 ? (float*)c->bsig : nullptr, nullptr,
+                            c->scratch, c->ticket, c->st, nullptr,
+                            sigma1d ? (double*)c->bsig : nullptr) != cudaSuccess)
+    return NS_ERR_CUDA;
+  if (sigma1d) return cuerr(ns::launch_bc_crop<double, double>(c->g, c->bc, 1, (double*)c->bsig, sigma1d, c->st));
+  return cuerr(ns::launch_bc_crop<float, float>(c->g, c->bc, 1, (float*)c->bsig, sigma1, c->st));
+}
+
+static void free_bounded(ns_ctx* c) {
+  for (void*& q : c->bstage) { if (q) cudaFree(q); q = nullptr; }
+  for (double*& q : c->bd) { if (q) cudaFree(q); q = nullptr; }
+  for (double*& q : c->ba) { if (q) cudaFree(q); q = nullptr; }
+  if (c->bsig) cudaFree(c->bsig);
+  c->bsig = nullptr;
+}
+
 extern "C" {
 
 const char* ns_error_string(int code) {
@@ -296,8 +450,45 @@ void ns_destroy(ns_ctx* c) {
   if (c->ticket) cudaFree(c->ticket);
   if (c->train_scratch) cudaFree(c->train_scratch);
   for (cudaEvent_t ev : c->events) cudaEventDestroy(ev);
+  free_bounded(c);
   ns_sweep_release(c);
   delete c;
+}
+
+int ns_set_boundaries(ns_ctx* c, int bc, const double* far, const double* wall_e) {
+  if (!c || bc < NS_BC_PERIODIC || bc > NS_BC_INOUT_WALLS) return NS_ERR_ARG;
+  const int inout = bc == NS_BC_INOUT || bc == NS_BC_INOUT_WALLS;
+  const int walls = bc == NS_BC_WALLS || bc == NS_BC_INOUT_WALLS;
+  if ((inout && !far) || (walls && !wall_e)) return NS_ERR_ARG;
+  if (inout && !(far[0] > 0 && far[4] > 0)) return NS_ERR_ARG;
+  if (walls && !(wall_e[0] > 0 && wall_e[1] > 0)) return NS_ERR_ARG;
+  if (cudaStreamSynchronize(c->st) != cudaSuccess) return NS_ERR_CUDA;
+  free_bounded(c);
+  c->bc = ns::BcDesc{};
+  c->bc.gamma = c->p.gamma;
+  if (!inout && !walls) return NS_OK;
+  c->bc.inout = inout;
+  c->bc.walls = walls;
+  for (int k = 0; k < 5; ++k) c->bc.far[k] = inout ? far[k] : 0.0;
+  for (int k = 0; k < 2; ++k) c->bc.wall_e[k] = walls ? wall_e[k] : 0.0;
+  c->gp = c->g;
+  c->gp.nx = c->g.nx + 2 * inout;
+  c->gp.ny = c->g.ny + 2 * walls;
+  c->gp.plane = (long long)c->gp.nx * c->gp.ny;
+  c->gp.cells = c->gp.plane * c->gp.nz;
+  const size_t np = (size_t)5 * c->gp.cells * c->p.batch, nc = (size_t)5 * c->g.cells * c->p.batch;
+  const size_t esz = mixed(c) ? sizeof(float) : sizeof(double);
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < 6 && e == cudaSuccess; ++i) e = cudaMalloc(&c->bstage[i], np * esz);
+  for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaMalloc(&c->bd[i], np * sizeof(double));
+  for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaMalloc(&c->ba[i], nc * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&c->bsig, (size_t)c->gp.cells * c->p.batch * sizeof(double));
+  if (e != cudaSuccess) {
+    free_bounded(c);
+    c->bc = ns::BcDesc{};
+    return NS_ERR_CUDA;
+  }
+  return NS_OK;
 }
 
 int ns_set_stream(ns_ctx* c, void* stream) {
@@ -316,6 +507,7 @@ size_t ns_workspace_bytes(const ns_ctx* c) { return c ? c->ws_bytes : 0; }
 
 int ns_rhs(ns_ctx* c, const double* w, const double* s, double* R) {
   if (!c || !w || !R || (const double*)R == w) return NS_ERR_ARG;
+  if (c->bounded()) return mixed(c) ? bounded_rhs_t<float>(c, w, s, R) : bounded_rhs_t<double>(c, w, s, R);
   if (mixed(c)) {
     float* wf = buf<float>(c, WF);
     if (ns::launch_to_float(w, wf, c->field, c->st) != cudaSuccess) return NS_ERR_CUDA;
@@ -329,7 +521,7 @@ int ns_rhs(ns_ctx* c, const double* w, const double* s, double* R) {
 }
 
 int ns_rhs_tangent(ns_ctx* c, const double* w, const double* wd, double* Rd) {
-  if (!c || !w || !wd || !Rd || Rd == w || Rd == wd) return NS_ERR_ARG;
+  if (!c || !w || !wd || !Rd || Rd == w || Rd == wd || c->bounded()) return NS_ERR_ARG;
   int r = ensure_tangent_buffers(c);
   if (r) return r;
   ns::StageArgs<double, double> a{};
@@ -339,6 +531,7 @@ int ns_rhs_tangent(ns_ctx* c, const double* w, const double* wd, double* Rd) {
 
 int ns_primal_step(ns_ctx* c, const double* w, const double* s, double* wo) {
   if (!c || !w || !wo || wo == w || wo == s) return NS_ERR_ARG;
+  if (c->bounded()) return mixed(c) ? bounded_primal_t<float>(c, w, s, wo) : bounded_primal_t<double>(c, w, s, wo);
   if (mixed(c)) {
     float* wf = buf<float>(c, WF);
     if (ns::launch_to_float(w, wf, c->field, c->st) != cudaSuccess) return NS_ERR_CUDA;
@@ -349,7 +542,7 @@ int ns_primal_step(ns_ctx* c, const double* w, const double* s, double* wo) {
 
 int ns_tangent_step(ns_ctx* c, const double* w, const double* s, const double* wd, const double* sd,
                     double* wdo) {
-  if (!c || !w || !wd || !wdo || wdo == wd || wdo == w) return NS_ERR_ARG;
+  if (!c || !w || !wd || !wdo || wdo == wd || wdo == w || c->bounded()) return NS_ERR_ARG;
   int r = ensure_tangent_buffers(c);
   if (r) return r;
   const Scheme& sc = scheme_of(c);
@@ -378,6 +571,9 @@ int ns_adjoint_step(ns_ctx* c, const double* w, const double* s, const double* l
                     double* lo, double* sbar) {
   if (!c || !w || !lam || !lo || lo == lam || lo == w || (sbar && (sbar == lo || sbar == lam)))
     return NS_ERR_ARG;
+  if (c->bounded())
+    return mixed(c) ? bounded_adjoint_t<float>(c, w, s, lam, nu, nullptr, lo, sbar)
+                    : bounded_adjoint_t<double>(c, w, s, lam, nu, nullptr, lo, sbar);
   if (mixed(c)) {
     float* wf = buf<float>(c, WF);
     float* lf = buf<float>(c, LF);
@@ -392,11 +588,14 @@ int ns_adjoint_step_f64(ns_ctx* c, const double* w, const double* s, const doubl
                         double* lo, double* sbar) {
   if (!c || mixed(c) || !w || !lam || !lo || lo == lam || lo == w || (sbar && (sbar == lo || sbar == lam)))
     return NS_ERR_ARG;
+  if (c->bounded()) return bounded_adjoint_t<double>(c, w, s, lam, nullptr, nu, lo, sbar);
   return adjoint_step_t<double>(c, c->cd, w, lam, s, lam, nullptr, lo, sbar, nullptr, nullptr, nu);
 }
 
 int ns_rhs_transpose(ns_ctx* c, const double* w, const double* a_, const float* nu, double* out) {
   if (!c || !w || !a_ || !out || out == w || out == a_) return NS_ERR_ARG;
+  if (c->bounded())
+    return mixed(c) ? bounded_transpose_t<float>(c, w, a_, nu, out) : bounded_transpose_t<double>(c, w, a_, nu, out);
   if (mixed(c)) {
     float* wf = buf<float>(c, WF);
     float* af = buf<float>(c, LF);
@@ -422,6 +621,10 @@ int ns_objective(ns_ctx* c, const double* w, double weight, double* J_acc, doubl
 
 int ns_growth_sigma1(ns_ctx* c, const double* w, float* sigma1, double* stats) {
   if (!c || !w || !sigma1) return NS_ERR_ARG;
+  if (c->bounded()) {
+    if (stats) return NS_ERR_ARG;
+    return mixed(c) ? bounded_sigma1_t<float>(c, w, sigma1, nullptr) : bounded_sigma1_t<double>(c, w, sigma1, nullptr);
+  }
   if (mixed(c)) {
     float* wf = buf<float>(c, WF);
     if (ns::launch_to_float(w, wf, c->field, c->st) != cudaSuccess) return NS_ERR_CUDA;
@@ -432,6 +635,7 @@ int ns_growth_sigma1(ns_ctx* c, const double* w, float* sigma1, double* stats) {
 
 int ns_growth_sigma1_f64(ns_ctx* c, const double* w, double* sigma1, double* stats) {
   if (!c || mixed(c) || !w || !sigma1) return NS_ERR_ARG;
+  if (c->bounded()) return stats ? NS_ERR_ARG : bounded_sigma1_t<double>(c, w, nullptr, sigma1);
   return cuerr(ns::launch_sigma1<double>(c->g, c->cd, w, nullptr, stats, c->scratch, c->ticket, c->st, nullptr,
                                          sigma1));
 }
@@ -455,7 +659,7 @@ int ns_add_adjoint_viscosity_f64(ns_ctx* c, const double* sigma1, double lambda,
 }
 
 int ns_apply_adjoint_viscosity(ns_ctx* c, const float* nu, const double* a, double* out) {
-  if (!c || !nu || !a || !out || out == a) return NS_ERR_ARG;
+  if (!c || !nu || !a || !out || out == a || c->bounded()) return NS_ERR_ARG;
   const double i2[3] = {1.0 / (c->p.dx * c->p.dx), 1.0 / (c->p.dy * c->p.dy), 1.0 / (c->p.dz * c->p.dz)};
   return cuerr(ns::launch_visc_apply(c->g, i2, c->nu_split, nu, a, out, c->st));
 }
@@ -508,7 +712,7 @@ int ns_mlp_get_moment(ns_ctx* c, const void* net, int which, float* out) {
 }
 
 int ns_mlp_features(ns_ctx* c, const double* w, float* feat) {
-  if (!c || !w || !feat) return NS_ERR_ARG;
+  if (!c || !w || !feat || c->bounded()) return NS_ERR_ARG;
   if (ns::launch_box_means(c->g, c->p.gamma, w, c->qbar, c->scratch, c->st) != cudaSuccess) return NS_ERR_CUDA;
   return cuerr(ns::launch_features(c->g, c->cf, w, c->qbar, feat, c->st));
 }
@@ -535,7 +739,7 @@ int ns_mlp_train_step(ns_ctx* c, void* net, const float* feat, const float* targ
 }
 
 int ns_adjoint_label(ns_ctx* c, const double* w, const double* lam, float* acc) {
-  if (!c || !w || !lam || !acc) return NS_ERR_ARG;
+  if (!c || !w || !lam || !acc || c->bounded()) return NS_ERR_ARG;
   if (mixed(c)) {
     float* wf = buf<float>(c, WF);
     if (ns::launch_to_float(w, wf, c->field, c->st) != cudaSuccess) return NS_ERR_CUDA;
@@ -697,3 +901,246 @@ int ns_i_mlp_features(ns_ctx* c, const double* w, const void* w_mirror, float* f
 }
 
 size_t ns_i_stage_bytes(const ns_ctx* c) { return c->field * (mixed(c) ? sizeof(float) : sizeof(double)); }
+
+// ---------------------------------------------------------------------------------
+// x-slab decomposition (section "Numerical methods": the solver's domain is split over
+// MPI ranks).  Every slab is a box of its own, padded with one ghost column on each x
+// side: columns 0 and nx-1 of a slab hold the neighbouring slabs' boundary columns, so
+// the periodic stencils of the stage kernels, run on the padded slab, give the exact
+// result in its interior columns (the residual and its transpose reach one cell in x).
+// Every stage of a step runs on all slabs, then the stage's output field is exchanged
+// (one strided copy per halo); the stage products and sums stay per cell.  The slabs
+// are periodic in x as a whole: slab 0's left neighbour is the last slab.
+// ---------------------------------------------------------------------------------
+struct ns_slab_group {
+  std::vector<ns_ctx*> c;
+  std::vector<cudaEvent_t> done, copied;
+  ns_halo_exchange_fn fn = nullptr;   // host exchange (one slab per process), or null
+  void* user = nullptr;
+};
+
+static int slab_exchange(ns_slab_group* G, void* const* f, int eb, int ncomp) {
+  const int n = (int)G->c.size();
+  if (G->fn) {
+    for (int k = 0; k < n; ++k)
+      if (G->fn(G->user, f[k], eb, ncomp) != 0) return NS_ERR_CUDA;
+    return NS_OK;
+  }
+  // producers done on every stream before any copy reads a neighbour's columns
+  for (int k = 0; k < n; ++k)
+    if (cudaEventRecord(G->done[k], G->c[k]->st) != cudaSuccess) return NS_ERR_CUDA;
+  for (int k = 0; k < n; ++k) {
+    ns_ctx* c = G->c[k];
+    const int L = (k + n - 1) % n, R = (k + 1) % n;
+    if (cudaStreamWaitEvent(c->st, G->done[L], 0) != cudaSuccess ||
+        cudaStreamWaitEvent(c->st, G->done[R], 0) != cudaSuccess)
+      return NS_ERR_CUDA;
+    const size_t rows = (size_t)c->g.batch * ncomp * c->g.nz * c->g.ny;
+    const int nxk = c->g.nx, nxl = G->c[L]->g.nx, nxr = G->c[R]->g.nx;
+    char* dst = (char*)f[k];
+    // left ghost <- the left slab's last interior column; right ghost <- the right
+    // slab's first interior column
+    if (cudaMemcpy2DAsync(dst, (size_t)nxk * eb, (const char*)f[L] + (size_t)(nxl - 2) * eb, (size_t)nxl * eb, eb,
+                          rows, cudaMemcpyDeviceToDevice, c->st) != cudaSuccess)
+      return NS_ERR_CUDA;
+    if (cudaMemcpy2DAsync(dst + (size_t)(nxk - 1) * eb, (size_t)nxk * eb, (const char*)f[R] + (size_t)eb,
+                          (size_t)nxr * eb, eb, rows, cudaMemcpyDeviceToDevice, c->st) != cudaSuccess)
+      return NS_ERR_CUDA;
+  }
+  // a neighbour's next kernel may overwrite the columns just read: it waits for the copies
+  for (int k = 0; k < n; ++k)
+    if (cudaEventRecord(G->copied[k], G->c[k]->st) != cudaSuccess) return NS_ERR_CUDA;
+  for (int k = 0; k < n; ++k) {
+    const int L = (k + n - 1) % n, R = (k + 1) % n;
+    if (cudaStreamWaitEvent(G->c[k]->st, G->copied[L], 0) != cudaSuccess ||
+        cudaStreamWaitEvent(G->c[k]->st, G->copied[R], 0) != cudaSuccess)
+      return NS_ERR_CUDA;
+  }
+  return NS_OK;
+}
+
+template <class CT>
+static const Coef<CT>& coef_of(const ns_ctx* c);
+template <>
+const Coef<float>& coef_of<float>(const ns_ctx* c) { return c->cf; }
+template <>
+const Coef<double>& coef_of<double>(const ns_ctx* c) { return c->cd; }
+
+// the stages of primal_step_t on every slab, with the stage outputs exchanged
+template <class CT>
+static int slab_primal_t(ns_slab_group* G, const CT* const* W1, const double* const* w, const double* const* s,
+                         double* const* wo) {
+  const int n = (int)G->c.size();
+  const Scheme& sc = scheme_of(G->c[0]);
+  const double dt = G->c[0]->p.dt;
+  std::vector<const CT*> in(W1, W1 + n);
+  std::vector<void*> out(n);
+  for (int i = 0; i < sc.ns; ++i) {
+    const bool last = i == sc.ns - 1;
+    for (int k = 0; k < n; ++k) {
+      ns_ctx* c = G->c[k];
+      CT* o = last ? nullptr : buf<CT>(c, i % 2 == 0 ? W2 : W3);
+      ns::StageArgs<CT, CT> a{};
+      a.W = in[k]; a.base = W1[k]; a.src = s ? s[k] : nullptr;
+      a.dacc = buf<CT>(c, GS); a.dacc_init = i == 0; a.cacc = sc.b[i] * dt;
+      a.Wout = o; a.cout = sc.cout[i] * dt; a.cd = sc.cd[i];
+      if (last) { a.wbase = w[k]; a.wout = wo[k]; }
+      if (ns::launch_rhs_stage<CT, CT, CT>(c->g, coef_of<CT>(c), a, c->st) != cudaSuccess) return NS_ERR_CUDA;
+      out[k] = last ? (void*)wo[k] : (void*)o;
+    }
+    int r = slab_exchange(G, out.data(), last ? (int)sizeof(double) : (int)sizeof(CT), 5);
+    if (r) return r;
+    for (int k = 0; k < n; ++k) in[k] = (const CT*)out[k];
+  }
+  return NS_OK;
+}
+
+// the stages of adjoint_step_t (recompute, then the transposed stages) on every slab,
+// with the recomputed stage states, the stage seeds and lam^n exchanged
+template <class CT>
+static int slab_adjoint_t(ns_slab_group* G, const CT* const* W1, const CT* const* lamf, const double* const* s,
+                          const double* const* lam, const float* const* nu, double* const* lo) {
+  const int n = (int)G->c.size();
+  const Scheme& sc = scheme_of(G->c[0]);
+  const double dt = G->c[0]->p.dt;
+  std::vector<std::vector<const CT*>> Wst(n, std::vector<const CT*>(3, nullptr));
+  std::vector<void*> out(n);
+  const int wb[3] = {W2, W3, W4};
+  for (int i = 0; i < sc.ns - 1; ++i) {
+    for (int k = 0; k < n; ++k) {
+      ns_ctx* c = G->c[k];
+      CT* o = buf<CT>(c, wb[i]);
+      ns::StageArgs<CT, CT> a{};
+      a.W = i == 0 ? W1[k] : Wst[k][i - 1]; a.base = W1[k]; a.src = s ? s[k] : nullptr;
+      a.Wout = o; a.cout = sc.cout[i] * dt; a.cd = sc.cd[i];
+      if (sc.needs_sum()) { a.dacc = buf<CT>(c, GS); a.dacc_init = i == 0; a.cacc = sc.b[i] * dt; }
+      if (ns::launch_rhs_stage<CT, CT, CT>(c->g, coef_of<CT>(c), a, c->st) != cudaSuccess) return NS_ERR_CUDA;
+      Wst[k][i] = o;
+      out[k] = o;
+    }
+    int r = slab_exchange(G, out.data(), (int)sizeof(CT), 5);
+    if (r) return r;
+  }
+  std::vector<const CT*> Ain(lamf, lamf + n);
+  for (int j = 0; j < sc.ns; ++j) {
+    const bool last = j == sc.ns - 1;
+    for (int k = 0; k < n; ++k) {
+      ns_ctx* c = G->c[k];
+      CT* Aout = last ? nullptr : buf<CT>(c, j % 2 == 0 ? AA : AB);
+      ns::AdjArgs<CT, CT, CT> a{};
+      a.W = last ? W1[k] : Wst[k][sc.ns - 2 - j];
+      a.A = Ain[k]; a.ca = j == 0 ? sc.ca0 * dt : 1.0; a.nu = nu ? nu[k] : nullptr; a.lamf = lamf[k];
+      for (int q = 0; q < 3; ++q) a.nus[q] = c->nu_split[q];
+      a.Gin = j == 0 ? nullptr : buf<CT>(c, GS);
+      a.Anext = Aout;
+      if (!last) {
+        a.cl = sc.cl[j] * dt; a.cg = sc.cg[j] * dt; a.cs = sc.cs[j] * dt;
+        a.Gout = buf<CT>(c, GS);
+      } else {
+        a.lam_in = lam[k];
+        a.lam_out = lo[k];
+      }
+      if (ns::launch_adj_stage<CT, CT, CT, CT>(c->g, coef_of<CT>(c), a, c->st) != cudaSuccess) return NS_ERR_CUDA;
+      out[k] = last ? (void*)lo[k] : (void*)Aout;
+    }
+    int r = slab_exchange(G, out.data(), last ? (int)sizeof(double) : (int)sizeof(CT), 5);
+    if (r) return r;
+    for (int k = 0; k < n; ++k) Ain[k] = (const CT*)out[k];
+  }
+  return NS_OK;
+}
+
+extern "C" {
+
+int ns_slab_group_create(ns_ctx* const* slabs, int n, ns_slab_group** out) {
+  if (!slabs || !out || n < 1) return NS_ERR_ARG;
+  *out = nullptr;
+  const ns_params& p0 = slabs[0] ? slabs[0]->p : ns_params{};
+  for (int k = 0; k < n; ++k) {
+    const ns_ctx* c = slabs[k];
+    if (!c || c->p.nx < 3 || c->bounded()) return NS_ERR_ARG;
+    const ns_params& p = c->p;
+    if (p.ny != p0.ny || p.nz != p0.nz || p.batch != p0.batch || p.precision != p0.precision ||
+        p.scheme != p0.scheme || p.flux != p0.flux || p.dt != p0.dt || p.dx != p0.dx || p.dy != p0.dy ||
+        p.dz != p0.dz || p.gamma != p0.gamma || p.mu != p0.mu || p.Pr != p0.Pr || p.roe_delta != p0.roe_delta)
+      return NS_ERR_ARG;
+  }
+  ns_slab_group* G = new ns_slab_group();
+  G->c.assign(slabs, slabs + n);
+  G->done.assign(n, nullptr);
+  G->copied.assign(n, nullptr);
+  for (int k = 0; k < n; ++k) {
+    if (cudaEventCreateWithFlags(&G->done[k], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&G->copied[k], cudaEventDisableTiming) != cudaSuccess) {
+      ns_slab_group_destroy(G);
+      return NS_ERR_CUDA;
+    }
+  }
+  *out = G;
+  return NS_OK;
+}
+
+void ns_slab_group_destroy(ns_slab_group* G) {
+  if (!G) return;
+  for (cudaEvent_t e : G->done)
+    if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : G->copied)
+    if (e) cudaEventDestroy(e);
+  delete G;
+}
+
+int ns_slab_set_exchange(ns_slab_group* G, ns_halo_exchange_fn fn, void* user) {
+  if (!G || (fn && G->c.size() != 1)) return NS_ERR_ARG;
+  G->fn = fn;
+  G->user = user;
+  return NS_OK;
+}
+
+int ns_slab_exchange(ns_slab_group* G, void* const* fields, int elem_bytes, int ncomp) {
+  if (!G || !fields || (elem_bytes != 4 && elem_bytes != 8) || ncomp < 1) return NS_ERR_ARG;
+  for (size_t k = 0; k < G->c.size(); ++k)
+    if (!fields[k]) return NS_ERR_ARG;
+  return slab_exchange(G, fields, elem_bytes, ncomp);
+}
+
+int ns_slab_primal_step(ns_slab_group* G, const double* const* w, const double* const* s, double* const* wo) {
+  if (!G || !w || !wo) return NS_ERR_ARG;
+  const int n = (int)G->c.size();
+  for (int k = 0; k < n; ++k)
+    if (!w[k] || !wo[k] || wo[k] == w[k] || (s && wo[k] == s[k])) return NS_ERR_ARG;
+  if (mixed(G->c[0])) {
+    std::vector<const float*> W1(n);
+    for (int k = 0; k < n; ++k) {
+      float* wf = buf<float>(G->c[k], WF);
+      if (ns::launch_to_float(w[k], wf, G->c[k]->field, G->c[k]->st) != cudaSuccess) return NS_ERR_CUDA;
+      W1[k] = wf;
+    }
+    return slab_primal_t<float>(G, W1.data(), w, s, wo);
+  }
+  return slab_primal_t<double>(G, w, w, s, wo);
+}
+
+int ns_slab_adjoint_step(ns_slab_group* G, const double* const* w, const double* const* s,
+                         const double* const* lam, const float* const* nu, double* const* lo) {
+  if (!G || !w || !lam || !lo) return NS_ERR_ARG;
+  const int n = (int)G->c.size();
+  for (int k = 0; k < n; ++k)
+    if (!w[k] || !lam[k] || !lo[k] || lo[k] == lam[k] || lo[k] == w[k] || (nu && !nu[k])) return NS_ERR_ARG;
+  if (mixed(G->c[0])) {
+    std::vector<const float*> W1(n), lf(n);
+    for (int k = 0; k < n; ++k) {
+      ns_ctx* c = G->c[k];
+      float* wf = buf<float>(c, WF);
+      float* lm = buf<float>(c, LF);
+      if (ns::launch_to_float(w[k], wf, c->field, c->st) != cudaSuccess ||
+          ns::launch_to_float(lam[k], lm, c->field, c->st) != cudaSuccess)
+        return NS_ERR_CUDA;
+      W1[k] = wf;
+      lf[k] = lm;
+    }
+    return slab_adjoint_t<float>(G, W1.data(), lf.data(), s, lam, nu, lo);
+  }
+  return slab_adjoint_t<double>(G, w, lam, s, lam, nu, lo);
+}
+
+}  // extern "C"

@@ -7,6 +7,7 @@
 
 #include "../../include/ns_adjoint.h"
 #include "ns_common.cuh"
+#include "ns_kernels.h"
 
 struct ns_sweep_state;
 
@@ -40,6 +41,14 @@ struct ns_ctx {
   unsigned* ticket = nullptr;        // per-box counters of the single-launch objective
   float* train_scratch = nullptr;    // closure training partials, allocated on first use
   size_t train_scratch_n = 0;
+  // bounded box (ns_set_boundaries): the padded grid and its workspace
+  ns::BcDesc bc{};
+  ns::GridDesc gp{};
+  void* bstage[6] = {};              // padded stage type: W1..W4, increment sum, adjoint seed
+  double* bd[4] = {};                // padded FP64: state, output, source, transposed product
+  double* ba[3] = {};                // FP64: seed, next seed, stage-product sum
+  void* bsig = nullptr;              // padded sigma_1 (double in FP64 contexts)
+  bool bounded() const { return bc.inout || bc.walls; }
 };
 
 // releases the sweep executor state of a context (defined with the executor)

@@ -128,4 +128,38 @@ cudaError_t launch_dot_boxes(const GridDesc& g, const double* field, int comp, c
 // doubles of scratch that launch_objective uses for a grid (its partials and plane sums)
 size_t objective_scratch_doubles(const GridDesc& g);
 
+// ---- bounded boxes (ns_bc.cu): characteristic inflow/outflow in x, isothermal walls in y
+struct BcDesc {
+  int inout;          // 1: characteristic inflow at x = 0 and outflow at x = L_x
+  int walls;          // 1: isothermal no-slip walls at y = 0 and y = L_y
+  double gamma;
+  double far[5];      // far-field primitive state (rho, u1, u2, u3, p)
+  double wall_e[2];   // internal energy e = c_v T of the bottom and the top wall
+};
+// one transposed stage's boundary epilogue (see k_bc_adj_epilogue)
+struct BcEpilogue {
+  const double* A;    // the stage's seed is sa * A (unpadded)
+  double sa;
+  double nus[3];      // viscosity factors of rho, rho u, rho E
+  double i2[3];       // 1 / dx_d^2
+  int mode, first, last;
+  const double* lam;
+  double* G;
+  double cl, cg, cs;
+  double* a_next;
+  double* out;
+  double* sbar;
+};
+long long bc_padded_cells(const GridDesc& g, const BcDesc& bc);
+template <class TO, class TI>
+cudaError_t launch_bc_embed(const GridDesc& g, const BcDesc& bc, int ncomp, double scale, const TI* src, TO* dst,
+                            cudaStream_t st);
+template <class TO, class TI>
+cudaError_t launch_bc_crop(const GridDesc& g, const BcDesc& bc, int ncomp, const TI* src, TO* dst, cudaStream_t st);
+template <class T>
+cudaError_t launch_bc_ghosts(const GridDesc& g, const BcDesc& bc, T* W, cudaStream_t st);
+template <class CT, class NU>
+cudaError_t launch_bc_adj_epilogue(const GridDesc& g, const BcDesc& bc, const BcEpilogue& e, const double* gp,
+                                   const CT* W, const NU* nu, cudaStream_t st);
+
 }  // namespace ns

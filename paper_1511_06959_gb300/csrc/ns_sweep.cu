@@ -528,7 +528,7 @@ extern "C" {
 
 static int forward_run_impl(ns_ctx* c, const double* w0, const double* s, const ns_run_opts* o, void* arena,
                             size_t arena_bytes, double* Jbar, bool objective_in_forward) {
-  if (!c || !w0 || !o || !arena || !Jbar) return NS_ERR_ARG;
+  if (!c || !w0 || !o || !arena || !Jbar || c->bounded()) return NS_ERR_ARG;
   if (((uintptr_t)arena & 255) != 0) return NS_ERR_ARG;
   if (!(o->lambda >= 0.0)) return NS_ERR_ARG;
   ns_sweep_release(c);

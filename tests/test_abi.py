@@ -100,3 +100,13 @@ def test_size_and_plane_checks_without_gpu():
     assert f(ctypes.byref(far), None, dummy, 1.0, dummy, None) == api.NS_ERR_ARG
     far.plane_i = -(1 << 30)
     assert f(ctypes.byref(far), None, dummy, 1.0, dummy, None) == api.NS_ERR_ARG
+
+
+def test_binding_refuses_undersized_tensors_before_any_call():
+    """The binding checks that every tensor holds the elements the library will touch
+    through its raw pointer (here on CPU tensors: the size check comes first)."""
+    torch = pytest.importorskip("torch")
+    from paper_1511_06959_gb300 import api
+    with pytest.raises(ValueError, match="elements"):
+        api._sized(torch.empty(7, dtype=torch.float64), torch.float64, 8, "field")
+    assert api._sized(None, torch.float64, 8, "field") is None
