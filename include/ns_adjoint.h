@@ -53,6 +53,9 @@ extern "C" {
 #define NS_ERR_NONFINITE (-3)
 #define NS_ERR_UNSTABLE (-4)
 #define NS_ERR_CUDA (-5)
+#define NS_ERR_CORRUPT (-6) /* a verified checkpoint snapshot changed between store and load */
+#define NS_ERR_BOUNDS (-7)  /* bounds-checking builds only (NS_DEBUG_BOUNDS): a stencil kernel
+                               met a field index outside its field and skipped the access */
 
 /* time integration (ns_params.scheme) */
 #define NS_RK4 0    /* classical four-stage fourth-order Runge-Kutta, constant dt */
@@ -274,6 +277,14 @@ typedef struct {
                         memory works but each copy then blocks the host); else ignored.
                         The host must not touch it while a sweep runs. */
   size_t host_bytes; /* its size in bytes */
+  int verify;        /* nonzero: a 64-bit checksum of every stored snapshot (device slots and
+                        host slots) is taken when it is stored and checked when it is loaded;
+                        a mismatch sets NS_ERR_CORRUPT in the sticky error word.  The
+                        checksum sums, mod 2^64, a 64-bit mix (the splitmix64 finaliser) of
+                        each 64-bit word keyed by its position, so any changed, lost or
+                        moved word changes it except with probability 2^-64, and its
+                        parallel sum is exact in any order.  Costs one read of the state
+                        per store and per load. */
 } ns_run_opts;
 
 /* Device bytes the caller must provide as the arena of ns_adjoint_run (state slots,

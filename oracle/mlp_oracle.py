@@ -107,10 +107,13 @@ def forward(p, X, quantize=True):
     return y, softplus(y), cache
 
 
-def loss_and_grads(p, X, t, quantize=True):
+def loss_and_grads(p, X, t, quantize=True, bf16_backward=False):
     """Mean squared error of softplus(MLP(X)) against targets t and its gradient with
     respect to every parameter (hand-derived backward; the BF16 rounding points are
-    treated as identity in the backward pass, the usual straight-through rule)."""
+    treated as identity in the backward pass, the usual straight-through rule).
+    bf16_backward=True also rounds the pre-activation gradients dZ2 and dZ1 to BF16
+    where they enter matrix products (the weight gradients and dH1), the data path of
+    a BF16 tensor-core backward pass; the bias gradients sum the unrounded ones."""
     q = bf16 if quantize else (lambda a: np.asarray(a, dtype=np.float64))
     n = X.shape[0]
     y, pred, c = forward(p, X, quantize)
@@ -122,11 +125,13 @@ def loss_and_grads(p, X, t, quantize=True):
     g["b3"] = np.array(np.sum(dy))
     dH2 = np.outer(dy, q(p["w3"]))
     dZ2 = dH2 * gelu_grad(c["Z2"])
-    g["W2"] = c["H1q"].T @ dZ2
+    dZ2m = bf16(dZ2) if bf16_backward else dZ2      # operand of the products below
+    g["W2"] = c["H1q"].T @ dZ2m
     g["b2"] = np.sum(dZ2, axis=0)
-    dH1 = dZ2 @ q(p["W2"]).T
+    dH1 = dZ2m @ q(p["W2"]).T
     dZ1 = dH1 * gelu_grad(c["Z1"])
-    g["W1"] = c["X0"].T @ dZ1
+    dZ1m = bf16(dZ1) if bf16_backward else dZ1
+    g["W1"] = c["X0"].T @ dZ1m
     g["b1"] = np.sum(dZ1, axis=0)
     return L, g
 

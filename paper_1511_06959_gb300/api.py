@@ -20,6 +20,8 @@ NS_ERR_BUDGET = -2
 NS_ERR_NONFINITE = -3
 NS_ERR_UNSTABLE = -4
 NS_ERR_CUDA = -5
+NS_ERR_CORRUPT = -6
+NS_ERR_BOUNDS = -7
 NS_FP64 = 0
 NS_MIXED = 1
 NS_RK4 = 0
@@ -80,7 +82,7 @@ class NsRunOpts(ctypes.Structure):
         ("nsteps", ctypes.c_int), ("schedule", ctypes.c_int), ("param", ctypes.c_int),
         ("lambda_", ctypes.c_double), ("tau", ctypes.c_double), ("record_energy", ctypes.c_int),
         ("record_sigma", ctypes.c_int), ("mlp", ctypes.c_void_p), ("host_arena", ctypes.c_void_p),
-        ("host_bytes", ctypes.c_size_t),
+        ("host_bytes", ctypes.c_size_t), ("verify", ctypes.c_int),
     ]
 
 
@@ -180,9 +182,12 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
 
 
 def _lib() -> ctypes.CDLL:
+    """The library, loaded on first use: libns_adjoint.so next to this file, or the
+    build named by the environment variable NS_ADJOINT_LIB (such as the bounds-checking
+    build, paper_1511_06959_gb300.build.build(debug=True))."""
     global _LIB
     if _LIB is None:
-        _LIB = load_library()
+        _LIB = load_library(os.environ.get("NS_ADJOINT_LIB") or LIB_PATH)
     return _LIB
 
 
@@ -420,15 +425,17 @@ class Solver:
 
     # --- checkpointed sweep ----------------------------------------------------------
     def run_opts(self, nsteps, schedule=NS_CKPT_ALL, param=0, lam_coef=0.0, tau=0.0,
-                 record_energy=False, record_sigma=False, mlp=None, host_arena=None):
+                 record_energy=False, record_sigma=False, mlp=None, host_arena=None, verify=False):
         """Sweep options; mlp: a network blob (uint8 CUDA tensor) selecting the learned
         closure, with lam_coef then its global factor kappa; host_arena: a uint8 CPU
         tensor (pinned for asynchronous copies) holding the snapshots of an
-        NS_CKPT_STRIDE_HOST sweep.  The options keep a reference to it."""
+        NS_CKPT_STRIDE_HOST sweep (the options keep a reference to it); verify: checksum
+        every snapshot when stored and check it when loaded (NS_ERR_CORRUPT)."""
         o = NsRunOpts(nsteps, schedule, param, lam_coef, tau, int(record_energy), int(record_sigma),
                       None if mlp is None else ctypes.c_void_p(mlp.data_ptr()),
                       _host_ptr(host_arena),
-                      0 if host_arena is None else host_arena.numel() * host_arena.element_size())
+                      0 if host_arena is None else host_arena.numel() * host_arena.element_size(),
+                      int(verify))
         o._host_arena = host_arena
         return o
 

@@ -15,6 +15,11 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libns_adjoint.so")
 BUILD = os.path.join(HERE, "_build")
+# bounds-checking build: every field access of the stencil kernels is checked against its
+# field's extent (NS_DEBUG_BOUNDS, NS_ERR_BOUNDS in the sticky error word); load it with
+# NS_ADJOINT_LIB=<OUT_DEBUG>
+OUT_DEBUG = os.path.join(HERE, "libns_adjoint_debug.so")
+BUILD_DEBUG = os.path.join(HERE, "_build_debug")
 SOURCES = ["ns_rhs.cu", "ns_adj.cu", "ns_diag.cu", "ns_api.cu", "ns_sweep.cu", "ns_noalloc.cu", "ns_mlp.cu",
            "ns_lambda.cu", "ns_probe.cu", "ns_bc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -29,8 +34,8 @@ def nvcc() -> str:
     return exe
 
 
-def _compile(src: str, extra) -> str:
-    obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
+def _compile(src: str, extra, bdir: str = BUILD) -> str:
+    obj = os.path.join(bdir, os.path.splitext(src)[0] + ".o")
     cmd = [nvcc(), *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
@@ -40,19 +45,21 @@ def _compile(src: str, extra) -> str:
     return obj
 
 
-def build(verbose: bool = False, extra=()) -> str:
-    os.makedirs(BUILD, exist_ok=True)
-    flags = list(extra)
+def build(verbose: bool = False, extra=(), debug: bool = False) -> str:
+    """Compile and link the library; debug: the bounds-checking build (OUT_DEBUG)."""
+    bdir, out = (BUILD_DEBUG, OUT_DEBUG) if debug else (BUILD, OUT)
+    os.makedirs(bdir, exist_ok=True)
+    flags = list(extra) + (["-DNS_DEBUG_BOUNDS"] if debug else [])
     if verbose:
         flags += ["-Xptxas", "-v"]
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, flags), SOURCES))
-    cmd = [nvcc(), *ARCH, "-shared", "-o", OUT, *objs, "-lcudart", "-ldl"]
+        objs = list(ex.map(lambda s: _compile(s, flags, bdir), SOURCES))
+    cmd = [nvcc(), *ARCH, "-shared", "-o", out, *objs, "-lcudart", "-ldl"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    return OUT
+    return out
 
 
 if __name__ == "__main__":
-    print(build(verbose="-v" in sys.argv))
+    print(build(verbose="-v" in sys.argv, debug="--debug" in sys.argv))

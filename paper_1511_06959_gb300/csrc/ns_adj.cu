@@ -77,26 +77,29 @@ __device__ __forceinline__ void adj_plane_load(AdjPlaneRegs<CT>& r, const GridDe
   const int kz = wrap(k, g.nz);
   const size_t pb = boxoff + (size_t)kz * g.plane;
   const CT cac = CT(ca);
+  const long long n1 = g.cells * g.batch, n5 = 5 * n1;   // field extents (debug bounds checks)
+  (void)n1;
+  (void)n5;
 #pragma unroll
   for (int it = 0; it < 2; ++it) {
     if (threadIdx.x + it * NT < SP) {
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
-        r.q[it][v] = cvt<CT>((W + pb + v * (size_t)g.cells)[h.o[it]]);
-        r.a[it][v] = cac * cvt<CT>((A + pb + v * (size_t)g.cells)[h.o[it]]);
+        r.q[it][v] = cvt<CT>(NS_LD(g, W, pb + v * (size_t)g.cells, h.o[it], n5));
+        r.a[it][v] = cac * cvt<CT>(NS_LD(g, A, pb + v * (size_t)g.cells, h.o[it], n5));
       }
     }
   }
   if (nu) {
-    const float* nk = nu + (size_t)b * g.cells + (size_t)kz * g.plane;
+    const size_t nb = (size_t)b * g.cells + (size_t)kz * g.plane;
 #pragma unroll
     for (int it = 0; it < 2; ++it)
-      if (threadIdx.x + it * NT < SP) r.n[it] = CT(nk[h.o[it]]);
+      if (threadIdx.x + it * NT < SP) r.n[it] = CT(NS_LD(g, nu, nb, h.o[it], n1));
   } else if (nud) {
-    const double* nk = nud + (size_t)b * g.cells + (size_t)kz * g.plane;
+    const size_t nb = (size_t)b * g.cells + (size_t)kz * g.plane;
 #pragma unroll
     for (int it = 0; it < 2; ++it)
-      if (threadIdx.x + it * NT < SP) r.n[it] = cvt<CT>(nk[h.o[it]]);
+      if (threadIdx.x + it * NT < SP) r.n[it] = cvt<CT>(NS_LD(g, nud, nb, h.o[it], n1));
   }
 }
 
@@ -389,16 +392,18 @@ __global__ void __launch_bounds__(NT, AdjMinBlocks<CT, ROE>::value) k_adj_stage(
     // per-cell operands of the assembly and epilogue, loaded ahead of the face work
     const size_t pbase = boxoff + (size_t)k * g.plane;   // component 0 of plane k
     const size_t fc = (size_t)g.cells;
+    const long long n5 = 5 * g.cells * g.batch;           // field extent (debug bounds checks)
+    (void)n5;
     CT gin[5] = {CT(0), CT(0), CT(0), CT(0), CT(0)};
     CT lfv[5] = {CT(0), CT(0), CT(0), CT(0), CT(0)};
     if (valid) {
       if (a.Gin) {
 #pragma unroll
-        for (int v = 0; v < 5; ++v) gin[v] = (a.Gin + pbase + v * fc)[cp];
+        for (int v = 0; v < 5; ++v) gin[v] = NS_LD(g, a.Gin, pbase + v * fc, cp, n5);
       }
       if (a.Anext) {
 #pragma unroll
-        for (int v = 0; v < 5; ++v) lfv[v] = (a.lamf + pbase + v * fc)[cp];
+        for (int v = 0; v < 5; ++v) lfv[v] = NS_LD(g, a.lamf, pbase + v * fc, cp, n5);
       }
     }
     const CT* F0 = fslot(k);
@@ -585,7 +590,7 @@ __global__ void __launch_bounds__(NT, AdjMinBlocks<CT, ROE>::value) k_adj_stage(
       for (int v = 0; v < 5; ++v) gs[v] = gin[v] + gout[v];
       if (a.Gout) {
 #pragma unroll
-        for (int v = 0; v < 5; ++v) (a.Gout + pbase + v * fc)[cp] = gs[v];
+        for (int v = 0; v < 5; ++v) NS_ST(g, a.Gout, pbase + v * fc, cp, n5, gs[v]);
       }
       if (a.lam_out) {
         double lv[5];
@@ -593,19 +598,19 @@ __global__ void __launch_bounds__(NT, AdjMinBlocks<CT, ROE>::value) k_adj_stage(
         for (int v = 0; v < 5; ++v) lv[v] = widen(gs[v]);
         if (a.lam_in) {
 #pragma unroll
-          for (int v = 0; v < 5; ++v) lv[v] = (a.lam_in + pbase + v * fc)[cp] + lv[v];
+          for (int v = 0; v < 5; ++v) lv[v] = NS_LD(g, a.lam_in, pbase + v * fc, cp, n5) + lv[v];
         }
 #pragma unroll
-        for (int v = 0; v < 5; ++v) (a.lam_out + pbase + v * fc)[cp] = lv[v];
+        for (int v = 0; v < 5; ++v) NS_ST(g, a.lam_out, pbase + v * fc, cp, n5, lv[v]);
         if (a.lam_out_mirror) {
 #pragma unroll
-          for (int v = 0; v < 5; ++v) (a.lam_out_mirror + pbase + v * fc)[cp] = cvt<TST>(lv[v]);
+          for (int v = 0; v < 5; ++v) NS_ST(g, a.lam_out_mirror, pbase + v * fc, cp, n5, cvt<TST>(lv[v]));
         }
       }
       if (a.Anext) {
 #pragma unroll
         for (int v = 0; v < 5; ++v)
-          (a.Anext + pbase + v * fc)[cp] = CT(a.cl) * lfv[v] + CT(a.cg) * gout[v] + CT(a.cs) * gs[v];
+          NS_ST(g, a.Anext, pbase + v * fc, cp, n5, CT(a.cl) * lfv[v] + CT(a.cg) * gout[v] + CT(a.cs) * gs[v]);
       }
       if (a.SBout || a.sbar) {
         CT ss[5];
@@ -613,15 +618,15 @@ __global__ void __launch_bounds__(NT, AdjMinBlocks<CT, ROE>::value) k_adj_stage(
         for (int v = 0; v < 5; ++v) ss[v] = A0[v * SP + ic];
         if (a.SBin) {
 #pragma unroll
-          for (int v = 0; v < 5; ++v) ss[v] = (a.SBin + pbase + v * fc)[cp] + ss[v];
+          for (int v = 0; v < 5; ++v) ss[v] = NS_LD(g, a.SBin, pbase + v * fc, cp, n5) + ss[v];
         }
         if (a.SBout) {
 #pragma unroll
-          for (int v = 0; v < 5; ++v) (a.SBout + pbase + v * fc)[cp] = ss[v];
+          for (int v = 0; v < 5; ++v) NS_ST(g, a.SBout, pbase + v * fc, cp, n5, ss[v]);
         }
         if (a.sbar) {
 #pragma unroll
-          for (int v = 0; v < 5; ++v) (a.sbar + pbase + v * fc)[cp] += widen(ss[v]);
+          for (int v = 0; v < 5; ++v) NS_ST(g, a.sbar, pbase + v * fc, cp, n5, NS_LD(g, a.sbar, pbase + v * fc, cp, n5) + widen(ss[v]));
         }
       }
     }

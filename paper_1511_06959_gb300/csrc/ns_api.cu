@@ -373,6 +373,8 @@ const char* ns_error_string(int code) {
     case NS_ERR_NONFINITE: return "non-finite value detected";
     case NS_ERR_UNSTABLE: return "adjoint viscosity exceeds the explicit stability limit";
     case NS_ERR_CUDA: return "CUDA error";
+    case NS_ERR_CORRUPT: return "a checkpoint snapshot changed between store and load";
+    case NS_ERR_BOUNDS: return "a field index outside its field (bounds-checking build)";
     default: return "unknown error";
   }
 }
@@ -434,6 +436,7 @@ int ns_create(const ns_params* p, void* stream, ns_ctx** out) {
     return NS_ERR_CUDA;
   }
   c->ws_bytes = ns_ctx::NSTAGE * c->field * esz + c->scratch_n * sizeof(double) + sizeof(unsigned);
+  c->g.dbg_err = c->err;   // the bounds checks of debug builds report here
   *out = c;
   return NS_OK;
 }
@@ -780,6 +783,8 @@ int ns_last_error(ns_ctx* c) {
   if (cudaStreamSynchronize(c->st) != cudaSuccess) return NS_ERR_CUDA;
   if (cudaMemcpy(&h, c->err, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess) return NS_ERR_CUDA;
   if (cudaMemset(c->err, 0, sizeof(unsigned)) != cudaSuccess) return NS_ERR_CUDA;
+  if (h & ns::ERRBIT_BOUNDS) return NS_ERR_BOUNDS;
+  if (h & ns::ERRBIT_CORRUPT) return NS_ERR_CORRUPT;
   if (h & ns::ERRBIT_NONFINITE) return NS_ERR_NONFINITE;
   if (h & ns::ERRBIT_UNSTABLE) return NS_ERR_UNSTABLE;
   return NS_OK;

@@ -1,7 +1,7 @@
 // Shared device-side definitions of the NS stencil kernels (sm_103a).
 //
-// Tile geometry: a CTA owns TX x TY cell columns of one box (the adjoint stage kernel's
-// tile below; the primal stage kernel uses 32 x 8) and marches a range of
+// Tile geometry: a CTA owns TX x TY cell columns of one box (TX = 32 below; both stage
+// kernels use 32 x 8, their TY set in their own files) and marches a range of
 // z-planes, keeping a ring of three planes (k-1, k, k+1) of primitive variables with
 // a one-cell halo in x and y in shared memory.  Every face flux of the range is
 // computed once; periodic wrap is resolved when a plane is loaded, so every shared
@@ -29,16 +29,13 @@ inline std::atomic<unsigned long long> g_launches{0};
 inline void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 constexpr int TX = 32;
-constexpr int TY = 4;
-constexpr int NT = TX * TY;   // threads per CTA
 constexpr int SX = TX + 2;    // shared plane width incl. halo
-constexpr int SY = TY + 2;
-constexpr int SP = SX * SY;   // cells per shared plane
 
 struct GridDesc {
   int nx, ny, nz, batch;
   long long plane;     // nx * ny
   long long cells;     // nx * ny * nz  (one box)
+  unsigned* dbg_err;   // sticky error word for the bounds checks of debug builds (may be null)
 };
 
 constexpr int MIN_PLANES = 4;   // fewest planes per CTA range (bounds the priming share)
@@ -266,5 +263,36 @@ cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, 
 // ---------------------------------------------------------------------------------
 constexpr unsigned ERRBIT_NONFINITE = 1u;
 constexpr unsigned ERRBIT_UNSTABLE = 2u;
+constexpr unsigned ERRBIT_CORRUPT = 4u;
+constexpr unsigned ERRBIT_BOUNDS = 8u;
+
+// ---------------------------------------------------------------------------------
+// Field accesses of the stencil kernels.  A field element is addressed as a base (box,
+// plane and component: uniform over the CTA) plus the thread's in-plane offset.  Debug
+// builds (NS_DEBUG_BOUNDS) check the element index base + off against the field's
+// extent n before every access: an index outside [0, n) sets ERRBIT_BOUNDS in the
+// sticky error word and the access is skipped (a load reads zero), so a wrong index
+// shows as an error code instead of a memory fault.  Release builds access directly.
+// ---------------------------------------------------------------------------------
+#ifdef NS_DEBUG_BOUNDS
+__device__ __forceinline__ bool dbg_ok(const GridDesc& g, long long i, long long n) {
+  if (i >= 0 && i < n) return true;
+  if (g.dbg_err) atomicOr(g.dbg_err, ERRBIT_BOUNDS);
+  return false;
+}
+#define NS_LD(g, p, base, off, n)                                                                  \
+  (::ns::dbg_ok((g), (long long)(base) + (long long)(off), (long long)(n))                         \
+       ? ((p) + (base))[(off)]                                                                     \
+       : std::remove_cv_t<std::remove_reference_t<decltype((p)[0])>>(0))
+#define NS_ST(g, p, base, off, n, val)                                                             \
+  do {                                                                                             \
+    if (::ns::dbg_ok((g), (long long)(base) + (long long)(off), (long long)(n))) ((p) + (base))[(off)] = (val); \
+  } while (0)
+#define NS_IN_BOUNDS(g, i, n) (::ns::dbg_ok((g), (long long)(i), (long long)(n)))
+#else
+#define NS_IN_BOUNDS(g, i, n) true
+#define NS_LD(g, p, base, off, n) (((p) + (base))[(off)])
+#define NS_ST(g, p, base, off, n, val) (((p) + (base))[(off)] = (val))
+#endif
 
 }  // namespace ns

@@ -262,10 +262,15 @@ __global__ void __launch_bounds__(256, 3) k_mlp_infer(long long n, MlpView net, 
 // ------------------------------------------------------------------------------------
 // training: forward + backward of one minibatch chunk of TS samples per CTA, with the
 // quantisation points of the inference path; per-CTA gradient partials, then a fixed-
-// order reduction and an FP32 Adam update that also rewrites the inference copies
+// order reduction and an FP32 Adam update that also rewrites the inference copies.
+// Every matrix product (the two layers, the backward through layer 2 and the two
+// weight gradients) runs on the tensor cores as BF16 m16n8k16 products with FP32
+// accumulation; their operands are the BF16 values of the inference path (inputs,
+// weights, hidden activations) and, in the backward pass, the BF16-rounded gradients
+// dZ2 and dZ1 of the pre-activations (the bias gradients sum the FP32 ones).
 // ------------------------------------------------------------------------------------
 constexpr int TS = 64;       // samples per CTA
-constexpr int TT = 256;      // threads per CTA
+constexpr int TT = 256;      // threads per CTA (8 warps)
 constexpr int LD = NH + 1;   // padded row of the per-sample activations
 
 struct TrainSmem {
@@ -282,6 +287,37 @@ struct TrainSmem {
   float b3;
 };
 
+// acc += A (rows m0..m0+15, K columns) * B (K rows, columns n0..n0+7) on the tensor
+// cores, one warp; A(m, k) = As[m ars + k acs], B(k, n) = Bs[k brs + n bcs] are floats
+// in shared memory rounded to BF16 as they are packed into the fragments (the m16n8k16
+// layouts: A rows gq and gq + 8, columns 2tq.. of each 16-wide k slice; B columns gq,
+// rows 2tq..; the accumulator rows gq, gq + 8 and columns 2tq, 2tq + 1).
+__device__ __forceinline__ void mma_tile(const float* As, int ars, int acs, const float* Bs, int brs, int bcs,
+                                         int m0, int n0, int K, float acc[4]) {
+  const int lane = threadIdx.x & 31, gq = lane >> 2, tq = lane & 3;
+  for (int k0 = 0; k0 < K; k0 += 16) {
+    const int ka = k0 + 2 * tq;
+    const float* r0 = As + (m0 + gq) * ars;
+    const float* r1 = As + (m0 + gq + 8) * ars;
+    unsigned a[4];
+    a[0] = pack_bf16(r0[ka * acs], r0[(ka + 1) * acs]);
+    a[1] = pack_bf16(r1[ka * acs], r1[(ka + 1) * acs]);
+    a[2] = pack_bf16(r0[(ka + 8) * acs], r0[(ka + 9) * acs]);
+    a[3] = pack_bf16(r1[(ka + 8) * acs], r1[(ka + 9) * acs]);
+    const float* cb = Bs + (n0 + gq) * bcs;
+    const unsigned b0 = pack_bf16(cb[ka * brs], cb[(ka + 1) * brs]);
+    const unsigned b1 = pack_bf16(cb[(ka + 8) * brs], cb[(ka + 9) * brs]);
+    mma_bf16(acc, a, b0, b1);
+  }
+}
+
+// the (m, n) accumulator element of fragment slot q (0..3) of this lane
+__device__ __forceinline__ void acc_at(int m0, int n0, int q, int& m, int& n) {
+  const int lane = threadIdx.x & 31, gq = lane >> 2, tq = lane & 3;
+  m = m0 + gq + (q >= 2 ? 8 : 0);
+  n = n0 + 2 * tq + (q & 1);
+}
+
 __global__ void __launch_bounds__(TT) k_mlp_train_partial(MlpView net, const float* __restrict__ feat,
                                                           const float* __restrict__ target,
                                                           const int* __restrict__ idx, int n,
@@ -289,6 +325,7 @@ __global__ void __launch_bounds__(TT) k_mlp_train_partial(MlpView net, const flo
   extern __shared__ __align__(16) unsigned char smraw[];
   TrainSmem& S = *reinterpret_cast<TrainSmem*>(smraw);
   const int tid = threadIdx.x;
+  const int warp = tid >> 5;
   const float* P = net.master;
   for (int q = tid; q < NF * NH; q += TT) {
     const int k = q / NH, j = q % NH;
@@ -308,24 +345,32 @@ __global__ void __launch_bounds__(TT) k_mlp_train_partial(MlpView net, const flo
     S.X[s][k] = (gs < n && k < NIN) ? bfr(feat[(size_t)idx[gs] * 16 + k]) : 0.0f;
   }
   __syncthreads();
-  // layer 1
-  for (int q = tid; q < TS * NH; q += TT) {
-    const int s = q / NH, j = q % NH;
-    float acc = 0.0f;
+  // layer 1: Z1 = X W1 + b1 (64 x 16 by 16 x 64), H1 = bf16(gelu(Z1))
+  for (int t = warp; t < (TS / 16) * (NH / 8); t += TT / 32) {
+    const int m0 = (t / (NH / 8)) * 16, n0 = (t % (NH / 8)) * 8;
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    mma_tile(&S.X[0][0], NF, 1, &S.W1[0][0], NH, 1, m0, n0, NF, acc);
 #pragma unroll
-    for (int k = 0; k < NIN; ++k) acc += S.X[s][k] * S.W1[k][j];
-    const float z = acc + S.b1[j];
-    S.Z1[s][j] = z;
-    S.H1[s][j] = bfr(gelu(z));
+    for (int q = 0; q < 4; ++q) {
+      int m, nn;
+      acc_at(m0, n0, q, m, nn);
+      const float z = acc[q] + S.b1[nn];
+      S.Z1[m][nn] = z;
+      S.H1[m][nn] = bfr(gelu(z));
+    }
   }
   __syncthreads();
-  // layer 2
-  for (int q = tid; q < TS * NH; q += TT) {
-    const int s = q / NH, j = q % NH;
-    float acc = 0.0f;
-#pragma unroll 8
-    for (int k = 0; k < NH; ++k) acc += S.H1[s][k] * S.W2[k][j];
-    S.Z2[s][j] = acc + S.b2[j];
+  // layer 2: Z2 = H1 W2 + b2 (64 x 64 by 64 x 64)
+  for (int t = warp; t < (TS / 16) * (NH / 8); t += TT / 32) {
+    const int m0 = (t / (NH / 8)) * 16, n0 = (t % (NH / 8)) * 8;
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    mma_tile(&S.H1[0][0], LD, 1, &S.W2[0][0], LD, 1, m0, n0, NH, acc);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      int m, nn;
+      acc_at(m0, n0, q, m, nn);
+      S.Z2[m][nn] = acc[q] + S.b2[nn];
+    }
   }
   __syncthreads();
   // output, loss and dL/dy
@@ -349,28 +394,43 @@ __global__ void __launch_bounds__(TT) k_mlp_train_partial(MlpView net, const flo
     S.D2[s][j] = S.dy[s] * S.w3[j] * gelu_grad(S.Z2[s][j]);
   }
   __syncthreads();
-  // dZ1 = (dZ2 W2^T) gelu'(Z1)
-  for (int q = tid; q < TS * NH; q += TT) {
-    const int s = q / NH, k = q % NH;
-    float acc = 0.0f;
-#pragma unroll 8
-    for (int j = 0; j < NH; ++j) acc += S.D2[s][j] * S.W2[k][j];
-    S.D1[s][k] = acc * gelu_grad(S.Z1[s][k]);
+  // dZ1 = (bf16(dZ2) W2^T) gelu'(Z1): A(s, j) = D2[s][j], B(j, k) = W2[k][j]
+  for (int t = warp; t < (TS / 16) * (NH / 8); t += TT / 32) {
+    const int m0 = (t / (NH / 8)) * 16, n0 = (t % (NH / 8)) * 8;
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    mma_tile(&S.D2[0][0], LD, 1, &S.W2[0][0], 1, LD, m0, n0, NH, acc);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      int m, kk;
+      acc_at(m0, n0, q, m, kk);
+      S.D1[m][kk] = acc[q] * gelu_grad(S.Z1[m][kk]);
+    }
   }
   __syncthreads();
-  // gradient partials of this CTA, in parameter order
+  // weight gradients of this CTA, in parameter order:
+  //   dW2[k][j] = sum_s H1[s][k] bf16(dZ2[s][j]),  dW1[k][j] = sum_s X[s][k] bf16(dZ1[s][j])
   float* G = partial + (size_t)blockIdx.x * NPAR;
-  for (int q = tid; q < NIN * NH; q += TT) {
-    const int k = q / NH, j = q % NH;
-    float acc = 0.0f;
-    for (int s = 0; s < TS; ++s) acc += S.X[s][k] * S.D1[s][j];
-    G[OFF_W1 + q] = acc;
+  for (int t = warp; t < (NH / 16) * (NH / 8); t += TT / 32) {
+    const int m0 = (t / (NH / 8)) * 16, n0 = (t % (NH / 8)) * 8;
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    mma_tile(&S.H1[0][0], 1, LD, &S.D2[0][0], LD, 1, m0, n0, TS, acc);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      int k, j;
+      acc_at(m0, n0, q, k, j);
+      G[OFF_W2 + k * NH + j] = acc[q];
+    }
   }
-  for (int q = tid; q < NH * NH; q += TT) {
-    const int k = q / NH, j = q % NH;
-    float acc = 0.0f;
-    for (int s = 0; s < TS; ++s) acc += S.H1[s][k] * S.D2[s][j];
-    G[OFF_W2 + q] = acc;
+  if (warp < NH / 8) {
+    const int n0 = warp * 8;
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    mma_tile(&S.X[0][0], 1, NF, &S.D1[0][0], LD, 1, 0, n0, TS, acc);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      int k, j;
+      acc_at(0, n0, q, k, j);
+      if (k < NIN) G[OFF_W1 + k * NH + j] = acc[q];
+    }
   }
   for (int j = tid; j < NH; j += TT) {
     float a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;

@@ -38,14 +38,19 @@ template <class CT, class TIN>
 struct Loader {
   const TIN* W;
   const double* Wd;
-  __device__ __forceinline__ CT ld(size_t base, int off) const { return cvt<CT>((W + base)[off]); }
+  const GridDesc* g;
+  __device__ __forceinline__ CT ld(size_t base, int off) const {
+    return cvt<CT>(NS_LD(*g, W, base, off, 5 * g->cells * g->batch));
+  }
 };
 template <>
 struct Loader<Dual, double> {
   const double* W;
   const double* Wd;
+  const GridDesc* g;
   __device__ __forceinline__ Dual ld(size_t base, int off) const {
-    return Dual((W + base)[off], (Wd + base)[off]);
+    const long long n = 5 * g->cells * g->batch;
+    return Dual(NS_LD(*g, W, base, off, n), NS_LD(*g, Wd, base, off, n));
   }
 };
 
@@ -249,7 +254,7 @@ __global__ void __launch_bounds__(NT, RhsMinBlocks<CT, ROE>::value) k_rhs_stage(
   CT* sFY = sFX + 5 * TY * (TX + 1);                  // [5][TY+1][TX]
   const int tid = threadIdx.x;
   const int tx = tid % TX, ty = tid / TX;
-  Loader<CT, TIN> in{a.W, a.Wd};
+  Loader<CT, TIN> in{a.W, a.Wd, &g};
   int b, x0, y0, kz0, kz1;
   march_range<TX, TY>(g, b, x0, y0, kz0, kz1);
   const int gx = x0 + tx, gy = y0 + ty;
@@ -283,6 +288,8 @@ __global__ void __launch_bounds__(NT, RhsMinBlocks<CT, ROE>::value) k_rhs_stage(
     PlaneRegs<CT> pf;
     if (more) plane_load(pf, g, boxoff, k + 2, h, in);
     const size_t pb = boxoff + (size_t)k * g.plane;   // component 0 of plane k
+    const long long n5 = 5 * g.cells * g.batch;        // field extent (debug bounds checks)
+    (void)n5;
     // epilogue operands of this plane, issued before the face fluxes so that their
     // latency overlaps the flux arithmetic (scalar path)
     CT e_src[5], e_dacc[5], e_base[5];
@@ -296,15 +303,15 @@ __global__ void __launch_bounds__(NT, RhsMinBlocks<CT, ROE>::value) k_rhs_stage(
       if (valid) {
         if (a.src) {
 #pragma unroll
-          for (int v = 0; v < 5; ++v) e_src[v] = cvt<CT>((a.src + pb + v * (size_t)g.cells)[cp]);
+          for (int v = 0; v < 5; ++v) e_src[v] = cvt<CT>(NS_LD(g, a.src, pb + v * (size_t)g.cells, cp, n5));
         }
         if (a.dacc && !a.dacc_init) {
 #pragma unroll
-          for (int v = 0; v < 5; ++v) e_dacc[v] = CT((a.dacc + pb + v * (size_t)g.cells)[cp]);
+          for (int v = 0; v < 5; ++v) e_dacc[v] = CT(NS_LD(g, a.dacc, pb + v * (size_t)g.cells, cp, n5));
         }
         if (a.Wout) {
 #pragma unroll
-          for (int v = 0; v < 5; ++v) e_base[v] = CT((a.base + pb + v * (size_t)g.cells)[cp]);
+          for (int v = 0; v < 5; ++v) e_base[v] = CT(NS_LD(g, a.base, pb + v * (size_t)g.cells, cp, n5));
         }
       }
     }
@@ -347,6 +354,7 @@ __global__ void __launch_bounds__(NT, RhsMinBlocks<CT, ROE>::value) k_rhs_stage(
 #pragma unroll
         for (int v = 0; v < 5; ++v) {
           const size_t o = pb + v * (size_t)g.cells + cp;
+          if (!NS_IN_BOUNDS(g, o, n5)) continue;
           double Rv = R[v].v, Rd = R[v].d;
           if (a.src) Rv += a.src[o];
           if (a.srcd) Rd += a.srcd[o];
@@ -374,27 +382,27 @@ __global__ void __launch_bounds__(NT, RhsMinBlocks<CT, ROE>::value) k_rhs_stage(
           double e_wbase[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
           if (a.wbase) {
 #pragma unroll
-            for (int v = 0; v < 5; ++v) e_wbase[v] = (a.wbase + pb + v * (size_t)g.cells)[cp];
+            for (int v = 0; v < 5; ++v) e_wbase[v] = NS_LD(g, a.wbase, pb + v * (size_t)g.cells, cp, n5);
           }
           if (a.wout_mirror) {
 #pragma unroll
             for (int v = 0; v < 5; ++v) {
               const double wv = e_wbase[v] + widen(dv[v]);
-              (a.wout + pb + v * (size_t)g.cells)[cp] = wv;
-              (a.wout_mirror + pb + v * (size_t)g.cells)[cp] = cvt<TST>(wv);
+              NS_ST(g, a.wout, pb + v * (size_t)g.cells, cp, n5, wv);
+              NS_ST(g, a.wout_mirror, pb + v * (size_t)g.cells, cp, n5, cvt<TST>(wv));
             }
           } else {
 #pragma unroll
-            for (int v = 0; v < 5; ++v) (a.wout + pb + v * (size_t)g.cells)[cp] = e_wbase[v] + widen(dv[v]);
+            for (int v = 0; v < 5; ++v) NS_ST(g, a.wout, pb + v * (size_t)g.cells, cp, n5, e_wbase[v] + widen(dv[v]));
           }
         } else if (a.dacc) {
 #pragma unroll
-          for (int v = 0; v < 5; ++v) (a.dacc + pb + v * (size_t)g.cells)[cp] = dv[v];
+          for (int v = 0; v < 5; ++v) NS_ST(g, a.dacc, pb + v * (size_t)g.cells, cp, n5, dv[v]);
         }
         if (a.Wout) {
 #pragma unroll
           for (int v = 0; v < 5; ++v)
-            (a.Wout + pb + v * (size_t)g.cells)[cp] = e_base[v] + CT(a.cout) * Rv[v] + CT(a.cd) * dv[v];
+            NS_ST(g, a.Wout, pb + v * (size_t)g.cells, cp, n5, e_base[v] + CT(a.cout) * Rv[v] + CT(a.cd) * dv[v]);
         }
       }
     }

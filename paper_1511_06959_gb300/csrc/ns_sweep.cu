@@ -38,6 +38,45 @@ int revolve_split(int l, int s) {
   return (int)m;
 }
 
+// Snapshot checksum: sum over the 64-bit words w_i of a state of mix(w_i + (i + 1) K),
+// mix the splitmix64 finaliser, mod 2^64.  Integer addition mod 2^64 is exactly
+// associative, so the atomic per-block accumulation gives the same value in any order.
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__global__ void k_checksum(const unsigned long long* __restrict__ x, size_t n, unsigned long long* out) {
+  unsigned long long s = 0ull;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    s += mix64(x[i] + (unsigned long long)(i + 1) * 0x9E3779B97F4A7C15ull);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(out, s);
+}
+
+__global__ void k_checksum_check(const unsigned long long* a, const unsigned long long* b, unsigned* err) {
+  if (*a != *b) atomicOr(err, ns::ERRBIT_CORRUPT);
+}
+
+// out = checksum of n 64-bit words (zeroed first)
+int checksum(ns_ctx* c, const void* x, size_t n, unsigned long long* out) {
+  if (cudaMemsetAsync(out, 0, sizeof(unsigned long long), c->st) != cudaSuccess) return NS_ERR_CUDA;
+  k_checksum<<<152 * 4, 256, 0, c->st>>>((const unsigned long long*)x, n, out);
+  ns::count_launch();
+  return cudaGetLastError() == cudaSuccess ? NS_OK : NS_ERR_CUDA;
+}
+
+// the checksum of x against the stored one; a mismatch sets the corrupt bit
+int checksum_verify(ns_ctx* c, const void* x, size_t n, unsigned long long* tmp, const unsigned long long* want) {
+  int r = checksum(c, x, n, tmp);
+  if (r) return r;
+  k_checksum_check<<<1, 1, 0, c->st>>>(tmp, want, c->err);
+  ns::count_launch();
+  return cudaGetLastError() == cudaSuccess ? NS_OK : NS_ERR_CUDA;
+}
+
 struct Planner {
   std::vector<ns_action> acts;
   std::vector<int> free_slots;
@@ -241,11 +280,12 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 // the stage states W2..W4 computed when the segment was replayed), so that the adjoint
 // of a replayed step neither recomputes its stages nor converts its state.
 struct Layout {
-  size_t state, lam, sig, nu, scal, feat, stage, mir, lmir, keep, total;
+  size_t state, lam, sig, nu, scal, feat, stage, mir, lmir, keep, sums, total;
   int nbuf, nkeep;
 };
 
-Layout layout_for(const ns_ctx* c, int slots_used, bool closure, int schedule, int param) {
+Layout layout_for(const ns_ctx* c, int slots_used, bool closure, int schedule, int param, int host_slots = 0,
+                  bool verify = false) {
   Layout L;
   L.nbuf = slots_used + 2;
   L.state = align256(c->field * sizeof(double));
@@ -262,7 +302,9 @@ Layout layout_for(const ns_ctx* c, int slots_used, bool closure, int schedule, i
   L.lmir = c->p.precision == NS_MIXED ? 2 * L.stage : 0;
   L.nkeep = (schedule == NS_CKPT_STRIDE || schedule == NS_CKPT_STRIDE_HOST) ? param : 0;
   L.keep = (size_t)L.nkeep * 4 * L.stage;
-  L.total = L.state * L.nbuf + L.lam + L.sig + L.nu + L.scal + L.feat + L.mir + L.lmir + L.keep;
+  // snapshot checksums: one per device slot and per host slot, and one to verify into
+  L.sums = verify ? align256(sizeof(unsigned long long) * (size_t)(slots_used + host_slots + 1)) : 0;
+  L.total = L.state * L.nbuf + L.lam + L.sig + L.nu + L.scal + L.feat + L.mir + L.lmir + L.keep + L.sums;
   return L;
 }
 
@@ -289,7 +331,7 @@ size_t ns_run_arena_bytes(const ns_ctx* c, const ns_run_opts* o) {
   if (!c || !o) return 0;
   Planner P;
   if (make_plan(o->nsteps, o->schedule, o->param, P)) return 0;
-  return layout_for(c, P.maxlive, o->mlp != nullptr, o->schedule, o->param).total;
+  return layout_for(c, P.maxlive, o->mlp != nullptr, o->schedule, o->param, P.maxhost, o->verify != 0).total;
 }
 
 size_t ns_run_host_bytes(const ns_ctx* c, const ns_run_opts* o) {
@@ -314,6 +356,7 @@ struct ns_sweep_state {
   float* sig = nullptr;
   float* nu = nullptr;
   bool f64nu = false;                // sigma_1 and nu held in FP64 (the regions hold doubles)
+  unsigned long long* sums = nullptr; // snapshot checksums (verify): device slots, host slots, scratch
   double* jtmp = nullptr;
   float* feat = nullptr;
   double* Jbar = nullptr;
@@ -423,9 +466,13 @@ int run_actions(ns_ctx* c, ns_sweep_state& S, int stop_op, double*& lam_cur, dou
         if (S.cur < 0) return NS_ERR_ARG;
         S.slot_buf[A.b] = S.cur;
         S.owned[S.cur] = 1;
+        if (S.sums && (r = checksum(c, S.buf[S.cur], c->field, S.sums + A.b))) return r;
         break;
       case NS_OP_LOAD: {
         S.cur = A.b < 0 ? -1 : S.slot_buf[A.b];
+        if (S.sums && A.b >= 0 &&
+            (r = checksum_verify(c, S.buf[S.cur], c->field, S.sums + S.P.maxlive + S.P.maxhost, S.sums + A.b)))
+          return r;
         const int K = S.L.nkeep;
         S.cur_mirror = (S.mixed && S.in_backward && S.kept_valid(A.a) && S.has_mirror[A.a % K])
                            ? S.keep[(size_t)(A.a % K) * 4]
@@ -440,6 +487,7 @@ int run_actions(ns_ctx* c, ns_sweep_state& S, int stop_op, double*& lam_cur, dou
         // stream-ordered: later kernels that reuse the buffer run after the copy
         if (S.cur < 0 || A.b < 0 || A.b >= S.P.maxhost) return NS_ERR_ARG;
         char* hp = (char*)S.o.host_arena + (size_t)A.b * S.L.state;
+        if (S.sums && (r = checksum(c, S.buf[S.cur], c->field, S.sums + S.P.maxlive + A.b))) return r;
         if (cudaMemcpyAsync(hp, S.buf[S.cur], c->field * sizeof(double), cudaMemcpyDeviceToHost, c->st) !=
             cudaSuccess)
           return NS_ERR_CUDA;
@@ -453,6 +501,9 @@ int run_actions(ns_ctx* c, ns_sweep_state& S, int stop_op, double*& lam_cur, dou
         if (cudaMemcpyAsync(S.buf[out], hp, c->field * sizeof(double), cudaMemcpyHostToDevice, c->st) !=
             cudaSuccess)
           return NS_ERR_CUDA;
+        if (S.sums && (r = checksum_verify(c, S.buf[out], c->field, S.sums + S.P.maxlive + S.P.maxhost,
+                                           S.sums + S.P.maxlive + A.b)))
+          return r;
         S.cur = out;
         S.cur_mirror = nullptr;
         break;
@@ -539,7 +590,7 @@ static int forward_run_impl(ns_ctx* c, const double* w0, const double* s, const 
     delete S;
     return r;
   }
-  S->L = layout_for(c, S->P.maxlive, o->mlp != nullptr, o->schedule, o->param);
+  S->L = layout_for(c, S->P.maxlive, o->mlp != nullptr, o->schedule, o->param, S->P.maxhost, o->verify != 0);
   if (arena_bytes < S->L.total) {
     delete S;
     return NS_ERR_BUDGET;
@@ -576,6 +627,8 @@ static int forward_run_impl(ns_ctx* c, const double* w0, const double* s, const 
   q += S->L.lmir;
   S->keep.resize((size_t)S->L.nkeep * 4);
   for (size_t i = 0; i < S->keep.size(); ++i) S->keep[i] = q + i * S->L.stage;
+  q += S->L.keep;
+  S->sums = S->L.sums ? (unsigned long long*)q : nullptr;
   S->has_mirror.assign(S->L.nkeep, 0);
   S->has_stages.assign(S->L.nkeep, 0);
   S->mixed = c->p.precision == NS_MIXED;

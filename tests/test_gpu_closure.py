@@ -81,7 +81,9 @@ def test_training_step_gradient_matches_oracle():
     S.mlp_get_moment(net.blob, 1, m)
     g_gpu = host(m).astype(np.float64) / 0.1
     p64 = {k: np.asarray(v, dtype=np.float64) for k, v in p.items()}
-    L, g = ML.loss_and_grads(p64, feat[idx, :14].astype(np.float64), target[idx].astype(np.float64), True)
+    # the tensor-core backward rounds dZ2 and dZ1 to BF16 where they enter products
+    L, g = ML.loss_and_grads(p64, feat[idx, :14].astype(np.float64), target[idx].astype(np.float64), True,
+                             bf16_backward=True)
     g_ref = C.pack(g).astype(np.float64)
     assert abs(loss.item() - L) < 1e-4 * L
     assert rel_l2(g_gpu, g_ref) < 2e-3

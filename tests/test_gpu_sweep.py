@@ -158,3 +158,43 @@ def test_host_snapshots_give_the_stride_bits(prec):
         S.adjoint_run(dev(w0), opts, arena, torch.empty(1, dtype=torch.float64, device="cuda"),
                       torch.empty(w0.shape, dtype=torch.float64, device="cuda"))
     assert e.value.code == api.NS_ERR_BUDGET
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_verified_snapshots_keep_the_bits_and_a_corrupted_host_snapshot_is_reported(prec):
+    """With verify on, every schedule gives the unverified sweep's bits and a clear error
+    word; a byte flipped in a host-tier snapshot between the forward and the backward
+    half (host memory, the caller's arena) is reported as NS_ERR_CORRUPT when the
+    snapshot comes back."""
+    api = _api()
+    w0 = synth.isentropic_vortex(33, 10, 3, noise=1e-3, seed=5)
+    P = params_for(w0, mu=1e-3, dt=4e-3)
+    N = 13
+    S = make_solver(api, w0, P, prec)
+    J0, lam0, _, _, _ = _run(api, S, w0, N, api.NS_CKPT_STRIDE, 4)
+    J = torch.empty(1, dtype=torch.float64, device="cuda")
+    lam = torch.empty_like(lam0)
+    for sched, prm in [(api.NS_CKPT_STRIDE, 4), (api.NS_CKPT_REVOLVE, 3), (api.NS_CKPT_STRIDE_HOST, 4)]:
+        host = None
+        if sched == api.NS_CKPT_STRIDE_HOST:
+            host = torch.zeros(S.host_bytes(S.run_opts(N, sched, prm)), dtype=torch.uint8, pin_memory=True)
+        opts = S.run_opts(N, sched, prm, host_arena=host, verify=True)
+        assert S.arena_bytes(opts) > S.arena_bytes(S.run_opts(N, sched, prm, host_arena=host))
+        arena = torch.empty(S.arena_bytes(opts), dtype=torch.uint8, device="cuda")
+        S.adjoint_run(dev(w0), opts, arena, J, lam)
+        torch.cuda.synchronize()
+        assert S.last_error() == 0
+        assert torch.equal(J, J0) and torch.equal(lam, lam0)
+    # forward half, then a flipped byte in the second host snapshot (step 8), then backward
+    host = torch.zeros(S.host_bytes(S.run_opts(N, api.NS_CKPT_STRIDE_HOST, 4)), dtype=torch.uint8,
+                       pin_memory=True)
+    opts = S.run_opts(N, api.NS_CKPT_STRIDE_HOST, 4, host_arena=host, verify=True)
+    arena = torch.empty(S.arena_bytes(opts), dtype=torch.uint8, device="cuda")
+    S.forward_run(dev(w0), opts, arena, J)
+    torch.cuda.synchronize()
+    slot = host.numel() // 3
+    host[slot + 1000] ^= 0x10
+    S.backward_run(lam)
+    torch.cuda.synchronize()
+    assert S.last_error() == api.NS_ERR_CORRUPT
+    assert S.last_error() == 0          # the word is cleared by the read

@@ -164,3 +164,34 @@ def test_label_closed_form_on_a_sinusoidal_shear(nz):
     got = ML.label_rate(w, lam, P)
     np.testing.assert_allclose(got, expect, rtol=1e-10, atol=1e-12 * expect.max())
     assert np.count_nonzero(expect) > expect.size // 4   # both signs of the growth occur
+
+
+def test_bf16_backward_moves_each_gradient_within_its_rounding_bound():
+    """Rounding dZ2 and dZ1 to BF16 before the products they enter leaves the loss and
+    the gradients that do not pass through them (w3, b3, b2) unchanged, and moves every
+    weight-gradient entry by at most its products' magnitudes times the BF16 unit
+    roundoff 2^-8 (8 significant bits, round to nearest: one rounding per product for
+    W2; for W1, the rounding of dZ1 plus the propagated rounding of dZ2 through dH1)."""
+    rng = np.random.default_rng(21)
+    X = rng.standard_normal((96, ML.NIN))
+    t = np.abs(rng.standard_normal(96))
+    p = ML.init_params(22)
+    L0, g0 = ML.loss_and_grads(p, X, t, True, bf16_backward=False)
+    L1, g1 = ML.loss_and_grads(p, X, t, True, bf16_backward=True)
+    assert L0 == L1
+    for k in ("w3", "b3", "b2"):
+        assert np.array_equal(g0[k], g1[k]), k
+    u = 2.0 ** -8
+    _, _, c = ML.forward(p, X, True)
+    y = c["y"]
+    dy = 2.0 * (ML.softplus(y) - t) / X.shape[0] * ML.softplus_grad(y)
+    dZ2 = np.outer(dy, ML.bf16(p["w3"])) * ML.gelu_grad(c["Z2"])
+    bound_W2 = np.abs(c["H1q"]).T @ np.abs(dZ2) * u
+    assert np.all(np.abs(g1["W2"] - g0["W2"]) <= bound_W2 * (1 + 1e-9) + 1e-300)
+    assert not np.array_equal(g1["W2"], g0["W2"])          # the rounding is really there
+    dH1_abs = np.abs(dZ2) @ np.abs(ML.bf16(p["W2"])).T
+    dZ1_abs = dH1_abs * np.abs(ML.gelu_grad(c["Z1"]))
+    bound_W1 = np.abs(c["X0"]).T @ (dZ1_abs * (2 * u + u * u))
+    assert np.all(np.abs(g1["W1"] - g0["W1"]) <= bound_W1 * (1 + 1e-9) + 1e-300)
+    bound_b1 = np.sum(dZ1_abs * u, axis=0)
+    assert np.all(np.abs(g1["b1"] - g0["b1"]) <= bound_b1 * (1 + 1e-9) + 1e-300)
