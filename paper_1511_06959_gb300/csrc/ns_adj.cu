@@ -600,6 +600,18 @@ __global__ void __launch_bounds__(NT, AdjMinBlocks<CT, ROE>::value) k_adj_stage(
 #pragma unroll
           for (int v = 0; v < 5; ++v) lv[v] = NS_LD(g, a.lam_in, pbase + v * fc, cp, n5) + lv[v];
         }
+        if (a.obj_ndsc && (gx == a.obj_iL || gx == a.obj_iR)) {
+          // the objective source of this step on the plane's two columns, added after
+          // the stage products (the order of the separate scatter it replaces)
+          const int nf = g.ny * g.nz;
+          const double* Af = a.obj_aface + ((size_t)b * nf + (size_t)k * g.ny + gy) * 5;
+          const double NoD = a.obj_ndsc[2 * b], sc = a.obj_ndsc[2 * b + 1];
+          const int reps = (gx == a.obj_iL ? 1 : 0) + (gx == a.obj_iR ? 1 : 0);
+          for (int q = 0; q < reps; ++q) {
+#pragma unroll
+            for (int v = 0; v < 5; ++v) lv[v] += sc * (Af[v] - (v == 0 ? NoD : 0.0));
+          }
+        }
 #pragma unroll
         for (int v = 0; v < 5; ++v) NS_ST(g, a.lam_out, pbase + v * fc, cp, n5, lv[v]);
         if (a.lam_out_mirror) {

@@ -154,7 +154,8 @@ static cudaError_t adj_launch(ns_ctx* c, const Coef<CT>& cf, const ns::AdjArgs<T
 template <class CT>
 static int adjoint_step_t(ns_ctx* c, const Coef<CT>& cf, const CT* W1, const CT* lamf, const double* s,
                           const double* lam, const float* nu, double* lo, double* sbar,
-                          const CT* const* kept = nullptr, CT* lo_mirror = nullptr, const double* nud = nullptr) {
+                          const CT* const* kept = nullptr, CT* lo_mirror = nullptr, const double* nud = nullptr,
+                          const ns_obj_src* obj = nullptr) {
   const Scheme& sc = scheme_of(c);
   const double dt = c->p.dt;
   const CT* Wst[3];
@@ -197,6 +198,12 @@ static int adjoint_step_t(ns_ctx* c, const Coef<CT>& cf, const CT* W1, const CT*
       a.lam_in = lam;
       a.lam_out = lo;
       a.lam_out_mirror = lo_mirror;
+      if (obj) {
+        a.obj_aface = obj->aface;
+        a.obj_ndsc = obj->ndsc;
+        a.obj_iL = obj->iL;
+        a.obj_iR = obj->iR;
+      }
     }
     if (sbar) {
       a.SBin = j == 0 ? nullptr : S;
@@ -836,9 +843,17 @@ int ns_i_primal(ns_ctx* c, const double* w, const void* w_mirror, const double* 
   return primal_step_t<double>(c, c->cd, w, w, s, wo, nullptr, (double* const*)keep3);
 }
 
+int ns_i_objective_sum(ns_ctx* c, const double* w, double weight, double* J_acc, ns_obj_src* obj) {
+  const int nx = c->g.nx, i0 = c->p.plane_i;
+  obj->iL = ((i0 - 1) % nx + nx) % nx;
+  obj->iR = (i0 % nx + nx) % nx;
+  return cuerr(ns::launch_objective_sum(c->g, c->p.gamma, i0, c->p.pt_in, w, weight, J_acc, c->err, c->scratch,
+                                        c->ticket, c->st, &obj->aface, &obj->ndsc));
+}
+
 int ns_i_adjoint(ns_ctx* c, const double* w, const void* w_mirror, const void* const* kept3, const double* s,
                  const double* lam, const void* lam_mirror, const float* nu, double* lo, void* lo_mirror,
-                 double* sbar, const double* nud) {
+                 double* sbar, const double* nud, const ns_obj_src* obj) {
   if (mixed(c)) {
     const float* W1 = (const float*)w_mirror;
     if (!W1) {
@@ -853,10 +868,10 @@ int ns_i_adjoint(ns_ctx* c, const double* w, const void* w_mirror, const void* c
       lf = t;
     }
     return adjoint_step_t<float>(c, c->cf, W1, lf, s, lam, nu, lo, sbar, (const float* const*)kept3,
-                                 (float*)lo_mirror);
+                                 (float*)lo_mirror, nullptr, obj);
   }
   return adjoint_step_t<double>(c, c->cd, w, lam, s, lam, nu, lo, sbar, (const double* const*)kept3, nullptr,
-                                nud);
+                                nud, obj);
 }
 
 int ns_i_energy(ns_ctx* c, const double* w, const void* w_mirror, const double* lam, const void* lam_mirror,
@@ -869,11 +884,6 @@ int ns_i_energy(ns_ctx* c, const double* w, const void* w_mirror, const double* 
   return ns_adjoint_energy(c, w, lam, E);
 }
 
-int ns_i_objective(ns_ctx* c, const double* w, double weight, double* J_acc, double* lam, void* lam_mirror) {
-  return cuerr(ns::launch_objective_fast(c->g, c->p.gamma, c->p.plane_i, c->p.pt_in, w, weight, J_acc, lam,
-                                         c->err, c->scratch, c->ticket, c->st,
-                                         mixed(c) ? (float*)lam_mirror : nullptr));
-}
 
 int ns_i_sigma1_f64(ns_ctx* c, const double* w, double* sigma1, double* stats, double lambda, double tau,
                     double* nu) {

@@ -58,16 +58,23 @@ void ns_sweep_release(ns_ctx* c);
 // the input and output states and kept stage states W2..W4 (stage-type buffers)
 int ns_i_primal(ns_ctx* c, const double* w, const void* w_mirror, const double* s, double* wo, void* wo_mirror,
                 void* const* keep3);
+// the objective source of an adjoint step, folded into its last transposed stage
+struct ns_obj_src {
+  const double* aface;
+  const double* ndsc;
+  int iL, iR;
+};
 int ns_i_adjoint(ns_ctx* c, const double* w, const void* w_mirror, const void* const* kept3, const double* s,
                  const double* lam, const void* lam_mirror, const float* nu, double* lo, void* lo_mirror,
-                 double* sbar, const double* nud = nullptr);
+                 double* sbar, const double* nud = nullptr, const ns_obj_src* obj = nullptr);
+// J_acc += weight J(w) and the gradient factors of the objective source for ns_i_adjoint
+// (uses the context's reduction scratch until the adjoint step has run)
+int ns_i_objective_sum(ns_ctx* c, const double* w, double weight, double* J_acc, ns_obj_src* obj);
 // ns_mlp_features from the float mirror of w when given (mixed mode; the same bits)
 int ns_i_mlp_features(ns_ctx* c, const double* w, const void* w_mirror, float* feat);
 // ns_adjoint_energy from the float mirrors of w and lam when both are given (mixed mode)
 int ns_i_energy(ns_ctx* c, const double* w, const void* w_mirror, const double* lam, const void* lam_mirror,
                 double* E);
-// ns_objective that also keeps a stage-type mirror of lam (mixed mode; may be null) in step
-int ns_i_objective(ns_ctx* c, const double* w, double weight, double* J_acc, double* lam, void* lam_mirror);
 // sigma_1 (and its stats when stats != null); with nu != null also the viscosity of the
 // sigma_1 rule (nu = lambda sigma_1 [sigma_1 > tau]) with the stability flag
 int ns_i_sigma1(ns_ctx* c, const double* w, const void* w_mirror, float* sigma1, double* stats,

@@ -886,6 +886,23 @@ cudaError_t launch_objective_fast(const GridDesc& g, double gamma, int plane_i, 
   return e;
 }
 
+cudaError_t launch_objective_sum(const GridDesc& g, double gamma, int plane_i, double pt_in, const double* w,
+                                 double weight, double* J_acc, unsigned* err, double* scratch, unsigned* ticket,
+                                 cudaStream_t st, const double** aface_out, const double** ndsc_out) {
+  const int nf = g.ny * g.nz;
+  int nblk = (nf + OMB - 1) / OMB;
+  if (nblk > RG) nblk = RG;
+  double* partial = scratch;
+  double* ndsc = scratch + (size_t)2 * RG * g.batch;
+  double* aface = ndsc + 2 * (size_t)g.batch;
+  cudaError_t e = launch_pdl(k_obj_sum, dim3(nblk, g.batch), dim3(OMB), 0, st, g, gamma, plane_i, pt_in, w, weight,
+                             J_acc, true, err, partial, aface, ndsc, ticket);
+  count_launch();
+  *aface_out = aface;
+  *ndsc_out = ndsc;
+  return e;
+}
+
 template <class CT>
 cudaError_t launch_sigma1(const GridDesc& g, const Coef<CT>& c, const CT* w, float* sigma1,
                           double* stats, double* scratch, unsigned* ticket, cudaStream_t st,

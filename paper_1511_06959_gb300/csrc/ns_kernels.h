@@ -61,6 +61,12 @@ struct AdjArgs {
   const TST* SBin;
   TST* SBout;
   double* sbar;
+  // objective source folded into the last stage (lam_out != 0): when obj_ndsc != 0,
+  // lam_out of the cells of plane columns obj_iL and obj_iR also receives
+  // sc (aface[f][v] - [v = 0] N/D), f = z ny + y, (N/D, sc) = obj_ndsc[2b..] (k_obj_sum)
+  const double* obj_aface;
+  const double* obj_ndsc;
+  int obj_iL, obj_iR;
 };
 
 template <class CT, class TIN, class TST>
@@ -77,6 +83,12 @@ size_t diag_scratch_doubles(const GridDesc& g, int nphi);
 cudaError_t launch_objective(const GridDesc& g, double gamma, int plane_i, double pt_in,
                              const double* w, double weight, double* J_acc, double* lam,
                              unsigned* err, double* scratch, cudaStream_t st);
+// the objective's plane sums and per-face gradient factors alone (k_obj_sum with the
+// gradient): J_acc += weight J; *aface, *ndsc receive the factors for an adjoint stage
+// that adds the gradient (AdjArgs::obj_*)
+cudaError_t launch_objective_sum(const GridDesc& g, double gamma, int plane_i, double pt_in, const double* w,
+                                 double weight, double* J_acc, unsigned* err, double* scratch, unsigned* ticket,
+                                 cudaStream_t st, const double** aface, const double** ndsc);
 // two-launch objective (value in one launch); ticket: batch zero-initialised counters
 cudaError_t launch_objective_fast(const GridDesc& g, double gamma, int plane_i, double pt_in, const double* w,
                                    double weight, double* J_acc, double* lam, unsigned* err, double* scratch,

@@ -554,13 +554,17 @@ int run_actions(ns_ctx* c, ns_sweep_state& S, int stop_op, double*& lam_cur, dou
             nup = S.nu;
           }
         }
+        // the objective of w^n (n >= 1): its plane sums first, its source folded into the
+        // last transposed stage of this step
+        ns_obj_src obj{};
+        if (A.a >= 1 && (r = ns_i_objective_sum(c, ptr(S.cur), wN, S.jtmp, &obj))) return r;
         if ((r = ns_i_adjoint(c, ptr(S.cur), mirror, kept ? kept3 : nullptr, S.s, lam_cur,
-                              S.lamf_valid ? S.lamf_cur : nullptr, nup, lam_nxt, S.lamf_nxt, sbar, nudp)))
+                              S.lamf_valid ? S.lamf_cur : nullptr, nup, lam_nxt, S.lamf_nxt, sbar, nudp,
+                              A.a >= 1 ? &obj : nullptr)))
           return r;
         std::swap(lam_cur, lam_nxt);
         std::swap(S.lamf_cur, S.lamf_nxt);
         S.lamf_valid = S.lamf_cur != nullptr;
-        if (A.a >= 1 && (r = ns_i_objective(c, ptr(S.cur), wN, S.jtmp, lam_cur, S.lamf_cur))) return r;
         if (S.o.record_energy && energy &&
             (r = ns_i_energy(c, ptr(S.cur), mirror, lam_cur, S.lamf_valid ? S.lamf_cur : nullptr,
                              energy + (size_t)A.a * B)))

@@ -1,0 +1,131 @@
+"""The adjoint of a statistically stationary turbulent box: a periodic box driven by a
+time-constant Kolmogorov shear force on the x-momentum equation (synth.kolmogorov_forcing)
+is spun up from a noisy uniform stream until its turbulence is developed; then the
+checkpointed adjoint of the pressure loss runs over a horizon from that state, and its
+adjoint energy growth (section "Results": the adjoint of a turbulent flow grows
+exponentially; section "Energy analysis": the sigma_1-scaled viscosity counters it) is
+fitted, and optionally the viscosity scaling factor is chosen over candidates
+(ns_estimate_lambda).
+
+The forcing amplitude follows from the laminar Kolmogorov profile it would sustain:
+u_1 = U0 sin(2 pi y / L_y) with mu (2 pi / L_y)^2 U0 = amp, at the forcing Reynolds number
+Re_f = rho U0 L_y / mu.
+
+    python -m paper_1511_06959_gb300.forced_study --spinup 6000 --nsteps 2000 \
+        --lambdas 0,0.05,0.1,0.2,0.4,0.8 --out forced128.json
+
+Prints one JSON object.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import time
+
+import numpy as np
+import torch
+
+from . import api
+from . import synth
+
+
+def run(nx, ny, nz, U0, Re_f, mach, spinup, nsteps, stride, lambdas, precision, cfl, seed):
+    gamma = 1.4
+    dx = synth.box_shape(nx, ny, nz)
+    Ly = ny * dx[1]
+    mu = U0 * Ly / Re_f
+    amp = U0 * mu * (2.0 * math.pi / Ly) ** 2
+    w0 = synth.forced_start(nx, ny, nz, mach=mach, seed=seed, gamma=gamma)
+    s_h = synth.kolmogorov_forcing(nx, ny, nz, amp)
+    pt_in = (1.0 / gamma) * (1.0 + 0.5 * (gamma - 1.0) * mach ** 2) ** (gamma / (gamma - 1.0))
+    S = api.Solver(nx, ny, nz, dx, gamma=gamma, mu=mu, Pr=0.72, dt=0.0, precision=precision,
+                   plane_i=(3 * nx) // 4, pt_in=pt_in)
+    w = torch.from_numpy(w0).cuda()
+    s = torch.from_numpy(s_h).cuda()
+    # dt from the largest wave speed the developed flow is expected to reach (the stream
+    # plus twice the laminar amplitude), at the given CFL number
+    dt = cfl * min(dx) / (1.0 + mach + 2.0 * U0)
+    S.set_dt(dt)
+    t0 = time.perf_counter()
+    a, b = w.clone(), torch.empty_like(w)
+    history = []
+    for n in range(spinup):
+        S.primal_step(a, b, s)
+        a, b = b, a
+        if (n + 1) % max(1, spinup // 10) == 0:
+            u = a[1:4] / a[0]
+            ke = float(0.5 * (a[0] * ((u[0] - mach) ** 2 + u[1] ** 2 + u[2] ** 2)).mean())
+            history.append({"step": n + 1, "fluct_kinetic_energy": ke})
+    torch.cuda.synchronize()
+    t_spin = time.perf_counter() - t0
+    m = torch.empty(1, dtype=torch.float64, device="cuda")
+    S.max_wave_speed(a, m)
+    wspun = a.contiguous()
+    out = {"box": [nx, ny, nz], "mu": mu, "forcing_amplitude": amp, "U0": U0, "Re_f": Re_f, "mach": mach,
+           "dt": dt, "cfl_at_spun_state": dt * m.item() / min(dx), "spinup_steps": spinup,
+           "spinup_seconds": t_spin, "spinup_history": history, "finite": bool(torch.isfinite(wspun).all())}
+    if not out["finite"]:
+        return out
+    # the plain adjoint from the developed state
+    opts = S.run_opts(nsteps, api.NS_CKPT_STRIDE, stride, 0.0, 0.0, True, True)
+    arena = torch.empty(S.arena_bytes(opts), dtype=torch.uint8, device="cuda")
+    J = torch.empty(1, dtype=torch.float64, device="cuda")
+    lam0 = torch.empty_like(wspun)
+    E = torch.zeros((nsteps + 1, 1), dtype=torch.float64, device="cuda")
+    sig = torch.zeros((nsteps, 1, 2), dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    S.adjoint_run(wspun, opts, arena, J, lam0, s=s, energy=E, sigma_stats=sig)
+    torch.cuda.synchronize()
+    Eh = E.cpu().numpy()[:, 0]
+    sh = sig.cpu().numpy()[:, 0, :]
+    norm = [float(Eh[nsteps - m] / (m + 1) ** 2) for m in (0, nsteps // 4, nsteps // 2, 3 * nsteps // 4, nsteps)]
+    out.update({"nsteps": nsteps, "adjoint_seconds": time.perf_counter() - t0, "J_bar": float(J.item()),
+                "E_normalised_at_m": dict(zip(["0", "N/4", "N/2", "3N/4", "N"], norm)),
+                "efolds": api.energy_efolds(E.cpu().numpy(), nsteps, 1)[0],
+                "sigma1_max_range": [float(sh[:, 0].min()), float(sh[:, 0].max())],
+                "sigma1_mean_range": [float(sh[:, 1].min()), float(sh[:, 1].max())],
+                "sticky_error": S.last_error()})
+    if lambdas:
+        lam_coefs = [t * dx[0] ** 2 for t in lambdas]
+        opts = S.run_opts(nsteps, api.NS_CKPT_STRIDE, stride)
+        arena = torch.empty(S.arena_bytes(opts), dtype=torch.uint8, device="cuda")
+        work = torch.empty(S.estimate_work_bytes(opts), dtype=torch.uint8, device="cuda")
+        t0 = time.perf_counter()
+        chosen, ef, ch = S.estimate_lambda(wspun, opts, lam_coefs, arena, work, s=s)
+        out.update({"lambda_tilde": list(lambdas), "lambda_efolds": ef, "lambda_change": ch,
+                    "chosen_index": chosen, "chosen_lambda_tilde": lambdas[chosen] if chosen >= 0 else None,
+                    "lambda_seconds": time.perf_counter() - t0, "sticky_error_lambda": S.last_error()})
+    return out
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--nx", type=int, default=128)
+    ap.add_argument("--ny", type=int, default=64)
+    ap.add_argument("--nz", type=int, default=64)
+    ap.add_argument("--U0", type=float, default=0.3)
+    ap.add_argument("--Re-f", type=float, default=2000.0)
+    ap.add_argument("--mach", type=float, default=0.3)
+    ap.add_argument("--spinup", type=int, default=6000)
+    ap.add_argument("--nsteps", type=int, default=2000)
+    ap.add_argument("--stride", type=int, default=50)
+    ap.add_argument("--lambdas", default="")
+    ap.add_argument("--fp64", action="store_true")
+    ap.add_argument("--cfl", type=float, default=0.5)
+    ap.add_argument("--seed", type=int, default=5)
+    ap.add_argument("--out", default=None)
+    a = ap.parse_args(argv)
+    lambdas = tuple(float(t) for t in a.lambdas.split(",")) if a.lambdas else ()
+    res = run(a.nx, a.ny, a.nz, a.U0, a.Re_f, a.mach, a.spinup, a.nsteps, a.stride, lambdas,
+              api.NS_FP64 if a.fp64 else api.NS_MIXED, a.cfl, a.seed)
+    line = json.dumps(res)
+    print(line)
+    if a.out:
+        with open(a.out, "w") as f:
+            f.write(line + "\n")
+
+
+if __name__ == "__main__":
+    main()

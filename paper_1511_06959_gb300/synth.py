@@ -172,3 +172,27 @@ def perturbed_uniform(nx, ny, nz, seed, amp=0.05, mach=0.5, gamma=1.4):
                   (amp * rng.standard_normal(shp)) if nz > 1 else np.zeros(shp)])
     p = (1.0 / gamma) * (1.0 + amp * rng.standard_normal(shp))
     return _conservative(rho, u, p, gamma)
+
+
+def kolmogorov_forcing(nx, ny, nz, amp, k=1):
+    """A time-constant body force on the x-momentum equation, s_1 = amp sin(2 pi k y / L_y)
+    (the other components zero): a Kolmogorov shear forcing that keeps a periodic box
+    turbulent instead of decaying.  Its y-mean is zero, so it adds no net momentum."""
+    X, Y, Z, (Lx, Ly, Lz) = _centres(nx, ny, nz)
+    s = np.zeros((5, nz, ny, nx))
+    s[1] = amp * np.sin(2.0 * math.pi * k * Y / Ly)
+    return s
+
+
+def forced_start(nx, ny, nz, mach=0.3, noise=0.02, seed=5, gamma=1.4):
+    """Initial state of a forced box: a uniform stream of the given Mach number along x
+    (rho = 1, p = 1/gamma, sound speed 1) with seeded relative noise on every velocity
+    component, from which the forcing's shear layers grow and break down."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    shp = (nz, ny, nx)
+    rho = np.ones(shp)
+    u = np.stack([mach + noise * mach * rng.standard_normal(shp),
+                  noise * mach * rng.standard_normal(shp),
+                  noise * mach * rng.standard_normal(shp) if nz > 1 else np.zeros(shp)])
+    p = np.full(shp, 1.0 / gamma)
+    return _conservative(rho, u, p, gamma)

@@ -113,3 +113,42 @@ def test_candidate_sweep_follows_the_store_all_adjoint():
     assert chosen == O.select_lambda(efolds, change, 1.0, 0.1)
     # more viscosity, less adjoint energy at the end of the sweep
     assert energies[2][0] < energies[1][0] < energies[0][0]
+
+
+@pytest.mark.parametrize("efold_tol,rel_tol", [(1.0, 0.1), (1.0, 0.02), (0.25, 0.1), (3.0, 0.5), (-0.5, 0.1)])
+def test_rule_on_a_constructed_family_with_a_closed_form_answer(efold_tol, rel_tol):
+    """A family of candidate runs built so that the right factor follows in closed form,
+    independent of the paper's table: candidate i (lambda_i = i h) has the adjoint
+    energy E_i^m = (N - m + 1)^2 exp(a_i (N - m)) with a growth rate a_i = a0 - k lambda_i
+    that the viscosity lowers, and the source sensitivity g_i = s + b lambda_i v (the
+    bias the viscosity adds) plus, while a_i > 0, an error that grows with exp(a_i N)
+    (the growing, wrong adjoint).  The energy fit returns a_i M exactly, and for damped
+    neighbours the change is b h |v| / |s + b lambda_{i+1} v|; the rule must pick the
+    smallest i meeting both thresholds."""
+    N, M = 40, 20
+    h, a0, k, b = 1e-3, 0.12, 30.0, 2.0
+    lam = h * np.arange(12)
+    rng = np.random.default_rng(3)
+    s = rng.standard_normal(50)
+    v = rng.standard_normal(50)
+    err = rng.standard_normal((12, 50))
+    a = a0 - k * lam
+    E = [[(N - m + 1) ** 2 * math.exp(a[i] * (N - m)) for m in range(N + 1)] for i in range(12)]
+    g = [s + b * lam[i] * v + (1e-3 * math.exp(a[i] * N) * err[i] if a[i] > 0 else 0.0) for i in range(12)]
+    ef = [O.energy_efolds(E[i]) for i in range(12)]
+    np.testing.assert_allclose(ef, a * M, rtol=1e-12, atol=1e-12)
+    ch = [O.sensitivity_change(g[i], g[i + 1]) for i in range(11)]
+    expect = -1
+    for i in range(11):
+        damped = a[i] * M <= efold_tol
+        if a[i + 1] <= 0 and a[i] <= 0:
+            closed = b * h * np.linalg.norm(v) / np.linalg.norm(s + b * lam[i + 1] * v)
+            assert ch[i] == pytest.approx(closed, rel=1e-12)
+        if damped and ch[i] <= rel_tol:
+            expect = i
+            break
+    assert O.select_lambda(ef, ch, efold_tol, rel_tol) == expect
+    if efold_tol >= 0.25 and rel_tol >= 0.1:
+        # with these thresholds the first damped candidate (a_i <= efold_tol / M) is chosen
+        first = int(np.argmax(a * M <= efold_tol))
+        assert expect == first
