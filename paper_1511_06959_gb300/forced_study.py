@@ -1,6 +1,7 @@
 """The adjoint of a statistically stationary turbulent box: a periodic box driven by a
 time-constant Kolmogorov shear force on the x-momentum equation (synth.kolmogorov_forcing)
-is spun up from a noisy uniform stream until its turbulence is developed; then the
+is spun up from the laminar shear profile the force sustains, with noise, until the
+profile's instability has grown into turbulence; then the
 checkpointed adjoint of the pressure loss runs over a horizon from that state, and its
 adjoint energy growth (section "Results": the adjoint of a turbulent flow grows
 exponentially; section "Energy analysis": the sigma_1-scaled viscosity counters it) is
@@ -30,17 +31,44 @@ from . import api
 from . import synth
 
 
-def run(nx, ny, nz, U0, Re_f, mach, spinup, nsteps, stride, lambdas, precision, cfl, seed):
+def separation(S, w, s, nsteps, eps=1e-9, seed=17):
+    """Growth of a small perturbation of w along the forced trajectory: two primal runs
+    from w and w + eps r (r seeded, unit rms per component), the rms difference recorded
+    every nsteps // 20 steps.  A chaotic flow separates exponentially at its leading
+    Lyapunov exponent, which bounds the adjoint's growth rate from below."""
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    r = torch.randn(w.shape, generator=g, dtype=torch.float64).to(w.device)
+    a, a2 = w.clone(), w + eps * r
+    b, b2 = torch.empty_like(a), torch.empty_like(a)
+    d0 = float((a2 - a).pow(2).mean().sqrt())
+    out = []
+    every = max(1, nsteps // 20)
+    for n in range(nsteps):
+        S.primal_step(a, b, s)
+        S.primal_step(a2, b2, s)
+        a, b = b, a
+        a2, b2 = b2, a2
+        if (n + 1) % every == 0:
+            out.append((n + 1, float((a2 - a).pow(2).mean().sqrt()) / d0))
+    return out
+
+
+def run(nx, ny, nz, U0, Re_f, mach, spinup, nsteps, stride, lambdas, precision, cfl, seed, flux="central",
+        sep_steps=0):
     gamma = 1.4
     dx = synth.box_shape(nx, ny, nz)
     Ly = ny * dx[1]
     mu = U0 * Ly / Re_f
     amp = U0 * mu * (2.0 * math.pi / Ly) ** 2
-    w0 = synth.forced_start(nx, ny, nz, mach=mach, seed=seed, gamma=gamma)
+    # start on the laminar profile the forcing sustains: its shear instability then grows
+    # from the noise at inviscid rates instead of the profile building up on the viscous
+    # time scale L_y^2 / nu
+    w0 = synth.forced_start(nx, ny, nz, mach=mach, shear=U0, seed=seed, gamma=gamma)
     s_h = synth.kolmogorov_forcing(nx, ny, nz, amp)
     pt_in = (1.0 / gamma) * (1.0 + 0.5 * (gamma - 1.0) * mach ** 2) ** (gamma / (gamma - 1.0))
     S = api.Solver(nx, ny, nz, dx, gamma=gamma, mu=mu, Pr=0.72, dt=0.0, precision=precision,
-                   plane_i=(3 * nx) // 4, pt_in=pt_in)
+                   plane_i=(3 * nx) // 4, pt_in=pt_in,
+                   flux=api.NS_FLUX_ROE if flux == "roe" else api.NS_FLUX_CENTRAL)
     w = torch.from_numpy(w0).cuda()
     s = torch.from_numpy(s_h).cuda()
     # dt from the largest wave speed the developed flow is expected to reach (the stream
@@ -55,18 +83,26 @@ def run(nx, ny, nz, U0, Re_f, mach, spinup, nsteps, stride, lambdas, precision, 
         a, b = b, a
         if (n + 1) % max(1, spinup // 10) == 0:
             u = a[1:4] / a[0]
-            ke = float(0.5 * (a[0] * ((u[0] - mach) ** 2 + u[1] ** 2 + u[2] ** 2)).mean())
-            history.append({"step": n + 1, "fluct_kinetic_energy": ke})
+            # kinetic energy of the cross-stream velocity: zero on the laminar profile
+            ke = float(0.5 * (a[0] * (u[1] ** 2 + u[2] ** 2)).mean())
+            history.append({"step": n + 1, "cross_stream_kinetic_energy": ke})
     torch.cuda.synchronize()
     t_spin = time.perf_counter() - t0
     m = torch.empty(1, dtype=torch.float64, device="cuda")
     S.max_wave_speed(a, m)
     wspun = a.contiguous()
-    out = {"box": [nx, ny, nz], "mu": mu, "forcing_amplitude": amp, "U0": U0, "Re_f": Re_f, "mach": mach,
+    out = {"box": [nx, ny, nz], "flux": flux, "mu": mu, "forcing_amplitude": amp, "U0": U0, "Re_f": Re_f, "mach": mach,
            "dt": dt, "cfl_at_spun_state": dt * m.item() / min(dx), "spinup_steps": spinup,
            "spinup_seconds": t_spin, "spinup_history": history, "finite": bool(torch.isfinite(wspun).all())}
     if not out["finite"]:
         return out
+    if sep_steps:
+        sep = separation(S, wspun, s, sep_steps)
+        out["separation"] = sep
+        # e-folds per step of the separation's growth over the second half of the record
+        h = sep[len(sep) // 2:]
+        if len(h) >= 2 and h[0][1] > 0 and h[-1][1] > 0:
+            out["separation_efolds_per_step"] = math.log(h[-1][1] / h[0][1]) / (h[-1][0] - h[0][0])
     # the plain adjoint from the developed state
     opts = S.run_opts(nsteps, api.NS_CKPT_STRIDE, stride, 0.0, 0.0, True, True)
     arena = torch.empty(S.arena_bytes(opts), dtype=torch.uint8, device="cuda")
@@ -115,11 +151,14 @@ def main(argv=None):
     ap.add_argument("--fp64", action="store_true")
     ap.add_argument("--cfl", type=float, default=0.5)
     ap.add_argument("--seed", type=int, default=5)
+    ap.add_argument("--flux", default="central", choices=["central", "roe"])
+    ap.add_argument("--separation", type=int, default=0,
+                    help="steps of the twin primal run that measures perturbation growth")
     ap.add_argument("--out", default=None)
     a = ap.parse_args(argv)
     lambdas = tuple(float(t) for t in a.lambdas.split(",")) if a.lambdas else ()
     res = run(a.nx, a.ny, a.nz, a.U0, a.Re_f, a.mach, a.spinup, a.nsteps, a.stride, lambdas,
-              api.NS_FP64 if a.fp64 else api.NS_MIXED, a.cfl, a.seed)
+              api.NS_FP64 if a.fp64 else api.NS_MIXED, a.cfl, a.seed, a.flux, a.separation)
     line = json.dumps(res)
     print(line)
     if a.out:

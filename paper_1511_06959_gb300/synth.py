@@ -184,15 +184,19 @@ def kolmogorov_forcing(nx, ny, nz, amp, k=1):
     return s
 
 
-def forced_start(nx, ny, nz, mach=0.3, noise=0.02, seed=5, gamma=1.4):
-    """Initial state of a forced box: a uniform stream of the given Mach number along x
-    (rho = 1, p = 1/gamma, sound speed 1) with seeded relative noise on every velocity
-    component, from which the forcing's shear layers grow and break down."""
+def forced_start(nx, ny, nz, mach=0.3, shear=0.0, k=1, noise=0.02, seed=5, gamma=1.4):
+    """Initial state of a forced box: a stream of the given Mach number along x (rho = 1,
+    p = 1/gamma, sound speed 1) carrying the shear profile shear sin(2 pi k y / L_y) that
+    the Kolmogorov forcing sustains, with seeded noise of relative size noise (of the
+    larger of mach and shear) on every velocity component, from which the shear layers'
+    instability grows."""
     rng = np.random.Generator(np.random.PCG64(seed))
     shp = (nz, ny, nx)
+    X, Y, Z, (Lx, Ly, Lz) = _centres(nx, ny, nz)
     rho = np.ones(shp)
-    u = np.stack([mach + noise * mach * rng.standard_normal(shp),
-                  noise * mach * rng.standard_normal(shp),
-                  noise * mach * rng.standard_normal(shp) if nz > 1 else np.zeros(shp)])
+    a = noise * max(mach, shear)
+    u = np.stack([mach + shear * np.sin(2.0 * math.pi * k * Y / Ly) + a * rng.standard_normal(shp),
+                  a * rng.standard_normal(shp),
+                  a * rng.standard_normal(shp) if nz > 1 else np.zeros(shp)])
     p = np.full(shp, 1.0 / gamma)
     return _conservative(rho, u, p, gamma)
