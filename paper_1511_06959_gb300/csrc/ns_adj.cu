@@ -204,24 +204,70 @@ __device__ __forceinline__ const CT& yf(const CT* F, int j, int fy, int col) {
   return F[j * NF + NXF + fy * SX + col];
 }
 
+// Face values of one plane slot, each face once.  Every thread computes its own cell's
+// lower x-face (shared row ty+1, fx = tx) and lower y-face (fy = ty, column tx+1); the
+// NRF remaining faces (x-faces of the halo rows and of the last column, y-faces of the
+// last row and of the halo columns) go to threads t < NRF.
+constexpr int NRF = NF - 2 * NT;
+static_assert(NRF == 2 * (SX - 1) + TY + SX + 2 * TY, "remaining faces of a plane slot");
+
 template <class CT>
-__device__ __forceinline__ void fill_faces(CT* F, const CT* sQ, const CT* sA, const Coef<CT>& c,
-                                           int slot) {
+__device__ __forceinline__ void store_face(CT* __restrict__ F, int t, const CT sv[3], CT fb4) {
+#pragma unroll
+  for (int j = 0; j < 3; ++j) F[j * NF + t] = sv[j];
+  F[3 * NF + t] = fb4;
+}
+
+template <class CT>
+__device__ __forceinline__ void fill_faces(CT* __restrict__ F, const CT* __restrict__ sQ,
+                                           const CT* __restrict__ sA, const Coef<CT>& c, int slot) {
   const CT* Q = sQ + slot * 5 * SP;
   const CT* A = sA + slot * 5 * SP;
-  for (int t = threadIdx.x; t < NF; t += NT) {
-    CT sv[3], fb4;
-    if (t < NXF) {
-      const int row = t / (SX - 1);
-      const int iL = row * SX + (t - row * (SX - 1));
+  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+  CT sv[3], fb4;
+  {
+    const int iL = (ty + 1) * SX + tx;
+    face_s<0>(c, Q, A, iL, Q, A, iL + 1, sv, fb4);
+    store_face(F, (ty + 1) * (SX - 1) + tx, sv, fb4);
+  }
+  {
+    const int iL = ty * SX + tx + 1;
+    face_s<1>(c, Q, A, iL, Q, A, iL + SX, sv, fb4);
+    store_face(F, NXF + iL, sv, fb4);
+  }
+  const int t = threadIdx.x;
+  if (t < NRF) {
+    if (t < 2 * (SX - 1) + TY) {
+      // x-faces: halo row 0, halo row SY-1, then the last face (fx = SX-2) of rows 1..TY
+      int row, fx;
+      if (t < SX - 1) {
+        row = 0;
+        fx = t;
+      } else if (t < 2 * (SX - 1)) {
+        row = SY - 1;
+        fx = t - (SX - 1);
+      } else {
+        row = 1 + t - 2 * (SX - 1);
+        fx = SX - 2;
+      }
+      const int iL = row * SX + fx;
       face_s<0>(c, Q, A, iL, Q, A, iL + 1, sv, fb4);
+      store_face(F, row * (SX - 1) + fx, sv, fb4);
     } else {
-      const int iL = t - NXF;   // fy * SX + col
+      // y-faces: the last row of faces (fy = TY) at every column, then columns 0 and SX-1
+      const int r = t - (2 * (SX - 1) + TY);
+      int fy, col;
+      if (r < SX) {
+        fy = TY;
+        col = r;
+      } else {
+        fy = (r - SX) >> 1;
+        col = ((r - SX) & 1) ? SX - 1 : 0;
+      }
+      const int iL = fy * SX + col;
       face_s<1>(c, Q, A, iL, Q, A, iL + SX, sv, fb4);
+      store_face(F, NXF + iL, sv, fb4);
     }
-#pragma unroll
-    for (int j = 0; j < 3; ++j) F[j * NF + t] = sv[j];
-    F[3 * NF + t] = fb4;
   }
 }
 
@@ -271,8 +317,8 @@ __device__ __forceinline__ void ypacket(const CT* sQ, const CT* F0, const Coef<C
 }
 
 template <class CT>
-__device__ __forceinline__ void zpacket(const CT* sQ, const CT* sA, const Coef<CT>& c, int sL,
-                                        int sR, int i, CT pk[7]) {
+__device__ __forceinline__ void zpacket(const CT* sQ, const Coef<CT>& c, int sL, int sR, int i,
+                                        const CT s[3], CT fb4, CT pk[7]) {
   const CT* QL = sQ + sL * 5 * SP;
   const CT* QR = sQ + sR * 5 * SP;
   CT gx[3], gy[3];
@@ -283,7 +329,7 @@ __device__ __forceinline__ void zpacket(const CT* sQ, const CT* sA, const Coef<C
     diff4_pair(a[i + 1], a[i - 1], bq[i + 1], bq[i - 1], c.i4dx[0], a[i + SX], a[i - SX], bq[i + SX],
                bq[i - SX], c.i4dx[1], gx[k], gy[k]);
   }
-  face_packet<2>(c, QL, sA + sL * 5 * SP, i, QR, sA + sR * 5 * SP, i, gx, gy, pk);
+  face_packet_s<2>(c, s, fb4, QL, i, QR, i, gx, gy, pk);
 }
 
 // Roe part of a face packet: the adjoints of the two cells' primitives from the Roe
@@ -302,19 +348,37 @@ __device__ __forceinline__ void roe_packet(const Coef<CT>& c, const CT* QL, cons
   roe_dissipation_adj<D>(c, qL, qR, Db, pk, pk + 5);
 }
 
-// z-face s-vectors between plane slots sL and sR at every shared column.
+// z-face s-vectors between plane slots sL and sR at every shared column: the thread's own
+// column ic (its s-vector and Fb[4] also returned for its z-packet) and the NH halo
+// positions of the slot (rows 0 and SY-1, then columns 0 and SX-1 of rows 1..TY) by
+// threads t < NH.
+constexpr int NH = 2 * SX + 2 * TY;
+static_assert(NH + NT == SP, "halo positions of a plane slot");
+
 template <class CT>
-__device__ __forceinline__ void fill_Z(CT* Z, const CT* sQ, const CT* sA, const Coef<CT>& c,
-                                       int sL, int sR) {
+__device__ __forceinline__ void fill_Z(CT* __restrict__ Z, const CT* __restrict__ sQ,
+                                       const CT* __restrict__ sA, const Coef<CT>& c, int sL, int sR, int ic,
+                                       CT s_own[3], CT& fb_own) {
   const CT* QL = sQ + sL * 5 * SP;
   const CT* AL = sA + sL * 5 * SP;
   const CT* QR = sQ + sR * 5 * SP;
   const CT* AR = sA + sR * 5 * SP;
-  for (int t = threadIdx.x; t < SP; t += NT) {
-    CT s[3], f;
-    face_s<2>(c, QL, AL, t, QR, AR, t, s, f);
+  face_s<2>(c, QL, AL, ic, QR, AR, ic, s_own, fb_own);
 #pragma unroll
-    for (int j = 0; j < 3; ++j) Z[j * SP + t] = s[j];
+  for (int j = 0; j < 3; ++j) Z[j * SP + ic] = s_own[j];
+  const int t = threadIdx.x;
+  if (t < NH) {
+    int i;
+    if (t < SX) i = t;
+    else if (t < 2 * SX) i = (SY - 1) * SX + (t - SX);
+    else {
+      const int r = t - 2 * SX;
+      i = (1 + (r >> 1)) * SX + ((r & 1) ? SX - 1 : 0);
+    }
+    CT sv[3], f;
+    face_s<2>(c, QL, AL, i, QR, AR, i, sv, f);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) Z[j * SP + i] = sv[j];
   }
 }
 
@@ -370,10 +434,11 @@ __global__ void __launch_bounds__(NT, AdjMinBlocks<CT, ROE>::value) k_adj_stage(
   __syncthreads();
   fill_faces(fslot(kz0 - 1), sQ, sA, c, slot(kz0 - 1));
   fill_faces(fslot(kz0), sQ, sA, c, slot(kz0));
-  fill_Z(sZ + zslot(kz0 - 1) * 3 * SP, sQ, sA, c, slot(kz0 - 1), slot(kz0));
   const int ic = (ty + 1) * SX + (tx + 1);
+  CT zs[3], zf;
+  fill_Z(sZ + zslot(kz0 - 1) * 3 * SP, sQ, sA, c, slot(kz0 - 1), slot(kz0), ic, zs, zf);
   CT zlo[NPK], zhi[NPK];
-  zpacket(sQ, sA, c, slot(kz0 - 1), slot(kz0), ic, zlo);
+  zpacket(sQ, c, slot(kz0 - 1), slot(kz0), ic, zs, zf, zlo);
   if constexpr (ROE)
     roe_packet<2>(c, sQ + slot(kz0 - 1) * 5 * SP, sA + slot(kz0 - 1) * 5 * SP, ic, sQ + slot(kz0) * 5 * SP,
                   sA + slot(kz0) * 5 * SP, ic, zlo + 7);
@@ -408,23 +473,23 @@ __global__ void __launch_bounds__(NT, AdjMinBlocks<CT, ROE>::value) k_adj_stage(
     }
     const CT* F0 = fslot(k);
     fill_faces(fslot(k + 1), sQ, sA, c, sp);
-    fill_Z(sZ + zslot(k) * 3 * SP, sQ, sA, c, s0, sp);
+    fill_Z(sZ + zslot(k) * 3 * SP, sQ, sA, c, s0, sp, ic, zs, zf);
     {
       const CT* Q0 = sQ + s0 * 5 * SP;
       const CT* A0 = sA + s0 * 5 * SP;
-      CT pk[NPK];
-      xpacket(sQ, F0, c, sm, s0, sp, ty + 1, tx, pk);
-      if constexpr (ROE) roe_packet<0>(c, Q0, A0, ic - 1, Q0, A0, ic, pk + 7);
+      CT pkx[NPK], pky[NPK];
+      xpacket(sQ, F0, c, sm, s0, sp, ty + 1, tx, pkx);
+      if constexpr (ROE) roe_packet<0>(c, Q0, A0, ic - 1, Q0, A0, ic, pkx + 7);
+      ypacket(sQ, F0, c, sm, s0, sp, ty, tx + 1, pky);
+      if constexpr (ROE) roe_packet<1>(c, Q0, A0, ic - SX, Q0, A0, ic, pky + 7);
+      zpacket(sQ, c, s0, sp, ic, zs, zf, zhi);
+      if constexpr (ROE)
+        roe_packet<2>(c, Q0, A0, ic, sQ + sp * 5 * SP, sA + sp * 5 * SP, ic, zhi + 7);
 #pragma unroll
-      for (int v = 0; v < NPK; ++v) sFX[(v * TY + ty) * (TX + 1) + tx] = pk[v];
-      ypacket(sQ, F0, c, sm, s0, sp, ty, tx + 1, pk);
-      if constexpr (ROE) roe_packet<1>(c, Q0, A0, ic - SX, Q0, A0, ic, pk + 7);
+      for (int v = 0; v < NPK; ++v) sFX[(v * TY + ty) * (TX + 1) + tx] = pkx[v];
 #pragma unroll
-      for (int v = 0; v < NPK; ++v) sFY[(v * (TY + 1) + ty) * TX + tx] = pk[v];
+      for (int v = 0; v < NPK; ++v) sFY[(v * (TY + 1) + ty) * TX + tx] = pky[v];
     }
-    zpacket(sQ, sA, c, s0, sp, ic, zhi);
-    if constexpr (ROE)
-      roe_packet<2>(c, sQ + s0 * 5 * SP, sA + s0 * 5 * SP, ic, sQ + sp * 5 * SP, sA + sp * 5 * SP, ic, zhi + 7);
     if (tid < TX) {
       CT pk[NPK];
       ypacket(sQ, F0, c, sm, s0, sp, TY, tid + 1, pk);

@@ -297,6 +297,9 @@ __device__ __forceinline__ Prim<T> prim_at(const T* __restrict__ w, size_t o, lo
 // polynomial with only real roots Laguerre's iteration started to the right of the
 // largest root decreases monotonically to it (cubically near a simple root), so a
 // fixed small number of steps suffices.  The matrix is scaled to unit trace first.
+// Only the lower triangle of A is read and written: step k reflects the column below
+// the diagonal onto its first entry (the off-diagonal alpha_k) and updates the trailing
+// block A[k+1.., k+1..] by the symmetric rank-2 form A - 2 (v q^T + q v^T).
 template <class T, int N>
 __device__ T max_eig_sym(T A[N][N]) {
   T tr = T(0);
@@ -307,8 +310,8 @@ __device__ T max_eig_sym(T A[N][N]) {
 #pragma unroll
   for (int i = 0; i < N; ++i)
 #pragma unroll
-    for (int j = 0; j < N; ++j) A[i][j] *= inv;
-  // Householder tridiagonalisation (A is symmetric; both triangles are kept)
+    for (int j = 0; j <= i; ++j) A[i][j] *= inv;
+  T off[N];   // off[i]: the entry (i+1, i) of the tridiagonal matrix
 #pragma unroll
   for (int k = 0; k < N - 2; ++k) {
     T nrm2 = T(0);
@@ -316,44 +319,46 @@ __device__ T max_eig_sym(T A[N][N]) {
     for (int i = k + 1; i < N; ++i) nrm2 += A[i][k] * A[i][k];
     const T x0 = A[k + 1][k];
     const T rest = nrm2 - x0 * x0;
+    off[k] = x0;
     if (!(rest > T(0))) continue;              // column already reduced
     const T nrm = sqrt(nrm2);
     const T alpha = x0 >= T(0) ? -nrm : nrm;
+    off[k] = alpha;
     T v[N];
 #pragma unroll
-    for (int i = 0; i < N; ++i) v[i] = i > k ? A[i][k] : T(0);
+    for (int i = k + 1; i < N; ++i) v[i] = A[i][k];
     v[k + 1] = x0 - alpha;
-    const T vn2 = v[k + 1] * v[k + 1] + rest;
-    const T sc = T(1) / sqrt(vn2);
+    const T sc = T(1) / sqrt(v[k + 1] * v[k + 1] + rest);
 #pragma unroll
     for (int i = k + 1; i < N; ++i) v[i] *= sc;
-    // p = A v, q = p - (v.p) v, A <- A - 2 (v q^T + q v^T)
-    T pv[N];
+    // p = B v over the trailing block B (lower triangle: B[i][j] = A[max][min])
+    T q[N];
 #pragma unroll
-    for (int i = 0; i < N; ++i) {
+    for (int i = k + 1; i < N; ++i) {
       T acc = T(0);
 #pragma unroll
-      for (int j = k + 1; j < N; ++j) acc += A[i][j] * v[j];
-      pv[i] = acc;
+      for (int j = k + 1; j < N; ++j) acc += (j <= i ? A[i][j] : A[j][i]) * v[j];
+      q[i] = acc;
     }
     T vp = T(0);
 #pragma unroll
-    for (int i = k + 1; i < N; ++i) vp += v[i] * pv[i];
+    for (int i = k + 1; i < N; ++i) vp += v[i] * q[i];
 #pragma unroll
-    for (int i = 0; i < N; ++i) pv[i] -= vp * v[i];
+    for (int i = k + 1; i < N; ++i) q[i] -= vp * v[i];
 #pragma unroll
-    for (int i = 0; i < N; ++i)
+    for (int i = k + 1; i < N; ++i)
 #pragma unroll
-      for (int j = 0; j < N; ++j) A[i][j] -= T(2) * (v[i] * pv[j] + pv[i] * v[j]);
+      for (int j = k + 1; j <= i; ++j) A[i][j] -= T(2) * (v[i] * q[j] + q[i] * v[j]);
   }
+  off[N - 2] = A[N - 1][N - 2];
   T d[N], e2[N];
   T ub = T(0);
 #pragma unroll
   for (int i = 0; i < N; ++i) {
     d[i] = A[i][i];
-    const T bl = i > 0 ? fabs(A[i][i - 1]) : T(0);
-    const T br = i < N - 1 ? fabs(A[i + 1][i]) : T(0);
-    e2[i] = i < N - 1 ? A[i + 1][i] * A[i + 1][i] : T(0);
+    const T bl = i > 0 ? fabs(off[i - 1]) : T(0);
+    const T br = i < N - 1 ? fabs(off[i]) : T(0);
+    e2[i] = i < N - 1 ? off[i] * off[i] : T(0);
     const T g = d[i] + bl + br;
     ub = g > ub ? g : ub;
   }
@@ -376,8 +381,9 @@ __device__ T max_eig_sym(T A[N][N]) {
       r0 = r1; r1 = r2;
     }
     if (p1 == T(0)) break;
-    const T G = q1 / p1;
-    const T H = G * G - r1 / p1;
+    const T ip = T(1) / p1;
+    const T G = q1 * ip;
+    const T H = G * G - r1 * ip;
     T disc = (n - T(1)) * (n * H - G * G);
     disc = disc > T(0) ? sqrt(disc) : T(0);
     const T den = G >= T(0) ? G + disc : G - disc;
@@ -406,8 +412,7 @@ __device__ T sigma1_of(const T M[5][5]) {
         const int kk = N == 5 ? id5[k] : id4[k];
         acc += M[kk][N == 5 ? id5[i] : id4[i]] * M[kk][N == 5 ? id5[j] : id4[j]];
       }
-      B[i][j] = acc;
-      B[j][i] = acc;
+      B[j][i] = acc;   // lower triangle (j >= i)
     }
   }
   const T l = max_eig_sym<T, N>(B);
