@@ -473,75 +473,225 @@ __device__ __forceinline__ void growth_matrix(const GridDesc& g, const Coef<CT>&
   M[4][4] -= gm1 / CT(2) * div;
 }
 
+// sigma_1 by plane marching.  A CTA owns a TX x SG_TY tile of columns and a range of
+// planes (march_range, as the stencil kernels); the primitives (rho, u1, u2, u3, p, a, b)
+// of three consecutive planes of the tile and its one-cell halo sit in a shared-memory
+// ring, filled from register-staged loads one plane ahead, so each state is loaded and
+// converted once per CTA instead of seven times per cell.  The growth matrix of a cell
+// is then the closed form of growth_matrix() on those values (the same operations, so the
+// same sigma_1 bits).  Statistics: every CTA writes its (max, sum) for its box and zeros
+// for the other boxes; the last CTA (ticket[0]) reduces them per box in a fixed order.
+namespace sgk {
+constexpr int TY = 8;
+constexpr int NT = TX * TY;
+constexpr int SY = TY + 2;
+constexpr int SP = SX * SY;
+constexpr int NV = 7;   // rho, u1, u2, u3, p, a, b
+static_assert(SP <= 2 * NT, "a plane must fit two load rounds");
+}  // namespace sgk
+
+size_t sigma1_march_ctas_bound(const GridDesc& g) {
+  // the padded (bounded) box has one more column on each side
+  const long long cols = (long long)((g.nx + 2 + TX - 1) / TX) * ((g.ny + 2 + sgk::TY - 1) / sgk::TY) * g.batch;
+  return (size_t)(cols > 2048 ? cols : 2048);
+}
+
 template <class CT>
-__global__ void __launch_bounds__(RB, sizeof(CT) == 4 ? 4 : 1) k_sigma1(GridDesc g, Coef<CT> c, const CT* __restrict__ w,
-                                               float* __restrict__ sig, double* partial, double* stats,
-                                               unsigned* ticket, NuRule rule, double* __restrict__ sigd) {
+__global__ void __launch_bounds__(sgk::NT, sizeof(CT) == 4 ? 3 : 1) k_sigma1(GridDesc g, Coef<CT> c,
+                                                                          const CT* __restrict__ w,
+                                                                          float* __restrict__ sig, double* partial,
+                                                                          double* stats, unsigned* ticket,
+                                                                          NuRule rule, double* __restrict__ sigd) {
+  using namespace sgk;
   pdl_enter();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  CT* sP = reinterpret_cast<CT*>(smem_raw);   // [3][NV][SP]
   __shared__ double sh[32];
   __shared__ bool last;
-  const int b = blockIdx.y;
-  // the max in the compute type (exact in any type), the sum in FP64
+  const int tid = threadIdx.x;
+  const int tx = tid % TX, ty = tid / TX;
+  int b, x0, y0, kz0, kz1;
+  march_range<TX, TY>(g, b, x0, y0, kz0, kz1);
+  const int gx = x0 + tx, gy = y0 + ty;
+  const bool valid = gx < g.nx && gy < g.ny;
+  const int cp = valid ? gy * g.nx + gx : 0;
+  const size_t boxoff = (size_t)b * 5 * g.cells;
+  const CT gam = c.gamma, gm1 = c.gm1;
+  const CT fb = CT(1) / sqrt(gam), fa = sqrt(gm1 / gam);
+  int ho[2];
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const int t = tid + it * NT;
+    const int ly = t / SX, lx = t - ly * SX;
+    ho[it] = t < SP ? wrap(y0 + ly - 1, g.ny) * g.nx + wrap(x0 + lx - 1, g.nx) : 0;
+  }
+  auto load = [&](CT (&q)[2][5], int k) {
+    const size_t pb = boxoff + (size_t)wrap(k, g.nz) * g.plane;
+#pragma unroll
+    for (int it = 0; it < 2; ++it)
+      if (tid + it * NT < SP) {
+#pragma unroll
+        for (int v = 0; v < 5; ++v) q[it][v] = w[pb + v * (size_t)g.cells + ho[it]];
+      }
+  };
+  auto store = [&](const CT (&q)[2][5], int slot) {
+    CT* P = sP + slot * NV * SP;
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+      const int t = tid + it * NT;
+      if (t < SP) {
+        // the operations of prim_at()
+        const CT rho = q[it][0];
+        const CT ir = CT(1) / rho;
+        const CT u0 = q[it][1] * ir, u1 = q[it][2] * ir, u2 = q[it][3] * ir;
+        const CT p = (gam - CT(1)) * (q[it][4] - CT(0.5) * rho * (u0 * u0 + u1 * u1 + u2 * u2));
+        const CT cs = sqrt(gam * p * ir);
+        P[0 * SP + t] = rho;
+        P[1 * SP + t] = u0;
+        P[2 * SP + t] = u1;
+        P[3 * SP + t] = u2;
+        P[4 * SP + t] = p;
+        P[5 * SP + t] = fa * cs;
+        P[6 * SP + t] = fb * cs;
+      }
+    }
+  };
+  auto slot = [&](int k) { return (k - kz0 + 1) % 3; };
+  {
+    CT q0[2][5], q1[2][5], q2[2][5];
+    load(q0, kz0 - 1);
+    load(q1, kz0);
+    load(q2, kz0 + 1);
+    store(q0, slot(kz0 - 1));
+    store(q1, slot(kz0));
+    store(q2, slot(kz0 + 1));
+  }
+  __syncthreads();
+  const int ic = (ty + 1) * SX + (tx + 1);
   CT vmax = CT(0);
   double vsum = 0.0;
-  for (long long i = (long long)blockIdx.x * RB + threadIdx.x; i < g.cells; i += (long long)gridDim.x * RB) {
-    const int x = (int)(i % g.nx);
-    const int y = (int)((i / g.nx) % g.ny);
-    const int z = (int)(i / g.plane);
-    CT M[5][5];
-    growth_matrix<CT>(g, c, w, b, x, y, z, M);
-    const CT s1 = g.nz == 1 ? sigma1_of<CT, 4>(M) : sigma1_of<CT, 5>(M);
-    const size_t o = (size_t)b * g.cells + i;
-    if (sigd) {
-      // FP64 contexts: sigma_1 and the rule's viscosity kept in FP64
-      const double sd = (double)s1;
-      sigd[o] = sd;
-      if (rule.nud) {
-        const double v = sd > rule.taud ? rule.lamd * sd : 0.0;
-        rule.nud[o] = v;
-        if (!(v <= rule.limitd)) atomicOr(rule.err, ERRBIT_UNSTABLE);
+  for (int k = kz0; k < kz1; ++k) {
+    const bool more = k + 1 < kz1;
+    CT qf[2][5];
+    if (more) load(qf, k + 2);
+    if (valid) {
+      const CT* P0 = sP + slot(k) * NV * SP;
+      const CT* Pm = sP + slot(k - 1) * NV * SP;
+      const CT* Pp = sP + slot(k + 1) * NV * SP;
+      // neighbour values of quantity v in direction j: (minus, plus)
+      auto nb = [&](int v, int j, CT& m, CT& pl) {
+        if (j == 0) {
+          m = P0[v * SP + ic - 1];
+          pl = P0[v * SP + ic + 1];
+        } else if (j == 1) {
+          m = P0[v * SP + ic - SX];
+          pl = P0[v * SP + ic + SX];
+        } else {
+          m = Pm[v * SP + ic];
+          pl = Pp[v * SP + ic];
+        }
+      };
+      CT drho[3], du[3][3], dp[3], da[3], db[3];
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const CT h = c.hidx[j];
+        CT m, pl;
+        nb(0, j, m, pl);
+        drho[j] = (pl - m) * h;
+        nb(4, j, m, pl);
+        dp[j] = (pl - m) * h;
+        nb(5, j, m, pl);
+        da[j] = (pl - m) * h;
+        nb(6, j, m, pl);
+        db[j] = (pl - m) * h;
+#pragma unroll
+        for (int kk = 0; kk < 3; ++kk) {
+          nb(1 + kk, j, m, pl);
+          du[kk][j] = (pl - m) * h;
+        }
       }
-      vmax = fmax(vmax, s1);
-      vsum += sd;
-    } else {
-      const float sf = (float)s1;
-      sig[o] = sf;
-      if (rule.nu) {
-        const float v = sf > rule.tau ? rule.lam * sf : 0.0f;
-        rule.nu[o] = v;
-        if (!(v <= rule.limit)) atomicOr(rule.err, ERRBIT_UNSTABLE);
+      const CT rho0 = P0[0 * SP + ic], p0 = P0[4 * SP + ic], a0 = P0[5 * SP + ic], b0 = P0[6 * SP + ic];
+      CT M[5][5];
+      const CT div = du[0][0] + du[1][1] + du[2][2];
+#pragma unroll
+      for (int i2 = 0; i2 < 5; ++i2)
+#pragma unroll
+        for (int j2 = 0; j2 < 5; ++j2) M[i2][j2] = i2 == j2 ? CT(0.5) * div : CT(0);
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        M[0][1 + j] = M[1 + j][0] = CT(0.5) * db[j];
+        M[1 + j][4] = M[4][1 + j] = CT(0.5) * da[j];
       }
-      vmax = fmax(vmax, CT(sf));
-      vsum += (double)sf;
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        M[0][1 + j] -= b0 / rho0 * drho[j];
+#pragma unroll
+        for (int kk = 0; kk < 3; ++kk) M[1 + kk][1 + j] -= du[kk][j];
+        M[4][1 + j] -= CT(2) / gm1 * da[j];
+        M[1 + j][4] -= a0 / (CT(2) * p0) * dp[j];
+      }
+      M[0][4] -= sqrt(gm1) / CT(2) * div;
+      M[4][4] -= gm1 / CT(2) * div;
+      const CT s1 = g.nz == 1 ? sigma1_of<CT, 4>(M) : sigma1_of<CT, 5>(M);
+      const size_t o = (size_t)b * g.cells + (size_t)k * g.plane + cp;
+      if (sigd) {
+        // FP64 contexts: sigma_1 and the rule's viscosity kept in FP64
+        const double sd = (double)s1;
+        sigd[o] = sd;
+        if (rule.nud) {
+          const double v = sd > rule.taud ? rule.lamd * sd : 0.0;
+          rule.nud[o] = v;
+          if (!(v <= rule.limitd)) atomicOr(rule.err, ERRBIT_UNSTABLE);
+        }
+        vmax = fmax(vmax, s1);
+        vsum += sd;
+      } else {
+        const float sf = (float)s1;
+        sig[o] = sf;
+        if (rule.nu) {
+          const float v = sf > rule.tau ? rule.lam * sf : 0.0f;
+          rule.nu[o] = v;
+          if (!(v <= rule.limit)) atomicOr(rule.err, ERRBIT_UNSTABLE);
+        }
+        vmax = fmax(vmax, CT(sf));
+        vsum += (double)sf;
+      }
     }
+    __syncthreads();   // plane k-1 no longer read
+    if (more) store(qf, slot(k - 1));
+    __syncthreads();   // plane k+2 visible
   }
   if (!stats) return;
   const double bmax = block_reduce(vmax, sh, MaxOp());
   const double bsum = block_reduce(vsum, sh, AddOp());
-  double* pmax = partial + (size_t)b * 2 * gridDim.x;
-  double* psum = pmax + gridDim.x;
-  if (threadIdx.x == 0) {
-    pmax[blockIdx.x] = bmax;
-    psum[blockIdx.x] = bsum;
+  const int G = gridDim.x;
+  if (tid < g.batch) {
+    partial[(size_t)(2 * tid) * G + blockIdx.x] = tid == b ? bmax : 0.0;
+    partial[(size_t)(2 * tid + 1) * G + blockIdx.x] = tid == b ? bsum : 0.0;
+  }
+  __syncthreads();
+  if (tid == 0) {
     __threadfence();
-    last = atomicAdd(&ticket[b], 1u) == gridDim.x - 1;
+    last = atomicAdd(&ticket[0], 1u) == (unsigned)G - 1;
   }
   __syncthreads();
   if (!last) return;
-  // the last block of the box: fixed-order reduction of the block partials
+  // the last CTA: per box, a fixed-order reduction of every CTA's partials
   __threadfence();
-  double m = 0.0, t = 0.0;
-  for (int j = threadIdx.x; j < (int)gridDim.x; j += RB) {
-    m = fmax(m, pmax[j]);
-    t += psum[j];
+  for (int bb = 0; bb < g.batch; ++bb) {
+    double m = 0.0, t = 0.0;
+    for (int j = tid; j < G; j += NT) {
+      m = fmax(m, partial[(size_t)(2 * bb) * G + j]);
+      t += partial[(size_t)(2 * bb + 1) * G + j];
+    }
+    m = block_reduce(m, sh, MaxOp());
+    t = block_reduce(t, sh, AddOp());
+    if (tid == 0) {
+      stats[2 * bb] = m;
+      stats[2 * bb + 1] = t / (double)g.cells;
+    }
   }
-  m = block_reduce(m, sh, MaxOp());
-  t = block_reduce(t, sh, AddOp());
-  if (threadIdx.x == 0) {
-    stats[2 * b] = m;
-    stats[2 * b + 1] = t / (double)g.cells;
-    ticket[b] = 0u;
-  }
+  if (tid == 0) ticket[0] = 0u;
 }
 
 // v_hat = S^-T V^-T lam of one cell (closed form of w_hat = T^T v_hat, "Symmetrization")
@@ -848,6 +998,9 @@ size_t diag_scratch_doubles(const GridDesc& g, int nphi) {
   // two-launch objective: partials, (N/D, sc) per box and 5 doubles per plane face
   const size_t ob = (size_t)2 * RG * g.batch + 2 * (size_t)g.batch + (size_t)g.ny * g.nz * g.batch * 5;
   if (ob > a) a = ob;
+  // sigma_1 statistics: (max, sum) per box for every CTA of the plane-marching launch
+  const size_t sg = 2 * sigma1_march_ctas_bound(g) * (size_t)g.batch;
+  if (sg > a) a = sg;
   size_t b = (size_t)RG * (nphi > 0 ? nphi : 1);
   return (a > b ? a : b) + 64;
 }
@@ -912,10 +1065,16 @@ template <class CT>
 cudaError_t launch_sigma1(const GridDesc& g, const Coef<CT>& c, const CT* w, float* sigma1,
                           double* stats, double* scratch, unsigned* ticket, cudaStream_t st,
                           const NuRule* rule, double* sigma1d) {
-  dim3 grid(RGS, g.batch);
   const NuRule r = rule ? *rule : NuRule{0.f, 0.f, 0.f, nullptr, nullptr, 0.0, 0.0, 0.0, nullptr};
-  cudaError_t e =
-      launch_pdl(k_sigma1<CT>, grid, dim3(RB), 0, st, g, c, w, sigma1, scratch, stats, ticket, r, sigma1d);
+  const size_t smem = sizeof(CT) * 3 * sgk::NV * sgk::SP;
+  static MarchShape<TX, sgk::TY> shape;
+  int ctas = 0;
+  cudaError_t e = shape.get(k_sigma1<CT>, smem, g, nullptr, ctas);
+  if (e != cudaSuccess) return e;
+  if ((size_t)ctas > sigma1_march_ctas_bound(g)) return cudaErrorInvalidConfiguration;
+  if (g.batch > sgk::NT) return cudaErrorInvalidConfiguration;
+  e = launch_pdl(k_sigma1<CT>, dim3(ctas), dim3(sgk::NT), smem, st, g, c, w, sigma1, scratch, stats, ticket, r,
+                 sigma1d);
   count_launch();
   return e;
 }

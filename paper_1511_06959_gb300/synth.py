@@ -174,6 +174,12 @@ def perturbed_uniform(nx, ny, nz, seed, amp=0.05, mach=0.5, gamma=1.4):
     return _conservative(rho, u, p, gamma)
 
 
+def kolmogorov_amplitude(U0, mu, Ly, k=1):
+    """Forcing amplitude that sustains the laminar profile u_1 = U0 sin(2 pi k y / L_y)
+    against viscosity (mu (2 pi k / L_y)^2 U0; density 1)."""
+    return U0 * mu * (2.0 * math.pi * k / Ly) ** 2
+
+
 def kolmogorov_forcing(nx, ny, nz, amp, k=1):
     """A time-constant body force on the x-momentum equation, s_1 = amp sin(2 pi k y / L_y)
     (the other components zero): a Kolmogorov shear forcing that keeps a periodic box

@@ -98,3 +98,50 @@ def test_forcing_bumps(nz):
     # distinct centres: no two bumps coincide
     peaks = {np.unravel_index(np.argmax(phi[m]), phi[m].shape) for m in range(64)}
     assert len(peaks) == 64
+
+
+def test_kolmogorov_forcing_and_forced_start():
+    """The Kolmogorov force acts on x-momentum only, with zero mean over y; the forced
+    start is the stream plus the laminar shear profile (rho = 1, p = 1/gamma) and seeded
+    noise of the stated relative size."""
+    nx, ny, nz = 8, 32, 4
+    s = synth.kolmogorov_forcing(nx, ny, nz, amp=0.7)
+    assert s.shape == (5, nz, ny, nx)
+    assert np.all(s[[0, 2, 3, 4]] == 0.0)
+    assert abs(s[1].mean()) < 1e-15 and abs(np.abs(s[1]).max() - 0.7) < 0.01
+    g = 1.4
+    w = synth.forced_start(nx, ny, nz, mach=0.3, shear=0.2, noise=0.0, gamma=g)
+    rho, u, p = _primitives(w, g)
+    np.testing.assert_allclose(rho, 1.0)
+    np.testing.assert_allclose(p, 1.0 / g, rtol=1e-12)
+    y = (np.arange(ny) + 0.5) / nx
+    prof = 0.3 + 0.2 * np.sin(2.0 * math.pi * y / (ny / nx))
+    np.testing.assert_allclose(u[0][0, :, 0], prof, rtol=1e-12)
+    wn = synth.forced_start(nx, ny, nz, mach=0.3, shear=0.2, noise=0.02, seed=3, gamma=g)
+    _, un, _ = _primitives(wn, g)
+    assert abs(np.std(un[1]) / (0.02 * 0.3) - 1.0) < 0.1
+    assert np.array_equal(wn, synth.forced_start(nx, ny, nz, mach=0.3, shear=0.2, noise=0.02, seed=3, gamma=g))
+
+
+def test_kolmogorov_amplitude_balances_the_discrete_viscous_term():
+    """On the laminar profile u_1 = U0 sin(k y) (k = 2 pi / L_y) the forcing of amplitude
+    mu k^2 U0 cancels the oracle's viscous x-momentum residual up to the three-point
+    Laplacian's error: R_1 + s_1 = mu U0 (k^2 - (4 / dy^2) sin^2(k dy / 2)) sin(k y),
+    about (k dy)^2 / 12 of the amplitude (mass and the other momenta stay at rest)."""
+    from oracle import ns_oracle as O
+    from tests.test_oracle_primal import params_for
+    nx, ny, nz = 4, 32, 2
+    U0, mu = 0.2, 0.01
+    w = synth.forced_start(nx, ny, nz, mach=0.3, shear=U0, noise=0.0)
+    dx = synth.box_shape(nx, ny, nz)
+    Ly = ny * dx[1]
+    amp = synth.kolmogorov_amplitude(U0, mu, Ly)
+    s = synth.kolmogorov_forcing(nx, ny, nz, amp)
+    P = params_for(w, mu=mu, dt=1e-3)
+    R = O.residual(w, P, s)
+    k, dy = 2.0 * math.pi / Ly, dx[1]
+    y = (np.arange(ny) + 0.5) * dy
+    exact = mu * U0 * (k * k - 4.0 / dy ** 2 * math.sin(0.5 * k * dy) ** 2) * np.sin(k * y)
+    np.testing.assert_allclose(R[1][0, :, 0], exact, rtol=1e-6, atol=1e-12 * amp)
+    assert abs(np.abs(R[1]).max() / amp - (k * dy) ** 2 / 12.0) < 0.01 * (k * dy) ** 2 / 12.0
+    assert np.abs(R[0]).max() < 1e-12 and np.abs(R[2:4]).max() < 1e-12
