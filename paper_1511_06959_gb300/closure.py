@@ -97,21 +97,21 @@ class Samples:
     target: torch.Tensor    # [n] float32
 
 
-def trajectory(S: api.Solver, w0: torch.Tensor, nsteps: int):
+def trajectory(S: api.Solver, w0: torch.Tensor, nsteps: int, s: torch.Tensor | None = None):
     ws = [w0]
     for _ in range(nsteps):
         nxt = torch.empty_like(w0)
-        S.primal_step(ws[-1], nxt)
+        S.primal_step(ws[-1], nxt, s)
         ws.append(nxt)
     return ws
 
 
 def generate_samples(S: api.Solver, w0: torch.Tensor, nsteps: int, every: int = 4,
-                     t_max: float = 10.0) -> Samples:
-    """Run the unstabilised adjoint of the pressure loss over nsteps (all states kept)
-    and, every `every` steps, pair the features of every cell of w^n with the label of
-    (w^n, lam^n)."""
-    ws = trajectory(S, w0, nsteps)
+                     t_max: float = 10.0, s: torch.Tensor | None = None) -> Samples:
+    """Run the unstabilised adjoint of the pressure loss over nsteps (all states kept,
+    the primal driven by the source s if given) and, every `every` steps, pair the
+    features of every cell of w^n with the label of (w^n, lam^n)."""
+    ws = trajectory(S, w0, nsteps, s)
     cells = S.cells * S.batch
     lam = torch.zeros_like(w0)
     J = torch.zeros(S.batch, dtype=torch.float64, device=w0.device)
