@@ -66,6 +66,8 @@ def parse():
                     help="time integrator (the workload's is RK4; ssprk3 is the paper's own)")
     ap.add_argument("--host-snapshots", action="store_true",
                     help="keep a stride schedule's snapshots in page-locked host memory")
+    ap.add_argument("--disk-snapshots", default=None, metavar="PATH",
+                    help="keep a stride schedule's snapshots in the file PATH (removed after each sweep)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -250,15 +252,19 @@ def run_ours(args, wl):
     if args.closure:
         from paper_1511_06959_gb300 import closure
         net = closure.Network(S, closure.init_params(3, out_bias=0.5))
-    run_sched, host = sched, None
-    if args.host_snapshots:
+    run_sched, host, disk = sched, None, None
+    if args.disk_snapshots:
+        if wl.schedule != "stride":
+            raise SystemExit("--disk-snapshots needs a workload with a stride schedule")
+        run_sched, disk = api.NS_CKPT_STRIDE_DISK, args.disk_snapshots
+    elif args.host_snapshots:
         if wl.schedule != "stride":
             raise SystemExit("--host-snapshots needs a workload with a stride schedule")
         run_sched = api.NS_CKPT_STRIDE_HOST
         probe = S.run_opts(wl.nsteps, run_sched, param)
         host = torch.empty(S.host_bytes(probe), dtype=torch.uint8, pin_memory=True)
     opts = S.run_opts(wl.nsteps, run_sched, param, 0.5 if net is not None else wl.lam_coef, 0.0, True, True,
-                      net.blob if net is not None else None, host_arena=host)
+                      net.blob if net is not None else None, host_arena=host, disk_path=disk)
     arena = torch.empty(S.arena_bytes(opts), dtype=torch.uint8, device=dev)
     J = torch.empty(wl.batch, dtype=torch.float64, device=dev)
     lam0 = torch.empty_like(w0)
@@ -356,7 +362,8 @@ def run_ours(args, wl):
                        "scheme": args.scheme, "flux": args.flux, "nu_split": list(split),
                        "viscosity": "learned closure (MLP, kappa 0.5)" if args.closure else "sigma_1 rule",
                        "nsteps": wl.nsteps,
-                       "schedule": wl.schedule + (" (snapshots in host memory)" if host is not None else ""),
+                       "schedule": wl.schedule + (" (snapshots in host memory)" if host is not None else
+                                                  " (snapshots in a file)" if disk is not None else ""),
                        "param": param,
                        "lambda_tilde": wl.lam_tilde, "precision": args.precision, "dt": dt,
                        "l2": "flushed (256 MB write) between timed steps; arena "

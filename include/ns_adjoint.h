@@ -23,7 +23,9 @@
  *    HOST memory appears only where a call says so: the plan (ns_plan), the energy fit
  *    and the choice of lambda (ns_energy_efolds, ns_lambda_select, the candidate and
  *    report arrays of ns_estimate_lambda), the snapshot arena of NS_CKPT_STRIDE_HOST
- *    (ns_run_opts.host_arena), the parameter structs, and values a call returns.
+ *    (ns_run_opts.host_arena), the parameter structs, and values a call returns.  The
+ *    snapshot file of NS_CKPT_STRIDE_DISK (ns_run_opts.disk_path) is the one file the
+ *    library writes.
  *  - Work is enqueued on the stream given to ns_create (or ns_set_stream) and is
  *    asynchronous unless a call says it returns a host value.
  *  - Every call returns NS_OK (0) or a negative NS_ERR_* code.  NS_ERR_ARG: null
@@ -31,7 +33,8 @@
  *    NS_ERR_BUDGET: a caller-provided buffer (arena, host arena, work buffer, plan
  *    array) is smaller than the call needs; these size checks run before the call
  *    enqueues any work.
- *    NS_ERR_CUDA: a launch or allocation failed.  Faults found on the device
+ *    NS_ERR_CUDA: a launch or allocation failed.  NS_ERR_IO: a snapshot file access
+ *    of NS_CKPT_STRIDE_DISK failed.  Faults found on the device
  *    (non-finite values, an unstable adjoint viscosity) set a sticky error word
  *    that ns_last_error() reads back.
  *  - A context owns only its workspace (stage buffers and reduction scratch,
@@ -56,6 +59,8 @@ extern "C" {
 #define NS_ERR_CORRUPT (-6) /* a verified checkpoint snapshot changed between store and load */
 #define NS_ERR_BOUNDS (-7)  /* bounds-checking builds only (NS_DEBUG_BOUNDS): a stencil kernel
                                met a field index outside its field and skipped the access */
+#define NS_ERR_IO (-8)      /* NS_CKPT_STRIDE_DISK: the snapshot file could not be created,
+                               written or read (the sweep stops; errno is left as set) */
 
 /* time integration (ns_params.scheme) */
 #define NS_RK4 0    /* classical four-stage fourth-order Runge-Kutta, constant dt */
@@ -227,11 +232,22 @@ int ns_max_wave_speed(ns_ctx* ctx, const double* w, double* out);
  *                   in device memory.  The copies run on the context's stream, so a
  *                   sweep gives the same bits as NS_CKPT_STRIDE.  On a Grace-hosted GPU
  *                   they cross NVLink-C2C.
+ *   NS_CKPT_STRIDE_DISK  the plan of NS_CKPT_STRIDE_HOST with the snapshots in a file
+ *                   (ns_run_opts.disk_path) instead of host memory: each snapshot is
+ *                   written once in the forward pass and read once when its segment is
+ *                   replayed, through a page-locked staging buffer of one state that the
+ *                   library allocates.  The stream is drained around each file access, so
+ *                   the sweep waits for the file system; it gives the same bits as
+ *                   NS_CKPT_STRIDE.  The file is created (truncated) by the forward pass,
+ *                   is written only by the library while the sweep holds it, and is
+ *                   removed when the sweep is released.  Use it for horizons whose
+ *                   snapshots fit neither device nor host memory.
  * ---------------------------------------------------------------------------- */
 #define NS_CKPT_ALL 0
 #define NS_CKPT_STRIDE 1
 #define NS_CKPT_REVOLVE 2
 #define NS_CKPT_STRIDE_HOST 3
+#define NS_CKPT_STRIDE_DISK 4
 
 #define NS_OP_ADVANCE 1 /* advance the current state from step a to step b */
 #define NS_OP_STORE 2   /* keep the current state (step a) in slot b */
@@ -240,10 +256,11 @@ int ns_max_wave_speed(ns_ctx* ctx, const double* w, double* out);
                            objective source of step a if a >= 1 */
 #define NS_OP_FREE 5    /* release slot b (held step a) */
 #define NS_OP_SOURCE 6  /* add the objective source of step a (current state w^a) */
-#define NS_OP_STORE_HOST 7 /* copy the current state (step a) to host slot b */
-#define NS_OP_LOAD_HOST 8  /* copy the state of step a from host slot b into a free device
-                              buffer and make it current */
-#define NS_OP_FREE_HOST 9  /* release host slot b (held step a) */
+#define NS_OP_STORE_HOST 7 /* copy the current state (step a) to host slot b (the file's
+                              slot b for NS_CKPT_STRIDE_DISK) */
+#define NS_OP_LOAD_HOST 8  /* copy the state of step a from host (file) slot b into a free
+                              device buffer and make it current */
+#define NS_OP_FREE_HOST 9  /* release host (file) slot b (held step a) */
 
 typedef struct {
   int op, a, b;
@@ -261,8 +278,8 @@ int ns_plan(int nsteps, int schedule, int param, ns_action* out, int max_actions
 typedef struct {
   int nsteps;        /* primal steps N; Jbar = (1/N) sum_{n=1..N} J(w^n) */
   int schedule;      /* NS_CKPT_* */
-  int param;         /* stride (NS_CKPT_STRIDE, NS_CKPT_STRIDE_HOST) or state slots
-                        (NS_CKPT_REVOLVE) */
+  int param;         /* stride (NS_CKPT_STRIDE, NS_CKPT_STRIDE_HOST, NS_CKPT_STRIDE_DISK) or
+                        state slots (NS_CKPT_REVOLVE) */
   double lambda;     /* added adjoint viscosity nu = lambda sigma_1 [sigma_1 > tau]; 0 = none */
   double tau;
   int record_energy; /* write E_vhat(w^n, lam^n), n = 0..N, to energy[n][batch] */
@@ -285,6 +302,8 @@ typedef struct {
                         moved word changes it except with probability 2^-64, and its
                         parallel sum is exact in any order.  Costs one read of the state
                         per store and per load. */
+  const char* disk_path; /* NS_CKPT_STRIDE_DISK: path of the snapshot file (NS_ERR_ARG if
+                        NULL); else ignored.  The string is copied by the forward pass. */
 } ns_run_opts;
 
 /* Device bytes the caller must provide as the arena of ns_adjoint_run (state slots,

@@ -22,6 +22,7 @@ NS_ERR_UNSTABLE = -4
 NS_ERR_CUDA = -5
 NS_ERR_CORRUPT = -6
 NS_ERR_BOUNDS = -7
+NS_ERR_IO = -8
 NS_FP64 = 0
 NS_MIXED = 1
 NS_RK4 = 0
@@ -58,6 +59,7 @@ NS_CKPT_ALL = 0
 NS_CKPT_STRIDE = 1
 NS_CKPT_REVOLVE = 2
 NS_CKPT_STRIDE_HOST = 3
+NS_CKPT_STRIDE_DISK = 4
 NS_OP_ADVANCE, NS_OP_STORE, NS_OP_LOAD, NS_OP_ADJOINT, NS_OP_FREE, NS_OP_SOURCE = 1, 2, 3, 4, 5, 6
 NS_OP_STORE_HOST, NS_OP_LOAD_HOST, NS_OP_FREE_HOST = 7, 8, 9
 
@@ -82,7 +84,7 @@ class NsRunOpts(ctypes.Structure):
         ("nsteps", ctypes.c_int), ("schedule", ctypes.c_int), ("param", ctypes.c_int),
         ("lambda_", ctypes.c_double), ("tau", ctypes.c_double), ("record_energy", ctypes.c_int),
         ("record_sigma", ctypes.c_int), ("mlp", ctypes.c_void_p), ("host_arena", ctypes.c_void_p),
-        ("host_bytes", ctypes.c_size_t), ("verify", ctypes.c_int),
+        ("host_bytes", ctypes.c_size_t), ("verify", ctypes.c_int), ("disk_path", ctypes.c_char_p),
     ]
 
 
@@ -425,17 +427,19 @@ class Solver:
 
     # --- checkpointed sweep ----------------------------------------------------------
     def run_opts(self, nsteps, schedule=NS_CKPT_ALL, param=0, lam_coef=0.0, tau=0.0,
-                 record_energy=False, record_sigma=False, mlp=None, host_arena=None, verify=False):
+                 record_energy=False, record_sigma=False, mlp=None, host_arena=None, verify=False,
+                 disk_path=None):
         """Sweep options; mlp: a network blob (uint8 CUDA tensor) selecting the learned
         closure, with lam_coef then its global factor kappa; host_arena: a uint8 CPU
         tensor (pinned for asynchronous copies) holding the snapshots of an
         NS_CKPT_STRIDE_HOST sweep (the options keep a reference to it); verify: checksum
-        every snapshot when stored and check it when loaded (NS_ERR_CORRUPT)."""
+        every snapshot when stored and check it when loaded (NS_ERR_CORRUPT); disk_path: the
+        snapshot file of an NS_CKPT_STRIDE_DISK sweep."""
         o = NsRunOpts(nsteps, schedule, param, lam_coef, tau, int(record_energy), int(record_sigma),
                       None if mlp is None else ctypes.c_void_p(mlp.data_ptr()),
                       _host_ptr(host_arena),
                       0 if host_arena is None else host_arena.numel() * host_arena.element_size(),
-                      int(verify))
+                      int(verify), None if disk_path is None else os.fsencode(disk_path))
         o._host_arena = host_arena
         return o
 

@@ -382,6 +382,7 @@ const char* ns_error_string(int code) {
     case NS_ERR_CUDA: return "CUDA error";
     case NS_ERR_CORRUPT: return "a checkpoint snapshot changed between store and load";
     case NS_ERR_BOUNDS: return "a field index outside its field (bounds-checking build)";
+    case NS_ERR_IO: return "the checkpoint snapshot file could not be created, written or read";
     default: return "unknown error";
   }
 }

@@ -3,11 +3,15 @@
 // snapshots and segment recomputation; here also binomial checkpointing) and the
 // executor that runs a plan on the context's stream with a pool of state buffers.
 #include <cuda_runtime.h>
+#include <errno.h>
+#include <fcntl.h>
 #include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
+#include <unistd.h>
 
 #include <algorithm>
 #include <map>
+#include <string>
 #include <vector>
 
 #include "../../include/ns_adjoint.h"
@@ -262,6 +266,7 @@ int make_plan(int N, int schedule, int param, Planner& P) {
       P.plan_revolve(N, param);
       break;
     case NS_CKPT_STRIDE_HOST:
+    case NS_CKPT_STRIDE_DISK:
       if (param < 1) return NS_ERR_ARG;
       P.plan_stride_host(N, param);
       break;
@@ -271,6 +276,21 @@ int make_plan(int N, int schedule, int param, Planner& P) {
 }
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// n bytes between buf and the file at offset off, in as many calls as the kernel needs;
+// false on an error or an early end of file
+bool file_io(int fd, void* buf, size_t n, long long off, bool write) {
+  char* p = (char*)buf;
+  while (n > 0) {
+    const ssize_t k = write ? pwrite(fd, p, n, (off_t)off) : pread(fd, p, n, (off_t)off);
+    if (k < 0 && errno == EINTR) continue;
+    if (k <= 0) return false;
+    p += k;
+    off += k;
+    n -= (size_t)k;
+  }
+  return true;
+}
 
 // Arena regions.  mir: two stage-type fields holding float mirrors of consecutive
 // states of an ADVANCE run (mixed precision).  lmir: two float mirrors of the adjoint,
@@ -300,7 +320,9 @@ Layout layout_for(const ns_ctx* c, int slots_used, bool closure, int schedule, i
   L.stage = align256(ns_i_stage_bytes(c));
   L.mir = 2 * L.stage;
   L.lmir = c->p.precision == NS_MIXED ? 2 * L.stage : 0;
-  L.nkeep = (schedule == NS_CKPT_STRIDE || schedule == NS_CKPT_STRIDE_HOST) ? param : 0;
+  L.nkeep = (schedule == NS_CKPT_STRIDE || schedule == NS_CKPT_STRIDE_HOST || schedule == NS_CKPT_STRIDE_DISK)
+                ? param
+                : 0;
   L.keep = (size_t)L.nkeep * 4 * L.stage;
   // snapshot checksums: one per device slot and per host slot, and one to verify into
   L.sums = verify ? align256(sizeof(unsigned long long) * (size_t)(slots_used + host_slots + 1)) : 0;
@@ -378,6 +400,17 @@ struct ns_sweep_state {
   char* lamf_nxt = nullptr;
   bool lamf_valid = false;
   bool kept_valid(int n) const { return L.nkeep > 0 && seg >= 0 && (n / L.nkeep) * L.nkeep == seg; }
+  // NS_CKPT_STRIDE_DISK: the snapshot file and the page-locked staging buffer of one state
+  int fd = -1;
+  std::string path;
+  void* staging = nullptr;
+  ~ns_sweep_state() {
+    if (fd >= 0) {
+      close(fd);
+      unlink(path.c_str());
+    }
+    if (staging) cudaFreeHost(staging);
+  }
 };
 
 void ns_sweep_release(ns_ctx* c) {
@@ -486,10 +519,18 @@ int run_actions(ns_ctx* c, ns_sweep_state& S, int stop_op, double*& lam_cur, dou
       case NS_OP_STORE_HOST: {
         // stream-ordered: later kernels that reuse the buffer run after the copy
         if (S.cur < 0 || A.b < 0 || A.b >= S.P.maxhost) return NS_ERR_ARG;
-        char* hp = (char*)S.o.host_arena + (size_t)A.b * S.L.state;
         if (S.sums && (r = checksum(c, S.buf[S.cur], c->field, S.sums + S.P.maxlive + A.b))) return r;
-        if (cudaMemcpyAsync(hp, S.buf[S.cur], c->field * sizeof(double), cudaMemcpyDeviceToHost, c->st) !=
-            cudaSuccess)
+        const size_t nb = c->field * sizeof(double);
+        if (S.fd >= 0) {
+          // file slot A.b: through the staging buffer, the stream drained before the write
+          if (cudaMemcpyAsync(S.staging, S.buf[S.cur], nb, cudaMemcpyDeviceToHost, c->st) != cudaSuccess ||
+              cudaStreamSynchronize(c->st) != cudaSuccess)
+            return NS_ERR_CUDA;
+          if (!file_io(S.fd, S.staging, nb, (long long)A.b * (long long)S.L.state, true)) return NS_ERR_IO;
+          break;
+        }
+        char* hp = (char*)S.o.host_arena + (size_t)A.b * S.L.state;
+        if (cudaMemcpyAsync(hp, S.buf[S.cur], nb, cudaMemcpyDeviceToHost, c->st) != cudaSuccess)
           return NS_ERR_CUDA;
         break;
       }
@@ -497,10 +538,18 @@ int run_actions(ns_ctx* c, ns_sweep_state& S, int stop_op, double*& lam_cur, dou
         if (A.b < 0 || A.b >= S.P.maxhost) return NS_ERR_ARG;
         const int out = pick_free();
         if (out < 0) return NS_ERR_BUDGET;
-        const char* hp = (const char*)S.o.host_arena + (size_t)A.b * S.L.state;
-        if (cudaMemcpyAsync(S.buf[out], hp, c->field * sizeof(double), cudaMemcpyHostToDevice, c->st) !=
-            cudaSuccess)
-          return NS_ERR_CUDA;
+        const size_t nb = c->field * sizeof(double);
+        if (S.fd >= 0) {
+          // the staging buffer is free: every earlier copy through it has completed
+          if (!file_io(S.fd, S.staging, nb, (long long)A.b * (long long)S.L.state, false)) return NS_ERR_IO;
+          if (cudaMemcpyAsync(S.buf[out], S.staging, nb, cudaMemcpyHostToDevice, c->st) != cudaSuccess ||
+              cudaStreamSynchronize(c->st) != cudaSuccess)
+            return NS_ERR_CUDA;
+        } else {
+          const char* hp = (const char*)S.o.host_arena + (size_t)A.b * S.L.state;
+          if (cudaMemcpyAsync(S.buf[out], hp, nb, cudaMemcpyHostToDevice, c->st) != cudaSuccess)
+            return NS_ERR_CUDA;
+        }
         if (S.sums && (r = checksum_verify(c, S.buf[out], c->field, S.sums + S.P.maxlive + S.P.maxhost,
                                            S.sums + S.P.maxlive + A.b)))
           return r;
@@ -603,6 +652,23 @@ static int forward_run_impl(ns_ctx* c, const double* w0, const double* s, const 
       (!o->host_arena || o->host_bytes < (size_t)S->P.maxhost * S->L.state)) {
     delete S;
     return NS_ERR_BUDGET;
+  }
+  if (o->schedule == NS_CKPT_STRIDE_DISK) {
+    if (!o->disk_path || !o->disk_path[0]) {
+      delete S;
+      return NS_ERR_ARG;
+    }
+    S->path = o->disk_path;
+    S->fd = open(S->path.c_str(), O_RDWR | O_CREAT | O_TRUNC, 0600);
+    if (S->fd < 0) {
+      delete S;
+      return NS_ERR_IO;
+    }
+    if (cudaMallocHost(&S->staging, c->field * sizeof(double)) != cudaSuccess) {
+      S->staging = nullptr;
+      delete S;
+      return NS_ERR_CUDA;
+    }
   }
   S->o = *o;
   S->w0 = w0;

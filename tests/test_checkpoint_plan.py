@@ -141,6 +141,15 @@ def test_revolve_repetition_bound(N, S):
     assert advances <= (r + 1) * N
 
 
+@pytest.mark.parametrize("N,k", [(1, 1), (13, 4), (201, 50)])
+def test_disk_tier_plan_is_the_host_tier_plan(N, k):
+    """NS_CKPT_STRIDE_DISK runs the host tier's plan, its host slots being file slots."""
+    api = _api()
+    assert api.plan(N, api.NS_CKPT_STRIDE_DISK, k) == api.plan(N, api.NS_CKPT_STRIDE_HOST, k)
+    with pytest.raises(api.NsError):
+        api.plan(N, api.NS_CKPT_STRIDE_DISK, 0)
+
+
 def test_plan_rejects_bad_arguments():
     api = _api()
     with pytest.raises(api.NsError):

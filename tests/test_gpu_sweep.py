@@ -198,3 +198,72 @@ def test_verified_snapshots_keep_the_bits_and_a_corrupted_host_snapshot_is_repor
     torch.cuda.synchronize()
     assert S.last_error() == api.NS_ERR_CORRUPT
     assert S.last_error() == 0          # the word is cleared by the read
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_disk_snapshots_give_the_stride_bits(prec, tmp_path):
+    """NS_CKPT_STRIDE_DISK keeps the every-k-th snapshots in a file (written once in the
+    forward pass, read once at replay, through the library's staging buffer): the
+    stabilised sweep with a source, energy and sigma_1 series gives the stride schedule's
+    bits in the host tier's device memory, and the file is gone when the sweep ends."""
+    api = _api()
+    w0 = synth.isentropic_vortex(33, 10, 3, noise=1e-3, seed=5)
+    P = params_for(w0, mu=1e-3, dt=4e-3)
+    s = np.zeros_like(w0)
+    s[1] = 0.05 * synth.forcing_bumps(33, 10, 3, n=4)[0]
+    N, k = 14, 4
+    lam_coef = 0.5 * P.dx[0] ** 2
+    S = make_solver(api, w0, P, prec)
+    ref = _run(api, S, w0, N, 1, k, s, lam_coef=lam_coef, energy=True, sigma=True)
+    path = tmp_path / "snapshots.bin"
+    opts = S.run_opts(N, api.NS_CKPT_STRIDE_DISK, k, lam_coef, 0.0, True, True, disk_path=str(path), verify=True)
+    assert S.host_bytes(opts) == 0
+    assert S.arena_bytes(opts) == S.arena_bytes(S.run_opts(N, api.NS_CKPT_STRIDE_HOST, k, lam_coef, 0.0, True, True,
+                                                           verify=True))
+    arena = torch.empty(S.arena_bytes(opts), dtype=torch.uint8, device="cuda")
+    J = torch.empty(1, dtype=torch.float64, device="cuda")
+    lam0 = torch.empty(w0.shape, dtype=torch.float64, device="cuda")
+    sbar = torch.empty_like(lam0)
+    E = torch.zeros((N + 1, 1), dtype=torch.float64, device="cuda")
+    st = torch.zeros((N, 1, 2), dtype=torch.float64, device="cuda")
+    S.adjoint_run(dev(w0), opts, arena, J, lam0, s=dev(s), sbar=sbar, energy=E, sigma_stats=st)
+    torch.cuda.synchronize()
+    assert S.last_error() == 0
+    for got, want in zip((J, lam0, sbar, E, st), ref):
+        assert torch.equal(got, want)
+    assert not path.exists()
+
+
+def test_disk_snapshot_errors(tmp_path):
+    """A path that cannot be created is NS_ERR_IO before any work is enqueued and a
+    missing path NS_ERR_ARG; a byte flipped in the snapshot file between the forward and
+    the backward half is NS_ERR_CORRUPT when the snapshot is read back (verify on)."""
+    api = _api()
+    w0 = synth.isentropic_vortex(33, 10, 3, noise=1e-3, seed=5)
+    P = params_for(w0, mu=1e-3, dt=4e-3)
+    N, k = 13, 4
+    S = make_solver(api, w0, P, 0)
+    J = torch.empty(1, dtype=torch.float64, device="cuda")
+    lam = torch.empty(w0.shape, dtype=torch.float64, device="cuda")
+    bad = S.run_opts(N, api.NS_CKPT_STRIDE_DISK, k, disk_path=str(tmp_path / "missing" / "s.bin"))
+    arena = torch.empty(S.arena_bytes(bad), dtype=torch.uint8, device="cuda")
+    with pytest.raises(api.NsError) as e:
+        S.adjoint_run(dev(w0), bad, arena, J, lam)
+    assert e.value.code == api.NS_ERR_IO
+    with pytest.raises(api.NsError) as e:
+        S.adjoint_run(dev(w0), S.run_opts(N, api.NS_CKPT_STRIDE_DISK, k), arena, J, lam)
+    assert e.value.code == api.NS_ERR_ARG
+    path = tmp_path / "snapshots.bin"
+    opts = S.run_opts(N, api.NS_CKPT_STRIDE_DISK, k, disk_path=str(path), verify=True)
+    arena = torch.empty(S.arena_bytes(opts), dtype=torch.uint8, device="cuda")
+    S.forward_run(dev(w0), opts, arena, J)
+    torch.cuda.synchronize()
+    data = bytearray(path.read_bytes())
+    # (N - 1) // k snapshots, each at a 256-byte-aligned slot offset
+    assert len(data) == ((N - 1) // k - 1) * (((w0.size * 8 + 255) // 256) * 256) + w0.size * 8
+    data[len(data) // 3 + 1000] ^= 0x10
+    path.write_bytes(bytes(data))
+    S.backward_run(lam)
+    torch.cuda.synchronize()
+    assert S.last_error() == api.NS_ERR_CORRUPT
+    assert not path.exists()
