@@ -524,9 +524,14 @@ const char* ns_error_string(int code);
  * the context's stream.  On a bounded context ns_rhs, ns_rhs_transpose,
  * ns_primal_step, ns_adjoint_step(_f64), ns_growth_sigma1(_f64) (stats NULL),
  * ns_objective (a plane inside the box), ns_add_adjoint_viscosity(_f64),
- * ns_adjoint_energy and ns_max_wave_speed apply; the tangent calls, the checkpointed
- * sweeps, ns_apply_adjoint_viscosity, the closure's features and label and slab groups
- * return NS_ERR_ARG.  NS_BC_PERIODIC restores the periodic box. */
+ * ns_adjoint_energy and ns_max_wave_speed apply, and so do the checkpointed sweeps
+ * (ns_adjoint_run, ns_forward_run / ns_backward_run, ns_estimate_lambda): they run the
+ * step calls above on every action of their plan, the states recomputed inside each
+ * adjoint step, with the same bits as those calls made step by step; a bounded sweep
+ * takes neither sigma_1 statistics (record_sigma) nor the learned closure (mlp), which
+ * are NS_ERR_ARG.  The tangent calls, ns_apply_adjoint_viscosity, the closure's
+ * features and label and slab groups return NS_ERR_ARG.  NS_BC_PERIODIC restores the
+ * periodic box. */
 int ns_set_boundaries(ns_ctx* ctx, int bc, const double* far, const double* wall_e);
 
 /* ------------------------------------------------------------------------------

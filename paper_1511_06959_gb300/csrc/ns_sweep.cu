@@ -306,6 +306,8 @@ struct Layout {
 
 Layout layout_for(const ns_ctx* c, int slots_used, bool closure, int schedule, int param, int host_slots = 0,
                   bool verify = false) {
+  // a bounded box forms its stage states inside its own step calls: nothing is kept
+  if (c->bounded()) schedule = -1;
   Layout L;
   L.nbuf = slots_used + 2;
   L.state = align256(c->field * sizeof(double));
@@ -378,6 +380,7 @@ struct ns_sweep_state {
   float* sig = nullptr;
   float* nu = nullptr;
   bool f64nu = false;                // sigma_1 and nu held in FP64 (the regions hold doubles)
+  bool bounded = false;              // a bounded box: every step through the public step calls
   unsigned long long* sums = nullptr; // snapshot checksums (verify): device slots, host slots, scratch
   double* jtmp = nullptr;
   float* feat = nullptr;
@@ -453,8 +456,8 @@ int run_actions(ns_ctx* c, ns_sweep_state& S, int stop_op, double*& lam_cur, dou
           const int out = pick_free();
           if (out < 0) return NS_ERR_BUDGET;
           const int K = S.L.nkeep;
-          const bool keep = S.in_backward && K > 0;
-          void* in_m = S.mixed ? S.cur_mirror : nullptr;
+          const bool keep = S.in_backward && K > 0 && !S.bounded;
+          void* in_m = S.mixed && !S.bounded ? S.cur_mirror : nullptr;
           void* out_m = nullptr;
           void* keep3[3] = {nullptr, nullptr, nullptr};
           if (keep) {
@@ -481,11 +484,15 @@ int run_actions(ns_ctx* c, ns_sweep_state& S, int stop_op, double*& lam_cur, dou
             keep3[1] = E[2];
             keep3[2] = E[3];
             S.has_stages[e] = 1;
-          } else if (S.mixed) {
+          } else if (S.mixed && !S.bounded) {
             out_m = S.mir[(n + 1) & 1];
             if (in_m == out_m) in_m = nullptr;
           }
-          if ((r = ns_i_primal(c, ptr(S.cur), in_m, S.s, S.buf[out], out_m, keep ? keep3 : nullptr))) return r;
+          if (S.bounded) {
+            if ((r = ns_primal_step(c, ptr(S.cur), S.s, S.buf[out]))) return r;
+          } else if ((r = ns_i_primal(c, ptr(S.cur), in_m, S.s, S.buf[out], out_m, keep ? keep3 : nullptr))) {
+            return r;
+          }
           if (n + 1 > S.touched) {
             if (S.obj_forward && (r = ns_objective(c, S.buf[out], wN, S.Jbar, nullptr))) return r;
             S.touched = n + 1;
@@ -568,6 +575,33 @@ int run_actions(ns_ctx* c, ns_sweep_state& S, int stop_op, double*& lam_cur, dou
         break;
       case NS_OP_ADJOINT: {
         Phase ph("ns adjoint step");
+        if (S.bounded) {
+          // the public step calls, which pad the box with its ghost layer: sigma_1 and the
+          // rule's viscosity, the step, then the objective source of w^n (n >= 1)
+          const double* w = ptr(S.cur);
+          const float* nup = nullptr;
+          const double* nudp = nullptr;
+          if (S.o.lambda > 0.0 && S.f64nu) {
+            if ((r = ns_growth_sigma1_f64(c, w, (double*)S.sig, nullptr)) ||
+                (r = ns_add_adjoint_viscosity_f64(c, (double*)S.sig, S.o.lambda, S.o.tau, (double*)S.nu)))
+              return r;
+            nudp = (const double*)S.nu;
+          } else if (S.o.lambda > 0.0) {
+            if ((r = ns_growth_sigma1(c, w, S.sig, nullptr)) ||
+                (r = ns_add_adjoint_viscosity(c, S.sig, S.o.lambda, S.o.tau, S.nu)))
+              return r;
+            nup = S.nu;
+          }
+          r = nudp ? ns_adjoint_step_f64(c, w, S.s, lam_cur, nudp, lam_nxt, sbar)
+                   : ns_adjoint_step(c, w, S.s, lam_cur, nup, lam_nxt, sbar);
+          if (r) return r;
+          std::swap(lam_cur, lam_nxt);
+          if (A.a >= 1 && (r = ns_objective(c, w, wN, S.jtmp, lam_cur))) return r;
+          S.lamf_valid = false;
+          if (S.o.record_energy && energy && (r = ns_adjoint_energy(c, w, lam_cur, energy + (size_t)A.a * B)))
+            return r;
+          break;
+        }
         const int K = S.L.nkeep;
         const void* mirror = S.mixed ? S.cur_mirror : nullptr;
         const void* kept3[3] = {nullptr, nullptr, nullptr};
@@ -632,7 +666,10 @@ extern "C" {
 
 static int forward_run_impl(ns_ctx* c, const double* w0, const double* s, const ns_run_opts* o, void* arena,
                             size_t arena_bytes, double* Jbar, bool objective_in_forward) {
-  if (!c || !w0 || !o || !arena || !Jbar || c->bounded()) return NS_ERR_ARG;
+  if (!c || !w0 || !o || !arena || !Jbar) return NS_ERR_ARG;
+  // bounded boxes: no learned closure and no sigma_1 statistics (their sigma_1 comes
+  // cropped from the padded box)
+  if (c->bounded() && (o->mlp || o->record_sigma)) return NS_ERR_ARG;
   if (((uintptr_t)arena & 255) != 0) return NS_ERR_ARG;
   if (!(o->lambda >= 0.0)) return NS_ERR_ARG;
   ns_sweep_release(c);
@@ -703,6 +740,7 @@ static int forward_run_impl(ns_ctx* c, const double* w0, const double* s, const 
   S->has_stages.assign(S->L.nkeep, 0);
   S->mixed = c->p.precision == NS_MIXED;
   S->f64nu = !S->mixed && o->mlp == nullptr;
+  S->bounded = c->bounded();
   S->slot_buf.assign(std::max(S->P.maxlive, 1), -1);
   S->owned.assign(S->L.nbuf, 0);
   c->sweep = S;

@@ -162,6 +162,66 @@ def test_bounded_stabilised_adjoint_step_fp64(bc):
     assert rel_l2(host(sb), sref) < 1e-12
 
 
+@pytest.mark.parametrize("bc", list(BCS))
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("sched", [(1, 3), (2, 3), (4, 3)])
+def test_bounded_checkpointed_sweep(bc, prec, sched, tmp_path):
+    """ns_adjoint_run on a bounded box (stride, revolve and disk-tier schedules, the sigma_1
+    rule's viscosity, a source, the energy series) gives the bits of the same calls made
+    step by step with every state kept, and matches the oracle's stabilised adjoint."""
+    api = _api()
+    w0, P = _case((33, 10, 4), 53, bc, mu=0.01, dt=3e-3)
+    s = np.zeros_like(w0)
+    s[1] = 0.05 * synth.forcing_bumps(33, 10, 4, n=4)[0]
+    N = 8
+    lam_coef = 0.4 * P.dx[0] ** 2
+    S = _solver(api, w0, P, prec)
+    sd = dev(s)
+    # step by step: the forward states, then the reverse with sigma_1, nu and the source
+    ws = [dev(w0)]
+    for n in range(N):
+        w1 = torch.empty_like(ws[0])
+        S.primal_step(ws[-1], w1, s=sd)
+        ws.append(w1)
+    J = torch.zeros(1, dtype=torch.float64, device="cuda")
+    lam = torch.zeros_like(ws[0])
+    sbar = torch.zeros_like(lam)
+    E = torch.zeros((N + 1, 1), dtype=torch.float64, device="cuda")
+    S.objective(ws[N], J, 1.0 / N, lam)
+    S.adjoint_energy(ws[N], lam, E[N])
+    sdt = torch.float64 if prec == 0 else torch.float32
+    sig = torch.empty(w0.shape[1:], dtype=sdt, device="cuda")
+    nu = torch.empty_like(sig)
+    for n in range(N - 1, -1, -1):
+        S.growth_sigma1(ws[n], sig)
+        S.add_adjoint_viscosity(sig, lam_coef, nu)
+        lo = torch.empty_like(lam)
+        S.adjoint_step(ws[n], lam, lo, s=sd, nu=nu, sbar=sbar)
+        lam = lo
+        if n >= 1:
+            S.objective(ws[n], J, 1.0 / N, lam)
+        S.adjoint_energy(ws[n], lam, E[n])
+    schedule, param = sched
+    path = str(tmp_path / "snap.bin") if schedule == 4 else None
+    opts = S.run_opts(N, schedule, param, lam_coef, 0.0, True, disk_path=path)
+    arena = torch.empty(S.arena_bytes(opts), dtype=torch.uint8, device="cuda")
+    Js = torch.empty(1, dtype=torch.float64, device="cuda")
+    lam0 = torch.empty_like(lam)
+    sb0 = torch.empty_like(lam)
+    Es = torch.zeros_like(E)
+    S.adjoint_run(dev(w0), opts, arena, Js, lam0, s=sd, sbar=sb0, energy=Es)
+    torch.cuda.synchronize()
+    assert S.last_error() == 0
+    assert torch.equal(Js, J) and torch.equal(lam0, lam) and torch.equal(sb0, sbar) and torch.equal(Es, E)
+    traj, Jref = O.primal_run(w0, P, N, s)
+    nu_of = lambda w: lam_coef * O.sigma1_field(w, P)
+    lam_ref, sbar_ref = O.adjoint_run(traj, P, s, nu_of)
+    tol = 1e-10 if prec == 0 else 1e-4
+    assert abs(Js.item() - Jref) <= tol * abs(Jref)
+    assert rel_l2(host(lam0), lam_ref) < tol
+    assert rel_l2(host(sb0), sbar_ref) < tol
+
+
 def test_bounded_context_refuses_the_periodic_only_calls():
     api = _api()
     w, P = _case((12, 6, 2), 52, "inout")
@@ -170,7 +230,8 @@ def test_bounded_context_refuses_the_periodic_only_calls():
     out = torch.empty_like(wd)
     with pytest.raises(api.NsError):
         S.rhs_tangent(wd, wd.clone(), out)
-    opts = S.run_opts(3, api.NS_CKPT_ALL, 0)
+    # the sweep runs on a bounded box, but without sigma_1 statistics or the learned closure
+    opts = S.run_opts(3, api.NS_CKPT_ALL, 0, record_sigma=True)
     arena = torch.empty(S.arena_bytes(opts), dtype=torch.uint8, device="cuda")
     with pytest.raises(api.NsError):
         S.adjoint_run(wd, opts, arena, torch.empty(1, dtype=torch.float64, device="cuda"), out)
