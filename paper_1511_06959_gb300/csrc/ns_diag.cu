@@ -473,6 +473,19 @@ __device__ __forceinline__ void growth_matrix(const GridDesc& g, const Coef<CT>&
   M[4][4] -= gm1 / CT(2) * div;
 }
 
+// (hi, lo) += (bhi, blo) for unevaluated float pairs hi + lo: Knuth's two-sum of the high
+// parts, the low parts added to its error, then a renormalising fast two-sum.  The pair
+// keeps the sum of float terms to about 2^-44 relative; the result does not depend on
+// the order of the two operands.
+__device__ __forceinline__ void df_add(float& hi, float& lo, float bhi, float blo) {
+  const float s = hi + bhi;
+  const float bb = s - hi;
+  float e = (hi - (s - bb)) + (bhi - bb);
+  e = e + (lo + blo);
+  hi = s + e;
+  lo = e - (hi - s);
+}
+
 // sigma_1 by plane marching.  A CTA owns a TX x SG_TY tile of columns and a range of
 // planes (march_range, as the stencil kernels); the primitives (rho, u1, u2, u3, p, a, b)
 // of three consecutive planes of the tile and its one-cell halo sit in a shared-memory
@@ -569,7 +582,8 @@ __global__ void __launch_bounds__(sgk::NT, sizeof(CT) == 4 ? 3 : 1) k_sigma1(Gri
   __syncthreads();
   const int ic = (ty + 1) * SX + (tx + 1);
   CT vmax = CT(0);
-  double vsum = 0.0;
+  double vsum = 0.0;             // FP64 contexts
+  float shi = 0.0f, slo = 0.0f;  // FP32 sigma_1: a compensated float-pair sum
   for (int k = kz0; k < kz1; ++k) {
     const bool more = k + 1 < kz1;
     CT qf[2][5];
@@ -654,7 +668,7 @@ __global__ void __launch_bounds__(sgk::NT, sizeof(CT) == 4 ? 3 : 1) k_sigma1(Gri
           if (!(v <= rule.limit)) atomicOr(rule.err, ERRBIT_UNSTABLE);
         }
         vmax = fmax(vmax, CT(sf));
-        vsum += (double)sf;
+        df_add(shi, slo, sf, 0.0f);
       }
     }
     __syncthreads();   // plane k-1 no longer read
@@ -663,7 +677,25 @@ __global__ void __launch_bounds__(sgk::NT, sizeof(CT) == 4 ? 3 : 1) k_sigma1(Gri
   }
   if (!stats) return;
   const double bmax = block_reduce(vmax, sh, MaxOp());
-  const double bsum = block_reduce(vsum, sh, AddOp());
+  double bsum;
+  if (sigd) {
+    bsum = block_reduce(vsum, sh, AddOp());
+  } else {
+    // the warp's float pairs, one FP64 value per warp, added in order by thread 0
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+      df_add(shi, slo, __shfl_xor_sync(0xffffffffu, shi, o), __shfl_xor_sync(0xffffffffu, slo, o));
+    __syncthreads();
+    if ((tid & 31) == 0) sh[tid >> 5] = widen(shi) + widen(slo);
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0.0;
+      for (int i = 0; i < NT / 32; ++i) t += sh[i];
+      sh[0] = t;
+    }
+    __syncthreads();
+    bsum = sh[0];
+  }
   const int G = gridDim.x;
   if (tid < g.batch) {
     partial[(size_t)(2 * tid) * G + blockIdx.x] = tid == b ? bmax : 0.0;
@@ -819,8 +851,8 @@ __global__ void k_visc_apply(GridDesc g, double ix2, double iy2, double iz2, dou
 // adjoint energy: v_hat = S^-T V^-T w_hat in closed form ("Symmetrization")
 // ---------------------------------------------------------------------------------
 template <class T, class TIN>
-__device__ __forceinline__ double energy_cell(const TIN* __restrict__ w, const TIN* __restrict__ lam,
-                                              size_t box, long long cells, long long i, T gamma) {
+__device__ __forceinline__ T energy_cell(const TIN* __restrict__ w, const TIN* __restrict__ lam,
+                                         size_t box, long long cells, long long i, T gamma) {
   const T gm1 = gamma - T(1), sg = sqrt(gamma), sgg = sqrt(gm1 / gamma);
   const T r = cvt<T>(w[box + i]), ir = T(1) / r;
   const T u0 = cvt<T>(w[box + cells + i]) * ir, u1 = cvt<T>(w[box + 2 * cells + i]) * ir,
@@ -837,8 +869,9 @@ __device__ __forceinline__ double energy_cell(const TIN* __restrict__ w, const T
   // v_hat = S^-T y
   const T v0 = sg * r / cs * y0 + r * cs / sg * y4;
   const T v4 = r * cs * sgg * y4;
-  return widen(v0 * v0 + y1 * y1 + y2 * y2 + y3 * y3 + v4 * v4);
+  return v0 * v0 + y1 * y1 + y2 * y2 + y3 * y3 + v4 * v4;
 }
+
 
 // E[b] = dV sum_cells |v_hat|^2; the last block of each box adds the block partials in
 // fixed order (ticket: per-box counters, zero on entry and on exit).
@@ -852,9 +885,26 @@ __global__ void __launch_bounds__(RB, sizeof(T) == 4 ? 8 : 1) k_energy(GridDesc 
   const int b = blockIdx.y;
   const size_t box = (size_t)b * 5 * g.cells;
   double acc = 0.0;
-  for (long long i = (long long)blockIdx.x * RB + threadIdx.x; i < g.cells; i += (long long)gridDim.x * RB)
-    acc += energy_cell<T, TIN>(w, lam, box, g.cells, i, T(gamma));
-  acc = block_reduce(acc, sh, AddOp());
+  if constexpr (sizeof(T) == 4) {
+    // FP32 cell energies: compensated float-pair sums per thread and across the warp
+    // (FP32 instructions; FP64 runs at a small fraction of their rate), one FP64 value
+    // per warp, the warps' values added in order by thread 0
+    float hi = 0.0f, lo = 0.0f;
+    for (long long i = (long long)blockIdx.x * RB + threadIdx.x; i < g.cells; i += (long long)gridDim.x * RB)
+      df_add(hi, lo, energy_cell<T, TIN>(w, lam, box, g.cells, i, T(gamma)), 0.0f);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+      df_add(hi, lo, __shfl_xor_sync(0xffffffffu, hi, o), __shfl_xor_sync(0xffffffffu, lo, o));
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = widen(hi) + widen(lo);
+    __syncthreads();
+    if (threadIdx.x == 0)
+      for (int i = 0; i < RB / 32; ++i) acc += sh[i];
+    __syncthreads();   // sh is reused by the last block's reduction
+  } else {
+    for (long long i = (long long)blockIdx.x * RB + threadIdx.x; i < g.cells; i += (long long)gridDim.x * RB)
+      acc += energy_cell<T, TIN>(w, lam, box, g.cells, i, T(gamma));
+    acc = block_reduce(acc, sh, AddOp());
+  }
   double* pb = partial + (size_t)b * gridDim.x;
   if (threadIdx.x == 0) {
     pb[blockIdx.x] = acc;

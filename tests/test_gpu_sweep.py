@@ -113,6 +113,28 @@ def test_batched_sweep_matches_single_boxes():
 
 
 @pytest.mark.parametrize("prec", [0, 1])
+def test_batched_sigma_and_energy_series_match_single_boxes(prec):
+    """A batch of three boxes: each box's sigma_1 statistics (per-box partials of every
+    CTA, reduced by the last one) and energy series equal the single box's, the maxima
+    exactly and the sums to their summation order."""
+    api = _api()
+    shape = (33, 8, 4)
+    ws0 = np.stack([synth.isentropic_vortex(*shape, noise=1e-3, seed=30 + i) for i in range(3)])
+    P = params_for(ws0[0], mu=1e-3, dt=4e-3)
+    N = 5
+    lam_coef = 0.5 * P.dx[0] ** 2
+    S = make_solver(api, ws0[0], P, prec, batch=3)
+    _, _, _, E, st = _run(api, S, ws0, N, 1, 2, lam_coef=lam_coef, energy=True, sigma=True)
+    assert S.last_error() == 0
+    S1 = make_solver(api, ws0[0], P, prec)
+    for i in range(3):
+        _, _, _, Ei, sti = _run(api, S1, ws0[i], N, 1, 2, lam_coef=lam_coef, energy=True, sigma=True)
+        assert torch.equal(st[:, i, 0], sti[:, 0, 0])
+        np.testing.assert_allclose(host(st[:, i, 1]), host(sti[:, 0, 1]), rtol=1e-12)
+        np.testing.assert_allclose(host(E[:, i]), host(Ei[:, 0]), rtol=1e-12)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
 def test_host_snapshots_give_the_stride_bits(prec):
     """NS_CKPT_STRIDE_HOST keeps the every-k-th snapshots in host memory and copies them
     on the context's stream: the sweep (stabilised, with a source, energy and sigma_1
