@@ -188,6 +188,13 @@ int ns_add_adjoint_viscosity_f64(ns_ctx* ctx, const double* sigma1, double lambd
  * non-negative values, else NS_ERR_ARG. */
 int ns_set_viscosity_split(ns_ctx* ctx, const double* split);
 
+/* cap != 0: every added adjoint viscosity this context forms afterwards (the sigma_1 rule
+ * of ns_add_adjoint_viscosity(_f64) and of the sweeps, and the learned closure) is held
+ * at the explicit stability limit named above in the cells where it would exceed it,
+ * instead of being left there and flagged with NS_ERR_UNSTABLE; a non-finite value is
+ * still flagged.  cap = 0 (the default) restores the flag. */
+int ns_set_viscosity_cap(ns_ctx* ctx, int cap);
+
 /* out += L_nu a = div(nu grad a) per component, nu_face = mean of the two cells
  * (the discrete added-viscosity operator alone), times the component's factor of
  * ns_set_viscosity_split. */

@@ -46,7 +46,7 @@ EXPORTED = [
     "ns_profile_read", "ns_to_float", "ns_forward_run", "ns_backward_run", "ns_scale_boxes",
     "ns_dot_boxes", "ns_mlp_net_bytes", "ns_mlp_set_params", "ns_mlp_get_params", "ns_mlp_get_moment",
     "ns_mlp_features", "ns_mlp_infer", "ns_mlp_train_step", "ns_adjoint_label", "ns_label_target",
-    "ns_launch_count", "ns_set_viscosity_split", "ns_energy_efolds", "ns_lambda_select",
+    "ns_launch_count", "ns_set_viscosity_split", "ns_set_viscosity_cap", "ns_energy_efolds", "ns_lambda_select",
     "ns_estimate_work_bytes", "ns_estimate_lambda", "ns_run_host_bytes", "ns_measure_fma_peak",
     "ns_sweep_generation", "ns_growth_sigma1_f64", "ns_add_adjoint_viscosity_f64", "ns_adjoint_step_f64",
     "ns_slab_group_create", "ns_slab_group_destroy", "ns_slab_set_exchange", "ns_slab_exchange",
@@ -163,6 +163,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "ns_slab_adjoint_step": ([P, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P),
                                   ctypes.POINTER(P)], I),
         "ns_set_viscosity_split": ([P, ctypes.POINTER(ctypes.c_double)], I),
+        "ns_set_viscosity_cap": ([P, I], I),
         "ns_plan": ([I, I, I, P, I, ctypes.POINTER(I), ctypes.POINTER(I),
                      ctypes.POINTER(ctypes.c_longlong)], I),
         "ns_run_arena_bytes": ([P, ctypes.POINTER(NsRunOpts)], S),
@@ -421,6 +422,11 @@ class Solver:
     def set_viscosity_split(self, f_rho: float, f_mom: float, f_en: float):
         arr = (ctypes.c_double * 3)(f_rho, f_mom, f_en)
         _check(self.lib.ns_set_viscosity_split(self._ctx, arr), "ns_set_viscosity_split")
+
+    def set_viscosity_cap(self, cap: bool):
+        """Hold the added viscosity at the explicit stability limit instead of flagging it
+        (ns_set_viscosity_cap)."""
+        _check(self.lib.ns_set_viscosity_cap(self._ctx, int(bool(cap))), "ns_set_viscosity_cap")
 
     def last_error(self) -> int:
         return int(self.lib.ns_last_error(self._ctx))

@@ -23,8 +23,12 @@ BUILD_DEBUG = os.path.join(HERE, "_build_debug")
 SOURCES = ["ns_rhs.cu", "ns_adj.cu", "ns_diag.cu", "ns_api.cu", "ns_sweep.cu", "ns_noalloc.cu", "ns_mlp.cu",
            "ns_lambda.cu", "ns_probe.cu", "ns_bc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# Single-precision division and square root in the fast form (-prec-div/-prec-sqrt off):
+# a few units in the last place instead of correctly rounded, in the FP32 products of the
+# mixed path only (FP64 is unaffected); the stencil and sigma_1 kernels spend many of
+# their instructions on them.
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
-         "-Xptxas", "-warn-spills"]
+         "-Xptxas", "-warn-spills", "-prec-div=false", "-prec-sqrt=false"]
 
 
 def nvcc() -> str:

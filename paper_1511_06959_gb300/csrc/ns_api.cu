@@ -661,12 +661,12 @@ static double nu_limit(const ns_ctx* c) {
 int ns_add_adjoint_viscosity(ns_ctx* c, const float* sigma1, double lambda, double tau, float* nu) {
   if (!c || !sigma1 || !nu || !(lambda >= 0)) return NS_ERR_ARG;
   const double limit = nu_limit(c);
-  return cuerr(ns::launch_nu_rule(c->g, sigma1, lambda, tau, limit, nu, c->err, c->st));
+  return cuerr(ns::launch_nu_rule(c->g, sigma1, lambda, tau, limit, nu, c->err, c->st, c->nu_cap != 0));
 }
 
 int ns_add_adjoint_viscosity_f64(ns_ctx* c, const double* sigma1, double lambda, double tau, double* nu) {
   if (!c || !sigma1 || !nu || !(lambda >= 0)) return NS_ERR_ARG;
-  return cuerr(ns::launch_nu_rule_f64(c->g, sigma1, lambda, tau, nu_limit(c), nu, c->err, c->st));
+  return cuerr(ns::launch_nu_rule_f64(c->g, sigma1, lambda, tau, nu_limit(c), nu, c->err, c->st, c->nu_cap != 0));
 }
 
 int ns_apply_adjoint_viscosity(ns_ctx* c, const float* nu, const double* a, double* out) {
@@ -732,7 +732,7 @@ int ns_mlp_infer(ns_ctx* c, const void* net, const float* feat, const float* sig
   if (!c || !net || !feat || !sigma1 || !nu || !(kappa >= 0)) return NS_ERR_ARG;
   const double scale = kappa * c->p.dx * c->p.dx;
   return cuerr(ns::launch_mlp_infer(c->g.cells * c->g.batch, const_cast<void*>(net), feat, sigma1, scale,
-                                    nu_limit(c), nu, c->err, c->st));
+                                    nu_limit(c), nu, c->err, c->st, c->nu_cap != 0));
 }
 
 int ns_mlp_train_step(ns_ctx* c, void* net, const float* feat, const float* target, const int* idx, int n,
@@ -773,6 +773,12 @@ int ns_to_float(ns_ctx* c, const double* in, float* out, size_t n) {
 int ns_max_wave_speed(ns_ctx* c, const double* w, double* out) {
   if (!c || !w || !out) return NS_ERR_ARG;
   return cuerr(ns::launch_max_wave(c->g, c->p.gamma, w, out, c->scratch, c->st));
+}
+
+int ns_set_viscosity_cap(ns_ctx* c, int cap) {
+  if (!c) return NS_ERR_ARG;
+  c->nu_cap = cap != 0;
+  return NS_OK;
 }
 
 int ns_set_viscosity_split(ns_ctx* c, const double* split) {
@@ -888,14 +894,14 @@ int ns_i_energy(ns_ctx* c, const double* w, const void* w_mirror, const double* 
 
 int ns_i_sigma1_f64(ns_ctx* c, const double* w, double* sigma1, double* stats, double lambda, double tau,
                     double* nu) {
-  ns::NuRule rule{0.f, 0.f, 0.f, nullptr, c->err, lambda, tau, nu_limit(c), nu};
+  ns::NuRule rule{0.f, 0.f, 0.f, nullptr, c->err, lambda, tau, nu_limit(c), nu, c->nu_cap};
   return cuerr(ns::launch_sigma1<double>(c->g, c->cd, w, nullptr, stats, c->scratch, c->ticket, c->st,
                                          nu ? &rule : nullptr, sigma1));
 }
 
 int ns_i_sigma1(ns_ctx* c, const double* w, const void* w_mirror, float* sigma1, double* stats, double lambda,
                 double tau, float* nu) {
-  ns::NuRule rule{(float)lambda, (float)tau, (float)nu_limit(c), nu, c->err, 0.0, 0.0, 0.0, nullptr};
+  ns::NuRule rule{(float)lambda, (float)tau, (float)nu_limit(c), nu, c->err, 0.0, 0.0, 0.0, nullptr, c->nu_cap};
   const ns::NuRule* rp = nu ? &rule : nullptr;
   if (mixed(c)) {
     const float* wf = (const float*)w_mirror;

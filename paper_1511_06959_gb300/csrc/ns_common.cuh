@@ -266,6 +266,16 @@ constexpr unsigned ERRBIT_UNSTABLE = 2u;
 constexpr unsigned ERRBIT_CORRUPT = 4u;
 constexpr unsigned ERRBIT_BOUNDS = 8u;
 
+// An added adjoint viscosity v against the explicit stability limit: held at the limit
+// where it exceeds it when cap is set; otherwise left, and flagged (NS_ERR_UNSTABLE) when
+// above the limit or not finite.
+template <class T>
+__device__ __forceinline__ T nu_checked(T v, T limit, bool cap, unsigned* err) {
+  if (cap && v > limit) return limit;
+  if (!(v <= limit)) atomicOr(err, ERRBIT_UNSTABLE);
+  return v;
+}
+
 // ---------------------------------------------------------------------------------
 // Field accesses of the stencil kernels.  A field element is addressed as a base (box,
 // plane and component: uniform over the CTA) plus the thread's in-plane offset.  Debug

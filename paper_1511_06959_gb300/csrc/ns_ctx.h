@@ -20,6 +20,7 @@ struct ns_ctx {
   ns::Coef<ns::Dual> cx;
   size_t field = 0;              // elements of one [batch][5][cells] field
   double nu_split[3] = {1.0, 1.0, 1.0};   // added-viscosity factors: rho, rho u, rho E
+  int nu_cap = 0;                         // hold nu at the explicit limit (ns_set_viscosity_cap)
   // stage buffers of the stage type (double in FP64 mode, float in MIXED mode):
   // float mirrors of w and lambda, stage states W2..W4, two seeds, the stage-product
   // (or RK increment) sum and the seed sum

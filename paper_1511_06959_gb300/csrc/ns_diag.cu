@@ -652,21 +652,15 @@ __global__ void __launch_bounds__(sgk::NT, sizeof(CT) == 4 ? 3 : 1) k_sigma1(Gri
         // FP64 contexts: sigma_1 and the rule's viscosity kept in FP64
         const double sd = (double)s1;
         sigd[o] = sd;
-        if (rule.nud) {
-          const double v = sd > rule.taud ? rule.lamd * sd : 0.0;
-          rule.nud[o] = v;
-          if (!(v <= rule.limitd)) atomicOr(rule.err, ERRBIT_UNSTABLE);
-        }
+        if (rule.nud)
+          rule.nud[o] = nu_checked(sd > rule.taud ? rule.lamd * sd : 0.0, rule.limitd, rule.cap != 0, rule.err);
         vmax = fmax(vmax, s1);
         vsum += sd;
       } else {
         const float sf = (float)s1;
         sig[o] = sf;
-        if (rule.nu) {
-          const float v = sf > rule.tau ? rule.lam * sf : 0.0f;
-          rule.nu[o] = v;
-          if (!(v <= rule.limit)) atomicOr(rule.err, ERRBIT_UNSTABLE);
-        }
+        if (rule.nu)
+          rule.nu[o] = nu_checked(sf > rule.tau ? rule.lam * sf : 0.0f, rule.limit, rule.cap != 0, rule.err);
         vmax = fmax(vmax, CT(sf));
         df_add(shi, slo, sf, 0.0f);
       }
@@ -796,24 +790,20 @@ __global__ void __launch_bounds__(RB) k_label(GridDesc g, Coef<CT> c, const CT* 
 // added adjoint viscosity: coefficient rule and the operator alone
 // ---------------------------------------------------------------------------------
 __global__ void k_nu_rule(long long n, const float* __restrict__ s1, float lam, float tau,
-                          float limit_nu, float* __restrict__ nu, unsigned* err) {
+                          float limit_nu, float* __restrict__ nu, unsigned* err, bool cap) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const float s = s1[i];
-  const float v = s > tau ? lam * s : 0.0f;
-  nu[i] = v;
-  if (!(v <= limit_nu)) atomicOr(err, ERRBIT_UNSTABLE);
+  nu[i] = nu_checked(s > tau ? lam * s : 0.0f, limit_nu, cap, err);
 }
 
 // the same rule in FP64 (FP64 contexts)
 __global__ void k_nu_rule_f64(long long n, const double* __restrict__ s1, double lam, double tau,
-                              double limit_nu, double* __restrict__ nu, unsigned* err) {
+                              double limit_nu, double* __restrict__ nu, unsigned* err, bool cap) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const double s = s1[i];
-  const double v = s > tau ? lam * s : 0.0;
-  nu[i] = v;
-  if (!(v <= limit_nu)) atomicOr(err, ERRBIT_UNSTABLE);
+  nu[i] = nu_checked(s > tau ? lam * s : 0.0, limit_nu, cap, err);
 }
 
 __global__ void k_visc_apply(GridDesc g, double ix2, double iy2, double iz2, double f_rho, double f_mom,
@@ -1115,7 +1105,7 @@ template <class CT>
 cudaError_t launch_sigma1(const GridDesc& g, const Coef<CT>& c, const CT* w, float* sigma1,
                           double* stats, double* scratch, unsigned* ticket, cudaStream_t st,
                           const NuRule* rule, double* sigma1d) {
-  const NuRule r = rule ? *rule : NuRule{0.f, 0.f, 0.f, nullptr, nullptr, 0.0, 0.0, 0.0, nullptr};
+  const NuRule r = rule ? *rule : NuRule{0.f, 0.f, 0.f, nullptr, nullptr, 0.0, 0.0, 0.0, nullptr, 0};
   const size_t smem = sizeof(CT) * 3 * sgk::NV * sgk::SP;
   static MarchShape<TX, sgk::TY> shape;
   int ctas = 0;
@@ -1147,18 +1137,18 @@ template cudaError_t launch_label<float>(const GridDesc&, const Coef<float>&, co
                                          float*, cudaStream_t);
 
 cudaError_t launch_nu_rule(const GridDesc& g, const float* sigma1, double lambda, double tau,
-                           double limit_nu, float* nu, unsigned* err, cudaStream_t st) {
+                           double limit_nu, float* nu, unsigned* err, cudaStream_t st, bool cap) {
   const long long n = g.cells * g.batch;
   k_nu_rule<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, sigma1, (float)lambda, (float)tau,
-                                                           (float)limit_nu, nu, err);
+                                                           (float)limit_nu, nu, err, cap);
   count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_nu_rule_f64(const GridDesc& g, const double* sigma1, double lambda, double tau,
-                               double limit_nu, double* nu, unsigned* err, cudaStream_t st) {
+                               double limit_nu, double* nu, unsigned* err, cudaStream_t st, bool cap) {
   const long long n = g.cells * g.batch;
-  k_nu_rule_f64<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, sigma1, lambda, tau, limit_nu, nu, err);
+  k_nu_rule_f64<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, sigma1, lambda, tau, limit_nu, nu, err, cap);
   count_launch();
   return cudaGetLastError();
 }

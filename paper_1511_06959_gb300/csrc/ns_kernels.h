@@ -100,6 +100,7 @@ struct NuRule {
   unsigned* err;
   double lamd, taud, limitd;   // the same rule in FP64 (with nud)
   double* nud;    // FP64 viscosity output (FP64 contexts, with an FP64 sigma_1 output)
+  int cap;        // hold nu at the limit instead of flagging it (ns_set_viscosity_cap)
 };
 
 // sigma_1 per cell; stats (may be null): [batch][2] = (max, mean), reduced by the last
@@ -115,9 +116,9 @@ template <class CT>
 cudaError_t launch_label(const GridDesc& g, const Coef<CT>& c, const CT* w, const double* lam, float* acc,
                          cudaStream_t st);
 cudaError_t launch_nu_rule(const GridDesc& g, const float* sigma1, double lambda, double tau,
-                           double limit_nu, float* nu, unsigned* err, cudaStream_t st);
+                           double limit_nu, float* nu, unsigned* err, cudaStream_t st, bool cap = false);
 cudaError_t launch_nu_rule_f64(const GridDesc& g, const double* sigma1, double lambda, double tau,
-                               double limit_nu, double* nu, unsigned* err, cudaStream_t st);
+                               double limit_nu, double* nu, unsigned* err, cudaStream_t st, bool cap = false);
 cudaError_t launch_visc_apply(const GridDesc& g, const double* idx2, const double* split,
                               const float* nu, const double* a, double* out, cudaStream_t st);
 cudaError_t launch_energy(const GridDesc& g, double gamma, double dV, const double* w,

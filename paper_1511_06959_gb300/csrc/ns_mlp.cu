@@ -178,7 +178,7 @@ constexpr int W2S = 36;   // padded row stride of W2t: 64 bf16 = 32 words
 
 __global__ void __launch_bounds__(256, 3) k_mlp_infer(long long n, MlpView net, const float* __restrict__ feat,
                                                       const float* __restrict__ sigma1, float scale, float limit_nu,
-                                                      float* __restrict__ nu, unsigned* err) {
+                                                      float* __restrict__ nu, unsigned* err, bool cap) {
   __shared__ unsigned sW1[NH * W1S];
   __shared__ unsigned sW2[NH * W2S];
   __shared__ float sb1[NH], sb2[NH], sw3[NH];
@@ -245,16 +245,8 @@ __global__ void __launch_bounds__(256, 3) k_mlp_infer(long long n, MlpView net, 
     y1 += __shfl_xor_sync(0xffffffffu, y1, 1);
     y1 += __shfl_xor_sync(0xffffffffu, y1, 2);
     if (tq == 0) {
-      if (r0 < n) {
-        const float v = scale * sigma1[r0] * softplus(y0 + b3);
-        nu[r0] = v;
-        if (!(v <= limit_nu)) atomicOr(err, ERRBIT_UNSTABLE);
-      }
-      if (r1 < n) {
-        const float v = scale * sigma1[r1] * softplus(y1 + b3);
-        nu[r1] = v;
-        if (!(v <= limit_nu)) atomicOr(err, ERRBIT_UNSTABLE);
-      }
+      if (r0 < n) nu[r0] = nu_checked(scale * sigma1[r0] * softplus(y0 + b3), limit_nu, cap, err);
+      if (r1 < n) nu[r1] = nu_checked(scale * sigma1[r1] * softplus(y1 + b3), limit_nu, cap, err);
     }
   }
 }
@@ -568,13 +560,13 @@ template cudaError_t launch_features<float>(const GridDesc&, const Coef<float>&,
                                             float*, cudaStream_t);
 
 cudaError_t launch_mlp_infer(long long n, void* blob, const float* feat, const float* sigma1, double scale,
-                             double limit_nu, float* nu, unsigned* err, cudaStream_t st) {
+                             double limit_nu, float* nu, unsigned* err, cudaStream_t st, bool cap) {
   const long long tiles = (n + 15) / 16;
   long long blocks = (tiles + 7) / 8;
   if (blocks > 3 * 152) blocks = 3 * 152;   // one wave at three resident CTAs per SM
   if (blocks < 1) blocks = 1;
   k_mlp_infer<<<(unsigned)blocks, 256, 0, st>>>(n, mlp_view(blob), feat, sigma1, (float)scale, (float)limit_nu,
-                                                nu, err);
+                                                nu, err, cap);
   count_launch();
   return cudaGetLastError();
 }

@@ -54,7 +54,7 @@ template <class TIN>
 cudaError_t launch_features(const GridDesc& g, const Coef<float>& c, const TIN* w, const double* qbar,
                             float* feat, cudaStream_t st);
 cudaError_t launch_mlp_infer(long long n, void* blob, const float* feat, const float* sigma1, double scale,
-                             double limit_nu, float* nu, unsigned* err, cudaStream_t st);
+                             double limit_nu, float* nu, unsigned* err, cudaStream_t st, bool cap = false);
 size_t mlp_train_scratch_floats(int n);
 cudaError_t launch_mlp_train_step(void* blob, const float* feat, const float* target, const int* idx, int n,
                                   int step, double lr, float* scratch, float* loss, cudaStream_t st);

@@ -102,7 +102,7 @@ def sensitivity_scan(S, w, s, nsteps, stride, lambdas, dx0):
 
 
 def closure_judge(S, S64, w, s, nsteps, stride, dx0, rule_tildes, kappas, g_ref, label_starts=(0, 2000, 4000),
-                  label_steps=100, label_every=5, train_steps=4000, batch=8192, lr=2e-3):
+                  label_steps=100, label_every=5, train_steps=4000, batch=8192, lr=2e-3, cap=False):
     """The learned closure against the sigma_1 rule on the forced box, with finite
     differences of J-bar (g_ref) as the reference (the unstabilised adjoint grows here, so
     it is no reference).  Labels come from short-horizon FP64 adjoints (S64) started at states
@@ -110,7 +110,9 @@ def closure_judge(S, S64, w, s, nsteps, stride, dx0, rule_tildes, kappas, g_ref,
     library's BF16 kernels; each closure setting is one stabilised sweep over nsteps
     (S, mixed precision), giving dJ-bar/dtheta for s(theta) = (1 + theta) s and the
     adjoint energy E_vhat(w^0, lam^0).  The errors of both closures are compared at the
-    energy of the rule's middle setting (log-linear interpolation in the energy)."""
+    energy of the rule's middle setting (log-linear interpolation in the energy).  cap:
+    both closures' coefficients held at the explicit stability limit
+    (ns_set_viscosity_cap) instead of dropping the settings that exceed it."""
     dev = w.device
     t0 = time.perf_counter()
     feats, targets = [], []
@@ -150,6 +152,7 @@ def closure_judge(S, S64, w, s, nsteps, stride, dx0, rule_tildes, kappas, g_ref,
 
     t0 = time.perf_counter()
     g0, E0, _ = sens(0.0, None)
+    S.set_viscosity_cap(cap)
 
     def sweep(coefs, mlp):
         rows, dropped = [], []
@@ -163,8 +166,9 @@ def closure_judge(S, S64, w, s, nsteps, stride, dx0, rule_tildes, kappas, g_ref,
 
     rule, rule_dropped = sweep([t * dx0 ** 2 for t in rule_tildes], None)
     learned, learned_dropped = sweep(list(kappas), net.blob)
+    S.set_viscosity_cap(False)
     t_judge = time.perf_counter() - t0
-    out = {"samples": nsamp, "train_loss_first": float(losses[:50].mean()),
+    out = {"samples": nsamp, "cap": bool(cap), "train_loss_first": float(losses[:50].mean()),
            "train_loss_last": float(losses[-50:].mean()),
            "seconds": {"generate": t_gen, "train": t_train, "judge": t_judge},
            "reference_dJ_dtheta": g_ref,
@@ -187,7 +191,7 @@ def closure_judge(S, S64, w, s, nsteps, stride, dx0, rule_tildes, kappas, g_ref,
 
 def run(nx, ny, nz, U0, Re_f, mach, spinup, nsteps, stride, lambdas, precision, cfl, seed, flux="central",
         sep_steps=0, sens_lambdas=(), fd_eps=(0.05, 0.1, 0.2), judge=False, fd_steps=0,
-        judge_rule=(0.2, 0.4, 0.8, 1.6, 2.4), judge_kappas=(0.2, 0.4, 0.8, 1.6, 3.2, 6.4, 12.8)):
+        judge_rule=(0.2, 0.4, 0.8, 1.6, 2.4), judge_kappas=(0.2, 0.4, 0.8, 1.6, 3.2, 6.4, 12.8), judge_cap=False):
     gamma = 1.4
     dx = synth.box_shape(nx, ny, nz)
     Ly = ny * dx[1]
@@ -247,7 +251,7 @@ def run(nx, ny, nz, U0, Re_f, mach, spinup, nsteps, stride, lambdas, precision, 
                          plane_i=(3 * nx) // 4, pt_in=pt_in,
                          flux=api.NS_FLUX_ROE if flux == "roe" else api.NS_FLUX_CENTRAL)
         out["closure_judge"] = closure_judge(S, S64, wspun, s, nsteps, stride, dx[0], judge_rule, judge_kappas,
-                                             out["finite_differences"]["mean_dJ_dtheta"])
+                                             out["finite_differences"]["mean_dJ_dtheta"], cap=judge_cap)
         del S64
     # the plain adjoint from the developed state
     opts = S.run_opts(nsteps, api.NS_CKPT_STRIDE, stride, 0.0, 0.0, True, True)
@@ -308,6 +312,8 @@ def main(argv=None):
                     help="train the learned closure on this flow and judge it against the sigma_1 rule")
     ap.add_argument("--judge-rule", default="0.2,0.4,0.8,1.6,2.4", help="lambda-tilde values of the rule's sweep")
     ap.add_argument("--judge-kappas", default="0.2,0.4,0.8,1.6,3.2,6.4,12.8", help="kappa values of the learned sweep")
+    ap.add_argument("--judge-cap", action="store_true",
+                    help="hold both closures' coefficients at the explicit stability limit")
     ap.add_argument("--out", default=None)
     a = ap.parse_args(argv)
     lambdas = tuple(float(t) for t in a.lambdas.split(",")) if a.lambdas else ()
@@ -315,7 +321,8 @@ def main(argv=None):
               api.NS_FP64 if a.fp64 else api.NS_MIXED, a.cfl, a.seed, a.flux, a.separation,
               tuple(float(t) for t in a.sens_lambdas.split(",")) if a.sens_lambdas else (),
               tuple(float(t) for t in a.fd_eps.split(",")), a.judge, a.fd_steps,
-              tuple(float(t) for t in a.judge_rule.split(",")), tuple(float(t) for t in a.judge_kappas.split(",")))
+              tuple(float(t) for t in a.judge_rule.split(",")), tuple(float(t) for t in a.judge_kappas.split(",")),
+              a.judge_cap)
     line = json.dumps(res)
     print(line)
     if a.out:

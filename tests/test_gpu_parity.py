@@ -227,6 +227,45 @@ def test_nu_rule_and_viscosity_operator():
     assert S.last_error() == api.NS_ERR_UNSTABLE
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_viscosity_cap_holds_nu_at_the_stability_limit(prec):
+    """With ns_set_viscosity_cap the rule's coefficient is min(lambda sigma_1, limit),
+    limit = 2.78 / (dt * 4 sum_d 1/dx_d^2) for RK4, with no error flag; without the cap
+    the same coefficient is left as it is and flagged.  Both the float rule and the FP64
+    rule, and the rule inside a sweep."""
+    api = _api()
+    shape = (37, 9, 5)
+    w = state(shape, 21)
+    P = params_for(w, dt=1e-3)
+    S = make_solver(api, w, P, prec)
+    limit = 2.78 / (P.dt * 4.0 * sum(1.0 / d ** 2 for d in P.dx))
+    s1 = np.abs(synth.random_field(w.shape[1:], 22))
+    lam = 1.5 * limit / s1.max()            # the largest cells exceed the limit
+    for dt_ in (np.float32, np.float64):
+        sig = torch.from_numpy(s1.astype(dt_)).cuda()
+        nu = torch.empty_like(sig)
+        S.add_adjoint_viscosity(sig, lam, nu)
+        raw = (dt_(lam) * s1.astype(dt_)).astype(dt_)
+        np.testing.assert_array_equal(host(nu), raw)
+        assert S.last_error() == api.NS_ERR_UNSTABLE
+        S.set_viscosity_cap(True)
+        S.add_adjoint_viscosity(sig, lam, nu)
+        assert S.last_error() == 0
+        np.testing.assert_array_equal(host(nu), np.minimum(raw, dt_(limit)))
+        assert (host(nu) == dt_(limit)).any() and (host(nu) < dt_(limit)).any()
+        S.set_viscosity_cap(False)
+    # a sweep whose rule exceeds the limit: flagged without the cap, clean with it
+    opts = S.run_opts(6, api.NS_CKPT_ALL, 0, 40.0 * P.dx[0] ** 2)
+    arena = torch.empty(S.arena_bytes(opts), dtype=torch.uint8, device="cuda")
+    J = torch.empty(1, dtype=torch.float64, device="cuda")
+    lam0 = torch.empty(w.shape, dtype=torch.float64, device="cuda")
+    S.adjoint_run(dev(w), opts, arena, J, lam0)
+    assert S.last_error() == api.NS_ERR_UNSTABLE
+    S.set_viscosity_cap(True)
+    S.adjoint_run(dev(w), opts, arena, J, lam0)
+    assert S.last_error() == 0 and torch.isfinite(lam0).all()
+
+
 def test_adjoint_energy_and_nonfinite_flag():
     api = _api()
     shape = (37, 9, 5)
