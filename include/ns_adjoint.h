@@ -586,6 +586,22 @@ int ns_slab_primal_step(ns_slab_group* group, const double* const* w, const doub
  * are current on return. */
 int ns_slab_adjoint_step(ns_slab_group* group, const double* const* w, const double* const* s,
                          const double* const* lam, const float* const* nu, double* const* lo);
+/* Workspace bytes of ns_slab_adjoint_run for each slab (bytes[k], host array of n). */
+int ns_slab_run_bytes(ns_slab_group* group, const ns_run_opts* o, size_t* bytes);
+/* The checkpointed sweep of ns_adjoint_run on a slab group: the same plan (NS_CKPT_ALL,
+ * NS_CKPT_STRIDE or NS_CKPT_REVOLVE; the host and disk tiers are NS_ERR_ARG) executed on
+ * every slab, each slab's states kept in its own workspace (work[k], device, 256-byte
+ * aligned, at least ns_slab_run_bytes; NS_ERR_BUDGET otherwise).  Slab `own` holds the
+ * objective plane (its two columns interior to it): it evaluates J and its source and
+ * Jbar (device, batch doubles, on own's stream) receives J-bar; lam0[k] (device fields)
+ * receives dJ-bar/dw^0 of each slab with current ghost columns.  With o->lambda > 0 the
+ * sigma_1 rule's viscosity is formed per slab (float, as ns_slab_adjoint_step takes it)
+ * and its ghost columns exchanged.  The learned closure, the energy and sigma_1 series
+ * and a source sensitivity are not available here (NS_ERR_ARG).  The results equal the
+ * same slab calls made step by step. */
+int ns_slab_adjoint_run(ns_slab_group* group, int own, const double* const* w0, const double* const* s,
+                        const ns_run_opts* o, void* const* work, const size_t* work_bytes, double* Jbar,
+                        double* const* lam0);
 
 /* Measured arithmetic peak of the current device: the rate of independent fused
  * multiply-adds (2 flops each) of kind NS_PEAK_FP32 (scalar FFMA), NS_PEAK_FP32X2 (the

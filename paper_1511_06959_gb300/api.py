@@ -50,7 +50,7 @@ EXPORTED = [
     "ns_estimate_work_bytes", "ns_estimate_lambda", "ns_run_host_bytes", "ns_measure_fma_peak",
     "ns_sweep_generation", "ns_growth_sigma1_f64", "ns_add_adjoint_viscosity_f64", "ns_adjoint_step_f64",
     "ns_slab_group_create", "ns_slab_group_destroy", "ns_slab_set_exchange", "ns_slab_exchange",
-    "ns_slab_primal_step", "ns_slab_adjoint_step", "ns_set_boundaries",
+    "ns_slab_primal_step", "ns_slab_adjoint_step", "ns_slab_run_bytes", "ns_slab_adjoint_run", "ns_set_boundaries",
 ]
 
 NS_MLP_PARAMS = 5185
@@ -160,6 +160,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "ns_slab_set_exchange": ([P, HALO_FN, P], I),
         "ns_slab_exchange": ([P, ctypes.POINTER(P), I, I], I),
         "ns_slab_primal_step": ([P, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P)], I),
+        "ns_slab_run_bytes": ([P, ctypes.POINTER(NsRunOpts), ctypes.POINTER(ctypes.c_size_t)], I),
+        "ns_slab_adjoint_run": ([P, I, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(NsRunOpts),
+                                 ctypes.POINTER(P), ctypes.POINTER(ctypes.c_size_t), P, ctypes.POINTER(P)], I),
         "ns_slab_adjoint_step": ([P, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P),
                                   ctypes.POINTER(P)], I),
         "ns_set_viscosity_split": ([P, ctypes.POINTER(ctypes.c_double)], I),
@@ -632,3 +635,22 @@ class SlabGroup:
                                              _ptr_array(s, torch.float64, f), _ptr_array(lam, torch.float64, f),
                                              _ptr_array(nu, torch.float32, self._sizes(1)),
                                              _ptr_array(lo, torch.float64, f)), "ns_slab_adjoint_step")
+
+    def run_bytes(self, opts):
+        """Workspace bytes of adjoint_run for each slab (ns_slab_run_bytes)."""
+        out = (ctypes.c_size_t * len(self.solvers))()
+        _check(self.lib.ns_slab_run_bytes(self._g, ctypes.byref(opts), out), "ns_slab_run_bytes")
+        return list(out)
+
+    def adjoint_run(self, own, w0, opts, work, Jbar, lam0, s=None):
+        """The checkpointed sweep on the group (ns_slab_adjoint_run): slab `own` holds the
+        objective plane; work: one uint8 CUDA tensor per slab of at least run_bytes."""
+        f = self._sizes(5)
+        if len(work) != len(self.solvers):
+            raise ValueError("one workspace per slab")
+        warr = (ctypes.c_void_p * len(work))(*[_ptr(t) for t in work])
+        wb = (ctypes.c_size_t * len(work))(*[t.numel() * t.element_size() for t in work])
+        _check(self.lib.ns_slab_adjoint_run(self._g, int(own), _ptr_array(w0, torch.float64, f),
+                                            _ptr_array(s, torch.float64, f), ctypes.byref(opts), warr, wb,
+                                            _sized(Jbar, torch.float64, self.solvers[own].batch, "Jbar"),
+                                            _ptr_array(lam0, torch.float64, f)), "ns_slab_adjoint_run")

@@ -1165,4 +1165,147 @@ int ns_slab_adjoint_step(ns_slab_group* G, const double* const* w, const double*
   return slab_adjoint_t<double>(G, w, lam, s, lam, nu, lo);
 }
 
+// The checkpointed sweep on a slab group: the plan of ns_plan, each action on every slab
+// (its states kept per slab), the objective and its source on slab `own`, the sigma_1
+// rule's viscosity per slab with its ghost columns exchanged, lambda's ghost columns
+// exchanged after every source.  Workspace of slab k: nbuf states, one adjoint field and,
+// with the rule, sigma_1 and nu (float), each 256-byte aligned.
+static size_t slab_state_bytes(const ns_ctx* c) { return (c->field * sizeof(double) + 255) & ~(size_t)255; }
+static size_t slab_scalar_bytes(const ns_ctx* c) {
+  return ((size_t)c->g.cells * c->g.batch * sizeof(float) + 255) & ~(size_t)255;
+}
+
+int ns_slab_run_bytes(ns_slab_group* G, const ns_run_opts* o, size_t* bytes) {
+  if (!G || !o || !bytes) return NS_ERR_ARG;
+  int nact = 0, slots = 0;
+  long long adv = 0;
+  int r = ns_plan(o->nsteps, o->schedule, o->param, nullptr, 0, &nact, &slots, &adv);
+  if (r) return r;
+  for (size_t k = 0; k < G->c.size(); ++k) {
+    const ns_ctx* c = G->c[k];
+    bytes[k] = (size_t)(slots + 3) * slab_state_bytes(c) + (o->lambda > 0.0 ? 2 * slab_scalar_bytes(c) : 0);
+  }
+  return NS_OK;
+}
+
+int ns_slab_adjoint_run(ns_slab_group* G, int own, const double* const* w0, const double* const* s,
+                        const ns_run_opts* o, void* const* work, const size_t* work_bytes, double* Jbar,
+                        double* const* lam0) {
+  if (!G || !w0 || !o || !work || !work_bytes || !Jbar || !lam0) return NS_ERR_ARG;
+  const int n = (int)G->c.size();
+  if (own < 0 || own >= n) return NS_ERR_ARG;
+  if (o->schedule != NS_CKPT_ALL && o->schedule != NS_CKPT_STRIDE && o->schedule != NS_CKPT_REVOLVE)
+    return NS_ERR_ARG;
+  if (o->mlp || o->record_energy || o->record_sigma || !(o->lambda >= 0.0)) return NS_ERR_ARG;
+  for (int k = 0; k < n; ++k)
+    if (!w0[k] || !work[k] || !lam0[k] || lam0[k] == w0[k] || ((uintptr_t)work[k] & 255) != 0) return NS_ERR_ARG;
+  int nact = 0, slots = 0;
+  long long adv = 0;
+  int r = ns_plan(o->nsteps, o->schedule, o->param, nullptr, 0, &nact, &slots, &adv);
+  if (r) return r;
+  std::vector<ns_action> acts(nact);
+  if ((r = ns_plan(o->nsteps, o->schedule, o->param, acts.data(), nact, &nact, &slots, &adv))) return r;
+  std::vector<size_t> need(n);
+  if ((r = ns_slab_run_bytes(G, o, need.data()))) return r;
+  for (int k = 0; k < n; ++k)
+    if (work_bytes[k] < need[k]) return NS_ERR_BUDGET;
+  // per slab: nbuf state buffers, the second adjoint field, sigma_1 and nu
+  const int nbuf = slots + 2;
+  std::vector<std::vector<double*>> buf(n, std::vector<double*>(nbuf));
+  std::vector<double*> lamB(n);
+  std::vector<float*> sig(n, nullptr), nu(n, nullptr);
+  for (int k = 0; k < n; ++k) {
+    char* q = (char*)work[k];
+    const size_t st = slab_state_bytes(G->c[k]);
+    for (int i = 0; i < nbuf; ++i) buf[k][i] = (double*)(q + (size_t)i * st);
+    lamB[k] = (double*)(q + (size_t)nbuf * st);
+    if (o->lambda > 0.0) {
+      sig[k] = (float*)(q + (size_t)(nbuf + 1) * st);
+      nu[k] = (float*)((char*)sig[k] + slab_scalar_bytes(G->c[k]));
+    }
+  }
+  std::vector<int> slot_buf(std::max(slots, 1), -1);
+  std::vector<char> owned(nbuf, 0);
+  int cur = -1;   // -1: the caller's w0
+  auto states = [&](int i) {
+    std::vector<const double*> v(n);
+    for (int k = 0; k < n; ++k) v[k] = i < 0 ? w0[k] : buf[k][i];
+    return v;
+  };
+  auto pick_free = [&]() -> int {
+    for (int i = 0; i < nbuf; ++i)
+      if (!owned[i] && i != cur) return i;
+    return -1;
+  };
+  // the adjoint fields alternate between lam0 and the workspace field, ending in lam0
+  const int N = o->nsteps;
+  std::vector<double*> lc(n), ln(n);
+  for (int k = 0; k < n; ++k) {
+    lc[k] = N % 2 == 0 ? lam0[k] : lamB[k];
+    ln[k] = N % 2 == 0 ? lamB[k] : lam0[k];
+  }
+  ns_ctx* co = G->c[own];
+  if (cudaMemsetAsync(Jbar, 0, (size_t)co->g.batch * sizeof(double), co->st) != cudaSuccess) return NS_ERR_CUDA;
+  const double wN = 1.0 / N;
+  for (const ns_action& A : acts) {
+    switch (A.op) {
+      case NS_OP_ADVANCE:
+        for (int m = A.a; m < A.b; ++m) {
+          const int out = pick_free();
+          if (out < 0) return NS_ERR_BUDGET;
+          std::vector<const double*> in = states(cur);
+          std::vector<double*> wo(n);
+          for (int k = 0; k < n; ++k) wo[k] = buf[k][out];
+          if ((r = ns_slab_primal_step(G, in.data(), s, wo.data()))) return r;
+          cur = out;
+        }
+        break;
+      case NS_OP_STORE:
+        if (cur < 0) return NS_ERR_ARG;
+        slot_buf[A.b] = cur;
+        owned[cur] = 1;
+        break;
+      case NS_OP_LOAD:
+        cur = A.b < 0 ? -1 : slot_buf[A.b];
+        break;
+      case NS_OP_FREE:
+        owned[slot_buf[A.b]] = 0;
+        slot_buf[A.b] = -1;
+        break;
+      case NS_OP_SOURCE: {
+        for (int k = 0; k < n; ++k)
+          if (cudaMemsetAsync(lc[k], 0, G->c[k]->field * sizeof(double), G->c[k]->st) != cudaSuccess)
+            return NS_ERR_CUDA;
+        if ((r = ns_objective(co, states(cur)[own], wN, Jbar, lc[own]))) return r;
+        if ((r = slab_exchange(G, (void* const*)lc.data(), (int)sizeof(double), 5))) return r;
+        break;
+      }
+      case NS_OP_ADJOINT: {
+        std::vector<const double*> w = states(cur);
+        if (o->lambda > 0.0) {
+          for (int k = 0; k < n; ++k)
+            if ((r = ns_growth_sigma1(G->c[k], w[k], sig[k], nullptr)) ||
+                (r = ns_add_adjoint_viscosity(G->c[k], sig[k], o->lambda, o->tau, nu[k])))
+              return r;
+          if ((r = slab_exchange(G, (void* const*)nu.data(), (int)sizeof(float), 1))) return r;
+        }
+        std::vector<const double*> lin(lc.begin(), lc.end());
+        std::vector<const float*> nup(nu.begin(), nu.end());
+        if ((r = ns_slab_adjoint_step(G, w.data(), s, lin.data(), o->lambda > 0.0 ? nup.data() : nullptr,
+                                      ln.data())))
+          return r;
+        std::swap(lc, ln);
+        if (A.a >= 1) {
+          if ((r = ns_objective(co, w[own], wN, Jbar, lc[own]))) return r;
+          if ((r = slab_exchange(G, (void* const*)lc.data(), (int)sizeof(double), 5))) return r;
+        }
+        break;
+      }
+      default:
+        return NS_ERR_ARG;
+    }
+  }
+  return NS_OK;
+}
+
 }  // extern "C"

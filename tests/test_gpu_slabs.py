@@ -172,6 +172,47 @@ def test_one_slab_with_a_host_exchange_hook():
     assert len(calls) == 4 * N + 7 * N + N
 
 
+@pytest.mark.parametrize("prec,lam_tilde", [(0, 0.0), (1, 0.5)])
+@pytest.mark.parametrize("sched", [(0, 0), (1, 2), (2, 2)])
+def test_slab_checkpointed_sweep(prec, lam_tilde, sched):
+    """ns_slab_adjoint_run (store-all, stride and revolve plans executed on every slab,
+    states kept per slab) gives the bits of the same slab calls made step by step, and so
+    the unsplit box's J-bar and dJ-bar/dw0 in every interior column."""
+    api = _api()
+    w0 = synth.isentropic_vortex(NX, NY, NZ, noise=1e-3, seed=10)
+    P = params_for(w0, mu=1e-3, dt=3e-3)
+    cuts = [(0, 13), (13, 32)]
+    lam_coef = lam_tilde * P.dx[0] ** 2
+    Ss = _slab_solvers(api, P, cuts, prec, P.plane_i)
+    G = api.SlabGroup(Ss)
+    own = _owner(cuts, P.plane_i)
+    wk0 = [dev(w) for w in SL.split(w0, cuts)]
+    _, Jref, lamref = _sweep_slabs(api, G, Ss, SL.split(w0, cuts), own, lam_coef)
+    schedule, param = sched
+    opts = Ss[0].run_opts(N, schedule, param, lam_coef)
+    work = [torch.empty(b, dtype=torch.uint8, device="cuda") for b in G.run_bytes(opts)]
+    J = torch.empty(1, dtype=torch.float64, device="cuda")
+    lam0 = [torch.empty_like(w) for w in wk0]
+    G.adjoint_run(own, wk0, opts, work, J, lam0)
+    torch.cuda.synchronize()
+    assert all(S.last_error() == 0 for S in Ss)
+    assert torch.equal(J, Jref)
+    for a, b in zip(lam0, lamref):
+        assert torch.equal(a, b)
+    # the unsplit box
+    S = make_solver(api, w0, P, prec)
+    _, Jf, lamf = _sweep_full(api, S, w0, lam_coef)
+    assert torch.equal(J, Jf)
+    assert torch.equal(SL.join(lam0), lamf)
+    # the host tier and a short workspace are refused
+    with pytest.raises(api.NsError):
+        G.adjoint_run(own, wk0, Ss[0].run_opts(N, api.NS_CKPT_STRIDE_HOST, 2), work, J, lam0)
+    short = [w[: w.numel() - 256] for w in work]
+    with pytest.raises(api.NsError) as e:
+        G.adjoint_run(own, wk0, opts, short, J, lam0)
+    assert e.value.code == api.NS_ERR_BUDGET
+
+
 def test_slab_group_arguments():
     api = _api()
     w0 = synth.isentropic_vortex(NX, NY, NZ, noise=0.0)
