@@ -249,12 +249,21 @@ int ns_max_wave_speed(ns_ctx* ctx, const double* w, double* out);
  *                   is written only by the library while the sweep holds it, and is
  *                   removed when the sweep is released.  Use it for horizons whose
  *                   snapshots fit neither device nor host memory.
+ *   NS_CKPT_REVOLVE_HOST, NS_CKPT_REVOLVE_DISK  the binomial plan of NS_CKPT_REVOLVE with
+ *                   its param checkpoint slots in host memory (ns_run_opts.host_arena,
+ *                   ns_run_host_bytes) or in a file (ns_run_opts.disk_path): every store
+ *                   and load of a checkpoint becomes a copy out or back, and the device
+ *                   holds only the two working states.  The same bits as NS_CKPT_REVOLVE;
+ *                   the slot count, and with it the recomputation, is then bounded by host
+ *                   memory or disk instead of HBM.
  * ---------------------------------------------------------------------------- */
 #define NS_CKPT_ALL 0
 #define NS_CKPT_STRIDE 1
 #define NS_CKPT_REVOLVE 2
 #define NS_CKPT_STRIDE_HOST 3
 #define NS_CKPT_STRIDE_DISK 4
+#define NS_CKPT_REVOLVE_HOST 5
+#define NS_CKPT_REVOLVE_DISK 6
 
 #define NS_OP_ADVANCE 1 /* advance the current state from step a to step b */
 #define NS_OP_STORE 2   /* keep the current state (step a) in slot b */
@@ -286,7 +295,7 @@ typedef struct {
   int nsteps;        /* primal steps N; Jbar = (1/N) sum_{n=1..N} J(w^n) */
   int schedule;      /* NS_CKPT_* */
   int param;         /* stride (NS_CKPT_STRIDE, NS_CKPT_STRIDE_HOST, NS_CKPT_STRIDE_DISK) or
-                        state slots (NS_CKPT_REVOLVE) */
+                        state slots (NS_CKPT_REVOLVE, NS_CKPT_REVOLVE_HOST, NS_CKPT_REVOLVE_DISK) */
   double lambda;     /* added adjoint viscosity nu = lambda sigma_1 [sigma_1 > tau]; 0 = none */
   double tau;
   int record_energy; /* write E_vhat(w^n, lam^n), n = 0..N, to energy[n][batch] */
@@ -295,7 +304,7 @@ typedef struct {
   const void* mlp;   /* learned closure (device network blob, see ns_mlp_*), or NULL: when set,
                         nu = lambda dx^2 sigma_1 softplus(MLP(f)) replaces the sigma_1 rule
                         (lambda is then the global factor kappa) */
-  void* host_arena;  /* NS_CKPT_STRIDE_HOST: caller-owned host memory of at least
+  void* host_arena;  /* NS_CKPT_STRIDE_HOST, NS_CKPT_REVOLVE_HOST: caller-owned host memory of at least
                         ns_run_host_bytes bytes for the snapshots (page-locked, e.g.
                         cudaHostAlloc, for the copies to run asynchronously; pageable
                         memory works but each copy then blocks the host); else ignored.
@@ -309,7 +318,7 @@ typedef struct {
                         moved word changes it except with probability 2^-64, and its
                         parallel sum is exact in any order.  Costs one read of the state
                         per store and per load. */
-  const char* disk_path; /* NS_CKPT_STRIDE_DISK: path of the snapshot file (NS_ERR_ARG if
+  const char* disk_path; /* NS_CKPT_STRIDE_DISK, NS_CKPT_REVOLVE_DISK: path of the snapshot file (NS_ERR_ARG if
                         NULL); else ignored.  The string is copied by the forward pass. */
 } ns_run_opts;
 
@@ -317,8 +326,9 @@ typedef struct {
  * two working states, one adjoint field, sigma_1 and nu fields, scalars). */
 size_t ns_run_arena_bytes(const ns_ctx* ctx, const ns_run_opts* o);
 
-/* Host bytes of the snapshot arena of an NS_CKPT_STRIDE_HOST sweep (one FP64 state per
- * snapshot held at once); 0 for the other schedules or a NULL argument. */
+/* Host bytes of the snapshot arena of an NS_CKPT_STRIDE_HOST or NS_CKPT_REVOLVE_HOST sweep
+ * (one FP64 state per snapshot held at once); 0 for the other schedules or a NULL
+ * argument. */
 size_t ns_run_host_bytes(const ns_ctx* ctx, const ns_run_opts* o);
 
 /* Whole forward + checkpointed backward sweep from w^0 with the time-constant source s

@@ -60,6 +60,8 @@ NS_CKPT_STRIDE = 1
 NS_CKPT_REVOLVE = 2
 NS_CKPT_STRIDE_HOST = 3
 NS_CKPT_STRIDE_DISK = 4
+NS_CKPT_REVOLVE_HOST = 5
+NS_CKPT_REVOLVE_DISK = 6
 NS_OP_ADVANCE, NS_OP_STORE, NS_OP_LOAD, NS_OP_ADJOINT, NS_OP_FREE, NS_OP_SOURCE = 1, 2, 3, 4, 5, 6
 NS_OP_STORE_HOST, NS_OP_LOAD_HOST, NS_OP_FREE_HOST = 7, 8, 9
 
@@ -456,7 +458,8 @@ class Solver:
         return int(self.lib.ns_run_arena_bytes(self._ctx, ctypes.byref(opts)))
 
     def host_bytes(self, opts) -> int:
-        """Host bytes of an NS_CKPT_STRIDE_HOST sweep's snapshot arena (0 otherwise)."""
+        """Host bytes of an NS_CKPT_STRIDE_HOST or NS_CKPT_REVOLVE_HOST sweep's snapshot
+        arena (0 otherwise)."""
         return int(self.lib.ns_run_host_bytes(self._ctx, ctypes.byref(opts)))
 
     def adjoint_run(self, w0, opts, arena, Jbar, lam0, s=None, sbar=None, energy=None,

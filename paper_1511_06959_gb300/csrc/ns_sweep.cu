@@ -270,6 +270,24 @@ int make_plan(int N, int schedule, int param, Planner& P) {
       if (param < 1) return NS_ERR_ARG;
       P.plan_stride_host(N, param);
       break;
+    case NS_CKPT_REVOLVE_HOST:
+    case NS_CKPT_REVOLVE_DISK: {
+      // the revolve plan with every checkpoint slot a host (file) slot: the device keeps
+      // only the working states
+      if (param < 1) return NS_ERR_ARG;
+      Planner D;
+      D.plan_revolve(N, param);
+      for (ns_action a : D.acts) {
+        if (a.op == NS_OP_STORE) a.op = NS_OP_STORE_HOST;
+        else if (a.op == NS_OP_LOAD && a.b >= 0) a.op = NS_OP_LOAD_HOST;
+        else if (a.op == NS_OP_FREE) a.op = NS_OP_FREE_HOST;
+        P.acts.push_back(a);
+      }
+      P.adv = D.adv;
+      P.maxhost = D.maxlive;
+      P.maxlive = 0;
+      break;
+    }
     default: return NS_ERR_ARG;
   }
   return NS_OK;
@@ -359,7 +377,7 @@ size_t ns_run_arena_bytes(const ns_ctx* c, const ns_run_opts* o) {
 }
 
 size_t ns_run_host_bytes(const ns_ctx* c, const ns_run_opts* o) {
-  if (!c || !o || o->schedule != NS_CKPT_STRIDE_HOST) return 0;
+  if (!c || !o || (o->schedule != NS_CKPT_STRIDE_HOST && o->schedule != NS_CKPT_REVOLVE_HOST)) return 0;
   Planner P;
   if (make_plan(o->nsteps, o->schedule, o->param, P)) return 0;
   return (size_t)P.maxhost * align256(c->field * sizeof(double));
@@ -685,12 +703,12 @@ static int forward_run_impl(ns_ctx* c, const double* w0, const double* s, const 
     delete S;
     return NS_ERR_BUDGET;
   }
-  if (o->schedule == NS_CKPT_STRIDE_HOST && S->P.maxhost > 0 &&
+  if ((o->schedule == NS_CKPT_STRIDE_HOST || o->schedule == NS_CKPT_REVOLVE_HOST) && S->P.maxhost > 0 &&
       (!o->host_arena || o->host_bytes < (size_t)S->P.maxhost * S->L.state)) {
     delete S;
     return NS_ERR_BUDGET;
   }
-  if (o->schedule == NS_CKPT_STRIDE_DISK) {
+  if (o->schedule == NS_CKPT_STRIDE_DISK || o->schedule == NS_CKPT_REVOLVE_DISK) {
     if (!o->disk_path || !o->disk_path[0]) {
       delete S;
       return NS_ERR_ARG;

@@ -150,6 +150,28 @@ def test_disk_tier_plan_is_the_host_tier_plan(N, k):
         api.plan(N, api.NS_CKPT_STRIDE_DISK, 0)
 
 
+@pytest.mark.parametrize("N,S", [(1, 1), (13, 3), (201, 5), (1000, 10)])
+def test_revolve_host_and_disk_tiers_plan_the_revolve_steps_in_host_slots(N, S):
+    """NS_CKPT_REVOLVE_HOST / _DISK run the binomial plan with every checkpoint slot a host
+    (file) slot: the same actions with STORE, LOAD (but the caller's w0) and FREE turned
+    into their host forms, no device slot, the revolve plan's slot count as the host
+    peak, and the plan's invariants under the symbolic run."""
+    api = _api()
+    ref, ref_slots, ref_adv = api.plan(N, api.NS_CKPT_REVOLVE, S)
+    to_host = {STORE: HSTORE, FREE: HFREE}
+    want = [(to_host.get(op, HLOAD if op == LOAD and b >= 0 else op), a, b) for op, a, b in ref]
+    for sched in (api.NS_CKPT_REVOLVE_HOST, api.NS_CKPT_REVOLVE_DISK):
+        actions, slots_used, advances = api.plan(N, sched, S)
+        assert actions == want and slots_used == 0 and advances == ref_adv
+        hp = []
+        first, adj, peak, adv = simulate(actions, N, slots_used, hp)
+        assert first == list(range(1, N + 1))
+        assert adj == list(range(N - 1, -1, -1))
+        assert adv == advances and hp == [ref_slots]
+    with pytest.raises(api.NsError):
+        api.plan(N, api.NS_CKPT_REVOLVE_HOST, 0)
+
+
 def test_plan_rejects_bad_arguments():
     api = _api()
     with pytest.raises(api.NsError):
@@ -200,7 +222,7 @@ def execute_with_oracle(actions, w0, P, N, s=None):
     return J, lam, sbar
 
 
-@pytest.mark.parametrize("schedule,param", [(0, 0), (1, 4), (2, 2), (2, 3), (3, 4), (3, 3), (3, 1)])
+@pytest.mark.parametrize("schedule,param", [(0, 0), (1, 4), (2, 2), (2, 3), (3, 4), (3, 3), (3, 1), (5, 2), (6, 3)])
 def test_plan_executed_with_oracle_equals_store_all(schedule, param):
     api = _api()
     w0 = synth.isentropic_vortex(8, 6, 1, noise=1e-3, seed=4)

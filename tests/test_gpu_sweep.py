@@ -256,6 +256,43 @@ def test_disk_snapshots_give_the_stride_bits(prec, tmp_path):
     assert not path.exists()
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_revolve_host_and_disk_tiers_give_the_revolve_bits(prec, tmp_path):
+    """NS_CKPT_REVOLVE_HOST / _DISK: the binomial plan with its checkpoints in host memory
+    or a file gives NS_CKPT_REVOLVE's bits (stabilised, with a source, energy and sigma_1
+    series, verified) in two device states."""
+    api = _api()
+    w0 = synth.isentropic_vortex(33, 10, 3, noise=1e-3, seed=5)
+    P = params_for(w0, mu=1e-3, dt=4e-3)
+    s = np.zeros_like(w0)
+    s[1] = 0.05 * synth.forcing_bumps(33, 10, 3, n=4)[0]
+    N, slots = 17, 3
+    lam_coef = 0.5 * P.dx[0] ** 2
+    S = make_solver(api, w0, P, prec)
+    ref = _run(api, S, w0, N, api.NS_CKPT_REVOLVE, slots, s, lam_coef=lam_coef, energy=True, sigma=True)
+    field = ((w0.size * 8 + 255) // 256) * 256
+    probe = S.run_opts(N, api.NS_CKPT_REVOLVE_HOST, slots, lam_coef, 0.0, True, True)
+    assert S.host_bytes(probe) == slots * field
+    host = torch.empty(S.host_bytes(probe), dtype=torch.uint8, pin_memory=True)
+    for sched, kw in ((api.NS_CKPT_REVOLVE_HOST, {"host_arena": host}),
+                      (api.NS_CKPT_REVOLVE_DISK, {"disk_path": str(tmp_path / "rev.bin")})):
+        opts = S.run_opts(N, sched, slots, lam_coef, 0.0, True, True, verify=True, **kw)
+        assert S.arena_bytes(opts) < S.arena_bytes(S.run_opts(N, api.NS_CKPT_REVOLVE, slots, lam_coef, 0.0, True,
+                                                              True, verify=True))
+        arena = torch.empty(S.arena_bytes(opts), dtype=torch.uint8, device="cuda")
+        J = torch.empty(1, dtype=torch.float64, device="cuda")
+        lam0 = torch.empty(w0.shape, dtype=torch.float64, device="cuda")
+        sbar = torch.empty_like(lam0)
+        E = torch.zeros((N + 1, 1), dtype=torch.float64, device="cuda")
+        st = torch.zeros((N, 1, 2), dtype=torch.float64, device="cuda")
+        S.adjoint_run(dev(w0), opts, arena, J, lam0, s=dev(s), sbar=sbar, energy=E, sigma_stats=st)
+        torch.cuda.synchronize()
+        assert S.last_error() == 0
+        for got, want in zip((J, lam0, sbar, E, st), ref):
+            assert torch.equal(got, want)
+    assert not (tmp_path / "rev.bin").exists()
+
+
 def test_disk_snapshot_errors(tmp_path):
     """A path that cannot be created is NS_ERR_IO before any work is enqueued and a
     missing path NS_ERR_ARG; a byte flipped in the snapshot file between the forward and
