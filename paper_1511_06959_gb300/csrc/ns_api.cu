@@ -437,6 +437,15 @@ int ns_create(const ns_params* p, void* stream, ns_ctx** out) {
   if (e == cudaSuccess) e = cudaMalloc(&c->qbar, sizeof(double) * 5 * p->batch);
   if (e == cudaSuccess) e = cudaMalloc(&c->ticket, sizeof(unsigned) * p->batch);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->ticket, 0, sizeof(unsigned) * p->batch, c->st);
+  // the side stream of the sweep's objective sums: partials, (N/D, sc) and the per-face
+  // factors of launch_objective_sum
+  const size_t on = ns::objective_scratch_doubles(c->g) + (size_t)c->g.ny * c->g.nz * c->g.batch * 5;
+  if (e == cudaSuccess) e = cudaMalloc(&c->oscratch, on * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&c->oticket, sizeof(unsigned) * p->batch);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->oticket, 0, sizeof(unsigned) * p->batch, c->st);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->ost, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ofork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ojoin, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->err, 0, sizeof(unsigned), c->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
   if (e != cudaSuccess) {
@@ -459,6 +468,11 @@ void ns_destroy(ns_ctx* c) {
   if (c->err) cudaFree(c->err);
   if (c->qbar) cudaFree(c->qbar);
   if (c->ticket) cudaFree(c->ticket);
+  if (c->oscratch) cudaFree(c->oscratch);
+  if (c->oticket) cudaFree(c->oticket);
+  if (c->ofork) cudaEventDestroy(c->ofork);
+  if (c->ojoin) cudaEventDestroy(c->ojoin);
+  if (c->ost) cudaStreamDestroy(c->ost);
   if (c->train_scratch) cudaFree(c->train_scratch);
   for (cudaEvent_t ev : c->events) cudaEventDestroy(ev);
   free_bounded(c);
@@ -850,12 +864,20 @@ int ns_i_primal(ns_ctx* c, const double* w, const void* w_mirror, const double* 
   return primal_step_t<double>(c, c->cd, w, w, s, wo, nullptr, (double* const*)keep3);
 }
 
-int ns_i_objective_sum(ns_ctx* c, const double* w, double weight, double* J_acc, ns_obj_src* obj) {
+int ns_i_objective_sum_forked(ns_ctx* c, const double* w, double weight, double* J_acc, ns_obj_src* obj) {
   const int nx = c->g.nx, i0 = c->p.plane_i;
   obj->iL = ((i0 - 1) % nx + nx) % nx;
   obj->iR = (i0 % nx + nx) % nx;
-  return cuerr(ns::launch_objective_sum(c->g, c->p.gamma, i0, c->p.pt_in, w, weight, J_acc, c->err, c->scratch,
-                                        c->ticket, c->st, &obj->aface, &obj->ndsc));
+  if (cudaEventRecord(c->ofork, c->st) != cudaSuccess || cudaStreamWaitEvent(c->ost, c->ofork, 0) != cudaSuccess)
+    return NS_ERR_CUDA;
+  if (ns::launch_objective_sum(c->g, c->p.gamma, i0, c->p.pt_in, w, weight, J_acc, c->err, c->oscratch, c->oticket,
+                               c->ost, &obj->aface, &obj->ndsc) != cudaSuccess)
+    return NS_ERR_CUDA;
+  return cudaEventRecord(c->ojoin, c->ost) == cudaSuccess ? NS_OK : NS_ERR_CUDA;
+}
+
+int ns_i_objective_join(ns_ctx* c) {
+  return cudaStreamWaitEvent(c->st, c->ojoin, 0) == cudaSuccess ? NS_OK : NS_ERR_CUDA;
 }
 
 int ns_i_adjoint(ns_ctx* c, const double* w, const void* w_mirror, const void* const* kept3, const double* s,

@@ -40,6 +40,12 @@ struct ns_ctx {
   long long pending_gen = 0;         // generation of the forward sweep awaiting its backward (0: none)
   double* qbar = nullptr;            // box-mean primitive states [batch][5] (closure features)
   unsigned* ticket = nullptr;        // per-box counters of the single-launch objective
+  // the sweep's objective sums on a side stream, concurrent with sigma_1 (their own
+  // scratch and counters; forked from and joined to st with events)
+  cudaStream_t ost = nullptr;
+  cudaEvent_t ofork = nullptr, ojoin = nullptr;
+  double* oscratch = nullptr;
+  unsigned* oticket = nullptr;
   float* train_scratch = nullptr;    // closure training partials, allocated on first use
   size_t train_scratch_n = 0;
   // bounded box (ns_set_boundaries): the padded grid and its workspace
@@ -68,9 +74,12 @@ struct ns_obj_src {
 int ns_i_adjoint(ns_ctx* c, const double* w, const void* w_mirror, const void* const* kept3, const double* s,
                  const double* lam, const void* lam_mirror, const float* nu, double* lo, void* lo_mirror,
                  double* sbar, const double* nud = nullptr, const ns_obj_src* obj = nullptr);
-// J_acc += weight J(w) and the gradient factors of the objective source for ns_i_adjoint
-// (uses the context's reduction scratch until the adjoint step has run)
-int ns_i_objective_sum(ns_ctx* c, const double* w, double weight, double* J_acc, ns_obj_src* obj);
+// J_acc += weight J(w) and the gradient factors of the objective source for ns_i_adjoint,
+// on the side stream ost after the work enqueued on st so far, in the side stream's own
+// scratch and counters (held until the adjoint step has run); ns_i_objective_join makes
+// st wait for it
+int ns_i_objective_sum_forked(ns_ctx* c, const double* w, double weight, double* J_acc, ns_obj_src* obj);
+int ns_i_objective_join(ns_ctx* c);
 // ns_mlp_features from the float mirror of w when given (mixed mode; the same bits)
 int ns_i_mlp_features(ns_ctx* c, const double* w, const void* w_mirror, float* feat);
 // ns_adjoint_energy from the float mirrors of w and lam when both are given (mixed mode)

@@ -634,6 +634,10 @@ int run_actions(ns_ctx* c, ns_sweep_state& S, int stop_op, double*& lam_cur, dou
         }
         const float* nup = nullptr;
         const double* nudp = nullptr;
+        // the objective of w^n (n >= 1): its plane sums on the side stream, concurrent with
+        // sigma_1, its source folded into the last transposed stage of this step
+        ns_obj_src obj{};
+        if (A.a >= 1 && (r = ns_i_objective_sum_forked(c, ptr(S.cur), wN, S.jtmp, &obj))) return r;
         if (need_sigma && S.f64nu) {
           double* stats = S.o.record_sigma && sigma_stats ? sigma_stats + (size_t)A.a * 2 * B : nullptr;
           const bool rule = S.o.lambda > 0.0;
@@ -655,10 +659,7 @@ int run_actions(ns_ctx* c, ns_sweep_state& S, int stop_op, double*& lam_cur, dou
             nup = S.nu;
           }
         }
-        // the objective of w^n (n >= 1): its plane sums first, its source folded into the
-        // last transposed stage of this step
-        ns_obj_src obj{};
-        if (A.a >= 1 && (r = ns_i_objective_sum(c, ptr(S.cur), wN, S.jtmp, &obj))) return r;
+        if (A.a >= 1 && (r = ns_i_objective_join(c))) return r;
         if ((r = ns_i_adjoint(c, ptr(S.cur), mirror, kept ? kept3 : nullptr, S.s, lam_cur,
                               S.lamf_valid ? S.lamf_cur : nullptr, nup, lam_nxt, S.lamf_nxt, sbar, nudp,
                               A.a >= 1 ? &obj : nullptr)))
