@@ -510,7 +510,7 @@ size_t sigma1_march_ctas_bound(const GridDesc& g) {
 }
 
 template <class CT>
-__global__ void __launch_bounds__(sgk::NT, sizeof(CT) == 4 ? 3 : 1) k_sigma1(GridDesc g, Coef<CT> c,
+__global__ void __launch_bounds__(sgk::NT, sizeof(CT) == 4 ? 4 : 1) k_sigma1(GridDesc g, Coef<CT> c,
                                                                           const CT* __restrict__ w,
                                                                           float* __restrict__ sig, double* partial,
                                                                           double* stats, unsigned* ticket,
