@@ -606,9 +606,9 @@ int ns_slab_run_bytes(ns_slab_group* group, const ns_run_opts* o, size_t* bytes)
  * Jbar (device, batch doubles, on own's stream) receives J-bar; lam0[k] (device fields)
  * receives dJ-bar/dw^0 of each slab with current ghost columns.  With o->lambda > 0 the
  * sigma_1 rule's viscosity is formed per slab (float, as ns_slab_adjoint_step takes it)
- * and its ghost columns exchanged.  The learned closure, the energy and sigma_1 series
- * and a source sensitivity are not available here (NS_ERR_ARG).  The results equal the
- * same slab calls made step by step. */
+ * and its ghost columns exchanged.  The learned closure, the energy and sigma_1 series,
+ * snapshot checksums (verify) and a source sensitivity are not available here
+ * (NS_ERR_ARG).  The results equal the same slab calls made step by step. */
 int ns_slab_adjoint_run(ns_slab_group* group, int own, const double* const* w0, const double* const* s,
                         const ns_run_opts* o, void* const* work, const size_t* work_bytes, double* Jbar,
                         double* const* lam0);

@@ -1218,7 +1218,7 @@ int ns_slab_adjoint_run(ns_slab_group* G, int own, const double* const* w0, cons
   if (own < 0 || own >= n) return NS_ERR_ARG;
   if (o->schedule != NS_CKPT_ALL && o->schedule != NS_CKPT_STRIDE && o->schedule != NS_CKPT_REVOLVE)
     return NS_ERR_ARG;
-  if (o->mlp || o->record_energy || o->record_sigma || !(o->lambda >= 0.0)) return NS_ERR_ARG;
+  if (o->mlp || o->record_energy || o->record_sigma || o->verify || !(o->lambda >= 0.0)) return NS_ERR_ARG;
   for (int k = 0; k < n; ++k)
     if (!w0[k] || !work[k] || !lam0[k] || lam0[k] == w0[k] || ((uintptr_t)work[k] & 255) != 0) return NS_ERR_ARG;
   int nact = 0, slots = 0;
