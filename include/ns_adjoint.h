@@ -228,7 +228,9 @@ int ns_max_wave_speed(ns_ctx* ctx, const double* w, double* out);
  * (ns_adjoint_run).  Schedules:
  *   NS_CKPT_ALL     keep every state (no recomputation)
  *   NS_CKPT_STRIDE  keep every param-th state; replay one segment at a time and keep
- *                   all its states during its reversal
+ *                   all its states during its reversal.  The last segment is not
+ *                   replayed: the forward pass keeps its states, so a sweep advances
+ *                   nsteps + ((nsteps - 1) / param) * (param - 1) primal steps
  *   NS_CKPT_REVOLVE binomial checkpointing with param state slots: each step is
  *                   recomputed at most r times, r the least integer with
  *                   C(param + r, param) >= nsteps
@@ -236,7 +238,8 @@ int ns_max_wave_speed(ns_ctx* ctx, const double* w, double* out);
  *                   memory (a caller-owned host arena, ns_run_opts.host_arena): each
  *                   snapshot is copied out once in the forward pass and back once when
  *                   its segment is replayed; only the replayed segment's states live
- *                   in device memory.  The copies run on the context's stream, so a
+ *                   in device memory (and, from the forward pass, the last segment's,
+ *                   which is not replayed).  The copies run on the context's stream, so a
  *                   sweep gives the same bits as NS_CKPT_STRIDE.  On a Grace-hosted GPU
  *                   they cross NVLink-C2C.
  *   NS_CKPT_STRIDE_DISK  the plan of NS_CKPT_STRIDE_HOST with the snapshots in a file

@@ -156,18 +156,23 @@ struct Planner {
     }
   }
 
+  // every k-th state in the forward pass, and every state of the last segment, which the
+  // backward pass then reverses without replaying it
   void plan_stride(int N, int k) {
+    const int alast = ((N - 1) / k) * k;
     for (int n = 0; n < N; ++n) {
-      if (n > 0 && n % k == 0) store(n);
+      if (n > 0 && (n % k == 0 || n > alast)) store(n);
       emit(NS_OP_ADVANCE, n, n + 1);
     }
     emit(NS_OP_SOURCE, N, 0);
-    for (int a = ((N - 1) / k) * k; a >= 0; a -= k) {
+    for (int a = alast; a >= 0; a -= k) {
       const int b = std::min(a + k, N);
-      load(a);
-      for (int j = a + 1; j < b; ++j) {
-        emit(NS_OP_ADVANCE, j - 1, j);
-        store(j);
+      if (a != alast) {
+        load(a);
+        for (int j = a + 1; j < b; ++j) {
+          emit(NS_OP_ADVANCE, j - 1, j);
+          store(j);
+        }
       }
       for (int n = b - 1; n >= a; --n) {
         load(n);
@@ -178,25 +183,33 @@ struct Planner {
   }
 
   // plan_stride with the snapshots in host slots: a segment's snapshot comes back into a
-  // device slot once, and the host slot is released at once
+  // device slot once, and the host slot is released at once.  The last segment's states,
+  // its first one included, stay in device slots from the forward pass.
   void plan_stride_host(int N, int k) {
+    const int alast = ((N - 1) / k) * k;
     for (int n = 0; n < N; ++n) {
-      if (n > 0 && n % k == 0) hstore(n);
+      if (n > 0 && n >= alast) {
+        store(n);
+      } else if (n > 0 && n % k == 0) {
+        hstore(n);
+      }
       emit(NS_OP_ADVANCE, n, n + 1);
     }
     emit(NS_OP_SOURCE, N, 0);
-    for (int a = ((N - 1) / k) * k; a >= 0; a -= k) {
+    for (int a = alast; a >= 0; a -= k) {
       const int b = std::min(a + k, N);
-      if (a == 0) {
-        load(0);
-      } else {
-        hload(a);
-        store(a);
-        hfree(a);
-      }
-      for (int j = a + 1; j < b; ++j) {
-        emit(NS_OP_ADVANCE, j - 1, j);
-        store(j);
+      if (a != alast) {
+        if (a == 0) {
+          load(0);
+        } else {
+          hload(a);
+          store(a);
+          hfree(a);
+        }
+        for (int j = a + 1; j < b; ++j) {
+          emit(NS_OP_ADVANCE, j - 1, j);
+          store(j);
+        }
       }
       for (int n = b - 1; n >= a; --n) {
         load(n);
@@ -474,7 +487,9 @@ int run_actions(ns_ctx* c, ns_sweep_state& S, int stop_op, double*& lam_cur, dou
           const int out = pick_free();
           if (out < 0) return NS_ERR_BUDGET;
           const int K = S.L.nkeep;
-          const bool keep = S.in_backward && K > 0 && !S.bounded;
+          // the stride plans replay every segment but the last, whose states they keep from
+          // the forward pass: its steps keep their stages there
+          const bool keep = K > 0 && !S.bounded && (S.in_backward || n >= ((N - 1) / K) * K);
           void* in_m = S.mixed && !S.bounded ? S.cur_mirror : nullptr;
           void* out_m = nullptr;
           void* keep3[3] = {nullptr, nullptr, nullptr};

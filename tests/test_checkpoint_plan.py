@@ -94,15 +94,21 @@ def test_plan_invariants(N, schedule, param):
         assert hp == [0]
     else:
         # the stride plan's steps, with the snapshots in host slots and only the replayed
-        # segment's states in device slots
+        # segment's states in device slots; the last segment's states, its first included,
+        # stay in device slots from the forward pass
         k = param
-        assert hp == [(N - 1) // k]
+        assert hp == [max((N - 1) // k - 1, 0)]
         assert slots_used <= k
         ref_actions, _, ref_adv = api.plan(N, 1, k)
         assert advances == ref_adv
         assert [x for x in actions if x[0] in (ADV, ADJ, SRC)] == [x for x in ref_actions if x[0] in (ADV, ADJ, SRC)]
     if schedule == 0:
         assert advances == N and slots_used == max(N - 1, 0)
+    if schedule in (1, 3):
+        # every segment but the last is replayed once, from its snapshot; the last one is
+        # reversed from the states the forward pass stored
+        k = param
+        assert advances == N + ((N - 1) // k) * (k - 1)
     if schedule == 1:
         k = param
         assert advances <= 2 * N

@@ -151,7 +151,8 @@ def test_host_snapshots_give_the_stride_bits(prec):
     ref = _run(api, S, w0, N, 1, k, s, lam_coef=lam_coef, energy=True, sigma=True)
     probe = S.run_opts(N, api.NS_CKPT_STRIDE_HOST, k, lam_coef, 0.0, True, True)
     field = ((w0.size * 8 + 255) // 256) * 256
-    assert S.host_bytes(probe) == ((N - 1) // k) * field
+    # the snapshots before the last segment, whose states stay on the device
+    assert S.host_bytes(probe) == ((N - 1) // k - 1) * field
     assert S.host_bytes(S.run_opts(N, api.NS_CKPT_STRIDE, k)) == 0
     assert S.arena_bytes(probe) < S.arena_bytes(S.run_opts(N, api.NS_CKPT_STRIDE, k, lam_coef))
     for pinned in (True, False):
@@ -318,8 +319,9 @@ def test_disk_snapshot_errors(tmp_path):
     S.forward_run(dev(w0), opts, arena, J)
     torch.cuda.synchronize()
     data = bytearray(path.read_bytes())
-    # (N - 1) // k snapshots, each at a 256-byte-aligned slot offset
-    assert len(data) == ((N - 1) // k - 1) * (((w0.size * 8 + 255) // 256) * 256) + w0.size * 8
+    # (N - 1) // k - 1 snapshots (the last segment's first state stays on the device), each
+    # at a 256-byte-aligned slot offset
+    assert len(data) == ((N - 1) // k - 2) * (((w0.size * 8 + 255) // 256) * 256) + w0.size * 8
     data[len(data) // 3 + 1000] ^= 0x10
     path.write_bytes(bytes(data))
     S.backward_run(lam)
