@@ -138,7 +138,8 @@ __device__ __forceinline__ void face_s(const Coef<CT>& c, const CT* QL, const CT
 }
 
 // Primal stress row D at a face from the two cells' primitives and the tangential face
-// gradients of (u1, u2, u3) along T1 = (D+1)%3, T2 = (D+2)%3.
+// gradients of (u1, u2, u3) along T1 = (D+1)%3, T2 = (D+2)%3.  Only gt1[D], gt2[D] (the
+// cross terms) and gt1[T1], gt2[T2] (the divergence) are read.
 template <int D, class CT>
 __device__ __forceinline__ void face_stress(const Coef<CT>& c, const CT* qL, const CT* qR,
                                             const CT* gt1, const CT* gt2, CT sig[3]) {
@@ -287,12 +288,16 @@ __device__ __forceinline__ void xpacket(const CT* sQ, const CT* F0, const Coef<C
   const CT* Q0 = sQ + s0 * 5 * SP;
   const CT* Qm = sQ + sm * 5 * SP;
   const CT* Qp = sQ + sp * 5 * SP;
-  CT gy[3], gz[3];
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    const CT* p0 = Q0 + (1 + k) * SP;
-    diff4_pair(p0[iL + SX], p0[iL - SX], p0[iR + SX], p0[iR - SX], c.i4dx[1], Qp[(1 + k) * SP + iL],
-               Qm[(1 + k) * SP + iL], Qp[(1 + k) * SP + iR], Qm[(1 + k) * SP + iR], c.i4dx[2], gy[k], gz[k]);
+  // the four tangential derivatives the stress row reads: u_x along y and z, u_y along
+  // y, u_z along z
+  CT gy[3] = {CT(0), CT(0), CT(0)}, gz[3] = {CT(0), CT(0), CT(0)};
+  {
+    const CT* u0 = Q0 + SP;
+    diff4_pair(u0[iL + SX], u0[iL - SX], u0[iR + SX], u0[iR - SX], c.i4dx[1], Qp[SP + iL], Qm[SP + iL],
+               Qp[SP + iR], Qm[SP + iR], c.i4dx[2], gy[0], gz[0]);
+    const CT* v0 = Q0 + 2 * SP;
+    diff4_pair(v0[iL + SX], v0[iL - SX], v0[iR + SX], v0[iR - SX], c.i4dx[1], Qp[3 * SP + iL],
+               Qm[3 * SP + iL], Qp[3 * SP + iR], Qm[3 * SP + iR], c.i4dx[2], gy[1], gz[2]);
   }
   const CT sv[3] = {xf(F0, 0, row, fx), xf(F0, 1, row, fx), xf(F0, 2, row, fx)};
   face_packet_s<0>(c, sv, xf(F0, 3, row, fx), Q0, iL, Q0, iR, gy, gz, pk);
@@ -305,12 +310,16 @@ __device__ __forceinline__ void ypacket(const CT* sQ, const CT* F0, const Coef<C
   const CT* Q0 = sQ + s0 * 5 * SP;
   const CT* Qm = sQ + sm * 5 * SP;
   const CT* Qp = sQ + sp * 5 * SP;
-  CT gz[3], gx[3];
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    const CT* p0 = Q0 + (1 + k) * SP;
-    diff4_pair(Qp[(1 + k) * SP + iL], Qm[(1 + k) * SP + iL], Qp[(1 + k) * SP + iR], Qm[(1 + k) * SP + iR],
-               c.i4dx[2], p0[iL + 1], p0[iL - 1], p0[iR + 1], p0[iR - 1], c.i4dx[0], gz[k], gx[k]);
+  // the four tangential derivatives the stress row reads: u_y along z and x, u_z along
+  // z, u_x along x
+  CT gz[3] = {CT(0), CT(0), CT(0)}, gx[3] = {CT(0), CT(0), CT(0)};
+  {
+    const CT* v0 = Q0 + 2 * SP;
+    diff4_pair(Qp[2 * SP + iL], Qm[2 * SP + iL], Qp[2 * SP + iR], Qm[2 * SP + iR], c.i4dx[2], v0[iL + 1],
+               v0[iL - 1], v0[iR + 1], v0[iR - 1], c.i4dx[0], gz[1], gx[1]);
+    const CT* u0 = Q0 + SP;
+    diff4_pair(Qp[3 * SP + iL], Qm[3 * SP + iL], Qp[3 * SP + iR], Qm[3 * SP + iR], c.i4dx[2], u0[iL + 1],
+               u0[iL - 1], u0[iR + 1], u0[iR - 1], c.i4dx[0], gz[2], gx[0]);
   }
   const CT sv[3] = {yf(F0, 0, fy, col), yf(F0, 1, fy, col), yf(F0, 2, fy, col)};
   face_packet_s<1>(c, sv, yf(F0, 3, fy, col), Q0, iL, Q0, iR, gz, gx, pk);
@@ -321,13 +330,20 @@ __device__ __forceinline__ void zpacket(const CT* sQ, const Coef<CT>& c, int sL,
                                         const CT s[3], CT fb4, CT pk[7]) {
   const CT* QL = sQ + sL * 5 * SP;
   const CT* QR = sQ + sR * 5 * SP;
-  CT gx[3], gy[3];
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    const CT* a = QL + (1 + k) * SP;
-    const CT* bq = QR + (1 + k) * SP;
+  // the four tangential derivatives the stress row reads: u_z along x and y, u_x along
+  // x, u_y along y
+  CT gx[3] = {CT(0), CT(0), CT(0)}, gy[3] = {CT(0), CT(0), CT(0)};
+  {
+    const CT* a = QL + 3 * SP;
+    const CT* bq = QR + 3 * SP;
     diff4_pair(a[i + 1], a[i - 1], bq[i + 1], bq[i - 1], c.i4dx[0], a[i + SX], a[i - SX], bq[i + SX],
-               bq[i - SX], c.i4dx[1], gx[k], gy[k]);
+               bq[i - SX], c.i4dx[1], gx[2], gy[2]);
+    const CT* ua = QL + SP;
+    const CT* ub = QR + SP;
+    const CT* va = QL + 2 * SP;
+    const CT* vb = QR + 2 * SP;
+    diff4_pair(ua[i + 1], ua[i - 1], ub[i + 1], ub[i - 1], c.i4dx[0], va[i + SX], va[i - SX], vb[i + SX],
+               vb[i - SX], c.i4dx[1], gx[0], gy[1]);
   }
   face_packet_s<2>(c, s, fb4, QL, i, QR, i, gx, gy, pk);
 }

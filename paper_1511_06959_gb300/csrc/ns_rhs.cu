@@ -111,7 +111,8 @@ __device__ __forceinline__ void plane_store(const PlaneRegs<CT>& r, CT* __restri
 }
 
 // Face flux Phi_D between cells L and R given the tangential face gradients of
-// (u1, u2, u3, e) along T1 = (D+1)%3 and T2 = (D+2)%3.
+// (u1, u2, u3, e) along T1 = (D+1)%3 and T2 = (D+2)%3.  Only gt1[D], gt2[D] (the stress
+// row's cross terms) and gt1[T1], gt2[T2] (the divergence) are read.
 template <int D, bool ROE, class CT>
 __device__ __forceinline__ void face_flux(const Coef<CT>& c, const CT* qL, const CT* qR,
                                           const CT* gt1, const CT* gt2, CT* phi) {
@@ -180,19 +181,22 @@ template <bool ROE, class CT>
 __device__ __forceinline__ void xface(const CT* sQ, const Coef<CT>& c, int sm, int s0, int sp,
                                       int row, int fx, CT* phi) {
   const int iL = row * SX + fx, iR = iL + 1;
-  CT qL[5], qR[5], gy[4], gz[4];
+  CT qL[5], qR[5];
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
     qL[v] = qs(sQ, s0, v)[iL];
     qR[v] = qs(sQ, s0, v)[iR];
   }
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const CT* p0 = qs(sQ, s0, 1 + k);
-    const CT* pm = qs(sQ, sm, 1 + k);
-    const CT* pp = qs(sQ, sp, 1 + k);
-    diff4_pair(p0[iL + SX], p0[iL - SX], p0[iR + SX], p0[iR - SX], c.i4dx[1], pp[iL], pm[iL], pp[iR], pm[iR],
-               c.i4dx[2], gy[k], gz[k]);
+  // the four tangential derivatives the flux reads: u_x along y and z, u_y along y, u_z
+  // along z (face_flux)
+  CT gy[4] = {CT(0), CT(0), CT(0), CT(0)}, gz[4] = {CT(0), CT(0), CT(0), CT(0)};
+  {
+    const CT* p0 = qs(sQ, s0, 1);
+    diff4_pair(p0[iL + SX], p0[iL - SX], p0[iR + SX], p0[iR - SX], c.i4dx[1], qs(sQ, sp, 1)[iL],
+               qs(sQ, sm, 1)[iL], qs(sQ, sp, 1)[iR], qs(sQ, sm, 1)[iR], c.i4dx[2], gy[0], gz[0]);
+    const CT* v0 = qs(sQ, s0, 2);
+    diff4_pair(v0[iL + SX], v0[iL - SX], v0[iR + SX], v0[iR - SX], c.i4dx[1], qs(sQ, sp, 3)[iL],
+               qs(sQ, sm, 3)[iL], qs(sQ, sp, 3)[iR], qs(sQ, sm, 3)[iR], c.i4dx[2], gy[1], gz[2]);
   }
   face_flux<0, ROE>(c, qL, qR, gy, gz, phi);
 }
@@ -202,19 +206,22 @@ template <bool ROE, class CT>
 __device__ __forceinline__ void yface(const CT* sQ, const Coef<CT>& c, int sm, int s0, int sp,
                                       int fy, int col, CT* phi) {
   const int iL = fy * SX + col, iR = iL + SX;
-  CT qL[5], qR[5], gz[4], gx[4];
+  CT qL[5], qR[5];
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
     qL[v] = qs(sQ, s0, v)[iL];
     qR[v] = qs(sQ, s0, v)[iR];
   }
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const CT* p0 = qs(sQ, s0, 1 + k);
-    const CT* pm = qs(sQ, sm, 1 + k);
-    const CT* pp = qs(sQ, sp, 1 + k);
-    diff4_pair(pp[iL], pm[iL], pp[iR], pm[iR], c.i4dx[2], p0[iL + 1], p0[iL - 1], p0[iR + 1], p0[iR - 1],
-               c.i4dx[0], gz[k], gx[k]);
+  // the four tangential derivatives the flux reads: u_y along z and x, u_z along z, u_x
+  // along x
+  CT gz[4] = {CT(0), CT(0), CT(0), CT(0)}, gx[4] = {CT(0), CT(0), CT(0), CT(0)};
+  {
+    const CT* v0 = qs(sQ, s0, 2);
+    diff4_pair(qs(sQ, sp, 2)[iL], qs(sQ, sm, 2)[iL], qs(sQ, sp, 2)[iR], qs(sQ, sm, 2)[iR], c.i4dx[2],
+               v0[iL + 1], v0[iL - 1], v0[iR + 1], v0[iR - 1], c.i4dx[0], gz[1], gx[1]);
+    const CT* u0 = qs(sQ, s0, 1);
+    diff4_pair(qs(sQ, sp, 3)[iL], qs(sQ, sm, 3)[iL], qs(sQ, sp, 3)[iR], qs(sQ, sm, 3)[iR], c.i4dx[2],
+               u0[iL + 1], u0[iL - 1], u0[iR + 1], u0[iR - 1], c.i4dx[0], gz[2], gx[0]);
   }
   face_flux<1, ROE>(c, qL, qR, gz, gx, phi);
 }
@@ -223,18 +230,26 @@ __device__ __forceinline__ void yface(const CT* sQ, const Coef<CT>& c, int sm, i
 template <bool ROE, class CT>
 __device__ __forceinline__ void zface(const CT* sQ, const Coef<CT>& c, int sL, int sR, int i,
                                       CT* phi) {
-  CT qL[5], qR[5], gx[4], gy[4];
+  CT qL[5], qR[5];
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
     qL[v] = qs(sQ, sL, v)[i];
     qR[v] = qs(sQ, sR, v)[i];
   }
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const CT* a = qs(sQ, sL, 1 + k);
-    const CT* bq = qs(sQ, sR, 1 + k);
+  // the four tangential derivatives the flux reads: u_z along x and y, u_x along x, u_y
+  // along y
+  CT gx[4] = {CT(0), CT(0), CT(0), CT(0)}, gy[4] = {CT(0), CT(0), CT(0), CT(0)};
+  {
+    const CT* a = qs(sQ, sL, 3);
+    const CT* bq = qs(sQ, sR, 3);
     diff4_pair(a[i + 1], a[i - 1], bq[i + 1], bq[i - 1], c.i4dx[0], a[i + SX], a[i - SX], bq[i + SX],
-               bq[i - SX], c.i4dx[1], gx[k], gy[k]);
+               bq[i - SX], c.i4dx[1], gx[2], gy[2]);
+    const CT* ua = qs(sQ, sL, 1);
+    const CT* ub = qs(sQ, sR, 1);
+    const CT* va = qs(sQ, sL, 2);
+    const CT* vb = qs(sQ, sR, 2);
+    diff4_pair(ua[i + 1], ua[i - 1], ub[i + 1], ub[i - 1], c.i4dx[0], va[i + SX], va[i - SX], vb[i + SX],
+               vb[i - SX], c.i4dx[1], gx[0], gy[1]);
   }
   face_flux<2, ROE>(c, qL, qR, gx, gy, phi);
 }
