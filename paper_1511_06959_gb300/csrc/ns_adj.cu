@@ -129,8 +129,20 @@ template <int D, class CT>
 __device__ __forceinline__ void face_s(const Coef<CT>& c, const CT* QL, const CT* AL, int iL,
                                        const CT* QR, const CT* AR, int iR, CT s[3], CT& fb4) {
   fb4 = (AL[4 * SP + iL] - AR[4 * SP + iR]) * c.idx[D];
+  int j0 = 0;
+  if constexpr (std::is_same<CT, float>::value) {
+    // components 1 and 2 side by side in paired FP32 instructions
+    const float2 fb = __fmul2_rn(sub2(f2(AL[SP + iL], AL[2 * SP + iL]), f2(AR[SP + iR], AR[2 * SP + iR])),
+                                 f2(c.idx[D], c.idx[D]));
+    const float2 uf = __fmul2_rn(f2(0.5f, 0.5f),
+                                 __fadd2_rn(f2(QL[SP + iL], QL[2 * SP + iL]), f2(QR[SP + iR], QR[2 * SP + iR])));
+    const float2 sv = __ffma2_rn(f2(fb4, fb4), uf, fb);
+    s[0] = sv.x;
+    s[1] = sv.y;
+    j0 = 2;
+  }
 #pragma unroll
-  for (int j = 0; j < 3; ++j) {
+  for (int j = j0; j < 3; ++j) {
     const CT fb = (AL[(1 + j) * SP + iL] - AR[(1 + j) * SP + iR]) * c.idx[D];
     const CT uf = CT(0.5) * (QL[(1 + j) * SP + iL] + QR[(1 + j) * SP + iR]);
     s[j] = fb + fb4 * uf;
@@ -655,8 +667,32 @@ __global__ void __launch_bounds__(NT, AdjMinBlocks<CT, ROE>::value) k_adj_stage(
         const CT nc = N0[ic], nxm = N0[ic - 1], nxp = N0[ic + 1], nym = N0[ic - SX], nyp = N0[ic + SX],
                  nzp = sN[sp * SP + ic];
         const CT ix2 = c.idx[0] * c.idx[0], iy2 = c.idx[1] * c.idx[1], iz2 = c.idx[2] * c.idx[2];
+        int v0 = 0;
+        if constexpr (std::is_same<CT, float>::value) {
+          // components (0, 1) and (2, 3) side by side in paired FP32 instructions
+          const float2 fxp = f2(h * (nc + nxp), h * (nc + nxp)), fxm = f2(-h * (nc + nxm), -h * (nc + nxm));
+          const float2 fyp = f2(h * (nc + nyp), h * (nc + nyp)), fym = f2(-h * (nc + nym), -h * (nc + nym));
+          const float2 fzp = f2(h * (nc + nzp), h * (nc + nzp)), fzm = f2(-h * (nc + nzm), -h * (nc + nzm));
 #pragma unroll
-        for (int v = 0; v < 5; ++v) {
+          for (int v = 0; v < 4; v += 2) {
+            const float* Av = A0 + v * SP;
+            const float* Aw = Av + SP;
+            const float2 ac = f2(Av[ic], Aw[ic]);
+            const float2 tx = __ffma2_rn(fxp, sub2(f2(Av[ic + 1], Aw[ic + 1]), ac),
+                                         __fmul2_rn(fxm, sub2(ac, f2(Av[ic - 1], Aw[ic - 1]))));
+            const float2 ty = __ffma2_rn(fyp, sub2(f2(Av[ic + SX], Aw[ic + SX]), ac),
+                                         __fmul2_rn(fym, sub2(ac, f2(Av[ic - SX], Aw[ic - SX]))));
+            const float2 tz = __ffma2_rn(fzp, sub2(f2(Ap[v * SP + ic], Ap[(v + 1) * SP + ic]), ac),
+                                         __fmul2_rn(fzm, sub2(ac, f2(am[v], am[v + 1]))));
+            const float2 L = __ffma2_rn(tz, f2(iz2, iz2), __ffma2_rn(ty, f2(iy2, iy2), __fmul2_rn(tx, f2(ix2, ix2))));
+            const float2 gv = __ffma2_rn(f2(float(a.nus[v == 0 ? 0 : 1]), float(a.nus[1])), L, f2(gout[v], gout[v + 1]));
+            gout[v] = gv.x;
+            gout[v + 1] = gv.y;
+          }
+          v0 = 4;
+        }
+#pragma unroll
+        for (int v = v0; v < 5; ++v) {
           const CT* Av = A0 + v * SP;
           const CT ac = Av[ic];
           CT L = (h * (nc + nxp) * (Av[ic + 1] - ac) - h * (nc + nxm) * (ac - Av[ic - 1])) * ix2 +
