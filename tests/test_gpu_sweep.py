@@ -38,7 +38,9 @@ def test_schedules_agree_bitwise_and_match_oracle(prec):
     s[1] = 0.05 * synth.forcing_bumps(33, 10, 3, n=4)[0]
     N = 13
     S = make_solver(api, w0, P, prec)
-    res = [_run(api, S, w0, N, sch, prm, s) for sch, prm in [(0, 0), (1, 4), (2, 3), (2, 1)]]
+    # stride 4, 5 and 20: a last segment of 1, 3 and all 13 steps, reversed from the
+    # states and stage states the forward pass keeps
+    res = [_run(api, S, w0, N, sch, prm, s) for sch, prm in [(0, 0), (1, 4), (1, 5), (1, 20), (2, 3), (2, 1)]]
     for J, lam, sb, _, _ in res[1:]:
         assert torch.equal(J, res[0][0])
         assert torch.equal(lam, res[0][1])
