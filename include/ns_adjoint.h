@@ -365,6 +365,35 @@ int ns_backward_run(ns_ctx* ctx, double* lam0, double* sbar, double* energy, dou
 long long ns_sweep_generation(const ns_ctx* ctx);
 
 /* ------------------------------------------------------------------------------
+ * A whole sweep as one CUDA graph.  ns_adjoint_run_capture records the launches,
+ * copies and stream forks of one ns_adjoint_run call with these arguments into a CUDA
+ * graph instead of running them; ns_graph_launch replays them on the context's stream
+ * as one graph launch.  A replay does all of the sweep's work again (forward pass,
+ * replays, adjoint steps, diagnostics): it reads w0 and s as they are at replay time and
+ * overwrites Jbar, lam0, sbar, energy and sigma_stats, and gives the same bits as
+ * ns_adjoint_run on the same inputs.  It keeps the pointers, the ns_run_opts values and
+ * the context's settings (dt, viscosity split and cap, boundaries, learned closure
+ * parameters' location) of the capture: the caller captures again after changing any of
+ * them.  The arena and the output arrays belong to the graph while it is replayed.
+ * Capture runs on a stream the library owns, so it works whatever stream the context
+ * uses.  NS_ERR_ARG for the host and disk tiers (their copies go through the host) and
+ * for a NULL out; the errors of ns_adjoint_run otherwise; NS_ERR_CUDA if the CUDA
+ * runtime refuses the capture.  The paper has no counterpart: this is how the sweep's
+ * thousands of short launches are issued from one host call. */
+typedef struct ns_graph ns_graph;
+int ns_adjoint_run_capture(ns_ctx* ctx, const double* w0, const double* s, const ns_run_opts* o,
+                           void* arena, size_t arena_bytes, double* Jbar, double* lam0, double* sbar,
+                           double* energy, double* sigma_stats, ns_graph** out);
+/* One replay on the context's current stream (ns_set_stream), ordered after the work
+ * already on it.  NS_ERR_ARG for a NULL graph. */
+int ns_graph_launch(ns_graph* graph);
+/* Kernel launches of one replay (this library's kernels; ns_launch_count does not count
+ * replays); -1 for a NULL graph. */
+long long ns_graph_kernels(const ns_graph* graph);
+/* Releases the graph (NULL is ignored).  The caller synchronises its replays first. */
+void ns_graph_destroy(ns_graph* graph);
+
+/* ------------------------------------------------------------------------------
  * Choice of the viscosity scaling factor lambda for a given problem.  The paper's
  * conclusion names this as the method's first open question; its results section
  * tabulates adjoint against finite-difference sensitivity over lambda: too little

@@ -8,6 +8,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import weakref
 
 import torch
 
@@ -51,6 +52,7 @@ EXPORTED = [
     "ns_sweep_generation", "ns_growth_sigma1_f64", "ns_add_adjoint_viscosity_f64", "ns_adjoint_step_f64",
     "ns_slab_group_create", "ns_slab_group_destroy", "ns_slab_set_exchange", "ns_slab_exchange",
     "ns_slab_primal_step", "ns_slab_adjoint_step", "ns_slab_run_bytes", "ns_slab_adjoint_run", "ns_set_boundaries",
+    "ns_adjoint_run_capture", "ns_graph_launch", "ns_graph_kernels", "ns_graph_destroy",
 ]
 
 NS_MLP_PARAMS = 5185
@@ -174,6 +176,11 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "ns_run_arena_bytes": ([P, ctypes.POINTER(NsRunOpts)], S),
         "ns_run_host_bytes": ([P, ctypes.POINTER(NsRunOpts)], S),
         "ns_adjoint_run": ([P, P, P, ctypes.POINTER(NsRunOpts), P, S, P, P, P, P, P], I),
+        "ns_adjoint_run_capture": ([P, P, P, ctypes.POINTER(NsRunOpts), P, S, P, P, P, P, P,
+                                    ctypes.POINTER(ctypes.c_void_p)], I),
+        "ns_graph_launch": ([P], I),
+        "ns_graph_kernels": ([P], ctypes.c_longlong),
+        "ns_graph_destroy": ([P], None),
         "ns_profile_enable": ([P, I], I),
         "ns_profile_read": ([P, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_longlong)], I),
         "ns_energy_efolds": ([ctypes.POINTER(D), I, I, ctypes.POINTER(D)], I),
@@ -286,6 +293,7 @@ class Solver:
         self.cells = nx * ny * nz
         self.batch = batch
         self._ctx = ctypes.c_void_p()
+        self._graphs = []   # weak references to this context's captured sweeps
         st = stream if stream is not None else torch.cuda.current_stream()
         _check(self.lib.ns_create(ctypes.byref(self.params), ctypes.c_void_p(st.cuda_stream),
                                   ctypes.byref(self._ctx)), "ns_create")
@@ -301,6 +309,11 @@ class Solver:
         return _sized(t, torch.float64, self.batch * per_box, "per-box array")
 
     def close(self):
+        # a captured sweep refers to the context: released first
+        for ref in getattr(self, "_graphs", []):
+            g = ref()
+            if g is not None:
+                g.close()
         if self._ctx:
             self.lib.ns_destroy(self._ctx)
             self._ctx = ctypes.c_void_p()
@@ -472,6 +485,20 @@ class Solver:
                                        self._B(Jbar), self._F(lam0), self._F(sbar), self._B(energy, N + 1),
                                        self._B(sigma_stats, 2 * N)), "ns_adjoint_run")
 
+    def adjoint_run_capture(self, w0, opts, arena, Jbar, lam0, s=None, sbar=None, energy=None,
+                            sigma_stats=None):
+        """adjoint_run recorded as one CUDA graph (nothing runs yet); returns a SweepGraph
+        whose launch() replays the whole sweep on the solver's stream."""
+        N = opts.nsteps
+        g = ctypes.c_void_p()
+        _check(self.lib.ns_adjoint_run_capture(self._ctx, self._F(w0), self._F(s),
+                                               ctypes.byref(opts), _ptr(arena),
+                                               arena.numel() * arena.element_size(), self._B(Jbar),
+                                               self._F(lam0), self._F(sbar), self._B(energy, N + 1),
+                                               self._B(sigma_stats, 2 * N), ctypes.byref(g)),
+               "ns_adjoint_run_capture")
+        return SweepGraph(self, g)
+
     def estimate_work_bytes(self, opts) -> int:
         return int(self.lib.ns_estimate_work_bytes(self._ctx, ctypes.byref(opts)))
 
@@ -574,6 +601,37 @@ def measure_fma_peak(kind: int) -> float:
     out = ctypes.c_double()
     _check(_lib().ns_measure_fma_peak(int(kind), ctypes.byref(out)), "ns_measure_fma_peak")
     return out.value
+
+
+class SweepGraph:
+    """One sweep captured as a CUDA graph (Solver.adjoint_run_capture).  launch() replays
+    the whole sweep on the solver's stream, reading w0 and s as they are then and
+    overwriting the outputs given at capture; kernels is the number of this library's
+    kernel launches in one replay."""
+
+    def __init__(self, solver, handle):
+        self.solver = solver
+        self.lib = solver.lib
+        self._g = handle
+        solver._graphs.append(weakref.ref(self))
+
+    @property
+    def kernels(self) -> int:
+        return int(self.lib.ns_graph_kernels(self._g))
+
+    def launch(self):
+        _check(self.lib.ns_graph_launch(self._g), "ns_graph_launch")
+
+    def close(self):
+        if self._g:
+            self.lib.ns_graph_destroy(self._g)
+            self._g = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def _ptr_array(tensors, dtype, sizes=None):

@@ -835,4 +835,68 @@ int ns_adjoint_run(ns_ctx* c, const double* w0, const double* s, const ns_run_op
 
 long long ns_sweep_generation(const ns_ctx* c) { return c ? c->pending_gen : 0; }
 
+// One ns_adjoint_run recorded as a CUDA graph: the executable graph, the context whose
+// stream replays it, and the kernel launches it holds.
+struct ns_graph {
+  ns_ctx* c = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  long long kernels = 0;
+};
+
+int ns_adjoint_run_capture(ns_ctx* c, const double* w0, const double* s, const ns_run_opts* o, void* arena,
+                           size_t arena_bytes, double* Jbar, double* lam0, double* sbar, double* energy,
+                           double* sigma_stats, ns_graph** out) {
+  if (!out) return NS_ERR_ARG;
+  *out = nullptr;
+  if (!c || !o) return NS_ERR_ARG;
+  // the host and disk tiers copy through host memory (and the disk tier waits on the
+  // stream): not a graph
+  if (o->schedule == NS_CKPT_STRIDE_HOST || o->schedule == NS_CKPT_STRIDE_DISK ||
+      o->schedule == NS_CKPT_REVOLVE_HOST || o->schedule == NS_CKPT_REVOLVE_DISK)
+    return NS_ERR_ARG;
+  // capture on a stream of our own (the legacy default stream cannot be captured); the
+  // context's side stream joins the capture through the sweep's fork and join events
+  cudaStream_t cs = nullptr;
+  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return NS_ERR_CUDA;
+  cudaStream_t st = c->st;
+  c->st = cs;
+  const unsigned long long k0 = ns::g_launches.load(std::memory_order_relaxed);
+  int r = NS_OK;
+  cudaGraph_t graph = nullptr;
+  if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+    r = NS_ERR_CUDA;
+  } else {
+    r = ns_adjoint_run(c, w0, s, o, arena, arena_bytes, Jbar, lam0, sbar, energy, sigma_stats);
+    const cudaError_t e = cudaStreamEndCapture(cs, &graph);
+    if (r == NS_OK && e != cudaSuccess) r = NS_ERR_CUDA;
+  }
+  const long long kernels = (long long)(ns::g_launches.load(std::memory_order_relaxed) - k0);
+  c->st = st;
+  if (r != NS_OK) ns_sweep_release(c);   // a sweep cut short by an error is not reversed later
+  cudaGraphExec_t exec = nullptr;
+  if (r == NS_OK && cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+    exec = nullptr;
+    r = NS_ERR_CUDA;
+  }
+  if (graph) cudaGraphDestroy(graph);
+  cudaStreamDestroy(cs);
+  cudaGetLastError();   // clear the runtime's last error after a refused capture
+  if (r != NS_OK) return r;
+  *out = new ns_graph{c, exec, kernels};
+  return NS_OK;
+}
+
+int ns_graph_launch(ns_graph* gr) {
+  if (!gr) return NS_ERR_ARG;
+  return cudaGraphLaunch(gr->exec, gr->c->st) == cudaSuccess ? NS_OK : NS_ERR_CUDA;
+}
+
+long long ns_graph_kernels(const ns_graph* gr) { return gr ? gr->kernels : -1; }
+
+void ns_graph_destroy(ns_graph* gr) {
+  if (!gr) return;
+  if (gr->exec) cudaGraphExecDestroy(gr->exec);
+  delete gr;
+}
+
 }  // extern "C"
