@@ -325,6 +325,20 @@ def run_ours(args, wl):
     S.profile_enable(False)
     clocks = clk.stop()
     kms, klaunch = S.profile_read()
+    # The same pass with the stride sweep's segments in sequence (ns_set_pipeline off):
+    # the adjoint stage alone on the SMs, where in the pipelined sweep it shares them with
+    # the concurrent replay of the next segment.
+    iso = None
+    if wl.schedule == "stride" and host is None and disk is None and wl.nsteps - 1 >= param >= 2:
+        S.set_pipeline(False)
+        S.profile_enable(True)
+        for i in range(args.steps):
+            flush.fill_(i & 0xFF)
+            direct_step()
+        torch.cuda.synchronize()
+        S.profile_enable(False)
+        S.set_pipeline(True)
+        iso = S.profile_read()
     if S.last_error() != 0:
         raise RuntimeError("device error word set in the timed region")
     Jv = J.cpu().numpy().copy()
@@ -387,7 +401,9 @@ def run_ours(args, wl):
                          "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                          "traffic": adj_traffic(wl, args.precision),
                          "avg_launch_us": 1e3 * kavg, "launches": klaunch,
-                         "kernel_timing": "second K-step pass, CUDA events around each step's adjoint-stage launches",
+                         "kernel_timing": "second K-step pass, CUDA events around each step's adjoint-stage launches"
+                                          " (in a pipelined stride sweep the next segment's replay runs on the"
+                                          " SMs meanwhile)",
                          "bytes_per_launch": bytes_launch,
                          "bytes_rule": f"{ADJ_STEP_BYTES:.0f} B per adjoint cell-step (read w^n and lam^(n+1), "
                                        f"write lam^n, FP64) / {stages} stage launches",
@@ -396,7 +412,14 @@ def run_ours(args, wl):
                          "operand_frac": operand_bytes / (kavg * 1e-3) / 1e9 / hbm,
                          "sweep": {"bytes_per_cell_step": SWEEP_BYTES, "achieved": sweep_gbs,
                                    "frac": sweep_gbs / hbm, "unit": "GB/s"},
-                         "alu": alu_roofline(wl, args.precision, kavg, api)},
+                         "alu": alu_roofline(wl, args.precision, kavg, api),
+                         "isolated": None if iso is None else {
+                             "avg_launch_us": 1e3 * iso[0] / max(iso[1], 1),
+                             "achieved": bytes_launch / (iso[0] / max(iso[1], 1) * 1e-3) / 1e9,
+                             "frac": bytes_launch / (iso[0] / max(iso[1], 1) * 1e-3) / 1e9 / hbm,
+                             "alu": alu_roofline(wl, args.precision, iso[0] / max(iso[1], 1), api),
+                             "kernel_timing": "the same pass with the segments in sequence "
+                                              "(ns_set_pipeline off): no replay shares the SMs"}},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(w0.numel() * 8),
                     "d2h_bytes_per_step": int(lam0.numel() * 8 + J.numel() * 8)},
             "gpu_launches": gl,

@@ -230,7 +230,12 @@ int ns_max_wave_speed(ns_ctx* ctx, const double* w, double* out);
  *   NS_CKPT_STRIDE  keep every param-th state; replay one segment at a time and keep
  *                   all its states during its reversal.  The last segment is not
  *                   replayed: the forward pass keeps its states, so a sweep advances
- *                   nsteps + ((nsteps - 1) / param) * (param - 1) primal steps
+ *                   nsteps + ((nsteps - 1) / param) * (param - 1) primal steps.  With two
+ *                   or more segments (and verify off, on a periodic box) the sweep is
+ *                   pipelined: the replay of the next segment runs on a second stream
+ *                   while the current one is reversed, with a second set of segment
+ *                   states and kept stages in the arena; the bits are those of the
+ *                   sequential order.  ns_set_pipeline turns this off.
  *   NS_CKPT_REVOLVE binomial checkpointing with param state slots: each step is
  *                   recomputed at most r times, r the least integer with
  *                   C(param + r, param) >= nsteps
@@ -363,6 +368,14 @@ int ns_backward_run(ns_ctx* ctx, double* lam0, double* sbar, double* energy, dou
  * forward and compares it before its backward, so that it never reverses another
  * forward's trajectory.  The paper has no counterpart. */
 long long ns_sweep_generation(const ns_ctx* ctx);
+
+/* Pipelined stride sweeps on this context (NS_CKPT_STRIDE above): on = 1 (the default
+ * unless the environment sets NS_PIPELINE=0) or 0.  The pipelined arena holds a second
+ * set of param - 1 segment states and of kept stages (ns_run_arena_bytes follows the
+ * setting); its replays run on a context the library creates on first use with this
+ * context's parameters, which reports into this context's error word.  NS_ERR_ARG for a
+ * NULL context. */
+int ns_set_pipeline(ns_ctx* ctx, int on);
 
 /* ------------------------------------------------------------------------------
  * A whole sweep as one CUDA graph.  ns_adjoint_run_capture records the launches,

@@ -52,7 +52,7 @@ EXPORTED = [
     "ns_sweep_generation", "ns_growth_sigma1_f64", "ns_add_adjoint_viscosity_f64", "ns_adjoint_step_f64",
     "ns_slab_group_create", "ns_slab_group_destroy", "ns_slab_set_exchange", "ns_slab_exchange",
     "ns_slab_primal_step", "ns_slab_adjoint_step", "ns_slab_run_bytes", "ns_slab_adjoint_run", "ns_set_boundaries",
-    "ns_adjoint_run_capture", "ns_graph_launch", "ns_graph_kernels", "ns_graph_destroy",
+    "ns_adjoint_run_capture", "ns_graph_launch", "ns_graph_kernels", "ns_graph_destroy", "ns_set_pipeline",
 ]
 
 NS_MLP_PARAMS = 5185
@@ -179,6 +179,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "ns_adjoint_run_capture": ([P, P, P, ctypes.POINTER(NsRunOpts), P, S, P, P, P, P, P,
                                     ctypes.POINTER(ctypes.c_void_p)], I),
         "ns_graph_launch": ([P], I),
+        "ns_set_pipeline": ([P, I], I),
         "ns_graph_kernels": ([P], ctypes.c_longlong),
         "ns_graph_destroy": ([P], None),
         "ns_profile_enable": ([P, I], I),
@@ -445,6 +446,11 @@ class Solver:
         """Hold the added viscosity at the explicit stability limit instead of flagging it
         (ns_set_viscosity_cap)."""
         _check(self.lib.ns_set_viscosity_cap(self._ctx, int(bool(cap))), "ns_set_viscosity_cap")
+
+    def set_pipeline(self, on: bool):
+        """Pipelined stride sweeps (the next segment replayed on a second stream while the
+        current one is reversed) on or off (ns_set_pipeline); arena_bytes follows."""
+        _check(self.lib.ns_set_pipeline(self._ctx, int(bool(on))), "ns_set_pipeline")
 
     def last_error(self) -> int:
         return int(self.lib.ns_last_error(self._ctx))

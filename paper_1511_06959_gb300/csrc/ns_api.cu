@@ -460,12 +460,18 @@ int ns_create(const ns_params* p, void* stream, ns_ctx** out) {
 
 void ns_destroy(ns_ctx* c) {
   if (!c) return;
+  ns_sweep_release(c);
+  if (c->rctx) ns_destroy(c->rctx);
   for (int i = 0; i < ns_ctx::NSTAGE; ++i)
     if (c->stage[i]) cudaFree(c->stage[i]);
   for (int i = 0; i < 6; ++i)
     if (c->tan[i]) cudaFree(c->tan[i]);
   if (c->scratch) cudaFree(c->scratch);
-  if (c->err) cudaFree(c->err);
+  if (c->own_err) {
+    cudaFree(c->own_err);   // a replay context: err is its owner's
+  } else if (c->err) {
+    cudaFree(c->err);
+  }
   if (c->qbar) cudaFree(c->qbar);
   if (c->ticket) cudaFree(c->ticket);
   if (c->oscratch) cudaFree(c->oscratch);
@@ -476,7 +482,7 @@ void ns_destroy(ns_ctx* c) {
   if (c->train_scratch) cudaFree(c->train_scratch);
   for (cudaEvent_t ev : c->events) cudaEventDestroy(ev);
   free_bounded(c);
-  ns_sweep_release(c);
+  if (c->owns_stream) cudaStreamDestroy(c->st);
   delete c;
 }
 

@@ -21,6 +21,7 @@ struct ns_ctx {
   size_t field = 0;              // elements of one [batch][5][cells] field
   double nu_split[3] = {1.0, 1.0, 1.0};   // added-viscosity factors: rho, rho u, rho E
   int nu_cap = 0;                         // hold nu at the explicit limit (ns_set_viscosity_cap)
+  int pipeline = -1;                      // pipelined stride sweeps: 1 on, 0 off, -1 NS_PIPELINE
   // stage buffers of the stage type (double in FP64 mode, float in MIXED mode):
   // float mirrors of w and lambda, stage states W2..W4, two seeds, the stage-product
   // (or RK increment) sum and the seed sum
@@ -55,6 +56,12 @@ struct ns_ctx {
   double* bd[4] = {};                // padded FP64: state, output, source, transposed product
   double* ba[3] = {};                // FP64: seed, next seed, stage-product sum
   void* bsig = nullptr;              // padded sigma_1 (double in FP64 contexts)
+  // the replay context of a pipelined stride sweep (created on first use): the same box
+  // and parameters, its own stage buffers and stream; it reports into this context's
+  // error word
+  ns_ctx* rctx = nullptr;
+  unsigned* own_err = nullptr;       // a replay context's own error word (err is its owner's)
+  bool owns_stream = false;          // st was created by the library (a replay context)
   bool bounded() const { return bc.inout || bc.walls; }
 };
 

@@ -330,13 +330,33 @@ bool file_io(int fd, void* buf, size_t n, long long off, bool write) {
 // four stage-type fields per step of the segment being reversed (the mirror of w^n and
 // the stage states W2..W4 computed when the segment was replayed), so that the adjoint
 // of a replayed step neither recomputes its stages nor converts its state.
+// pool, keep2: a pipelined stride sweep's second set of kept entries and its two sets of
+// k-1 replayed states (the forward pass's buffers hold the last segment's).
 struct Layout {
-  size_t state, lam, sig, nu, scal, feat, stage, mir, lmir, keep, sums, total;
+  size_t state, lam, sig, nu, scal, feat, stage, mir, lmir, keep, sums, pool, keep2, total;
   int nbuf, nkeep;
 };
 
+// NS_PIPELINE=0 (or ns_set_pipeline(ctx, 0)) reverses the stride plan's segments one
+// after the other, each replay before its reversal, on the context's stream alone.
+bool pipeline_enabled() {
+  static const bool on = [] {
+    const char* e = getenv("NS_PIPELINE");
+    return !(e && e[0] == '0');
+  }();
+  return on;
+}
+
+// A stride sweep of at least two segments on a periodic box, without snapshot checksums,
+// replays segment i+1 on a second stream while segment i is reversed.
+bool pipelined(const ns_ctx* c, int nsteps, int schedule, int param, bool verify) {
+  const bool on = c->pipeline < 0 ? pipeline_enabled() : c->pipeline != 0;
+  return on && schedule == NS_CKPT_STRIDE && !c->bounded() && !verify && param >= 2 &&
+         nsteps - 1 >= param;
+}
+
 Layout layout_for(const ns_ctx* c, int slots_used, bool closure, int schedule, int param, int host_slots = 0,
-                  bool verify = false) {
+                  bool verify = false, bool pipe = false) {
   // a bounded box forms its stage states inside its own step calls: nothing is kept
   if (c->bounded()) schedule = -1;
   Layout L;
@@ -359,7 +379,10 @@ Layout layout_for(const ns_ctx* c, int slots_used, bool closure, int schedule, i
   L.keep = (size_t)L.nkeep * 4 * L.stage;
   // snapshot checksums: one per device slot and per host slot, and one to verify into
   L.sums = verify ? align256(sizeof(unsigned long long) * (size_t)(slots_used + host_slots + 1)) : 0;
-  L.total = L.state * L.nbuf + L.lam + L.sig + L.nu + L.scal + L.feat + L.mir + L.lmir + L.keep + L.sums;
+  L.pool = pipe ? (size_t)2 * (param - 1) * L.state : 0;
+  L.keep2 = pipe ? L.keep : 0;
+  L.total = L.state * L.nbuf + L.lam + L.sig + L.nu + L.scal + L.feat + L.mir + L.lmir + L.keep + L.sums + L.pool +
+            L.keep2;
   return L;
 }
 
@@ -386,7 +409,9 @@ size_t ns_run_arena_bytes(const ns_ctx* c, const ns_run_opts* o) {
   if (!c || !o) return 0;
   Planner P;
   if (make_plan(o->nsteps, o->schedule, o->param, P)) return 0;
-  return layout_for(c, P.maxlive, o->mlp != nullptr, o->schedule, o->param, P.maxhost, o->verify != 0).total;
+  return layout_for(c, P.maxlive, o->mlp != nullptr, o->schedule, o->param, P.maxhost, o->verify != 0,
+                    pipelined(c, o->nsteps, o->schedule, o->param, o->verify != 0))
+      .total;
 }
 
 size_t ns_run_host_bytes(const ns_ctx* c, const ns_run_opts* o) {
@@ -438,12 +463,23 @@ struct ns_sweep_state {
   int fd = -1;
   std::string path;
   void* staging = nullptr;
+  // pipelined stride sweep: the replay context, the two sets of replayed states and the
+  // second set of kept entries, the forward-pass buffer of each stored step, and the
+  // events that order the replay stream against the context's stream
+  bool pipe = false;
+  ns_ctx* rc = nullptr;
+  std::vector<double*> pool[2];
+  std::vector<char*> keep2;
+  std::vector<int> buf_of_step;
+  cudaEvent_t ev_fwd = nullptr, ev_rep[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};
   ~ns_sweep_state() {
     if (fd >= 0) {
       close(fd);
       unlink(path.c_str());
     }
     if (staging) cudaFreeHost(staging);
+    for (cudaEvent_t e : {ev_fwd, ev_rep[0], ev_rep[1], ev_free[0], ev_free[1]})
+      if (e) cudaEventDestroy(e);
   }
 };
 
@@ -453,6 +489,58 @@ void ns_sweep_release(ns_ctx* c) {
 }
 
 namespace {
+
+// Adjoint step n of the sweep on the context's stream: sigma_1 and the viscosity, the
+// objective's plane sums of w^n on the side stream (n >= 1), the four transposed stages
+// with the objective source folded in, and the energy.  w: the state w^n; mirror: its
+// float mirror or NULL; kept3: its kept stage states, or NULL to recompute them.
+int adjoint_at(ns_ctx* c, ns_sweep_state& S, int n, const double* w, const void* mirror, const void* const* kept3,
+               double*& lam_cur, double*& lam_nxt, double* sbar, double* energy, double* sigma_stats) {
+  const int B = c->g.batch;
+  const double wN = 1.0 / S.o.nsteps;
+  const bool need_sigma = S.o.lambda > 0.0 || S.o.record_sigma || S.o.mlp;
+  int r;
+  const float* nup = nullptr;
+  const double* nudp = nullptr;
+  // the objective of w^n (n >= 1): its plane sums on the side stream, concurrent with
+  // sigma_1, its source folded into the last transposed stage of this step
+  ns_obj_src obj{};
+  if (n >= 1 && (r = ns_i_objective_sum_forked(c, w, wN, S.jtmp, &obj))) return r;
+  if (need_sigma && S.f64nu) {
+    double* stats = S.o.record_sigma && sigma_stats ? sigma_stats + (size_t)n * 2 * B : nullptr;
+    const bool rule = S.o.lambda > 0.0;
+    if ((r = ns_i_sigma1_f64(c, w, (double*)S.sig, stats, S.o.lambda, S.o.tau,
+                             rule ? (double*)S.nu : nullptr)))
+      return r;
+    if (rule) nudp = (const double*)S.nu;
+  } else if (need_sigma) {
+    double* stats = S.o.record_sigma && sigma_stats ? sigma_stats + (size_t)n * 2 * B : nullptr;
+    // the sigma_1 rule's viscosity comes out of the same launch as sigma_1
+    const bool rule = !S.o.mlp && S.o.lambda > 0.0;
+    if ((r = ns_i_sigma1(c, w, mirror, S.sig, stats, S.o.lambda, S.o.tau, rule ? S.nu : nullptr)))
+      return r;
+    if (S.o.mlp) {
+      if ((r = ns_i_mlp_features(c, w, mirror, S.feat))) return r;
+      if ((r = ns_mlp_infer(c, S.o.mlp, S.feat, S.sig, S.o.lambda, S.nu))) return r;
+      nup = S.nu;
+    } else if (rule) {
+      nup = S.nu;
+    }
+  }
+  if (n >= 1 && (r = ns_i_objective_join(c))) return r;
+  if ((r = ns_i_adjoint(c, w, mirror, kept3, S.s, lam_cur,
+                        S.lamf_valid ? S.lamf_cur : nullptr, nup, lam_nxt, S.lamf_nxt, sbar, nudp,
+                        n >= 1 ? &obj : nullptr)))
+    return r;
+  std::swap(lam_cur, lam_nxt);
+  std::swap(S.lamf_cur, S.lamf_nxt);
+  S.lamf_valid = S.lamf_cur != nullptr;
+  if (S.o.record_energy && energy &&
+      (r = ns_i_energy(c, w, mirror, lam_cur, S.lamf_valid ? S.lamf_cur : nullptr,
+                       energy + (size_t)n * B)))
+    return r;
+  return NS_OK;
+}
 
 // Run actions [S.pos, end) until (not including) the first action with op == stop_op
 // (stop_op = 0: to the end).  lam_cur/lam_nxt, sbar, energy, sigma_stats are used by
@@ -647,50 +735,113 @@ int run_actions(ns_ctx* c, ns_sweep_state& S, int stop_op, double*& lam_cur, dou
           kept = true;
           if (S.mixed) mirror = E[0];
         }
-        const float* nup = nullptr;
-        const double* nudp = nullptr;
-        // the objective of w^n (n >= 1): its plane sums on the side stream, concurrent with
-        // sigma_1, its source folded into the last transposed stage of this step
-        ns_obj_src obj{};
-        if (A.a >= 1 && (r = ns_i_objective_sum_forked(c, ptr(S.cur), wN, S.jtmp, &obj))) return r;
-        if (need_sigma && S.f64nu) {
-          double* stats = S.o.record_sigma && sigma_stats ? sigma_stats + (size_t)A.a * 2 * B : nullptr;
-          const bool rule = S.o.lambda > 0.0;
-          if ((r = ns_i_sigma1_f64(c, ptr(S.cur), (double*)S.sig, stats, S.o.lambda, S.o.tau,
-                                   rule ? (double*)S.nu : nullptr)))
-            return r;
-          if (rule) nudp = (const double*)S.nu;
-        } else if (need_sigma) {
-          double* stats = S.o.record_sigma && sigma_stats ? sigma_stats + (size_t)A.a * 2 * B : nullptr;
-          // the sigma_1 rule's viscosity comes out of the same launch as sigma_1
-          const bool rule = !S.o.mlp && S.o.lambda > 0.0;
-          if ((r = ns_i_sigma1(c, ptr(S.cur), mirror, S.sig, stats, S.o.lambda, S.o.tau, rule ? S.nu : nullptr)))
-            return r;
-          if (S.o.mlp) {
-            if ((r = ns_i_mlp_features(c, ptr(S.cur), mirror, S.feat))) return r;
-            if ((r = ns_mlp_infer(c, S.o.mlp, S.feat, S.sig, S.o.lambda, S.nu))) return r;
-            nup = S.nu;
-          } else if (rule) {
-            nup = S.nu;
-          }
-        }
-        if (A.a >= 1 && (r = ns_i_objective_join(c))) return r;
-        if ((r = ns_i_adjoint(c, ptr(S.cur), mirror, kept ? kept3 : nullptr, S.s, lam_cur,
-                              S.lamf_valid ? S.lamf_cur : nullptr, nup, lam_nxt, S.lamf_nxt, sbar, nudp,
-                              A.a >= 1 ? &obj : nullptr)))
-          return r;
-        std::swap(lam_cur, lam_nxt);
-        std::swap(S.lamf_cur, S.lamf_nxt);
-        S.lamf_valid = S.lamf_cur != nullptr;
-        if (S.o.record_energy && energy &&
-            (r = ns_i_energy(c, ptr(S.cur), mirror, lam_cur, S.lamf_valid ? S.lamf_cur : nullptr,
-                             energy + (size_t)A.a * B)))
+        if ((r = adjoint_at(c, S, A.a, ptr(S.cur), mirror, kept ? kept3 : nullptr, lam_cur, lam_nxt, sbar, energy,
+                            sigma_stats)))
           return r;
         break;
       }
       default: return NS_ERR_ARG;
     }
   }
+  return NS_OK;
+}
+
+// The replay context of c: created on first use with c's parameters and a stream of its
+// own, reporting into c's error word; its coefficients are refreshed from c (dt may have
+// changed) at every sweep.
+int replay_context(ns_ctx* c, ns_ctx** out) {
+  if (!c->rctx) {
+    cudaStream_t rs = nullptr;
+    if (cudaStreamCreateWithFlags(&rs, cudaStreamNonBlocking) != cudaSuccess) return NS_ERR_CUDA;
+    ns_ctx* r = nullptr;
+    const int e = ns_create(&c->p, (void*)rs, &r);
+    if (e != NS_OK) {
+      cudaStreamDestroy(rs);
+      return e;
+    }
+    r->owns_stream = true;
+    r->own_err = r->err;
+    r->err = c->err;
+    r->g.dbg_err = c->err;
+    c->rctx = r;
+  }
+  ns_ctx* r = c->rctx;
+  r->p = c->p;
+  r->cd = c->cd;
+  r->cf = c->cf;
+  r->cx = c->cx;
+  *out = r;
+  return NS_OK;
+}
+
+// The stride plan's backward pass, pipelined.  Segment 0 is the last one, whose states
+// and kept stages the forward pass left; segment i >= 1 starts at alast - i k and is
+// replayed on the replay context's stream into state set and kept-entry set i % 2 while
+// segment i-1 is reversed on the context's stream.  A replay waits until the reversal two
+// segments back has released its set (ev_free); a reversal waits for its replay (ev_rep).
+// Every launch is the one the sequential plan makes, so the bits are the same.
+int run_pipelined(ns_ctx* c, ns_sweep_state& S, double*& lam_cur, double*& lam_nxt, double* sbar, double* energy,
+                  double* sigma_stats) {
+  const int N = S.o.nsteps, k = S.o.param;
+  const int alast = ((N - 1) / k) * k;
+  const int nseg = alast / k + 1;
+  ns_ctx* rc = S.rc;
+  if (S.seg != alast) return NS_ERR_ARG;   // the forward pass keeps the last segment
+  // no replay reads a checkpoint before the forward pass and the source are done
+  if (cudaEventRecord(S.ev_fwd, c->st) != cudaSuccess || cudaStreamWaitEvent(rc->st, S.ev_fwd, 0) != cudaSuccess)
+    return NS_ERR_CUDA;
+  auto state_of = [&](int i, int n) -> const double* {
+    if (n == 0) return S.w0;
+    if (i == 0 || n % k == 0) return S.buf[S.buf_of_step[n]];
+    return S.pool[i % 2][n % k - 1];
+  };
+  auto entry = [&](int i, int e) -> char** { return (i % 2 == 0 ? &S.keep[0] : &S.keep2[0]) + (size_t)e * 4; };
+  auto replay = [&](int i) -> int {
+    Phase ph("ns replay");
+    const int a = alast - i * k, p = i % 2;
+    if (i >= 2 && cudaStreamWaitEvent(rc->st, S.ev_free[p], 0) != cudaSuccess) return NS_ERR_CUDA;
+    const double* w = state_of(i, a);
+    void* in_m = nullptr;
+    if (S.mixed) {
+      in_m = entry(i, 0)[0];
+      if (ns::launch_to_float(w, (float*)in_m, c->field, rc->st) != cudaSuccess) return NS_ERR_CUDA;
+    }
+    for (int e = 0; e < k - 1; ++e) {   // step a + e, into state a + e + 1
+      char** E = entry(i, e);
+      void* out_m = S.mixed ? entry(i, e + 1)[0] : nullptr;
+      void* keep3[3] = {E[1], E[2], E[3]};
+      double* wo = S.pool[p][e];
+      const int r = ns_i_primal(rc, w, in_m, S.s, wo, out_m, keep3);
+      if (r) return r;
+      w = wo;
+      in_m = out_m;
+    }
+    return cudaEventRecord(S.ev_rep[p], rc->st) == cudaSuccess ? NS_OK : NS_ERR_CUDA;
+  };
+  auto reverse = [&](int i) -> int {
+    Phase ph("ns adjoint step");
+    const int a = alast - i * k, b = std::min(a + k, N), p = i % 2;
+    if (i >= 1 && cudaStreamWaitEvent(c->st, S.ev_rep[p], 0) != cudaSuccess) return NS_ERR_CUDA;
+    for (int n = b - 1; n >= a; --n) {
+      const int e = n - a;
+      char** E = entry(i, e);
+      // the replay forms the stages of every step but the segment's last one
+      const bool kept = i == 0 ? S.has_stages[e] != 0 : e < k - 1;
+      const bool has_m = i == 0 ? S.has_mirror[e] != 0 : true;
+      const void* kept3[3] = {E[1], E[2], E[3]};
+      const void* mirror = S.mixed && has_m ? E[0] : nullptr;
+      const int r = adjoint_at(c, S, n, state_of(i, n), mirror, kept ? kept3 : nullptr, lam_cur, lam_nxt, sbar,
+                               energy, sigma_stats);
+      if (r) return r;
+    }
+    return cudaEventRecord(S.ev_free[p], c->st) == cudaSuccess ? NS_OK : NS_ERR_CUDA;
+  };
+  int r;
+  for (int i = 0; i < nseg; ++i) {
+    if (i + 1 < nseg && (r = replay(i + 1))) return r;
+    if ((r = reverse(i))) return r;
+  }
+  S.pos = S.P.acts.size();
   return NS_OK;
 }
 
@@ -714,7 +865,9 @@ static int forward_run_impl(ns_ctx* c, const double* w0, const double* s, const 
     delete S;
     return r;
   }
-  S->L = layout_for(c, S->P.maxlive, o->mlp != nullptr, o->schedule, o->param, S->P.maxhost, o->verify != 0);
+  S->pipe = pipelined(c, o->nsteps, o->schedule, o->param, o->verify != 0);
+  S->L = layout_for(c, S->P.maxlive, o->mlp != nullptr, o->schedule, o->param, S->P.maxhost, o->verify != 0,
+                    S->pipe);
   if (arena_bytes < S->L.total) {
     delete S;
     return NS_ERR_BUDGET;
@@ -770,6 +923,24 @@ static int forward_run_impl(ns_ctx* c, const double* w0, const double* s, const 
   for (size_t i = 0; i < S->keep.size(); ++i) S->keep[i] = q + i * S->L.stage;
   q += S->L.keep;
   S->sums = S->L.sums ? (unsigned long long*)q : nullptr;
+  q += S->L.sums;
+  if (S->pipe) {
+    for (int p = 0; p < 2; ++p)
+      for (int i = 0; i < o->param - 1; ++i) {
+        S->pool[p].push_back((double*)q);
+        q += S->L.state;
+      }
+    S->keep2.resize(S->keep.size());
+    for (size_t i = 0; i < S->keep2.size(); ++i) S->keep2[i] = q + i * S->L.stage;
+    q += S->L.keep2;
+    int e = replay_context(c, &S->rc);
+    for (cudaEvent_t* ev : {&S->ev_fwd, &S->ev_rep[0], &S->ev_rep[1], &S->ev_free[0], &S->ev_free[1]})
+      if (e == NS_OK && cudaEventCreateWithFlags(ev, cudaEventDisableTiming) != cudaSuccess) e = NS_ERR_CUDA;
+    if (e != NS_OK) {
+      delete S;
+      return e;
+    }
+  }
   S->has_mirror.assign(S->L.nkeep, 0);
   S->has_stages.assign(S->L.nkeep, 0);
   S->mixed = c->p.precision == NS_MIXED;
@@ -808,7 +979,19 @@ int ns_backward_run(ns_ctx* c, double* lam0, double* sbar, double* energy, doubl
   S.forward_done = false;   // a plan is reversed once
   c->pending_gen = 0;
   S.in_backward = true;
-  int r = run_actions(c, S, 0, lam_cur, lam_nxt, sbar, energy, sigma_stats);
+  int r;
+  if (S.pipe) {
+    // the forward pass's buffer of every stored step (nothing is freed before the source)
+    S.buf_of_step.assign(N, -1);
+    for (size_t i = 0; i < S.pos && i < S.P.acts.size(); ++i)
+      if (S.P.acts[i].op == NS_OP_STORE) S.buf_of_step[S.P.acts[i].a] = S.slot_buf[S.P.acts[i].b];
+    // the source at step N, then the segments (the plan's remaining actions describe the
+    // same steps in sequence)
+    r = run_actions(c, S, NS_OP_ADJOINT, lam_cur, lam_nxt, sbar, energy, sigma_stats);
+    if (!r) r = run_pipelined(c, S, lam_cur, lam_nxt, sbar, energy, sigma_stats);
+  } else {
+    r = run_actions(c, S, 0, lam_cur, lam_nxt, sbar, energy, sigma_stats);
+  }
   if (r) return r;
   if (lam_cur != lam0 &&
       cudaMemcpyAsync(lam0, lam_cur, fbytes, cudaMemcpyDeviceToDevice, c->st) != cudaSuccess)
@@ -834,6 +1017,12 @@ int ns_adjoint_run(ns_ctx* c, const double* w0, const double* s, const ns_run_op
 }
 
 long long ns_sweep_generation(const ns_ctx* c) { return c ? c->pending_gen : 0; }
+
+int ns_set_pipeline(ns_ctx* c, int on) {
+  if (!c) return NS_ERR_ARG;
+  c->pipeline = on ? 1 : 0;
+  return NS_OK;
+}
 
 // One ns_adjoint_run recorded as a CUDA graph: the executable graph, the context whose
 // stream replays it, and the kernel launches it holds.
