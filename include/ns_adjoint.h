@@ -244,7 +244,9 @@ int ns_max_wave_speed(ns_ctx* ctx, const double* w, double* out);
  *                   snapshot is copied out once in the forward pass and back once when
  *                   its segment is replayed; only the replayed segment's states live
  *                   in device memory (and, from the forward pass, the last segment's,
- *                   which is not replayed).  The copies run on the context's stream, so a
+ *                   which is not replayed).  Pipelined like NS_CKPT_STRIDE (each replay
+ *                   copies its snapshot back on the replay stream); ns_set_pipeline(ctx, 0)
+ *                   keeps the device footprint smallest.  The copies run on the context's stream, so a
  *                   sweep gives the same bits as NS_CKPT_STRIDE.  On a Grace-hosted GPU
  *                   they cross NVLink-C2C.
  *   NS_CKPT_STRIDE_DISK  the plan of NS_CKPT_STRIDE_HOST with the snapshots in a file

@@ -331,7 +331,8 @@ bool file_io(int fd, void* buf, size_t n, long long off, bool write) {
 // the stage states W2..W4 computed when the segment was replayed), so that the adjoint
 // of a replayed step neither recomputes its stages nor converts its state.
 // pool, keep2: a pipelined stride sweep's second set of kept entries and its two sets of
-// k-1 replayed states (the forward pass's buffers hold the last segment's).
+// k-1 replayed states, plus the segment's snapshot for the host tier (the forward pass's
+// buffers hold the last segment's).
 struct Layout {
   size_t state, lam, sig, nu, scal, feat, stage, mir, lmir, keep, sums, pool, keep2, total;
   int nbuf, nkeep;
@@ -348,11 +349,12 @@ bool pipeline_enabled() {
 }
 
 // A stride sweep of at least two segments on a periodic box, without snapshot checksums,
-// replays segment i+1 on a second stream while segment i is reversed.
+// with its snapshots in device or host memory (not in a file, whose accesses wait on the
+// stream), replays segment i+1 on a second stream while segment i is reversed.
 bool pipelined(const ns_ctx* c, int nsteps, int schedule, int param, bool verify) {
   const bool on = c->pipeline < 0 ? pipeline_enabled() : c->pipeline != 0;
-  return on && schedule == NS_CKPT_STRIDE && !c->bounded() && !verify && param >= 2 &&
-         nsteps - 1 >= param;
+  return on && (schedule == NS_CKPT_STRIDE || schedule == NS_CKPT_STRIDE_HOST) && !c->bounded() && !verify &&
+         param >= 2 && nsteps - 1 >= param;
 }
 
 Layout layout_for(const ns_ctx* c, int slots_used, bool closure, int schedule, int param, int host_slots = 0,
@@ -379,7 +381,8 @@ Layout layout_for(const ns_ctx* c, int slots_used, bool closure, int schedule, i
   L.keep = (size_t)L.nkeep * 4 * L.stage;
   // snapshot checksums: one per device slot and per host slot, and one to verify into
   L.sums = verify ? align256(sizeof(unsigned long long) * (size_t)(slots_used + host_slots + 1)) : 0;
-  L.pool = pipe ? (size_t)2 * (param - 1) * L.state : 0;
+  // a host-tier set also holds the device copy of its segment's snapshot
+  L.pool = pipe ? (size_t)2 * (param - 1 + (schedule == NS_CKPT_STRIDE_HOST ? 1 : 0)) * L.state : 0;
   L.keep2 = pipe ? L.keep : 0;
   L.total = L.state * L.nbuf + L.lam + L.sig + L.nu + L.scal + L.feat + L.mir + L.lmir + L.keep + L.sums + L.pool +
             L.keep2;
@@ -471,6 +474,7 @@ struct ns_sweep_state {
   std::vector<double*> pool[2];
   std::vector<char*> keep2;
   std::vector<int> buf_of_step;
+  std::vector<int> hslot_of_step;        // host tier: the host slot of each snapshot
   cudaEvent_t ev_fwd = nullptr, ev_rep[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};
   ~ns_sweep_state() {
     if (fd >= 0) {
@@ -790,9 +794,11 @@ int run_pipelined(ns_ctx* c, ns_sweep_state& S, double*& lam_cur, double*& lam_n
   // no replay reads a checkpoint before the forward pass and the source are done
   if (cudaEventRecord(S.ev_fwd, c->st) != cudaSuccess || cudaStreamWaitEvent(rc->st, S.ev_fwd, 0) != cudaSuccess)
     return NS_ERR_CUDA;
+  const bool host = S.o.schedule == NS_CKPT_STRIDE_HOST;
   auto state_of = [&](int i, int n) -> const double* {
     if (n == 0) return S.w0;
-    if (i == 0 || n % k == 0) return S.buf[S.buf_of_step[n]];
+    if (i == 0) return S.buf[S.buf_of_step[n]];
+    if (n % k == 0) return host ? S.pool[i % 2][k - 1] : S.buf[S.buf_of_step[n]];
     return S.pool[i % 2][n % k - 1];
   };
   auto entry = [&](int i, int e) -> char** { return (i % 2 == 0 ? &S.keep[0] : &S.keep2[0]) + (size_t)e * 4; };
@@ -800,6 +806,13 @@ int run_pipelined(ns_ctx* c, ns_sweep_state& S, double*& lam_cur, double*& lam_n
     Phase ph("ns replay");
     const int a = alast - i * k, p = i % 2;
     if (i >= 2 && cudaStreamWaitEvent(rc->st, S.ev_free[p], 0) != cudaSuccess) return NS_ERR_CUDA;
+    if (host && a > 0) {
+      // the segment's snapshot back from its host slot into the set's last buffer
+      const char* hp = (const char*)S.o.host_arena + (size_t)S.hslot_of_step[a] * S.L.state;
+      if (cudaMemcpyAsync(S.pool[p][k - 1], hp, c->field * sizeof(double), cudaMemcpyHostToDevice, rc->st) !=
+          cudaSuccess)
+        return NS_ERR_CUDA;
+    }
     const double* w = state_of(i, a);
     void* in_m = nullptr;
     if (S.mixed) {
@@ -925,8 +938,9 @@ static int forward_run_impl(ns_ctx* c, const double* w0, const double* s, const 
   S->sums = S->L.sums ? (unsigned long long*)q : nullptr;
   q += S->L.sums;
   if (S->pipe) {
+    const int per_set = o->param - 1 + (o->schedule == NS_CKPT_STRIDE_HOST ? 1 : 0);
     for (int p = 0; p < 2; ++p)
-      for (int i = 0; i < o->param - 1; ++i) {
+      for (int i = 0; i < per_set; ++i) {
         S->pool[p].push_back((double*)q);
         q += S->L.state;
       }
@@ -983,8 +997,12 @@ int ns_backward_run(ns_ctx* c, double* lam0, double* sbar, double* energy, doubl
   if (S.pipe) {
     // the forward pass's buffer of every stored step (nothing is freed before the source)
     S.buf_of_step.assign(N, -1);
-    for (size_t i = 0; i < S.pos && i < S.P.acts.size(); ++i)
-      if (S.P.acts[i].op == NS_OP_STORE) S.buf_of_step[S.P.acts[i].a] = S.slot_buf[S.P.acts[i].b];
+    S.hslot_of_step.assign(N, -1);
+    for (size_t i = 0; i < S.pos && i < S.P.acts.size(); ++i) {
+      const ns_action& A = S.P.acts[i];
+      if (A.op == NS_OP_STORE) S.buf_of_step[A.a] = S.slot_buf[A.b];
+      if (A.op == NS_OP_STORE_HOST) S.hslot_of_step[A.a] = A.b;
+    }
     // the source at step N, then the segments (the plan's remaining actions describe the
     // same steps in sequence)
     r = run_actions(c, S, NS_OP_ADJOINT, lam_cur, lam_nxt, sbar, energy, sigma_stats);

@@ -183,7 +183,10 @@ def test_host_snapshots_give_the_stride_bits(prec):
     # the snapshots before the last segment, whose states stay on the device
     assert S.host_bytes(probe) == ((N - 1) // k - 1) * field
     assert S.host_bytes(S.run_opts(N, api.NS_CKPT_STRIDE, k)) == 0
-    assert S.arena_bytes(probe) < S.arena_bytes(S.run_opts(N, api.NS_CKPT_STRIDE, k, lam_coef))
+    # no snapshot in the device arena: smaller than the stride arena once the snapshots
+    # outweigh the host tier's device copy of one per pipelined set (40 steps, 9 snapshots)
+    assert (S.arena_bytes(S.run_opts(40, api.NS_CKPT_STRIDE_HOST, k, lam_coef)) <
+            S.arena_bytes(S.run_opts(40, api.NS_CKPT_STRIDE, k, lam_coef)))
     for pinned in (True, False):
         host = torch.empty(S.host_bytes(probe), dtype=torch.uint8, pin_memory=pinned)
         opts = S.run_opts(N, api.NS_CKPT_STRIDE_HOST, k, lam_coef, 0.0, True, True, host_arena=host)
@@ -215,7 +218,7 @@ def test_host_snapshots_give_the_stride_bits(prec):
 @pytest.mark.parametrize("prec", [0, 1])
 def test_verified_snapshots_keep_the_bits_and_a_corrupted_host_snapshot_is_reported(prec):
     """With verify on, every schedule gives the unverified sweep's bits and a clear error
-    word (the verified stride sweep runs its segments in sequence, the unverified one
+    word (the verified stride sweeps run their segments in sequence, the unverified ones
     pipelined); a byte flipped in a host-tier snapshot between the forward and the backward
     half (host memory, the caller's arena) is reported as NS_ERR_CORRUPT when the
     snapshot comes back."""
@@ -232,9 +235,10 @@ def test_verified_snapshots_keep_the_bits_and_a_corrupted_host_snapshot_is_repor
         if sched == api.NS_CKPT_STRIDE_HOST:
             host = torch.zeros(S.host_bytes(S.run_opts(N, sched, prm)), dtype=torch.uint8, pin_memory=True)
         opts = S.run_opts(N, sched, prm, host_arena=host, verify=True)
-        if sched != api.NS_CKPT_STRIDE:
-            # the checksums' region; a verified stride sweep is not pipelined, so it has no
-            # second set of replayed states and its arena is the smaller one
+        if sched == api.NS_CKPT_REVOLVE:
+            # the checksums' region; a verified stride sweep (device or host tier) is not
+            # pipelined, so it has no second set of replayed states and its arena is the
+            # smaller one
             assert S.arena_bytes(opts) > S.arena_bytes(S.run_opts(N, sched, prm, host_arena=host))
         arena = torch.empty(S.arena_bytes(opts), dtype=torch.uint8, device="cuda")
         S.adjoint_run(dev(w0), opts, arena, J, lam)
