@@ -153,6 +153,36 @@ def test_closure_inside_the_sweep_matches_oracle():
     assert rel_l2(host(lam0), ref) < 1e-5
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_closure_in_a_pipelined_stride_sweep_gives_the_sequential_bits(prec):
+    """The learned closure inside a stride sweep of several segments: the pipelined sweep
+    (the next segment replayed on a second stream) and the same sweep with its segments in
+    sequence give the same bits."""
+    api = _api()
+    C = _closure()
+    w0 = synth.isentropic_vortex(40, 12, 1, noise=1e-3, seed=6)
+    P = params_for(w0, mu=1e-3, dt=4e-3)
+    N = 11
+    S = make_solver(api, w0, P, prec)
+    p = ML.init_params(12)
+    p["b3"] = np.array(0.5)
+    net = C.Network(S, p)
+    opts = S.run_opts(N, api.NS_CKPT_STRIDE, 3, 0.3, 0.0, True, True, net.blob)
+    out = []
+    for on in (True, False):
+        S.set_pipeline(on)
+        arena = torch.empty(S.arena_bytes(opts), dtype=torch.uint8, device="cuda")
+        J = torch.empty(1, dtype=torch.float64, device="cuda")
+        lam0 = torch.empty(w0.shape, dtype=torch.float64, device="cuda")
+        E = torch.zeros((N + 1, 1), dtype=torch.float64, device="cuda")
+        S.adjoint_run(dev(w0), opts, arena, J, lam0, energy=E)
+        torch.cuda.synchronize()
+        assert S.last_error() == 0
+        out.append((J, lam0, E))
+    for a, b in zip(*out):
+        assert torch.equal(a, b)
+
+
 def test_judge_learned_closure_against_sigma1_rule():
     """Train on adjoint data of two vortex boxes, then judge on a third: gradient error
     of each closure against the exact short-horizon FP64 adjoint at the same adjoint
