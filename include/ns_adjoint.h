@@ -333,7 +333,9 @@ typedef struct {
 } ns_run_opts;
 
 /* Device bytes the caller must provide as the arena of ns_adjoint_run (state slots,
- * two working states, one adjoint field, sigma_1 and nu fields, scalars). */
+ * two working states, one adjoint field, sigma_1 and nu fields, scalars; for a stride
+ * plan one segment's kept stage states and mirrors, and when the sweep is pipelined a
+ * second set of them with param - 1 segment states per set, see ns_set_pipeline). */
 size_t ns_run_arena_bytes(const ns_ctx* ctx, const ns_run_opts* o);
 
 /* Host bytes of the snapshot arena of an NS_CKPT_STRIDE_HOST or NS_CKPT_REVOLVE_HOST sweep
